@@ -1,0 +1,604 @@
+/*
+ * mlsd_oracle.c -- plain, slow FP64 CPU oracle of the seamless multiscale
+ * method for passive advection-diffusion (Lee & Engquist).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or
+ * call this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code, header, table or constant generator
+ * with the CUDA library.
+ *
+ * Conventions (the library's, restated here independently):
+ *   domain [0, 2*pi)^2, periodic; fields are stored row-major [b][a] with a
+ *   along x1 (fast) and b along x2 (slow).
+ *   psi(x) = sum_modes Re[(re + i im) exp(i k.x)] over a Hermitian mode list.
+ *
+ * Every routine below follows one step of the paper:
+ *   orc_band_of         -- Fourier decomposition, Sec. 3.1 (psi_11, psi_12,
+ *                          psi_21, psi_2, repeated with alpha^2, alpha^3 ...)
+ *   orc_patch_psi       -- local domains of the level hierarchy, Sec. 3
+ *   orc_velocity        -- v = (-d psi/dx2, d psi/dx1), Sec. 2.1
+ *   orc_patch_k         -- numerical homogenization K[psi, B; D]: two linear
+ *                          reconstructions with orthogonal gradients, periodic
+ *                          fluctuation, evolution to quasi-stationarity, flux
+ *                          averaging (HMM steps 1-3, Sec. 2.2)
+ *   orc_offdiag_q / orc_offdiag_apply
+ *                       -- Algorithm 1 (shear closed form per line, harmonic
+ *                          mean across lines) and Algorithm 2 (sum of the two
+ *                          off-diagonal effects minus the common base)
+ *   orc_chain           -- Algorithm 3 applied level by level, finest first
+ *   orc_macro_run       -- macro solver for U_t = div(K grad U), Eq. (homo)
+ *   orc_dns_run         -- direct simulation of Eq. (model) on the full grid
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1: Fourier decomposition.                                          */
+/*                                                                           */
+/* Level l (1-based) owns wavenumber magnitudes in [lo_l, e_l) where          */
+/* lo_1 = 0 and lo_l = e_{l-1} (the paper's "<= alpha" read with             */
+/* lower-inclusive integer edges).  For a mode with la = level(|k1|) and     */
+/* lb = level(|k2|):                                                         */
+/*   la == lb  -> diagonal part of level la            (psi_11 at that level)*/
+/*   la <  lb  -> off-diagonal psi_12 of level la (|k1| low, |k2| high)      */
+/*   la >  lb  -> off-diagonal psi_21 of level lb (|k1| high, |k2| low)      */
+/* A magnitude at or above the last edge counts as "above every level".      */
+/* kind: 0 diagonal, 1 psi_12, 2 psi_21, -1 dropped (both parts too fine).   */
+/* ------------------------------------------------------------------------ */
+static int level_of_mag(int m, int n_levels, const double *edges)
+{
+    for (int l = 1; l <= n_levels; ++l) {
+        double lo = (l == 1) ? 0.0 : edges[l - 1];
+        if ((double)m >= lo && (double)m < edges[l]) return l;
+    }
+    return n_levels + 1;
+}
+
+void orc_band_of(int n_modes, const int *k1, const int *k2, int n_levels,
+                 const double *edges, int *level, int *kind)
+{
+    for (int t = 0; t < n_modes; ++t) {
+        int la = level_of_mag(abs(k1[t]), n_levels, edges);
+        int lb = level_of_mag(abs(k2[t]), n_levels, edges);
+        if (la == lb) {
+            level[t] = la; kind[t] = (la <= n_levels) ? 0 : -1;
+        } else if (la < lb) {
+            level[t] = la; kind[t] = 1;
+        } else {
+            level[t] = lb; kind[t] = 2;
+        }
+        if (level[t] > n_levels) { level[t] = -1; kind[t] = -1; }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3: local domain of level l centred at macro node X_ij = (iH, jH).     */
+/* The patch has n x n nodes with spacing h = L / n on the lattice           */
+/* 2*pi*idx / Nl (Nl = 2*pi / h, an integer); its centre is the lattice      */
+/* node nearest to X_ij (ties rounded up) and node a sits at lattice index   */
+/* centre - n/2 + a.                                                         */
+/* ------------------------------------------------------------------------ */
+long orc_patch_origin(int i, int n_macro, long Nl, int n)
+{
+    /* nearest lattice index to i * Nl / n_macro, halves rounded up */
+    long c = (2L * (long)i * Nl + (long)n_macro) / (2L * (long)n_macro);
+    return c - n / 2;
+}
+
+static long pmod(long a, long m) { long r = a % m; return r < 0 ? r + m : r; }
+
+/* psi at lattice indices (gx, gy) of an Nl-point lattice, summed mode by mode */
+static double psi_at(int n_modes, const int *k1, const int *k2, const double *re,
+                     const double *im, const unsigned char *use, long Nl, long gx, long gy)
+{
+    double s = 0.0;
+    for (int t = 0; t < n_modes; ++t) {
+        if (use && !use[t]) continue;
+        long r = pmod((long)k1[t] * gx + (long)k2[t] * gy, Nl);   /* exact phase index */
+        double th = 2.0 * ORC_PI * (double)r / (double)Nl;
+        s += re[t] * cos(th) - im[t] * sin(th);
+    }
+    return s;
+}
+
+/* psi of the selected modes on the patch nodes, patch mean removed. */
+void orc_patch_psi(int n_modes, const int *k1, const int *k2, const double *re,
+                   const double *im, const unsigned char *use, long Nl, long ox, long oy,
+                   int n, double *psi)
+{
+    double mean = 0.0;
+    for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+            double p = psi_at(n_modes, k1, k2, re, im, use, Nl, ox + a, oy + b);
+            psi[(long)b * n + a] = p;
+            mean += p;
+        }
+    mean /= (double)n * (double)n;
+    for (long c = 0; c < (long)n * n; ++c) psi[c] -= mean;
+}
+
+/* Sec. 2.1: v = (-d psi/dx2, d psi/dx1) with central differences; indices  */
+/* wrap on the patch (periodic local problem).                               */
+void orc_velocity(int n, double h, const double *psi, double *v1, double *v2)
+{
+    for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+            int ap = (a + 1) % n, am = (a + n - 1) % n;
+            int bp = (b + 1) % n, bm = (b + n - 1) % n;
+            v1[b * n + a] = -(psi[bp * n + a] - psi[bm * n + a]) / (2.0 * h);
+            v2[b * n + a] = (psi[b * n + ap] - psi[b * n + am]) / (2.0 * h);
+        }
+}
+
+/* smallest eigenvalue of the symmetric 2x2 tensor (B11, B12, B22) */
+double orc_lambda_min(const double *B)
+{
+    double tr = B[0] + B[2];
+    double d = sqrt((B[0] - B[2]) * (B[0] - B[2]) + 4.0 * B[1] * B[1]);
+    return 0.5 * (tr - d);
+}
+
+/* Time step of the micro solver: CFL on advection and on diffusion, and     */
+/* never above the RK2 + central-advection stability bound                   */
+/* (8 lambda_min h^2 / vmax^4)^(1/3).  vmax = max(|v1| + |v2|).              */
+double orc_micro_dt(double h, double vmax, const double *B, double cfl)
+{
+    double dd = h * h / (2.0 * (B[0] + B[2]) + 4.0 * fabs(B[1]));
+    double dt = dd;
+    if (vmax > 0.0) {
+        double da = h / vmax;
+        if (da < dt) dt = da;
+    }
+    dt *= cfl;
+    if (vmax > 0.0) {
+        double ds = cbrt(8.0 * orc_lambda_min(B) * h * h / (vmax * vmax * vmax * vmax));
+        if (ds < dt) dt = ds;
+    }
+    return dt;
+}
+
+/* Quasi-stationarity window: relaxation time tau = L^2 / (4 pi^2 lambda_min)*/
+/* of the slowest patch mode; burn-in t_burn * tau, averaging t_avg * tau.   */
+void orc_micro_steps(double L, const double *B, double dt, double t_burn, double t_avg,
+                     long *n_burn, long *n_avg)
+{
+    double tau = L * L / (4.0 * ORC_PI * ORC_PI * orc_lambda_min(B));
+    *n_burn = (long)ceil(t_burn * tau / dt);
+    *n_avg = (long)ceil(t_avg * tau / dt);
+    if (*n_avg < 1) *n_avg = 1;
+}
+
+/* right-hand side f_j(w) of the corrector equation for gradient e_j         */
+static void corrector_rhs(int n, double h, const double *v1, const double *v2,
+                          const double *B, int j, const double *w, double *f)
+{
+    double g1 = (j == 1) ? 1.0 : 0.0, g2 = (j == 2) ? 1.0 : 0.0;
+    for (int b = 0; b < n; ++b) {
+        int bp = (b + 1) % n, bm = (b + n - 1) % n;
+        for (int a = 0; a < n; ++a) {
+            int ap = (a + 1) % n, am = (a + n - 1) % n;
+            double wc = w[b * n + a];
+            double d0x = (w[b * n + ap] - w[b * n + am]) / (2.0 * h);
+            double d0y = (w[bp * n + a] - w[bm * n + a]) / (2.0 * h);
+            double dxx = (w[b * n + ap] - 2.0 * wc + w[b * n + am]) / (h * h);
+            double dyy = (w[bp * n + a] - 2.0 * wc + w[bm * n + a]) / (h * h);
+            double dxy = (w[bp * n + ap] - w[bp * n + am] - w[bm * n + ap] + w[bm * n + am])
+                         / (4.0 * h * h);
+            f[b * n + a] = v1[b * n + a] * (d0x + g1) + v2[b * n + a] * (d0y + g2)
+                         + B[0] * dxx + 2.0 * B[1] * dxy + B[2] * dyy;
+        }
+    }
+}
+
+/* Exposed for the brute-force steady-state test: f_j(w) on a patch. */
+void orc_corrector_rhs(int n, double h, const double *psi, const double *B, int j,
+                       const double *w, double *f)
+{
+    double *v1 = malloc(sizeof(double) * n * n), *v2 = malloc(sizeof(double) * n * n);
+    orc_velocity(n, h, psi, v1, v2);
+    corrector_rhs(n, h, v1, v2, B, j, w, f);
+    free(v1); free(v2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.2 (HMM steps 1-3) and the K[psi, B; D] notation of Sec. 2.2:       */
+/* for each gradient G = e_j the reconstruction is u = G.x + w with w        */
+/* periodic on the patch, w(0) = 0; w is advanced with Heun's RK2 for        */
+/* n_burn + n_avg steps; after each of the last n_avg steps the spatial mean */
+/* of v_i w_j is added to S_ij.  The effective flux for G = e_j is           */
+/* P_j = B e_j + S_.j / n_avg, and K is its symmetric part:                  */
+/*   K11 = P_1,1   K22 = P_2,2   K12 = (P_1,2 + P_2,1) / 2.                  */
+/* Optional outputs: w_out[2][n][n] (final corrector fields), S_out[4] =     */
+/* time-averaged (S11, S21, S12, S22).                                       */
+/* ------------------------------------------------------------------------ */
+void orc_patch_k(int n, double h, const double *psi, const double *B, double dt,
+                 long n_burn, long n_avg, double *K, double *w_out, double *S_out)
+{
+    long nn = (long)n * n;
+    double *v1 = malloc(sizeof(double) * nn), *v2 = malloc(sizeof(double) * nn);
+    double *w = malloc(sizeof(double) * nn), *ws = malloc(sizeof(double) * nn);
+    double *f = malloc(sizeof(double) * nn);
+    double S[2][2] = {{0, 0}, {0, 0}};          /* S[i][j] = sum of mean(v_i w_j) */
+    orc_velocity(n, h, psi, v1, v2);
+    for (int j = 1; j <= 2; ++j) {
+        memset(w, 0, sizeof(double) * nn);
+        for (long s = 1; s <= n_burn + n_avg; ++s) {
+            corrector_rhs(n, h, v1, v2, B, j, w, f);
+            for (long c = 0; c < nn; ++c) ws[c] = w[c] + dt * f[c];
+            corrector_rhs(n, h, v1, v2, B, j, ws, f);
+            for (long c = 0; c < nn; ++c) w[c] = 0.5 * (w[c] + ws[c] + dt * f[c]);
+            if (s > n_burn) {
+                double m1 = 0.0, m2 = 0.0;
+                for (long c = 0; c < nn; ++c) { m1 += v1[c] * w[c]; m2 += v2[c] * w[c]; }
+                S[0][j - 1] += m1 / (double)nn;
+                S[1][j - 1] += m2 / (double)nn;
+            }
+        }
+        if (w_out) memcpy(w_out + (j - 1) * nn, w, sizeof(double) * nn);
+    }
+    double P11 = B[0] + S[0][0] / (double)n_avg;   /* P_1 = B e_1 + S_.1 */
+    double P21 = B[1] + S[1][0] / (double)n_avg;
+    double P12 = B[1] + S[0][1] / (double)n_avg;   /* P_2 = B e_2 + S_.2 */
+    double P22 = B[2] + S[1][1] / (double)n_avg;
+    K[0] = P11;
+    K[1] = 0.5 * (P21 + P12);
+    K[2] = P22;
+    if (S_out) {
+        S_out[0] = S[0][0] / n_avg; S_out[1] = S[1][0] / n_avg;
+        S_out[2] = S[0][1] / n_avg; S_out[3] = S[1][1] / n_avg;
+    }
+    free(v1); free(v2); free(w); free(ws); free(f);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 (per off-diagonal part): treat psi_12 (fine in x2) as a shear */
+/* on every patch column x1 = x_a and psi_21 (fine in x1) as a shear on      */
+/* every patch row x2 = x_b.  q is the line variance of the part, sampled at */
+/* r points per patch cell along the line, r = ceil(10 kmax L / (2 pi n)):   */
+/*   q12[a] = mean_s (psi12(x_a, y_s) - mean)^2,                             */
+/*   q21[b] = mean_s (psi21(x_s, y_b) - mean)^2.                             */
+/* Inputs: the level's mode list with part flags (kind 1 or 2).             */
+/* ------------------------------------------------------------------------ */
+static int line_refine(int n_modes, const int *kx, const unsigned char *use, double L, int n)
+{
+    int kmax = 0;
+    for (int t = 0; t < n_modes; ++t)
+        if (use[t] && abs(kx[t]) > kmax) kmax = abs(kx[t]);
+    double need = 10.0 * kmax * L / (2.0 * ORC_PI);
+    int r = (int)ceil(need / (double)n);
+    return r < 1 ? 1 : r;
+}
+
+void orc_offdiag_q(int n_modes, const int *k1, const int *k2, const double *re,
+                   const double *im, const unsigned char *use12, const unsigned char *use21,
+                   long Nl, long ox, long oy, int n, double L, double *q12, double *q21)
+{
+    int r12 = line_refine(n_modes, k2, use12, L, n);
+    int r21 = line_refine(n_modes, k1, use21, L, n);
+    int any12 = 0, any21 = 0;
+    for (int t = 0; t < n_modes; ++t) { any12 |= use12[t]; any21 |= use21[t]; }
+    for (int a = 0; a < n; ++a) {
+        q12[a] = 0.0;
+        if (!any12) continue;
+        /* column x_a = lattice index ox + a on the Nl lattice, i.e. index     */
+        /* (ox + a) * r12 on the refined lattice of Nl * r12 points; samples   */
+        /* y_s at refined indices oy * r12 + s, s = 0 .. n * r12 - 1           */
+        long m = (long)n * r12, Nr = Nl * r12;
+        double mean = 0.0, sq = 0.0;
+        double *g = malloc(sizeof(double) * m);
+        for (long s = 0; s < m; ++s) {
+            g[s] = psi_at(n_modes, k1, k2, re, im, use12, Nr, (ox + a) * (long)r12, oy * r12 + s);
+            mean += g[s];
+        }
+        mean /= (double)m;
+        for (long s = 0; s < m; ++s) sq += (g[s] - mean) * (g[s] - mean);
+        q12[a] = sq / (double)m;
+        free(g);
+    }
+    for (int b = 0; b < n; ++b) {
+        q21[b] = 0.0;
+        if (!any21) continue;
+        long m = (long)n * r21, Nr = Nl * r21;
+        double mean = 0.0, sq = 0.0;
+        double *g = malloc(sizeof(double) * m);
+        for (long s = 0; s < m; ++s) {
+            g[s] = psi_at(n_modes, k1, k2, re, im, use21, Nr, ox * r21 + s, (oy + b) * (long)r21);
+            mean += g[s];
+        }
+        mean /= (double)m;
+        for (long s = 0; s < m; ++s) sq += (g[s] - mean) * (g[s] - mean);
+        q21[b] = sq / (double)m;
+        free(g);
+    }
+}
+
+/* Algorithms 1 and 2 given the line variances:                             */
+/*   psi_12: K*11(x_a) = B11 + q12[a] / B22 (Eq. shearhomoY), then the      */
+/*           layered-medium harmonic mean across the columns;               */
+/*   psi_21: K*22(x_b) = B22 + q21[b] / B11 (Eq. shearhomoX), harmonic mean */
+/*           across the rows;                                               */
+/*   K_off = K[psi_12; B] + K[psi_21; B] - B.                               */
+/* B12 and the component along the layers pass through unchanged.          */
+void orc_offdiag_apply(int n, const double *q12, const double *q21, const double *B,
+                       double *Koff)
+{
+    double s1 = 0.0, s2 = 0.0;
+    for (int a = 0; a < n; ++a) s1 += 1.0 / (B[0] + q12[a] / B[2]);
+    for (int b = 0; b < n; ++b) s2 += 1.0 / (B[2] + q21[b] / B[0]);
+    double K12_11 = (double)n / s1;          /* K[psi_12; B] = diag(K12_11, B22) + B12 */
+    double K21_22 = (double)n / s2;          /* K[psi_21; B] = diag(B11, K21_22) + B12 */
+    Koff[0] = K12_11 + B[0] - B[0];
+    Koff[1] = B[1] + B[1] - B[1];
+    Koff[2] = B[2] + K21_22 - B[2];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Level description used by the chain: one entry per level.                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int n;          /* patch grid n x n */
+    long Nl;        /* lattice points per 2*pi: L = 2 pi n / Nl */
+} orc_level;
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 3, applied recursively from the finest level (L) to the        */
+/* coarsest (1), for a set of macro nodes:                                   */
+/*   B_1 = kappa I;  Koff_l = K_off,l(B_l);  B_{l+1} = Koff_l   (top-down)  */
+/*   K*_L = K[psi_L,diag ; K_off,L(B_L)]                                    */
+/*   for l = L-1 .. 1:  Knet = K*_{l+1} - Koff_l + B_l                      */
+/*                      K*_l = K[psi_l,diag ; K_off,l(Knet)]                */
+/*   K = K*_1                                                               */
+/* psi_l,diag is the diagonal band of level l; K_off,l is Algorithms 1-2     */
+/* with level l's off-diagonal parts (the identity when there are none).    */
+/* Outputs per node: K[3] and, optionally, the per-level K*_l [L][3].        */
+/* The time step and window of every patch solve follow orc_micro_dt and    */
+/* orc_micro_steps, unless n_burn_fixed / n_avg_fixed are positive.         */
+/* ------------------------------------------------------------------------ */
+void orc_chain(int n_modes, const int *k1, const int *k2, const double *re, const double *im,
+               int n_levels, const double *edges, const int *patch_n, const long *Nl,
+               int n_macro, double kappa, double cfl, double t_burn, double t_avg,
+               long n_burn_fixed, long n_avg_fixed,
+               int n_nodes, const int *node_i, const int *node_j,
+               double *K_out, double *Kstar_levels_out)
+{
+    int *lev = malloc(sizeof(int) * n_modes), *kind = malloc(sizeof(int) * n_modes);
+    orc_band_of(n_modes, k1, k2, n_levels, edges, lev, kind);
+
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = 0; p < n_nodes; ++p) {
+        unsigned char *ud = malloc(n_modes), *u12 = malloc(n_modes), *u21 = malloc(n_modes);
+        double (*Bl)[3] = malloc(sizeof(double) * 3 * (n_levels + 2));
+        double (*Koffl)[3] = malloc(sizeof(double) * 3 * (n_levels + 2));
+        double Kstar[3], base[3], Knet[3];
+        int nmax = 0;
+        for (int l = 0; l < n_levels; ++l) if (patch_n[l] > nmax) nmax = patch_n[l];
+        double *psi = malloc(sizeof(double) * nmax * nmax);
+        double **Q12 = malloc(sizeof(double *) * n_levels), **Q21 = malloc(sizeof(double *) * n_levels);
+
+        /* per level: line variances of the off-diagonal parts at this node */
+        for (int l = 1; l <= n_levels; ++l) {
+            int n = patch_n[l - 1];
+            long ox = orc_patch_origin(node_i[p], n_macro, Nl[l - 1], n);
+            long oy = orc_patch_origin(node_j[p], n_macro, Nl[l - 1], n);
+            double L = 2.0 * ORC_PI * n / (double)Nl[l - 1];
+            for (int t = 0; t < n_modes; ++t) {
+                u12[t] = (lev[t] == l && kind[t] == 1);
+                u21[t] = (lev[t] == l && kind[t] == 2);
+            }
+            Q12[l - 1] = malloc(sizeof(double) * n);
+            Q21[l - 1] = malloc(sizeof(double) * n);
+            orc_offdiag_q(n_modes, k1, k2, re, im, u12, u21, Nl[l - 1], ox, oy, n, L,
+                          Q12[l - 1], Q21[l - 1]);
+        }
+        /* top-down closed forms */
+        Bl[1][0] = kappa; Bl[1][1] = 0.0; Bl[1][2] = kappa;
+        for (int l = 1; l <= n_levels; ++l) {
+            orc_offdiag_apply(patch_n[l - 1], Q12[l - 1], Q21[l - 1], Bl[l], Koffl[l]);
+            if (l < n_levels) memcpy(Bl[l + 1], Koffl[l], sizeof(double) * 3);
+        }
+        /* bottom-up patch solves */
+        for (int l = n_levels; l >= 1; --l) {
+            int n = patch_n[l - 1];
+            long ox = orc_patch_origin(node_i[p], n_macro, Nl[l - 1], n);
+            long oy = orc_patch_origin(node_j[p], n_macro, Nl[l - 1], n);
+            double L = 2.0 * ORC_PI * n / (double)Nl[l - 1];
+            double h = L / n;
+            if (l == n_levels) {
+                memcpy(base, Koffl[l], sizeof(base));
+            } else {
+                for (int c = 0; c < 3; ++c) Knet[c] = Kstar[c] - Koffl[l][c] + Bl[l][c];
+                orc_offdiag_apply(n, Q12[l - 1], Q21[l - 1], Knet, base);
+            }
+            for (int t = 0; t < n_modes; ++t) ud[t] = (lev[t] == l && kind[t] == 0);
+            orc_patch_psi(n_modes, k1, k2, re, im, ud, Nl[l - 1], ox, oy, n, psi);
+            double *v1 = malloc(sizeof(double) * n * n), *v2 = malloc(sizeof(double) * n * n);
+            orc_velocity(n, h, psi, v1, v2);
+            double vmax = 0.0;
+            for (long c = 0; c < (long)n * n; ++c) {
+                double s = fabs(v1[c]) + fabs(v2[c]);
+                if (s > vmax) vmax = s;
+            }
+            free(v1); free(v2);
+            double dt = orc_micro_dt(h, vmax, base, cfl);
+            long nb, na;
+            orc_micro_steps(L, base, dt, t_burn, t_avg, &nb, &na);
+            if (n_burn_fixed >= 0 && n_avg_fixed > 0) { nb = n_burn_fixed; na = n_avg_fixed; }
+            orc_patch_k(n, h, psi, base, dt, nb, na, Kstar, NULL, NULL);
+            if (Kstar_levels_out)
+                memcpy(Kstar_levels_out + ((long)p * n_levels + (l - 1)) * 3, Kstar,
+                       sizeof(double) * 3);
+        }
+        memcpy(K_out + (long)p * 3, Kstar, sizeof(double) * 3);
+        for (int l = 0; l < n_levels; ++l) { free(Q12[l]); free(Q21[l]); }
+        free(Q12); free(Q21); free(psi);
+        free(ud); free(u12); free(u21); free(Bl); free(Koffl);
+    }
+    free(lev); free(kind);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Macro solver for Eq. (homo): U_t = div(K grad U) on the periodic N x N    */
+/* node grid (spacing H = 2 pi / N), conservative form with face tensors     */
+/* K_f = (K_node + K_neighbour) / 2:                                         */
+/*   Fx(i+1/2,j) = K11f (U(i+1,j) - U(i,j)) / H                              */
+/*              + K12f (U(i,j+1) + U(i+1,j+1) - U(i,j-1) - U(i+1,j-1)) / (4H)*/
+/*   Fy(i,j+1/2) = K22f (U(i,j+1) - U(i,j)) / H                              */
+/*              + K12f (U(i+1,j) + U(i+1,j+1) - U(i-1,j) - U(i-1,j+1)) / (4H)*/
+/*   U_t = (Fx(i+1/2) - Fx(i-1/2) + Fy(j+1/2) - Fy(j-1/2)) / H               */
+/* advanced with Heun's RK2.  K is [N*N][3] in node order j*N + i.           */
+/* mass_out (nsteps + 1 values or NULL) receives sum(U) * H^2 per step.      */
+/* ------------------------------------------------------------------------ */
+static void macro_rhs(int N, double H, const double *K, const double *U, double *R)
+{
+    for (int j = 0; j < N; ++j) {
+        int jp = (j + 1) % N, jm = (j + N - 1) % N;
+        for (int i = 0; i < N; ++i) {
+            int ip = (i + 1) % N, im_ = (i + N - 1) % N;
+            /* east face (i+1/2, j) and west face (i-1/2, j) */
+            double fe, fw, fn, fs;
+            {
+                const double *a = K + 3L * (j * N + i), *b = K + 3L * (j * N + ip);
+                double k11 = 0.5 * (a[0] + b[0]), k12 = 0.5 * (a[1] + b[1]);
+                fe = k11 * (U[j * N + ip] - U[j * N + i]) / H
+                   + k12 * (U[jp * N + i] + U[jp * N + ip] - U[jm * N + i] - U[jm * N + ip]) / (4.0 * H);
+            }
+            {
+                const double *a = K + 3L * (j * N + im_), *b = K + 3L * (j * N + i);
+                double k11 = 0.5 * (a[0] + b[0]), k12 = 0.5 * (a[1] + b[1]);
+                fw = k11 * (U[j * N + i] - U[j * N + im_]) / H
+                   + k12 * (U[jp * N + im_] + U[jp * N + i] - U[jm * N + im_] - U[jm * N + i]) / (4.0 * H);
+            }
+            {
+                const double *a = K + 3L * (j * N + i), *b = K + 3L * (jp * N + i);
+                double k22 = 0.5 * (a[2] + b[2]), k12 = 0.5 * (a[1] + b[1]);
+                fn = k22 * (U[jp * N + i] - U[j * N + i]) / H
+                   + k12 * (U[j * N + ip] + U[jp * N + ip] - U[j * N + im_] - U[jp * N + im_]) / (4.0 * H);
+            }
+            {
+                const double *a = K + 3L * (jm * N + i), *b = K + 3L * (j * N + i);
+                double k22 = 0.5 * (a[2] + b[2]), k12 = 0.5 * (a[1] + b[1]);
+                fs = k22 * (U[j * N + i] - U[jm * N + i]) / H
+                   + k12 * (U[jm * N + ip] + U[j * N + ip] - U[jm * N + im_] - U[j * N + im_]) / (4.0 * H);
+            }
+            R[j * N + i] = (fe - fw + fn - fs) / H;
+        }
+    }
+}
+
+/* dt = cfl * H^2 / max_nodes(K11 + K22 + |K12|) */
+double orc_macro_dt(int N, const double *K, double cfl)
+{
+    double H = 2.0 * ORC_PI / N, m = 0.0;
+    for (long p = 0; p < (long)N * N; ++p) {
+        double s = K[3 * p] + K[3 * p + 2] + fabs(K[3 * p + 1]);
+        if (s > m) m = s;
+    }
+    return cfl * H * H / m;
+}
+
+void orc_macro_run(int N, double *U, const double *K, double dt, long nsteps, double *mass_out)
+{
+    double H = 2.0 * ORC_PI / N;
+    long nn = (long)N * N;
+    double *R = malloc(sizeof(double) * nn), *Us = malloc(sizeof(double) * nn);
+    if (mass_out) { double m = 0; for (long c = 0; c < nn; ++c) m += U[c]; mass_out[0] = m * H * H; }
+    for (long s = 1; s <= nsteps; ++s) {
+        macro_rhs(N, H, K, U, R);
+        for (long c = 0; c < nn; ++c) Us[c] = U[c] + dt * R[c];
+        macro_rhs(N, H, K, Us, R);
+        for (long c = 0; c < nn; ++c) U[c] = 0.5 * (U[c] + Us[c] + dt * R[c]);
+        if (mass_out) { double m = 0; for (long c = 0; c < nn; ++c) m += U[c]; mass_out[s] = m * H * H; }
+    }
+    free(R); free(Us);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Direct simulation of Eq. (model), u_t = v.grad u + kappa Lap u, on the    */
+/* full Nf x Nf grid with the same second-order central differences and      */
+/* Heun's RK2 as the local problems (the Sec. 4 reference scheme: second     */
+/* order in space and time).  psi is the stream function on the grid.       */
+/* ------------------------------------------------------------------------ */
+static void dns_rhs(int Nf, double h, const double *v1, const double *v2, double kappa,
+                    const double *u, double *f)
+{
+#pragma omp parallel for
+    for (int b = 0; b < Nf; ++b) {
+        int bp = (b + 1) % Nf, bm = (b + Nf - 1) % Nf;
+        for (int a = 0; a < Nf; ++a) {
+            int ap = (a + 1) % Nf, am = (a + Nf - 1) % Nf;
+            long c = (long)b * Nf + a;
+            double uc = u[c];
+            double d0x = (u[(long)b * Nf + ap] - u[(long)b * Nf + am]) / (2.0 * h);
+            double d0y = (u[(long)bp * Nf + a] - u[(long)bm * Nf + a]) / (2.0 * h);
+            double lap = (u[(long)b * Nf + ap] + u[(long)b * Nf + am] + u[(long)bp * Nf + a]
+                          + u[(long)bm * Nf + a] - 4.0 * uc) / (h * h);
+            f[c] = v1[c] * d0x + v2[c] * d0y + kappa * lap;
+        }
+    }
+}
+
+void orc_dns_run(int Nf, const double *psi, double kappa, double dt, long nsteps, double *u)
+{
+    long nn = (long)Nf * Nf;
+    double h = 2.0 * ORC_PI / Nf;
+    double *v1 = malloc(sizeof(double) * nn), *v2 = malloc(sizeof(double) * nn);
+    double *f = malloc(sizeof(double) * nn), *us = malloc(sizeof(double) * nn);
+    orc_velocity(Nf, h, psi, v1, v2);
+    for (long s = 0; s < nsteps; ++s) {
+        dns_rhs(Nf, h, v1, v2, kappa, u, f);
+        for (long c = 0; c < nn; ++c) us[c] = u[c] + dt * f[c];
+        dns_rhs(Nf, h, v1, v2, kappa, us, f);
+        for (long c = 0; c < nn; ++c) u[c] = 0.5 * (u[c] + us[c] + dt * f[c]);
+    }
+    free(v1); free(v2); free(f); free(us);
+}
+
+/* stream function of the given modes on the full Nf x Nf grid */
+void orc_grid_psi(int n_modes, const int *k1, const int *k2, const double *re,
+                  const double *im, int Nf, double *psi)
+{
+#pragma omp parallel for
+    for (int b = 0; b < Nf; ++b)
+        for (int a = 0; a < Nf; ++a)
+            psi[(long)b * Nf + a] = psi_at(n_modes, k1, k2, re, im, NULL, Nf, a, b);
+}
+
+/* box average of the fine field onto the macro grid: macro node (i, j)      */
+/* averages the r x r fine nodes with indices i*r - r/2 .. i*r + r/2 - 1     */
+/* (periodic), r = Nf / N.  mass = sum over the fine grid of u * h^2.        */
+void orc_coarse_grain(int Nf, const double *u, int N, double *U, double *mass)
+{
+    int r = Nf / N;
+    for (int j = 0; j < N; ++j)
+        for (int i = 0; i < N; ++i) {
+            double s = 0.0;
+            for (int db = 0; db < r; ++db)
+                for (int da = 0; da < r; ++da) {
+                    long b = pmod((long)j * r - r / 2 + db, Nf), a = pmod((long)i * r - r / 2 + da, Nf);
+                    s += u[b * Nf + a];
+                }
+            U[j * N + i] = s / ((double)r * r);
+        }
+    if (mass) {
+        double h = 2.0 * ORC_PI / Nf, m = 0.0;
+        for (long c = 0; c < (long)Nf * Nf; ++c) m += u[c];
+        *mass = m * h * h;
+    }
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
