@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the batched multiscale effective-diffusivity solve.
+
+One step = the whole hot path on the 3-level cellular hierarchy
+(psi = sum_j 4^-j sin(4^j x) sin(4^j y), kappa = 0.01, 128 x 128 macro grid,
+one 64^2 patch per macro node and level, 16384 patches per level, FP32 stencil
+with FP64 averages, full relaxation window): Algorithm 3 over the 3 levels
+(off-diagonal closed forms, three levels of batched patch solves, composition)
+followed by the macro solve of U_t = div(K grad U) to T = 1.
+
+Printed (rank 0, one JSON line): patch cell-updates/s of the whole job (a
+cell-update = one cell of one corrector field advanced one full RK2 step),
+K_eff tensors/s, the roofline of the patch-solve kernel, the oracle timed on
+the host cores, an end-to-end figure through the C ABI with host buffers, SM
+clocks sampled during the timed region, and the number of library kernel
+launches inside it.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (there is no other implementation of this method to compare with).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "K_eff tensors/s & patch cell-updates/s, surrogate vs plain GPU at ≤1e-3 K_eff err"
+UNIT = "cell-updates/s"
+FLOP_PER_CELL_UPDATE = 40      # two Heun stages (17 + 19 FLOP) + two flux products (4 FLOP)
+WORKLOAD = "three_level_cellular"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def _clock_sampler(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200", "-i", str(_local_rank())],
+                                stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except OSError:
+        return None
+
+
+def _clock_summary(path):
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+    except OSError:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+    return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def _local_rank():
+    return int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _workload():
+    import inputs
+    return inputs.config_problem(WORKLOAD)
+
+
+def _oracle_nodes(cores, N):
+    return [((37 * k + 5) % N, (59 * k + 3) % N) for k in range(cores)]
+
+
+def _oracle_sample(cores):
+    """Time the oracle (as it stands) on a bounded sample of the workload: the
+    full Algorithm 3 chain (all levels, full relaxation window) for `cores`
+    macro nodes.  Returns (cell-updates/s, seconds, description, nodes, K)."""
+    import oracle
+    cfg = _workload()
+    N = cfg["n_macro"]
+    nodes = _oracle_nodes(cores, N)
+    t0 = time.perf_counter()
+    K, steps = oracle.chain(cfg["spectrum"], cfg["edges"], cfg["patch_n"], N, cfg["kappa"], nodes,
+                            cfl=cfg["cfl"], t_burn=8.0, t_avg=4.0, want_steps=True)
+    dt = time.perf_counter() - t0
+    n2 = np.array([n * n for n in cfg["patch_n"]], dtype=np.float64)
+    cu = float(np.sum(2.0 * steps * n2[None, :]))
+    sample = (f"{len(nodes)} of the {N * N} macro nodes: full 3-level chain of 64^2 patch "
+              f"solves with the full 8+4 tau window")
+    return cu / dt, dt, sample, nodes, K
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    cores = oracle.num_threads()
+    for _ in range(args.warmup):
+        _oracle_sample(cores)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, dt, sample, _, _ = _oracle_sample(cores)
+        vals.append(v); secs.append(dt)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_macro": 128, "patch_n": 64, "levels": 3},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mlsd", choices=["mlsd", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+    import paper_1510_00451_gb300 as mlsd
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(_local_rank())
+    dev = torch.device("cuda", _local_rank())
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cfg = _workload()
+    N, L = cfg["n_macro"], len(cfg["patch_n"])
+    stream = torch.cuda.current_stream()
+    lv = mlsd.Levels(cfg["spectrum"], cfg["kappa"], N, cfg["edges"], cfg["patch_n"],
+                     cfl=cfg["cfl"], t_burn_tau=8.0, t_avg_tau=4.0, precision=cfg["precision"])
+    K = torch.zeros(N * N, 3, dtype=torch.float64, device=dev)
+    U0 = torch.tensor(__import__("inputs").gaussian_u0(N, cfg["sigma"]), dtype=torch.float32,
+                      device=dev)
+    U = torch.empty_like(U0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def step():
+        lv.effective_diffusivity(K)
+        dt = mlsd.macro_dt(K, N, cfg["cfl"])
+        ns = max(1, math.ceil(cfg["T"] / dt))
+        U.copy_(U0)
+        mlsd.macro_step(U, K, cfg["T"] / ns, ns, want_mass=False)
+
+    for _ in range(args.warmup):
+        step()
+    assert lv.status() == 0
+    work = [lv.level_work(l + 1)[0] for l in range(L)]
+    cell_updates = sum(work)
+
+    # ---- timed region: K steps, device time per step (L2 flushed between steps)
+    clk_path = tempfile.mktemp(prefix="mlsd_clocks_", suffix=".csv")
+    sampler = _clock_sampler(clk_path)
+    for l in range(L):
+        lv.profile_collect(l + 1)          # drop warm-up events
+    lv.profile(True)
+    launches0 = mlsd.launch_count()
+    evs = []
+    barrier()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = mlsd.launch_count() - launches0
+    lv.profile(False)
+    if sampler:
+        sampler.terminate(); sampler.wait()
+    clocks = _clock_summary(clk_path)
+    ms_step = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    kern_ms, kern_n, kern_flop = 0.0, 0, 0.0
+    for l in range(L):
+        ms, n = lv.profile_collect(l + 1)
+        kern_ms += ms; kern_n += n
+        kern_flop += n * work[l] * FLOP_PER_CELL_UPDATE
+    assert lv.status() == 0
+    t_max = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_step = float(t_max.item())
+    value = world * cell_updates / (ms_step * 1e-3)
+    tensors = world * N * N / (ms_step * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        U0_h = U0.cpu().pin_memory()
+        K_h = torch.empty(N * N, 3, dtype=torch.float64).pin_memory()
+        U_h = torch.empty(N, N, dtype=torch.float32).pin_memory()
+        Ud = torch.empty_like(U0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            Ud.copy_(U0_h, non_blocking=True)
+            lv.effective_diffusivity(K)
+            dt = mlsd.macro_dt(K, N, cfg["cfl"])
+            ns = max(1, math.ceil(cfg["T"] / dt))
+            mlsd.macro_step(Ud, K, cfg["T"] / ns, ns, want_mass=False)
+            K_h.copy_(K, non_blocking=True)
+            U_h.copy_(Ud, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        ms_e2e = e0.elapsed_time(e1) / args.steps
+        te = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * cell_updates / (float(te.item()) * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": U0_h.numel() * 4,
+               "d2h_bytes_per_step": K_h.numel() * 8 + U_h.numel() * 4}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    line_extra = {}
+    peaks = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA at max clock
+    achieved = kern_flop / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        cores = oracle.num_threads()
+        v, secs, sample, nodes, Kor = _oracle_sample(cores)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "seconds": secs}
+        Kg = K.cpu().numpy()
+        errs = [float(np.linalg.norm(Kg[j * N + i] - Kor[t]) / np.linalg.norm(Kor[t]))
+                for t, (i, j) in enumerate(nodes)]
+        line_extra["k_eff_rel_err_vs_oracle"] = {"max": max(errs), "nodes": len(nodes)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_macro": N, "patch_n": cfg["patch_n"][0],
+                   "levels": L, "patches_per_level": N * N, "kappa": cfg["kappa"],
+                   "window": "8 tau burn-in + 4 tau average", "macro_T": cfg["T"],
+                   "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "k_eff_tensors_per_s": tensors,
+        "cell_updates_per_step": cell_updates * world,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+                     "kernel": "k_patch_solve", "launches": kern_n,
+                     "kernel_ms_per_step": kern_ms / args.steps,
+                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {sm_max:.0f} MHz"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "wall_s_timed": t_wall,
+    }
+    line.update(line_extra)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * mlsd.h -- C ABI of the GB300 (sm_103a) library for the seamless multiscale
+ * estimate of the effective diffusivity of passive advection-diffusion
+ *
+ *     u_t = v . grad u + kappa Lap u,   div v = 0,   v = (-d psi/dx2, d psi/dx1)
+ *
+ * (Lee & Engquist, Eq. (model) and Sec. 2.1).  Every call takes plain host or
+ * device pointers and sizes; no C++ or framework types cross this boundary.
+ *
+ * Conventions for every entry point:
+ *   - Domain [0, 2*pi)^2, periodic.  Macro grid N x N with nodes X_ij = (iH, jH),
+ *     H = 2*pi/N; node (and patch) index p = j*N + i.
+ *   - Symmetric tensors are stored as 3 doubles (K11, K12, K22); arrays of them
+ *     as [count][3], row-major.
+ *   - Fields are row-major [b][a] with a along x1 (fast) and b along x2 (slow).
+ *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as
+ *     void*, NULL = the legacy default stream) unless stated otherwise.  Device
+ *     pointers must stay valid until the stream reaches the call.
+ *   - Return 0 on success or a negative MLSD_E* code.  On a host-detected error
+ *     (bad argument, allocation failure) nothing is enqueued and output buffers
+ *     are left untouched.  Errors found on the device (non-finite result) are
+ *     latched in the handle's status word and reported by mlsd_status().
+ *   - Output buffers are owned by the caller; the library never frees them.
+ *   - A handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef MLSD_H
+#define MLSD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLSD_OK            0
+#define MLSD_EINVAL       -1   /* invalid argument */
+#define MLSD_ENOMEM       -2   /* device or host allocation failed */
+#define MLSD_ECUDA        -3   /* a CUDA runtime call failed */
+#define MLSD_ETIMEOUT     -4   /* a bounded device wait ran out */
+#define MLSD_ENONFINITE   -5   /* a NaN or Inf appeared in a result */
+#define MLSD_EUNSUPPORTED -6   /* configuration not supported by this build */
+
+#define MLSD_FP32 0            /* stencil arithmetic and storage in FP32, averages in FP64 */
+#define MLSD_FP64 1            /* everything in FP64 */
+
+#define MLSD_PLAIN     0       /* every patch solved by time stepping */
+#define MLSD_SURROGATE 1       /* learned estimate, time stepping as fallback */
+
+/* Problem statement: the stream function, the molecular diffusivity and the
+ * level hierarchy (Sec. 3: Fourier decomposition with factor alpha, local
+ * domains whose side and grid spacing shrink by the same factor per level).
+ *
+ *   psi(x) = sum_t Re[(re[t] + i im[t]) exp(i (k1[t] x1 + k2[t] x2))]
+ *
+ * The mode list must be Hermitian-complete (each mode with its mirror -k and
+ * the conjugate coefficient) and must not contain k = 0.  Level l = 1..L
+ * (1 = coarsest) owns wavenumber magnitudes in [e_{l-1}, e_l) with the first
+ * level's lower bound read as 0 (band_edges = e_0 < e_1 < ... < e_L); a mode
+ * whose two magnitudes fall in the same level is part of that level's
+ * diagonal band (psi_11 / psi_22), otherwise it is an off-diagonal part
+ * (psi_12 or psi_21) of the lower of the two levels.
+ * The local domain (patch) of level l is a square of side L_l = 2*pi/m_l
+ * centred at the macro node (snapped to the nearest grid node of spacing
+ * h_l = L_l/n_l) with an n_l x n_l periodic grid.                           */
+typedef struct {
+    int n_macro;               /* N >= 1 */
+    double kappa;              /* molecular diffusivity, > 0 */
+    int n_modes;
+    const int32_t *k1, *k2;    /* host arrays [n_modes] */
+    const double *re, *im;     /* host arrays [n_modes] */
+    int n_levels;              /* L >= 1 */
+    const double *band_edges;  /* host [L + 1], increasing */
+    const int32_t *patch_div;  /* host [L] integers m_l >= 1, or NULL: m_l = e_{l-1} (must be integer) */
+    const int32_t *patch_n;    /* host [L] patch grid sizes, each 32, 64, 128 or 256 */
+    double cfl;                /* micro time-step factor, e.g. 0.2 */
+    double t_burn_tau;         /* burn-in length in relaxation times tau, e.g. 8 */
+    double t_avg_tau;          /* averaging window in tau, e.g. 4 */
+    int64_t n_burn_fixed;      /* if n_avg_fixed > 0: fixed step counts replace the tau rule */
+    int64_t n_avg_fixed;
+    int precision;             /* MLSD_FP32 or MLSD_FP64 */
+} mlsd_problem;
+
+/* Description of one level, as built. */
+typedef struct {
+    int n;                     /* patch grid n x n */
+    int64_t Nl;                /* grid points per 2*pi at this level: h = 2*pi/Nl, L = n h */
+    double L, h;
+    int64_t n_patches;         /* = N*N */
+    int n_diag_modes, n_off12_modes, n_off21_modes;
+} mlsd_level_desc;
+
+typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and scratch */
+
+/* Validate the problem, decompose the spectrum (Sec. 3.1), synthesise every
+ * level's diagonal band on the device, and precompute the line variances that
+ * Algorithm 1 needs.  Allocates device memory; blocks until set-up is done.
+ * Returns MLSD_EINVAL for an invalid problem, MLSD_EUNSUPPORTED for a patch
+ * size or precision without a kernel, MLSD_ENOMEM / MLSD_ECUDA otherwise.   */
+int mlsd_build_levels(const mlsd_problem *p, void *cuda_stream, mlsd_levels **out);
+
+/* Free a handle (synchronises with its work first).  NULL is ignored. */
+void mlsd_free_levels(mlsd_levels *h);
+
+int mlsd_level_info(const mlsd_levels *h, int level, mlsd_level_desc *out);
+
+/* One level of patch solves: the numerical homogenization K[psi_l, B; Omega_l]
+ * of Sec. 2.2 for every macro node at once.  For each patch and each
+ * gradient G = e_j (j = 1, 2) the fluctuation w_j (u = G.x + w_j, w_j periodic
+ * on the patch, w_j(0) = 0) is advanced with Heun's RK2 on the second-order
+ * central-difference operator
+ *     w_t = v.(grad_h w + G) + B11 Dxx w + 2 B12 Dxy w + B22 Dyy w
+ * for n_burn + n_avg steps; the spatial mean of v_i w_j after each of the last
+ * n_avg steps is averaged in FP64 into S_ij and
+ *     K11 = B11 + S11,  K22 = B22 + S22,  K12 = B12 + (S12 + S21)/2.
+ * The time step is cfl * min(h / max(|v1|+|v2|), h^2 / (2 tr B + 4|B12|)),
+ * capped by the RK2 stability bound (8 lambda_min h^2 / vmax^4)^(1/3); the
+ * window is t_burn_tau and t_avg_tau relaxation times L^2/(4 pi^2 lambda_min(B))
+ * (or the fixed step counts of the problem).
+ *   level      1..L
+ *   K_base_dev device [P][3] base diffusivity B per patch (symmetric positive definite)
+ *   K_out_dev  device [P][3] result; may not alias K_base_dev
+ *   w_dump_dev device [P][2][n][n] of float (MLSD_FP32) or double (MLSD_FP64)
+ *              receiving the final w_1, w_2 of every patch, or NULL          */
+int mlsd_solve_level(mlsd_levels *h, int level, const double *K_base_dev, double *K_out_dev,
+                     void *w_dump_dev, void *cuda_stream);
+
+/* Algorithms 1-2 of level l for every patch: each off-diagonal part is treated
+ * as a shear on every patch line (Eq. shearhomoX/Y with base B), the line
+ * values are combined by the layered-medium harmonic mean, and
+ *     K_off = K[psi_12; B] + K[psi_21; B] - B.
+ * Identity where the level has no off-diagonal part.
+ *   B_dev, Koff_dev  device [P][3]; may alias.                              */
+int mlsd_offdiag(mlsd_levels *h, int level, const double *B_dev, double *Koff_dev,
+                 void *cuda_stream);
+
+/* Algorithm 3 over the whole hierarchy, finest level first, for every macro node:
+ *   B_1 = kappa I, Koff_l = K_off,l(B_l), B_{l+1} = Koff_l;
+ *   K*_L = K[psi_L; K_off,L(B_L)];
+ *   K*_l = K[psi_l; K_off,l(K*_{l+1} - Koff_l + B_l)] for l = L-1 .. 1;
+ *   K_macro = K*_1.
+ *   mode            MLSD_PLAIN (MLSD_SURROGATE needs a loaded surrogate)
+ *   K_macro_dev     device [P][3]
+ *   K_levels_dev    device [L][P][3] receiving K*_l, or NULL               */
+int mlsd_effective_diffusivity(mlsd_levels *h, int mode, double *K_macro_dev,
+                               double *K_levels_dev, void *cuda_stream);
+
+/* Synchronise the handle's stream and return the first error latched on the
+ * device since the last call (MLSD_ENONFINITE ...), then clear it.          */
+int mlsd_status(mlsd_levels *h, void *cuda_stream);
+
+/* Macro solver for Eq. (homo), U_t = div(K grad U), HMM step 4: conservative
+ * flux form on the periodic N x N grid with face tensors
+ * K_f = (K_node + K_neighbour)/2 (full tensor, 9-point), Heun's RK2.
+ *   U_dev       device [N][N], float (MLSD_FP32) or double (MLSD_FP64), in place
+ *   K_dev       device [N*N][3]
+ *   dt, nsteps  time step and number of steps (nsteps >= 0)
+ *   mass_out    host [nsteps + 1] or NULL: H^2 * sum(U) after each step (FP64);
+ *               when non-NULL the call blocks until the steps are done.
+ * Allocates (stream-ordered) a device scratch of N*N reals plus the mass list. */
+int mlsd_macro_step(int n_macro, void *U_dev, int precision, const double *K_dev, double dt,
+                    int nsteps, double *mass_out_host, void *cuda_stream);
+
+/* Stable macro time step dt = cfl H^2 / max_nodes(K11 + K22 + |K12|).
+ * Blocks until it is known.                                                 */
+int mlsd_macro_dt(int n_macro, const double *K_dev, double cfl, double *dt_out_host,
+                  void *cuda_stream);
+
+/* Stream function of a mode list on the full nf x nf grid (nodes 2*pi*a/nf):
+ * psi_dev device [nf][nf] float.  Blocks until done (device staging).       */
+int mlsd_grid_psi(int n_modes, const int32_t *k1, const int32_t *k2, const double *re,
+                  const double *im, int nf, float *psi_dev, void *cuda_stream);
+
+/* Direct simulation of Eq. (model) on the full nf x nf grid (the Sec. 4
+ * reference: second-order central differences, second-order Runge-Kutta):
+ * u_t = v.grad_h u + kappa Lap_h u with v from psi by central differences,
+ * Heun's RK2, nsteps steps.  u_dev [nf][nf] float in place; u_tmp_dev is a
+ * caller-provided work field of the same size.                              */
+int mlsd_dns_run(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev, double kappa,
+                 double dt, int nsteps, void *cuda_stream);
+
+/* Box average of the fine field onto the macro grid: node (i, j) averages the
+ * r x r fine nodes i*r - r/2 .. i*r + r/2 - 1 (periodic), r = nf/N.
+ *   U_dev device [N][N] float; mass_out_host (or NULL): h^2 * sum(u) in FP64
+ *   (blocks when non-NULL).                                                 */
+int mlsd_coarse_grain(int nf, const float *u_dev, int n_macro, float *U_dev,
+                      double *mass_out_host, void *cuda_stream);
+
+/* Work done by the last solve of a level (mlsd_solve_level or the level's part
+ * of mlsd_effective_diffusivity): cell_updates = sum over patches and the two
+ * fields of n^2 (n_burn + n_avg) (one cell of one field advanced one full RK2
+ * step), and the largest per-patch step count.  Synchronises the stream.     */
+int mlsd_level_work(mlsd_levels *h, int level, int64_t *cell_updates_out,
+                    int64_t *max_steps_out, void *cuda_stream);
+
+/* Kernel timing of the patch solves: when enabled, every patch-solve launch of
+ * the handle is bracketed by CUDA events recorded on the launching stream.
+ * mlsd_profile_collect synchronises, returns the summed device time (ms) and
+ * the number of patch-solve launches of the level since the last collect, and
+ * clears them.                                                              */
+int mlsd_profile(mlsd_levels *h, int enable);
+int mlsd_profile_collect(mlsd_levels *h, int level, double *kernel_ms_out,
+                         int64_t *launches_out);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (process-wide counter, host side).                                        */
+int64_t mlsd_launch_count(void);
+
+const char *mlsd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLSD_H */

@@ -52,7 +52,7 @@ def _declare(L):
     L.orc_offdiag_q.argtypes = [_i, _p, _p, _p, _p, _p, _p, _l, _l, _l, _i, _d, _p, _p]
     L.orc_offdiag_apply.argtypes = [_i, _p, _p, _p, _p]
     L.orc_chain.argtypes = [_i, _p, _p, _p, _p, _i, _p, _p, _p, _i, _d, _d, _d, _d, _l, _l,
-                            _i, _p, _p, _p, _p]
+                            _i, _p, _p, _p, _p, _p]
     L.orc_macro_dt.argtypes = [_i, _p, _d]
     L.orc_macro_dt.restype = _d
     L.orc_macro_run.argtypes = [_i, _p, _p, _d, _l, _p]
@@ -166,9 +166,13 @@ def offdiag_q(spec, use12, use21, Nl, ox, oy, n, L):
 
 
 def offdiag_apply(q12, q21, B):
-    q12 = _f64(q12); q21 = _f64(q21); B = _f64(B)
+    """Algorithms 1-2 from line variances; pass None for a part the level lacks."""
+    q12 = None if q12 is None else _f64(q12)
+    q21 = None if q21 is None else _f64(q21)
+    B = _f64(B)
+    n = len(q12) if q12 is not None else (len(q21) if q21 is not None else 1)
     out = np.zeros(3)
-    lib().orc_offdiag_apply(len(q12), _ptr(q12), _ptr(q21), _ptr(B), _ptr(out))
+    lib().orc_offdiag_apply(n, _ptr(q12), _ptr(q21), _ptr(B), _ptr(out))
     return out
 
 
@@ -182,8 +186,11 @@ def level_lattice(edges, patch_n, patch_div=None):
 
 
 def chain(spec, edges, patch_n, n_macro, kappa, nodes, cfl=0.2, t_burn=8.0, t_avg=4.0,
-          n_burn_fixed=-1, n_avg_fixed=0, patch_div=None, want_levels=False):
-    """Algorithm 3 down the whole level hierarchy for the macro nodes (i, j) given."""
+          n_burn_fixed=-1, n_avg_fixed=0, patch_div=None, want_levels=False, want_steps=False):
+    """Algorithm 3 down the whole level hierarchy for the macro nodes (i, j) given.
+
+    Returns K [nodes][3]; with want_levels also K*_l [nodes][L][3]; with want_steps
+    also the step counts n_burn + n_avg [nodes][L] of every patch solve."""
     k1, k2, re, im = _modes(spec)
     e = _f64(edges)
     Lc = len(e) - 1
@@ -193,11 +200,17 @@ def chain(spec, edges, patch_n, n_macro, kappa, nodes, cfl=0.2, t_burn=8.0, t_av
     ni = _i32(nodes[:, 0]); nj = _i32(nodes[:, 1])
     K = np.zeros((len(ni), 3))
     Kl = np.zeros((len(ni), Lc, 3)) if want_levels else None
+    st = np.zeros((len(ni), Lc), dtype=np.int64) if want_steps else None
     lib().orc_chain(len(k1), _ptr(k1), _ptr(k2), _ptr(re), _ptr(im), Lc, _ptr(e), _ptr(pn),
                     _ptr(Nl), int(n_macro), float(kappa), float(cfl), float(t_burn), float(t_avg),
                     int(n_burn_fixed), int(n_avg_fixed), len(ni), _ptr(ni), _ptr(nj),
-                    _ptr(K), _ptr(Kl))
-    return (K, Kl) if want_levels else K
+                    _ptr(K), _ptr(Kl), _ptr(st))
+    out = [K]
+    if want_levels:
+        out.append(Kl)
+    if want_steps:
+        out.append(st)
+    return out[0] if len(out) == 1 else tuple(out)
 
 
 def macro_dt(K, n_macro, cfl):

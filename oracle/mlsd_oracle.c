@@ -326,15 +326,23 @@ void orc_offdiag_q(int n_modes, const int *k1, const int *k2, const double *re,
 /*   psi_21: K*22(x_b) = B22 + q21[b] / B11 (Eq. shearhomoX), harmonic mean */
 /*           across the rows;                                               */
 /*   K_off = K[psi_12; B] + K[psi_21; B] - B.                               */
-/* B12 and the component along the layers pass through unchanged.          */
+/* B12 and the component along the layers pass through unchanged.  A part   */
+/* the level does not have (q array NULL) contributes K[0; B] = B exactly.  */
 void orc_offdiag_apply(int n, const double *q12, const double *q21, const double *B,
                        double *Koff)
 {
-    double s1 = 0.0, s2 = 0.0;
-    for (int a = 0; a < n; ++a) s1 += 1.0 / (B[0] + q12[a] / B[2]);
-    for (int b = 0; b < n; ++b) s2 += 1.0 / (B[2] + q21[b] / B[0]);
-    double K12_11 = (double)n / s1;          /* K[psi_12; B] = diag(K12_11, B22) + B12 */
-    double K21_22 = (double)n / s2;          /* K[psi_21; B] = diag(B11, K21_22) + B12 */
+    double K12_11 = B[0], K21_22 = B[2];   /* K[psi_12; B] = [[K12_11, B12], [B12, B22]] */
+    if (q12) {                              /* K[psi_21; B] = [[B11, B12], [B12, K21_22]] */
+        double s1 = 0.0;
+        for (int a = 0; a < n; ++a) s1 += 1.0 / (B[0] + q12[a] / B[2]);
+        K12_11 = (double)n / s1;
+    }
+    if (q21) {
+        double s2 = 0.0;
+        for (int b = 0; b < n; ++b) s2 += 1.0 / (B[2] + q21[b] / B[0]);
+        K21_22 = (double)n / s2;
+    }
+    if (!q12 && !q21) { memcpy(Koff, B, sizeof(double) * 3); return; }
     Koff[0] = K12_11 + B[0] - B[0];
     Koff[1] = B[1] + B[1] - B[1];
     Koff[2] = B[2] + K21_22 - B[2];
@@ -358,7 +366,8 @@ typedef struct {
 /*   K = K*_1                                                               */
 /* psi_l,diag is the diagonal band of level l; K_off,l is Algorithms 1-2     */
 /* with level l's off-diagonal parts (the identity when there are none).    */
-/* Outputs per node: K[3] and, optionally, the per-level K*_l [L][3].        */
+/* Outputs per node: K[3] and, optionally, the per-level K*_l [L][3] and the  */
+/* step counts n_burn + n_avg of every level's patch solve [L].              */
 /* The time step and window of every patch solve follow orc_micro_dt and    */
 /* orc_micro_steps, unless n_burn_fixed / n_avg_fixed are positive.         */
 /* ------------------------------------------------------------------------ */
@@ -367,7 +376,7 @@ void orc_chain(int n_modes, const int *k1, const int *k2, const double *re, cons
                int n_macro, double kappa, double cfl, double t_burn, double t_avg,
                long n_burn_fixed, long n_avg_fixed,
                int n_nodes, const int *node_i, const int *node_j,
-               double *K_out, double *Kstar_levels_out)
+               double *K_out, double *Kstar_levels_out, long *steps_out)
 {
     int *lev = malloc(sizeof(int) * n_modes), *kind = malloc(sizeof(int) * n_modes);
     orc_band_of(n_modes, k1, k2, n_levels, edges, lev, kind);
@@ -393,10 +402,14 @@ void orc_chain(int n_modes, const int *k1, const int *k2, const double *re, cons
                 u12[t] = (lev[t] == l && kind[t] == 1);
                 u21[t] = (lev[t] == l && kind[t] == 2);
             }
+            int any12 = 0, any21 = 0;
+            for (int t = 0; t < n_modes; ++t) { any12 |= u12[t]; any21 |= u21[t]; }
             Q12[l - 1] = malloc(sizeof(double) * n);
             Q21[l - 1] = malloc(sizeof(double) * n);
             orc_offdiag_q(n_modes, k1, k2, re, im, u12, u21, Nl[l - 1], ox, oy, n, L,
                           Q12[l - 1], Q21[l - 1]);
+            if (!any12) { free(Q12[l - 1]); Q12[l - 1] = NULL; }
+            if (!any21) { free(Q21[l - 1]); Q21[l - 1] = NULL; }
         }
         /* top-down closed forms */
         Bl[1][0] = kappa; Bl[1][1] = 0.0; Bl[1][2] = kappa;
@@ -431,6 +444,7 @@ void orc_chain(int n_modes, const int *k1, const int *k2, const double *re, cons
             long nb, na;
             orc_micro_steps(L, base, dt, t_burn, t_avg, &nb, &na);
             if (n_burn_fixed >= 0 && n_avg_fixed > 0) { nb = n_burn_fixed; na = n_avg_fixed; }
+            if (steps_out) steps_out[(long)p * n_levels + (l - 1)] = nb + na;
             orc_patch_k(n, h, psi, base, dt, nb, na, Kstar, NULL, NULL);
             if (Kstar_levels_out)
                 memcpy(Kstar_levels_out + ((long)p * n_levels + (l - 1)) * 3, Kstar,

@@ -1,0 +1,223 @@
+"""Python binding of libmlsd (include/mlsd.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module converts
+numpy arrays and torch tensors to pointers and C structs and checks return
+codes.  Importing it fails loudly when the library has not been built: there
+is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmlsd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libmlsd.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+MLSD_FP32, MLSD_FP64 = 0, 1
+MLSD_PLAIN, MLSD_SURROGATE = 0, 1
+ERRORS = {0: "MLSD_OK", -1: "MLSD_EINVAL", -2: "MLSD_ENOMEM", -3: "MLSD_ECUDA",
+          -4: "MLSD_ETIMEOUT", -5: "MLSD_ENONFINITE", -6: "MLSD_EUNSUPPORTED"}
+EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_solve_level",
+            "mlsd_offdiag", "mlsd_effective_diffusivity", "mlsd_status", "mlsd_macro_step",
+            "mlsd_macro_dt", "mlsd_grid_psi", "mlsd_dns_run", "mlsd_coarse_grain",
+            "mlsd_level_work", "mlsd_launch_count", "mlsd_profile", "mlsd_profile_collect",
+            "mlsd_strerror"]
+
+
+class MlsdError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib.mlsd_strerror(code).decode()
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({msg})")
+
+
+class mlsd_problem(ctypes.Structure):
+    _fields_ = [("n_macro", ctypes.c_int), ("kappa", ctypes.c_double), ("n_modes", ctypes.c_int),
+                ("k1", ctypes.c_void_p), ("k2", ctypes.c_void_p), ("re", ctypes.c_void_p),
+                ("im", ctypes.c_void_p), ("n_levels", ctypes.c_int),
+                ("band_edges", ctypes.c_void_p), ("patch_div", ctypes.c_void_p),
+                ("patch_n", ctypes.c_void_p), ("cfl", ctypes.c_double),
+                ("t_burn_tau", ctypes.c_double), ("t_avg_tau", ctypes.c_double),
+                ("n_burn_fixed", ctypes.c_int64), ("n_avg_fixed", ctypes.c_int64),
+                ("precision", ctypes.c_int)]
+
+
+class mlsd_level_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("Nl", ctypes.c_int64), ("L", ctypes.c_double),
+                ("h", ctypes.c_double), ("n_patches", ctypes.c_int64),
+                ("n_diag_modes", ctypes.c_int), ("n_off12_modes", ctypes.c_int),
+                ("n_off21_modes", ctypes.c_int)]
+
+
+_P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+_lib.mlsd_build_levels.argtypes = [ctypes.POINTER(mlsd_problem), _P, ctypes.POINTER(_P)]
+_lib.mlsd_free_levels.argtypes = [_P]
+_lib.mlsd_free_levels.restype = None
+_lib.mlsd_level_info.argtypes = [_P, _I, ctypes.POINTER(mlsd_level_desc)]
+_lib.mlsd_solve_level.argtypes = [_P, _I, _P, _P, _P, _P]
+_lib.mlsd_offdiag.argtypes = [_P, _I, _P, _P, _P]
+_lib.mlsd_effective_diffusivity.argtypes = [_P, _I, _P, _P, _P]
+_lib.mlsd_status.argtypes = [_P, _P]
+_lib.mlsd_macro_step.argtypes = [_I, _P, _I, _P, _D, _I, _P, _P]
+_lib.mlsd_macro_dt.argtypes = [_I, _P, _D, ctypes.POINTER(_D), _P]
+_lib.mlsd_grid_psi.argtypes = [_I, _P, _P, _P, _P, _I, _P, _P]
+_lib.mlsd_dns_run.argtypes = [_I, _P, _P, _P, _D, _D, _I, _P]
+_lib.mlsd_coarse_grain.argtypes = [_I, _P, _I, _P, _P, _P]
+_lib.mlsd_level_work.argtypes = [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_L), _P]
+_lib.mlsd_profile.argtypes = [_P, _I]
+_lib.mlsd_profile_collect.argtypes = [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_L)]
+_lib.mlsd_launch_count.argtypes = []
+_lib.mlsd_launch_count.restype = _L
+_lib.mlsd_strerror.argtypes = [_I]
+_lib.mlsd_strerror.restype = ctypes.c_char_p
+
+
+def lib():
+    return _lib
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise MlsdError(rc, where)
+
+
+def _dptr(t):
+    """Device pointer of a CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Levels:
+    """Handle of a built level hierarchy (mlsd_build_levels)."""
+
+    def __init__(self, spectrum, kappa, n_macro, edges, patch_n, patch_div=None, cfl=0.2,
+                 t_burn_tau=8.0, t_avg_tau=4.0, n_burn_fixed=0, n_avg_fixed=0,
+                 precision="fp32", stream=None):
+        k1, k2, re, im = spectrum.as_arrays()
+        self._keep = [k1, k2, re, im,
+                      np.ascontiguousarray(edges, dtype=np.float64),
+                      np.ascontiguousarray(patch_n, dtype=np.int32),
+                      None if patch_div is None else np.ascontiguousarray(patch_div, dtype=np.int32)]
+        e, pn, pdv = self._keep[4], self._keep[5], self._keep[6]
+        self.precision = MLSD_FP64 if precision in ("fp64", MLSD_FP64) else MLSD_FP32
+        p = mlsd_problem(n_macro=int(n_macro), kappa=float(kappa), n_modes=len(k1),
+                         k1=k1.ctypes.data, k2=k2.ctypes.data, re=re.ctypes.data,
+                         im=im.ctypes.data, n_levels=len(e) - 1, band_edges=e.ctypes.data,
+                         patch_div=None if pdv is None else pdv.ctypes.data,
+                         patch_n=pn.ctypes.data, cfl=float(cfl), t_burn_tau=float(t_burn_tau),
+                         t_avg_tau=float(t_avg_tau), n_burn_fixed=int(n_burn_fixed),
+                         n_avg_fixed=int(n_avg_fixed), precision=self.precision)
+        h = _P()
+        _check(_lib.mlsd_build_levels(ctypes.byref(p), _stream(stream), ctypes.byref(h)),
+               "mlsd_build_levels")
+        self.h = h
+        self.n_macro = int(n_macro)
+        self.n_levels = len(e) - 1
+        self.P = self.n_macro ** 2
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.mlsd_free_levels(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self, level):
+        d = mlsd_level_desc()
+        _check(_lib.mlsd_level_info(self.h, int(level), ctypes.byref(d)), "mlsd_level_info")
+        return {f: getattr(d, f) for f, _ in d._fields_}
+
+    def solve_level(self, level, K_base, K_out, w_dump=None, stream=None):
+        _check(_lib.mlsd_solve_level(self.h, int(level), _dptr(K_base), _dptr(K_out),
+                                     _dptr(w_dump), _stream(stream)), "mlsd_solve_level")
+
+    def offdiag(self, level, B, Koff, stream=None):
+        _check(_lib.mlsd_offdiag(self.h, int(level), _dptr(B), _dptr(Koff), _stream(stream)),
+               "mlsd_offdiag")
+
+    def effective_diffusivity(self, K_macro, K_levels=None, mode=MLSD_PLAIN, stream=None):
+        _check(_lib.mlsd_effective_diffusivity(self.h, int(mode), _dptr(K_macro),
+                                               _dptr(K_levels), _stream(stream)),
+               "mlsd_effective_diffusivity")
+
+    def status(self, stream=None):
+        return _lib.mlsd_status(self.h, _stream(stream))
+
+    def level_work(self, level, stream=None):
+        """(cell-updates, max steps per patch) of the level's last solve."""
+        cu, ms = _L(), _L()
+        _check(_lib.mlsd_level_work(self.h, int(level), ctypes.byref(cu), ctypes.byref(ms),
+                                    _stream(stream)), "mlsd_level_work")
+        return cu.value, ms.value
+
+
+    def profile(self, enable=True):
+        _check(_lib.mlsd_profile(self.h, 1 if enable else 0), "mlsd_profile")
+
+    def profile_collect(self, level):
+        """(summed patch-kernel ms, launches) of the level since the last collect."""
+        ms, n = _D(), _L()
+        _check(_lib.mlsd_profile_collect(self.h, int(level), ctypes.byref(ms), ctypes.byref(n)),
+               "mlsd_profile_collect")
+        return ms.value, n.value
+
+
+def launch_count():
+    return int(_lib.mlsd_launch_count())
+
+
+def macro_step(U, K, dt, nsteps, want_mass=True, stream=None):
+    """In-place Heun steps of U_t = div(K grad U); returns the FP64 mass list."""
+    import torch
+    prec = MLSD_FP64 if U.dtype == torch.float64 else MLSD_FP32
+    mass = np.zeros(nsteps + 1) if want_mass else None
+    _check(_lib.mlsd_macro_step(U.shape[0], _dptr(U), prec, _dptr(K), float(dt), int(nsteps),
+                                None if mass is None else mass.ctypes.data, _stream(stream)),
+           "mlsd_macro_step")
+    return mass
+
+
+def macro_dt(K, n_macro, cfl, stream=None):
+    out = ctypes.c_double()
+    _check(_lib.mlsd_macro_dt(int(n_macro), _dptr(K), float(cfl), ctypes.byref(out),
+                              _stream(stream)), "mlsd_macro_dt")
+    return out.value
+
+
+def grid_psi(spectrum, nf, psi_out, stream=None):
+    k1, k2, re, im = spectrum.as_arrays()
+    _check(_lib.mlsd_grid_psi(len(k1), k1.ctypes.data, k2.ctypes.data, re.ctypes.data,
+                              im.ctypes.data, int(nf), _dptr(psi_out), _stream(stream)),
+           "mlsd_grid_psi")
+
+
+def dns_run(u, u_tmp, psi, kappa, dt, nsteps, stream=None):
+    _check(_lib.mlsd_dns_run(u.shape[0], _dptr(u), _dptr(u_tmp), _dptr(psi), float(kappa),
+                             float(dt), int(nsteps), _stream(stream)), "mlsd_dns_run")
+
+
+def coarse_grain(u, n_macro, U_out, want_mass=True, stream=None):
+    m = ctypes.c_double()
+    _check(_lib.mlsd_coarse_grain(u.shape[0], _dptr(u), int(n_macro), _dptr(U_out),
+                                  ctypes.byref(m) if want_mass else None, _stream(stream)),
+           "mlsd_coarse_grain")
+    return m.value if want_mass else None

@@ -1,0 +1,233 @@
+// Level hierarchy on the device: band synthesis (Sec. 3.1), the line
+// variances and harmonic means of Algorithms 1-2, and the per-patch tensor
+// bookkeeping of Algorithm 3.
+#include "mlsd_internal.cuh"
+
+namespace mlsd {
+namespace {
+
+// cos/sin(2 pi r / Nl) for an exactly reduced phase index r in [0, Nl)
+__device__ __forceinline__ void twiddle(long long r, long long Nl, double &c, double &s)
+{
+    sincospi(2.0 * (double)r / (double)Nl, &s, &c);
+}
+
+// Pass 1: G[g][y] = sum_{modes of group g} (re + i im) e^{i k2 2 pi y / Nl}
+__global__ void k_band_pass1(ModeGroups m, long long Nl, double2 *G)
+{
+    const int g = blockIdx.y;
+    const long long y = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (y >= Nl) return;
+    double gr = 0.0, gi = 0.0;
+    for (int t = m.gofs[g]; t < m.gofs[g + 1]; ++t) {
+        double c, s;
+        twiddle(pmod_ll((long long)m.k2[t] * y, Nl), Nl, c, s);
+        const double re = m.re[t], im = m.im[t];
+        gr += re * c - im * s;
+        gi += re * s + im * c;
+    }
+    G[(long long)g * Nl + y] = make_double2(gr, gi);
+}
+
+// Pass 2: psi[y][x] = sum_g Re(e^{i k1_g 2 pi x / Nl} G[g][y])
+template <typename T>
+__global__ void k_band_pass2(ModeGroups m, long long Nl, const double2 *G, T *out)
+{
+    const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long y = blockIdx.y;
+    if (x >= Nl) return;
+    double acc = 0.0;
+    for (int g = 0; g < m.n_groups; ++g) {
+        double c, s;
+        twiddle(pmod_ll((long long)m.gk1[g] * x, Nl), Nl, c, s);
+        const double2 v = G[(long long)g * Nl + y];
+        acc += v.x * c - v.y * s;
+    }
+    out[y * Nl + x] = (T)acc;
+}
+
+// psi of a mode list at lattice point (gx, gy) of an Nr lattice
+__device__ double psi_point(const ModeList &m, long long Nr, long long gx, long long gy)
+{
+    double acc = 0.0;
+    for (int t = 0; t < m.n; ++t) {
+        double c, s;
+        twiddle(pmod_ll((long long)m.k1[t] * gx + (long long)m.k2[t] * gy, Nr), Nr, c, s);
+        acc += m.re[t] * c - m.im[t] * s;
+    }
+    return acc;
+}
+
+// Algorithm 1 line variances, one thread block per (patch, line):
+//   q12[p][a] = var_s psi_12(x_a, y_s), y_s on the r12-times refined lattice,
+//   q21[p][b] = var_s psi_21(x_s, y_b).
+__global__ void k_offdiag_q(ModeList m12, ModeList m21, long long Nl, int n, int r12, int r21,
+                            int n_macro, double *q12, double *q21)
+{
+    __shared__ double red[2][32];
+    const long long p = blockIdx.x;
+    const int line = blockIdx.y;          // 0..n-1 -> psi_12 column, n..2n-1 -> psi_21 row
+    const bool is12 = line < n;
+    const ModeList &m = is12 ? m12 : m21;
+    double *q = is12 ? q12 : q21;
+    if (m.n == 0 || q == nullptr) return;
+    const int k = is12 ? line : line - n;
+    const int r = is12 ? r12 : r21;
+    const long long ox = patch_origin(p % n_macro, n_macro, Nl, n);
+    const long long oy = patch_origin(p / n_macro, n_macro, Nl, n);
+    const long long Nr = Nl * r, ms = (long long)n * r;
+    double s1 = 0.0, s2 = 0.0;
+    // two-pass variance in one sweep of the samples: accumulate sum and sum of squares
+    // of the shifted value (psi - psi at the first sample) to limit cancellation
+    const double ref = is12 ? psi_point(m, Nr, (ox + k) * r, oy * r)
+                            : psi_point(m, Nr, ox * r, (oy + k) * r);
+    for (long long s = threadIdx.x; s < ms; s += blockDim.x) {
+        const double g = (is12 ? psi_point(m, Nr, (ox + k) * r, oy * r + s)
+                               : psi_point(m, Nr, ox * r + s, (oy + k) * r)) - ref;
+        s1 += g;
+        s2 += g * g;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = s1; red[1][threadIdx.x >> 5] = s2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; }
+        const double mean = a / (double)ms;
+        double var = b / (double)ms - mean * mean;
+        q[p * n + k] = var > 0.0 ? var : 0.0;
+    }
+}
+
+// Algorithms 1-2 for one patch: K_off = K[psi_12; B] + K[psi_21; B] - B with the
+// shear closed forms K*11 = B11 + q12/B22, K*22 = B22 + q21/B11 on every line
+// and their harmonic means.  A part that is absent leaves B unchanged.
+__device__ void offdiag_apply(const OffdiagLevel &o, long long p, const double *B, double *K)
+{
+    double k12_11 = B[0], k21_22 = B[2];
+    if (o.q12) {
+        double s = 0.0;
+        for (int a = 0; a < o.n; ++a) s += 1.0 / (B[0] + o.q12[p * o.n + a] / B[2]);
+        k12_11 = (double)o.n / s;
+    }
+    if (o.q21) {
+        double s = 0.0;
+        for (int b = 0; b < o.n; ++b) s += 1.0 / (B[2] + o.q21[p * o.n + b] / B[0]);
+        k21_22 = (double)o.n / s;
+    }
+    if (!o.q12 && !o.q21) { K[0] = B[0]; K[1] = B[1]; K[2] = B[2]; return; }
+    K[0] = k12_11 + B[0] - B[0];
+    K[1] = B[1] + B[1] - B[1];
+    K[2] = B[2] + k21_22 - B[2];
+}
+
+// Top-down closed forms: B_1 = kappa I, Koff_l = K_off,l(B_l), B_{l+1} = Koff_l.
+__global__ void k_topdown(ChainTables t)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= t.P) return;
+    double B[3] = {t.kappa, 0.0, t.kappa}, K[3];
+    for (int l = 0; l < t.L; ++l) {
+        t.B[l][3 * p] = B[0]; t.B[l][3 * p + 1] = B[1]; t.B[l][3 * p + 2] = B[2];
+        offdiag_apply(t.off[l], p, B, K);
+        t.Koff[l][3 * p] = K[0]; t.Koff[l][3 * p + 1] = K[1]; t.Koff[l][3 * p + 2] = K[2];
+        B[0] = K[0]; B[1] = K[1]; B[2] = K[2];
+    }
+}
+
+__global__ void k_level_base(long long P, int finest, const double *base_next, const double *S_next,
+                             double *Kstar_next, const double *Koff_l, const double *B_l,
+                             OffdiagLevel off, double *base_out)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    double X[3];
+    if (finest) {
+        X[0] = B_l[3 * p]; X[1] = B_l[3 * p + 1]; X[2] = B_l[3 * p + 2];
+    } else {
+        // K*_{l+1} = sym(P) with P_j = B e_j + S_.j  (same order as the compose step)
+        const double *b = base_next + 3 * p, *s = S_next + 4 * p;
+        const double k11 = b[0] + s[0], k12 = 0.5 * ((b[1] + s[1]) + (b[1] + s[2])), k22 = b[2] + s[3];
+        if (Kstar_next) { Kstar_next[3 * p] = k11; Kstar_next[3 * p + 1] = k12; Kstar_next[3 * p + 2] = k22; }
+        // Algorithm 3 step 3: K*_net = K* - K_off + B
+        X[0] = k11 - Koff_l[3 * p] + B_l[3 * p];
+        X[1] = k12 - Koff_l[3 * p + 1] + B_l[3 * p + 1];
+        X[2] = k22 - Koff_l[3 * p + 2] + B_l[3 * p + 2];
+    }
+    double K[3];
+    offdiag_apply(off, p, X, K);
+    base_out[3 * p] = K[0]; base_out[3 * p + 1] = K[1]; base_out[3 * p + 2] = K[2];
+}
+
+__global__ void k_offdiag_apply(long long P, OffdiagLevel off, const double *B, double *Koff)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    double X[3] = {B[3 * p], B[3 * p + 1], B[3 * p + 2]}, K[3];
+    offdiag_apply(off, p, X, K);
+    Koff[3 * p] = K[0]; Koff[3 * p + 1] = K[1]; Koff[3 * p + 2] = K[2];
+}
+
+}  // namespace
+
+cudaError_t launch_band_synth(const ModeGroups &m, long long Nl, double2 *G, void *out,
+                              int out_double, cudaStream_t s)
+{
+    if (m.n_groups == 0) {
+        return cudaMemsetAsync(out, 0, (size_t)Nl * Nl * (out_double ? 8 : 4), s);
+    }
+    const int t = 256;
+    dim3 g1((unsigned)((Nl + t - 1) / t), (unsigned)m.n_groups);
+    count_launches(2);
+    k_band_pass1<<<g1, t, 0, s>>>(m, Nl, G);
+    dim3 g2((unsigned)((Nl + t - 1) / t), (unsigned)Nl);
+    if (out_double) k_band_pass2<double><<<g2, t, 0, s>>>(m, Nl, G, static_cast<double *>(out));
+    else k_band_pass2<float><<<g2, t, 0, s>>>(m, Nl, G, static_cast<float *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_offdiag_q(const ModeList &m12, const ModeList &m21, long long Nl, int n,
+                             int r12, int r21, int n_macro, long long P, double *q12,
+                             double *q21, cudaStream_t s)
+{
+    if (m12.n == 0 && m21.n == 0) return cudaSuccess;
+    dim3 g((unsigned)P, (unsigned)(2 * n));
+    count_launches(1);
+    k_offdiag_q<<<g, 128, 0, s>>>(m12, m21, Nl, n, r12, r21, n_macro, q12, q21);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_topdown(const ChainTables &t, cudaStream_t s)
+{
+    const int th = 128;
+    count_launches(1);
+    k_topdown<<<(unsigned)((t.P + th - 1) / th), th, 0, s>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_base(long long P, int finest, const double *base_next,
+                              const double *S_next, double *Kstar_next, const double *Koff_l,
+                              const double *B_l, OffdiagLevel off, double *base_out,
+                              cudaStream_t s)
+{
+    const int th = 128;
+    count_launches(1);
+    k_level_base<<<(unsigned)((P + th - 1) / th), th, 0, s>>>(P, finest, base_next, S_next,
+                                                               Kstar_next, Koff_l, B_l, off,
+                                                               base_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_offdiag_apply(long long P, OffdiagLevel off, const double *B, double *Koff,
+                                 cudaStream_t s)
+{
+    const int th = 128;
+    count_launches(1);
+    k_offdiag_apply<<<(unsigned)((P + th - 1) / th), th, 0, s>>>(P, off, B, Koff);
+    return cudaGetLastError();
+}
+
+}  // namespace mlsd

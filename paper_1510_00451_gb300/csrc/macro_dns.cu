@@ -1,0 +1,346 @@
+// Macro solver for Eq. (homo) and direct simulation of Eq. (model).
+//
+// Macro step (HMM step 4): U_t = div(K grad U) in conservative flux form on
+// the periodic N x N grid, face tensors K_f = (K_node + K_neighbour)/2, the
+// mixed term by the 4-point average of cross differences (9-point stencil),
+// Heun's RK2.  Every face flux is evaluated by both adjacent cells with the
+// same operations, so sum(U) telescopes exactly apart from summation rounding.
+//   N <= 64: one persistent CTA keeps U, U* and K in shared memory for all steps.
+//   N  > 64: one launch per RK stage over the grid.
+// The mass H^2 sum(U) of every step is summed in FP64.
+//
+// DNS: u_t = v1 D0x u + v2 D0y u + kappa (Dxx + Dyy) u, v = (-D0y psi, D0x psi),
+// both RK stages fused per tile (u and psi staged with a halo of 2 in shared
+// memory), one pass over HBM per time step: read u, read psi, write u.
+#include "mlsd_internal.cuh"
+
+namespace mlsd {
+namespace {
+
+template <typename real>
+__device__ __forceinline__ real macro_rhs(int N, real invH, real inv4H, const real *U,
+                                          const real *K11, const real *K12, const real *K22,
+                                          int i, int j)
+{
+    const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
+    const int jp = (j + 1 == N) ? 0 : j + 1, jm = (j == 0) ? N - 1 : j - 1;
+    const int c = j * N + i;
+    const real h = (real)0.5;
+    // east face (i+1/2, j)
+    real k11 = h * (K11[c] + K11[j * N + ip]), k12 = h * (K12[c] + K12[j * N + ip]);
+    const real fe = k11 * (U[j * N + ip] - U[c]) * invH
+                  + k12 * (U[jp * N + i] + U[jp * N + ip] - U[jm * N + i] - U[jm * N + ip]) * inv4H;
+    // west face (i-1/2, j)
+    k11 = h * (K11[j * N + im] + K11[c]); k12 = h * (K12[j * N + im] + K12[c]);
+    const real fw = k11 * (U[c] - U[j * N + im]) * invH
+                  + k12 * (U[jp * N + im] + U[jp * N + i] - U[jm * N + im] - U[jm * N + i]) * inv4H;
+    // north face (i, j+1/2)
+    real k22 = h * (K22[c] + K22[jp * N + i]); k12 = h * (K12[c] + K12[jp * N + i]);
+    const real fn = k22 * (U[jp * N + i] - U[c]) * invH
+                  + k12 * (U[j * N + ip] + U[jp * N + ip] - U[j * N + im] - U[jp * N + im]) * inv4H;
+    // south face (i, j-1/2)
+    k22 = h * (K22[jm * N + i] + K22[c]); k12 = h * (K12[jm * N + i] + K12[c]);
+    const real fs = k22 * (U[c] - U[jm * N + i]) * invH
+                  + k12 * (U[jm * N + ip] + U[c + (ip - i)] - U[jm * N + im] - U[c + (im - i)]) * inv4H;
+    return (fe - fw + fn - fs) * invH;
+}
+
+// deterministic FP64 block sum (all threads return the total)
+__device__ double block_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
+// one CTA, everything in shared memory
+template <typename real>
+__global__ void __launch_bounds__(1024) k_macro_resident(int N, real *Ug, const double *Kg,
+                                                         real dt, int nsteps, double *mass)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *U = reinterpret_cast<real *>(smem_raw);
+    real *Us = U + N * N, *K11 = Us + N * N, *K12 = K11 + N * N, *K22 = K12 + N * N;
+    __shared__ double red[32];
+    const int NN = N * N;
+    const double H = 2.0 * kPi / N;
+    const real invH = (real)(1.0 / H), inv4H = (real)(1.0 / (4.0 * H));
+    const double H2 = H * H;
+    double m = 0.0;
+    for (int c = threadIdx.x; c < NN; c += blockDim.x) {
+        U[c] = Ug[c];
+        K11[c] = (real)Kg[3 * c]; K12[c] = (real)Kg[3 * c + 1]; K22[c] = (real)Kg[3 * c + 2];
+        m += (double)U[c];
+    }
+    m = block_sum(m, red);
+    if (threadIdx.x == 0 && mass) mass[0] = m * H2;
+    for (int s = 1; s <= nsteps; ++s) {
+        for (int c = threadIdx.x; c < NN; c += blockDim.x)
+            Us[c] = U[c] + dt * macro_rhs<real>(N, invH, inv4H, U, K11, K12, K22, c % N, c / N);
+        __syncthreads();
+        real nu[4];
+        int k = 0;
+        for (int c = threadIdx.x; c < NN; c += blockDim.x, ++k)
+            nu[k] = (real)0.5 * (U[c] + Us[c] + dt * macro_rhs<real>(N, invH, inv4H, Us, K11, K12, K22, c % N, c / N));
+        __syncthreads();
+        k = 0;
+        m = 0.0;
+        for (int c = threadIdx.x; c < NN; c += blockDim.x, ++k) { U[c] = nu[k]; m += (double)nu[k]; }
+        if (mass) {
+            m = block_sum(m, red);
+            if (threadIdx.x == 0) mass[s] = m * H2;
+        } else {
+            __syncthreads();
+        }
+    }
+    for (int c = threadIdx.x; c < NN; c += blockDim.x) Ug[c] = U[c];
+}
+
+template <typename real>
+__global__ void k_split_K(int NN, const double *Kg, real *K11, real *K12, real *K22)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= NN) return;
+    K11[c] = (real)Kg[3 * c]; K12[c] = (real)Kg[3 * c + 1]; K22[c] = (real)Kg[3 * c + 2];
+}
+
+// stage 1: Us = U + dt R(U); stage 2: U = (U + Us + dt R(Us)) / 2, with the block's
+// share of sum(U) written to part[block]
+template <typename real, bool SECOND>
+__global__ void k_macro_stage(int N, real *U, real *Us, const real *K11, const real *K12,
+                              const real *K22, real dt, double *part)
+{
+    __shared__ double red[32];
+    const int NN = N * N;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const double H = 2.0 * kPi / N;
+    const real invH = (real)(1.0 / H), inv4H = (real)(1.0 / (4.0 * H));
+    double m = 0.0;
+    if (c < NN) {
+        if (!SECOND) {
+            Us[c] = U[c] + dt * macro_rhs<real>(N, invH, inv4H, U, K11, K12, K22, c % N, c / N);
+        } else {
+            const real v = (real)0.5 * (U[c] + Us[c] + dt * macro_rhs<real>(N, invH, inv4H, Us, K11, K12, K22, c % N, c / N));
+            m = (double)v;
+            // U is read by neighbours only in stage 1, so the in-place write is safe here
+            U[c] = v;
+        }
+    }
+    if (SECOND && part) {
+        m = block_sum(m, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = m;
+    }
+}
+
+template <typename real>
+__global__ void k_mass_part(int NN, const real *U, double *part)
+{
+    __shared__ double red[32];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double m = c < NN ? (double)U[c] : 0.0;
+    m = block_sum(m, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = m;
+}
+
+// mass[s] = H^2 * sum_b part[s][b]
+__global__ void k_mass_final(int nsteps1, int nblocks, const double *part, double H2, double *mass)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsteps1) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += part[(long long)s * nblocks + b];
+    mass[s] = t * H2;
+}
+
+__global__ void k_kmax(int NN, const double *K, double *out)
+{
+    __shared__ double red[32];
+    double m = 0.0;
+    for (int c = threadIdx.x; c < NN; c += blockDim.x)
+        m = fmax(m, K[3 * c] + K[3 * c + 2] + fabs(K[3 * c + 1]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+        *out = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// DNS: tile of TX x TY outputs per CTA, u and psi staged with halo 2 (x range
+// padded to 16-byte boundaries), stage 1 on the tile plus a 1-cell ring, stage 2
+// on the tile.
+constexpr int DTX = 64, DTY = 32, DTH = 256;
+constexpr int DLX = DTX + 8;          // staged x range: x0-4 .. x0+TX+3
+constexpr int DLY = DTY + 4;          // staged y range: y0-2 .. y0+TY+1
+constexpr int DSX = DTX + 2, DSY = DTY + 2;
+
+__global__ void __launch_bounds__(DTH) k_dns_step(int nf, const float *__restrict__ u,
+                                                   const float *__restrict__ psi,
+                                                   float *__restrict__ un, float ax, float kd,
+                                                   float dt)
+{
+    __shared__ __align__(16) float su[DLY][DLX];
+    __shared__ __align__(16) float sp[DLY][DLX];
+    __shared__ float ss[DSY][DSX];
+    const int x0 = blockIdx.x * DTX, y0 = blockIdx.y * DTY;
+    // stage u and psi: DLY rows x DLX/4 float4 each (x0 - 4 is 16-byte aligned; nf % 4 == 0)
+    for (int k = threadIdx.x; k < DLY * (DLX / 4); k += DTH) {
+        const int r = k / (DLX / 4), q = k % (DLX / 4);
+        int gy = y0 - 2 + r; gy = gy < 0 ? gy + nf : (gy >= nf ? gy - nf : gy);
+        int gx = x0 - 4 + 4 * q; gx = gx < 0 ? gx + nf : (gx >= nf ? gx - nf : gx);
+        const long long off = (long long)gy * nf + gx;
+        const float4 a = *reinterpret_cast<const float4 *>(u + off);
+        const float4 b = *reinterpret_cast<const float4 *>(psi + off);
+        *reinterpret_cast<float4 *>(&su[r][4 * q]) = a;
+        *reinterpret_cast<float4 *>(&sp[r][4 * q]) = b;
+    }
+    __syncthreads();
+    // f(u) at staged coords (r, c): v1 = -(psi_N - psi_S) ax, v2 = (psi_E - psi_W) ax, ax = 1/(2h)
+    // stage 1 on rows y0-1 .. y0+TY, cols x0-1 .. x0+TX  (staged r = 1.., c = 3..)
+    for (int k = threadIdx.x; k < DSY * DSX; k += DTH) {
+        const int r = 1 + k / DSX, c = 3 + k % DSX;
+        const float uc = su[r][c], uE = su[r][c + 1], uW = su[r][c - 1], uN = su[r + 1][c], uS = su[r - 1][c];
+        const float v1 = (sp[r - 1][c] - sp[r + 1][c]) * ax;
+        const float v2 = (sp[r][c + 1] - sp[r][c - 1]) * ax;
+        const float f = v1 * (uE - uW) * ax + v2 * (uN - uS) * ax + kd * (uE + uW + uN + uS - 4.0f * uc);
+        ss[r - 1][c - 3] = uc + dt * f;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < DTY * DTX; k += DTH) {
+        const int ty = k / DTX, tx = k % DTX;
+        const int r = ty + 2, c = tx + 4;          // staged coords
+        const int sr = ty + 1, sc = tx + 1;        // stage-1 coords
+        const float sC = ss[sr][sc], sE = ss[sr][sc + 1], sW = ss[sr][sc - 1], sN = ss[sr + 1][sc], sS = ss[sr - 1][sc];
+        const float v1 = (sp[r - 1][c] - sp[r + 1][c]) * ax;
+        const float v2 = (sp[r][c + 1] - sp[r][c - 1]) * ax;
+        const float f = v1 * (sE - sW) * ax + v2 * (sN - sS) * ax + kd * (sE + sW + sN + sS - 4.0f * sC);
+        un[(long long)(y0 + ty) * nf + x0 + tx] = 0.5f * (su[r][c] + sC + dt * f);
+    }
+}
+
+// box average onto the macro grid; box[j*N+i] = FP64 sum of the box
+__global__ void k_coarse(int nf, const float *u, int N, float *U, double *box)
+{
+    __shared__ double red[32];
+    const int i = blockIdx.x, j = blockIdx.y, r = nf / N;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < r * r; k += blockDim.x) {
+        const int db = k / r, da = k % r;
+        int b = j * r - r / 2 + db; b = b < 0 ? b + nf : (b >= nf ? b - nf : b);
+        int a = i * r - r / 2 + da; a = a < 0 ? a + nf : (a >= nf ? a - nf : a);
+        s += (double)u[(long long)b * nf + a];
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        U[j * N + i] = (float)(s / ((double)r * r));
+        if (box) box[j * N + i] = s;
+    }
+}
+
+__global__ void k_sum(int n, const double *x, double scale, double *out)
+{
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s += x[k];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) *out = s * scale;
+}
+
+}  // namespace
+
+size_t macro_scratch_bytes(int N, int precision, int nsteps)
+{
+    const size_t rs = precision == MLSD_FP64 ? 8 : 4;
+    const size_t NN = (size_t)N * N;
+    if (N <= 64) return 0;
+    const size_t nblocks = (NN + 255) / 256;
+    return 4 * NN * rs + 256 + (size_t)(nsteps + 1) * nblocks * sizeof(double);
+}
+
+template <typename real>
+static cudaError_t macro_run_t(int N, real *U, const double *K, double dt, int nsteps,
+                               double *mass, void *scratch, cudaStream_t s)
+{
+    const int NN = N * N;
+    const double H = 2.0 * kPi / N;
+    if (N <= 64) {
+        const size_t smem = 5 * (size_t)NN * sizeof(real);
+        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_macro_resident<real>),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int threads = NN >= 1024 ? 1024 : ((NN + 31) / 32) * 32;
+        count_launches(1);
+        k_macro_resident<real><<<1, threads, smem, s>>>(N, U, K, (real)dt, nsteps, mass);
+        return cudaGetLastError();
+    }
+    real *Us = static_cast<real *>(scratch);
+    real *K11 = Us + NN, *K12 = K11 + NN, *K22 = K12 + NN;
+    const int th = 256, nb = (NN + th - 1) / th;
+    double *part = reinterpret_cast<double *>(
+        (reinterpret_cast<uintptr_t>(K22 + NN) + 255) & ~(uintptr_t)255);
+    count_launches(1 + 2 * (long long)nsteps + (mass ? 2 : 0));
+    k_split_K<real><<<nb, th, 0, s>>>(NN, K, K11, K12, K22);
+    if (mass) k_mass_part<real><<<nb, th, 0, s>>>(NN, U, part);
+    for (int st = 1; st <= nsteps; ++st) {
+        k_macro_stage<real, false><<<nb, th, 0, s>>>(N, U, Us, K11, K12, K22, (real)dt, nullptr);
+        k_macro_stage<real, true><<<nb, th, 0, s>>>(N, U, Us, K11, K12, K22, (real)dt,
+                                                    mass ? part + (size_t)st * nb : nullptr);
+    }
+    if (mass) k_mass_final<<<(nsteps + 1 + 127) / 128, 128, 0, s>>>(nsteps + 1, nb, part, H * H, mass);
+    return cudaGetLastError();
+}
+
+cudaError_t macro_run(int N, void *U, int precision, const double *K, double dt, int nsteps,
+                      double *mass_dev, void *scratch, cudaStream_t s)
+{
+    if (precision == MLSD_FP64)
+        return macro_run_t<double>(N, static_cast<double *>(U), K, dt, nsteps, mass_dev, scratch, s);
+    return macro_run_t<float>(N, static_cast<float *>(U), K, dt, nsteps, mass_dev, scratch, s);
+}
+
+cudaError_t macro_dt_max(int N, const double *K, double *max_dev, cudaStream_t s)
+{
+    count_launches(1);
+    k_kmax<<<1, 1024, 0, s>>>(N * N, K, max_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kappa, double dt,
+                    int nsteps, cudaStream_t s)
+{
+    const double h = 2.0 * kPi / nf;
+    const float ax = (float)(1.0 / (2.0 * h));
+    const float kd = (float)(kappa / (h * h));
+    dim3 grid(nf / DTX, nf / DTY);
+    float *a = u, *b = u_tmp;
+    count_launches(nsteps);
+    for (int st = 0; st < nsteps; ++st) {
+        k_dns_step<<<grid, DTH, 0, s>>>(nf, a, psi, b, ax, kd, (float)dt);
+        float *t = a; a = b; b = t;
+    }
+    if (a != u)
+        return cudaMemcpyAsync(u, a, (size_t)nf * nf * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError();
+}
+
+cudaError_t coarse_grain(int nf, const float *u, int N, float *U, double *mass_dev,
+                         cudaStream_t s)
+{
+    double *box = mass_dev ? mass_dev + 1 : nullptr;
+    count_launches(mass_dev ? 2 : 1);
+    k_coarse<<<dim3(N, N), 256, 0, s>>>(nf, u, N, U, box);
+    if (mass_dev) {
+        const double h = 2.0 * kPi / nf;
+        k_sum<<<1, 1024, 0, s>>>(N * N, box, h * h, mass_dev);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mlsd

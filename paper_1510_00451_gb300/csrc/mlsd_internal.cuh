@@ -1,0 +1,126 @@
+// Internal declarations shared by the translation units of libmlsd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/mlsd.h"
+
+namespace mlsd {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxLevels = 16;
+
+// ---------------------------------------------------------------------------
+// Patch solve launch description (one level, all patches).
+struct PatchParams {
+    const void *band;        // level band grid [Nl][Nl], float or double
+    long long Nl;            // band grid points per 2*pi
+    int n_macro;
+    double h, L;             // patch spacing and side
+    const double *Kb;        // [P][3] base diffusivity
+    double *S;               // [P][4] time-averaged (S11, S21, S12, S22)
+    void *wdump;             // [P][2][n][n] or nullptr
+    int *status;             // device status word
+    double cfl, t_burn, t_avg;
+    long long nb_fixed, na_fixed;
+    long long P;             // patches
+    long long item0, items;  // work items [item0, item0 + items), item = 2p + (j - 1)
+    long long *steps;        // [P] n_burn + n_avg per patch (written by the j = 1 CTA) or nullptr
+};
+
+// Variant of the patch kernel: thread block shape per patch size and precision.
+struct PatchVariant {
+    int n, precision, bx, by, threads;
+    size_t smem;
+    const void *fn;
+};
+
+int patch_variants(int n, int precision, std::vector<PatchVariant> &out);
+cudaError_t launch_patch(const PatchVariant &v, const PatchParams &p, long long grid,
+                         cudaStream_t s);
+
+// Combine the two fields' flux averages: K = B + sym(S).
+cudaError_t launch_compose(long long P, const double *B, const double *S, double *K,
+                           int *status, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Level chain (Algorithm 3) helpers.
+struct OffdiagLevel {
+    const double *q12;       // [P][n] line variances of psi_12 or nullptr
+    const double *q21;       // [P][n] line variances of psi_21 or nullptr
+    int n;
+};
+struct ChainTables {
+    int L;
+    long long P;
+    double kappa;
+    OffdiagLevel off[kMaxLevels];
+    double *B[kMaxLevels];       // [P][3]  base entering level l from above
+    double *Koff[kMaxLevels];    // [P][3]
+};
+cudaError_t launch_topdown(const ChainTables &t, cudaStream_t s);
+// base_l = K_off,l(K*_{l+1} - Koff_l + B_l) (or K_off,L(B_L) at the finest level);
+// also writes K*_{l+1} = base_{l+1} + sym(S_{l+1}) when Kstar_next != nullptr.
+cudaError_t launch_level_base(long long P, int finest, const double *base_next,
+                              const double *S_next, double *Kstar_next, const double *Koff_l,
+                              const double *B_l, OffdiagLevel off, double *base_out,
+                              cudaStream_t s);
+cudaError_t launch_offdiag_apply(long long P, OffdiagLevel off, const double *B, double *Koff,
+                                 cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Band synthesis (set-up): psi on an Nl x Nl lattice from a mode list.
+// Modes are grouped by k1: group g holds modes [gofs[g], gofs[g+1]) with
+// wavenumber gk1[g]; per mode k2, re, im.
+struct ModeGroups {
+    int n_groups;
+    const int *gk1;          // [n_groups]
+    const int *gofs;         // [n_groups + 1]
+    const int *k2;           // [n_modes]
+    const double *re, *im;   // [n_modes]
+};
+// G scratch: [n_groups][Nl] double2.  out: float or double [Nl][Nl].
+cudaError_t launch_band_synth(const ModeGroups &m, long long Nl, double2 *G, void *out,
+                              int out_double, cudaStream_t s);
+
+// Line variances of Algorithm 1 for every patch of a level (direct sums).
+struct ModeList {
+    int n;
+    const int *k1, *k2;
+    const double *re, *im;
+};
+cudaError_t launch_offdiag_q(const ModeList &m12, const ModeList &m21, long long Nl, int n,
+                             int r12, int r21, int n_macro, long long P, double *q12,
+                             double *q21, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Macro solver and direct simulation.
+cudaError_t macro_run(int N, void *U, int precision, const double *K, double dt, int nsteps,
+                      double *mass_dev, void *scratch, cudaStream_t s);
+size_t macro_scratch_bytes(int N, int precision, int nsteps);
+cudaError_t macro_dt_max(int N, const double *K, double *max_dev, cudaStream_t s);
+
+cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kappa, double dt,
+                    int nsteps, cudaStream_t s);
+cudaError_t coarse_grain(int nf, const float *u, int N, float *U, double *mass_dev,
+                         cudaStream_t s);
+
+// Kernel launch counter (host side, all launches of this library).
+void count_launches(long long n);
+long long launch_count();
+
+// Shared small device helpers ------------------------------------------------
+__host__ __device__ inline long long pmod_ll(long long a, long long m)
+{
+    long long r = a % m;
+    return r < 0 ? r + m : r;
+}
+// nearest lattice index to i * Nl / N (halves rounded up), minus n/2
+__host__ __device__ inline long long patch_origin(long long i, long long N, long long Nl, int n)
+{
+    return (2 * i * Nl + N) / (2 * N) - n / 2;
+}
+
+}  // namespace mlsd

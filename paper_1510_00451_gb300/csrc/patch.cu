@@ -1,0 +1,459 @@
+// Batched local patch solves: the numerical homogenization K[psi, B; Omega]
+// of Sec. 2.2 (HMM steps 1-3) for every macro node of one level.
+//
+// One CTA advances one corrector field w_j of one patch (work item 2p + j - 1)
+// for all its time steps with the whole field resident on chip:
+//   * every thread owns a BX x BY block of cells and keeps w, the Heun stage
+//     value and the two advection coefficients of its cells in registers;
+//   * per RK stage the block edges go through shared memory (rows row-major,
+//     columns in a transposed buffer, both 16-byte vectorised), one barrier
+//     per stage (double-buffered exchange);
+//   * the flux averages <v_i w_j> are summed in FP32 per thread over a window
+//     of at most 32 steps and then added to FP64 accumulators; the CTA reduces
+//     them in FP64 at the end.
+// The stencil is the second-order central-difference operator
+//   w_t = v1 (D0x w + d_j1) + v2 (D0y w + d_j2) + B11 Dxx w + 2 B12 Dxy w + B22 Dyy w
+// with Dxy w = (D0x w(b+1) - D0x w(b-1)) / (2h), i.e. the E-W differences of
+// the rows above and below, and Heun's RK2 w* = w + dt f(w),
+// w <- (w + w* + dt f(w*)) / 2 with dt folded into the coefficients.
+#include <cstdio>
+
+#include "mlsd_internal.cuh"
+
+namespace mlsd {
+namespace {
+
+constexpr int kFlush = 32;   // FP32 flux partials are flushed to FP64 this often (steps)
+constexpr long long kMaxSteps = 1ll << 30;   // larger step counts are rejected
+
+template <typename T, int CNT>
+__device__ __forceinline__ void st_vec(T *dst, const T (&src)[CNT])
+{
+    constexpr int bytes = CNT * (int)sizeof(T);
+    if constexpr (bytes % 16 == 0) {
+        constexpr int per = 16 / sizeof(T);
+#pragma unroll
+        for (int k = 0; k < CNT / per; ++k) {
+            if constexpr (sizeof(T) == 4)
+                reinterpret_cast<float4 *>(dst)[k] =
+                    make_float4(src[4 * k], src[4 * k + 1], src[4 * k + 2], src[4 * k + 3]);
+            else
+                reinterpret_cast<double2 *>(dst)[k] = make_double2(src[2 * k], src[2 * k + 1]);
+        }
+    } else if constexpr (bytes % 8 == 0 && sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < CNT / 2; ++k)
+            reinterpret_cast<float2 *>(dst)[k] = make_float2(src[2 * k], src[2 * k + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < CNT; ++k) dst[k] = src[k];
+    }
+}
+
+template <typename T, int CNT>
+__device__ __forceinline__ void ld_vec(T (&dst)[CNT], const T *src, int off = 0)
+{
+    constexpr int bytes = CNT * (int)sizeof(T);
+    if constexpr (bytes % 16 == 0) {
+        constexpr int per = 16 / sizeof(T);
+#pragma unroll
+        for (int k = 0; k < CNT / per; ++k) {
+            if constexpr (sizeof(T) == 4) {
+                float4 v = reinterpret_cast<const float4 *>(src)[k];
+                dst[off + 4 * k] = v.x; dst[off + 4 * k + 1] = v.y;
+                dst[off + 4 * k + 2] = v.z; dst[off + 4 * k + 3] = v.w;
+            } else {
+                double2 v = reinterpret_cast<const double2 *>(src)[k];
+                dst[off + 2 * k] = v.x; dst[off + 2 * k + 1] = v.y;
+            }
+        }
+    } else if constexpr (bytes % 8 == 0 && sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < CNT / 2; ++k) {
+            float2 v = reinterpret_cast<const float2 *>(src)[k];
+            dst[off + 2 * k] = v.x; dst[off + 2 * k + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < CNT; ++k) dst[off + k] = src[k];
+    }
+}
+
+// column-buffer row stride: n plus a 16-byte pad (conflict-free transposed stores)
+template <int N, typename real> struct Geo {
+    static constexpr int CS = N + 16 / (int)sizeof(real);
+};
+
+template <int N, int BX, int BY, typename real>
+struct Smem {
+    static constexpr int NBX = N / BX, NBY = N / BY;
+    static constexpr int CS = Geo<N, real>::CS;
+    static constexpr int ROW = NBY * N;          // one row buffer (top or bottom edges)
+    static constexpr int COL = NBX * CS;         // one column buffer (left or right edges)
+    static constexpr int STAGE = 2 * ROW + 2 * COL;
+    static constexpr int EXCH = 2 * STAGE;       // double buffered
+    static constexpr int SETUP = N * N;          // psi tile at set-up
+    static constexpr int WORDS = (EXCH > SETUP ? EXCH : SETUP);
+    static constexpr size_t BYTES = (size_t)WORDS * sizeof(real) + 64 * sizeof(double);
+};
+
+// Micro time step and window (same rules and operation order as the problem
+// statement in mlsd.h): CFL on advection and diffusion, the RK2 stability cap,
+// tau = L^2 / (4 pi^2 lambda_min).
+__device__ void micro_schedule(double h, double L, double vmax, double B11, double B12,
+                               double B22, double cfl, double t_burn, double t_avg,
+                               long long nb_fixed, long long na_fixed, double &dt,
+                               long long &nb, long long &na)
+{
+    double lmin = 0.5 * ((B11 + B22) - sqrt((B11 - B22) * (B11 - B22) + 4.0 * B12 * B12));
+    double dd = h * h / (2.0 * (B11 + B22) + 4.0 * fabs(B12));
+    dt = dd;
+    if (vmax > 0.0) {
+        double da = h / vmax;
+        if (da < dt) dt = da;
+    }
+    dt *= cfl;
+    if (vmax > 0.0) {
+        double ds = cbrt(8.0 * lmin * h * h / (vmax * vmax * vmax * vmax));
+        if (ds < dt) dt = ds;
+    }
+    double tau = L * L / (4.0 * kPi * kPi * lmin);
+    const double fb = ceil(t_burn * tau / dt), fa = ceil(t_avg * tau / dt);
+    // out-of-range counts (lmin <= 0, NaN) are mapped to -1 and rejected by the caller
+    nb = (fb >= 0.0 && fb < 4.0e18) ? (long long)fb : -1;
+    na = (fa >= 0.0 && fa < 4.0e18) ? (long long)fa : -1;
+    if (na == 0) na = 1;
+    if (!(lmin > 0.0)) { nb = -1; na = -1; }
+    if (na_fixed > 0) { nb = nb_fixed; na = na_fixed; }
+}
+
+template <int N, int BX, int BY, typename real>
+struct Tile {
+    static constexpr int NBX = N / BX, NBY = N / BY, NT = NBX * NBY;
+    using S = Smem<N, BX, BY, real>;
+
+    // Exchange the edges of x through buffer `buf`, then form
+    //   g = bc x + b11 (xE + xW) + b22 (xN + xS) + A1 (xE - xW [+2h]) + A2 (xN - xS [+2h])
+    //       + bx (dEW(b+1) - dEW(b-1)),
+    // i.e. x + dt f(x); SECOND: out = (w + g) / 2, else out = g.
+    template <int J, bool SECOND>
+    __device__ __forceinline__ static void stage(real *sm, int buf, int tx, int ty,
+                                                 const real (&x)[BY][BX], real (&out)[BY][BX],
+                                                 const real (&A1)[BY][BX], const real (&A2)[BY][BX],
+                                                 real b11, real b22, real bx, real bc, real twoh)
+    {
+        const int a0 = tx * BX, b0 = ty * BY;
+        real *rowT = sm + buf * S::STAGE;
+        real *rowB = rowT + S::ROW;
+        real *colL = rowB + S::ROW;
+        real *colR = colL + S::COL;
+        // publish edges
+        {
+            real t[BX], bt[BX];
+#pragma unroll
+            for (int c = 0; c < BX; ++c) { t[c] = x[0][c]; bt[c] = x[BY - 1][c]; }
+            st_vec<real, BX>(rowT + ty * N + a0, t);
+            st_vec<real, BX>(rowB + ty * N + a0, bt);
+            real l[BY], r[BY];
+#pragma unroll
+            for (int k = 0; k < BY; ++k) { l[k] = x[k][0]; r[k] = x[k][BX - 1]; }
+            st_vec<real, BY>(colL + tx * S::CS + b0, l);
+            st_vec<real, BY>(colR + tx * S::CS + b0, r);
+        }
+        __syncthreads();
+        // halos: south row b0-1, north row b0+BY, west column a0-1, east column a0+BX
+        real hS[BX], hN[BX], hW[BY + 2], hE[BY + 2];
+        {
+            const int tyS = (ty + NBY - 1) % NBY, tyN = (ty + 1) % NBY;
+            const int txW = (tx + NBX - 1) % NBX, txE = (tx + 1) % NBX;
+            ld_vec<real, BX>(hS, rowB + tyS * N + a0);
+            ld_vec<real, BX>(hN, rowT + tyN * N + a0);
+            const real *cw = colR + txW * S::CS;
+            const real *ce = colL + txE * S::CS;
+            real tmpw[BY], tmpe[BY];
+            ld_vec<real, BY>(tmpw, cw + b0);
+            ld_vec<real, BY>(tmpe, ce + b0);
+            const int bs = (b0 + N - 1) % N, bn = (b0 + BY) % N;
+            hW[0] = cw[bs]; hE[0] = ce[bs];
+            hW[BY + 1] = cw[bn]; hE[BY + 1] = ce[bn];
+#pragma unroll
+            for (int k = 0; k < BY; ++k) { hW[k + 1] = tmpw[k]; hE[k + 1] = tmpe[k]; }
+        }
+        // rolling E-W differences of rows r-1, r, r+1
+        real dm[BX], d0[BX], dp[BX];
+#pragma unroll
+        for (int c = 0; c < BX; ++c) {
+            real e = (c + 1 < BX) ? hS[c + 1] : hE[0];
+            real w = (c > 0) ? hS[c - 1] : hW[0];
+            dm[c] = e - w;
+            real e0 = (c + 1 < BX) ? x[0][c + 1] : hE[1];
+            real w0 = (c > 0) ? x[0][c - 1] : hW[1];
+            d0[c] = e0 - w0;
+        }
+#pragma unroll
+        for (int r = 0; r < BY; ++r) {
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                real e, w;
+                if (r + 1 < BY) {
+                    e = (c + 1 < BX) ? x[r + 1][c + 1] : hE[r + 2];
+                    w = (c > 0) ? x[r + 1][c - 1] : hW[r + 2];
+                } else {
+                    e = (c + 1 < BX) ? hN[c + 1] : hE[BY + 1];
+                    w = (c > 0) ? hN[c - 1] : hW[BY + 1];
+                }
+                dp[c] = e - w;
+            }
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                const real xc = x[r][c];
+                const real xE = (c + 1 < BX) ? x[r][c + 1] : hE[r + 1];
+                const real xW = (c > 0) ? x[r][c - 1] : hW[r + 1];
+                const real xN = (r + 1 < BY) ? x[r + 1][c] : hN[c];
+                const real xS = (r > 0) ? x[r - 1][c] : hS[c];
+                real d1 = d0[c];
+                real d2 = xN - xS;
+                if constexpr (J == 1) d1 = d1 + twoh; else d2 = d2 + twoh;
+                const real s1 = xE + xW, s2 = xN + xS;
+                const real cr = dp[c] - dm[c];
+                real g = A1[r][c] * d1;
+                g = fma(A2[r][c], d2, g);
+                g = fma(b11, s1, g);
+                g = fma(b22, s2, g);
+                g = fma(bx, cr, g);
+                g = fma(bc, xc, g);
+                if constexpr (SECOND) out[r][c] = (real)0.5 * (out[r][c] + g);
+                else out[r][c] = g;
+            }
+#pragma unroll
+            for (int c = 0; c < BX; ++c) { dm[c] = d0[c]; d0[c] = dp[c]; }
+        }
+    }
+
+    template <int J>
+    __device__ static void run(const PatchParams &prm, real *sm, long long p)
+    {
+        const int tid = threadIdx.x, tx = tid % NBX, ty = tid / NBX;
+        const int a0 = tx * BX, b0 = ty * BY;
+        double *red = reinterpret_cast<double *>(sm + S::WORDS);
+        const long long Nl = prm.Nl;
+        const long long pi = p % prm.n_macro, pj = p / prm.n_macro;
+        const long long ox = patch_origin(pi, prm.n_macro, Nl, N);
+        const long long oy = patch_origin(pj, prm.n_macro, Nl, N);
+
+        // ---- set-up: psi tile (patch-periodic), velocity, time step --------
+        real *psi = sm;
+        const real *band = static_cast<const real *>(prm.band);
+        for (int c = tid; c < N * N; c += NT) {
+            const int b = c / N, a = c % N;
+            psi[c] = band[pmod_ll(oy + b, Nl) * Nl + pmod_ll(ox + a, Nl)];
+        }
+        __syncthreads();
+        const real inv2h = (real)(1.0 / (2.0 * prm.h));
+        real A1[BY][BX], A2[BY][BX];
+        real vmax = 0;
+#pragma unroll
+        for (int r = 0; r < BY; ++r) {
+            const int b = b0 + r, bp = (b + 1) % N, bm = (b + N - 1) % N;
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                const int a = a0 + c, ap = (a + 1) % N, am = (a + N - 1) % N;
+                const real v1 = (psi[bm * N + a] - psi[bp * N + a]) * inv2h;
+                const real v2 = (psi[b * N + ap] - psi[b * N + am]) * inv2h;
+                A1[r][c] = v1;
+                A2[r][c] = v2;
+                vmax = fmax(vmax, fabs(v1) + fabs(v2));
+            }
+        }
+        // block max of |v1| + |v2|
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if ((tid & 31) == 0) red[tid >> 5] = (double)vmax;
+        __syncthreads();
+        double vm = 0.0;
+        for (int k = 0; k < (NT + 31) / 32; ++k) vm = fmax(vm, red[k]);
+
+        const double B11 = prm.Kb[3 * p], B12 = prm.Kb[3 * p + 1], B22 = prm.Kb[3 * p + 2];
+        double dt;
+        long long nb, na;
+        micro_schedule(prm.h, prm.L, vm, B11, B12, B22, prm.cfl, prm.t_burn, prm.t_avg,
+                       prm.nb_fixed, prm.na_fixed, dt, nb, na);
+        // a base tensor that is not positive definite (or not finite) gives no usable
+        // schedule: latch an error and return instead of stepping
+        if (!(dt > 0.0) || !isfinite(dt) || nb < 0 || na < 1 || nb + na > kMaxSteps) {
+            if (tid == 0) {
+                prm.S[4 * p + 2 * (J - 1)] = __longlong_as_double(0x7ff8000000000000ll);
+                prm.S[4 * p + 2 * (J - 1) + 1] = __longlong_as_double(0x7ff8000000000000ll);
+                atomicCAS(prm.status, 0, MLSD_EINVAL);
+            }
+            return;
+        }
+        if (J == 1 && tid == 0 && prm.steps) prm.steps[p] = nb + na;
+        const double hh = prm.h * prm.h;
+        const real cA = (real)(dt / (2.0 * prm.h));
+        const real b11 = (real)(dt * B11 / hh), b22 = (real)(dt * B22 / hh);
+        const real bx = (real)(dt * B12 / (2.0 * hh));
+        const real bc = (real)(1.0 - 2.0 * (dt * B11 / hh + dt * B22 / hh));
+        const real twoh = (real)(2.0 * prm.h);
+#pragma unroll
+        for (int r = 0; r < BY; ++r)
+#pragma unroll
+            for (int c = 0; c < BX; ++c) { A1[r][c] *= cA; A2[r][c] *= cA; }
+        __syncthreads();   // psi tile is dead; its space becomes the exchange buffers
+
+        // ---- time stepping ------------------------------------------------
+        real w[BY][BX], s[BY][BX];
+#pragma unroll
+        for (int r = 0; r < BY; ++r)
+#pragma unroll
+            for (int c = 0; c < BX; ++c) w[r][c] = 0;
+        real p1 = 0, p2 = 0;
+        double f1 = 0.0, f2 = 0.0;
+        int win = 0;
+        const long long ntot = nb + na;
+        for (long long step = 0; step < ntot; ++step) {
+            stage<J, false>(sm, 0, tx, ty, w, s, A1, A2, b11, b22, bx, bc, twoh);
+            stage<J, true>(sm, 1, tx, ty, s, w, A1, A2, b11, b22, bx, bc, twoh);
+            if (step >= nb) {
+                real q1 = 0, q2 = 0;
+#pragma unroll
+                for (int r = 0; r < BY; ++r)
+#pragma unroll
+                    for (int c = 0; c < BX; ++c) {
+                        q1 = fma(A1[r][c], w[r][c], q1);
+                        q2 = fma(A2[r][c], w[r][c], q2);
+                    }
+                p1 += q1;
+                p2 += q2;
+                if (++win == kFlush) { f1 += (double)p1; f2 += (double)p2; p1 = 0; p2 = 0; win = 0; }
+            }
+        }
+        f1 += (double)p1;
+        f2 += (double)p2;
+
+        // ---- outputs ------------------------------------------------------
+        if (prm.wdump) {
+            real *wd = static_cast<real *>(prm.wdump) + (2 * p + (J - 1)) * (long long)N * N;
+#pragma unroll
+            for (int r = 0; r < BY; ++r)
+#pragma unroll
+                for (int c = 0; c < BX; ++c) wd[(b0 + r) * N + a0 + c] = w[r][c];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            f1 += __shfl_xor_sync(0xffffffffu, f1, o);
+            f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+        }
+        __syncthreads();
+        if ((tid & 31) == 0) { red[2 * (tid >> 5)] = f1; red[2 * (tid >> 5) + 1] = f2; }
+        __syncthreads();
+        if (tid == 0) {
+            double t1 = 0.0, t2 = 0.0;
+            for (int k = 0; k < (NT + 31) / 32; ++k) { t1 += red[2 * k]; t2 += red[2 * k + 1]; }
+            // v_i = A_i / cA;  S_ij = (1/na) sum_steps mean_cells v_i w_j
+            const double scale = 1.0 / ((double)cA * (double)N * (double)N * (double)na);
+            const double s1j = t1 * scale, s2j = t2 * scale;
+            prm.S[4 * p + 2 * (J - 1)] = s1j;
+            prm.S[4 * p + 2 * (J - 1) + 1] = s2j;
+            if (!isfinite(s1j) || !isfinite(s2j)) atomicCAS(prm.status, 0, MLSD_ENONFINITE);
+        }
+    }
+};
+
+template <int N, int BX, int BY, typename real>
+__global__ void __launch_bounds__((N / BX) * (N / BY))
+k_patch_solve(PatchParams prm)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *sm = reinterpret_cast<real *>(smem_raw);
+    const long long item = prm.item0 + blockIdx.x;
+    if (item >= prm.item0 + prm.items) return;
+    const long long p = item >> 1;
+    if (item & 1) Tile<N, BX, BY, real>::template run<2>(prm, sm, p);
+    else Tile<N, BX, BY, real>::template run<1>(prm, sm, p);
+}
+
+template <int N, int BX, int BY, typename real>
+void add_variant(std::vector<PatchVariant> &out)
+{
+    PatchVariant v;
+    v.n = N;
+    v.precision = sizeof(real) == 4 ? MLSD_FP32 : MLSD_FP64;
+    v.bx = BX;
+    v.by = BY;
+    v.threads = (N / BX) * (N / BY);
+    v.smem = Smem<N, BX, BY, real>::BYTES;
+    v.fn = reinterpret_cast<const void *>(&k_patch_solve<N, BX, BY, real>);
+    out.push_back(v);
+}
+
+__global__ void k_compose(long long P, const double *B, const double *S, double *K, int *status)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const double *b = B + 3 * p, *s = S + 4 * p;
+    // P_1 = B e_1 + S_.1, P_2 = B e_2 + S_.2; K = sym(P)
+    double P11 = b[0] + s[0], P21 = b[1] + s[1], P12 = b[1] + s[2], P22 = b[2] + s[3];
+    double k12 = 0.5 * (P21 + P12);
+    K[3 * p] = P11;
+    K[3 * p + 1] = k12;
+    K[3 * p + 2] = P22;
+    if (!isfinite(P11) || !isfinite(k12) || !isfinite(P22)) atomicCAS(status, 0, MLSD_ENONFINITE);
+}
+
+}  // namespace
+
+int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
+{
+    out.clear();
+    if (precision == MLSD_FP32) {
+        switch (n) {
+        case 32:
+            add_variant<32, 4, 8, float>(out);
+            add_variant<32, 4, 4, float>(out);
+            break;
+        case 64:
+            add_variant<64, 4, 8, float>(out);
+            add_variant<64, 4, 4, float>(out);
+            add_variant<64, 8, 4, float>(out);
+            add_variant<64, 2, 8, float>(out);
+            break;
+        default: break;
+        }
+    } else {
+        switch (n) {
+        case 32:
+            add_variant<32, 2, 4, double>(out);
+            add_variant<32, 4, 4, double>(out);
+            break;
+        case 64:
+            add_variant<64, 2, 4, double>(out);
+            add_variant<64, 4, 4, double>(out);
+            break;
+        default: break;
+        }
+    }
+    return (int)out.size();
+}
+
+cudaError_t launch_patch(const PatchVariant &v, const PatchParams &p, long long grid,
+                         cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)v.smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {const_cast<PatchParams *>(&p)};
+    count_launches(1);
+    return cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.threads), args, v.smem, s);
+}
+
+cudaError_t launch_compose(long long P, const double *B, const double *S, double *K,
+                           int *status, cudaStream_t s)
+{
+    const int t = 256;
+    count_launches(1);
+    k_compose<<<(unsigned)((P + t - 1) / t), t, 0, s>>>(P, B, S, K, status);
+    return cudaGetLastError();
+}
+
+}  // namespace mlsd

@@ -1,0 +1,584 @@
+// Host runtime and C ABI (include/mlsd.h): level tables, device buffers,
+// Algorithm 3 orchestration, error handling.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <utility>
+#include <vector>
+
+#include "mlsd_internal.cuh"
+
+using namespace mlsd;
+
+namespace mlsd {
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace mlsd
+
+namespace {
+
+#define CK(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)",    \
+                          #call, cudaGetErrorString(e_), __FILE__, __LINE__);      \
+            return e_ == cudaErrorMemoryAllocation ? MLSD_ENOMEM : MLSD_ECUDA;     \
+        }                                                                          \
+    } while (0)
+
+thread_local char g_last_error[512] = "";
+
+struct DevLevel {
+    int n = 0;
+    int m = 1;                  // patch side L = 2 pi / m
+    long long Nl = 0;           // n * m
+    double L = 0, h = 0;
+    int n_diag = 0, n_12 = 0, n_21 = 0;
+    int r12 = 1, r21 = 1;       // Algorithm 1 line refinement
+    void *band = nullptr;       // [Nl][Nl] float or double
+    double *q12 = nullptr, *q21 = nullptr;   // [P][n] or null
+    double *B = nullptr, *Koff = nullptr, *base = nullptr, *S = nullptr, *Kstar = nullptr;
+    long long *steps = nullptr; // [P] n_burn + n_avg of the last solve
+    PatchVariant variant{};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;   // profiling: one pair per launch
+};
+
+}  // namespace
+
+struct mlsd_levels {
+    int N = 0;
+    long long P = 0;
+    int L = 0;
+    int precision = MLSD_FP32;
+    double kappa = 0, cfl = 0.2, t_burn = 8, t_avg = 4;
+    long long nb_fixed = 0, na_fixed = 0;
+    std::vector<DevLevel> lev;
+    int *status = nullptr;
+    std::vector<void *> allocs;
+    bool profile = false;
+};
+
+namespace {
+
+int dev_alloc(mlsd_levels *h, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) return MLSD_OK;
+    CK(cudaMalloc(p, bytes));
+    h->allocs.push_back(*p);
+    return MLSD_OK;
+}
+
+int level_of_mag(int m, int L, const double *e)
+{
+    for (int l = 1; l <= L; ++l) {
+        const double lo = (l == 1) ? 0.0 : e[l - 1];
+        if ((double)m >= lo && (double)m < e[l]) return l;
+    }
+    return L + 1;
+}
+
+struct HostMode { int k1, k2; double re, im; };
+
+// group modes by k1 and upload: returns device ModeGroups pointing into `blob`
+int upload_groups(mlsd_levels *h, const std::vector<HostMode> &modes, ModeGroups &g)
+{
+    std::vector<HostMode> ms = modes;
+    std::sort(ms.begin(), ms.end(), [](const HostMode &a, const HostMode &b) {
+        return a.k1 != b.k1 ? a.k1 < b.k1 : a.k2 < b.k2;
+    });
+    std::vector<int> gk1, gofs, k2;
+    std::vector<double> re, im;
+    for (size_t t = 0; t < ms.size(); ++t) {
+        if (t == 0 || ms[t].k1 != ms[t - 1].k1) { gk1.push_back(ms[t].k1); gofs.push_back((int)t); }
+        k2.push_back(ms[t].k2); re.push_back(ms[t].re); im.push_back(ms[t].im);
+    }
+    gofs.push_back((int)ms.size());
+    g.n_groups = (int)gk1.size();
+    if (ms.empty()) { g.gk1 = g.gofs = g.k2 = nullptr; g.re = g.im = nullptr; return MLSD_OK; }
+    void *p[5];
+    int rc;
+    if ((rc = dev_alloc(h, &p[0], gk1.size() * 4))) return rc;
+    if ((rc = dev_alloc(h, &p[1], gofs.size() * 4))) return rc;
+    if ((rc = dev_alloc(h, &p[2], k2.size() * 4))) return rc;
+    if ((rc = dev_alloc(h, &p[3], re.size() * 8))) return rc;
+    if ((rc = dev_alloc(h, &p[4], im.size() * 8))) return rc;
+    CK(cudaMemcpy(p[0], gk1.data(), gk1.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p[1], gofs.data(), gofs.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p[2], k2.data(), k2.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p[3], re.data(), re.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p[4], im.data(), im.size() * 8, cudaMemcpyHostToDevice));
+    g.gk1 = (int *)p[0]; g.gofs = (int *)p[1]; g.k2 = (int *)p[2];
+    g.re = (double *)p[3]; g.im = (double *)p[4];
+    return MLSD_OK;
+}
+
+int upload_list(mlsd_levels *h, const std::vector<HostMode> &modes, ModeList &m)
+{
+    m.n = (int)modes.size();
+    m.k1 = m.k2 = nullptr; m.re = m.im = nullptr;
+    if (modes.empty()) return MLSD_OK;
+    std::vector<int> k1, k2;
+    std::vector<double> re, im;
+    for (auto &x : modes) { k1.push_back(x.k1); k2.push_back(x.k2); re.push_back(x.re); im.push_back(x.im); }
+    void *p[4];
+    int rc;
+    if ((rc = dev_alloc(h, &p[0], k1.size() * 4))) return rc;
+    if ((rc = dev_alloc(h, &p[1], k2.size() * 4))) return rc;
+    if ((rc = dev_alloc(h, &p[2], re.size() * 8))) return rc;
+    if ((rc = dev_alloc(h, &p[3], im.size() * 8))) return rc;
+    CK(cudaMemcpy(p[0], k1.data(), k1.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p[1], k2.data(), k2.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p[2], re.data(), re.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p[3], im.data(), im.size() * 8, cudaMemcpyHostToDevice));
+    m.k1 = (int *)p[0]; m.k2 = (int *)p[1]; m.re = (double *)p[2]; m.im = (double *)p[3];
+    return MLSD_OK;
+}
+
+// refinement of the line samples of Algorithm 1: at least 10 samples per
+// wavelength of the finest wavenumber along the line, a multiple of n in all
+int line_refine(const std::vector<HostMode> &ms, bool along_x2, double L, int n)
+{
+    int kmax = 0;
+    for (auto &x : ms) kmax = std::max(kmax, std::abs(along_x2 ? x.k2 : x.k1));
+    const double need = 10.0 * kmax * L / (2.0 * kPi);
+    const int r = (int)std::ceil(need / (double)n);
+    return r < 1 ? 1 : r;
+}
+
+int validate(const mlsd_problem *p)
+{
+    if (!p || p->n_macro < 1 || !(p->kappa > 0) || p->n_levels < 1 || p->n_levels > kMaxLevels)
+        return MLSD_EINVAL;
+    if (p->n_modes < 0 || (p->n_modes > 0 && (!p->k1 || !p->k2 || !p->re || !p->im)))
+        return MLSD_EINVAL;
+    if (!p->band_edges || !p->patch_n || !(p->cfl > 0)) return MLSD_EINVAL;
+    if (p->precision != MLSD_FP32 && p->precision != MLSD_FP64) return MLSD_EINVAL;
+    for (int l = 0; l < p->n_levels; ++l)
+        if (!(p->band_edges[l + 1] > p->band_edges[l])) return MLSD_EINVAL;
+    if (p->n_avg_fixed <= 0 && (!(p->t_burn_tau >= 0) || !(p->t_avg_tau > 0))) return MLSD_EINVAL;
+    if (p->n_avg_fixed > 0 && p->n_burn_fixed < 0) return MLSD_EINVAL;
+    // Hermitian completeness and no k = 0
+    std::map<std::pair<int, int>, std::pair<double, double>> mm;
+    for (int t = 0; t < p->n_modes; ++t) {
+        if (p->k1[t] == 0 && p->k2[t] == 0) return MLSD_EINVAL;
+        if (!std::isfinite(p->re[t]) || !std::isfinite(p->im[t])) return MLSD_EINVAL;
+        mm[{p->k1[t], p->k2[t]}] = {p->re[t], p->im[t]};
+    }
+    for (auto &kv : mm) {
+        auto it = mm.find({-kv.first.first, -kv.first.second});
+        if (it == mm.end()) return MLSD_EINVAL;
+        const double tol = 1e-12 * (std::fabs(kv.second.first) + std::fabs(kv.second.second) + 1e-300);
+        if (std::fabs(it->second.first - kv.second.first) > tol ||
+            std::fabs(it->second.second + kv.second.second) > tol)
+            return MLSD_EINVAL;
+    }
+    return MLSD_OK;
+}
+
+int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
+{
+    int rc;
+    h->N = p->n_macro;
+    h->P = (long long)p->n_macro * p->n_macro;
+    h->L = p->n_levels;
+    h->precision = p->precision;
+    h->kappa = p->kappa;
+    h->cfl = p->cfl;
+    h->t_burn = p->t_burn_tau;
+    h->t_avg = p->t_avg_tau;
+    h->nb_fixed = p->n_burn_fixed;
+    h->na_fixed = p->n_avg_fixed;
+    if ((rc = dev_alloc(h, (void **)&h->status, sizeof(int)))) return rc;
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+
+    // Sec. 3.1 decomposition: per level, diagonal band and off-diagonal parts
+    const int L = p->n_levels;
+    std::vector<std::vector<HostMode>> diag(L), off12(L), off21(L);
+    for (int t = 0; t < p->n_modes; ++t) {
+        const int la = level_of_mag(std::abs(p->k1[t]), L, p->band_edges);
+        const int lb = level_of_mag(std::abs(p->k2[t]), L, p->band_edges);
+        const HostMode m{p->k1[t], p->k2[t], p->re[t], p->im[t]};
+        if (la == lb) { if (la <= L) diag[la - 1].push_back(m); }
+        else if (la < lb) off12[la - 1].push_back(m);
+        else off21[lb - 1].push_back(m);
+    }
+    h->lev.resize(L);
+    const size_t rs = p->precision == MLSD_FP64 ? 8 : 4;
+    for (int l = 0; l < L; ++l) {
+        DevLevel &d = h->lev[l];
+        d.n = p->patch_n[l];
+        if (p->patch_div) d.m = p->patch_div[l];
+        else {
+            const double e = p->band_edges[l];
+            d.m = (int)std::llround(e);
+            if (std::fabs(e - d.m) > 0 || d.m < 1) return MLSD_EINVAL;
+        }
+        if (d.m < 1) return MLSD_EINVAL;
+        std::vector<PatchVariant> vs;
+        if (patch_variants(d.n, p->precision, vs) == 0) return MLSD_EUNSUPPORTED;
+        d.variant = vs[0];
+        d.Nl = (long long)d.n * d.m;
+        d.L = 2.0 * kPi / d.m;
+        d.h = d.L / d.n;
+        d.n_diag = (int)diag[l].size();
+        d.n_12 = (int)off12[l].size();
+        d.n_21 = (int)off21[l].size();
+
+        // band grid (set-up)
+        ModeGroups g;
+        if ((rc = upload_groups(h, diag[l], g))) return rc;
+        if ((rc = dev_alloc(h, &d.band, (size_t)d.Nl * d.Nl * rs))) return rc;
+        void *G = nullptr;
+        if (g.n_groups > 0) CK(cudaMalloc(&G, (size_t)g.n_groups * d.Nl * sizeof(double2)));
+        cudaError_t e = launch_band_synth(g, d.Nl, static_cast<double2 *>(G), d.band,
+                                          p->precision == MLSD_FP64, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (G) cudaFree(G);
+        CK(e);
+
+        // Algorithm 1 line variances (set-up; independent of the base tensor)
+        ModeList m12, m21;
+        if ((rc = upload_list(h, off12[l], m12))) return rc;
+        if ((rc = upload_list(h, off21[l], m21))) return rc;
+        d.r12 = line_refine(off12[l], true, d.L, d.n);
+        d.r21 = line_refine(off21[l], false, d.L, d.n);
+        if (d.n_12 && (rc = dev_alloc(h, (void **)&d.q12, (size_t)h->P * d.n * 8))) return rc;
+        if (d.n_21 && (rc = dev_alloc(h, (void **)&d.q21, (size_t)h->P * d.n * 8))) return rc;
+        CK(launch_offdiag_q(m12, m21, d.Nl, d.n, d.r12, d.r21, h->N, h->P, d.q12, d.q21, s));
+
+        // per-level tensors
+        if ((rc = dev_alloc(h, (void **)&d.B, (size_t)h->P * 3 * 8))) return rc;
+        if ((rc = dev_alloc(h, (void **)&d.Koff, (size_t)h->P * 3 * 8))) return rc;
+        if ((rc = dev_alloc(h, (void **)&d.base, (size_t)h->P * 3 * 8))) return rc;
+        if ((rc = dev_alloc(h, (void **)&d.Kstar, (size_t)h->P * 3 * 8))) return rc;
+        if ((rc = dev_alloc(h, (void **)&d.S, (size_t)h->P * 4 * 8))) return rc;
+        if ((rc = dev_alloc(h, (void **)&d.steps, (size_t)h->P * 8))) return rc;
+        CK(cudaMemsetAsync(d.steps, 0, (size_t)h->P * 8, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return MLSD_OK;
+}
+
+OffdiagLevel off_of(const DevLevel &d)
+{
+    OffdiagLevel o;
+    o.q12 = d.q12;
+    o.q21 = d.q21;
+    o.n = d.n;
+    return o;
+}
+
+PatchParams patch_params(const mlsd_levels *h, const DevLevel &d, const double *Kb, double *S,
+                         void *wdump)
+{
+    PatchParams pp;
+    pp.band = d.band;
+    pp.Nl = d.Nl;
+    pp.n_macro = h->N;
+    pp.h = d.h;
+    pp.L = d.L;
+    pp.Kb = Kb;
+    pp.S = S;
+    pp.wdump = wdump;
+    pp.status = h->status;
+    pp.cfl = h->cfl;
+    pp.t_burn = h->t_burn;
+    pp.t_avg = h->t_avg;
+    pp.nb_fixed = h->nb_fixed;
+    pp.na_fixed = h->na_fixed;
+    pp.P = h->P;
+    pp.item0 = 0;
+    pp.items = 2 * h->P;
+    pp.steps = d.steps;
+    return pp;
+}
+
+int run_patches(mlsd_levels *h, DevLevel &d, const double *Kb, double *S, void *wdump,
+                cudaStream_t s)
+{
+    PatchParams pp = patch_params(h, d, Kb, S, wdump);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->profile) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, s));
+    }
+    CK(launch_patch(d.variant, pp, pp.items, s));
+    if (h->profile) {
+        CK(cudaEventRecord(e1, s));
+        d.ev.emplace_back(e0, e1);
+    }
+    return MLSD_OK;
+}
+
+void drop_events(DevLevel &d)
+{
+    for (auto &e : d.ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    d.ev.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mlsd_strerror(int code)
+{
+    switch (code) {
+    case MLSD_OK: return "ok";
+    case MLSD_EINVAL: return "invalid argument";
+    case MLSD_ENOMEM: return "out of memory";
+    case MLSD_ECUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+    case MLSD_ETIMEOUT: return "device wait timed out";
+    case MLSD_ENONFINITE: return "non-finite value in a result";
+    case MLSD_EUNSUPPORTED: return "unsupported configuration";
+    default: return "unknown error";
+    }
+}
+
+int mlsd_build_levels(const mlsd_problem *p, void *cuda_stream, mlsd_levels **out)
+{
+    if (!out) return MLSD_EINVAL;
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    mlsd_levels *h = new (std::nothrow) mlsd_levels();
+    if (!h) return MLSD_ENOMEM;
+    rc = build(p, static_cast<cudaStream_t>(cuda_stream), h);
+    if (rc) { mlsd_free_levels(h); return rc; }
+    *out = h;
+    return MLSD_OK;
+}
+
+void mlsd_free_levels(mlsd_levels *h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    for (auto &d : h->lev) drop_events(d);
+    for (void *p : h->allocs) cudaFree(p);
+    delete h;
+}
+
+int mlsd_level_info(const mlsd_levels *h, int level, mlsd_level_desc *out)
+{
+    if (!h || !out || level < 1 || level > h->L) return MLSD_EINVAL;
+    const DevLevel &d = h->lev[level - 1];
+    out->n = d.n;
+    out->Nl = d.Nl;
+    out->L = d.L;
+    out->h = d.h;
+    out->n_patches = h->P;
+    out->n_diag_modes = d.n_diag;
+    out->n_off12_modes = d.n_12;
+    out->n_off21_modes = d.n_21;
+    return MLSD_OK;
+}
+
+int mlsd_solve_level(mlsd_levels *h, int level, const double *K_base_dev, double *K_out_dev,
+                     void *w_dump_dev, void *cuda_stream)
+{
+    if (!h || level < 1 || level > h->L || !K_base_dev || !K_out_dev || K_base_dev == K_out_dev)
+        return MLSD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    DevLevel &d = h->lev[level - 1];
+    int rc = run_patches(h, d, K_base_dev, d.S, w_dump_dev, s);
+    if (rc) return rc;
+    CK(launch_compose(h->P, K_base_dev, d.S, K_out_dev, h->status, s));
+    return MLSD_OK;
+}
+
+int mlsd_offdiag(mlsd_levels *h, int level, const double *B_dev, double *Koff_dev,
+                 void *cuda_stream)
+{
+    if (!h || level < 1 || level > h->L || !B_dev || !Koff_dev) return MLSD_EINVAL;
+    CK(launch_offdiag_apply(h->P, off_of(h->lev[level - 1]), B_dev, Koff_dev,
+                            static_cast<cudaStream_t>(cuda_stream)));
+    return MLSD_OK;
+}
+
+int mlsd_effective_diffusivity(mlsd_levels *h, int mode, double *K_macro_dev,
+                               double *K_levels_dev, void *cuda_stream)
+{
+    if (!h || !K_macro_dev) return MLSD_EINVAL;
+    if (mode != MLSD_PLAIN) return MLSD_EUNSUPPORTED;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int L = h->L;
+    ChainTables t;
+    t.L = L;
+    t.P = h->P;
+    t.kappa = h->kappa;
+    for (int l = 0; l < L; ++l) {
+        t.off[l] = off_of(h->lev[l]);
+        t.B[l] = h->lev[l].B;
+        t.Koff[l] = h->lev[l].Koff;
+    }
+    CK(launch_topdown(t, s));
+    for (int l = L - 1; l >= 0; --l) {
+        DevLevel &d = h->lev[l];
+        const bool finest = (l == L - 1);
+        const DevLevel *nx = finest ? nullptr : &h->lev[l + 1];
+        CK(launch_level_base(h->P, finest ? 1 : 0, nx ? nx->base : nullptr, nx ? nx->S : nullptr,
+                             nx ? nx->Kstar : nullptr, d.Koff, d.B, off_of(d), d.base, s));
+        int rc = run_patches(h, d, d.base, d.S, nullptr, s);
+        if (rc) return rc;
+    }
+    DevLevel &c = h->lev[0];
+    CK(launch_compose(h->P, c.base, c.S, c.Kstar, h->status, s));
+    CK(cudaMemcpyAsync(K_macro_dev, c.Kstar, (size_t)h->P * 3 * 8, cudaMemcpyDeviceToDevice, s));
+    if (K_levels_dev) {
+        for (int l = 0; l < L; ++l)
+            CK(cudaMemcpyAsync(K_levels_dev + (size_t)l * h->P * 3, h->lev[l].Kstar,
+                               (size_t)h->P * 3 * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    return MLSD_OK;
+}
+
+int mlsd_status(mlsd_levels *h, void *cuda_stream)
+{
+    if (!h) return MLSD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    CK(cudaStreamSynchronize(s));
+    int v = 0;
+    CK(cudaMemcpy(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v) CK(cudaMemset(h->status, 0, sizeof(int)));
+    return v;
+}
+
+int mlsd_level_work(mlsd_levels *h, int level, int64_t *cell_updates_out,
+                    int64_t *max_steps_out, void *cuda_stream)
+{
+    if (!h || level < 1 || level > h->L) return MLSD_EINVAL;
+    const DevLevel &d = h->lev[level - 1];
+    std::vector<long long> st((size_t)h->P);
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
+    CK(cudaMemcpy(st.data(), d.steps, (size_t)h->P * 8, cudaMemcpyDeviceToHost));
+    long long tot = 0, mx = 0;
+    for (long long v : st) { tot += v; mx = std::max(mx, v); }
+    if (cell_updates_out) *cell_updates_out = tot * 2 * (long long)d.n * d.n;
+    if (max_steps_out) *max_steps_out = mx;
+    return MLSD_OK;
+}
+
+int64_t mlsd_launch_count(void) { return launch_count(); }
+
+int mlsd_profile(mlsd_levels *h, int enable)
+{
+    if (!h) return MLSD_EINVAL;
+    h->profile = enable != 0;
+    return MLSD_OK;
+}
+
+int mlsd_profile_collect(mlsd_levels *h, int level, double *kernel_ms_out, int64_t *launches_out)
+{
+    if (!h || level < 1 || level > h->L) return MLSD_EINVAL;
+    DevLevel &d = h->lev[level - 1];
+    double tot = 0.0;
+    for (auto &e : d.ev) {
+        CK(cudaEventSynchronize(e.second));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e.first, e.second));
+        tot += ms;
+    }
+    if (kernel_ms_out) *kernel_ms_out = tot;
+    if (launches_out) *launches_out = (int64_t)d.ev.size();
+    drop_events(d);
+    return MLSD_OK;
+}
+
+int mlsd_macro_step(int n_macro, void *U_dev, int precision, const double *K_dev, double dt,
+                    int nsteps, double *mass_out_host, void *cuda_stream)
+{
+    if (n_macro < 2 || !U_dev || !K_dev || !(dt > 0) || nsteps < 0) return MLSD_EINVAL;
+    if (precision != MLSD_FP32 && precision != MLSD_FP64) return MLSD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t sb = macro_scratch_bytes(n_macro, precision, nsteps);
+    const size_t mb = mass_out_host ? (size_t)(nsteps + 1) * sizeof(double) : 0;
+    void *scratch = nullptr;
+    if (sb + mb) CK(cudaMallocAsync(&scratch, sb + mb + 256, s));
+    double *mass = mass_out_host
+        ? reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(scratch) + sb + 255) & ~(uintptr_t)255)
+        : nullptr;
+    cudaError_t e = macro_run(n_macro, U_dev, precision, K_dev, dt, nsteps, mass, scratch, s);
+    if (e == cudaSuccess && mass_out_host)
+        e = cudaMemcpyAsync(mass_out_host, mass, mb, cudaMemcpyDeviceToHost, s);
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess && mass_out_host) e = cudaStreamSynchronize(s);
+    CK(e);
+    return MLSD_OK;
+}
+
+int mlsd_macro_dt(int n_macro, const double *K_dev, double cfl, double *dt_out_host,
+                  void *cuda_stream)
+{
+    if (n_macro < 2 || !K_dev || !(cfl > 0) || !dt_out_host) return MLSD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    double *m = nullptr;
+    CK(cudaMallocAsync((void **)&m, sizeof(double), s));
+    cudaError_t e = macro_dt_max(n_macro, K_dev, m, s);
+    double mx = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&mx, m, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(m, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    CK(e);
+    if (!(mx > 0) || !std::isfinite(mx)) return MLSD_ENONFINITE;
+    const double H = 2.0 * kPi / n_macro;
+    *dt_out_host = cfl * H * H / mx;
+    return MLSD_OK;
+}
+
+int mlsd_grid_psi(int n_modes, const int32_t *k1, const int32_t *k2, const double *re,
+                  const double *im, int nf, float *psi_dev, void *cuda_stream)
+{
+    if (n_modes < 0 || nf < 1 || !psi_dev || (n_modes > 0 && (!k1 || !k2 || !re || !im)))
+        return MLSD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    mlsd_levels tmp;   // owns the staging buffers for this call only
+    std::vector<HostMode> ms;
+    for (int t = 0; t < n_modes; ++t) ms.push_back({k1[t], k2[t], re[t], im[t]});
+    ModeGroups g;
+    int rc = upload_groups(&tmp, ms, g);
+    void *G = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!rc && g.n_groups > 0) e = cudaMalloc(&G, (size_t)g.n_groups * nf * sizeof(double2));
+    if (!rc && e == cudaSuccess) e = launch_band_synth(g, nf, static_cast<double2 *>(G), psi_dev, 0, s);
+    if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (G) cudaFree(G);
+    for (void *p : tmp.allocs) cudaFree(p);
+    if (rc) return rc;
+    CK(e);
+    return MLSD_OK;
+}
+
+int mlsd_dns_run(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev, double kappa,
+                 double dt, int nsteps, void *cuda_stream)
+{
+    if (nf < 64 || nf % 64 || !u_dev || !u_tmp_dev || !psi_dev || u_dev == u_tmp_dev ||
+        !(kappa >= 0) || !(dt > 0) || nsteps < 0)
+        return MLSD_EINVAL;
+    CK(dns_run(nf, u_dev, u_tmp_dev, psi_dev, kappa, dt, nsteps,
+               static_cast<cudaStream_t>(cuda_stream)));
+    return MLSD_OK;
+}
+
+int mlsd_coarse_grain(int nf, const float *u_dev, int n_macro, float *U_dev,
+                      double *mass_out_host, void *cuda_stream)
+{
+    if (nf < 1 || n_macro < 1 || nf % n_macro || !u_dev || !U_dev) return MLSD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    double *m = nullptr;
+    if (mass_out_host)
+        CK(cudaMallocAsync((void **)&m, (1 + (size_t)n_macro * n_macro) * sizeof(double), s));
+    cudaError_t e = coarse_grain(nf, u_dev, n_macro, U_dev, m, s);
+    if (e == cudaSuccess && m) e = cudaMemcpyAsync(mass_out_host, m, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (m) cudaFreeAsync(m, s);
+    if (e == cudaSuccess && m) e = cudaStreamSynchronize(s);
+    CK(e);
+    return MLSD_OK;
+}
+
+}  // extern "C"

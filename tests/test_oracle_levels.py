@@ -84,7 +84,7 @@ def test_alg1_on_pure_x2_shear_equals_closed_form(A, m):
     np.testing.assert_allclose(q12, A * A / 2, rtol=1e-13)
     assert not np.any(q21)
     B = np.array([0.3, 0.05, 0.7])
-    np.testing.assert_allclose(oracle.offdiag_apply(q12, q21, B),
+    np.testing.assert_allclose(oracle.offdiag_apply(q12, None, B),
                                [B[0] + A * A / (2 * B[2]), B[1], B[2]], rtol=1e-14)
 
 
@@ -106,7 +106,7 @@ def test_alg1_harmonic_mean_across_columns():
     xa = 2 * math.pi * np.arange(n) / Nl
     np.testing.assert_allclose(q12, A * A * np.cos(xa) ** 2 / 2, atol=1e-14)
     B = np.array([0.2, 0.0, 0.5])
-    K = oracle.offdiag_apply(q12, np.zeros(n), B)
+    K = oracle.offdiag_apply(q12, None, B)
     a, b = B[0], A * A / (2 * B[2])
     assert K[0] == pytest.approx(math.sqrt(a * (a + b)), rel=1e-12)
     assert K[2] == B[2]
@@ -116,11 +116,15 @@ def test_alg2_one_zero_part_returns_the_other():
     rng = np.random.default_rng(0)
     q = rng.uniform(0.1, 0.5, 8)
     B = np.array([0.3, 0.02, 0.4])
-    K = oracle.offdiag_apply(q, np.zeros(8), B)
-    K2 = oracle.offdiag_apply(np.zeros(8), q, B)
-    # the harmonic mean of a constant line is that constant (to rounding)
-    assert K[2] == pytest.approx(B[2], rel=1e-15) and K[1] == B[1]
-    assert K2[0] == pytest.approx(B[0], rel=1e-15) and K2[1] == B[1]
+    K = oracle.offdiag_apply(q, None, B)
+    K2 = oracle.offdiag_apply(None, q, B)
+    # an absent part leaves its component exactly; a zero-variance part gives the
+    # harmonic mean of a constant line, i.e. that constant to rounding
+    assert K[2] == B[2] and K[1] == B[1]
+    assert K2[0] == B[0] and K2[1] == B[1]
+    Kz = oracle.offdiag_apply(q, np.zeros(8), B)
+    assert Kz[2] == pytest.approx(B[2], rel=1e-15)
+    assert np.array_equal(oracle.offdiag_apply(None, None, B), B)
     both = oracle.offdiag_apply(q, q, B)
     np.testing.assert_allclose(both, [K[0], B[1], K2[2]], rtol=1e-15)
 
