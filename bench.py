@@ -143,6 +143,24 @@ def reference_arm(args):
     return 0
 
 
+def profile_case():
+    """The benchmark's levels and launch shapes with a 200-step window per patch."""
+    import torch
+    import paper_1510_00451_gb300 as mlsd
+    cfg = _workload()
+    N = cfg["n_macro"]
+    lv = mlsd.Levels(cfg["spectrum"], cfg["kappa"], N, cfg["edges"], cfg["patch_n"],
+                     cfl=cfg["cfl"], n_burn_fixed=100, n_avg_fixed=100, precision=cfg["precision"])
+    K = torch.zeros(N * N, 3, dtype=torch.float64, device="cuda:0")
+    lv.effective_diffusivity(K)
+    rc = lv.status()
+    torch.cuda.synchronize()
+    work = sum(lv.level_work(l + 1)[0] for l in range(len(cfg["patch_n"])))
+    print(json.dumps({"case": "profile", "status": rc, "cell_updates": work,
+                      "K0": K[0].tolist()}), flush=True)
+    return 0 if rc == 0 else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -151,9 +169,14 @@ def main():
     ap.add_argument("--impl", default="mlsd", choices=["mlsd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--case", default="full", choices=["full", "profile"],
+                    help="profile: one pass of the same workload with a fixed 200-step window "
+                         "per patch (a small case for ncu captures); prints no bench line")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.case == "profile":
+        return profile_case()
 
     import torch
     import torch.distributed as dist
