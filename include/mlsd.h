@@ -186,6 +186,25 @@ int mlsd_dns_run(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev, d
 int mlsd_coarse_grain(int nf, const float *u_dev, int n_macro, float *U_dev,
                       double *mass_out_host, void *cuda_stream);
 
+/* Coarse-graining that allocates nothing (no counterpart in the paper).
+ * Same inputs, outputs and results as mlsd_coarse_grain, for callers that
+ * cannot call cudaMalloc or a stream-ordered allocator (code running where
+ * allocation is forbidden or would break their own memory accounting).  The
+ * FP64 box sums and the mass use a fixed scratch array in the library's device
+ * memory, 1 + MLSD_NOALLOC_MAX_MACRO^2 doubles (~512 KiB) held on every device
+ * that loads the library until the process exits.
+ *   n_macro > MLSD_NOALLOC_MAX_MACRO -> MLSD_EINVAL, nothing enqueued.
+ * The first call on a device looks up the scratch address there (a host-side
+ * query, no allocation); make that first call before any stream capture.
+ * All calls share the one scratch array: calls whose work overlaps on the
+ * GPU (different streams, or different host threads) race and may corrupt
+ * each other's mass and box sums.  Every call overwrites all of the scratch it
+ * uses, so no state carries over between calls.  Blocks when mass_out_host is
+ * non-NULL.                                                                 */
+#define MLSD_NOALLOC_MAX_MACRO 256
+int mlsd_coarse_grain_noalloc(int nf, const float *u_dev, int n_macro, float *U_dev,
+                              double *mass_out_host, void *cuda_stream);
+
 /* Work done by the last solve of a level (mlsd_solve_level or the level's part
  * of mlsd_effective_diffusivity): cell_updates = sum over patches and the two
  * fields of n^2 (n_burn + n_avg) (one cell of one field advanced one full RK2

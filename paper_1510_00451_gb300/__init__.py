@@ -26,7 +26,8 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_offdiag", "mlsd_effective_diffusivity", "mlsd_status", "mlsd_macro_step",
             "mlsd_macro_dt", "mlsd_grid_psi", "mlsd_dns_run", "mlsd_coarse_grain",
             "mlsd_level_work", "mlsd_launch_count", "mlsd_profile", "mlsd_profile_collect",
-            "mlsd_strerror"]
+            "mlsd_coarse_grain_noalloc", "mlsd_strerror"]
+NOALLOC_MAX_MACRO = 256
 
 
 class MlsdError(RuntimeError):
@@ -73,6 +74,7 @@ _lib.mlsd_profile.argtypes = [_P, _I]
 _lib.mlsd_profile_collect.argtypes = [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_L)]
 _lib.mlsd_launch_count.argtypes = []
 _lib.mlsd_launch_count.restype = _L
+_lib.mlsd_coarse_grain_noalloc.argtypes = [_I, _P, _I, _P, _P, _P]
 _lib.mlsd_strerror.argtypes = [_I]
 _lib.mlsd_strerror.restype = ctypes.c_char_p
 
@@ -220,4 +222,13 @@ def coarse_grain(u, n_macro, U_out, want_mass=True, stream=None):
     _check(_lib.mlsd_coarse_grain(u.shape[0], _dptr(u), int(n_macro), _dptr(U_out),
                                   ctypes.byref(m) if want_mass else None, _stream(stream)),
            "mlsd_coarse_grain")
+    return m.value if want_mass else None
+
+
+def coarse_grain_noalloc(u, n_macro, U_out, want_mass=True, stream=None):
+    """mlsd_coarse_grain_noalloc: same result as coarse_grain, no device allocation."""
+    m = ctypes.c_double()
+    _check(_lib.mlsd_coarse_grain_noalloc(u.shape[0], _dptr(u), int(n_macro), _dptr(U_out),
+                                          ctypes.byref(m) if want_mass else None, _stream(stream)),
+           "mlsd_coarse_grain_noalloc")
     return m.value if want_mass else None

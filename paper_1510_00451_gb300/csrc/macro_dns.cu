@@ -12,6 +12,8 @@
 // DNS: u_t = v1 D0x u + v2 D0y u + kappa (Dxx + Dyy) u, v = (-D0y psi, D0x psi),
 // both RK stages fused per tile (u and psi staged with a halo of 2 in shared
 // memory), one pass over HBM per time step: read u, read psi, write u.
+#include <mutex>
+
 #include "mlsd_internal.cuh"
 
 namespace mlsd {
@@ -344,3 +346,59 @@ cudaError_t coarse_grain(int nf, const float *u, int N, float *U, double *mass_d
 }
 
 }  // namespace mlsd
+
+// ---------------------------------------------------------------------------
+// Coarse-graining without allocation.
+//
+// Callers that must not allocate device memory (code running inside a host
+// callback or a memory-pool-free embedding, allocator-less runtimes, or code
+// that has handed all device memory to its own pool) get a variant of
+// mlsd_coarse_grain whose scratch -- the FP64 box sums and the mass -- lives
+// in the file-scope array below.  It holds 1 + MLSD_NOALLOC_MAX_MACRO^2
+// doubles (about 512 KiB) on every device that loads the library, until the
+// process exits.  Host code may not use the array's name as a pointer (it is
+// a host-side stand-in): its device address is looked up once per device with
+// cudaGetSymbolAddress, with that device current, on the first call there.
+namespace mlsd {
+namespace {
+constexpr int kNoallocMax = MLSD_NOALLOC_MAX_MACRO;
+constexpr int kNoallocDevices = 64;
+static __device__ __align__(256) double g_cg_scratch[1 + kNoallocMax * kNoallocMax];
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kNoallocDevices] = {};
+
+cudaError_t noalloc_scratch(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoallocDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_cg_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+}  // namespace mlsd
+
+extern "C" int mlsd_coarse_grain_noalloc(int nf, const float *u_dev, int n_macro, float *U_dev,
+                                         double *mass_out_host, void *cuda_stream)
+{
+    using namespace mlsd;
+    if (nf < 1 || n_macro < 1 || nf % n_macro || !u_dev || !U_dev) return MLSD_EINVAL;
+    if (n_macro > kNoallocMax) return MLSD_EINVAL;          // scratch holds N <= 256 only
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    double *scratch = nullptr;
+    if (noalloc_scratch(&scratch) != cudaSuccess) return MLSD_ECUDA;
+    // every box sum and the mass are overwritten by this call: nothing carries over
+    cudaError_t e = coarse_grain(nf, u_dev, n_macro, U_dev, mass_out_host ? scratch : nullptr, s);
+    if (e == cudaSuccess && mass_out_host)
+        e = cudaMemcpyAsync(mass_out_host, scratch, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && mass_out_host) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? MLSD_OK : MLSD_ECUDA;
+}
