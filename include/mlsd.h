@@ -88,6 +88,9 @@ typedef struct {
     double L, h;
     int64_t n_patches;         /* = N*N */
     int n_diag_modes, n_off12_modes, n_off21_modes;
+    int tile_bx, tile_by;      /* cells per thread of the patch kernel the autotuner chose */
+    int threads;               /* threads per CTA of that kernel */
+    int packed;                /* 1: one CTA per patch, both fields in f32x2 pairs; 0: one per field */
 } mlsd_level_desc;
 
 typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and scratch */
@@ -95,6 +98,11 @@ typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and 
 /* Validate the problem, decompose the spectrum (Sec. 3.1), synthesise every
  * level's diagonal band on the device, and precompute the line variances that
  * Algorithm 1 needs.  Allocates device memory; blocks until set-up is done.
+ * Set-up also picks the thread-block tiling of the patch kernel per patch
+ * size: every compiled candidate is timed on a sample of the level's patches
+ * (a short fixed window) and the fastest is kept for the process; the
+ * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][p] forces one
+ * (p: the packed kernel that advances both fields of a patch in f32x2 pairs).
  * Returns MLSD_EINVAL for an invalid problem, MLSD_EUNSUPPORTED for a patch
  * size or precision without a kernel, MLSD_ENOMEM / MLSD_ECUDA otherwise.   */
 int mlsd_build_levels(const mlsd_problem *p, void *cuda_stream, mlsd_levels **out);

@@ -32,7 +32,7 @@ struct PatchParams {
 
 // Variant of the patch kernel: thread block shape per patch size and precision.
 struct PatchVariant {
-    int n, precision, bx, by, threads;
+    int n, precision, bx, by, minb, packed, threads;   // packed: both fields per CTA (f32x2)
     size_t smem;
     const void *fn;
 };

@@ -360,8 +360,8 @@ struct Tile {
     }
 };
 
-template <int N, int BX, int BY, typename real>
-__global__ void __launch_bounds__((N / BX) * (N / BY))
+template <int N, int BX, int BY, typename real, int MINB>
+__global__ void __launch_bounds__((N / BX) * (N / BY), MINB)
 k_patch_solve(PatchParams prm)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -373,17 +373,329 @@ k_patch_solve(PatchParams prm)
     else Tile<N, BX, BY, real>::template run<1>(prm, sm, p);
 }
 
-template <int N, int BX, int BY, typename real>
+template <int N, int BX, int BY, typename real, int MINB = 1>
 void add_variant(std::vector<PatchVariant> &out)
 {
+    static_assert(((N / BX) * (N / BY)) % 32 == 0, "whole warps only");
     PatchVariant v;
     v.n = N;
     v.precision = sizeof(real) == 4 ? MLSD_FP32 : MLSD_FP64;
     v.bx = BX;
     v.by = BY;
+    v.minb = MINB;
+    v.packed = 0;
     v.threads = (N / BX) * (N / BY);
     v.smem = Smem<N, BX, BY, real>::BYTES;
-    v.fn = reinterpret_cast<const void *>(&k_patch_solve<N, BX, BY, real>);
+    v.fn = reinterpret_cast<const void *>(&k_patch_solve<N, BX, BY, real, MINB>);
+    out.push_back(v);
+}
+
+// ---------------------------------------------------------------------------
+// Packed variant: one CTA advances BOTH corrector fields of a patch, each cell
+// holding (w_1, w_2) in one float2 and every stencil operation issued as a
+// Blackwell f32x2 instruction (FFMA2 / FADD2 / FMUL2).  The two fields share
+// v, B and dt; only the source term differs, (2h, 0) on the E-W difference
+// and (0, 2h) on the N-S difference.  a - b is formed as fma(b, -1, a), which
+// rounds exactly like a subtraction, so the results equal the scalar kernel's.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
+template <int CNT>
+__device__ __forceinline__ void st_vec2(float2 *dst, const float2 (&src)[CNT])
+{
+    static_assert(CNT % 2 == 0, "pairs of float2");
+#pragma unroll
+    for (int k = 0; k < CNT / 2; ++k)
+        reinterpret_cast<float4 *>(dst)[k] =
+            make_float4(src[2 * k].x, src[2 * k].y, src[2 * k + 1].x, src[2 * k + 1].y);
+}
+
+template <int CNT>
+__device__ __forceinline__ void ld_vec2(float2 (&dst)[CNT], const float2 *src)
+{
+#pragma unroll
+    for (int k = 0; k < CNT / 2; ++k) {
+        const float4 v = reinterpret_cast<const float4 *>(src)[k];
+        dst[2 * k] = make_float2(v.x, v.y);
+        dst[2 * k + 1] = make_float2(v.z, v.w);
+    }
+}
+
+template <int N, int BX, int BY>
+struct Smem2 {
+    static constexpr int NBX = N / BX, NBY = N / BY;
+    static constexpr int CS = N + 2;              // column stride in float2 (16-byte pad)
+    static constexpr int ROW = NBY * N, COL = NBX * CS;
+    static constexpr int STAGE = 2 * ROW + 2 * COL;
+    static constexpr int EXCH = 2 * STAGE;        // float2 words, double buffered
+    static constexpr int SETUP = (N * N + 1) / 2; // psi tile (floats) in float2 words
+    static constexpr int WORDS = (EXCH > SETUP ? EXCH : SETUP);
+    static constexpr size_t BYTES = (size_t)WORDS * sizeof(float2) + 64 * sizeof(double);
+};
+
+template <int N, int BX, int BY>
+struct Tile2 {
+    static constexpr int NBX = N / BX, NBY = N / BY, NT = NBX * NBY;
+    using S = Smem2<N, BX, BY>;
+
+    template <bool SECOND>
+    __device__ __forceinline__ static void stage(float2 *sm, int buf, int tx, int ty,
+                                                 const float2 (&x)[BY][BX], float2 (&out)[BY][BX],
+                                                 const float2 (&A1)[BY][BX], const float2 (&A2)[BY][BX],
+                                                 float2 b11, float2 b22, float2 bx, float2 bc,
+                                                 float2 T1, float2 T2)
+    {
+        const int a0 = tx * BX, b0 = ty * BY;
+        float2 *rowT = sm + buf * S::STAGE;
+        float2 *rowB = rowT + S::ROW;
+        float2 *colL = rowB + S::ROW;
+        float2 *colR = colL + S::COL;
+        {
+            float2 t[BX], bt[BX];
+#pragma unroll
+            for (int c = 0; c < BX; ++c) { t[c] = x[0][c]; bt[c] = x[BY - 1][c]; }
+            st_vec2<BX>(rowT + ty * N + a0, t);
+            st_vec2<BX>(rowB + ty * N + a0, bt);
+            float2 l[BY], r[BY];
+#pragma unroll
+            for (int k = 0; k < BY; ++k) { l[k] = x[k][0]; r[k] = x[k][BX - 1]; }
+            st_vec2<BY>(colL + tx * S::CS + b0, l);
+            st_vec2<BY>(colR + tx * S::CS + b0, r);
+        }
+        __syncthreads();
+        float2 hS[BX], hN[BX], hW[BY + 2], hE[BY + 2];
+        {
+            const int tyS = (ty + NBY - 1) % NBY, tyN = (ty + 1) % NBY;
+            const int txW = (tx + NBX - 1) % NBX, txE = (tx + 1) % NBX;
+            ld_vec2<BX>(hS, rowB + tyS * N + a0);
+            ld_vec2<BX>(hN, rowT + tyN * N + a0);
+            const float2 *cw = colR + txW * S::CS;
+            const float2 *ce = colL + txE * S::CS;
+            float2 tw[BY], te[BY];
+            ld_vec2<BY>(tw, cw + b0);
+            ld_vec2<BY>(te, ce + b0);
+            const int bs = (b0 + N - 1) % N, bn = (b0 + BY) % N;
+            hW[0] = cw[bs]; hE[0] = ce[bs];
+            hW[BY + 1] = cw[bn]; hE[BY + 1] = ce[bn];
+#pragma unroll
+            for (int k = 0; k < BY; ++k) { hW[k + 1] = tw[k]; hE[k + 1] = te[k]; }
+        }
+        float2 dm[BX], d0[BX], dp[BX];
+#pragma unroll
+        for (int c = 0; c < BX; ++c) {
+            const float2 e = (c + 1 < BX) ? hS[c + 1] : hE[0];
+            const float2 w = (c > 0) ? hS[c - 1] : hW[0];
+            dm[c] = sub2(e, w);
+            const float2 e0 = (c + 1 < BX) ? x[0][c + 1] : hE[1];
+            const float2 w0 = (c > 0) ? x[0][c - 1] : hW[1];
+            d0[c] = sub2(e0, w0);
+        }
+#pragma unroll
+        for (int r = 0; r < BY; ++r) {
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                float2 e, w;
+                if (r + 1 < BY) {
+                    e = (c + 1 < BX) ? x[r + 1][c + 1] : hE[r + 2];
+                    w = (c > 0) ? x[r + 1][c - 1] : hW[r + 2];
+                } else {
+                    e = (c + 1 < BX) ? hN[c + 1] : hE[BY + 1];
+                    w = (c > 0) ? hN[c - 1] : hW[BY + 1];
+                }
+                dp[c] = sub2(e, w);
+            }
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                const float2 xc = x[r][c];
+                const float2 xE = (c + 1 < BX) ? x[r][c + 1] : hE[r + 1];
+                const float2 xW = (c > 0) ? x[r][c - 1] : hW[r + 1];
+                const float2 xN = (r + 1 < BY) ? x[r + 1][c] : hN[c];
+                const float2 xS = (r > 0) ? x[r - 1][c] : hS[c];
+                const float2 d1 = __fadd2_rn(d0[c], T1);
+                const float2 d2 = __fadd2_rn(sub2(xN, xS), T2);
+                const float2 s1 = __fadd2_rn(xE, xW), s2 = __fadd2_rn(xN, xS);
+                const float2 cr = sub2(dp[c], dm[c]);
+                float2 g = __fmul2_rn(A1[r][c], d1);
+                g = __ffma2_rn(A2[r][c], d2, g);
+                g = __ffma2_rn(b11, s1, g);
+                g = __ffma2_rn(b22, s2, g);
+                g = __ffma2_rn(bx, cr, g);
+                g = __ffma2_rn(bc, xc, g);
+                if constexpr (SECOND)
+                    out[r][c] = __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(out[r][c], g));
+                else
+                    out[r][c] = g;
+            }
+#pragma unroll
+            for (int c = 0; c < BX; ++c) { dm[c] = d0[c]; d0[c] = dp[c]; }
+        }
+    }
+
+    __device__ static void run(const PatchParams &prm, float2 *sm, long long p)
+    {
+        const int tid = threadIdx.x, tx = tid % NBX, ty = tid / NBX;
+        const int a0 = tx * BX, b0 = ty * BY;
+        double *red = reinterpret_cast<double *>(sm + S::WORDS);
+        const long long Nl = prm.Nl;
+        const long long ox = patch_origin(p % prm.n_macro, prm.n_macro, Nl, N);
+        const long long oy = patch_origin(p / prm.n_macro, prm.n_macro, Nl, N);
+        float *psi = reinterpret_cast<float *>(sm);
+        const float *band = static_cast<const float *>(prm.band);
+        for (int c = tid; c < N * N; c += NT) {
+            const int b = c / N, a = c % N;
+            psi[c] = band[pmod_ll(oy + b, Nl) * Nl + pmod_ll(ox + a, Nl)];
+        }
+        __syncthreads();
+        const float inv2h = (float)(1.0 / (2.0 * prm.h));
+        float v1r[BY][BX], v2r[BY][BX];
+        float vmax = 0.f;
+#pragma unroll
+        for (int r = 0; r < BY; ++r) {
+            const int b = b0 + r, bp = (b + 1) % N, bm = (b + N - 1) % N;
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                const int a = a0 + c, ap = (a + 1) % N, am = (a + N - 1) % N;
+                const float v1 = (psi[bm * N + a] - psi[bp * N + a]) * inv2h;
+                const float v2 = (psi[b * N + ap] - psi[b * N + am]) * inv2h;
+                v1r[r][c] = v1;
+                v2r[r][c] = v2;
+                vmax = fmaxf(vmax, fabsf(v1) + fabsf(v2));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if ((tid & 31) == 0) red[tid >> 5] = (double)vmax;
+        __syncthreads();
+        double vm = 0.0;
+        for (int k = 0; k < NT / 32; ++k) vm = fmax(vm, red[k]);
+
+        const double B11 = prm.Kb[3 * p], B12 = prm.Kb[3 * p + 1], B22 = prm.Kb[3 * p + 2];
+        double dt;
+        long long nb, na;
+        micro_schedule(prm.h, prm.L, vm, B11, B12, B22, prm.cfl, prm.t_burn, prm.t_avg,
+                       prm.nb_fixed, prm.na_fixed, dt, nb, na);
+        if (!(dt > 0.0) || !isfinite(dt) || nb < 0 || na < 1 || nb + na > kMaxSteps) {
+            if (tid == 0) {
+                const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+                for (int k = 0; k < 4; ++k) prm.S[4 * p + k] = qnan;
+                atomicCAS(prm.status, 0, MLSD_EINVAL);
+            }
+            return;
+        }
+        if (tid == 0 && prm.steps) prm.steps[p] = nb + na;
+        const double hh = prm.h * prm.h;
+        const float cA = (float)(dt / (2.0 * prm.h));
+        const float fb11 = (float)(dt * B11 / hh), fb22 = (float)(dt * B22 / hh);
+        const float fbx = (float)(dt * B12 / (2.0 * hh));
+        const float fbc = (float)(1.0 - 2.0 * (dt * B11 / hh + dt * B22 / hh));
+        const float twoh = (float)(2.0 * prm.h);
+        const float2 b11 = make_float2(fb11, fb11), b22 = make_float2(fb22, fb22);
+        const float2 bx = make_float2(fbx, fbx), bc = make_float2(fbc, fbc);
+        const float2 T1 = make_float2(twoh, 0.f), T2 = make_float2(0.f, twoh);
+        float2 A1[BY][BX], A2[BY][BX];
+#pragma unroll
+        for (int r = 0; r < BY; ++r)
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                const float a1 = v1r[r][c] * cA, a2 = v2r[r][c] * cA;
+                A1[r][c] = make_float2(a1, a1);
+                A2[r][c] = make_float2(a2, a2);
+            }
+        __syncthreads();
+
+        float2 w[BY][BX], st[BY][BX];
+#pragma unroll
+        for (int r = 0; r < BY; ++r)
+#pragma unroll
+            for (int c = 0; c < BX; ++c) w[r][c] = make_float2(0.f, 0.f);
+        float2 p1 = make_float2(0.f, 0.f), p2 = make_float2(0.f, 0.f);
+        double f11 = 0.0, f12 = 0.0, f21 = 0.0, f22 = 0.0;   // f_ij ~ sum A_i w_j
+        int win = 0;
+        const long long ntot = nb + na;
+        for (long long step = 0; step < ntot; ++step) {
+            stage<false>(sm, 0, tx, ty, w, st, A1, A2, b11, b22, bx, bc, T1, T2);
+            stage<true>(sm, 1, tx, ty, st, w, A1, A2, b11, b22, bx, bc, T1, T2);
+            if (step >= nb) {
+                float2 q1 = make_float2(0.f, 0.f), q2 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int r = 0; r < BY; ++r)
+#pragma unroll
+                    for (int c = 0; c < BX; ++c) {
+                        q1 = __ffma2_rn(A1[r][c], w[r][c], q1);
+                        q2 = __ffma2_rn(A2[r][c], w[r][c], q2);
+                    }
+                p1 = __fadd2_rn(p1, q1);
+                p2 = __fadd2_rn(p2, q2);
+                if (++win == kFlush) {
+                    f11 += (double)p1.x; f12 += (double)p1.y; f21 += (double)p2.x; f22 += (double)p2.y;
+                    p1 = make_float2(0.f, 0.f); p2 = make_float2(0.f, 0.f); win = 0;
+                }
+            }
+        }
+        f11 += (double)p1.x; f12 += (double)p1.y; f21 += (double)p2.x; f22 += (double)p2.y;
+
+        if (prm.wdump) {
+            float *wd = static_cast<float *>(prm.wdump) + 2 * p * (long long)N * N;
+#pragma unroll
+            for (int r = 0; r < BY; ++r)
+#pragma unroll
+                for (int c = 0; c < BX; ++c) {
+                    wd[(b0 + r) * N + a0 + c] = w[r][c].x;
+                    wd[(long long)N * N + (b0 + r) * N + a0 + c] = w[r][c].y;
+                }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            f11 += __shfl_xor_sync(0xffffffffu, f11, o);
+            f12 += __shfl_xor_sync(0xffffffffu, f12, o);
+            f21 += __shfl_xor_sync(0xffffffffu, f21, o);
+            f22 += __shfl_xor_sync(0xffffffffu, f22, o);
+        }
+        __syncthreads();
+        if ((tid & 31) == 0) {
+            const int k = tid >> 5;
+            red[4 * k] = f11; red[4 * k + 1] = f21; red[4 * k + 2] = f12; red[4 * k + 3] = f22;
+        }
+        __syncthreads();
+        if (tid < 4) {
+            double t = 0.0;
+            for (int k = 0; k < NT / 32; ++k) t += red[4 * k + tid];
+            // (S11, S21, S12, S22): v_i = A_i / cA, mean over cells and window
+            const double v = t / ((double)cA * (double)N * (double)N * (double)na);
+            prm.S[4 * p + tid] = v;
+            if (!isfinite(v)) atomicCAS(prm.status, 0, MLSD_ENONFINITE);
+        }
+    }
+};
+
+template <int N, int BX, int BY, int MINB>
+__global__ void __launch_bounds__((N / BX) * (N / BY), MINB)
+k_patch_solve2(PatchParams prm)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *sm = reinterpret_cast<float2 *>(smem_raw);
+    const long long p = prm.item0 / 2 + blockIdx.x;
+    if (2 * p >= prm.item0 + prm.items) return;
+    Tile2<N, BX, BY>::run(prm, sm, p);
+}
+
+template <int N, int BX, int BY, int MINB = 1>
+void add_variant2(std::vector<PatchVariant> &out)
+{
+    static_assert(((N / BX) * (N / BY)) % 32 == 0, "whole warps only");
+    static_assert((N / BX) * (N / BY) / 32 * 4 <= 64, "reduction scratch");
+    PatchVariant v;
+    v.n = N;
+    v.precision = MLSD_FP32;
+    v.bx = BX;
+    v.by = BY;
+    v.minb = MINB;
+    v.packed = 1;
+    v.threads = (N / BX) * (N / BY);
+    v.smem = Smem2<N, BX, BY>::BYTES;
+    v.fn = reinterpret_cast<const void *>(&k_patch_solve2<N, BX, BY, MINB>);
     out.push_back(v);
 }
 
@@ -405,18 +717,29 @@ __global__ void k_compose(long long P, const double *B, const double *S, double 
 
 int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
 {
+    // candidate thread-block tilings; the autotuner in the runtime times them
     out.clear();
     if (precision == MLSD_FP32) {
         switch (n) {
         case 32:
             add_variant<32, 4, 8, float>(out);
             add_variant<32, 4, 4, float>(out);
+            add_variant<32, 2, 8, float>(out);
+            add_variant<32, 2, 4, float>(out);
+            add_variant2<32, 4, 4>(out);
+            add_variant2<32, 2, 4>(out);
+            add_variant2<32, 4, 2>(out);
             break;
         case 64:
             add_variant<64, 4, 8, float>(out);
+            add_variant<64, 4, 8, float, 3>(out);
             add_variant<64, 4, 4, float>(out);
-            add_variant<64, 8, 4, float>(out);
             add_variant<64, 2, 8, float>(out);
+            add_variant<64, 8, 4, float>(out);
+            add_variant<64, 2, 4, float>(out);
+            add_variant2<64, 4, 4>(out);
+            add_variant2<64, 2, 4>(out);
+            add_variant2<64, 4, 2>(out);
             break;
         default: break;
         }
@@ -444,7 +767,9 @@ cudaError_t launch_patch(const PatchVariant &v, const PatchParams &p, long long 
     if (e != cudaSuccess) return e;
     void *args[] = {const_cast<PatchParams *>(&p)};
     count_launches(1);
-    return cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3(v.threads), args, v.smem, s);
+    // packed kernels take one CTA per patch (both fields), item0 and grid even
+    const long long g = v.packed ? (grid + 1) / 2 : grid;
+    return cudaLaunchKernel(v.fn, dim3((unsigned)g), dim3(v.threads), args, v.smem, s);
 }
 
 cudaError_t launch_compose(long long P, const double *B, const double *S, double *K,

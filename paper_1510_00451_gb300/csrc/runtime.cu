@@ -5,7 +5,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -181,6 +184,8 @@ int validate(const mlsd_problem *p)
     return MLSD_OK;
 }
 
+int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s);
+
 int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
 {
     int rc;
@@ -220,9 +225,10 @@ int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
             if (std::fabs(e - d.m) > 0 || d.m < 1) return MLSD_EINVAL;
         }
         if (d.m < 1) return MLSD_EINVAL;
-        std::vector<PatchVariant> vs;
-        if (patch_variants(d.n, p->precision, vs) == 0) return MLSD_EUNSUPPORTED;
-        d.variant = vs[0];
+        {
+            std::vector<PatchVariant> vs;
+            if (patch_variants(d.n, p->precision, vs) == 0) return MLSD_EUNSUPPORTED;
+        }
         d.Nl = (long long)d.n * d.m;
         d.L = 2.0 * kPi / d.m;
         d.h = d.L / d.n;
@@ -260,8 +266,91 @@ int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
         if ((rc = dev_alloc(h, (void **)&d.S, (size_t)h->P * 4 * 8))) return rc;
         if ((rc = dev_alloc(h, (void **)&d.steps, (size_t)h->P * 8))) return rc;
         CK(cudaMemsetAsync(d.steps, 0, (size_t)h->P * 8, s));
+        if ((rc = tune_level(h, d, s))) return rc;
     }
     CK(cudaStreamSynchronize(s));
+    return MLSD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: time every compiled tiling of the patch kernel on a sample of the
+// level's patches (short fixed window, the level's own band, base kappa I) and
+// keep the fastest per (device, n, precision) for the rest of the process.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;   // -> (bx, code(by, minb, packed))
+
+int tile_code(const PatchVariant &v) { return v.by * 16 + v.minb + 4096 * v.packed; }
+
+int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s)
+{
+    std::vector<PatchVariant> vs;
+    patch_variants(d.n, h->precision, vs);
+    if (vs.empty()) return MLSD_EUNSUPPORTED;
+    d.variant = vs[0];
+    if (const char *env = std::getenv("MLSD_TILE")) {
+        // <bx>x<by>[m<minb>][p]: p selects the packed two-field kernel
+        int bx = 0, by = 0, mb = 1, pk = 0;
+        char rest[16] = "";
+        if (std::sscanf(env, "%dx%d%15s", &bx, &by, rest) >= 2) {
+            for (const char *c = rest; *c; ++c) {
+                if (*c == 'm') mb = std::atoi(c + 1);
+                if (*c == 'p') pk = 1;
+            }
+            for (auto &v : vs)
+                if (v.bx == bx && v.by == by && v.minb == mb && v.packed == pk) { d.variant = v; return MLSD_OK; }
+        }
+        return MLSD_EINVAL;
+    }
+    if (vs.size() == 1) return MLSD_OK;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, d.n, h->precision);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            for (auto &v : vs)
+                if (v.bx == it->second.first && tile_code(v) == it->second.second) d.variant = v;
+            return MLSD_OK;
+        }
+    }
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // base kappa I for the sampled patches (the level's B array is free at set-up)
+    std::vector<double> kb((size_t)h->P * 3);
+    for (long long p = 0; p < h->P; ++p) { kb[3 * p] = h->kappa; kb[3 * p + 1] = 0; kb[3 * p + 2] = h->kappa; }
+    CK(cudaMemcpyAsync(d.B, kb.data(), kb.size() * 8, cudaMemcpyHostToDevice, s));
+    PatchParams pp;
+    pp.band = d.band; pp.Nl = d.Nl; pp.n_macro = h->N; pp.h = d.h; pp.L = d.L;
+    pp.Kb = d.B; pp.S = d.S; pp.wdump = nullptr; pp.status = h->status;
+    pp.cfl = h->cfl; pp.t_burn = 8; pp.t_avg = 4; pp.nb_fixed = 0;
+    pp.na_fixed = d.n <= 32 ? 64 : 32;
+    pp.P = h->P; pp.item0 = 0; pp.steps = nullptr;
+    pp.items = std::min<long long>(2 * h->P, (long long)sms * 48);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (auto &v : vs) {
+        float t = 1e30f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) {
+            cudaEventRecord(e0, s);
+            ok = launch_patch(v, pp, pp.items, s) == cudaSuccess;
+            cudaEventRecord(e1, s);
+            if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess;
+            float ms = 0.f;
+            if (ok && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t = std::min(t, ms);
+        }
+        if (!ok) { cudaGetLastError(); continue; }   // a tiling this device cannot launch
+        if (t < best) { best = t; d.variant = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = {d.variant.bx, tile_code(d.variant)};
     return MLSD_OK;
 }
 
@@ -376,6 +465,10 @@ int mlsd_level_info(const mlsd_levels *h, int level, mlsd_level_desc *out)
     out->n_diag_modes = d.n_diag;
     out->n_off12_modes = d.n_12;
     out->n_off21_modes = d.n_21;
+    out->tile_bx = d.variant.bx;
+    out->tile_by = d.variant.by;
+    out->threads = d.variant.threads;
+    out->packed = d.variant.packed;
     return MLSD_OK;
 }
 

@@ -1,0 +1,52 @@
+"""Every thread-block tiling the autotuner may choose, forced one at a time
+(MLSD_TILE), against the oracle on the same seeded patches."""
+import os
+
+import numpy as np
+import pytest
+
+from inputs import flows
+from tests._parity import oracle_level, random_spd, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+FP32 = {32: ["4x8", "4x4", "2x8", "2x4", "4x4p", "2x4p", "4x2p"],
+        64: ["4x8", "4x8m3", "4x4", "2x8", "8x4", "2x4", "4x4p", "2x4p", "4x2p"]}
+FP64 = {32: ["2x4", "4x4"], 64: ["2x4", "4x4"]}
+CASES = ([(n, "fp32", t) for n, ts in FP32.items() for t in ts]
+         + [(n, "fp64", t) for n, ts in FP64.items() for t in ts])
+_REF = {}
+
+
+def _ref(n, prec, spec, edges, pn, N, B):
+    key = (n, prec)
+    if key not in _REF:
+        _REF[key] = oracle_level(spec, edges, pn, 2, N, B, list(range(N * N)),
+                                 n_burn_fixed=90, n_avg_fixed=70, want_w=True)
+    return _REF[key]
+
+
+@pytest.mark.parametrize("n,prec,tile", CASES)
+def test_tiling_parity(n, prec, tile, monkeypatch):
+    import torch
+    import paper_1510_00451_gb300 as mlsd
+    monkeypatch.setenv("MLSD_TILE", tile)
+    spec = flows.cellular_two_scale(0.8, 0.5, 4)
+    edges, pn, N = [1, 4, 8], [n, n], 3
+    lv = mlsd.Levels(spec, 0.03, N, edges, pn, n_burn_fixed=90, n_avg_fixed=70, precision=prec)
+    info = lv.info(2)
+    want = tile.replace("p", "").split("m")[0]
+    assert f"{info['tile_bx']}x{info['tile_by']}" == want and info["packed"] == ("p" in tile)
+    B = random_spd(N * N, np.random.default_rng(n), 0.03, 0.1)
+    dev = torch.device("cuda:0")
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    Kb = torch.tensor(B, dtype=torch.float64, device=dev)
+    Ko = torch.zeros_like(Kb)
+    w = torch.zeros(N * N, 2, n, n, dtype=dtype, device=dev)
+    lv.solve_level(2, Kb, Ko, w)
+    assert lv.status() == 0
+    K, w = Ko.cpu().numpy(), w.cpu().numpy()
+    ktol, wtol = (1e-4, 1e-5) if prec == "fp32" else (1e-10, 1e-10)
+    for p, (Kr, wr) in enumerate(_ref(n, prec, spec, edges, pn, N, B)):
+        assert rel_l2(K[p], Kr) < ktol, (p, K[p], Kr)
+        assert rel_l2(w[p], wr) < wtol
