@@ -143,6 +143,47 @@ def reference_arm(args):
     return 0
 
 
+DNS_BYTES_PER_CELL_STEP = 12     # read u, read psi, write u (both RK stages fused)
+
+
+def dns_case(nf, steps, warmup=20, report=False):
+    """Direct simulation of the continuous-spectrum flow (|k| <= 256, kappa = 1e-3)
+    on an nf x nf FP32 grid: `steps` fused RK2 steps timed with CUDA events."""
+    import torch
+    import inputs
+    import paper_1510_00451_gb300 as mlsd
+    dev = torch.device("cuda", _local_rank())
+    cfg = inputs.config_problem("continuous_spectrum")
+    psi = torch.empty(nf, nf, dtype=torch.float32, device=dev)
+    mlsd.grid_psi(cfg["spectrum"], nf, psi)
+    dt = mlsd.dns_dt(psi, cfg["kappa"], cfg["cfl"])
+    u0 = torch.tensor(inputs.gaussian_u0(nf, cfg["sigma"]), dtype=torch.float32, device=dev)
+    u = u0.clone()
+    ut = torch.empty_like(u)
+    mlsd.dns_run(u, ut, psi, cfg["kappa"], dt, warmup)
+    u.copy_(u0)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mlsd.dns_run(u, ut, psi, cfg["kappa"], dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    N = cfg["n_macro"]
+    U = torch.empty(N, N, dtype=torch.float32, device=dev)
+    mass = mlsd.coarse_grain(u, N, U)
+    m0 = mlsd.coarse_grain(u0, N, U.clone())
+    out = {"grid": nf, "steps": steps, "dt": dt, "ms": ms,
+           "cell_steps_per_s": nf * nf * steps / (ms * 1e-3),
+           "mass_rel_drift": abs(mass - m0) / m0,
+           "finite": bool(torch.isfinite(u).all().item())}
+    if report:
+        print(json.dumps({"case": "dns-profile", **out}), flush=True)
+        return 0 if out["finite"] else 1
+    return out
+
+
 def profile_case():
     """The benchmark's levels and launch shapes with a 200-step window per patch."""
     import torch
@@ -169,7 +210,8 @@ def main():
     ap.add_argument("--impl", default="mlsd", choices=["mlsd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--case", default="full", choices=["full", "profile"],
+    ap.add_argument("--no-dns", action="store_true")
+    ap.add_argument("--case", default="full", choices=["full", "profile", "dns-profile"],
                     help="profile: one pass of the same workload with a fixed 200-step window "
                          "per patch (a small case for ncu captures); prints no bench line")
     args = ap.parse_args()
@@ -177,6 +219,8 @@ def main():
         return reference_arm(args)
     if args.case == "profile":
         return profile_case()
+    if args.case == "dns-profile":
+        return dns_case(4096, 20, warmup=2, report=True)
 
     import torch
     import torch.distributed as dist
@@ -284,6 +328,18 @@ def main():
                "h2d_bytes_per_step": U0_h.numel() * 4,
                "d2h_bytes_per_step": K_h.numel() * 8 + U_h.numel() * 4}
 
+    dns = None
+    if not args.no_dns:
+        d = dns_case(8192, 1000)
+        gbs = DNS_BYTES_PER_CELL_STEP * d["cell_steps_per_s"] / 1e9
+        hbm = _peaks().get("hbm_gbs", 6789.6)
+        dns = {"workload": "continuous_spectrum_dns (8192^2 FP32, |k|<=256, kappa=1e-3, 1000 steps)",
+               "value": d["cell_steps_per_s"] * world, "unit": "cell-steps/s", "ms": d["ms"],
+               "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                            "frac": gbs / hbm, "traffic": None, "kernel": "k_dns_step",
+                            "algorithmic_bytes_per_cell_step": DNS_BYTES_PER_CELL_STEP},
+               "mass_rel_drift": d["mass_rel_drift"], "finite": d["finite"]}
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -327,6 +383,7 @@ def main():
         "clocks": clocks,
         "gpu_launches": launches,
         "wall_s_timed": t_wall,
+        "dns": dns,
     }
     line.update(line_extra)
     print(json.dumps(line), flush=True)

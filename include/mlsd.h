@@ -72,7 +72,7 @@ typedef struct {
     int n_levels;              /* L >= 1 */
     const double *band_edges;  /* host [L + 1], increasing */
     const int32_t *patch_div;  /* host [L] integers m_l >= 1, or NULL: m_l = e_{l-1} (must be integer) */
-    const int32_t *patch_n;    /* host [L] patch grid sizes, each 32, 64, 128 or 256 */
+    const int32_t *patch_n;    /* host [L] patch grid sizes: 32, 64, 128 or 256 (FP32); 32 or 64 (FP64) */
     double cfl;                /* micro time-step factor, e.g. 0.2 */
     double t_burn_tau;         /* burn-in length in relaxation times tau, e.g. 8 */
     double t_avg_tau;          /* averaging window in tau, e.g. 4 */
@@ -91,6 +91,8 @@ typedef struct {
     int tile_bx, tile_by;      /* cells per thread of the patch kernel the autotuner chose */
     int threads;               /* threads per CTA of that kernel */
     int packed;                /* 1: one CTA per patch, both fields in f32x2 pairs; 0: one per field */
+    int cluster;               /* CTAs (a thread-block cluster) sharing one patch field, in row slabs */
+    int min_ctas;              /* register cap of the kernel: at least this many CTAs per SM */
 } mlsd_level_desc;
 
 typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and scratch */
@@ -101,8 +103,12 @@ typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and 
  * Set-up also picks the thread-block tiling of the patch kernel per patch
  * size: every compiled candidate is timed on a sample of the level's patches
  * (a short fixed window) and the fastest is kept for the process; the
- * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][p] forces one
- * (p: the packed kernel that advances both fields of a patch in f32x2 pairs).
+ * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][c<cluster>][p]
+ * forces one where it exists for the level's patch size (p: the packed kernel
+ * that advances both fields of a patch in f32x2 pairs; c: CTAs per patch field).
+ * Patch sizes 32 and 64 run one CTA per field (or per patch, packed); 128 and
+ * 256 split each field over a thread-block cluster of 2-16 CTAs that exchange
+ * their slab edges through distributed shared memory.
  * Returns MLSD_EINVAL for an invalid problem, MLSD_EUNSUPPORTED for a patch
  * size or precision without a kernel, MLSD_ENOMEM / MLSD_ECUDA otherwise.   */
 int mlsd_build_levels(const mlsd_problem *p, void *cuda_stream, mlsd_levels **out);
@@ -186,6 +192,11 @@ int mlsd_grid_psi(int n_modes, const int32_t *k1, const int32_t *k2, const doubl
  * caller-provided work field of the same size.                              */
 int mlsd_dns_run(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev, double kappa,
                  double dt, int nsteps, void *cuda_stream);
+
+/* Stable DNS time step: dt = cfl * min(h / max(|v1| + |v2|), h^2 / (4 kappa)),
+ * v from psi by central differences, h = 2*pi/nf.  Blocks until known.    */
+int mlsd_dns_dt(int nf, const float *psi_dev, double kappa, double cfl, double *dt_out_host,
+                void *cuda_stream);
 
 /* Box average of the fine field onto the macro grid: node (i, j) averages the
  * r x r fine nodes i*r - r/2 .. i*r + r/2 - 1 (periodic), r = nf/N.

@@ -26,7 +26,7 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_offdiag", "mlsd_effective_diffusivity", "mlsd_status", "mlsd_macro_step",
             "mlsd_macro_dt", "mlsd_grid_psi", "mlsd_dns_run", "mlsd_coarse_grain",
             "mlsd_level_work", "mlsd_launch_count", "mlsd_profile", "mlsd_profile_collect",
-            "mlsd_coarse_grain_noalloc", "mlsd_strerror"]
+            "mlsd_coarse_grain_noalloc", "mlsd_dns_dt", "mlsd_strerror"]
 NOALLOC_MAX_MACRO = 256
 
 
@@ -53,7 +53,8 @@ class mlsd_level_desc(ctypes.Structure):
                 ("h", ctypes.c_double), ("n_patches", ctypes.c_int64),
                 ("n_diag_modes", ctypes.c_int), ("n_off12_modes", ctypes.c_int),
                 ("n_off21_modes", ctypes.c_int), ("tile_bx", ctypes.c_int),
-                ("tile_by", ctypes.c_int), ("threads", ctypes.c_int), ("packed", ctypes.c_int)]
+                ("tile_by", ctypes.c_int), ("threads", ctypes.c_int), ("packed", ctypes.c_int),
+                ("cluster", ctypes.c_int), ("min_ctas", ctypes.c_int)]
 
 
 _P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
@@ -75,6 +76,7 @@ _lib.mlsd_profile.argtypes = [_P, _I]
 _lib.mlsd_profile_collect.argtypes = [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_L)]
 _lib.mlsd_launch_count.argtypes = []
 _lib.mlsd_launch_count.restype = _L
+_lib.mlsd_dns_dt.argtypes = [_I, _P, _D, _D, ctypes.POINTER(_D), _P]
 _lib.mlsd_coarse_grain_noalloc.argtypes = [_I, _P, _I, _P, _P, _P]
 _lib.mlsd_strerror.argtypes = [_I]
 _lib.mlsd_strerror.restype = ctypes.c_char_p
@@ -216,6 +218,13 @@ def grid_psi(spectrum, nf, psi_out, stream=None):
 def dns_run(u, u_tmp, psi, kappa, dt, nsteps, stream=None):
     _check(_lib.mlsd_dns_run(u.shape[0], _dptr(u), _dptr(u_tmp), _dptr(psi), float(kappa),
                              float(dt), int(nsteps), _stream(stream)), "mlsd_dns_run")
+
+
+def dns_dt(psi, kappa, cfl, stream=None):
+    out = ctypes.c_double()
+    _check(_lib.mlsd_dns_dt(psi.shape[0], _dptr(psi), float(kappa), float(cfl), ctypes.byref(out),
+                            _stream(stream)), "mlsd_dns_dt")
+    return out.value
 
 
 def coarse_grain(u, n_macro, U_out, want_mass=True, stream=None):

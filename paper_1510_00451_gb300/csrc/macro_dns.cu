@@ -227,6 +227,24 @@ __global__ void __launch_bounds__(DTH) k_dns_step(int nf, const float *__restric
     }
 }
 
+// max over the grid of |v1| + |v2| (non-negative floats order like their bit patterns)
+__global__ void k_dns_vmax(int nf, const float *psi, float ax, unsigned *out)
+{
+    float m = 0.f;
+    const long long n2 = (long long)nf * nf;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n2;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(c / nf), a = (int)(c % nf);
+        const int bp = b + 1 == nf ? 0 : b + 1, bm = b == 0 ? nf - 1 : b - 1;
+        const int ap = a + 1 == nf ? 0 : a + 1, am = a == 0 ? nf - 1 : a - 1;
+        const float v1 = (psi[(long long)bm * nf + a] - psi[(long long)bp * nf + a]) * ax;
+        const float v2 = (psi[(long long)b * nf + ap] - psi[(long long)b * nf + am]) * ax;
+        m = fmaxf(m, fabsf(v1) + fabsf(v2));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
 // box average onto the macro grid; box[j*N+i] = FP64 sum of the box
 __global__ void k_coarse(int nf, const float *u, int N, float *U, double *box)
 {
@@ -329,6 +347,16 @@ cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kap
     }
     if (a != u)
         return cudaMemcpyAsync(u, a, (size_t)nf * nf * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError();
+}
+
+cudaError_t dns_vmax(int nf, const float *psi, unsigned *vmax_bits, cudaStream_t s)
+{
+    const double h = 2.0 * kPi / nf;
+    cudaError_t e = cudaMemsetAsync(vmax_bits, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    k_dns_vmax<<<1024, 256, 0, s>>>(nf, psi, (float)(1.0 / (2.0 * h)), vmax_bits);
     return cudaGetLastError();
 }
 

@@ -33,6 +33,7 @@ struct PatchParams {
 // Variant of the patch kernel: thread block shape per patch size and precision.
 struct PatchVariant {
     int n, precision, bx, by, minb, packed, threads;   // packed: both fields per CTA (f32x2)
+    int cluster;             // CTAs per patch field (slabs of n / cluster rows), 1 = one CTA
     size_t smem;
     const void *fn;
 };
@@ -104,6 +105,7 @@ cudaError_t macro_dt_max(int N, const double *K, double *max_dev, cudaStream_t s
 
 cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kappa, double dt,
                     int nsteps, cudaStream_t s);
+cudaError_t dns_vmax(int nf, const float *psi, unsigned *vmax_bits, cudaStream_t s);
 cudaError_t coarse_grain(int nf, const float *u, int N, float *U, double *mass_dev,
                          cudaStream_t s);
 

@@ -16,9 +16,12 @@
 // with Dxy w = (D0x w(b+1) - D0x w(b-1)) / (2h), i.e. the E-W differences of
 // the rows above and below, and Heun's RK2 w* = w + dt f(w),
 // w <- (w + w* + dt f(w*)) / 2 with dt folded into the coefficients.
+#include <cooperative_groups.h>
 #include <cstdio>
 
 #include "mlsd_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace mlsd {
 namespace {
@@ -79,20 +82,22 @@ __device__ __forceinline__ void ld_vec(T (&dst)[CNT], const T *src, int off = 0)
     }
 }
 
-// column-buffer row stride: n plus a 16-byte pad (conflict-free transposed stores)
-template <int N, typename real> struct Geo {
-    static constexpr int CS = N + 16 / (int)sizeof(real);
-};
-
-template <int N, int BX, int BY, typename real>
+// Shared-memory layout of one CTA.  A patch field of N x N cells is split over
+// a cluster of C CTAs, each owning a slab of NS = N / C rows (C = 1: the whole
+// field in one CTA).  Per RK stage every thread publishes the edges of its
+// BX x BY block: top/bottom rows into row buffers (row-major), left/right
+// columns into transposed column buffers whose stride is the slab height plus
+// a 16-byte pad (conflict-free 128-bit transposed stores).  Double buffered.
+template <int N, int C, int BX, int BY, typename real>
 struct Smem {
-    static constexpr int NBX = N / BX, NBY = N / BY;
-    static constexpr int CS = Geo<N, real>::CS;
+    static constexpr int NS = N / C;
+    static constexpr int NBX = N / BX, NBY = NS / BY;
+    static constexpr int CS = NS + 16 / (int)sizeof(real);
     static constexpr int ROW = NBY * N;          // one row buffer (top or bottom edges)
     static constexpr int COL = NBX * CS;         // one column buffer (left or right edges)
     static constexpr int STAGE = 2 * ROW + 2 * COL;
     static constexpr int EXCH = 2 * STAGE;       // double buffered
-    static constexpr int SETUP = N * N;          // psi tile at set-up
+    static constexpr int SETUP = N * (NS + 2);   // psi rows of the slab plus one halo row each side
     static constexpr int WORDS = (EXCH > SETUP ? EXCH : SETUP);
     static constexpr size_t BYTES = (size_t)WORDS * sizeof(real) + 64 * sizeof(double);
 };
@@ -127,17 +132,33 @@ __device__ void micro_schedule(double h, double L, double vmax, double B11, doub
     if (na_fixed > 0) { nb = nb_fixed; na = na_fixed; }
 }
 
-template <int N, int BX, int BY, typename real>
+// CTA-level barrier, or cluster-wide (release/acquire) when the field is split
+template <int C>
+__device__ __forceinline__ void tile_sync()
+{
+    if constexpr (C == 1) __syncthreads();
+    else cg::this_cluster().sync();
+}
+
+// shared memory of cluster rank r (the CTA's own when C == 1)
+template <int C, typename T>
+__device__ __forceinline__ T *rank_ptr(T *p, int r)
+{
+    if constexpr (C == 1) return p;
+    else return cg::this_cluster().map_shared_rank(p, r);
+}
+
+template <int N, int C, int BX, int BY, typename real>
 struct Tile {
-    static constexpr int NBX = N / BX, NBY = N / BY, NT = NBX * NBY;
-    using S = Smem<N, BX, BY, real>;
+    using S = Smem<N, C, BX, BY, real>;
+    static constexpr int NS = S::NS, NBX = S::NBX, NBY = S::NBY, NT = NBX * NBY;
 
     // Exchange the edges of x through buffer `buf`, then form
     //   g = bc x + b11 (xE + xW) + b22 (xN + xS) + A1 (xE - xW [+2h]) + A2 (xN - xS [+2h])
     //       + bx (dEW(b+1) - dEW(b-1)),
     // i.e. x + dt f(x); SECOND: out = (w + g) / 2, else out = g.
     template <int J, bool SECOND>
-    __device__ __forceinline__ static void stage(real *sm, int buf, int tx, int ty,
+    __device__ __forceinline__ static void stage(real *sm, int buf, int rank, int tx, int ty,
                                                  const real (&x)[BY][BX], real (&out)[BY][BX],
                                                  const real (&A1)[BY][BX], const real (&A2)[BY][BX],
                                                  real b11, real b22, real bx, real bc, real twoh)
@@ -160,22 +181,25 @@ struct Tile {
             st_vec<real, BY>(colL + tx * S::CS + b0, l);
             st_vec<real, BY>(colR + tx * S::CS + b0, r);
         }
-        __syncthreads();
-        // halos: south row b0-1, north row b0+BY, west column a0-1, east column a0+BX
+        tile_sync<C>();
+        // halos: south row b0-1, north row b0+BY, west column a0-1, east column a0+BX;
+        // rows beyond the slab come from the neighbouring CTA of the cluster (ring)
         real hS[BX], hN[BX], hW[BY + 2], hE[BY + 2];
         {
+            const int rS = (ty == 0) ? (rank + C - 1) % C : rank;
+            const int rN = (ty == NBY - 1) ? (rank + 1) % C : rank;
             const int tyS = (ty + NBY - 1) % NBY, tyN = (ty + 1) % NBY;
             const int txW = (tx + NBX - 1) % NBX, txE = (tx + 1) % NBX;
-            ld_vec<real, BX>(hS, rowB + tyS * N + a0);
-            ld_vec<real, BX>(hN, rowT + tyN * N + a0);
+            ld_vec<real, BX>(hS, rank_ptr<C>(rowB + tyS * N + a0, rS));
+            ld_vec<real, BX>(hN, rank_ptr<C>(rowT + tyN * N + a0, rN));
             const real *cw = colR + txW * S::CS;
             const real *ce = colL + txE * S::CS;
             real tmpw[BY], tmpe[BY];
             ld_vec<real, BY>(tmpw, cw + b0);
             ld_vec<real, BY>(tmpe, ce + b0);
-            const int bs = (b0 + N - 1) % N, bn = (b0 + BY) % N;
-            hW[0] = cw[bs]; hE[0] = ce[bs];
-            hW[BY + 1] = cw[bn]; hE[BY + 1] = ce[bn];
+            const int bs = (b0 + NS - 1) % NS, bn = (b0 + BY) % NS;
+            hW[0] = *rank_ptr<C>(cw + bs, rS); hE[0] = *rank_ptr<C>(ce + bs, rS);
+            hW[BY + 1] = *rank_ptr<C>(cw + bn, rN); hE[BY + 1] = *rank_ptr<C>(ce + bn, rN);
 #pragma unroll
             for (int k = 0; k < BY; ++k) { hW[k + 1] = tmpw[k]; hE[k + 1] = tmpe[k]; }
         }
@@ -231,21 +255,23 @@ struct Tile {
     }
 
     template <int J>
-    __device__ static void run(const PatchParams &prm, real *sm, long long p)
+    __device__ static void run(const PatchParams &prm, real *sm, long long p, int rank)
     {
         const int tid = threadIdx.x, tx = tid % NBX, ty = tid / NBX;
-        const int a0 = tx * BX, b0 = ty * BY;
+        const int a0 = tx * BX, b0 = ty * BY;          // slab-local
+        const int g0 = rank * NS;                       // first patch row of the slab
         double *red = reinterpret_cast<double *>(sm + S::WORDS);
         const long long Nl = prm.Nl;
         const long long pi = p % prm.n_macro, pj = p / prm.n_macro;
         const long long ox = patch_origin(pi, prm.n_macro, Nl, N);
         const long long oy = patch_origin(pj, prm.n_macro, Nl, N);
 
-        // ---- set-up: psi tile (patch-periodic), velocity, time step --------
+        // ---- set-up: psi rows g0-1 .. g0+NS (patch-periodic), velocity, time step --
         real *psi = sm;
         const real *band = static_cast<const real *>(prm.band);
-        for (int c = tid; c < N * N; c += NT) {
-            const int b = c / N, a = c % N;
+        for (int c = tid; c < N * (NS + 2); c += NT) {
+            const int rr = c / N, a = c % N;
+            const int b = (g0 - 1 + rr + N) % N;
             psi[c] = band[pmod_ll(oy + b, Nl) * Nl + pmod_ll(ox + a, Nl)];
         }
         __syncthreads();
@@ -254,24 +280,30 @@ struct Tile {
         real vmax = 0;
 #pragma unroll
         for (int r = 0; r < BY; ++r) {
-            const int b = b0 + r, bp = (b + 1) % N, bm = (b + N - 1) % N;
+            const int rr = b0 + r + 1;                  // psi row of this cell
 #pragma unroll
             for (int c = 0; c < BX; ++c) {
                 const int a = a0 + c, ap = (a + 1) % N, am = (a + N - 1) % N;
-                const real v1 = (psi[bm * N + a] - psi[bp * N + a]) * inv2h;
-                const real v2 = (psi[b * N + ap] - psi[b * N + am]) * inv2h;
+                const real v1 = (psi[(rr - 1) * N + a] - psi[(rr + 1) * N + a]) * inv2h;
+                const real v2 = (psi[rr * N + ap] - psi[rr * N + am]) * inv2h;
                 A1[r][c] = v1;
                 A2[r][c] = v2;
                 vmax = fmax(vmax, fabs(v1) + fabs(v2));
             }
         }
-        // block max of |v1| + |v2|
+        // patch max of |v1| + |v2|: warps -> CTA -> cluster (all ranks read all slots)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
         if ((tid & 31) == 0) red[tid >> 5] = (double)vmax;
         __syncthreads();
         double vm = 0.0;
-        for (int k = 0; k < (NT + 31) / 32; ++k) vm = fmax(vm, red[k]);
+        for (int k = 0; k < NT / 32; ++k) vm = fmax(vm, red[k]);
+        if constexpr (C > 1) {
+            if (tid == 0) red[32] = vm;
+            tile_sync<C>();
+            vm = 0.0;
+            for (int r = 0; r < C; ++r) vm = fmax(vm, *rank_ptr<C>(red + 32, r));
+        }
 
         const double B11 = prm.Kb[3 * p], B12 = prm.Kb[3 * p + 1], B22 = prm.Kb[3 * p + 2];
         double dt;
@@ -279,16 +311,18 @@ struct Tile {
         micro_schedule(prm.h, prm.L, vm, B11, B12, B22, prm.cfl, prm.t_burn, prm.t_avg,
                        prm.nb_fixed, prm.na_fixed, dt, nb, na);
         // a base tensor that is not positive definite (or not finite) gives no usable
-        // schedule: latch an error and return instead of stepping
+        // schedule: latch an error and return instead of stepping (every rank of the
+        // cluster takes this branch together: same inputs, same arithmetic)
         if (!(dt > 0.0) || !isfinite(dt) || nb < 0 || na < 1 || nb + na > kMaxSteps) {
-            if (tid == 0) {
+            if (tid == 0 && rank == 0) {
                 prm.S[4 * p + 2 * (J - 1)] = __longlong_as_double(0x7ff8000000000000ll);
                 prm.S[4 * p + 2 * (J - 1) + 1] = __longlong_as_double(0x7ff8000000000000ll);
                 atomicCAS(prm.status, 0, MLSD_EINVAL);
             }
+            if constexpr (C > 1) tile_sync<C>();   // no rank leaves while others read its slot
             return;
         }
-        if (J == 1 && tid == 0 && prm.steps) prm.steps[p] = nb + na;
+        if (J == 1 && tid == 0 && rank == 0 && prm.steps) prm.steps[p] = nb + na;
         const double hh = prm.h * prm.h;
         const real cA = (real)(dt / (2.0 * prm.h));
         const real b11 = (real)(dt * B11 / hh), b22 = (real)(dt * B22 / hh);
@@ -299,7 +333,7 @@ struct Tile {
         for (int r = 0; r < BY; ++r)
 #pragma unroll
             for (int c = 0; c < BX; ++c) { A1[r][c] *= cA; A2[r][c] *= cA; }
-        __syncthreads();   // psi tile is dead; its space becomes the exchange buffers
+        tile_sync<C>();   // psi tile (and the vmax slots) are dead; the space becomes the exchange buffers
 
         // ---- time stepping ------------------------------------------------
         real w[BY][BX], s[BY][BX];
@@ -312,8 +346,8 @@ struct Tile {
         int win = 0;
         const long long ntot = nb + na;
         for (long long step = 0; step < ntot; ++step) {
-            stage<J, false>(sm, 0, tx, ty, w, s, A1, A2, b11, b22, bx, bc, twoh);
-            stage<J, true>(sm, 1, tx, ty, s, w, A1, A2, b11, b22, bx, bc, twoh);
+            stage<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, b11, b22, bx, bc, twoh);
+            stage<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, b11, b22, bx, bc, twoh);
             if (step >= nb) {
                 real q1 = 0, q2 = 0;
 #pragma unroll
@@ -337,7 +371,7 @@ struct Tile {
 #pragma unroll
             for (int r = 0; r < BY; ++r)
 #pragma unroll
-                for (int c = 0; c < BX; ++c) wd[(b0 + r) * N + a0 + c] = w[r][c];
+                for (int c = 0; c < BX; ++c) wd[(g0 + b0 + r) * N + a0 + c] = w[r][c];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -349,7 +383,15 @@ struct Tile {
         __syncthreads();
         if (tid == 0) {
             double t1 = 0.0, t2 = 0.0;
-            for (int k = 0; k < (NT + 31) / 32; ++k) { t1 += red[2 * k]; t2 += red[2 * k + 1]; }
+            for (int k = 0; k < NT / 32; ++k) { t1 += red[2 * k]; t2 += red[2 * k + 1]; }
+            red[40] = t1;
+            red[41] = t2;
+        }
+        if constexpr (C > 1) tile_sync<C>();
+        else __syncthreads();
+        if (tid == 0 && rank == 0) {
+            double t1 = 0.0, t2 = 0.0;
+            for (int r = 0; r < C; ++r) { t1 += *rank_ptr<C>(red + 40, r); t2 += *rank_ptr<C>(red + 41, r); }
             // v_i = A_i / cA;  S_ij = (1/na) sum_steps mean_cells v_i w_j
             const double scale = 1.0 / ((double)cA * (double)N * (double)N * (double)na);
             const double s1j = t1 * scale, s2j = t2 * scale;
@@ -357,26 +399,30 @@ struct Tile {
             prm.S[4 * p + 2 * (J - 1) + 1] = s2j;
             if (!isfinite(s1j) || !isfinite(s2j)) atomicCAS(prm.status, 0, MLSD_ENONFINITE);
         }
+        if constexpr (C > 1) tile_sync<C>();   // keep every slab's shared memory alive until rank 0 has read it
     }
 };
 
-template <int N, int BX, int BY, typename real, int MINB>
-__global__ void __launch_bounds__((N / BX) * (N / BY), MINB)
+template <int N, int BX, int BY, typename real, int MINB, int C>
+__global__ void __launch_bounds__((N / BX) * (N / C / BY), MINB)
 k_patch_solve(PatchParams prm)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sm = reinterpret_cast<real *>(smem_raw);
-    const long long item = prm.item0 + blockIdx.x;
-    if (item >= prm.item0 + prm.items) return;
+    const long long item = prm.item0 + blockIdx.x / C;
+    const int rank = (int)(blockIdx.x % C);
+    if (item >= prm.item0 + prm.items) return;      // whole clusters only: C divides the grid
     const long long p = item >> 1;
-    if (item & 1) Tile<N, BX, BY, real>::template run<2>(prm, sm, p);
-    else Tile<N, BX, BY, real>::template run<1>(prm, sm, p);
+    if (item & 1) Tile<N, C, BX, BY, real>::template run<2>(prm, sm, p, rank);
+    else Tile<N, C, BX, BY, real>::template run<1>(prm, sm, p, rank);
 }
 
-template <int N, int BX, int BY, typename real, int MINB = 1>
+template <int N, int BX, int BY, typename real, int MINB = 1, int C = 1>
 void add_variant(std::vector<PatchVariant> &out)
 {
-    static_assert(((N / BX) * (N / BY)) % 32 == 0, "whole warps only");
+    static_assert(((N / BX) * (N / C / BY)) % 32 == 0, "whole warps only");
+    static_assert((N / BX) * (N / C / BY) <= 512, "reduction slots 0..31 (warp pairs), 32, 40, 41");
+    static_assert(N % C == 0 && (N / C) % BY == 0 && N % BX == 0, "tiling");
     PatchVariant v;
     v.n = N;
     v.precision = sizeof(real) == 4 ? MLSD_FP32 : MLSD_FP64;
@@ -384,9 +430,10 @@ void add_variant(std::vector<PatchVariant> &out)
     v.by = BY;
     v.minb = MINB;
     v.packed = 0;
-    v.threads = (N / BX) * (N / BY);
-    v.smem = Smem<N, BX, BY, real>::BYTES;
-    v.fn = reinterpret_cast<const void *>(&k_patch_solve<N, BX, BY, real, MINB>);
+    v.cluster = C;
+    v.threads = (N / BX) * (N / C / BY);
+    v.smem = Smem<N, C, BX, BY, real>::BYTES;
+    v.fn = reinterpret_cast<const void *>(&k_patch_solve<N, BX, BY, real, MINB, C>);
     out.push_back(v);
 }
 
@@ -693,6 +740,7 @@ void add_variant2(std::vector<PatchVariant> &out)
     v.by = BY;
     v.minb = MINB;
     v.packed = 1;
+    v.cluster = 1;
     v.threads = (N / BX) * (N / BY);
     v.smem = Smem2<N, BX, BY>::BYTES;
     v.fn = reinterpret_cast<const void *>(&k_patch_solve2<N, BX, BY, MINB>);
@@ -741,6 +789,16 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
             add_variant2<64, 2, 4>(out);
             add_variant2<64, 4, 2>(out);
             break;
+        case 128:   // split over a cluster of CTAs (rows in slabs)
+            add_variant<128, 4, 8, float, 3, 4>(out);
+            add_variant<128, 4, 8, float, 1, 2>(out);
+            add_variant<128, 4, 4, float, 1, 4>(out);
+            break;
+        case 256:
+            add_variant<256, 4, 8, float, 1, 8>(out);
+            add_variant<256, 4, 4, float, 1, 8>(out);
+            add_variant<256, 4, 8, float, 3, 16>(out);
+            break;
         default: break;
         }
     } else {
@@ -767,6 +825,25 @@ cudaError_t launch_patch(const PatchVariant &v, const PatchParams &p, long long 
     if (e != cudaSuccess) return e;
     void *args[] = {const_cast<PatchParams *>(&p)};
     count_launches(1);
+    if (v.cluster > 1) {
+        if (v.cluster > 8) {
+            e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(grid * v.cluster));
+        cfg.blockDim = dim3(v.threads);
+        cfg.dynamicSmemBytes = v.smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)v.cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelExC(&cfg, v.fn, args);
+    }
     // packed kernels take one CTA per patch (both fields), item0 and grid even
     const long long g = v.packed ? (grid + 1) / 2 : grid;
     return cudaLaunchKernel(v.fn, dim3((unsigned)g), dim3(v.threads), args, v.smem, s);

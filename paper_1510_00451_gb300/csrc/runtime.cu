@@ -279,7 +279,10 @@ int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;   // -> (bx, code(by, minb, packed))
 
-int tile_code(const PatchVariant &v) { return v.by * 16 + v.minb + 4096 * v.packed; }
+int tile_code(const PatchVariant &v)
+{
+    return v.by * 16 + v.minb + 4096 * v.packed + 65536 * v.cluster;
+}
 
 int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s)
 {
@@ -288,18 +291,24 @@ int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s)
     if (vs.empty()) return MLSD_EUNSUPPORTED;
     d.variant = vs[0];
     if (const char *env = std::getenv("MLSD_TILE")) {
-        // <bx>x<by>[m<minb>][p]: p selects the packed two-field kernel
-        int bx = 0, by = 0, mb = 1, pk = 0;
+        // <bx>x<by>[m<minb>][c<cluster>][p]: p selects the packed two-field kernel
+        int bx = 0, by = 0, mb = 1, pk = 0, cl = 1;
         char rest[16] = "";
         if (std::sscanf(env, "%dx%d%15s", &bx, &by, rest) >= 2) {
             for (const char *c = rest; *c; ++c) {
                 if (*c == 'm') mb = std::atoi(c + 1);
+                if (*c == 'c') cl = std::atoi(c + 1);
                 if (*c == 'p') pk = 1;
             }
             for (auto &v : vs)
-                if (v.bx == bx && v.by == by && v.minb == mb && v.packed == pk) { d.variant = v; return MLSD_OK; }
+                if (v.bx == bx && v.by == by && v.minb == mb && v.packed == pk && v.cluster == cl) {
+                    d.variant = v;
+                    return MLSD_OK;
+                }
+            // the forced tiling is not compiled for this patch size: use the tuner
+        } else {
+            return MLSD_EINVAL;
         }
-        return MLSD_EINVAL;
     }
     if (vs.size() == 1) return MLSD_OK;
     int dev = 0;
@@ -469,6 +478,8 @@ int mlsd_level_info(const mlsd_levels *h, int level, mlsd_level_desc *out)
     out->tile_by = d.variant.by;
     out->threads = d.variant.threads;
     out->packed = d.variant.packed;
+    out->cluster = d.variant.cluster;
+    out->min_ctas = d.variant.minb;
     return MLSD_OK;
 }
 
@@ -655,6 +666,29 @@ int mlsd_dns_run(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev, d
         return MLSD_EINVAL;
     CK(dns_run(nf, u_dev, u_tmp_dev, psi_dev, kappa, dt, nsteps,
                static_cast<cudaStream_t>(cuda_stream)));
+    return MLSD_OK;
+}
+
+int mlsd_dns_dt(int nf, const float *psi_dev, double kappa, double cfl, double *dt_out_host,
+                void *cuda_stream)
+{
+    if (nf < 2 || !psi_dev || !(kappa > 0) || !(cfl > 0) || !dt_out_host) return MLSD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    unsigned *m = nullptr;
+    CK(cudaMallocAsync((void **)&m, sizeof(unsigned), s));
+    cudaError_t e = dns_vmax(nf, psi_dev, m, s);
+    unsigned bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, m, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(m, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    CK(e);
+    float vmax;
+    std::memcpy(&vmax, &bits, sizeof(float));
+    if (!std::isfinite(vmax)) return MLSD_ENONFINITE;
+    const double h = 2.0 * kPi / nf;
+    double dt = h * h / (4.0 * kappa);
+    if (vmax > 0) dt = std::min(dt, h / (double)vmax);
+    *dt_out_host = cfl * dt;
     return MLSD_OK;
 }
 

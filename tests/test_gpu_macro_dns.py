@@ -91,6 +91,7 @@ def test_dns_parity(mlsd, torch_mod, nf, steps):
     dev = torch_mod.device("cuda:0")
     psi = torch_mod.zeros(nf, nf, dtype=torch_mod.float32, device=dev)
     mlsd.grid_psi(spec, nf, psi)
+    assert mlsd.dns_dt(psi, kappa, 0.2) == pytest.approx(dt, rel=1e-6)
     u = torch_mod.tensor(u0, dtype=torch_mod.float32, device=dev)
     ut = torch_mod.empty_like(u)
     mlsd.dns_run(u, ut, psi, kappa, dt, steps)
