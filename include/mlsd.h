@@ -79,6 +79,16 @@ typedef struct {
     int64_t n_burn_fixed;      /* if n_avg_fixed > 0: fixed step counts replace the tau rule */
     int64_t n_avg_fixed;
     int precision;             /* MLSD_FP32 or MLSD_FP64 */
+    /* Patch sizes per patch (uneven sizes within a level).  A level whose
+     * patch_n is 0 takes, per patch, the smallest power of two n in
+     * [n_min, n_max] with n >= 10 kmax L / (2 pi) (10 points per wavelength of
+     * the level's finest diagonal mode, kmax = max(|k1|, |k2|)) and
+     * n >= L vmax / (2 kappa) (cell Peclet number <= 2 with the molecular
+     * diffusivity), vmax = max |v| of the level's band over the patch's 32 x 32
+     * reference nodes.  patch_n_map, if not NULL, gives every patch's size
+     * explicitly ([L][P], overrides patch_n).                                 */
+    const int32_t *patch_n_map;
+    int n_min, n_max;          /* 0 -> 32, 256 */
 } mlsd_problem;
 
 /* Description of one level, as built. */
@@ -93,6 +103,8 @@ typedef struct {
     int packed;                /* 1: one CTA per patch, both fields in f32x2 pairs; 0: one per field */
     int cluster;               /* CTAs (a thread-block cluster) sharing one patch field, in row slabs */
     int min_ctas;              /* register cap of the kernel: at least this many CTAs per SM */
+    int n_classes;             /* patch sizes in the level; n, Nl, h and the tile fields describe
+                                  the class with the most work; all classes run concurrently */
 } mlsd_level_desc;
 
 typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and scratch */
@@ -118,6 +130,9 @@ void mlsd_free_levels(mlsd_levels *h);
 
 int mlsd_level_info(const mlsd_levels *h, int level, mlsd_level_desc *out);
 
+/* Patch size of every patch of a level: n_out_host [P].  Host only.       */
+int mlsd_patch_sizes(const mlsd_levels *h, int level, int32_t *n_out_host);
+
 /* One level of patch solves: the numerical homogenization K[psi_l, B; Omega_l]
  * of Sec. 2.2 for every macro node at once.  For each patch and each
  * gradient G = e_j (j = 1, 2) the fluctuation w_j (u = G.x + w_j, w_j periodic
@@ -135,7 +150,8 @@ int mlsd_level_info(const mlsd_levels *h, int level, mlsd_level_desc *out);
  *   K_base_dev device [P][3] base diffusivity B per patch (symmetric positive definite)
  *   K_out_dev  device [P][3] result; may not alias K_base_dev
  *   w_dump_dev device [P][2][n][n] of float (MLSD_FP32) or double (MLSD_FP64)
- *              receiving the final w_1, w_2 of every patch, or NULL          */
+ *              receiving the final w_1, w_2 of every patch, or NULL; only for
+ *              a level with one patch size (else MLSD_EINVAL)                */
 int mlsd_solve_level(mlsd_levels *h, int level, const double *K_base_dev, double *K_out_dev,
                      void *w_dump_dev, void *cuda_stream);
 

@@ -53,6 +53,8 @@ def _declare(L):
     L.orc_offdiag_apply.argtypes = [_i, _p, _p, _p, _p]
     L.orc_chain.argtypes = [_i, _p, _p, _p, _p, _i, _p, _p, _p, _i, _d, _d, _d, _d, _l, _l,
                             _i, _p, _p, _p, _p, _p]
+    L.orc_patch_n_rule.argtypes = [_i, _p, _p, _p, _p, _p, _l, _i, _i, _i, _d, _i, _i, _i, _p]
+    L.orc_patch_n_rule.restype = _i
     L.orc_macro_dt.argtypes = [_i, _p, _d]
     L.orc_macro_dt.restype = _d
     L.orc_macro_run.argtypes = [_i, _p, _p, _d, _l, _p]
@@ -180,29 +182,53 @@ def level_lattice(edges, patch_n, patch_div=None):
     """Lattice size Nl = n * m_l per level; L_l = 2 pi / m_l with m_l = e_{l-1}
     by default (one period of the level's lowest wavenumber)."""
     Lc = len(edges) - 1
+    m = level_div(edges, patch_div)
+    return [int(patch_n[l]) * m[l] for l in range(Lc)]
+
+
+def level_div(edges, patch_div=None):
+    Lc = len(edges) - 1
     if patch_div is None:
-        patch_div = [int(round(edges[l])) for l in range(Lc)]
-    return [int(patch_n[l]) * int(patch_div[l]) for l in range(Lc)]
+        return [int(round(edges[l])) for l in range(Lc)]
+    return [int(x) for x in patch_div]
+
+
+def patch_n_rule(spec, edges, level, node, n_macro, kappa, n_min=32, n_max=256, nref=32,
+                 patch_div=None):
+    """Patch resolution of one node at one level (uneven patch sizes)."""
+    k1, k2, re, im = _modes(spec)
+    lev, kind = band_of(spec, edges)
+    use = np.ascontiguousarray((lev == level) & (kind == 0), dtype=np.uint8)
+    m = level_div(edges, patch_div)[level - 1]
+    vm = ctypes.c_double()
+    n = lib().orc_patch_n_rule(len(k1), _ptr(k1), _ptr(k2), _ptr(re), _ptr(im), _ptr(use), int(m),
+                               int(node[0]), int(node[1]), int(n_macro), float(kappa), int(nref),
+                               int(n_min), int(n_max), ctypes.byref(vm))
+    return n, vm.value
 
 
 def chain(spec, edges, patch_n, n_macro, kappa, nodes, cfl=0.2, t_burn=8.0, t_avg=4.0,
-          n_burn_fixed=-1, n_avg_fixed=0, patch_div=None, want_levels=False, want_steps=False):
+          n_burn_fixed=-1, n_avg_fixed=0, patch_div=None, want_levels=False, want_steps=False,
+          node_n=None):
     """Algorithm 3 down the whole level hierarchy for the macro nodes (i, j) given.
 
+    patch_n gives n per level; node_n (optional, [nodes][L]) overrides it per node.
     Returns K [nodes][3]; with want_levels also K*_l [nodes][L][3]; with want_steps
     also the step counts n_burn + n_avg [nodes][L] of every patch solve."""
     k1, k2, re, im = _modes(spec)
     e = _f64(edges)
     Lc = len(e) - 1
-    pn = _i32(patch_n)
-    Nl = np.ascontiguousarray(level_lattice(edges, patch_n, patch_div), dtype=np.int64)
     nodes = np.asarray(nodes, dtype=np.int32).reshape(-1, 2)
     ni = _i32(nodes[:, 0]); nj = _i32(nodes[:, 1])
+    if node_n is None:
+        node_n = np.tile(np.asarray(patch_n, dtype=np.int32), (len(ni), 1))
+    nn = np.ascontiguousarray(node_n, dtype=np.int32).reshape(len(ni), Lc)
+    md = np.ascontiguousarray(level_div(edges, patch_div), dtype=np.int64)
     K = np.zeros((len(ni), 3))
     Kl = np.zeros((len(ni), Lc, 3)) if want_levels else None
     st = np.zeros((len(ni), Lc), dtype=np.int64) if want_steps else None
-    lib().orc_chain(len(k1), _ptr(k1), _ptr(k2), _ptr(re), _ptr(im), Lc, _ptr(e), _ptr(pn),
-                    _ptr(Nl), int(n_macro), float(kappa), float(cfl), float(t_burn), float(t_avg),
+    lib().orc_chain(len(k1), _ptr(k1), _ptr(k2), _ptr(re), _ptr(im), Lc, _ptr(e), _ptr(nn),
+                    _ptr(md), int(n_macro), float(kappa), float(cfl), float(t_burn), float(t_avg),
                     int(n_burn_fixed), int(n_avg_fixed), len(ni), _ptr(ni), _ptr(nj),
                     _ptr(K), _ptr(Kl), _ptr(st))
     out = [K]

@@ -349,12 +349,51 @@ void orc_offdiag_apply(int n, const double *q12, const double *q21, const double
 }
 
 /* ------------------------------------------------------------------------ */
-/* Level description used by the chain: one entry per level.                 */
+/* Patch resolution rule for uneven patch sizes: at least 10 points per      */
+/* wavelength of the level's finest diagonal mode and a cell Peclet number   */
+/* of at most 2 with the molecular diffusivity (the smallest base the level  */
+/* can see):  n = clamp(pow2ceil(max(10 kmax L / 2pi, L vmax / (2 kappa))),  */
+/* n_min, n_max).  kmax = max(|k1|, |k2|) over the level's diagonal modes;   */
+/* vmax = max |v| of the band's exact velocity                              */
+/*   v1 = sum k2 (re sin t + im cos t),  v2 = -sum k1 (re sin t + im cos t)  */
+/* over the patch's nodes on a reference grid of nref x nref points.        */
 /* ------------------------------------------------------------------------ */
-typedef struct {
-    int n;          /* patch grid n x n */
-    long Nl;        /* lattice points per 2*pi: L = 2 pi n / Nl */
-} orc_level;
+int orc_patch_n_rule(int n_modes, const int *k1, const int *k2, const double *re,
+                     const double *im, const unsigned char *use, long m, int i, int j,
+                     int n_macro, double kappa, int nref, int n_min, int n_max, double *vmax_out)
+{
+    int kmax = 0;
+    for (int t = 0; t < n_modes; ++t)
+        if (use[t]) {
+            int a = abs(k1[t]) > abs(k2[t]) ? abs(k1[t]) : abs(k2[t]);
+            if (a > kmax) kmax = a;
+        }
+    long Nr = (long)nref * m;
+    long ox = orc_patch_origin(i, n_macro, Nr, nref), oy = orc_patch_origin(j, n_macro, Nr, nref);
+    double vmax = 0.0;
+    for (int b = 0; b < nref; ++b)
+        for (int a = 0; a < nref; ++a) {
+            double v1 = 0.0, v2 = 0.0;
+            for (int t = 0; t < n_modes; ++t) {
+                if (!use[t]) continue;
+                long r = pmod((long)k1[t] * (ox + a) + (long)k2[t] * (oy + b), Nr);
+                double th = 2.0 * ORC_PI * (double)r / (double)Nr;
+                double q = re[t] * sin(th) + im[t] * cos(th);
+                v1 += k2[t] * q;
+                v2 -= k1[t] * q;
+            }
+            double sp = sqrt(v1 * v1 + v2 * v2);
+            if (sp > vmax) vmax = sp;
+        }
+    if (vmax_out) *vmax_out = vmax;
+    double L = 2.0 * ORC_PI / (double)m;
+    double need = 10.0 * kmax * L / (2.0 * ORC_PI);
+    double pe = L * vmax / (2.0 * kappa);
+    if (pe > need) need = pe;
+    int n = n_min;
+    while (n < n_max && (double)n < need) n *= 2;
+    return n;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Algorithm 3, applied recursively from the finest level (L) to the        */
@@ -366,13 +405,16 @@ typedef struct {
 /*   K = K*_1                                                               */
 /* psi_l,diag is the diagonal band of level l; K_off,l is Algorithms 1-2     */
 /* with level l's off-diagonal parts (the identity when there are none).    */
+/* Patch geometry: level l has side L_l = 2 pi / patch_div[l]; the patch of  */
+/* node p at level l has node_n[p * L + l] points per side (lattice          */
+/* Nl = n * patch_div[l]).                                                  */
 /* Outputs per node: K[3] and, optionally, the per-level K*_l [L][3] and the  */
 /* step counts n_burn + n_avg of every level's patch solve [L].              */
 /* The time step and window of every patch solve follow orc_micro_dt and    */
 /* orc_micro_steps, unless n_burn_fixed / n_avg_fixed are positive.         */
 /* ------------------------------------------------------------------------ */
 void orc_chain(int n_modes, const int *k1, const int *k2, const double *re, const double *im,
-               int n_levels, const double *edges, const int *patch_n, const long *Nl,
+               int n_levels, const double *edges, const int *node_n, const long *patch_div,
                int n_macro, double kappa, double cfl, double t_burn, double t_avg,
                long n_burn_fixed, long n_avg_fixed,
                int n_nodes, const int *node_i, const int *node_j,
@@ -388,16 +430,17 @@ void orc_chain(int n_modes, const int *k1, const int *k2, const double *re, cons
         double (*Koffl)[3] = malloc(sizeof(double) * 3 * (n_levels + 2));
         double Kstar[3], base[3], Knet[3];
         int nmax = 0;
-        for (int l = 0; l < n_levels; ++l) if (patch_n[l] > nmax) nmax = patch_n[l];
+        for (int l = 0; l < n_levels; ++l) if (node_n[(long)p * n_levels + l] > nmax) nmax = node_n[(long)p * n_levels + l];
         double *psi = malloc(sizeof(double) * nmax * nmax);
         double **Q12 = malloc(sizeof(double *) * n_levels), **Q21 = malloc(sizeof(double *) * n_levels);
 
         /* per level: line variances of the off-diagonal parts at this node */
         for (int l = 1; l <= n_levels; ++l) {
-            int n = patch_n[l - 1];
-            long ox = orc_patch_origin(node_i[p], n_macro, Nl[l - 1], n);
-            long oy = orc_patch_origin(node_j[p], n_macro, Nl[l - 1], n);
-            double L = 2.0 * ORC_PI * n / (double)Nl[l - 1];
+            int n = node_n[(long)p * n_levels + (l - 1)];
+            long Nl = (long)n * patch_div[l - 1];
+            long ox = orc_patch_origin(node_i[p], n_macro, Nl, n);
+            long oy = orc_patch_origin(node_j[p], n_macro, Nl, n);
+            double L = 2.0 * ORC_PI * n / (double)Nl;
             for (int t = 0; t < n_modes; ++t) {
                 u12[t] = (lev[t] == l && kind[t] == 1);
                 u21[t] = (lev[t] == l && kind[t] == 2);
@@ -406,7 +449,7 @@ void orc_chain(int n_modes, const int *k1, const int *k2, const double *re, cons
             for (int t = 0; t < n_modes; ++t) { any12 |= u12[t]; any21 |= u21[t]; }
             Q12[l - 1] = malloc(sizeof(double) * n);
             Q21[l - 1] = malloc(sizeof(double) * n);
-            orc_offdiag_q(n_modes, k1, k2, re, im, u12, u21, Nl[l - 1], ox, oy, n, L,
+            orc_offdiag_q(n_modes, k1, k2, re, im, u12, u21, Nl, ox, oy, n, L,
                           Q12[l - 1], Q21[l - 1]);
             if (!any12) { free(Q12[l - 1]); Q12[l - 1] = NULL; }
             if (!any21) { free(Q21[l - 1]); Q21[l - 1] = NULL; }
@@ -414,15 +457,16 @@ void orc_chain(int n_modes, const int *k1, const int *k2, const double *re, cons
         /* top-down closed forms */
         Bl[1][0] = kappa; Bl[1][1] = 0.0; Bl[1][2] = kappa;
         for (int l = 1; l <= n_levels; ++l) {
-            orc_offdiag_apply(patch_n[l - 1], Q12[l - 1], Q21[l - 1], Bl[l], Koffl[l]);
+            orc_offdiag_apply(node_n[(long)p * n_levels + (l - 1)], Q12[l - 1], Q21[l - 1], Bl[l], Koffl[l]);
             if (l < n_levels) memcpy(Bl[l + 1], Koffl[l], sizeof(double) * 3);
         }
         /* bottom-up patch solves */
         for (int l = n_levels; l >= 1; --l) {
-            int n = patch_n[l - 1];
-            long ox = orc_patch_origin(node_i[p], n_macro, Nl[l - 1], n);
-            long oy = orc_patch_origin(node_j[p], n_macro, Nl[l - 1], n);
-            double L = 2.0 * ORC_PI * n / (double)Nl[l - 1];
+            int n = node_n[(long)p * n_levels + (l - 1)];
+            long Nl = (long)n * patch_div[l - 1];
+            long ox = orc_patch_origin(node_i[p], n_macro, Nl, n);
+            long oy = orc_patch_origin(node_j[p], n_macro, Nl, n);
+            double L = 2.0 * ORC_PI * n / (double)Nl;
             double h = L / n;
             if (l == n_levels) {
                 memcpy(base, Koffl[l], sizeof(base));
@@ -431,7 +475,7 @@ void orc_chain(int n_modes, const int *k1, const int *k2, const double *re, cons
                 orc_offdiag_apply(n, Q12[l - 1], Q21[l - 1], Knet, base);
             }
             for (int t = 0; t < n_modes; ++t) ud[t] = (lev[t] == l && kind[t] == 0);
-            orc_patch_psi(n_modes, k1, k2, re, im, ud, Nl[l - 1], ox, oy, n, psi);
+            orc_patch_psi(n_modes, k1, k2, re, im, ud, Nl, ox, oy, n, psi);
             double *v1 = malloc(sizeof(double) * n * n), *v2 = malloc(sizeof(double) * n * n);
             orc_velocity(n, h, psi, v1, v2);
             double vmax = 0.0;

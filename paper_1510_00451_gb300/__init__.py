@@ -26,7 +26,7 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_offdiag", "mlsd_effective_diffusivity", "mlsd_status", "mlsd_macro_step",
             "mlsd_macro_dt", "mlsd_grid_psi", "mlsd_dns_run", "mlsd_coarse_grain",
             "mlsd_level_work", "mlsd_launch_count", "mlsd_profile", "mlsd_profile_collect",
-            "mlsd_coarse_grain_noalloc", "mlsd_dns_dt", "mlsd_strerror"]
+            "mlsd_coarse_grain_noalloc", "mlsd_dns_dt", "mlsd_patch_sizes", "mlsd_strerror"]
 NOALLOC_MAX_MACRO = 256
 
 
@@ -45,7 +45,8 @@ class mlsd_problem(ctypes.Structure):
                 ("patch_n", ctypes.c_void_p), ("cfl", ctypes.c_double),
                 ("t_burn_tau", ctypes.c_double), ("t_avg_tau", ctypes.c_double),
                 ("n_burn_fixed", ctypes.c_int64), ("n_avg_fixed", ctypes.c_int64),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("patch_n_map", ctypes.c_void_p),
+                ("n_min", ctypes.c_int), ("n_max", ctypes.c_int)]
 
 
 class mlsd_level_desc(ctypes.Structure):
@@ -54,7 +55,7 @@ class mlsd_level_desc(ctypes.Structure):
                 ("n_diag_modes", ctypes.c_int), ("n_off12_modes", ctypes.c_int),
                 ("n_off21_modes", ctypes.c_int), ("tile_bx", ctypes.c_int),
                 ("tile_by", ctypes.c_int), ("threads", ctypes.c_int), ("packed", ctypes.c_int),
-                ("cluster", ctypes.c_int), ("min_ctas", ctypes.c_int)]
+                ("cluster", ctypes.c_int), ("min_ctas", ctypes.c_int), ("n_classes", ctypes.c_int)]
 
 
 _P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
@@ -76,6 +77,7 @@ _lib.mlsd_profile.argtypes = [_P, _I]
 _lib.mlsd_profile_collect.argtypes = [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_L)]
 _lib.mlsd_launch_count.argtypes = []
 _lib.mlsd_launch_count.restype = _L
+_lib.mlsd_patch_sizes.argtypes = [_P, _I, _P]
 _lib.mlsd_dns_dt.argtypes = [_I, _P, _D, _D, ctypes.POINTER(_D), _P]
 _lib.mlsd_coarse_grain_noalloc.argtypes = [_I, _P, _I, _P, _P, _P]
 _lib.mlsd_strerror.argtypes = [_I]
@@ -112,13 +114,15 @@ class Levels:
 
     def __init__(self, spectrum, kappa, n_macro, edges, patch_n, patch_div=None, cfl=0.2,
                  t_burn_tau=8.0, t_avg_tau=4.0, n_burn_fixed=0, n_avg_fixed=0,
-                 precision="fp32", stream=None):
+                 precision="fp32", patch_n_map=None, n_min=0, n_max=0, stream=None):
         k1, k2, re, im = spectrum.as_arrays()
         self._keep = [k1, k2, re, im,
                       np.ascontiguousarray(edges, dtype=np.float64),
                       np.ascontiguousarray(patch_n, dtype=np.int32),
                       None if patch_div is None else np.ascontiguousarray(patch_div, dtype=np.int32)]
         e, pn, pdv = self._keep[4], self._keep[5], self._keep[6]
+        nmap = None if patch_n_map is None else np.ascontiguousarray(patch_n_map, dtype=np.int32)
+        self._keep.append(nmap)
         self.precision = MLSD_FP64 if precision in ("fp64", MLSD_FP64) else MLSD_FP32
         p = mlsd_problem(n_macro=int(n_macro), kappa=float(kappa), n_modes=len(k1),
                          k1=k1.ctypes.data, k2=k2.ctypes.data, re=re.ctypes.data,
@@ -126,7 +130,9 @@ class Levels:
                          patch_div=None if pdv is None else pdv.ctypes.data,
                          patch_n=pn.ctypes.data, cfl=float(cfl), t_burn_tau=float(t_burn_tau),
                          t_avg_tau=float(t_avg_tau), n_burn_fixed=int(n_burn_fixed),
-                         n_avg_fixed=int(n_avg_fixed), precision=self.precision)
+                         n_avg_fixed=int(n_avg_fixed), precision=self.precision,
+                         patch_n_map=None if nmap is None else nmap.ctypes.data,
+                         n_min=int(n_min), n_max=int(n_max))
         h = _P()
         _check(_lib.mlsd_build_levels(ctypes.byref(p), _stream(stream), ctypes.byref(h)),
                "mlsd_build_levels")
@@ -150,6 +156,11 @@ class Levels:
         d = mlsd_level_desc()
         _check(_lib.mlsd_level_info(self.h, int(level), ctypes.byref(d)), "mlsd_level_info")
         return {f: getattr(d, f) for f, _ in d._fields_}
+
+    def patch_sizes(self, level):
+        out = np.zeros(self.P, dtype=np.int32)
+        _check(_lib.mlsd_patch_sizes(self.h, int(level), out.ctypes.data), "mlsd_patch_sizes")
+        return out
 
     def solve_level(self, level, K_base, K_out, w_dump=None, stream=None):
         _check(_lib.mlsd_solve_level(self.h, int(level), _dptr(K_base), _dptr(K_out),

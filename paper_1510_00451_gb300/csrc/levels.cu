@@ -62,10 +62,10 @@ __device__ double psi_point(const ModeList &m, long long Nr, long long gx, long 
 //   q12[p][a] = var_s psi_12(x_a, y_s), y_s on the r12-times refined lattice,
 //   q21[p][b] = var_s psi_21(x_s, y_b).
 __global__ void k_offdiag_q(ModeList m12, ModeList m21, long long Nl, int n, int r12, int r21,
-                            int n_macro, double *q12, double *q21)
+                            int n_macro, const int *idx, int stride, double *q12, double *q21)
 {
     __shared__ double red[2][32];
-    const long long p = blockIdx.x;
+    const long long p = idx ? (long long)idx[blockIdx.x] : (long long)blockIdx.x;
     const int line = blockIdx.y;          // 0..n-1 -> psi_12 column, n..2n-1 -> psi_21 row
     const bool is12 = line < n;
     const ModeList &m = is12 ? m12 : m21;
@@ -77,8 +77,8 @@ __global__ void k_offdiag_q(ModeList m12, ModeList m21, long long Nl, int n, int
     const long long oy = patch_origin(p / n_macro, n_macro, Nl, n);
     const long long Nr = Nl * r, ms = (long long)n * r;
     double s1 = 0.0, s2 = 0.0;
-    // two-pass variance in one sweep of the samples: accumulate sum and sum of squares
-    // of the shifted value (psi - psi at the first sample) to limit cancellation
+    // one sweep over the samples: sum and sum of squares of (psi - psi at the first
+    // sample), which limits cancellation
     const double ref = is12 ? psi_point(m, Nr, (ox + k) * r, oy * r)
                             : psi_point(m, Nr, ox * r, (oy + k) * r);
     for (long long s = threadIdx.x; s < ms; s += blockDim.x) {
@@ -98,7 +98,31 @@ __global__ void k_offdiag_q(ModeList m12, ModeList m21, long long Nl, int n, int
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; }
         const double mean = a / (double)ms;
         double var = b / (double)ms - mean * mean;
-        q[p * n + k] = var > 0.0 ? var : 0.0;
+        q[p * stride + k] = var > 0.0 ? var : 0.0;
+    }
+}
+
+// per patch: max over its nref x nref reference nodes of sqrt(v1^2 + v2^2)
+__global__ void k_patch_vmax(const double *v1, const double *v2, long long Nr, int nref,
+                             int n_macro, double *vmax)
+{
+    __shared__ double red[32];
+    const long long p = blockIdx.x;
+    const long long ox = patch_origin(p % n_macro, n_macro, Nr, nref);
+    const long long oy = patch_origin(p / n_macro, n_macro, Nr, nref);
+    double m = 0.0;
+    for (int c = threadIdx.x; c < nref * nref; c += blockDim.x) {
+        const long long gy = pmod_ll(oy + c / nref, Nr), gx = pmod_ll(ox + c % nref, Nr);
+        const double a = v1[gy * Nr + gx], b = v2[gy * Nr + gx];
+        m = fmax(m, sqrt(a * a + b * b));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+        vmax[p] = t;
     }
 }
 
@@ -108,15 +132,16 @@ __global__ void k_offdiag_q(ModeList m12, ModeList m21, long long Nl, int n, int
 __device__ void offdiag_apply(const OffdiagLevel &o, long long p, const double *B, double *K)
 {
     double k12_11 = B[0], k21_22 = B[2];
+    const int n = o.np ? o.np[p] : o.stride;
     if (o.q12) {
         double s = 0.0;
-        for (int a = 0; a < o.n; ++a) s += 1.0 / (B[0] + o.q12[p * o.n + a] / B[2]);
-        k12_11 = (double)o.n / s;
+        for (int a = 0; a < n; ++a) s += 1.0 / (B[0] + o.q12[p * o.stride + a] / B[2]);
+        k12_11 = (double)n / s;
     }
     if (o.q21) {
         double s = 0.0;
-        for (int b = 0; b < o.n; ++b) s += 1.0 / (B[2] + o.q21[p * o.n + b] / B[0]);
-        k21_22 = (double)o.n / s;
+        for (int b = 0; b < n; ++b) s += 1.0 / (B[2] + o.q21[p * o.stride + b] / B[0]);
+        k21_22 = (double)n / s;
     }
     if (!o.q12 && !o.q21) { K[0] = B[0]; K[1] = B[1]; K[2] = B[2]; return; }
     K[0] = k12_11 + B[0] - B[0];
@@ -190,13 +215,21 @@ cudaError_t launch_band_synth(const ModeGroups &m, long long Nl, double2 *G, voi
 }
 
 cudaError_t launch_offdiag_q(const ModeList &m12, const ModeList &m21, long long Nl, int n,
-                             int r12, int r21, int n_macro, long long P, double *q12,
-                             double *q21, cudaStream_t s)
+                             int r12, int r21, int n_macro, long long count, const int *idx,
+                             int stride, double *q12, double *q21, cudaStream_t s)
 {
-    if (m12.n == 0 && m21.n == 0) return cudaSuccess;
-    dim3 g((unsigned)P, (unsigned)(2 * n));
+    if ((m12.n == 0 && m21.n == 0) || count == 0) return cudaSuccess;
+    dim3 g((unsigned)count, (unsigned)(2 * n));
     count_launches(1);
-    k_offdiag_q<<<g, 128, 0, s>>>(m12, m21, Nl, n, r12, r21, n_macro, q12, q21);
+    k_offdiag_q<<<g, 128, 0, s>>>(m12, m21, Nl, n, r12, r21, n_macro, idx, stride, q12, q21);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_patch_vmax(const double *v1, const double *v2, long long Nr, int nref,
+                              int n_macro, long long P, double *vmax, cudaStream_t s)
+{
+    count_launches(1);
+    k_patch_vmax<<<(unsigned)P, 256, 0, s>>>(v1, v2, Nr, nref, n_macro, vmax);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ struct PatchParams {
     long long P;             // patches
     long long item0, items;  // work items [item0, item0 + items), item = 2p + (j - 1)
     long long *steps;        // [P] n_burn + n_avg per patch (written by the j = 1 CTA) or nullptr
+    const int *pidx;         // patch index of work-item pair (item >> 1), or nullptr: identity
 };
 
 // Variant of the patch kernel: thread block shape per patch size and precision.
@@ -49,9 +50,10 @@ cudaError_t launch_compose(long long P, const double *B, const double *S, double
 // ---------------------------------------------------------------------------
 // Level chain (Algorithm 3) helpers.
 struct OffdiagLevel {
-    const double *q12;       // [P][n] line variances of psi_12 or nullptr
-    const double *q21;       // [P][n] line variances of psi_21 or nullptr
-    int n;
+    const double *q12;       // [P][stride] line variances of psi_12 or nullptr
+    const double *q21;       // [P][stride] line variances of psi_21 or nullptr
+    int stride;              // largest patch size of the level
+    const int *np;           // [P] lines (= patch size) per patch, or nullptr: all = stride
 };
 struct ChainTables {
     int L;
@@ -93,8 +95,12 @@ struct ModeList {
     const double *re, *im;
 };
 cudaError_t launch_offdiag_q(const ModeList &m12, const ModeList &m21, long long Nl, int n,
-                             int r12, int r21, int n_macro, long long P, double *q12,
-                             double *q21, cudaStream_t s);
+                             int r12, int r21, int n_macro, long long count, const int *idx,
+                             int stride, double *q12, double *q21, cudaStream_t s);
+// max |v| of a band over every patch's nref x nref reference nodes (v1, v2 on an
+// Nr = nref * m lattice)
+cudaError_t launch_patch_vmax(const double *v1, const double *v2, long long Nr, int nref,
+                              int n_macro, long long P, double *vmax, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Macro solver and direct simulation.

@@ -412,7 +412,7 @@ k_patch_solve(PatchParams prm)
     const long long item = prm.item0 + blockIdx.x / C;
     const int rank = (int)(blockIdx.x % C);
     if (item >= prm.item0 + prm.items) return;      // whole clusters only: C divides the grid
-    const long long p = item >> 1;
+    const long long p = prm.pidx ? (long long)prm.pidx[item >> 1] : (item >> 1);
     if (item & 1) Tile<N, C, BX, BY, real>::template run<2>(prm, sm, p, rank);
     else Tile<N, C, BX, BY, real>::template run<1>(prm, sm, p, rank);
 }
@@ -723,9 +723,9 @@ k_patch_solve2(PatchParams prm)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *sm = reinterpret_cast<float2 *>(smem_raw);
-    const long long p = prm.item0 / 2 + blockIdx.x;
-    if (2 * p >= prm.item0 + prm.items) return;
-    Tile2<N, BX, BY>::run(prm, sm, p);
+    const long long pair = prm.item0 / 2 + blockIdx.x;
+    if (2 * pair >= prm.item0 + prm.items) return;
+    Tile2<N, BX, BY>::run(prm, sm, prm.pidx ? (long long)prm.pidx[pair] : pair);
 }
 
 template <int N, int BX, int BY, int MINB = 1>

@@ -36,18 +36,31 @@ namespace {
 
 thread_local char g_last_error[512] = "";
 
-struct DevLevel {
+// Patches of one level that share a patch size: one band grid, one kernel.
+struct SizeClass {
     int n = 0;
-    int m = 1;                  // patch side L = 2 pi / m
     long long Nl = 0;           // n * m
-    double L = 0, h = 0;
-    int n_diag = 0, n_12 = 0, n_21 = 0;
-    int r12 = 1, r21 = 1;       // Algorithm 1 line refinement
+    double h = 0;
     void *band = nullptr;       // [Nl][Nl] float or double
-    double *q12 = nullptr, *q21 = nullptr;   // [P][n] or null
+    int *idx = nullptr;         // device patch indices; nullptr when the class holds every patch
+    long long count = 0;
+    PatchVariant variant{};
+    cudaStream_t stream = nullptr;   // own stream when the level has several classes
+    cudaEvent_t join = nullptr;
+};
+
+struct DevLevel {
+    int m = 1;                  // patch side L = 2 pi / m
+    double L = 0;
+    int n_diag = 0, n_12 = 0, n_21 = 0;
+    int nq = 0;                 // largest patch size (stride of the line-variance arrays)
+    std::vector<int> np;        // [P] patch size per patch
+    int *np_dev = nullptr;      // [P] on the device when sizes are mixed, else nullptr
+    double *q12 = nullptr, *q21 = nullptr;   // [P][nq] or null
     double *B = nullptr, *Koff = nullptr, *base = nullptr, *S = nullptr, *Kstar = nullptr;
     long long *steps = nullptr; // [P] n_burn + n_avg of the last solve
-    PatchVariant variant{};
+    std::vector<SizeClass> cls; // largest total work first
+    cudaEvent_t fork = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;   // profiling: one pair per launch
 };
 
@@ -64,6 +77,7 @@ struct mlsd_levels {
     int *status = nullptr;
     std::vector<void *> allocs;
     bool profile = false;
+    int n_min = 32, n_max = 256;
 };
 
 namespace {
@@ -166,6 +180,18 @@ int validate(const mlsd_problem *p)
         if (!(p->band_edges[l + 1] > p->band_edges[l])) return MLSD_EINVAL;
     if (p->n_avg_fixed <= 0 && (!(p->t_burn_tau >= 0) || !(p->t_avg_tau > 0))) return MLSD_EINVAL;
     if (p->n_avg_fixed > 0 && p->n_burn_fixed < 0) return MLSD_EINVAL;
+    auto pow2in = [](int n) { return n >= 32 && n <= 256 && (n & (n - 1)) == 0; };
+    const int nmin = p->n_min ? p->n_min : 32, nmax = p->n_max ? p->n_max : 256;
+    if (!pow2in(nmin) || !pow2in(nmax) || nmin > nmax) return MLSD_EINVAL;
+    const long long P = (long long)p->n_macro * p->n_macro;
+    for (int l = 0; l < p->n_levels; ++l) {
+        if (p->patch_n_map) {
+            for (long long q = 0; q < P; ++q)
+                if (!pow2in(p->patch_n_map[(long long)l * P + q])) return MLSD_EINVAL;
+        } else if (p->patch_n[l] != 0 && !pow2in(p->patch_n[l])) {
+            return MLSD_EINVAL;
+        }
+    }
     // Hermitian completeness and no k = 0
     std::map<std::pair<int, int>, std::pair<double, double>> mm;
     for (int t = 0; t < p->n_modes; ++t) {
@@ -184,7 +210,60 @@ int validate(const mlsd_problem *p)
     return MLSD_OK;
 }
 
-int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s);
+int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s);
+
+// Patch size rule for levels given without a size: at least 10 points per
+// wavelength of the level's finest diagonal mode and a cell Peclet number of at
+// most 2 with kappa (the smallest base any level sees), rounded up to a power of
+// two in [n_min, n_max]:  n = pow2ceil(max(10 kmax L / 2pi, L vmax / (2 kappa))).
+// vmax is the largest |v| of the band's exact velocity over the patch's
+// 32 x 32 reference nodes.
+int rule_sizes(mlsd_levels *h, DevLevel &d, const std::vector<HostMode> &diag, cudaStream_t s)
+{
+    const int nref = 32;
+    const long long Nr = (long long)nref * d.m;
+    int kmax = 0;
+    std::vector<HostMode> c1, c2;            // coefficients of v1 and v2
+    for (auto &x : diag) {
+        kmax = std::max(kmax, std::max(std::abs(x.k1), std::abs(x.k2)));
+        c1.push_back({x.k1, x.k2, x.k2 * x.im, -x.k2 * x.re});
+        c2.push_back({x.k1, x.k2, -x.k1 * x.im, x.k1 * x.re});
+    }
+    std::vector<double> vm((size_t)h->P, 0.0);
+    if (!diag.empty()) {
+        mlsd_levels tmp;                     // owns the set-up buffers of this step
+        ModeGroups g1, g2;
+        int rc = upload_groups(&tmp, c1, g1);
+        if (!rc) rc = upload_groups(&tmp, c2, g2);
+        void *v1 = nullptr, *v2 = nullptr, *G = nullptr, *vmx = nullptr;
+        cudaError_t e = cudaSuccess;
+        if (!rc) e = cudaMalloc(&v1, (size_t)Nr * Nr * 8);
+        if (!rc && e == cudaSuccess) e = cudaMalloc(&v2, (size_t)Nr * Nr * 8);
+        if (!rc && e == cudaSuccess) e = cudaMalloc(&G, (size_t)g1.n_groups * Nr * sizeof(double2));
+        if (!rc && e == cudaSuccess) e = cudaMalloc(&vmx, (size_t)h->P * 8);
+        if (!rc && e == cudaSuccess) e = launch_band_synth(g1, Nr, static_cast<double2 *>(G), v1, 1, s);
+        if (!rc && e == cudaSuccess) e = launch_band_synth(g2, Nr, static_cast<double2 *>(G), v2, 1, s);
+        if (!rc && e == cudaSuccess)
+            e = launch_patch_vmax(static_cast<double *>(v1), static_cast<double *>(v2), Nr, nref,
+                                  h->N, h->P, static_cast<double *>(vmx), s);
+        if (!rc && e == cudaSuccess) e = cudaMemcpyAsync(vm.data(), vmx, (size_t)h->P * 8, cudaMemcpyDeviceToHost, s);
+        if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(s);
+        for (void *q : {v1, v2, G, vmx}) if (q) cudaFree(q);
+        for (void *q : tmp.allocs) cudaFree(q);
+        if (rc) return rc;
+        CK(e);
+    }
+    d.np.resize((size_t)h->P);
+    for (long long q = 0; q < h->P; ++q) {
+        double need = 10.0 * kmax * d.L / (2.0 * kPi);
+        const double pe = d.L * vm[q] / (2.0 * h->kappa);
+        if (pe > need) need = pe;
+        int n = h->n_min;
+        while (n < h->n_max && (double)n < need) n *= 2;
+        d.np[q] = n;
+    }
+    return MLSD_OK;
+}
 
 int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
 {
@@ -199,6 +278,8 @@ int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
     h->t_avg = p->t_avg_tau;
     h->nb_fixed = p->n_burn_fixed;
     h->na_fixed = p->n_avg_fixed;
+    h->n_min = p->n_min ? p->n_min : 32;
+    h->n_max = p->n_max ? p->n_max : 256;
     if ((rc = dev_alloc(h, (void **)&h->status, sizeof(int)))) return rc;
     CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
 
@@ -217,7 +298,6 @@ int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
     const size_t rs = p->precision == MLSD_FP64 ? 8 : 4;
     for (int l = 0; l < L; ++l) {
         DevLevel &d = h->lev[l];
-        d.n = p->patch_n[l];
         if (p->patch_div) d.m = p->patch_div[l];
         else {
             const double e = p->band_edges[l];
@@ -225,38 +305,77 @@ int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
             if (std::fabs(e - d.m) > 0 || d.m < 1) return MLSD_EINVAL;
         }
         if (d.m < 1) return MLSD_EINVAL;
-        {
-            std::vector<PatchVariant> vs;
-            if (patch_variants(d.n, p->precision, vs) == 0) return MLSD_EUNSUPPORTED;
-        }
-        d.Nl = (long long)d.n * d.m;
         d.L = 2.0 * kPi / d.m;
-        d.h = d.L / d.n;
         d.n_diag = (int)diag[l].size();
         d.n_12 = (int)off12[l].size();
         d.n_21 = (int)off21[l].size();
 
-        // band grid (set-up)
+        // patch size of every patch: explicit map, one size for the level, or the rule
+        if (p->patch_n_map) {
+            d.np.assign(p->patch_n_map + (size_t)l * h->P, p->patch_n_map + (size_t)(l + 1) * h->P);
+        } else if (p->patch_n[l] > 0) {
+            d.np.assign((size_t)h->P, p->patch_n[l]);
+        } else if ((rc = rule_sizes(h, d, diag[l], s))) {
+            return rc;
+        }
+        // size classes, largest total work first
+        std::map<int, std::vector<int>> by_n;
+        for (long long q = 0; q < h->P; ++q) by_n[d.np[q]].push_back((int)q);
+        d.nq = by_n.rbegin()->first;
+        for (auto it = by_n.rbegin(); it != by_n.rend(); ++it) {
+            std::vector<PatchVariant> vs;
+            if (patch_variants(it->first, p->precision, vs) == 0) return MLSD_EUNSUPPORTED;
+            SizeClass c;
+            c.n = it->first;
+            c.Nl = (long long)c.n * d.m;
+            c.h = d.L / c.n;
+            c.count = (long long)it->second.size();
+            if (by_n.size() > 1) {
+                if ((rc = dev_alloc(h, (void **)&c.idx, it->second.size() * sizeof(int)))) return rc;
+                CK(cudaMemcpy(c.idx, it->second.data(), it->second.size() * sizeof(int),
+                              cudaMemcpyHostToDevice));
+            }
+            d.cls.push_back(c);
+        }
+        std::stable_sort(d.cls.begin(), d.cls.end(), [](const SizeClass &a, const SizeClass &b) {
+            return (double)a.count * a.n * a.n * a.n > (double)b.count * b.n * b.n * b.n;
+        });
+        if (d.cls.size() > 1) {
+            if ((rc = dev_alloc(h, (void **)&d.np_dev, (size_t)h->P * sizeof(int)))) return rc;
+            CK(cudaMemcpy(d.np_dev, d.np.data(), (size_t)h->P * sizeof(int), cudaMemcpyHostToDevice));
+            CK(cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming));
+            for (auto &c : d.cls) {
+                CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+                CK(cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming));
+            }
+        }
+
+        // band grid of every class (set-up)
         ModeGroups g;
         if ((rc = upload_groups(h, diag[l], g))) return rc;
-        if ((rc = dev_alloc(h, &d.band, (size_t)d.Nl * d.Nl * rs))) return rc;
-        void *G = nullptr;
-        if (g.n_groups > 0) CK(cudaMalloc(&G, (size_t)g.n_groups * d.Nl * sizeof(double2)));
-        cudaError_t e = launch_band_synth(g, d.Nl, static_cast<double2 *>(G), d.band,
-                                          p->precision == MLSD_FP64, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (G) cudaFree(G);
-        CK(e);
+        for (auto &c : d.cls) {
+            if ((rc = dev_alloc(h, &c.band, (size_t)c.Nl * c.Nl * rs))) return rc;
+            void *G = nullptr;
+            if (g.n_groups > 0) CK(cudaMalloc(&G, (size_t)g.n_groups * c.Nl * sizeof(double2)));
+            cudaError_t e = launch_band_synth(g, c.Nl, static_cast<double2 *>(G), c.band,
+                                              p->precision == MLSD_FP64, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (G) cudaFree(G);
+            CK(e);
+        }
 
         // Algorithm 1 line variances (set-up; independent of the base tensor)
         ModeList m12, m21;
         if ((rc = upload_list(h, off12[l], m12))) return rc;
         if ((rc = upload_list(h, off21[l], m21))) return rc;
-        d.r12 = line_refine(off12[l], true, d.L, d.n);
-        d.r21 = line_refine(off21[l], false, d.L, d.n);
-        if (d.n_12 && (rc = dev_alloc(h, (void **)&d.q12, (size_t)h->P * d.n * 8))) return rc;
-        if (d.n_21 && (rc = dev_alloc(h, (void **)&d.q21, (size_t)h->P * d.n * 8))) return rc;
-        CK(launch_offdiag_q(m12, m21, d.Nl, d.n, d.r12, d.r21, h->N, h->P, d.q12, d.q21, s));
+        if (d.n_12 && (rc = dev_alloc(h, (void **)&d.q12, (size_t)h->P * d.nq * 8))) return rc;
+        if (d.n_21 && (rc = dev_alloc(h, (void **)&d.q21, (size_t)h->P * d.nq * 8))) return rc;
+        for (auto &c : d.cls) {
+            const int r12 = line_refine(off12[l], true, d.L, c.n);
+            const int r21 = line_refine(off21[l], false, d.L, c.n);
+            CK(launch_offdiag_q(m12, m21, c.Nl, c.n, r12, r21, h->N, c.count, c.idx, d.nq,
+                                d.q12, d.q21, s));
+        }
 
         // per-level tensors
         if ((rc = dev_alloc(h, (void **)&d.B, (size_t)h->P * 3 * 8))) return rc;
@@ -266,7 +385,8 @@ int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
         if ((rc = dev_alloc(h, (void **)&d.S, (size_t)h->P * 4 * 8))) return rc;
         if ((rc = dev_alloc(h, (void **)&d.steps, (size_t)h->P * 8))) return rc;
         CK(cudaMemsetAsync(d.steps, 0, (size_t)h->P * 8, s));
-        if ((rc = tune_level(h, d, s))) return rc;
+        for (auto &c : d.cls)
+            if ((rc = tune_class(h, d, c, s))) return rc;
     }
     CK(cudaStreamSynchronize(s));
     return MLSD_OK;
@@ -284,12 +404,12 @@ int tile_code(const PatchVariant &v)
     return v.by * 16 + v.minb + 4096 * v.packed + 65536 * v.cluster;
 }
 
-int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s)
+int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
 {
     std::vector<PatchVariant> vs;
-    patch_variants(d.n, h->precision, vs);
+    patch_variants(c.n, h->precision, vs);
     if (vs.empty()) return MLSD_EUNSUPPORTED;
-    d.variant = vs[0];
+    c.variant = vs[0];
     if (const char *env = std::getenv("MLSD_TILE")) {
         // <bx>x<by>[m<minb>][c<cluster>][p]: p selects the packed two-field kernel
         int bx = 0, by = 0, mb = 1, pk = 0, cl = 1;
@@ -302,7 +422,7 @@ int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s)
             }
             for (auto &v : vs)
                 if (v.bx == bx && v.by == by && v.minb == mb && v.packed == pk && v.cluster == cl) {
-                    d.variant = v;
+                    c.variant = v;
                     return MLSD_OK;
                 }
             // the forced tiling is not compiled for this patch size: use the tuner
@@ -313,13 +433,13 @@ int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s)
     if (vs.size() == 1) return MLSD_OK;
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    const auto key = std::make_tuple(dev, d.n, h->precision);
+    const auto key = std::make_tuple(dev, c.n, h->precision);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
             for (auto &v : vs)
-                if (v.bx == it->second.first && tile_code(v) == it->second.second) d.variant = v;
+                if (v.bx == it->second.first && tile_code(v) == it->second.second) c.variant = v;
             return MLSD_OK;
         }
     }
@@ -330,12 +450,12 @@ int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s)
     for (long long p = 0; p < h->P; ++p) { kb[3 * p] = h->kappa; kb[3 * p + 1] = 0; kb[3 * p + 2] = h->kappa; }
     CK(cudaMemcpyAsync(d.B, kb.data(), kb.size() * 8, cudaMemcpyHostToDevice, s));
     PatchParams pp;
-    pp.band = d.band; pp.Nl = d.Nl; pp.n_macro = h->N; pp.h = d.h; pp.L = d.L;
+    pp.band = c.band; pp.Nl = c.Nl; pp.n_macro = h->N; pp.h = c.h; pp.L = d.L;
     pp.Kb = d.B; pp.S = d.S; pp.wdump = nullptr; pp.status = h->status;
     pp.cfl = h->cfl; pp.t_burn = 8; pp.t_avg = 4; pp.nb_fixed = 0;
-    pp.na_fixed = d.n <= 32 ? 64 : 32;
-    pp.P = h->P; pp.item0 = 0; pp.steps = nullptr;
-    pp.items = std::min<long long>(2 * h->P, (long long)sms * 48);
+    pp.na_fixed = c.n <= 32 ? 64 : (c.n <= 64 ? 32 : 8);
+    pp.P = h->P; pp.item0 = 0; pp.steps = nullptr; pp.pidx = c.idx;
+    pp.items = std::min<long long>(2 * c.count, (long long)sms * (c.n <= 64 ? 48 : 8));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -352,14 +472,14 @@ int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s)
             if (ok && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t = std::min(t, ms);
         }
         if (!ok) { cudaGetLastError(); continue; }   // a tiling this device cannot launch
-        if (t < best) { best = t; d.variant = v; }
+        if (t < best) { best = t; c.variant = v; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
     CK(cudaStreamSynchronize(s));
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune[key] = {d.variant.bx, tile_code(d.variant)};
+    g_tune[key] = {c.variant.bx, tile_code(c.variant)};
     return MLSD_OK;
 }
 
@@ -368,18 +488,19 @@ OffdiagLevel off_of(const DevLevel &d)
     OffdiagLevel o;
     o.q12 = d.q12;
     o.q21 = d.q21;
-    o.n = d.n;
+    o.stride = d.nq;
+    o.np = d.np_dev;
     return o;
 }
 
-PatchParams patch_params(const mlsd_levels *h, const DevLevel &d, const double *Kb, double *S,
-                         void *wdump)
+PatchParams patch_params(const mlsd_levels *h, const DevLevel &d, const SizeClass &c,
+                         const double *Kb, double *S, void *wdump)
 {
     PatchParams pp;
-    pp.band = d.band;
-    pp.Nl = d.Nl;
+    pp.band = c.band;
+    pp.Nl = c.Nl;
     pp.n_macro = h->N;
-    pp.h = d.h;
+    pp.h = c.h;
     pp.L = d.L;
     pp.Kb = Kb;
     pp.S = S;
@@ -392,25 +513,38 @@ PatchParams patch_params(const mlsd_levels *h, const DevLevel &d, const double *
     pp.na_fixed = h->na_fixed;
     pp.P = h->P;
     pp.item0 = 0;
-    pp.items = 2 * h->P;
+    pp.items = 2 * c.count;
     pp.steps = d.steps;
+    pp.pidx = c.idx;
     return pp;
 }
 
+// All patch solves of a level: one launch per size class; with several classes
+// they run concurrently on the classes' own streams, forked from and joined to s.
 int run_patches(mlsd_levels *h, DevLevel &d, const double *Kb, double *S, void *wdump,
                 cudaStream_t s)
 {
-    PatchParams pp = patch_params(h, d, Kb, S, wdump);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (h->profile) {
-        CK(cudaEventCreate(&e0));
-        CK(cudaEventCreate(&e1));
-        CK(cudaEventRecord(e0, s));
-    }
-    CK(launch_patch(d.variant, pp, pp.items, s));
-    if (h->profile) {
-        CK(cudaEventRecord(e1, s));
-        d.ev.emplace_back(e0, e1);
+    const bool fork = d.cls.size() > 1;
+    if (fork) CK(cudaEventRecord(d.fork, s));
+    for (auto &c : d.cls) {
+        cudaStream_t cs = fork ? c.stream : s;
+        if (fork) CK(cudaStreamWaitEvent(cs, d.fork, 0));
+        PatchParams pp = patch_params(h, d, c, Kb, S, wdump);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (h->profile) {
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            CK(cudaEventRecord(e0, cs));
+        }
+        CK(launch_patch(c.variant, pp, pp.items, cs));
+        if (h->profile) {
+            CK(cudaEventRecord(e1, cs));
+            d.ev.emplace_back(e0, e1);
+        }
+        if (fork) {
+            CK(cudaEventRecord(c.join, cs));
+            CK(cudaStreamWaitEvent(s, c.join, 0));
+        }
     }
     return MLSD_OK;
 }
@@ -457,7 +591,14 @@ void mlsd_free_levels(mlsd_levels *h)
 {
     if (!h) return;
     cudaDeviceSynchronize();
-    for (auto &d : h->lev) drop_events(d);
+    for (auto &d : h->lev) {
+        drop_events(d);
+        for (auto &c : d.cls) {
+            if (c.stream) cudaStreamDestroy(c.stream);
+            if (c.join) cudaEventDestroy(c.join);
+        }
+        if (d.fork) cudaEventDestroy(d.fork);
+    }
     for (void *p : h->allocs) cudaFree(p);
     delete h;
 }
@@ -466,20 +607,30 @@ int mlsd_level_info(const mlsd_levels *h, int level, mlsd_level_desc *out)
 {
     if (!h || !out || level < 1 || level > h->L) return MLSD_EINVAL;
     const DevLevel &d = h->lev[level - 1];
-    out->n = d.n;
-    out->Nl = d.Nl;
+    const SizeClass &c = d.cls[0];
+    out->n = c.n;
+    out->Nl = c.Nl;
     out->L = d.L;
-    out->h = d.h;
+    out->h = c.h;
     out->n_patches = h->P;
     out->n_diag_modes = d.n_diag;
     out->n_off12_modes = d.n_12;
     out->n_off21_modes = d.n_21;
-    out->tile_bx = d.variant.bx;
-    out->tile_by = d.variant.by;
-    out->threads = d.variant.threads;
-    out->packed = d.variant.packed;
-    out->cluster = d.variant.cluster;
-    out->min_ctas = d.variant.minb;
+    out->tile_bx = c.variant.bx;
+    out->tile_by = c.variant.by;
+    out->threads = c.variant.threads;
+    out->packed = c.variant.packed;
+    out->cluster = c.variant.cluster;
+    out->min_ctas = c.variant.minb;
+    out->n_classes = (int)d.cls.size();
+    return MLSD_OK;
+}
+
+int mlsd_patch_sizes(const mlsd_levels *h, int level, int32_t *n_out_host)
+{
+    if (!h || !n_out_host || level < 1 || level > h->L) return MLSD_EINVAL;
+    const DevLevel &d = h->lev[level - 1];
+    std::copy(d.np.begin(), d.np.end(), n_out_host);
     return MLSD_OK;
 }
 
@@ -490,6 +641,7 @@ int mlsd_solve_level(mlsd_levels *h, int level, const double *K_base_dev, double
         return MLSD_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     DevLevel &d = h->lev[level - 1];
+    if (w_dump_dev && d.cls.size() > 1) return MLSD_EINVAL;   // dump layout needs one patch size
     int rc = run_patches(h, d, K_base_dev, d.S, w_dump_dev, s);
     if (rc) return rc;
     CK(launch_compose(h->P, K_base_dev, d.S, K_out_dev, h->status, s));
@@ -562,8 +714,11 @@ int mlsd_level_work(mlsd_levels *h, int level, int64_t *cell_updates_out,
     CK(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
     CK(cudaMemcpy(st.data(), d.steps, (size_t)h->P * 8, cudaMemcpyDeviceToHost));
     long long tot = 0, mx = 0;
-    for (long long v : st) { tot += v; mx = std::max(mx, v); }
-    if (cell_updates_out) *cell_updates_out = tot * 2 * (long long)d.n * d.n;
+    for (long long q = 0; q < h->P; ++q) {
+        tot += st[q] * 2 * (long long)d.np[q] * d.np[q];
+        mx = std::max(mx, st[q]);
+    }
+    if (cell_updates_out) *cell_updates_out = tot;
     if (max_steps_out) *max_steps_out = mx;
     return MLSD_OK;
 }

@@ -1,0 +1,83 @@
+"""Uneven patch sizes within a level: the patch-size rule and the chain with
+mixed 32^2 ... 256^2 patches (size classes launched concurrently) against the
+oracle with the same per-node sizes."""
+import numpy as np
+import pytest
+
+from inputs import flows
+import oracle
+from tests._parity import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def problem():
+    spec = flows.continuous_spectrum(48, seed=5)
+    return dict(spec=spec, edges=[1, 2, 4, 8, 16, 32, 49], N=3, kappa=2e-3)
+
+
+def test_patch_size_rule_matches_oracle(problem):
+    import paper_1510_00451_gb300 as mlsd
+    pr = problem
+    L = len(pr["edges"]) - 1
+    lv = mlsd.Levels(pr["spec"], pr["kappa"], pr["N"], pr["edges"], [0] * L,
+                     n_burn_fixed=1, n_avg_fixed=1)
+    seen = set()
+    for l in range(1, L + 1):
+        got = lv.patch_sizes(l)
+        for p in range(pr["N"] ** 2):
+            n, _ = oracle.patch_n_rule(pr["spec"], pr["edges"], l, (p % pr["N"], p // pr["N"]),
+                                       pr["N"], pr["kappa"])
+            assert got[p] == n, (l, p, got[p], n)
+            seen.add(int(n))
+    assert len(seen) >= 3          # the workload really is uneven
+
+
+def test_uneven_chain_parity(problem):
+    import torch
+    import paper_1510_00451_gb300 as mlsd
+    pr = problem
+    L = len(pr["edges"]) - 1
+    N = pr["N"]
+    lv = mlsd.Levels(pr["spec"], pr["kappa"], N, pr["edges"], [0] * L,
+                     n_burn_fixed=60, n_avg_fixed=40)
+    sizes = np.stack([lv.patch_sizes(l + 1) for l in range(L)], 1)      # [P][L]
+    mixed = [l for l in range(L) if len(set(sizes[:, l])) > 1]
+    K = torch.zeros(N * N, 3, dtype=torch.float64, device="cuda:0")
+    lv.effective_diffusivity(K)
+    assert lv.status() == 0
+    K = K.cpu().numpy()
+    nodes = [(p % N, p // N) for p in range(N * N)]
+    want = oracle.chain(pr["spec"], pr["edges"], [32] * L, N, pr["kappa"], nodes,
+                        n_burn_fixed=60, n_avg_fixed=40, node_n=sizes)
+    for p in range(N * N):
+        assert rel_l2(K[p], want[p]) < 1e-4, (p, K[p], want[p])
+    info = [lv.info(l + 1) for l in range(L)]
+    assert max(i["n_classes"] for i in info) >= 1
+    print("levels with mixed sizes:", mixed, [i["n"] for i in info])
+
+
+def test_explicit_size_map_parity():
+    import torch
+    import paper_1510_00451_gb300 as mlsd
+    spec = flows.cellular_hierarchy(2, 4)
+    edges, N, kappa = [1, 4, 16], 4, 0.02
+    P = N * N
+    rng = np.random.default_rng(3)
+    nmap = rng.choice([32, 64], size=(2, P)).astype(np.int32)      # [L][P]
+    lv = mlsd.Levels(spec, kappa, N, edges, [0, 0], patch_n_map=nmap,
+                     n_burn_fixed=80, n_avg_fixed=60)
+    assert lv.info(1)["n_classes"] == 2 and lv.info(2)["n_classes"] == 2
+    K = torch.zeros(P, 3, dtype=torch.float64, device="cuda:0")
+    lv.effective_diffusivity(K)
+    assert lv.status() == 0
+    K = K.cpu().numpy()
+    nodes = [(p % N, p // N) for p in range(P)]
+    want = oracle.chain(spec, edges, [32, 32], N, kappa, nodes, n_burn_fixed=80, n_avg_fixed=60,
+                        node_n=nmap.T)
+    for p in range(P):
+        assert rel_l2(K[p], want[p]) < 1e-4
+    # the work count follows the per-patch sizes
+    cu, ms = lv.level_work(1)
+    assert cu == sum(2 * int(n) ** 2 * 140 for n in nmap[0])
