@@ -62,6 +62,9 @@ def _declare(L):
     L.orc_grid_psi.argtypes = [_i, _p, _p, _p, _p, _i, _p]
     L.orc_coarse_grain.argtypes = [_i, _p, _i, _p, _p]
     L.orc_num_threads.restype = _i
+    L.orc_features.argtypes = [_i, _p, _p, _d, _p]
+    L.orc_mlp.argtypes = [_i, _i, _i, _p, _p, _i, _p, _p, _p]
+    L.orc_mlp.restype = _d
 
 
 def _ptr(a):
@@ -270,3 +273,32 @@ def coarse_grain(u, N):
     U = np.zeros((N, N)); m = ctypes.c_double()
     lib().orc_coarse_grain(u.shape[0], _ptr(u), int(N), _ptr(U), ctypes.byref(m))
     return U, m.value
+
+
+N_FEATURES = 582
+
+
+def features(psi, B, kappa):
+    """582 surrogate inputs of one patch (psi with its patch mean removed)."""
+    psi = _f64(psi); B = _f64(B)
+    f = np.zeros(N_FEATURES)
+    lib().orc_features(psi.shape[0], _ptr(psi), _ptr(B), float(kappa), _ptr(f))
+    return f
+
+
+def mlp_param_count(d0, h):
+    return h * d0 + h + 2 * (h * h + h) + 3 * h + 3
+
+
+def mlp(X, params, h, bf16=True, Y=None, want_grad=False):
+    """FP64 forward (and loss / gradient) of one surrogate member."""
+    X = _f64(X); params = _f64(params)
+    M, d0 = X.shape
+    assert params.size == mlp_param_count(d0, h)
+    out = np.zeros((M, 3))
+    Yc = None if Y is None else _f64(Y)
+    g = np.zeros_like(params) if want_grad else None
+    loss = lib().orc_mlp(M, d0, h, _ptr(X), _ptr(params), 1 if bf16 else 0, _ptr(Yc), _ptr(out), _ptr(g))
+    if Y is None:
+        return out
+    return (out, loss, g) if want_grad else (out, loss)

@@ -660,3 +660,131 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned surrogate of the patch solve (not in the paper; the library's     */
+/* estimator it is checked against is orc_patch_k).                          */
+/*                                                                           */
+/* Features of a patch (582 values):                                         */
+/*   [0, 578): Re and Im of psihat(k) = n^-2 sum_ab psi[b][a]               */
+/*             exp(-2 pi i (k1 a + k2 b) / n) for k2 = -8..8 (slow),         */
+/*             k1 = -8..8 (fast), each divided by tr(B)/2 (a Peclet scale);  */
+/*             psi is the patch's band with the patch mean removed           */
+/*   578..580: B11/kappa, B12/kappa, B22/kappa;  581: log(kappa)             */
+/* Target: (K - B) / tr(B) for the three components (K11, K12, K22).         */
+/* ------------------------------------------------------------------------ */
+#define ORC_NF 582
+void orc_features(int n, const double *psi, const double *B, double kappa, double *f)
+{
+    double scale = 0.5 * (B[0] + B[2]);
+    int t = 0;
+    for (int k2 = -8; k2 <= 8; ++k2)
+        for (int k1 = -8; k1 <= 8; ++k1) {
+            double sr = 0.0, si = 0.0;
+            for (int b = 0; b < n; ++b)
+                for (int a = 0; a < n; ++a) {
+                    long r = pmod((long)k1 * a + (long)k2 * b, n);
+                    double th = -2.0 * ORC_PI * (double)r / (double)n;
+                    sr += psi[(long)b * n + a] * cos(th);
+                    si += psi[(long)b * n + a] * sin(th);
+                }
+            f[t++] = sr / ((double)n * n) / scale;
+            f[t++] = si / ((double)n * n) / scale;
+        }
+    f[t++] = B[0] / kappa;
+    f[t++] = B[1] / kappa;
+    f[t++] = B[2] / kappa;
+    f[t++] = log(kappa);
+}
+
+/* round to bfloat16 (via float, round to nearest even); NaN-free inputs */
+static double bf16r(double x)
+{
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    u &= 0xFFFF0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+static double gelu(double z) { return 0.5 * z * (1.0 + erf(z / sqrt(2.0))); }
+static double gelu_d(double z)
+{
+    return 0.5 * (1.0 + erf(z / sqrt(2.0))) + z * exp(-0.5 * z * z) / sqrt(2.0 * ORC_PI);
+}
+
+/* One member of the surrogate: 4 dense layers d0 -> h -> h -> h -> 3 with the */
+/* exact-erf GELU after the first three.  Parameters (row-major, out x in):    */
+/*   W1[h][d0] b1[h] W2[h][h] b2[h] W3[h][h] b3[h] W4[3][h] b4[3]              */
+/* in one array.  With bf16 != 0 the inputs, weights and hidden activations    */
+/* are rounded to bfloat16 where the GPU stores them in bfloat16.              */
+/* Forward: out[M][3].  With Y != NULL also the loss mean((out - Y)^2) over    */
+/* the M x 3 entries and its gradient g (same layout as the parameters).       */
+double orc_mlp(int M, int d0, int h, const double *X, const double *params, int bf16,
+               const double *Y, double *out, double *g)
+{
+    const int dims[5] = {d0, h, h, h, 3};
+    long off[9];
+    long o = 0;
+    for (int l = 0; l < 4; ++l) { off[2 * l] = o; o += (long)dims[l + 1] * dims[l]; off[2 * l + 1] = o; o += dims[l + 1]; }
+    long np = o;
+    double *Wq = malloc(sizeof(double) * np);
+    for (long q = 0; q < np; ++q) Wq[q] = params[q];
+    for (int l = 0; l < 4; ++l)           /* weights in bf16; biases stay FP32 */
+        if (bf16) for (long q = off[2 * l]; q < off[2 * l + 1]; ++q) Wq[q] = bf16r(Wq[q]);
+    double *A[5], *Z[5];
+    for (int l = 0; l <= 4; ++l) { A[l] = malloc(sizeof(double) * M * dims[l]); Z[l] = malloc(sizeof(double) * M * dims[l]); }
+    for (long q = 0; q < (long)M * d0; ++q) A[0][q] = bf16 ? bf16r(X[q]) : X[q];
+    for (int l = 0; l < 4; ++l) {
+        const double *W = Wq + off[2 * l], *bb = Wq + off[2 * l + 1];
+        for (int m = 0; m < M; ++m)
+            for (int j = 0; j < dims[l + 1]; ++j) {
+                double s = bb[j];
+                for (int k = 0; k < dims[l]; ++k) s += A[l][(long)m * dims[l] + k] * W[(long)j * dims[l] + k];
+                Z[l + 1][(long)m * dims[l + 1] + j] = s;
+                double a = (l < 3) ? gelu(s) : s;
+                A[l + 1][(long)m * dims[l + 1] + j] = (l < 3 && bf16) ? bf16r(a) : a;
+            }
+    }
+    for (long q = 0; q < (long)M * 3; ++q) out[q] = A[4][q];
+    double loss = 0.0;
+    if (Y) {
+        for (long q = 0; q < (long)M * 3; ++q) loss += (A[4][q] - Y[q]) * (A[4][q] - Y[q]);
+        loss /= (double)M * 3.0;
+        if (g) {
+            /* backward: dZ4 = 2 (out - Y) / (3M); dW = dZ^T A; dA = dZ W; dZ = dA gelu'(Z) */
+            double *dZ = malloc(sizeof(double) * M * h), *dA = malloc(sizeof(double) * M * h);
+            double *dZn = malloc(sizeof(double) * M * h);
+            for (long q = 0; q < (long)M * 3; ++q) dZ[q] = 2.0 * (A[4][q] - Y[q]) / ((double)M * 3.0);
+            for (int l = 3; l >= 0; --l) {
+                int din = dims[l], dout = dims[l + 1];
+                double *gW = g + off[2 * l], *gb = g + off[2 * l + 1];
+                const double *W = Wq + off[2 * l];
+                for (int j = 0; j < dout; ++j) {
+                    double sb = 0.0;
+                    for (int m = 0; m < M; ++m) sb += dZ[(long)m * dout + j];
+                    gb[j] = sb;
+                    for (int k = 0; k < din; ++k) {
+                        double s = 0.0;
+                        for (int m = 0; m < M; ++m) s += dZ[(long)m * dout + j] * A[l][(long)m * din + k];
+                        gW[(long)j * din + k] = s;
+                    }
+                }
+                if (l == 0) break;
+                for (int m = 0; m < M; ++m)
+                    for (int k = 0; k < din; ++k) {
+                        double s = 0.0;
+                        for (int j = 0; j < dout; ++j) s += dZ[(long)m * dout + j] * W[(long)j * din + k];
+                        dZn[(long)m * din + k] = s * gelu_d(Z[l][(long)m * din + k]);
+                    }
+                double *t = dZ; dZ = dZn; dZn = t;
+            }
+            free(dZ); free(dA); free(dZn);
+        }
+    }
+    for (int l = 0; l <= 4; ++l) { free(A[l]); free(Z[l]); }
+    free(Wq);
+    return loss;
+}
