@@ -175,6 +175,59 @@ int mlsd_offdiag(mlsd_levels *h, int level, const double *B_dev, double *Koff_de
 int mlsd_effective_diffusivity(mlsd_levels *h, int mode, double *K_macro_dev,
                                double *K_levels_dev, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate of the patch solve (not in the paper).  A small ensemble
+ * of MLPs maps a patch's features to (K - B) / tr(B); where the members
+ * disagree, the plain patch solve above is run instead.
+ *
+ * Features of a patch (MLSD_SUR_FEATURES = 582 values, stored as one bfloat16
+ * row of MLSD_SUR_IN = 640, zero padded): Re and Im of the patch DFT
+ *   psihat(k) = n^-2 sum_ab (psi[b][a] - mean psi) exp(-2 pi i (k1 a + k2 b)/n)
+ * of the level's band at the patch nodes, k2 = -8..8 (slow), k1 = -8..8, each
+ * divided by tr(B)/2; then B11/kappa, B12/kappa, B22/kappa, log kappa.
+ * Member network: 640 -> h -> h -> h -> 3, exact-erf GELU after the first three
+ * layers, bfloat16 weights and activations, FP32 accumulation.  Parameters of
+ * a member in one FP32 array, row-major (out x in):
+ *   W1[h][640] b1[h] W2[h][h] b2[h] W3[h][h] b3[h] W4[3][h] b4[3].         */
+#define MLSD_SUR_IN 640
+#define MLSD_SUR_FEATURES 582
+typedef struct mlsd_surrogate mlsd_surrogate;
+
+int64_t mlsd_surrogate_param_count(int hidden);          /* per member */
+/* members >= 1, hidden a multiple of 32 (<= 512), max_batch rows per call of
+ * the training kernels (prediction is chunked by it).  Weights start at 0.  */
+int mlsd_surrogate_create(int members, int hidden, int max_batch, mlsd_surrogate **out);
+void mlsd_surrogate_free(mlsd_surrogate *s);
+/* host FP32 parameter arrays (layout above); set resets the Adam state      */
+int mlsd_surrogate_set_params(mlsd_surrogate *s, int member, const float *params_host);
+int mlsd_surrogate_get_params(mlsd_surrogate *s, int member, float *params_host);
+/* Features of every patch of a level (one patch size <= 64 per level) with
+ * base B_dev [P][3]: X_dev bfloat16 [P][640]; F32_dev [P][582] or NULL.     */
+int mlsd_surrogate_features(mlsd_levels *h, int level, const double *B_dev, void *X_dev,
+                            float *F32_dev, void *cuda_stream);
+/* Mean-squared-error loss of one member on M <= max_batch rows (X bfloat16
+ * [M][640], Y [M][3]) and its gradient grad_dev (FP32, parameter layout; NULL
+ * to skip).  Blocks for the loss.                                          */
+int mlsd_surrogate_grad(mlsd_surrogate *s, int member, const void *X_dev, const float *Y_dev,
+                        int M, float *grad_dev, double *loss_host, void *cuda_stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) of one member on
+ * a batch; loss_host (or NULL) receives the batch loss before the step.     */
+int mlsd_surrogate_train_step(mlsd_surrogate *s, int member, const void *X_dev,
+                              const float *Y_dev, int M, float lr, double *loss_host,
+                              void *cuda_stream);
+/* Every member on M rows: out_dev FP32 [members][M][3].                     */
+int mlsd_surrogate_predict(mlsd_surrogate *s, const void *X_dev, int64_t M, float *out_dev,
+                           void *cuda_stream);
+/* One level with the surrogate: features, ensemble, K_m = B + tr(B) out_m;
+ * a patch whose members disagree,
+ *     max_{m,c} |K_m,c - mean_m K_m,c| > threshold * ||mean K||_F,
+ * is solved by the plain patch solve (mlsd_solve_level's kernel) instead; the
+ * rest take the ensemble mean.  n_fallback_out receives the number of plain
+ * solves.  Blocks once (to size the fallback launch).                       */
+int mlsd_solve_level_surrogate(mlsd_levels *h, mlsd_surrogate *s, int level,
+                               const double *K_base_dev, double *K_out_dev, double threshold,
+                               int64_t *n_fallback_out, void *cuda_stream);
+
 /* Synchronise the handle's stream and return the first error latched on the
  * device since the last call (MLSD_ENONFINITE ...), then clear it.          */
 int mlsd_status(mlsd_levels *h, void *cuda_stream);

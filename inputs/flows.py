@@ -186,3 +186,26 @@ def config_problem(name):
                     edges=[1.0, 2.0, 4.0, 8.0, 16.0, 32.0, 64.0, 128.0, 257.0],
                     patch_n=None, precision="fp32", cfl=0.2, T=1.0, sigma=0.5)
     raise KeyError(name)
+
+
+def mlp_init(d0, hidden, seed):
+    """Seeded initial parameters of one surrogate member (FP32, layout
+    W1[h][d0] b1 W2[h][h] b2 W3[h][h] b3 W4[3][h] b4): weights uniform in
+    +-1/sqrt(fan_in), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for din, dout in [(d0, hidden), (hidden, hidden), (hidden, hidden), (hidden, 3)]:
+        a = 1.0 / math.sqrt(din)
+        parts.append(rng.uniform(-a, a, dout * din))
+        parts.append(np.zeros(dout))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def random_bases(P, kappa, seed, spread=1.5, cross=0.3):
+    """Seeded symmetric positive definite base tensors around kappa:
+    B11 = kappa e^a, B22 = kappa e^b (a, b uniform in [0, spread]),
+    B12 = c sqrt(B11 B22) with c uniform in [-cross, cross]."""
+    rng = np.random.default_rng(seed)
+    a = kappa * np.exp(rng.uniform(0, spread, (P, 2)))
+    c = rng.uniform(-cross, cross, P) * np.sqrt(a[:, 0] * a[:, 1])
+    return np.stack([a[:, 0], c, a[:, 1]], 1)

@@ -26,7 +26,12 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_offdiag", "mlsd_effective_diffusivity", "mlsd_status", "mlsd_macro_step",
             "mlsd_macro_dt", "mlsd_grid_psi", "mlsd_dns_run", "mlsd_coarse_grain",
             "mlsd_level_work", "mlsd_launch_count", "mlsd_profile", "mlsd_profile_collect",
-            "mlsd_coarse_grain_noalloc", "mlsd_dns_dt", "mlsd_patch_sizes", "mlsd_strerror"]
+            "mlsd_coarse_grain_noalloc", "mlsd_dns_dt", "mlsd_patch_sizes",
+            "mlsd_surrogate_param_count", "mlsd_surrogate_create", "mlsd_surrogate_free",
+            "mlsd_surrogate_set_params", "mlsd_surrogate_get_params", "mlsd_surrogate_features",
+            "mlsd_surrogate_grad", "mlsd_surrogate_train_step", "mlsd_surrogate_predict",
+            "mlsd_solve_level_surrogate", "mlsd_strerror"]
+SUR_IN, SUR_FEATURES = 640, 582
 NOALLOC_MAX_MACRO = 256
 
 
@@ -80,6 +85,18 @@ _lib.mlsd_launch_count.restype = _L
 _lib.mlsd_patch_sizes.argtypes = [_P, _I, _P]
 _lib.mlsd_dns_dt.argtypes = [_I, _P, _D, _D, ctypes.POINTER(_D), _P]
 _lib.mlsd_coarse_grain_noalloc.argtypes = [_I, _P, _I, _P, _P, _P]
+_lib.mlsd_surrogate_param_count.argtypes = [_I]
+_lib.mlsd_surrogate_param_count.restype = _L
+_lib.mlsd_surrogate_create.argtypes = [_I, _I, _I, ctypes.POINTER(_P)]
+_lib.mlsd_surrogate_free.argtypes = [_P]
+_lib.mlsd_surrogate_free.restype = None
+_lib.mlsd_surrogate_set_params.argtypes = [_P, _I, _P]
+_lib.mlsd_surrogate_get_params.argtypes = [_P, _I, _P]
+_lib.mlsd_surrogate_features.argtypes = [_P, _I, _P, _P, _P, _P]
+_lib.mlsd_surrogate_grad.argtypes = [_P, _I, _P, _P, _I, _P, ctypes.POINTER(_D), _P]
+_lib.mlsd_surrogate_train_step.argtypes = [_P, _I, _P, _P, _I, ctypes.c_float, ctypes.POINTER(_D), _P]
+_lib.mlsd_surrogate_predict.argtypes = [_P, _P, _L, _P, _P]
+_lib.mlsd_solve_level_surrogate.argtypes = [_P, _P, _I, _P, _P, _D, ctypes.POINTER(_L), _P]
 _lib.mlsd_strerror.argtypes = [_I]
 _lib.mlsd_strerror.restype = ctypes.c_char_p
 
@@ -161,6 +178,19 @@ class Levels:
         out = np.zeros(self.P, dtype=np.int32)
         _check(_lib.mlsd_patch_sizes(self.h, int(level), out.ctypes.data), "mlsd_patch_sizes")
         return out
+
+    def features(self, level, B, X, F32=None, stream=None):
+        """Surrogate inputs of every patch: X bfloat16 [P][640], F32 [P][582] or None."""
+        _check(_lib.mlsd_surrogate_features(self.h, int(level), _dptr(B), _dptr(X), _dptr(F32),
+                                            _stream(stream)), "mlsd_surrogate_features")
+
+    def solve_level_surrogate(self, sur, level, K_base, K_out, threshold, stream=None):
+        """Surrogate level solve; returns the number of plain fallback solves."""
+        n = _L()
+        _check(_lib.mlsd_solve_level_surrogate(self.h, sur.s, int(level), _dptr(K_base),
+                                               _dptr(K_out), float(threshold), ctypes.byref(n),
+                                               _stream(stream)), "mlsd_solve_level_surrogate")
+        return n.value
 
     def solve_level(self, level, K_base, K_out, w_dump=None, stream=None):
         _check(_lib.mlsd_solve_level(self.h, int(level), _dptr(K_base), _dptr(K_out),
@@ -253,3 +283,56 @@ def coarse_grain_noalloc(u, n_macro, U_out, want_mass=True, stream=None):
                                           ctypes.byref(m) if want_mass else None, _stream(stream)),
            "mlsd_coarse_grain_noalloc")
     return m.value if want_mass else None
+
+
+class Surrogate:
+    """Ensemble MLP surrogate handle (mlsd_surrogate_*)."""
+
+    def __init__(self, members=4, hidden=256, max_batch=4096):
+        h = _P()
+        _check(_lib.mlsd_surrogate_create(int(members), int(hidden), int(max_batch),
+                                          ctypes.byref(h)), "mlsd_surrogate_create")
+        self.s = h
+        self.members, self.hidden, self.max_batch = members, hidden, max_batch
+        self.n_params = int(_lib.mlsd_surrogate_param_count(int(hidden)))
+
+    def close(self):
+        if getattr(self, "s", None):
+            _lib.mlsd_surrogate_free(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, member, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.n_params
+        _check(_lib.mlsd_surrogate_set_params(self.s, int(member), p.ctypes.data),
+               "mlsd_surrogate_set_params")
+
+    def get_params(self, member):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _check(_lib.mlsd_surrogate_get_params(self.s, int(member), p.ctypes.data),
+               "mlsd_surrogate_get_params")
+        return p
+
+    def grad(self, member, X, Y, grad_out=None, stream=None):
+        loss = _D()
+        _check(_lib.mlsd_surrogate_grad(self.s, int(member), _dptr(X), _dptr(Y), X.shape[0],
+                                        _dptr(grad_out), ctypes.byref(loss), _stream(stream)),
+               "mlsd_surrogate_grad")
+        return loss.value
+
+    def train_step(self, member, X, Y, lr, want_loss=False, stream=None):
+        loss = _D()
+        _check(_lib.mlsd_surrogate_train_step(self.s, int(member), _dptr(X), _dptr(Y), X.shape[0],
+                                              float(lr), ctypes.byref(loss) if want_loss else None,
+                                              _stream(stream)), "mlsd_surrogate_train_step")
+        return loss.value if want_loss else None
+
+    def predict(self, X, out, stream=None):
+        _check(_lib.mlsd_surrogate_predict(self.s, _dptr(X), X.shape[0], _dptr(out),
+                                           _stream(stream)), "mlsd_surrogate_predict")

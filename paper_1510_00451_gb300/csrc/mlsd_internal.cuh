@@ -119,6 +119,24 @@ cudaError_t coarse_grain(int nf, const float *u, int N, float *U, double *mass_d
 void count_launches(long long n);
 long long launch_count();
 
+// Surrogate (surrogate.cu)
+long long sur_param_count(int h);
+cudaError_t launch_features(const float *band, long long Nl, int n, int n_macro, const int *pidx,
+                            long long count, const double *B, double kappa, void *X, float *F32,
+                            cudaStream_t s);
+cudaError_t sur_forward(int h, int M, const void *X, const float *wf, const void *wb,
+                        float *Z[4], void *Aact[3], cudaStream_t s);
+cudaError_t sur_grad(int h, int M, const void *X, const float *Y, const float *wf, const void *wb,
+                     float *Z[4], void *Aact[3], float *dA, float *dB, float *g, double *part,
+                     double *loss_dev, cudaStream_t s);
+cudaError_t sur_adam(long long n, float *w, const float *g, float *m, float *v, float lr, int t,
+                     void *wb, cudaStream_t s);
+cudaError_t sur_to_bf16(long long n, const float *w, void *wb, cudaStream_t s);
+cudaError_t sur_disagree(long long P, int members, const float *out, const double *B, double thr,
+                         double *K, int *flag, int *idx, int *count, cudaStream_t s);
+cudaError_t sur_merge(int n, const int *idx, const double *B, const double *S, double *K,
+                      cudaStream_t s);
+
 // Shared small device helpers ------------------------------------------------
 __host__ __device__ inline long long pmod_ll(long long a, long long m)
 {

@@ -863,4 +863,207 @@ int mlsd_coarse_grain(int nf, const float *u_dev, int n_macro, float *U_dev,
     return MLSD_OK;
 }
 
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Surrogate handle
+struct mlsd_surrogate {
+    int members = 0, h = 0, max_batch = 0;
+    long long np = 0;
+    std::vector<float *> w, g, m, v;      // FP32 master, gradient, Adam moments
+    std::vector<void *> wb;               // bfloat16 copies
+    std::vector<int> t;                   // Adam step per member
+    float *Z[4] = {};
+    void *A[3] = {};
+    float *dA = nullptr, *dB = nullptr;
+    double *part = nullptr, *loss = nullptr;
+    std::vector<void *> allocs;
+};
+
+namespace {
+int sur_alloc(mlsd_surrogate *s, void **p, size_t bytes)
+{
+    *p = nullptr;
+    CK(cudaMalloc(p, bytes));
+    s->allocs.push_back(*p);
+    return MLSD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int64_t mlsd_surrogate_param_count(int hidden) { return sur_param_count(hidden); }
+
+void mlsd_surrogate_free(mlsd_surrogate *s)
+{
+    if (!s) return;
+    cudaDeviceSynchronize();
+    for (void *p : s->allocs) cudaFree(p);
+    delete s;
+}
+
+int mlsd_surrogate_create(int members, int hidden, int max_batch, mlsd_surrogate **out)
+{
+    if (!out || members < 1 || members > 16 || hidden < 32 || hidden > 512 || hidden % 32 ||
+        max_batch < 1)
+        return MLSD_EINVAL;
+    *out = nullptr;
+    mlsd_surrogate *s = new (std::nothrow) mlsd_surrogate();
+    if (!s) return MLSD_ENOMEM;
+    s->members = members;
+    s->h = hidden;
+    s->max_batch = max_batch;
+    s->np = sur_param_count(hidden);
+    int rc = MLSD_OK;
+    const size_t np = (size_t)s->np, M = (size_t)max_batch, H = (size_t)hidden;
+    for (int k = 0; k < members && !rc; ++k) {
+        void *p[5];
+        for (int q = 0; q < 4 && !rc; ++q) rc = sur_alloc(s, &p[q], np * 4);
+        if (!rc) rc = sur_alloc(s, &p[4], np * 2);
+        if (rc) break;
+        s->w.push_back((float *)p[0]); s->g.push_back((float *)p[1]);
+        s->m.push_back((float *)p[2]); s->v.push_back((float *)p[3]);
+        s->wb.push_back(p[4]);
+        s->t.push_back(0);
+        for (int q = 0; q < 5; ++q) if (cudaMemset(p[q], 0, q < 4 ? np * 4 : np * 2)) rc = MLSD_ECUDA;
+    }
+    for (int l = 0; l < 4 && !rc; ++l) rc = sur_alloc(s, (void **)&s->Z[l], M * (l < 3 ? H : 3) * 4);
+    for (int l = 0; l < 3 && !rc; ++l) rc = sur_alloc(s, &s->A[l], M * H * 2);
+    if (!rc) rc = sur_alloc(s, (void **)&s->dA, M * H * 4);
+    if (!rc) rc = sur_alloc(s, (void **)&s->dB, M * H * 4);
+    if (!rc) rc = sur_alloc(s, (void **)&s->part, ((3 * M + 255) / 256 + 1) * 8);
+    if (!rc) rc = sur_alloc(s, (void **)&s->loss, 8);
+    if (rc) { mlsd_surrogate_free(s); return rc; }
+    *out = s;
+    return MLSD_OK;
+}
+
+int mlsd_surrogate_set_params(mlsd_surrogate *s, int member, const float *params_host)
+{
+    if (!s || member < 0 || member >= s->members || !params_host) return MLSD_EINVAL;
+    const size_t np = (size_t)s->np;
+    CK(cudaMemcpy(s->w[member], params_host, np * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemset(s->m[member], 0, np * 4));
+    CK(cudaMemset(s->v[member], 0, np * 4));
+    s->t[member] = 0;
+    CK(sur_to_bf16(s->np, s->w[member], s->wb[member], nullptr));
+    CK(cudaDeviceSynchronize());
+    return MLSD_OK;
+}
+
+int mlsd_surrogate_get_params(mlsd_surrogate *s, int member, float *params_host)
+{
+    if (!s || member < 0 || member >= s->members || !params_host) return MLSD_EINVAL;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(params_host, s->w[member], (size_t)s->np * 4, cudaMemcpyDeviceToHost));
+    return MLSD_OK;
+}
+
+int mlsd_surrogate_features(mlsd_levels *h, int level, const double *B_dev, void *X_dev,
+                            float *F32_dev, void *cuda_stream)
+{
+    if (!h || level < 1 || level > h->L || !B_dev || !X_dev) return MLSD_EINVAL;
+    DevLevel &d = h->lev[level - 1];
+    if (d.cls.size() != 1 || d.cls[0].n > 64 || h->precision != MLSD_FP32) return MLSD_EUNSUPPORTED;
+    const SizeClass &c = d.cls[0];
+    CK(launch_features(static_cast<const float *>(c.band), c.Nl, c.n, h->N, nullptr, h->P, B_dev,
+                       h->kappa, X_dev, F32_dev, static_cast<cudaStream_t>(cuda_stream)));
+    return MLSD_OK;
+}
+
+int mlsd_surrogate_grad(mlsd_surrogate *s, int member, const void *X_dev, const float *Y_dev,
+                        int M, float *grad_dev, double *loss_host, void *cuda_stream)
+{
+    if (!s || member < 0 || member >= s->members || !X_dev || !Y_dev || M < 1 || M > s->max_batch)
+        return MLSD_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    CK(sur_grad(s->h, M, X_dev, Y_dev, s->w[member], s->wb[member], s->Z, s->A, s->dA, s->dB,
+                s->g[member], s->part, s->loss, st));
+    if (grad_dev)
+        CK(cudaMemcpyAsync(grad_dev, s->g[member], (size_t)s->np * 4, cudaMemcpyDeviceToDevice, st));
+    if (loss_host) {
+        CK(cudaMemcpyAsync(loss_host, s->loss, 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return MLSD_OK;
+}
+
+int mlsd_surrogate_train_step(mlsd_surrogate *s, int member, const void *X_dev,
+                              const float *Y_dev, int M, float lr, double *loss_host,
+                              void *cuda_stream)
+{
+    if (!s || member < 0 || member >= s->members || !X_dev || !Y_dev || M < 1 ||
+        M > s->max_batch || !(lr > 0))
+        return MLSD_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    CK(sur_grad(s->h, M, X_dev, Y_dev, s->w[member], s->wb[member], s->Z, s->A, s->dA, s->dB,
+                s->g[member], s->part, s->loss, st));
+    s->t[member] += 1;
+    CK(sur_adam(s->np, s->w[member], s->g[member], s->m[member], s->v[member], lr, s->t[member],
+                s->wb[member], st));
+    if (loss_host) {
+        CK(cudaMemcpyAsync(loss_host, s->loss, 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return MLSD_OK;
+}
+
+int mlsd_surrogate_predict(mlsd_surrogate *s, const void *X_dev, int64_t M, float *out_dev,
+                           void *cuda_stream)
+{
+    if (!s || !X_dev || !out_dev || M < 1) return MLSD_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const char *X = static_cast<const char *>(X_dev);
+    for (int k = 0; k < s->members; ++k)
+        for (int64_t r0 = 0; r0 < M; r0 += s->max_batch) {
+            const int mb = (int)std::min<int64_t>(s->max_batch, M - r0);
+            float *Z[4] = {s->Z[0], s->Z[1], s->Z[2], out_dev + ((size_t)k * M + r0) * 3};
+            CK(sur_forward(s->h, mb, X + (size_t)r0 * MLSD_SUR_IN * 2, s->w[k], s->wb[k], Z, s->A, st));
+        }
+    return MLSD_OK;
+}
+
+int mlsd_solve_level_surrogate(mlsd_levels *h, mlsd_surrogate *s, int level,
+                               const double *K_base_dev, double *K_out_dev, double threshold,
+                               int64_t *n_fallback_out, void *cuda_stream)
+{
+    if (!h || !s || level < 1 || level > h->L || !K_base_dev || !K_out_dev || !(threshold >= 0))
+        return MLSD_EINVAL;
+    DevLevel &d = h->lev[level - 1];
+    if (d.cls.size() != 1 || d.cls[0].n > 64 || h->precision != MLSD_FP32) return MLSD_EUNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const long long P = h->P;
+    char *ws = nullptr;
+    const size_t xb = (size_t)P * MLSD_SUR_IN * 2, ob = (size_t)s->members * P * 3 * 4;
+    const size_t fb = (size_t)P * 4, ib = (size_t)P * 4;
+    CK(cudaMallocAsync((void **)&ws, xb + ob + fb + ib + 256, st));
+    void *X = ws;
+    float *out = reinterpret_cast<float *>(ws + xb);
+    int *flag = reinterpret_cast<int *>(ws + xb + ob);
+    int *idx = reinterpret_cast<int *>(ws + xb + ob + fb);
+    int *cnt = reinterpret_cast<int *>(ws + xb + ob + fb + ib);
+    int count = 0;
+    int rc = mlsd_surrogate_features(h, level, K_base_dev, X, nullptr, cuda_stream);
+    if (!rc) rc = mlsd_surrogate_predict(s, X, P, out, cuda_stream);
+    cudaError_t e = cudaSuccess;
+    if (!rc) e = sur_disagree(P, s->members, out, K_base_dev, threshold, K_out_dev, flag, idx, cnt, st);
+    if (!rc && e == cudaSuccess) e = cudaMemcpyAsync(&count, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (!rc && e == cudaSuccess && count > 0) {
+        // the plain patch solve on the flagged patches only
+        SizeClass fc = d.cls[0];
+        fc.idx = idx;
+        fc.count = count;
+        PatchParams pp = patch_params(h, d, fc, K_base_dev, d.S, nullptr);
+        e = launch_patch(fc.variant, pp, pp.items, st);
+        if (e == cudaSuccess) e = sur_merge(count, idx, K_base_dev, d.S, K_out_dev, st);
+    }
+    cudaFreeAsync(ws, st);
+    if (rc) return rc;
+    CK(e);
+    if (n_fallback_out) *n_fallback_out = count;
+    return MLSD_OK;
+}
+
 }  // extern "C"

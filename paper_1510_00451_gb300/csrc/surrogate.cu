@@ -1,0 +1,448 @@
+// Learned surrogate of the patch solve (not part of the paper's method; the
+// plain patch solve stays its fallback and the judge of its error).
+//
+// Features (K8): per patch, the 17 x 17 low-mode DFT of the patch's band psi
+// (patch mean removed), divided by tr(B)/2, then B/kappa and log kappa:
+// 582 values stored as one bfloat16 row of MLSD_SUR_IN (640, zero padded).
+// Network: an ensemble of members, each 640 -> h -> h -> h -> 3 with the exact
+// erf GELU, bfloat16 weights and activations, FP32 accumulation; output
+// (K - B) / tr(B).  Training kernels here run on the CUDA cores (FP32 FMA on
+// bfloat16 operands); the inference forward has a tensor-core (tcgen05) kernel
+// in mlp_tc.cu.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "mlsd_internal.cuh"
+
+namespace mlsd {
+namespace {
+
+constexpr int KMODE = 8;                   // local modes -8..8
+constexpr int NMODE = 2 * KMODE + 1;       // 17
+
+// ---------------------------------------------------------------------------
+// K8 features: one CTA per patch (n <= 64: the patch is staged in shared memory)
+__global__ void k_features(const float *band, long long Nl, int n, int n_macro, const int *pidx,
+                           long long count, const double *B, double kappa, __nv_bfloat16 *X,
+                           float *F32)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *psi = reinterpret_cast<float *>(smem_raw);              // [n][n]
+    float2 *Fr = reinterpret_cast<float2 *>(psi + n * n);          // [n][17] row transforms
+    __shared__ double red[32];
+    const long long item = blockIdx.x;
+    if (item >= count) return;
+    const long long p = pidx ? (long long)pidx[item] : item;
+    const long long ox = patch_origin(p % n_macro, n_macro, Nl, n);
+    const long long oy = patch_origin(p / n_macro, n_macro, Nl, n);
+    double sum = 0.0;
+    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
+        const int b = c / n, a = c % n;
+        const float v = band[pmod_ll(oy + b, Nl) * Nl + pmod_ll(ox + a, Nl)];
+        psi[c] = v;
+        sum += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    const float mean = (float)(tot / ((double)n * n));
+    // rows: Fr[b][k1] = sum_a (psi - mean) e^{-2 pi i k1 a / n}
+    for (int t = threadIdx.x; t < n * NMODE; t += blockDim.x) {
+        const int b = t / NMODE, k1 = t % NMODE - KMODE;
+        float sr = 0.f, si = 0.f;
+        for (int a = 0; a < n; ++a) {
+            const int r = (int)pmod_ll((long long)k1 * a, n);
+            float s, c;
+            sincospif(-2.0f * (float)r / (float)n, &s, &c);
+            const float v = psi[b * n + a] - mean;
+            sr = fmaf(v, c, sr);
+            si = fmaf(v, s, si);
+        }
+        Fr[t] = make_float2(sr, si);
+    }
+    __syncthreads();
+    const double trh = 0.5 * (B[3 * p] + B[3 * p + 2]);
+    const float scale = (float)(1.0 / ((double)n * n * trh));
+    __nv_bfloat16 *xr = X + item * (long long)MLSD_SUR_IN;
+    float *fr = F32 ? F32 + item * (long long)MLSD_SUR_FEATURES : nullptr;
+    for (int t = threadIdx.x; t < NMODE * NMODE; t += blockDim.x) {
+        const int k2 = t / NMODE - KMODE, k1i = t % NMODE;
+        float sr = 0.f, si = 0.f;
+        for (int b = 0; b < n; ++b) {
+            const int r = (int)pmod_ll((long long)k2 * b, n);
+            float s, c;
+            sincospif(-2.0f * (float)r / (float)n, &s, &c);
+            const float2 f = Fr[b * NMODE + k1i];
+            // (f.x + i f.y)(c + i s)
+            sr += f.x * c - f.y * s;
+            si += f.x * s + f.y * c;
+        }
+        const float re = sr * scale, im = si * scale;
+        xr[2 * t] = __float2bfloat16_rn(re);
+        xr[2 * t + 1] = __float2bfloat16_rn(im);
+        if (fr) { fr[2 * t] = re; fr[2 * t + 1] = im; }
+    }
+    if (threadIdx.x < MLSD_SUR_IN - 2 * NMODE * NMODE) {
+        const int t = 2 * NMODE * NMODE + threadIdx.x;
+        float v = 0.f;
+        if (t == 578) v = (float)(B[3 * p] / kappa);
+        else if (t == 579) v = (float)(B[3 * p + 1] / kappa);
+        else if (t == 580) v = (float)(B[3 * p + 2] / kappa);
+        else if (t == 581) v = (float)log(kappa);
+        xr[t] = __float2bfloat16_rn(v);
+        if (fr && t < MLSD_SUR_FEATURES) fr[t] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core GEMM with bfloat16 or FP32 operands and FP32 accumulation:
+//   C[i][j] = sum_k A(i, k) B(k, j) (+ bias[j]) (+ C[i][j] if accumulate)
+// A(i, k) = A[i * sam + k * sak], B(k, j) = B[k * sbk + j * sbn].
+// Optional epilogue: act[i][j] = bf16(gelu(C[i][j])).
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+__device__ __forceinline__ float gelu_f(float z)
+{
+    return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_d(float z)
+{
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+constexpr int GT = 64, GK = 16;
+
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const TA *A, long long sam,
+                                              long long sak, const TB *Bm, long long sbk,
+                                              long long sbn, float *C, long long scm,
+                                              const float *bias, int accumulate,
+                                              __nv_bfloat16 *act, long long sactm)
+{
+    __shared__ float As[GK][GT + 4], Bs[GK][GT + 4];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += GK) {
+        for (int t = threadIdx.x; t < GT * GK; t += 256) {
+            const int r = t / GK, k = t % GK;              // A tile: row r, col k
+            const int gi = i0 + r, gk = k0 + k;
+            As[k][r] = (gi < M && gk < K) ? to_f(A[gi * sam + gk * sak]) : 0.f;
+            const int c = t % GT, kb = t / GT;             // B tile: k row kb, col c
+            const int gj = j0 + c, gkb = k0 + kb;
+            Bs[kb][c] = (gj < N && gkb < K) ? to_f(Bm[gkb * sbk + gj * sbn]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GK; ++k) {
+            float a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { a[q] = As[k][ty * 4 + q]; b[q] = Bs[k][tx * 4 + q]; }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[q][r] = fmaf(a[q], b[r], acc[q][r]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int gi = i0 + ty * 4 + q, gj = j0 + tx * 4 + r;
+            if (gi >= M || gj >= N) continue;
+            float v = acc[q][r];
+            if (bias) v += bias[gj];
+            if (accumulate) v += C[gi * scm + gj];
+            C[gi * scm + gj] = v;
+            if (act) act[gi * sactm + gj] = __float2bfloat16_rn(gelu_f(v));
+        }
+}
+
+template <typename TA, typename TB>
+cudaError_t gemm(cudaStream_t s, int M, int N, int K, const TA *A, long long sam, long long sak,
+                 const TB *B, long long sbk, long long sbn, float *C, long long scm,
+                 const float *bias, int accumulate, __nv_bfloat16 *act, long long sactm)
+{
+    dim3 g((N + GT - 1) / GT, (M + GT - 1) / GT);
+    count_launches(1);
+    k_gemm<TA, TB><<<g, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, scm, bias, accumulate,
+                                     act, sactm);
+    return cudaGetLastError();
+}
+
+// dZ = dA * gelu'(Z)   (in place on dA)
+__global__ void k_gelu_bwd(long long n, const float *Z, float *dA)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) dA[i] *= gelu_d(Z[i]);
+}
+
+// db[j] = sum_i dZ[i][j]
+__global__ void k_colsum(int M, int N, const float *dZ, float *db)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    float s = 0.f;
+    for (int i = 0; i < M; ++i) s += dZ[(long long)i * N + j];
+    db[j] = s;
+}
+
+// dZ4 = 2 (Z4 - Y) / (3 M), loss partial sums per block
+__global__ void k_mse(int M, const float *Z4, const float *Y, float *dZ4, double *part)
+{
+    __shared__ double red[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (i < 3 * M) {
+        const float d = Z4[i] - Y[i];
+        dZ4[i] = 2.0f * d / (3.0f * (float)M);
+        l = (double)d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_sum_parts(int n, const double *part, double scale, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) t += part[i];
+        *out = t * scale;
+    }
+}
+
+// Adam on the FP32 master parameters, refreshed bfloat16 copies of the weights
+__global__ void k_adam(long long n, float *w, const float *g, float *m, float *v, float lr,
+                       float b1, float b2, float eps, float c1, float c2, __nv_bfloat16 *wb)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    wb[i] = __float2bfloat16_rn(wi);
+}
+
+__global__ void k_to_bf16(long long n, const float *w, __nv_bfloat16 *wb)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) wb[i] = __float2bfloat16_rn(w[i]);
+}
+
+// Ensemble disagreement on K: for every patch, K_m = B + tr(B) out_m; flag when
+//   max_{m,c} |K_m,c - mean_m K_m,c| > thr * ||mean K||_F.
+// Surrogate estimate where not flagged: K = B + tr(B) mean_m out_m.
+__global__ void k_disagree(long long P, int members, const float *out, const double *B,
+                           double thr, double *K, int *flag)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const double tr = B[3 * p] + B[3 * p + 2];
+    double mean[3] = {0, 0, 0};
+    for (int m = 0; m < members; ++m)
+        for (int c = 0; c < 3; ++c) mean[c] += (double)out[((long long)m * P + p) * 3 + c];
+    double Km[3];
+    for (int c = 0; c < 3; ++c) Km[c] = B[3 * p + c] + tr * mean[c] / members;
+    const double fro = sqrt(Km[0] * Km[0] + 2.0 * Km[1] * Km[1] + Km[2] * Km[2]);
+    double dev = 0.0;
+    for (int m = 0; m < members; ++m)
+        for (int c = 0; c < 3; ++c) {
+            const double km = B[3 * p + c] + tr * (double)out[((long long)m * P + p) * 3 + c];
+            dev = fmax(dev, fabs(km - Km[c]));
+        }
+    const int f = !(dev <= thr * fro);           // NaN -> flagged
+    flag[p] = f;
+    K[3 * p] = Km[0]; K[3 * p + 1] = Km[1]; K[3 * p + 2] = Km[2];
+}
+
+// Stable compaction of the flagged patch indices, one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_compact(long long P, const int *flag, int *idx, int *count)
+{
+    __shared__ int wsum[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (long long c0 = 0; c0 < P; c0 += 1024) {
+        const long long p = c0 + threadIdx.x;
+        const int f = (p < P) ? flag[p] : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        const int pre = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) wsum[w] = __popc(bal);
+        __syncthreads();
+        int off = 0;
+        for (int q = 0; q < w; ++q) off += wsum[q];
+        if (f) idx[base + off + pre] = (int)p;
+        __syncthreads();
+        if (threadIdx.x == 0) { int t = 0; for (int q = 0; q < 32; ++q) t += wsum[q]; base += t; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = base;
+}
+
+// flagged patches take the plain solve: K = sym(B e_j + S_.j)
+__global__ void k_merge_fallback(int n, const int *idx, const double *B, const double *S, double *K)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const long long p = idx[t];
+    const double *b = B + 3 * p, *s = S + 4 * p;
+    K[3 * p] = b[0] + s[0];
+    K[3 * p + 1] = 0.5 * ((b[1] + s[1]) + (b[1] + s[2]));
+    K[3 * p + 2] = b[2] + s[3];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host-side pieces used by the runtime
+long long sur_param_count(int h)
+{
+    return (long long)h * MLSD_SUR_IN + h + 2 * ((long long)h * h + h) + 3LL * h + 3;
+}
+
+cudaError_t launch_features(const float *band, long long Nl, int n, int n_macro, const int *pidx,
+                            long long count, const double *B, double kappa, void *X, float *F32,
+                            cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    const size_t smem = (size_t)n * n * 4 + (size_t)n * NMODE * 8;
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_features),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    k_features<<<(unsigned)count, 320, smem, s>>>(band, Nl, n, n_macro, pidx, count, B, kappa,
+                                                  static_cast<__nv_bfloat16 *>(X), F32);
+    return cudaGetLastError();
+}
+
+// Layer views of one member's parameters (FP32 master or bfloat16 copy)
+struct Layers {
+    long long w[4], b[4];
+    int din[4], dout[4];
+};
+static Layers layers(int h)
+{
+    Layers L;
+    const int dims[5] = {MLSD_SUR_IN, h, h, h, 3};
+    long long o = 0;
+    for (int l = 0; l < 4; ++l) {
+        L.din[l] = dims[l];
+        L.dout[l] = dims[l + 1];
+        L.w[l] = o; o += (long long)dims[l + 1] * dims[l];
+        L.b[l] = o; o += dims[l + 1];
+    }
+    return L;
+}
+
+// Forward of one member on M rows: Z_l (FP32) and bf16 activations A_l.
+// ws: Z1..Z3 [M][h], Z4 [M][3] FP32; A1..A3 [M][h] bf16.
+cudaError_t sur_forward(int h, int M, const void *X, const float *wf, const void *wb_,
+                        float *Z[4], void *Aact[3], cudaStream_t s)
+{
+    const Layers L = layers(h);
+    const __nv_bfloat16 *wb = static_cast<const __nv_bfloat16 *>(wb_);
+    const __nv_bfloat16 *in = static_cast<const __nv_bfloat16 *>(X);
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+        __nv_bfloat16 *act = l < 3 ? static_cast<__nv_bfloat16 *>(Aact[l]) : nullptr;
+        e = gemm<__nv_bfloat16, __nv_bfloat16>(s, M, L.dout[l], L.din[l], in, L.din[l], 1,
+                                               wb + L.w[l], 1, L.din[l], Z[l], L.dout[l],
+                                               wf + L.b[l], 0, act, L.dout[l]);
+        in = act;
+    }
+    return e;
+}
+
+// Loss and gradient of one member (forward included).  ws holds Z[4], A[3] and
+// two [M][h] FP32 gradient buffers; part: >= (3M + 255)/256 doubles; loss_dev: 1 double.
+cudaError_t sur_grad(int h, int M, const void *X, const float *Y, const float *wf, const void *wb_,
+                     float *Z[4], void *Aact[3], float *dA, float *dB_, float *g, double *part,
+                     double *loss_dev, cudaStream_t s)
+{
+    const Layers L = layers(h);
+    const __nv_bfloat16 *wb = static_cast<const __nv_bfloat16 *>(wb_);
+    cudaError_t e = sur_forward(h, M, X, wf, wb_, Z, Aact, s);
+    if (e != cudaSuccess) return e;
+    const int nb = (3 * M + 255) / 256;
+    count_launches(2);
+    k_mse<<<nb, 256, 0, s>>>(M, Z[3], Y, dA, part);
+    k_sum_parts<<<1, 32, 0, s>>>(nb, part, 1.0 / (3.0 * M), loss_dev);
+    float *dZ = dA, *dN = dB_;
+    for (int l = 3; l >= 0; --l) {
+        const __nv_bfloat16 *Ain = l > 0 ? static_cast<const __nv_bfloat16 *>(Aact[l - 1])
+                                         : static_cast<const __nv_bfloat16 *>(X);
+        // dW_l[j][k] = sum_m dZ[m][j] Ain[m][k]
+        e = gemm<float, __nv_bfloat16>(s, L.dout[l], L.din[l], M, dZ, 1, L.dout[l], Ain, L.din[l],
+                                       1, g + L.w[l], L.din[l], nullptr, 0, nullptr, 0);
+        if (e != cudaSuccess) return e;
+        count_launches(1);
+        k_colsum<<<(L.dout[l] + 127) / 128, 128, 0, s>>>(M, L.dout[l], dZ, g + L.b[l]);
+        if (l == 0) break;
+        // dA_{l-1}[m][k] = sum_j dZ[m][j] W_l[j][k];  dZ_{l-1} = dA * gelu'(Z_{l-1})
+        e = gemm<float, __nv_bfloat16>(s, M, L.din[l], L.dout[l], dZ, L.dout[l], 1, wb + L.w[l],
+                                       L.din[l], 1, dN, L.din[l], nullptr, 0, nullptr, 0);
+        if (e != cudaSuccess) return e;
+        const long long n = (long long)M * L.din[l];
+        count_launches(1);
+        k_gelu_bwd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, Z[l - 1], dN);
+        float *t = dZ; dZ = dN; dN = t;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t sur_adam(long long n, float *w, const float *g, float *m, float *v, float lr, int t,
+                     void *wb, cudaStream_t s)
+{
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    count_launches(1);
+    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, w, g, m, v, lr, b1, b2, 1e-8f, c1, c2,
+                                                      static_cast<__nv_bfloat16 *>(wb));
+    return cudaGetLastError();
+}
+
+cudaError_t sur_to_bf16(long long n, const float *w, void *wb, cudaStream_t s)
+{
+    count_launches(1);
+    k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, w, static_cast<__nv_bfloat16 *>(wb));
+    return cudaGetLastError();
+}
+
+cudaError_t sur_disagree(long long P, int members, const float *out, const double *B, double thr,
+                         double *K, int *flag, int *idx, int *count, cudaStream_t s)
+{
+    count_launches(2);
+    k_disagree<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(P, members, out, B, thr, K, flag);
+    k_compact<<<1, 1024, 0, s>>>(P, flag, idx, count);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_merge(int n, const int *idx, const double *B, const double *S, double *K,
+                      cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    count_launches(1);
+    k_merge_fallback<<<(n + 255) / 256, 256, 0, s>>>(n, idx, B, S, K);
+    return cudaGetLastError();
+}
+
+}  // namespace mlsd

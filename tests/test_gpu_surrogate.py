@@ -1,0 +1,141 @@
+"""GPU parity of the surrogate kernels against the oracle: patch features (DFT),
+the MLP forward and gradient with bfloat16 rounding at the same points, and
+the fallback path of the surrogate level solve."""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+from inputs import flows
+import oracle
+from tests._parity import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def mlsd():
+    import paper_1510_00451_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_features_match_oracle(mlsd, torch_mod, n):
+    spec = flows.continuous_spectrum(40, seed=9)
+    edges, N, kappa = [1, 4, 16, 41], 3, 2e-3
+    lv = mlsd.Levels(spec, kappa, N, edges, [n, n, n], n_burn_fixed=1, n_avg_fixed=1)
+    B = inputs.random_bases(N * N, kappa, 4)
+    dev = torch_mod.device("cuda:0")
+    Bd = torch_mod.tensor(B, dtype=torch_mod.float64, device=dev)
+    X = torch_mod.zeros(N * N, mlsd.SUR_IN, dtype=torch_mod.bfloat16, device=dev)
+    F = torch_mod.zeros(N * N, mlsd.SUR_FEATURES, dtype=torch_mod.float32, device=dev)
+    lev, kind = oracle.band_of(spec, edges)
+    for level in (2, 3):
+        lv.features(level, Bd, X, F)
+        torch_mod.cuda.synchronize()
+        Fg = F.cpu().numpy()
+        Nl = oracle.level_lattice(edges, [n] * 3)[level - 1]
+        for p in range(N * N):
+            ox = oracle.patch_origin(p % N, N, Nl, n); oy = oracle.patch_origin(p // N, N, Nl, n)
+            psi = oracle.patch_psi(spec, Nl, ox, oy, n, use=(lev == level) & (kind == 0))
+            f = oracle.features(psi, B[p], kappa)
+            scale = np.abs(f[:578]).max()
+            assert np.abs(Fg[p, :578] - f[:578]).max() < 1e-5 * scale, (level, p)
+            np.testing.assert_allclose(Fg[p, 578:], f[578:], rtol=1e-6)
+        # the bfloat16 row is the rounded FP32 row, zero padded
+        Xg = X.float().cpu().numpy()
+        np.testing.assert_array_equal(Xg[:, :582], F.to(torch_mod.bfloat16).float().cpu().numpy())
+        assert not np.any(Xg[:, 582:])
+
+
+def test_gradient_matches_bf16_oracle(mlsd, torch_mod):
+    h, M = 64, 96
+    sur = mlsd.Surrogate(members=2, hidden=h, max_batch=128)
+    rng = np.random.default_rng(5)
+    dev = torch_mod.device("cuda:0")
+    for member in range(2):
+        params = inputs.mlp_init(mlsd.SUR_IN, h, 100 + member) * 3.0
+        params[::7] += 0.05                       # nonzero biases too
+        sur.set_params(member, params)
+        Xf = np.zeros((M, mlsd.SUR_IN), np.float32)
+        Xf[:, :582] = rng.standard_normal((M, 582)).astype(np.float32)
+        X = torch_mod.tensor(Xf, device=dev).to(torch_mod.bfloat16)
+        Y = torch_mod.tensor(rng.standard_normal((M, 3)) * 0.3, dtype=torch_mod.float32, device=dev)
+        g = torch_mod.zeros(sur.n_params, dtype=torch_mod.float32, device=dev)
+        loss = sur.grad(member, X, Y, g)
+        out_o, loss_o, g_o = oracle.mlp(X.float().cpu().numpy(), params.astype(np.float64), h,
+                                        bf16=True, Y=Y.cpu().numpy(), want_grad=True)
+        assert loss == pytest.approx(loss_o, rel=1e-4)
+        g = g.cpu().numpy()
+        # per tensor (W1 b1 W2 b2 W3 b3 W4 b4)
+        sizes = [h * 640, h, h * h, h, h * h, h, 3 * h, 3]
+        o = 0
+        for sz in sizes:
+            assert rel_l2(g[o:o + sz], g_o[o:o + sz]) < 1e-3, (member, o, sz)
+            o += sz
+        # prediction of every member equals the oracle forward
+        out = torch_mod.zeros(2, M, 3, dtype=torch_mod.float32, device=dev)
+        sur.predict(X, out)
+        assert rel_l2(out[member].cpu().numpy(), out_o) < 1e-3
+
+
+def test_training_lowers_the_loss(mlsd, torch_mod):
+    # a smooth synthetic regression from the first features
+    h, M = 64, 512
+    sur = mlsd.Surrogate(members=1, hidden=h, max_batch=M)
+    sur.set_params(0, inputs.mlp_init(mlsd.SUR_IN, h, 7))
+    rng = np.random.default_rng(8)
+    Xf = np.zeros((M, mlsd.SUR_IN), np.float32)
+    Xf[:, :8] = rng.uniform(-1, 1, (M, 8))
+    Yf = np.stack([np.sin(Xf[:, 0]), Xf[:, 1] * Xf[:, 2], 0.5 * Xf[:, 3] ** 2], 1).astype(np.float32)
+    dev = torch_mod.device("cuda:0")
+    X = torch_mod.tensor(Xf, device=dev).to(torch_mod.bfloat16)
+    Y = torch_mod.tensor(Yf, device=dev)
+    l0 = sur.train_step(0, X, Y, 2e-3, want_loss=True)
+    for _ in range(300):
+        sur.train_step(0, X, Y, 2e-3)
+    l1 = sur.train_step(0, X, Y, 2e-3, want_loss=True)
+    assert l1 < 0.1 * l0, (l0, l1)
+    # parameters round-trip through the host (checkpoint / resume)
+    p = sur.get_params(0)
+    sur2 = mlsd.Surrogate(members=1, hidden=h, max_batch=M)
+    sur2.set_params(0, p)
+    o1 = torch_mod.zeros(1, M, 3, device=dev); o2 = torch_mod.zeros(1, M, 3, device=dev)
+    sur.predict(X, o1); sur2.predict(X, o2)
+    assert torch_mod.equal(o1, o2)
+
+
+def test_surrogate_level_fallback_paths(mlsd, torch_mod):
+    spec = flows.continuous_spectrum(40, seed=9)
+    edges, N, kappa = [1, 4, 16, 41], 4, 2e-3
+    lv = mlsd.Levels(spec, kappa, N, edges, [32] * 3, n_burn_fixed=50, n_avg_fixed=50)
+    dev = torch_mod.device("cuda:0")
+    B = torch_mod.tensor(inputs.random_bases(N * N, kappa, 1), dtype=torch_mod.float64, device=dev)
+    K_plain = torch_mod.zeros_like(B)
+    lv.solve_level(2, B, K_plain)
+    sur = mlsd.Surrogate(members=4, hidden=64, max_batch=64)
+    for m in range(4):
+        sur.set_params(m, inputs.mlp_init(mlsd.SUR_IN, 64, m))
+    # threshold 0: every patch falls back -> exactly the plain result
+    K0 = torch_mod.zeros_like(B)
+    assert lv.solve_level_surrogate(sur, 2, B, K0, 0.0) == N * N
+    assert torch_mod.equal(K0, K_plain)
+    # huge threshold: no fallback, K = B + tr(B) * ensemble mean
+    K1 = torch_mod.zeros_like(B)
+    assert lv.solve_level_surrogate(sur, 2, B, K1, 1e30) == 0
+    X = torch_mod.zeros(N * N, mlsd.SUR_IN, dtype=torch_mod.bfloat16, device=dev)
+    lv.features(2, B, X)
+    out = torch_mod.zeros(4, N * N, 3, device=dev)
+    sur.predict(X, out)
+    tr = (B[:, 0] + B[:, 2]).unsqueeze(1)
+    want = B + tr * out.double().mean(0)
+    assert torch_mod.allclose(K1, want, rtol=1e-12, atol=0)
+    assert lv.status() == 0
