@@ -146,6 +146,69 @@ def reference_arm(args):
 DNS_BYTES_PER_CELL_STEP = 12     # read u, read psi, write u (both RK stages fused)
 
 
+def surrogate_case(N=256, epochs=40, members=4, hidden=256, batch=4096, threshold=1e-3,
+                   seed=1510):
+    """Surrogate vs plain on the diagonal band of the continuous-spectrum flow's
+    6th octave (32 <= |k1|, |k2| < 64, patch side 2 pi / 32, 32^2 patches,
+    kappa = 1e-3, N x N patches, full relaxation window).  Training data: 3
+    seeded base sets on every patch (3 N^2 plain solves); test: a 4th base set."""
+    import torch
+    import inputs
+    from inputs import flows
+    import paper_1510_00451_gb300 as mlsd
+    from paper_1510_00451_gb300 import surrogate as S
+    dev = torch.device("cuda", _local_rank())
+    full = flows.continuous_spectrum(256)
+    a, b = np.abs(full.k1), np.abs(full.k2)
+    keep = (a >= 32) & (a < 64) & (b >= 32) & (b < 64)
+    band = flows.Spectrum(full.k1[keep], full.k2[keep], full.re[keep], full.im[keep])
+    kappa = 1e-3
+    lv = mlsd.Levels(band, kappa, N, [32.0, 64.0], [32], patch_div=[32], cfl=0.2)
+    P = N * N
+    t0 = time.perf_counter()
+    X, Y = S.make_dataset(lv, 1, [inputs.random_bases(P, kappa, seed + i) for i in range(3)])
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    sur = mlsd.Surrogate(members=members, hidden=hidden, max_batch=batch)
+    for m in range(members):
+        sur.set_params(m, inputs.mlp_init(mlsd.SUR_IN, hidden, seed * 10 + m))
+    t0 = time.perf_counter()
+    losses = S.train(sur, X, Y, epochs, batch, 1e-3, seed=seed, lr_final=3e-5)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    Bt = torch.tensor(inputs.random_bases(P, kappa, seed + 99), dtype=torch.float64, device=dev)
+    Kp = torch.empty_like(Bt); Ks = torch.empty_like(Bt)
+    stream = torch.cuda.current_stream()
+    lv.solve_level(1, Bt, Kp)                       # warm-up of both paths
+    lv.solve_level_surrogate(sur, 1, Bt, Ks, threshold)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream); lv.solve_level(1, Bt, Kp); e1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) * 1e-3
+    cu_plain = lv.level_work(1)[0]
+    e0.record(stream); nfb = lv.solve_level_surrogate(sur, 1, Bt, Ks, threshold); e1.record(stream)
+    torch.cuda.synchronize()
+    t_sur = e0.elapsed_time(e1) * 1e-3
+    err = S.k_error(Ks.cpu().numpy(), Kp.cpu().numpy())
+    # the ensemble alone (no fallback) on the same patches, for the error it would make
+    Kn = torch.empty_like(Bt)
+    lv.solve_level_surrogate(sur, 1, Bt, Kn, 1e30)
+    err_nf = S.k_error(Kn.cpu().numpy(), Kp.cpu().numpy())
+    return {"workload": f"continuous-spectrum octave 32-64 diagonal band, {P} patches of 32^2, "
+                        "kappa=1e-3, full window; 3x{P} training solves",
+            "members": members, "hidden": hidden, "epochs": epochs, "final_loss": losses,
+            "threshold": threshold, "fallback": nfb, "fallback_frac": nfb / P,
+            "plain_k_tensors_per_s": P / t_plain, "surrogate_k_tensors_per_s": P / t_sur,
+            "speedup": t_plain / t_sur, "plain_cell_updates_per_s": cu_plain / t_plain,
+            "k_rel_err_vs_plain": {"max": float(err.max()), "p99": float(np.quantile(err, 0.99)),
+                                   "median": float(np.median(err)),
+                                   "frac_le_1e-3": float(np.mean(err <= 1e-3))},
+            "ensemble_only_err": {"max": float(err_nf.max()), "median": float(np.median(err_nf)),
+                                  "frac_le_1e-3": float(np.mean(err_nf <= 1e-3))},
+            "seconds": {"dataset": t_data, "train": t_train, "plain": t_plain, "surrogate": t_sur}}
+
+
 def dns_case(nf, steps, warmup=20, report=False):
     """Direct simulation of the continuous-spectrum flow (|k| <= 256, kappa = 1e-3)
     on an nf x nf FP32 grid: `steps` fused RK2 steps timed with CUDA events."""
@@ -211,7 +274,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dns", action="store_true")
-    ap.add_argument("--case", default="full", choices=["full", "profile", "dns-profile"],
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--case", default="full", choices=["full", "profile", "dns-profile", "surrogate"],
                     help="profile: one pass of the same workload with a fixed 200-step window "
                          "per patch (a small case for ncu captures); prints no bench line")
     args = ap.parse_args()
@@ -221,6 +285,9 @@ def main():
         return profile_case()
     if args.case == "dns-profile":
         return dns_case(4096, 20, warmup=2, report=True)
+    if args.case == "surrogate":
+        print(json.dumps({"case": "surrogate", **surrogate_case()}), flush=True)
+        return 0
 
     import torch
     import torch.distributed as dist
@@ -340,6 +407,10 @@ def main():
                             "algorithmic_bytes_per_cell_step": DNS_BYTES_PER_CELL_STEP},
                "mass_rel_drift": d["mass_rel_drift"], "finite": d["finite"]}
 
+    sur = None
+    if not args.no_surrogate:
+        sur = surrogate_case()
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -384,6 +455,7 @@ def main():
         "gpu_launches": launches,
         "wall_s_timed": t_wall,
         "dns": dns,
+        "surrogate": sur,
     }
     line.update(line_extra)
     print(json.dumps(line), flush=True)
