@@ -215,6 +215,16 @@ int mlsd_surrogate_grad(mlsd_surrogate *s, int member, const void *X_dev, const 
 int mlsd_surrogate_train_step(mlsd_surrogate *s, int member, const void *X_dev,
                               const float *Y_dev, int M, float lr, double *loss_host,
                               void *cuda_stream);
+/* Inference engine: MLSD_SUR_TENSOR (default where the width allows: one
+ * tcgen05 kernel running all layers of a member on 128-row tiles, bfloat16
+ * operands in shared memory, FP32 accumulators in tensor memory) or
+ * MLSD_SUR_CUDA (the FP32-FMA kernels the training uses).                   */
+#define MLSD_SUR_CUDA 0
+#define MLSD_SUR_TENSOR 1
+int mlsd_surrogate_set_engine(mlsd_surrogate *s, int engine);
+/* Device errors of the tensor-core engine (a bounded wait that ran out:
+ * MLSD_ETIMEOUT); synchronises, returns and clears the first one.          */
+int mlsd_surrogate_status(mlsd_surrogate *s, void *cuda_stream);
 /* Every member on M rows: out_dev FP32 [members][M][3].                     */
 int mlsd_surrogate_predict(mlsd_surrogate *s, const void *X_dev, int64_t M, float *out_dev,
                            void *cuda_stream);

@@ -30,7 +30,9 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_surrogate_param_count", "mlsd_surrogate_create", "mlsd_surrogate_free",
             "mlsd_surrogate_set_params", "mlsd_surrogate_get_params", "mlsd_surrogate_features",
             "mlsd_surrogate_grad", "mlsd_surrogate_train_step", "mlsd_surrogate_predict",
-            "mlsd_solve_level_surrogate", "mlsd_strerror"]
+            "mlsd_solve_level_surrogate", "mlsd_surrogate_set_engine", "mlsd_surrogate_status",
+            "mlsd_strerror"]
+SUR_CUDA, SUR_TENSOR = 0, 1
 SUR_IN, SUR_FEATURES = 640, 582
 NOALLOC_MAX_MACRO = 256
 
@@ -97,6 +99,8 @@ _lib.mlsd_surrogate_grad.argtypes = [_P, _I, _P, _P, _I, _P, ctypes.POINTER(_D),
 _lib.mlsd_surrogate_train_step.argtypes = [_P, _I, _P, _P, _I, ctypes.c_float, ctypes.POINTER(_D), _P]
 _lib.mlsd_surrogate_predict.argtypes = [_P, _P, _L, _P, _P]
 _lib.mlsd_solve_level_surrogate.argtypes = [_P, _P, _I, _P, _P, _D, ctypes.POINTER(_L), _P]
+_lib.mlsd_surrogate_set_engine.argtypes = [_P, _I]
+_lib.mlsd_surrogate_status.argtypes = [_P, _P]
 _lib.mlsd_strerror.argtypes = [_I]
 _lib.mlsd_strerror.restype = ctypes.c_char_p
 
@@ -332,6 +336,12 @@ class Surrogate:
                                               float(lr), ctypes.byref(loss) if want_loss else None,
                                               _stream(stream)), "mlsd_surrogate_train_step")
         return loss.value if want_loss else None
+
+    def set_engine(self, engine):
+        _check(_lib.mlsd_surrogate_set_engine(self.s, int(engine)), "mlsd_surrogate_set_engine")
+
+    def status(self, stream=None):
+        return _lib.mlsd_surrogate_status(self.s, _stream(stream))
 
     def predict(self, X, out, stream=None):
         _check(_lib.mlsd_surrogate_predict(self.s, _dptr(X), X.shape[0], _dptr(out),

@@ -137,6 +137,12 @@ cudaError_t sur_disagree(long long P, int members, const float *out, const doubl
 cudaError_t sur_merge(int n, const int *idx, const double *B, const double *S, double *K,
                       cudaStream_t s);
 
+// Tensor-core inference (mlp_tc.cu)
+size_t mlp_tc_smem();
+bool mlp_tc_supported(int h);
+cudaError_t launch_mlp_tc(const void *X, long long M, int h, int members, const void *const *wb_dev,
+                          const float *const *wf_dev, float *out, int *status, cudaStream_t s);
+
 // Shared small device helpers ------------------------------------------------
 __host__ __device__ inline long long pmod_ll(long long a, long long m)
 {

@@ -878,6 +878,10 @@ struct mlsd_surrogate {
     void *A[3] = {};
     float *dA = nullptr, *dB = nullptr;
     double *part = nullptr, *loss = nullptr;
+    void **wb_ptrs = nullptr;             // device arrays of the members' parameter pointers
+    float **wf_ptrs = nullptr;
+    int *status = nullptr;
+    int engine = MLSD_SUR_CUDA;
     std::vector<void *> allocs;
 };
 
@@ -934,6 +938,16 @@ int mlsd_surrogate_create(int members, int hidden, int max_batch, mlsd_surrogate
     if (!rc) rc = sur_alloc(s, (void **)&s->dB, M * H * 4);
     if (!rc) rc = sur_alloc(s, (void **)&s->part, ((3 * M + 255) / 256 + 1) * 8);
     if (!rc) rc = sur_alloc(s, (void **)&s->loss, 8);
+    if (!rc) rc = sur_alloc(s, (void **)&s->wb_ptrs, members * sizeof(void *));
+    if (!rc) rc = sur_alloc(s, (void **)&s->wf_ptrs, members * sizeof(float *));
+    if (!rc) rc = sur_alloc(s, (void **)&s->status, sizeof(int));
+    if (!rc) {
+        if (cudaMemcpy(s->wb_ptrs, s->wb.data(), members * sizeof(void *), cudaMemcpyHostToDevice) ||
+            cudaMemcpy(s->wf_ptrs, s->w.data(), members * sizeof(float *), cudaMemcpyHostToDevice) ||
+            cudaMemset(s->status, 0, sizeof(int)))
+            rc = MLSD_ECUDA;
+    }
+    if (!rc && mlp_tc_supported(hidden)) s->engine = MLSD_SUR_TENSOR;
     if (rc) { mlsd_surrogate_free(s); return rc; }
     *out = s;
     return MLSD_OK;
@@ -1009,11 +1023,33 @@ int mlsd_surrogate_train_step(mlsd_surrogate *s, int member, const void *X_dev,
     return MLSD_OK;
 }
 
+int mlsd_surrogate_set_engine(mlsd_surrogate *s, int engine)
+{
+    if (!s || (engine != MLSD_SUR_CUDA && engine != MLSD_SUR_TENSOR)) return MLSD_EINVAL;
+    if (engine == MLSD_SUR_TENSOR && !mlp_tc_supported(s->h)) return MLSD_EUNSUPPORTED;
+    s->engine = engine;
+    return MLSD_OK;
+}
+
+int mlsd_surrogate_status(mlsd_surrogate *s, void *cuda_stream)
+{
+    if (!s) return MLSD_EINVAL;
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
+    int v = 0;
+    CK(cudaMemcpy(&v, s->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v) CK(cudaMemset(s->status, 0, sizeof(int)));
+    return v;
+}
+
 int mlsd_surrogate_predict(mlsd_surrogate *s, const void *X_dev, int64_t M, float *out_dev,
                            void *cuda_stream)
 {
     if (!s || !X_dev || !out_dev || M < 1) return MLSD_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (s->engine == MLSD_SUR_TENSOR) {
+        CK(launch_mlp_tc(X_dev, M, s->h, s->members, s->wb_ptrs, s->wf_ptrs, out_dev, s->status, st));
+        return MLSD_OK;
+    }
     const char *X = static_cast<const char *>(X_dev);
     for (int k = 0; k < s->members; ++k)
         for (int64_t r0 = 0; r0 < M; r0 += s->max_batch) {

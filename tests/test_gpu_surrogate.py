@@ -139,3 +139,34 @@ def test_surrogate_level_fallback_paths(mlsd, torch_mod):
     want = B + tr * out.double().mean(0)
     assert torch_mod.allclose(K1, want, rtol=1e-12, atol=0)
     assert lv.status() == 0
+
+
+@pytest.mark.parametrize("M,h", [(300, 256), (128, 64), (1000, 128)])
+def test_tensor_core_inference_matches_oracle(mlsd, torch_mod, M, h):
+    # tcgen05 engine against the bfloat16-emulating oracle and the CUDA-core engine
+    members = 2
+    sur = mlsd.Surrogate(members=members, hidden=h, max_batch=512)
+    rng = np.random.default_rng(M + h)
+    params = []
+    for m in range(members):
+        p = inputs.mlp_init(mlsd.SUR_IN, h, 40 + m) * 2.0
+        o = h * mlsd.SUR_IN
+        p[o:o + h] = rng.uniform(-0.2, 0.2, h)            # biases of layer 1
+        params.append(p)
+        sur.set_params(m, p)
+    dev = torch_mod.device("cuda:0")
+    Xf = np.zeros((M, mlsd.SUR_IN), np.float32)
+    Xf[:, :582] = rng.standard_normal((M, 582))
+    X = torch_mod.tensor(Xf, device=dev).to(torch_mod.bfloat16)
+    out_tc = torch_mod.full((members, M, 3), float("nan"), device=dev)
+    sur.set_engine(mlsd.SUR_TENSOR)
+    sur.predict(X, out_tc)
+    assert sur.status() == 0
+    out_cc = torch_mod.zeros(members, M, 3, device=dev)
+    sur.set_engine(mlsd.SUR_CUDA)
+    sur.predict(X, out_cc)
+    Xo = X.float().cpu().numpy()
+    for m in range(members):
+        ref = oracle.mlp(Xo, params[m].astype(np.float64), h, bf16=True)
+        assert rel_l2(out_tc[m].cpu().numpy(), ref) < 1e-3, m
+        assert rel_l2(out_cc[m].cpu().numpy(), ref) < 1e-3, m
