@@ -229,6 +229,44 @@ def surrogate_case(N=256, epochs=120, members=4, hidden=256, batch=2048, lr=3e-3
             "seconds": {"dataset": t_data, "train": t_train, "plain": t_plain}}
 
 
+def dns_case(nf, steps, warmup=20, report=False):
+    """Direct simulation of the continuous-spectrum flow (|k| <= 256, kappa = 1e-3)
+    on an nf x nf FP32 grid: `steps` fused RK2 steps timed with CUDA events."""
+    import torch
+    import inputs
+    import paper_1510_00451_gb300 as mlsd
+    dev = torch.device("cuda", _local_rank())
+    cfg = inputs.config_problem("continuous_spectrum")
+    psi = torch.empty(nf, nf, dtype=torch.float32, device=dev)
+    mlsd.grid_psi(cfg["spectrum"], nf, psi)
+    dt = mlsd.dns_dt(psi, cfg["kappa"], cfg["cfl"])
+    u0 = torch.tensor(inputs.gaussian_u0(nf, cfg["sigma"]), dtype=torch.float32, device=dev)
+    u = u0.clone()
+    ut = torch.empty_like(u)
+    mlsd.dns_run(u, ut, psi, cfg["kappa"], dt, warmup)
+    u.copy_(u0)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mlsd.dns_run(u, ut, psi, cfg["kappa"], dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    N = cfg["n_macro"]
+    U = torch.empty(N, N, dtype=torch.float32, device=dev)
+    mass = mlsd.coarse_grain(u, N, U)
+    m0 = mlsd.coarse_grain(u0, N, U.clone())
+    out = {"grid": nf, "steps": steps, "dt": dt, "ms": ms,
+           "cell_steps_per_s": nf * nf * steps / (ms * 1e-3),
+           "mass_rel_drift": abs(mass - m0) / m0,
+           "finite": bool(torch.isfinite(u).all().item())}
+    if report:
+        print(json.dumps({"case": "dns-profile", **out}), flush=True)
+        return 0 if out["finite"] else 1
+    return out
+
+
 def profile_case():
     """The benchmark's levels and launch shapes with a 200-step window per patch."""
     import torch

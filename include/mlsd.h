@@ -171,7 +171,12 @@ int mlsd_offdiag(mlsd_levels *h, int level, const double *B_dev, double *Koff_de
  *   K_macro = K*_1.
  *   mode            MLSD_PLAIN (MLSD_SURROGATE needs a loaded surrogate)
  *   K_macro_dev     device [P][3]
- *   K_levels_dev    device [L][P][3] receiving K*_l, or NULL               */
+ *   K_levels_dev    device [L][P][3] receiving K*_l, or NULL
+ * The first call (and any call with other output pointers) captures the
+ * whole sequence -- every level's kernels, with concurrent size classes on
+ * forked streams -- into a CUDA graph on an internal stream; later calls
+ * replay it on cuda_stream.  With profiling on (mlsd_profile) or the
+ * environment variable MLSD_NO_GRAPH set, the kernels are launched directly. */
 int mlsd_effective_diffusivity(mlsd_levels *h, int mode, double *K_macro_dev,
                                double *K_levels_dev, void *cuda_stream);
 
@@ -268,7 +273,7 @@ int mlsd_grid_psi(int n_modes, const int32_t *k1, const int32_t *k2, const doubl
  * reference: second-order central differences, second-order Runge-Kutta):
  * u_t = v.grad_h u + kappa Lap_h u with v from psi by central differences,
  * Heun's RK2, nsteps steps.  u_dev [nf][nf] float in place; u_tmp_dev is a
- * caller-provided work field of the same size.                              */
+ * caller-provided work field of the same size.  nf a multiple of 128.        */
 int mlsd_dns_run(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev, double kappa,
                  double dt, int nsteps, void *cuda_stream);
 

@@ -175,55 +175,127 @@ __global__ void k_kmax(int NN, const double *K, double *out)
 }
 
 // ---------------------------------------------------------------------------
-// DNS: tile of TX x TY outputs per CTA, u and psi staged with halo 2 (x range
-// padded to 16-byte boundaries), stage 1 on the tile plus a 1-cell ring, stage 2
-// on the tile.
-constexpr int DTX = 64, DTY = 32, DTH = 256;
-constexpr int DLX = DTX + 8;          // staged x range: x0-4 .. x0+TX+3
-constexpr int DLY = DTY + 4;          // staged y range: y0-2 .. y0+TY+1
-constexpr int DSX = DTX + 2, DSY = DTY + 2;
+// DNS step, both Heun stages fused, one pass over HBM (read u, read psi,
+// write u).  A CTA owns a 128 x 64 output tile.  u and psi are staged with a
+// 2-row / 8-column halo by 16-byte cp.async copies.  Thread (g, seg) owns the
+// 4 columns x0 - 4 + 4g .. +3 (g = 0 and 33 are halo groups) and the 8 output
+// rows y0 + 8 seg .. +7: it computes stage 1 on those rows plus one row above
+// and below (kept in registers), publishes its left and right edge columns of
+// the stage-1 field for its own rows, and after one barrier computes stage 2
+// on its output rows from registers (north, south) and the neighbours' edges
+// (east, west).
+constexpr int DTX = 128, DTY = 64, DRS = 8;
+constexpr int DG = DTX / 4 + 2;                // column groups incl. the two halo groups
+constexpr int DSEG = DTY / DRS;                // row segments
+constexpr int DTH = DG * DSEG;                 // 272 threads
+constexpr int DLX = DTX + 16;                  // staged columns x0-8 .. x0+TX+7
+constexpr int DLY = DTY + 4;                   // staged rows    y0-2 .. y0+TY+1
+constexpr size_t DNS_SMEM = (size_t)2 * DLY * DLX * 4 + (size_t)2 * DTY * DG * 4;
 
-__global__ void __launch_bounds__(DTH) k_dns_step(int nf, const float *__restrict__ u,
-                                                   const float *__restrict__ psi,
-                                                   float *__restrict__ un, float ax, float kd,
-                                                   float dt)
+__device__ __forceinline__ void cp16(void *dst, const void *src)
 {
-    __shared__ __align__(16) float su[DLY][DLX];
-    __shared__ __align__(16) float sp[DLY][DLX];
-    __shared__ float ss[DSY][DSX];
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::
+                 "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+
+__global__ void __launch_bounds__(DTH, 2) k_dns_step(int nf, const float *__restrict__ u,
+                                                     const float *__restrict__ psi,
+                                                     float *__restrict__ un, float ax, float kd,
+                                                     float dt)
+{
+    extern __shared__ __align__(16) float dsm[];
+    float *su = dsm;                          // [DLY][DLX]
+    float *sp = su + DLY * DLX;               // [DLY][DLX]
+    float *eL = sp + DLY * DLX;               // [DTY][DG]  stage-1 value of a group's column 0
+    float *eR = eL + DTY * DG;                // [DTY][DG]  ... of its column 3
     const int x0 = blockIdx.x * DTX, y0 = blockIdx.y * DTY;
-    // stage u and psi: DLY rows x DLX/4 float4 each (x0 - 4 is 16-byte aligned; nf % 4 == 0)
     for (int k = threadIdx.x; k < DLY * (DLX / 4); k += DTH) {
         const int r = k / (DLX / 4), q = k % (DLX / 4);
         int gy = y0 - 2 + r; gy = gy < 0 ? gy + nf : (gy >= nf ? gy - nf : gy);
-        int gx = x0 - 4 + 4 * q; gx = gx < 0 ? gx + nf : (gx >= nf ? gx - nf : gx);
+        int gx = x0 - 8 + 4 * q; gx = gx < 0 ? gx + nf : (gx >= nf ? gx - nf : gx);
         const long long off = (long long)gy * nf + gx;
-        const float4 a = *reinterpret_cast<const float4 *>(u + off);
-        const float4 b = *reinterpret_cast<const float4 *>(psi + off);
-        *reinterpret_cast<float4 *>(&su[r][4 * q]) = a;
-        *reinterpret_cast<float4 *>(&sp[r][4 * q]) = b;
+        cp16(su + r * DLX + 4 * q, u + off);
+        cp16(sp + r * DLX + 4 * q, psi + off);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+
+    const int g = threadIdx.x % DG, seg = threadIdx.x / DG;
+    const int c0 = 4 + 4 * g;                 // staged column of the group's first column
+    const int rbase = 2 + DRS * seg;          // staged row of the segment's first output row
+    // ---- stage 1 on rows rbase-1 .. rbase+DRS (registers s[0..DRS+1]) ----
+    float s1[DRS + 2][4];
+    {
+        float um[4], uc[4], up[4], pm[4], pc[4], pp[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            um[c] = su[(rbase - 2) * DLX + c0 + c]; uc[c] = su[(rbase - 1) * DLX + c0 + c];
+            pm[c] = sp[(rbase - 2) * DLX + c0 + c]; pc[c] = sp[(rbase - 1) * DLX + c0 + c];
+        }
+#pragma unroll
+        for (int k = 0; k < DRS + 2; ++k) {
+            const int r = rbase - 1 + k;
+            const float4 un4 = *reinterpret_cast<const float4 *>(su + (r + 1) * DLX + c0);
+            const float4 pn4 = *reinterpret_cast<const float4 *>(sp + (r + 1) * DLX + c0);
+            up[0] = un4.x; up[1] = un4.y; up[2] = un4.z; up[3] = un4.w;
+            pp[0] = pn4.x; pp[1] = pn4.y; pp[2] = pn4.z; pp[3] = pn4.w;
+            const float uw = su[r * DLX + c0 - 1], ue = su[r * DLX + c0 + 4];
+            const float pw = sp[r * DLX + c0 - 1], pe = sp[r * DLX + c0 + 4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float uE = c < 3 ? uc[c + 1] : ue, uW = c > 0 ? uc[c - 1] : uw;
+                const float pE = c < 3 ? pc[c + 1] : pe, pW = c > 0 ? pc[c - 1] : pw;
+                const float v1 = (pm[c] - pp[c]) * ax, v2 = (pE - pW) * ax;
+                const float f = v1 * (uE - uW) * ax + v2 * (up[c] - um[c]) * ax +
+                                kd * (uE + uW + up[c] + um[c] - 4.0f * uc[c]);
+                s1[k][c] = uc[c] + dt * f;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { um[c] = uc[c]; uc[c] = up[c]; pm[c] = pc[c]; pc[c] = pp[c]; }
+        }
+    }
+    // publish the edge columns of the stage-1 field on the segment's own rows
+#pragma unroll
+    for (int k = 0; k < DRS; ++k) {
+        eL[(DRS * seg + k) * DG + g] = s1[k + 1][0];
+        eR[(DRS * seg + k) * DG + g] = s1[k + 1][3];
     }
     __syncthreads();
-    // f(u) at staged coords (r, c): v1 = -(psi_N - psi_S) ax, v2 = (psi_E - psi_W) ax, ax = 1/(2h)
-    // stage 1 on rows y0-1 .. y0+TY, cols x0-1 .. x0+TX  (staged r = 1.., c = 3..)
-    for (int k = threadIdx.x; k < DSY * DSX; k += DTH) {
-        const int r = 1 + k / DSX, c = 3 + k % DSX;
-        const float uc = su[r][c], uE = su[r][c + 1], uW = su[r][c - 1], uN = su[r + 1][c], uS = su[r - 1][c];
-        const float v1 = (sp[r - 1][c] - sp[r + 1][c]) * ax;
-        const float v2 = (sp[r][c + 1] - sp[r][c - 1]) * ax;
-        const float f = v1 * (uE - uW) * ax + v2 * (uN - uS) * ax + kd * (uE + uW + uN + uS - 4.0f * uc);
-        ss[r - 1][c - 3] = uc + dt * f;
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < DTY * DTX; k += DTH) {
-        const int ty = k / DTX, tx = k % DTX;
-        const int r = ty + 2, c = tx + 4;          // staged coords
-        const int sr = ty + 1, sc = tx + 1;        // stage-1 coords
-        const float sC = ss[sr][sc], sE = ss[sr][sc + 1], sW = ss[sr][sc - 1], sN = ss[sr + 1][sc], sS = ss[sr - 1][sc];
-        const float v1 = (sp[r - 1][c] - sp[r + 1][c]) * ax;
-        const float v2 = (sp[r][c + 1] - sp[r][c - 1]) * ax;
-        const float f = v1 * (sE - sW) * ax + v2 * (sN - sS) * ax + kd * (sE + sW + sN + sS - 4.0f * sC);
-        un[(long long)(y0 + ty) * nf + x0 + tx] = 0.5f * (su[r][c] + sC + dt * f);
+    if (g == 0 || g == DG - 1) return;        // halo groups: stage-1 values only
+    // ---- stage 2 on the output rows ----
+    {
+        float pm[4], pc[4], pp[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            pm[c] = sp[(rbase - 1) * DLX + c0 + c];
+            pc[c] = sp[rbase * DLX + c0 + c];
+        }
+        const int gx = x0 + 4 * (g - 1);
+#pragma unroll
+        for (int k = 0; k < DRS; ++k) {
+            const int r = rbase + k;
+            const float4 pn4 = *reinterpret_cast<const float4 *>(sp + (r + 1) * DLX + c0);
+            pp[0] = pn4.x; pp[1] = pn4.y; pp[2] = pn4.z; pp[3] = pn4.w;
+            const float pw = sp[r * DLX + c0 - 1], pe = sp[r * DLX + c0 + 4];
+            const float sw = eR[(DRS * seg + k) * DG + g - 1], se = eL[(DRS * seg + k) * DG + g + 1];
+            const float4 u4 = *reinterpret_cast<const float4 *>(su + r * DLX + c0);
+            const float uo[4] = {u4.x, u4.y, u4.z, u4.w};
+            float o[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float sC = s1[k + 1][c], sN = s1[k + 2][c], sS = s1[k][c];
+                const float sE = c < 3 ? s1[k + 1][c + 1] : se, sW = c > 0 ? s1[k + 1][c - 1] : sw;
+                const float pE = c < 3 ? pc[c + 1] : pe, pW = c > 0 ? pc[c - 1] : pw;
+                const float v1 = (pm[c] - pp[c]) * ax, v2 = (pE - pW) * ax;
+                const float f = v1 * (sE - sW) * ax + v2 * (sN - sS) * ax +
+                                kd * (sE + sW + sN + sS - 4.0f * sC);
+                o[c] = 0.5f * (uo[c] + sC + dt * f);
+            }
+            *reinterpret_cast<float4 *>(un + (long long)(y0 + DRS * seg + k) * nf + gx) =
+                make_float4(o[0], o[1], o[2], o[3]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { pm[c] = pc[c]; pc[c] = pp[c]; }
+        }
     }
 }
 
@@ -338,11 +410,14 @@ cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kap
     const double h = 2.0 * kPi / nf;
     const float ax = (float)(1.0 / (2.0 * h));
     const float kd = (float)(kappa / (h * h));
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_dns_step),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DNS_SMEM);
+    if (e != cudaSuccess) return e;
     dim3 grid(nf / DTX, nf / DTY);
     float *a = u, *b = u_tmp;
     count_launches(nsteps);
     for (int st = 0; st < nsteps; ++st) {
-        k_dns_step<<<grid, DTH, 0, s>>>(nf, a, psi, b, ax, kd, (float)dt);
+        k_dns_step<<<grid, DTH, DNS_SMEM, s>>>(nf, a, psi, b, ax, kd, (float)dt);
         float *t = a; a = b; b = t;
     }
     if (a != u)

@@ -195,3 +195,22 @@ def test_full_three_level_cellular_sampled(mlsd, torch_mod):
         spread = np.abs(Kl[l] - Kl[l][0]).max() / np.abs(Kl[l][0]).max()
         assert spread < 1e-5, (l, spread)
     assert np.all(K[:, 0] > cfg["kappa"]) and np.all(K[:, 2] > cfg["kappa"])
+
+
+def test_graph_replay_matches_direct_launches(mlsd, torch_mod, monkeypatch):
+    # the captured CUDA graph of Algorithm 3 replays bit for bit what the direct
+    # launches compute, on every replay
+    spec = flows.continuous_spectrum(24, seed=5)
+    args = (spec, 2e-3, 3, [1, 2, 4, 8, 16, 25], [32] * 5)
+    dev = torch_mod.device("cuda:0")
+    lv = mlsd.Levels(*args, n_burn_fixed=60, n_avg_fixed=40)
+    K1 = torch_mod.zeros(9, 3, dtype=torch_mod.float64, device=dev)
+    K2 = torch_mod.zeros_like(K1)
+    lv.effective_diffusivity(K1)            # capture + replay
+    lv.effective_diffusivity(K1)            # replay
+    lv.effective_diffusivity(K2)            # new output pointer: capture again
+    monkeypatch.setenv("MLSD_NO_GRAPH", "1")
+    K3 = torch_mod.zeros_like(K1)
+    lv.effective_diffusivity(K3)            # direct launches
+    assert lv.status() == 0
+    assert torch_mod.equal(K1, K2) and torch_mod.equal(K1, K3)
