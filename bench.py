@@ -229,6 +229,65 @@ def surrogate_case(N=256, epochs=120, members=4, hidden=256, batch=2048, lr=3e-3
             "seconds": {"dataset": t_data, "train": t_train, "plain": t_plain}}
 
 
+def uneven_case(n_avg=32):
+    """The continuous-spectrum workload at full size: |k| <= 256, 8 octave levels,
+    256 x 256 macro nodes (65536 patches per level), patch sizes 32^2 .. 256^2
+    from the size rule, every level's size classes launched concurrently inside
+    one captured graph.  Fixed n_avg-step window per patch (the full window of
+    the 256^2 levels needs ~1e6 steps)."""
+    import torch
+    import inputs
+    import paper_1510_00451_gb300 as mlsd
+    cfg = inputs.config_problem("continuous_spectrum")
+    N, L = cfg["n_macro"], len(cfg["edges"]) - 1
+    t0 = time.perf_counter()
+    lv = mlsd.Levels(cfg["spectrum"], cfg["kappa"], N, cfg["edges"], [0] * L, cfl=cfg["cfl"],
+                     n_burn_fixed=0, n_avg_fixed=n_avg)
+    t_setup = time.perf_counter() - t0
+    hist = []
+    for l in range(1, L + 1):
+        sz = lv.patch_sizes(l)
+        vals, cnt = np.unique(sz, return_counts=True)
+        hist.append({int(v): int(c) for v, c in zip(vals, cnt)})
+    K = torch.zeros(N * N, 3, dtype=torch.float64, device=torch.device("cuda", _local_rank()))
+    lv.effective_diffusivity(K)                   # capture + warm-up
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream); lv.effective_diffusivity(K); e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    assert lv.status() == 0
+    cu = sum(lv.level_work(l + 1)[0] for l in range(L))
+    tiles = [lv.info(l + 1) for l in range(L)]
+    return {"workload": "continuous spectrum |k|<=256, 8 octave levels, 65536 patches/level, "
+                        f"sizes 32^2..256^2 by the size rule, {n_avg}-step window",
+            "cell_updates_per_s": cu / t, "seconds": t, "cell_updates": cu,
+            "k_eff_tensors_per_s": N * N / t, "setup_s": t_setup, "sizes_per_level": hist,
+            "largest_class_tiling": [f"{i['tile_bx']}x{i['tile_by']} c{i['cluster']} m{i['min_ctas']}"
+                                     f"{' packed' if i['packed'] else ''} n={i['n']}" for i in tiles],
+            "finite": bool(torch.isfinite(K).all().item())}
+
+
+def mlp_case(M=65536, members=4, hidden=256):
+    """One tensor-core ensemble inference on M random feature rows (ncu case)."""
+    import torch
+    import inputs
+    import paper_1510_00451_gb300 as mlsd
+    dev = torch.device("cuda", _local_rank())
+    sur = mlsd.Surrogate(members=members, hidden=hidden, max_batch=1024)
+    for m in range(members):
+        sur.set_params(m, inputs.mlp_init(mlsd.SUR_IN, hidden, m))
+    g = torch.Generator(device=dev); g.manual_seed(0)
+    X = torch.randn(M, mlsd.SUR_IN, device=dev, generator=g).to(torch.bfloat16)
+    out = torch.empty(members, M, 3, device=dev)
+    sur.predict(X, out)
+    sur.predict(X, out)
+    ok = sur.status() == 0 and bool(torch.isfinite(out).all().item())
+    print(json.dumps({"case": "mlp-profile", "ok": ok, "rows": M}), flush=True)
+    return 0 if ok else 1
+
+
 def dns_case(nf, steps, warmup=20, report=False):
     """Direct simulation of the continuous-spectrum flow (|k| <= 256, kappa = 1e-3)
     on an nf x nf FP32 grid: `steps` fused RK2 steps timed with CUDA events."""
@@ -295,7 +354,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dns", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--case", default="full", choices=["full", "profile", "dns-profile", "surrogate"],
+    ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--case", default="full",
+                    choices=["full", "profile", "dns-profile", "surrogate", "uneven", "mlp-profile"],
                     help="profile: one pass of the same workload with a fixed 200-step window "
                          "per patch (a small case for ncu captures); prints no bench line")
     args = ap.parse_args()
@@ -307,6 +368,11 @@ def main():
         return dns_case(4096, 20, warmup=2, report=True)
     if args.case == "surrogate":
         print(json.dumps({"case": "surrogate", **surrogate_case()}), flush=True)
+        return 0
+    if args.case == "mlp-profile":
+        return mlp_case()
+    if args.case == "uneven":
+        print(json.dumps({"case": "uneven", **uneven_case()}), flush=True)
         return 0
 
     import torch
@@ -430,6 +496,9 @@ def main():
     sur = None
     if not args.no_surrogate:
         sur = surrogate_case()
+    unev = None
+    if not args.no_uneven:
+        unev = uneven_case()
 
     if rank != 0:
         if world > 1:
@@ -476,6 +545,7 @@ def main():
         "wall_s_timed": t_wall,
         "dns": dns,
         "surrogate": sur,
+        "uneven_sizes": unev,
     }
     line.update(line_extra)
     print(json.dumps(line), flush=True)

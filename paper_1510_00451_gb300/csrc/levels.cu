@@ -46,50 +46,67 @@ __global__ void k_band_pass2(ModeGroups m, long long Nl, const double2 *G, T *ou
     out[y * Nl + x] = (T)acc;
 }
 
-// psi of a mode list at lattice point (gx, gy) of an Nr lattice
-__device__ double psi_point(const ModeList &m, long long Nr, long long gx, long long gy)
+// Factorised Algorithm 1 line variances.  An off-diagonal part restricted to a
+// patch line (psi_12 on a column x = x_a, psi_21 on a row y = y_b) is
+//   g(s) = Re sum_groups e^{i kc x_line} G_o(kc, s),
+//   G_o(kc, s) = sum_{modes with that kc} c e^{i kv t_s},
+// where kc is the wavenumber across the line (k1 for psi_12) and kv the one
+// along it; the samples t_s of every patch of macro row (column) o coincide,
+// so G is synthesised once per o (pass A) and combined per patch line (pass B).
+//   Gout[o][g][s], o < n_macro, g < groups, s < ms (samples per line)
+__global__ void k_line_synth(ModeGroups grp, long long Nl, int n, int r, int n_macro, int ms,
+                             double2 *Gout)
 {
-    double acc = 0.0;
-    for (int t = 0; t < m.n; ++t) {
-        double c, s;
-        twiddle(pmod_ll((long long)m.k1[t] * gx + (long long)m.k2[t] * gy, Nr), Nr, c, s);
-        acc += m.re[t] * c - m.im[t] * s;
+    const int o = blockIdx.y, g = blockIdx.z;
+    const long long Nr = Nl * r;
+    const long long t0 = patch_origin(o, n_macro, Nl, n) * r;     // first sample's lattice index
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ms; s += gridDim.x * blockDim.x) {
+        double gr = 0.0, gi = 0.0;
+        for (int t = grp.gofs[g]; t < grp.gofs[g + 1]; ++t) {
+            double c, sn;
+            twiddle(pmod_ll((long long)grp.k2[t] * (t0 + s), Nr), Nr, c, sn);
+            gr += grp.re[t] * c - grp.im[t] * sn;
+            gi += grp.re[t] * sn + grp.im[t] * c;
+        }
+        Gout[((long long)o * grp.n_groups + g) * ms + s] = make_double2(gr, gi);
     }
-    return acc;
 }
 
-// Algorithm 1 line variances, one thread block per (patch, line):
-//   q12[p][a] = var_s psi_12(x_a, y_s), y_s on the r12-times refined lattice,
-//   q21[p][b] = var_s psi_21(x_s, y_b).
-__global__ void k_offdiag_q(ModeList m12, ModeList m21, long long Nl, int n, int r12, int r21,
-                            int n_macro, const int *idx, int stride, double *q12, double *q21)
+// one CTA per (patch, line): variance over the ms samples of the line
+__global__ void k_line_var(ModeGroups grp, const double2 *G, long long Nl, int n, int ms,
+                           int n_macro, int along_x2, const int *idx, int stride, double *q)
 {
     __shared__ double red[2][32];
+    __shared__ double2 tw[256];
     const long long p = idx ? (long long)idx[blockIdx.x] : (long long)blockIdx.x;
-    const int line = blockIdx.y;          // 0..n-1 -> psi_12 column, n..2n-1 -> psi_21 row
-    const bool is12 = line < n;
-    const ModeList &m = is12 ? m12 : m21;
-    double *q = is12 ? q12 : q21;
-    if (m.n == 0 || q == nullptr) return;
-    const int k = is12 ? line : line - n;
-    const int r = is12 ? r12 : r21;
-    const long long ox = patch_origin(p % n_macro, n_macro, Nl, n);
-    const long long oy = patch_origin(p / n_macro, n_macro, Nl, n);
-    const long long Nr = Nl * r, ms = (long long)n * r;
-    double s1 = 0.0, s2 = 0.0;
-    // one sweep over the samples: sum and sum of squares of (psi - psi at the first
-    // sample), which limits cancellation
-    const double ref = is12 ? psi_point(m, Nr, (ox + k) * r, oy * r)
-                            : psi_point(m, Nr, ox * r, (oy + k) * r);
-    for (long long s = threadIdx.x; s < ms; s += blockDim.x) {
-        const double g = (is12 ? psi_point(m, Nr, (ox + k) * r, oy * r + s)
-                               : psi_point(m, Nr, ox * r + s, (oy + k) * r)) - ref;
-        s1 += g;
-        s2 += g * g;
+    const int line = blockIdx.y;
+    // psi_12 (along x2): line origin o = macro row, constant coordinate = column x_a;
+    // psi_21 (along x1): o = macro column, constant coordinate = row y_b
+    const long long o = along_x2 ? p / n_macro : p % n_macro;
+    const long long oc = patch_origin(along_x2 ? p % n_macro : p / n_macro, n_macro, Nl, n);
+    for (int g = threadIdx.x; g < grp.n_groups; g += blockDim.x) {
+        double c, sn;
+        twiddle(pmod_ll((long long)grp.gk1[g] * (oc + line), Nl), Nl, c, sn);
+        tw[g] = make_double2(c, sn);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    __syncthreads();
+    const double2 *Go = G + o * grp.n_groups * (long long)ms;
+    double ref = 0.0;
+    for (int g = 0; g < grp.n_groups; ++g) ref += Go[(long long)g * ms].x * tw[g].x - Go[(long long)g * ms].y * tw[g].y;
+    double s1 = 0.0, s2 = 0.0;
+    for (int s = threadIdx.x; s < ms; s += blockDim.x) {
+        double v = 0.0;
+        for (int g = 0; g < grp.n_groups; ++g) {
+            const double2 a = Go[(long long)g * ms + s];
+            v += a.x * tw[g].x - a.y * tw[g].y;
+        }
+        v -= ref;
+        s1 += v;
+        s2 += v * v;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
     }
     if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = s1; red[1][threadIdx.x >> 5] = s2; }
     __syncthreads();
@@ -97,8 +114,8 @@ __global__ void k_offdiag_q(ModeList m12, ModeList m21, long long Nl, int n, int
         double a = 0.0, b = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; }
         const double mean = a / (double)ms;
-        double var = b / (double)ms - mean * mean;
-        q[p * stride + k] = var > 0.0 ? var : 0.0;
+        const double var = b / (double)ms - mean * mean;
+        q[p * stride + line] = var > 0.0 ? var : 0.0;
     }
 }
 
@@ -214,14 +231,18 @@ cudaError_t launch_band_synth(const ModeGroups &m, long long Nl, double2 *G, voi
     return cudaGetLastError();
 }
 
-cudaError_t launch_offdiag_q(const ModeList &m12, const ModeList &m21, long long Nl, int n,
-                             int r12, int r21, int n_macro, long long count, const int *idx,
-                             int stride, double *q12, double *q21, cudaStream_t s)
+cudaError_t launch_line_var(const ModeGroups &grp, long long Nl, int n, int r, int n_macro,
+                            long long count, const int *idx, int along_x2, int stride, double *q,
+                            double2 *Gscratch, cudaStream_t s)
 {
-    if ((m12.n == 0 && m21.n == 0) || count == 0) return cudaSuccess;
-    dim3 g((unsigned)count, (unsigned)(2 * n));
-    count_launches(1);
-    k_offdiag_q<<<g, 128, 0, s>>>(m12, m21, Nl, n, r12, r21, n_macro, idx, stride, q12, q21);
+    if (grp.n_groups == 0 || count == 0) return cudaSuccess;
+    if (grp.n_groups > 256) return cudaErrorInvalidValue;
+    const int ms = n * r;
+    dim3 ga((unsigned)((ms + 127) / 128), (unsigned)n_macro, (unsigned)grp.n_groups);
+    count_launches(2);
+    k_line_synth<<<ga, 128, 0, s>>>(grp, Nl, n, r, n_macro, ms, Gscratch);
+    dim3 gb((unsigned)count, (unsigned)n);
+    k_line_var<<<gb, 128, 0, s>>>(grp, Gscratch, Nl, n, ms, n_macro, along_x2, idx, stride, q);
     return cudaGetLastError();
 }
 

@@ -88,15 +88,12 @@ struct ModeGroups {
 cudaError_t launch_band_synth(const ModeGroups &m, long long Nl, double2 *G, void *out,
                               int out_double, cudaStream_t s);
 
-// Line variances of Algorithm 1 for every patch of a level (direct sums).
-struct ModeList {
-    int n;
-    const int *k1, *k2;
-    const double *re, *im;
-};
-cudaError_t launch_offdiag_q(const ModeList &m12, const ModeList &m21, long long Nl, int n,
-                             int r12, int r21, int n_macro, long long count, const int *idx,
-                             int stride, double *q12, double *q21, cudaStream_t s);
+// Factorised line variances of one off-diagonal part (groups keyed by the
+// wavenumber across the line, per-mode k2 field = the one along it);
+// Gscratch holds n_macro * groups * n * r double2.
+cudaError_t launch_line_var(const ModeGroups &grp, long long Nl, int n, int r, int n_macro,
+                            long long count, const int *idx, int along_x2, int stride, double *q,
+                            double2 *Gscratch, cudaStream_t s);
 // max |v| of a band over every patch's nref x nref reference nodes (v1, v2 on an
 // Nr = nref * m lattice)
 cudaError_t launch_patch_vmax(const double *v1, const double *v2, long long Nr, int nref,

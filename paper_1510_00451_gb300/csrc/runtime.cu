@@ -140,28 +140,6 @@ int upload_groups(mlsd_levels *h, const std::vector<HostMode> &modes, ModeGroups
     return MLSD_OK;
 }
 
-int upload_list(mlsd_levels *h, const std::vector<HostMode> &modes, ModeList &m)
-{
-    m.n = (int)modes.size();
-    m.k1 = m.k2 = nullptr; m.re = m.im = nullptr;
-    if (modes.empty()) return MLSD_OK;
-    std::vector<int> k1, k2;
-    std::vector<double> re, im;
-    for (auto &x : modes) { k1.push_back(x.k1); k2.push_back(x.k2); re.push_back(x.re); im.push_back(x.im); }
-    void *p[4];
-    int rc;
-    if ((rc = dev_alloc(h, &p[0], k1.size() * 4))) return rc;
-    if ((rc = dev_alloc(h, &p[1], k2.size() * 4))) return rc;
-    if ((rc = dev_alloc(h, &p[2], re.size() * 8))) return rc;
-    if ((rc = dev_alloc(h, &p[3], im.size() * 8))) return rc;
-    CK(cudaMemcpy(p[0], k1.data(), k1.size() * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(p[1], k2.data(), k2.size() * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(p[2], re.data(), re.size() * 8, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(p[3], im.data(), im.size() * 8, cudaMemcpyHostToDevice));
-    m.k1 = (int *)p[0]; m.k2 = (int *)p[1]; m.re = (double *)p[2]; m.im = (double *)p[3];
-    return MLSD_OK;
-}
-
 // refinement of the line samples of Algorithm 1: at least 10 samples per
 // wavelength of the finest wavenumber along the line, a multiple of n in all
 int line_refine(const std::vector<HostMode> &ms, bool along_x2, double L, int n)
@@ -369,17 +347,38 @@ int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
             CK(e);
         }
 
-        // Algorithm 1 line variances (set-up; independent of the base tensor)
-        ModeList m12, m21;
-        if ((rc = upload_list(h, off12[l], m12))) return rc;
-        if ((rc = upload_list(h, off21[l], m21))) return rc;
+        // Algorithm 1 line variances (set-up; independent of the base tensor),
+        // factorised: psi_12 grouped by k1 (across its columns), psi_21 by k2
         if (d.n_12 && (rc = dev_alloc(h, (void **)&d.q12, (size_t)h->P * d.nq * 8))) return rc;
         if (d.n_21 && (rc = dev_alloc(h, (void **)&d.q21, (size_t)h->P * d.nq * 8))) return rc;
-        for (auto &c : d.cls) {
-            const int r12 = line_refine(off12[l], true, d.L, c.n);
-            const int r21 = line_refine(off21[l], false, d.L, c.n);
-            CK(launch_offdiag_q(m12, m21, c.Nl, c.n, r12, r21, h->N, c.count, c.idx, d.nq,
-                                d.q12, d.q21, s));
+        if (d.n_12 || d.n_21) {
+            mlsd_levels tmp;                 // set-up buffers of this step
+            std::vector<HostMode> sw21;
+            for (auto &x : off21[l]) sw21.push_back({x.k2, x.k1, x.re, x.im});
+            ModeGroups g12, g21;
+            rc = upload_groups(&tmp, off12[l], g12);
+            if (!rc) rc = upload_groups(&tmp, sw21, g21);
+            cudaError_t e = cudaSuccess;
+            for (auto &c : d.cls) {
+                if (rc || e != cudaSuccess) break;
+                const int r12 = line_refine(off12[l], true, d.L, c.n);
+                const int r21 = line_refine(off21[l], false, d.L, c.n);
+                const size_t need = std::max((size_t)g12.n_groups * c.n * r12,
+                                             (size_t)g21.n_groups * c.n * r21) * h->N * sizeof(double2);
+                void *G = nullptr;
+                e = cudaMalloc(&G, std::max<size_t>(need, 16));
+                if (e == cudaSuccess && d.n_12)
+                    e = launch_line_var(g12, c.Nl, c.n, r12, h->N, c.count, c.idx, 1, d.nq, d.q12,
+                                        static_cast<double2 *>(G), s);
+                if (e == cudaSuccess && d.n_21)
+                    e = launch_line_var(g21, c.Nl, c.n, r21, h->N, c.count, c.idx, 0, d.nq, d.q21,
+                                        static_cast<double2 *>(G), s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (G) cudaFree(G);
+            }
+            for (void *q : tmp.allocs) cudaFree(q);
+            if (rc) return rc;
+            CK(e);
         }
 
         // per-level tensors
