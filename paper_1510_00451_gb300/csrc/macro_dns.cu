@@ -12,6 +12,8 @@
 // DNS: u_t = v1 D0x u + v2 D0y u + kappa (Dxx + Dyy) u, v = (-D0y psi, D0x psi),
 // both RK stages fused per tile (u and psi staged with a halo of 2 in shared
 // memory), one pass over HBM per time step: read u, read psi, write u.
+#include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "mlsd_internal.cuh"
@@ -184,13 +186,15 @@ __global__ void k_kmax(int NN, const double *K, double *out)
 // the stage-1 field for its own rows, and after one barrier computes stage 2
 // on its output rows from registers (north, south) and the neighbours' edges
 // (east, west).
-constexpr int DTX = 128, DTY = 64, DRS = 8;
+constexpr int DTX = 128, DRS = 8;
 constexpr int DG = DTX / 4 + 2;                // column groups incl. the two halo groups
-constexpr int DSEG = DTY / DRS;                // row segments
-constexpr int DTH = DG * DSEG;                 // 272 threads
 constexpr int DLX = DTX + 16;                  // staged columns x0-8 .. x0+TX+7
-constexpr int DLY = DTY + 4;                   // staged rows    y0-2 .. y0+TY+1
-constexpr size_t DNS_SMEM = (size_t)2 * DLY * DLX * 4 + (size_t)2 * DTY * DG * 4;
+template <int DTY> struct DnsTile {
+    static constexpr int DSEG = DTY / DRS;     // row segments
+    static constexpr int DTH = DG * DSEG;      // threads
+    static constexpr int DLY = DTY + 4;        // staged rows y0-2 .. y0+TY+1
+    static constexpr size_t SMEM = (size_t)2 * DLY * DLX * 4 + (size_t)2 * DTY * DG * 4;
+};
 
 __device__ __forceinline__ void cp16(void *dst, const void *src)
 {
@@ -198,11 +202,13 @@ __device__ __forceinline__ void cp16(void *dst, const void *src)
                  "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
 }
 
-__global__ void __launch_bounds__(DTH, 2) k_dns_step(int nf, const float *__restrict__ u,
-                                                     const float *__restrict__ psi,
-                                                     float *__restrict__ un, float ax, float kd,
-                                                     float dt)
+template <int DTY>
+__global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const float *__restrict__ u,
+                                                               const float *__restrict__ psi,
+                                                               float *__restrict__ un, float ax,
+                                                               float kd, float dt)
 {
+    constexpr int DLY = DnsTile<DTY>::DLY, DTH = DnsTile<DTY>::DTH;
     extern __shared__ __align__(16) float dsm[];
     float *su = dsm;                          // [DLY][DLX]
     float *sp = su + DLY * DLX;               // [DLY][DLX]
@@ -404,20 +410,64 @@ cudaError_t macro_dt_max(int N, const double *K, double *max_dev, cudaStream_t s
     return cudaGetLastError();
 }
 
+template <int DTY>
+static cudaError_t dns_launch(int nf, const float *a, const float *psi, float *b, float ax, float kd,
+                              float dt, cudaStream_t s)
+{
+    using T = DnsTile<DTY>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_dns_step<DTY>),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_dns_step<DTY><<<dim3(nf / DTX, nf / DTY), T::DTH, T::SMEM, s>>>(nf, a, psi, b, ax, kd, dt);
+    return cudaGetLastError();
+}
+
+// tile height: 64 rows (2 CTAs/SM) or 32 rows (4 CTAs/SM, loads of one CTA overlap
+// another's compute); picked once per process by timing both on the caller's grid
+static int g_dns_ty = 0;
+
 cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kappa, double dt,
                     int nsteps, cudaStream_t s)
 {
     const double h = 2.0 * kPi / nf;
     const float ax = (float)(1.0 / (2.0 * h));
     const float kd = (float)(kappa / (h * h));
-    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_dns_step),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DNS_SMEM);
-    if (e != cudaSuccess) return e;
-    dim3 grid(nf / DTX, nf / DTY);
+    if (const char *env = std::getenv("MLSD_DNS_TY")) g_dns_ty = std::atoi(env) == 32 ? 32 : 64;
+    if (g_dns_ty == 0 && nsteps > 0) {
+        // one trial step of each into u_tmp (u is not modified), best of two
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        for (int ty : {64, 32}) {
+            float t = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, s);
+                cudaError_t e = ty == 64 ? dns_launch<64>(nf, u, psi, u_tmp, ax, kd, (float)dt, s)
+                                         : dns_launch<32>(nf, u, psi, u_tmp, ax, kd, (float)dt, s);
+                cudaEventRecord(e1, s);
+                if (e != cudaSuccess) return e;
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) t = std::min(t, ms);
+            }
+            count_launches(3);
+            if (t < best) { best = t; g_dns_ty = ty; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
     float *a = u, *b = u_tmp;
     count_launches(nsteps);
     for (int st = 0; st < nsteps; ++st) {
-        k_dns_step<<<grid, DTH, DNS_SMEM, s>>>(nf, a, psi, b, ax, kd, (float)dt);
+        cudaError_t e = g_dns_ty == 32 ? dns_launch<32>(nf, a, psi, b, ax, kd, (float)dt, s)
+                                       : dns_launch<64>(nf, a, psi, b, ax, kd, (float)dt, s);
+        if (e != cudaSuccess) return e;
         float *t = a; a = b; b = t;
     }
     if (a != u)

@@ -95,7 +95,10 @@ struct Smem {
     static constexpr int CS = NS + 16 / (int)sizeof(real);
     static constexpr int ROW = NBY * N;          // one row buffer (top or bottom edges)
     static constexpr int COL = NBX * CS;         // one column buffer (left or right edges)
-    static constexpr int STAGE = 2 * ROW + 2 * COL;
+    // C > 1: the neighbouring slabs' edge rows are pushed into HS (row below the
+    // slab) and HN (row above) of this CTA before the stage barrier
+    static constexpr int HALO = C > 1 ? 2 * N : 0;
+    static constexpr int STAGE = 2 * ROW + 2 * COL + HALO;
     static constexpr int EXCH = 2 * STAGE;       // double buffered
     static constexpr int SETUP = N * (NS + 2);   // psi rows of the slab plus one halo row each side
     static constexpr int WORDS = (EXCH > SETUP ? EXCH : SETUP);
@@ -153,6 +156,74 @@ struct Tile {
     using S = Smem<N, C, BX, BY, real>;
     static constexpr int NS = S::NS, NBX = S::NBX, NBY = S::NBY, NT = NBX * NBY;
 
+    // Publish the edges of x into buffer `buf`; with a cluster, also push the
+    // slab's first row into the HN slot of the rank below (its row above) and the
+    // slab's last row into the HS slot of the rank above (its row below).
+    __device__ __forceinline__ static void publish_edges(real *sm, int buf, int rank, int tx, int ty,
+                                                         const real (&x)[BY][BX])
+    {
+        const int a0 = tx * BX, b0 = ty * BY;
+        real *rowT = sm + buf * S::STAGE;
+        real *rowB = rowT + S::ROW;
+        real *colL = rowB + S::ROW;
+        real *colR = colL + S::COL;
+        real t[BX], bt[BX];
+#pragma unroll
+        for (int c = 0; c < BX; ++c) { t[c] = x[0][c]; bt[c] = x[BY - 1][c]; }
+        st_vec<real, BX>(rowT + ty * N + a0, t);
+        st_vec<real, BX>(rowB + ty * N + a0, bt);
+        real l[BY], r[BY];
+#pragma unroll
+        for (int k = 0; k < BY; ++k) { l[k] = x[k][0]; r[k] = x[k][BX - 1]; }
+        st_vec<real, BY>(colL + tx * S::CS + b0, l);
+        st_vec<real, BY>(colR + tx * S::CS + b0, r);
+        if constexpr (C > 1) {
+            real *HS = colR + S::COL, *HN = HS + N;
+            if (ty == NBY - 1) st_vec<real, BX>(rank_ptr<C>(HS + a0, (rank + 1) % C), bt);
+            if (ty == 0) st_vec<real, BX>(rank_ptr<C>(HN + a0, (rank + C - 1) % C), t);
+        }
+    }
+
+    // halos of block (tx, ty) from buffer `buf`, all local after the barrier
+    __device__ __forceinline__ static void load_halos(real *sm, int buf, int tx, int ty,
+                                                      real (&hS)[BX], real (&hN)[BX],
+                                                      real (&hW)[BY + 2], real (&hE)[BY + 2])
+    {
+        const int a0 = tx * BX, b0 = ty * BY;
+        real *rowT = sm + buf * S::STAGE;
+        real *rowB = rowT + S::ROW;
+        real *colL = rowB + S::ROW;
+        real *colR = colL + S::COL;
+        const int tyS = (ty + NBY - 1) % NBY, tyN = (ty + 1) % NBY;
+        const int txW = (tx + NBX - 1) % NBX, txE = (tx + 1) % NBX;
+        const real *cw = colR + txW * S::CS;
+        const real *ce = colL + txE * S::CS;
+        real tmpw[BY], tmpe[BY];
+        ld_vec<real, BY>(tmpw, cw + b0);
+        ld_vec<real, BY>(tmpe, ce + b0);
+#pragma unroll
+        for (int k = 0; k < BY; ++k) { hW[k + 1] = tmpw[k]; hE[k + 1] = tmpe[k]; }
+        const int aw = (a0 + N - 1) % N, ae = (a0 + BX) % N;
+        if (C > 1 && ty == 0) {
+            const real *HS = colR + S::COL;
+            ld_vec<real, BX>(hS, HS + a0);
+            hW[0] = HS[aw]; hE[0] = HS[ae];
+        } else {
+            ld_vec<real, BX>(hS, rowB + tyS * N + a0);
+            const int bs = (b0 + NS - 1) % NS;
+            hW[0] = cw[bs]; hE[0] = ce[bs];
+        }
+        if (C > 1 && ty == NBY - 1) {
+            const real *HN = colR + S::COL + N;
+            ld_vec<real, BX>(hN, HN + a0);
+            hW[BY + 1] = HN[aw]; hE[BY + 1] = HN[ae];
+        } else {
+            ld_vec<real, BX>(hN, rowT + tyN * N + a0);
+            const int bn = (b0 + BY) % NS;
+            hW[BY + 1] = cw[bn]; hE[BY + 1] = ce[bn];
+        }
+    }
+
     // Exchange the edges of x through buffer `buf`, then form
     //   g = bc x + b11 (xE + xW) + b22 (xN + xS) + A1 (xE - xW [+2h]) + A2 (xN - xS [+2h])
     //       + bx (dEW(b+1) - dEW(b-1)),
@@ -163,46 +234,11 @@ struct Tile {
                                                  const real (&A1)[BY][BX], const real (&A2)[BY][BX],
                                                  real b11, real b22, real bx, real bc, real twoh)
     {
-        const int a0 = tx * BX, b0 = ty * BY;
-        real *rowT = sm + buf * S::STAGE;
-        real *rowB = rowT + S::ROW;
-        real *colL = rowB + S::ROW;
-        real *colR = colL + S::COL;
-        // publish edges
-        {
-            real t[BX], bt[BX];
-#pragma unroll
-            for (int c = 0; c < BX; ++c) { t[c] = x[0][c]; bt[c] = x[BY - 1][c]; }
-            st_vec<real, BX>(rowT + ty * N + a0, t);
-            st_vec<real, BX>(rowB + ty * N + a0, bt);
-            real l[BY], r[BY];
-#pragma unroll
-            for (int k = 0; k < BY; ++k) { l[k] = x[k][0]; r[k] = x[k][BX - 1]; }
-            st_vec<real, BY>(colL + tx * S::CS + b0, l);
-            st_vec<real, BY>(colR + tx * S::CS + b0, r);
-        }
+        publish_edges(sm, buf, rank, tx, ty, x);
         tile_sync<C>();
-        // halos: south row b0-1, north row b0+BY, west column a0-1, east column a0+BX;
-        // rows beyond the slab come from the neighbouring CTA of the cluster (ring)
+        // halos: south row b0-1, north row b0+BY, west column a0-1, east column a0+BX
         real hS[BX], hN[BX], hW[BY + 2], hE[BY + 2];
-        {
-            const int rS = (ty == 0) ? (rank + C - 1) % C : rank;
-            const int rN = (ty == NBY - 1) ? (rank + 1) % C : rank;
-            const int tyS = (ty + NBY - 1) % NBY, tyN = (ty + 1) % NBY;
-            const int txW = (tx + NBX - 1) % NBX, txE = (tx + 1) % NBX;
-            ld_vec<real, BX>(hS, rank_ptr<C>(rowB + tyS * N + a0, rS));
-            ld_vec<real, BX>(hN, rank_ptr<C>(rowT + tyN * N + a0, rN));
-            const real *cw = colR + txW * S::CS;
-            const real *ce = colL + txE * S::CS;
-            real tmpw[BY], tmpe[BY];
-            ld_vec<real, BY>(tmpw, cw + b0);
-            ld_vec<real, BY>(tmpe, ce + b0);
-            const int bs = (b0 + NS - 1) % NS, bn = (b0 + BY) % NS;
-            hW[0] = *rank_ptr<C>(cw + bs, rS); hE[0] = *rank_ptr<C>(ce + bs, rS);
-            hW[BY + 1] = *rank_ptr<C>(cw + bn, rN); hE[BY + 1] = *rank_ptr<C>(ce + bn, rN);
-#pragma unroll
-            for (int k = 0; k < BY; ++k) { hW[k + 1] = tmpw[k]; hE[k + 1] = tmpe[k]; }
-        }
+        load_halos(sm, buf, tx, ty, hS, hN, hW, hE);
         // rolling E-W differences of rows r-1, r, r+1
         real dm[BX], d0[BX], dp[BX];
 #pragma unroll
@@ -254,7 +290,87 @@ struct Tile {
         }
     }
 
-    template <int J>
+    // Split-phase stage.  On entry x's edges are in buffer `buf` and this thread
+    // has arrived at the stage barrier.  Interior cells (no halo needed) are
+    // computed while the barrier completes; then the halos are read and the
+    // boundary ring is computed; finally out's edges go to buffer buf ^ 1 and
+    // the thread arrives for the next stage.
+    __device__ __forceinline__ static void cell(real &o, real w_old, real xc, real xE, real xW,
+                                                real xN, real xS, real dEW, real dm, real dp,
+                                                real a1, real a2, real b11, real b22, real bx,
+                                                real bc, real twoh, int J, bool second)
+    {
+        real d1 = dEW, d2 = xN - xS;
+        if (J == 1) d1 = d1 + twoh; else d2 = d2 + twoh;
+        const real s1 = xE + xW, s2 = xN + xS, cr = dp - dm;
+        real g = a1 * d1;
+        g = fma(a2, d2, g);
+        g = fma(b11, s1, g);
+        g = fma(b22, s2, g);
+        g = fma(bx, cr, g);
+        g = fma(bc, xc, g);
+        o = second ? (real)0.5 * (w_old + g) : g;
+    }
+
+    template <int J, bool SECOND>
+    __device__ __forceinline__ static void stage_split(real *sm, int buf, int rank, int tx, int ty,
+                                                       const real (&x)[BY][BX], real (&out)[BY][BX],
+                                                       const real (&A1)[BY][BX], const real (&A2)[BY][BX],
+                                                       real b11, real b22, real bx, real bc, real twoh)
+    {
+        const int a0 = tx * BX, b0 = ty * BY;
+        // ---- interior: rows 1..BY-2, columns 1..BX-2 (rolling E-W differences) ----
+        {
+            real dm[BX], d0[BX], dp[BX];
+#pragma unroll
+            for (int c = 1; c < BX - 1; ++c) { dm[c] = x[0][c + 1] - x[0][c - 1]; d0[c] = x[1][c + 1] - x[1][c - 1]; }
+#pragma unroll
+            for (int r = 1; r < BY - 1; ++r) {
+#pragma unroll
+                for (int c = 1; c < BX - 1; ++c) dp[c] = x[r + 1][c + 1] - x[r + 1][c - 1];
+#pragma unroll
+                for (int c = 1; c < BX - 1; ++c)
+                    cell(out[r][c], out[r][c], x[r][c], x[r][c + 1], x[r][c - 1], x[r + 1][c],
+                         x[r - 1][c], d0[c], dm[c], dp[c], A1[r][c], A2[r][c], b11, b22, bx, bc,
+                         twoh, J, SECOND);
+#pragma unroll
+                for (int c = 1; c < BX - 1; ++c) { dm[c] = d0[c]; d0[c] = dp[c]; }
+            }
+        }
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        real hS[BX], hN[BX], hW[BY + 2], hE[BY + 2];
+        load_halos(sm, buf, tx, ty, hS, hN, hW, hE);
+        // x with halos: X(r, c) for r = -1..BY, c = -1..BX
+        auto X = [&](int r, int c) -> real {
+            if (r < 0) return c < 0 ? hW[0] : (c >= BX ? hE[0] : hS[c]);
+            if (r >= BY) return c < 0 ? hW[BY + 1] : (c >= BX ? hE[BY + 1] : hN[c]);
+            return c < 0 ? hW[r + 1] : (c >= BX ? hE[r + 1] : x[r][c]);
+        };
+        auto D = [&](int r, int c) -> real { return X(r, c + 1) - X(r, c - 1); };
+        // ---- boundary ring: rows 0 and BY-1 (all columns), then columns 0 and BX-1 ----
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int r = e == 0 ? 0 : BY - 1;
+#pragma unroll
+            for (int c = 0; c < BX; ++c)
+                cell(out[r][c], out[r][c], x[r][c], X(r, c + 1), X(r, c - 1), X(r + 1, c), X(r - 1, c),
+                     D(r, c), D(r - 1, c), D(r + 1, c), A1[r][c], A2[r][c], b11, b22, bx, bc, twoh,
+                     J, SECOND);
+        }
+#pragma unroll
+        for (int r = 1; r < BY - 1; ++r)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int c = e == 0 ? 0 : BX - 1;
+                cell(out[r][c], out[r][c], x[r][c], X(r, c + 1), X(r, c - 1), X(r + 1, c), X(r - 1, c),
+                     D(r, c), D(r - 1, c), D(r + 1, c), A1[r][c], A2[r][c], b11, b22, bx, bc, twoh,
+                     J, SECOND);
+            }
+        publish_edges(sm, buf ^ 1, rank, tx, ty, out);
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    }
+
+    template <int J, bool SPLIT>
     __device__ static void run(const PatchParams &prm, real *sm, long long p, int rank)
     {
         const int tid = threadIdx.x, tx = tid % NBX, ty = tid / NBX;
@@ -345,9 +461,18 @@ struct Tile {
         double f1 = 0.0, f2 = 0.0;
         int win = 0;
         const long long ntot = nb + na;
+        if constexpr (SPLIT) {
+            publish_edges(sm, 0, rank, tx, ty, w);
+            asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        }
         for (long long step = 0; step < ntot; ++step) {
-            stage<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, b11, b22, bx, bc, twoh);
-            stage<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, b11, b22, bx, bc, twoh);
+            if constexpr (SPLIT) {
+                stage_split<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, b11, b22, bx, bc, twoh);
+                stage_split<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, b11, b22, bx, bc, twoh);
+            } else {
+                stage<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, b11, b22, bx, bc, twoh);
+                stage<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, b11, b22, bx, bc, twoh);
+            }
             if (step >= nb) {
                 real q1 = 0, q2 = 0;
 #pragma unroll
@@ -364,6 +489,7 @@ struct Tile {
         }
         f1 += (double)p1;
         f2 += (double)p2;
+        if constexpr (SPLIT) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 
         // ---- outputs ------------------------------------------------------
         if (prm.wdump) {
@@ -403,7 +529,7 @@ struct Tile {
     }
 };
 
-template <int N, int BX, int BY, typename real, int MINB, int C>
+template <int N, int BX, int BY, typename real, int MINB, int C, bool SPLIT>
 __global__ void __launch_bounds__((N / BX) * (N / C / BY), MINB)
 k_patch_solve(PatchParams prm)
 {
@@ -413,11 +539,11 @@ k_patch_solve(PatchParams prm)
     const int rank = (int)(blockIdx.x % C);
     if (item >= prm.item0 + prm.items) return;      // whole clusters only: C divides the grid
     const long long p = prm.pidx ? (long long)prm.pidx[item >> 1] : (item >> 1);
-    if (item & 1) Tile<N, C, BX, BY, real>::template run<2>(prm, sm, p, rank);
-    else Tile<N, C, BX, BY, real>::template run<1>(prm, sm, p, rank);
+    if (item & 1) Tile<N, C, BX, BY, real>::template run<2, SPLIT>(prm, sm, p, rank);
+    else Tile<N, C, BX, BY, real>::template run<1, SPLIT>(prm, sm, p, rank);
 }
 
-template <int N, int BX, int BY, typename real, int MINB = 1, int C = 1>
+template <int N, int BX, int BY, typename real, int MINB = 1, int C = 1, bool SPLIT = false>
 void add_variant(std::vector<PatchVariant> &out)
 {
     static_assert(((N / BX) * (N / C / BY)) % 32 == 0, "whole warps only");
@@ -431,9 +557,10 @@ void add_variant(std::vector<PatchVariant> &out)
     v.minb = MINB;
     v.packed = 0;
     v.cluster = C;
+    v.split = SPLIT ? 1 : 0;
     v.threads = (N / BX) * (N / C / BY);
     v.smem = Smem<N, C, BX, BY, real>::BYTES;
-    v.fn = reinterpret_cast<const void *>(&k_patch_solve<N, BX, BY, real, MINB, C>);
+    v.fn = reinterpret_cast<const void *>(&k_patch_solve<N, BX, BY, real, MINB, C, SPLIT>);
     out.push_back(v);
 }
 
@@ -741,6 +868,7 @@ void add_variant2(std::vector<PatchVariant> &out)
     v.minb = MINB;
     v.packed = 1;
     v.cluster = 1;
+    v.split = 0;
     v.threads = (N / BX) * (N / BY);
     v.smem = Smem2<N, BX, BY>::BYTES;
     v.fn = reinterpret_cast<const void *>(&k_patch_solve2<N, BX, BY, MINB>);
@@ -771,6 +899,7 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
         switch (n) {
         case 32:
             add_variant<32, 4, 8, float>(out);
+            add_variant<32, 4, 8, float, 1, 1, true>(out);
             add_variant<32, 4, 4, float>(out);
             add_variant<32, 2, 8, float>(out);
             add_variant<32, 2, 4, float>(out);
@@ -781,6 +910,8 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
         case 64:
             add_variant<64, 4, 8, float>(out);
             add_variant<64, 4, 8, float, 3>(out);
+            add_variant<64, 4, 8, float, 3, 1, true>(out);
+            add_variant<64, 4, 4, float, 2, 1, true>(out);
             add_variant<64, 4, 4, float>(out);
             add_variant<64, 2, 8, float>(out);
             add_variant<64, 8, 4, float>(out);
@@ -791,11 +922,14 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
             break;
         case 128:   // split over a cluster of CTAs (rows in slabs)
             add_variant<128, 4, 8, float, 3, 4>(out);
+            add_variant<128, 4, 8, float, 3, 4, true>(out);
             add_variant<128, 4, 8, float, 1, 2>(out);
             add_variant<128, 4, 4, float, 1, 4>(out);
             break;
         case 256:
             add_variant<256, 4, 8, float, 1, 8>(out);
+            add_variant<256, 4, 8, float, 1, 8, true>(out);
+            add_variant<256, 4, 8, float, 2, 8, true>(out);
             add_variant<256, 4, 4, float, 1, 8>(out);
             add_variant<256, 4, 8, float, 3, 16>(out);
             break;
@@ -825,7 +959,7 @@ cudaError_t launch_patch(const PatchVariant &v, const PatchParams &p, long long 
     if (e != cudaSuccess) return e;
     void *args[] = {const_cast<PatchParams *>(&p)};
     count_launches(1);
-    if (v.cluster > 1) {
+    if (v.cluster > 1 || v.split) {
         if (v.cluster > 8) {
             e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return e;

@@ -405,7 +405,7 @@ std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;   // -> (bx, co
 
 int tile_code(const PatchVariant &v)
 {
-    return v.by * 16 + v.minb + 4096 * v.packed + 65536 * v.cluster;
+    return v.by * 16 + v.minb + 4096 * v.packed + 65536 * v.cluster + (1 << 24) * v.split;
 }
 
 int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
@@ -415,17 +415,20 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
     if (vs.empty()) return MLSD_EUNSUPPORTED;
     c.variant = vs[0];
     if (const char *env = std::getenv("MLSD_TILE")) {
-        // <bx>x<by>[m<minb>][c<cluster>][p]: p selects the packed two-field kernel
-        int bx = 0, by = 0, mb = 1, pk = 0, cl = 1;
+        // <bx>x<by>[m<minb>][c<cluster>][p][s]: p selects the packed two-field kernel,
+        // s the split-phase stage barriers
+        int bx = 0, by = 0, mb = 1, pk = 0, cl = 1, sp = 0;
         char rest[16] = "";
         if (std::sscanf(env, "%dx%d%15s", &bx, &by, rest) >= 2) {
             for (const char *c = rest; *c; ++c) {
                 if (*c == 'm') mb = std::atoi(c + 1);
                 if (*c == 'c') cl = std::atoi(c + 1);
                 if (*c == 'p') pk = 1;
+                if (*c == 's') sp = 1;
             }
             for (auto &v : vs)
-                if (v.bx == bx && v.by == by && v.minb == mb && v.packed == pk && v.cluster == cl) {
+                if (v.bx == bx && v.by == by && v.minb == mb && v.packed == pk && v.cluster == cl &&
+                    v.split == sp) {
                     c.variant = v;
                     return MLSD_OK;
                 }
@@ -628,6 +631,7 @@ int mlsd_level_info(const mlsd_levels *h, int level, mlsd_level_desc *out)
     out->packed = c.variant.packed;
     out->cluster = c.variant.cluster;
     out->min_ctas = c.variant.minb;
+    out->split = c.variant.split;
     out->n_classes = (int)d.cls.size();
     return MLSD_OK;
 }
