@@ -1,5 +1,7 @@
 // Tensor-core (tcgen05) inference of the surrogate ensemble: one CTA runs all
-// four layers of one member on a 128-row tile.
+// four layers of one member on a 128-row tile.  Two kernels: k_mlp_tma (TMA
+// ring, used when the tensor maps can be built) and k_mlp_tc (operands staged
+// by the threads; the fallback).
 //
 //   * operands are staged in shared memory in the canonical no-swizzle
 //     K-major layout: 8-row x 16-byte core matrices, consecutive along K
@@ -12,9 +14,11 @@
 //     rounds to bfloat16 and writes the next layer's A operand in shared memory.
 // A wait that exceeds its iteration limit latches MLSD_ETIMEOUT, skips the rest
 // of the tile, frees the tensor memory and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "mlsd_internal.cuh"
 
@@ -243,7 +247,265 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(TcArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-fed variant.  Operands arrive by cp.async.bulk.tensor through a 3-D view
+// of each row-major [rows][K] bfloat16 matrix: (8 elements) x (rows) x (K / 8
+// groups), strides (2 B, K * 2 B, 16 B).  A box {8, R, 8} lands in shared memory
+// as K-group-major slabs of R x 16 B, i.e. the no-swizzle K-major core-matrix
+// layout with core matrices 128 B apart along M / N and R * 16 B apart along K.
+// A 3-slot ring (full / empty mbarriers) prefetches 64-wide K chunks across the
+// layers while one thread issues the MMAs; the epilogue writes activations in the
+// same layout (conflict-free 16-byte stores) for the next layer's A operand.
+constexpr int RING = 3;
+constexpr int A_BYTES = TM * KC * 2;           // 16 KB
+constexpr int B_BYTES = HMAX * KC * 2;         // 32 KB
+constexpr int SLOT = A_BYTES + B_BYTES;
+
+struct TmaArgs {
+    CUtensorMap xmap;                          // X [M][640]
+    CUtensorMap wmap[4][4];                    // [member][layer]
+    long long M;
+    int h, members;
+    const float *const *wf;
+    float *out;
+    int *status;
+};
+
+__device__ __forceinline__ void tma3(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                     uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) k_mlp_tma(const __grid_constant__ TmaArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *ring = smem;                          // RING x (A 16 KB | B 32 KB)
+    unsigned char *Hs = smem + RING * SLOT;              // [K/8][128][16 B] activations
+    __shared__ __align__(8) uint64_t full[RING], empty[RING], accb;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+
+    const int member = blockIdx.y;
+    const long long row0 = (long long)blockIdx.x * TM;
+    const int rows_valid = (int)min((long long)TM, a.M - row0);
+    const int h = a.h;
+    const float *wf = a.wf[member];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long ob1 = (long long)h * MLSD_SUR_IN, ob2 = ob1 + h + (long long)h * h;
+    const long long ob3 = ob2 + h + (long long)h * h, ob4 = ob3 + h + 3LL * h;
+
+    // chunk schedule over the four layers: K chunks of 64, N rows of the weight tile
+    const int nk1 = MLSD_SUR_IN / KC, nkh = h / KC;
+    const int total = nk1 + 3 * nkh;
+    auto layer_of = [&](int q) { return q < nk1 ? 0 : 1 + (q - nk1) / nkh; };
+    auto kc_of = [&](int q) { return q < nk1 ? q : (q - nk1) % nkh; };
+    auto nrows = [&](int l) { return l < 3 ? h : 16; };
+
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int i = 0; i < RING; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[i])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&accb)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_slot)), "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t taddr_row = tmem + ((uint32_t)(warp * 32) << 16);
+
+    auto issue_load = [&](int q) {
+        const int l = layer_of(q), kc = kc_of(q), slot = q % RING;
+        unsigned char *sA = ring + slot * SLOT, *sB = sA + A_BYTES;
+        const uint32_t fb = smem_u32(&full[slot]);
+        const int nr = nrows(l);
+        expect_tx(fb, (l == 0 ? A_BYTES : 0) + nr * KC * 2);
+        if (l == 0) tma3(smem_u32(sA), &a.xmap, 0, (int)row0, kc * (KC / 8), fb);
+        tma3(smem_u32(sB), &a.wmap[member][l], 0, 0, kc * (KC / 8), fb);
+    };
+
+    uint32_t acc_phase = 0;
+    bool ok = true;
+    int issued = 0;                          // chunks whose loads thread 0 has issued
+    if (threadIdx.x == 0)
+        for (; issued < RING && issued < total; ++issued) issue_load(issued);
+    int q = 0;
+    for (int l = 0; l < 4 && ok; ++l) {
+        const int nk = l == 0 ? nk1 : nkh;
+        const int N = nrows(l);
+        const uint32_t idesc = inst_desc(TM, N);
+        if (threadIdx.x == 0) {
+            for (int kc = 0; kc < nk && ok; ++kc, ++q) {
+                const int slot = q % RING;
+                if (!mbar_wait(smem_u32(&full[slot]), (uint32_t)((q / RING) & 1))) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                unsigned char *sA = ring + slot * SLOT, *sB = sA + A_BYTES;
+#pragma unroll
+                for (int ks = 0; ks < KC / 16; ++ks) {
+                    uint64_t da, db;
+                    if (l == 0) da = mat_desc(smem_u32(sA + ks * 2 * (TM * 16)), TM * 16, 128);
+                    else da = mat_desc(smem_u32(Hs + ((kc * KC + ks * 16) >> 3) * (TM * 16)), TM * 16, 128);
+                    db = mat_desc(smem_u32(sB + ks * 2 * (N * 16)), N * 16, 128);
+                    mma_bf16(tmem, da, db, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+                }
+                mma_commit(smem_u32(&empty[slot]));
+                if (kc == nk - 1) mma_commit(smem_u32(&accb));
+                // refill the slot of the previous chunk once its MMAs are done
+                const int qn = q - 1 + RING;
+                if (q >= 1 && qn < total) {
+                    const int ps = (q - 1) % RING;
+                    if (!mbar_wait(smem_u32(&empty[ps]), (uint32_t)(((q - 1) / RING) & 1))) { ok = false; break; }
+                    issue_load(qn);
+                    issued = qn + 1;
+                }
+            }
+            if (!ok) failed = 1;
+        } else {
+            q += nk;
+        }
+        // accumulator of layer l complete
+        const bool got = mbar_wait(smem_u32(&accb), acc_phase);
+        acc_phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!got) failed = 1;
+        __syncthreads();
+        if (failed) { ok = false; break; }
+        const int r = warp * 32 + lane;
+        if (l < 3) {
+            const float *bias = wf + (l == 0 ? ob1 : (l == 1 ? ob2 : ob3));
+            for (int c0 = 0; c0 < h; c0 += 16) {
+                float v[16];
+                tmem_ld16(taddr_row + (uint32_t)c0, v);
+                __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(gelu_tc(v[i] + bias[c0 + i]));
+                *reinterpret_cast<uint4 *>(Hs + (c0 >> 3) * (TM * 16) + r * 16) = *reinterpret_cast<const uint4 *>(o);
+                *reinterpret_cast<uint4 *>(Hs + ((c0 >> 3) + 1) * (TM * 16) + r * 16) = *reinterpret_cast<const uint4 *>(o + 8);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        } else {
+            float v[16];
+            tmem_ld16(taddr_row, v);
+            if (r < rows_valid) {
+                float *o = a.out + ((long long)member * a.M + row0 + r) * 3;
+                o[0] = v[0] + wf[ob4];
+                o[1] = v[1] + wf[ob4 + 1];
+                o[2] = v[2] + wf[ob4 + 2];
+            }
+        }
+    }
+    if (!ok && threadIdx.x == 0) {
+        atomicCAS(a.status, 0, MLSD_ETIMEOUT);
+        // let the copies still in flight land (bounded) before the CTA leaves
+        for (int k = q; k < issued; ++k) mbar_wait(smem_u32(&full[k % RING]), (uint32_t)((k / RING) & 1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// 3-D core-matrix view of a row-major [rows][K] bfloat16 matrix, box {8, box_rows, 8}
+bool encode_view(CUtensorMap *m, const void *base, long long rows, int K, int box_rows)
+{
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {8, (cuuint64_t)rows, (cuuint64_t)(K / 8)};
+    cuuint64_t strides[2] = {(cuuint64_t)K * 2, 16};
+    cuuint32_t box[3] = {8, (cuuint32_t)box_rows, 8};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
+
+// Host: tensor maps of every member's weights; false when TMA views are unavailable.
+bool mlp_tma_prepare(int h, int members, void *const *wb_host, void *maps_out)
+{
+    if (h % KC || h > HMAX || members > 4) return false;
+    CUtensorMap *mp = static_cast<CUtensorMap *>(maps_out);     // [4][4]
+    std::memset(mp, 0, sizeof(CUtensorMap) * 16);
+    for (int m = 0; m < members; ++m) {
+        const __nv_bfloat16 *w = static_cast<const __nv_bfloat16 *>(wb_host[m]);
+        const long long oW2 = (long long)h * MLSD_SUR_IN + h, oW3 = oW2 + (long long)h * h + h;
+        const long long oW4 = oW3 + (long long)h * h + h;
+        if (!encode_view(&mp[m * 4 + 0], w, h, MLSD_SUR_IN, h)) return false;
+        if (!encode_view(&mp[m * 4 + 1], w + oW2, h, h, h)) return false;
+        if (!encode_view(&mp[m * 4 + 2], w + oW3, h, h, h)) return false;
+        if (!encode_view(&mp[m * 4 + 3], w + oW4, 3, h, 16)) return false;
+    }
+    return true;
+}
+
+size_t mlp_tma_maps_bytes() { return sizeof(CUtensorMap) * 16; }
+
+cudaError_t launch_mlp_tma(const void *X, long long M, int h, int members, const void *maps,
+                           const float *const *wf_dev, float *out, int *status, cudaStream_t s)
+{
+    TmaArgs a;
+    std::memset(&a, 0, sizeof(a));
+    if (!encode_view(&a.xmap, X, M, MLSD_SUR_IN, TM)) return cudaErrorNotSupported;
+    std::memcpy(a.wmap, maps, sizeof(a.wmap));
+    a.M = M;
+    a.h = h;
+    a.members = members;
+    a.wf = wf_dev;
+    a.out = out;
+    a.status = status;
+    const size_t smem = (size_t)RING * SLOT + (size_t)TM * HMAX * 2;
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_mlp_tma),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)members);
+    count_launches(1);
+    k_mlp_tma<<<grid, 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
 
 size_t mlp_tc_smem() { return (size_t)TM * KC * 2 + (size_t)HMAX * KC * 2 + (size_t)TM * HMAX * 2; }
 

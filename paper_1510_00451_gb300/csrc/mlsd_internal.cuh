@@ -140,6 +140,11 @@ size_t mlp_tc_smem();
 bool mlp_tc_supported(int h);
 cudaError_t launch_mlp_tc(const void *X, long long M, int h, int members, const void *const *wb_dev,
                           const float *const *wf_dev, float *out, int *status, cudaStream_t s);
+// TMA-fed variant: weight tensor maps prepared once (host), X map per call
+bool mlp_tma_prepare(int h, int members, void *const *wb_host, void *maps_out);
+size_t mlp_tma_maps_bytes();
+cudaError_t launch_mlp_tma(const void *X, long long M, int h, int members, const void *maps,
+                           const float *const *wf_dev, float *out, int *status, cudaStream_t s);
 
 // Shared small device helpers ------------------------------------------------
 __host__ __device__ inline long long pmod_ll(long long a, long long m)

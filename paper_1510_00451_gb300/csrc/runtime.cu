@@ -926,6 +926,8 @@ struct mlsd_surrogate {
     float **wf_ptrs = nullptr;
     int *status = nullptr;
     int engine = MLSD_SUR_CUDA;
+    bool tma = false;                     // TMA-fed tensor-core kernel available
+    std::vector<unsigned char> maps;      // its weight tensor maps
     std::vector<void *> allocs;
 };
 
@@ -992,6 +994,10 @@ int mlsd_surrogate_create(int members, int hidden, int max_batch, mlsd_surrogate
             rc = MLSD_ECUDA;
     }
     if (!rc && mlp_tc_supported(hidden)) s->engine = MLSD_SUR_TENSOR;
+    if (!rc && !std::getenv("MLSD_NO_TMA")) {
+        s->maps.assign(mlp_tma_maps_bytes(), 0);
+        s->tma = mlp_tma_prepare(hidden, members, s->wb.data(), s->maps.data());
+    }
     if (rc) { mlsd_surrogate_free(s); return rc; }
     *out = s;
     return MLSD_OK;
@@ -1091,6 +1097,9 @@ int mlsd_surrogate_predict(mlsd_surrogate *s, const void *X_dev, int64_t M, floa
     if (!s || !X_dev || !out_dev || M < 1) return MLSD_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (s->engine == MLSD_SUR_TENSOR) {
+        if (s->tma && launch_mlp_tma(X_dev, M, s->h, s->members, s->maps.data(), s->wf_ptrs, out_dev,
+                                     s->status, st) == cudaSuccess)
+            return MLSD_OK;
         CK(launch_mlp_tc(X_dev, M, s->h, s->members, s->wb_ptrs, s->wf_ptrs, out_dev, s->status, st));
         return MLSD_OK;
     }
