@@ -1140,10 +1140,21 @@ int mlsd_solve_level_surrogate(mlsd_levels *h, mlsd_surrogate *s, int level,
     if (!rc && e == cudaSuccess) e = cudaMemcpyAsync(&count, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (!rc && e == cudaSuccess && count > 0) {
-        // the plain patch solve on the flagged patches only
+        // the plain patch solve on the flagged patches only; when they are too few to
+        // fill the GPU their serial step latency decides, so take the tiling with the
+        // most threads per patch field instead of the throughput-tuned one
         SizeClass fc = d.cls[0];
         fc.idx = idx;
         fc.count = count;
+        int sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (count < sms) {
+            std::vector<PatchVariant> vs;
+            patch_variants(fc.n, h->precision, vs);
+            for (auto &v : vs)
+                if (!v.packed && !v.split && v.cluster == 1 && v.threads > fc.variant.threads) fc.variant = v;
+        }
         PatchParams pp = patch_params(h, d, fc, K_base_dev, d.S, nullptr);
         e = launch_patch(fc.variant, pp, pp.items, st);
         if (e == cudaSuccess) e = sur_merge(count, idx, K_base_dev, d.S, K_out_dev, st);
