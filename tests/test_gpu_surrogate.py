@@ -124,10 +124,11 @@ def test_surrogate_level_fallback_paths(mlsd, torch_mod):
     sur = mlsd.Surrogate(members=4, hidden=64, max_batch=64)
     for m in range(4):
         sur.set_params(m, inputs.mlp_init(mlsd.SUR_IN, 64, m))
-    # threshold 0: every patch falls back -> exactly the plain result
+    # threshold 0: every patch falls back -> the plain result (a few fallback patches
+    # run the lowest-latency tiling, so only the order of the flux sums may differ)
     K0 = torch_mod.zeros_like(B)
     assert lv.solve_level_surrogate(sur, 2, B, K0, 0.0) == N * N
-    assert torch_mod.equal(K0, K_plain)
+    assert rel_l2(K0.cpu().numpy(), K_plain.cpu().numpy()) < 1e-6
     # huge threshold: no fallback, K = B + tr(B) * ensemble mean
     K1 = torch_mod.zeros_like(B)
     assert lv.solve_level_surrogate(sur, 2, B, K1, 1e30) == 0
