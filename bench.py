@@ -36,7 +36,13 @@ import numpy as np  # noqa: E402
 
 METRIC = "K_eff tensors/s & patch cell-updates/s, surrogate vs plain GPU at ≤1e-3 K_eff err"
 UNIT = "cell-updates/s"
-FLOP_PER_CELL_UPDATE = 40      # two Heun stages (17 + 19 FLOP) + two flux products (4 FLOP)
+# Algorithmic FP32 work of k_patch_solve.  Per cell-update (one cell of one field,
+# one full Heun step): stage 1 = 4 FADD + 6 FFMA, stage 2 = 4 FADD + 7 FFMA.
+# Per cell-update inside the averaging window, add the flux sums: 2 FFMA + 1 FADD.
+OPS_PER_CELL_UPDATE = 21       # FP32-pipe instructions
+OPS_PER_WINDOW_UPDATE = 3
+FLOP_PER_CELL_UPDATE = 34
+FLOP_PER_WINDOW_UPDATE = 5
 WORKLOAD = "three_level_cellular"
 
 
@@ -265,8 +271,37 @@ def uneven_case(n_avg=32):
             "cell_updates_per_s": cu / t, "seconds": t, "cell_updates": cu,
             "k_eff_tensors_per_s": N * N / t, "setup_s": t_setup, "sizes_per_level": hist,
             "largest_class_tiling": [f"{i['tile_bx']}x{i['tile_by']} c{i['cluster']} m{i['min_ctas']}"
-                                     f"{' packed' if i['packed'] else ''} n={i['n']}" for i in tiles],
+                                     f"{' packed' if i['packed'] else ''}{' split' if i['split'] else ''}"
+                                     f" n={i['n']}" for i in tiles],
             "finite": bool(torch.isfinite(K).all().item())}
+
+
+def cluster_case(N=32, n_burn=32, n_avg=32):
+    """The first octave level of the continuous-spectrum flow with 256^2 patches
+    (each field split over a thread-block cluster) on an N x N macro grid, fixed
+    window: the launch shape of the largest size class, small enough to profile."""
+    import torch
+    import inputs
+    import paper_1510_00451_gb300 as mlsd
+    cfg = inputs.config_problem("continuous_spectrum")
+    lv = mlsd.Levels(cfg["spectrum"], cfg["kappa"], N, cfg["edges"][:2], [256], cfl=cfg["cfl"],
+                     n_burn_fixed=n_burn, n_avg_fixed=n_avg)
+    K = torch.zeros(N * N, 3, dtype=torch.float64, device=torch.device("cuda", _local_rank()))
+    lv.effective_diffusivity(K)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream); lv.effective_diffusivity(K); e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    rc = lv.status()
+    cu = lv.level_work(1)[0]
+    i = lv.info(1)
+    print(json.dumps({"case": "cluster-profile", "status": rc, "cell_updates_per_s": cu / t,
+                      "seconds": t, "tiling": f"{i['tile_bx']}x{i['tile_by']} c{i['cluster']} "
+                      f"m{i['min_ctas']}{' split' if i['split'] else ''}",
+                      "finite": bool(torch.isfinite(K).all().item())}), flush=True)
+    return 0 if rc == 0 else 1
 
 
 def mlp_case(M=65536, members=4, hidden=256):
@@ -356,7 +391,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--case", default="full",
-                    choices=["full", "profile", "dns-profile", "surrogate", "uneven", "mlp-profile"],
+                    choices=["full", "profile", "dns-profile", "surrogate", "uneven", "mlp-profile",
+                             "cluster-profile"],
                     help="profile: one pass of the same workload with a fixed 200-step window "
                          "per patch (a small case for ncu captures); prints no bench line")
     args = ap.parse_args()
@@ -371,6 +407,8 @@ def main():
         return 0
     if args.case == "mlp-profile":
         return mlp_case()
+    if args.case == "cluster-profile":
+        return cluster_case()
     if args.case == "uneven":
         print(json.dumps({"case": "uneven", **uneven_case()}), flush=True)
         return 0
@@ -412,8 +450,9 @@ def main():
     for _ in range(args.warmup):
         step()
     assert lv.status() == 0
-    work = [lv.level_work(l + 1)[0] for l in range(L)]
-    cell_updates = sum(work)
+    work = [lv.level_work(l + 1) for l in range(L)]
+    cell_updates = sum(w[0] for w in work)
+    window_updates = sum(w[2] for w in work)
 
     # ---- timed region: K steps, device time per step (L2 flushed between steps)
     clk_path = tempfile.mktemp(prefix="mlsd_clocks_", suffix=".csv")
@@ -440,11 +479,14 @@ def main():
         sampler.terminate(); sampler.wait()
     clocks = _clock_summary(clk_path)
     ms_step = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    kern_ms, kern_n, kern_flop = 0.0, 0, 0.0
+    kern_ms, kern_n = 0.0, 0
     for l in range(L):
         ms, n = lv.profile_collect(l + 1)
         kern_ms += ms; kern_n += n
-        kern_flop += n * work[l] * FLOP_PER_CELL_UPDATE
+    kern_ops = args.steps * (cell_updates * OPS_PER_CELL_UPDATE
+                             + window_updates * OPS_PER_WINDOW_UPDATE)
+    kern_flop = args.steps * (cell_updates * FLOP_PER_CELL_UPDATE
+                              + window_updates * FLOP_PER_WINDOW_UPDATE)
     assert lv.status() == 0
     t_max = torch.tensor([ms_step], dtype=torch.float64, device=dev)
     if world > 1:
@@ -509,8 +551,10 @@ def main():
     peaks = _peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA at max clock
-    achieved = kern_flop / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
+    issue_peak = sm_count * 128 * sm_max * 1e6 / 1e12             # T FP32 instructions/s
+    flop_peak = 2 * issue_peak                                     # TFLOP/s, all FFMA
+    achieved = kern_ops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
+    achieved_flop = kern_flop / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         import oracle
@@ -533,11 +577,20 @@ def main():
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "k_eff_tensors_per_s": tensors,
         "cell_updates_per_step": cell_updates * world,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
+                     "unit": "T FP32-pipe instructions/s",
+                     "frac": (achieved / issue_peak) if achieved else None, "traffic": None,
                      "kernel": "k_patch_solve", "launches": kern_n,
                      "kernel_ms_per_step": kern_ms / args.steps,
-                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {sm_max:.0f} MHz"},
+                     "algorithmic": f"{OPS_PER_CELL_UPDATE} FP32 FADD/FMUL/FFMA per cell-update "
+                                    f"+ {OPS_PER_WINDOW_UPDATE} per averaging-window cell-update",
+                     "window_fraction": window_updates / cell_updates,
+                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz, one "
+                                   "FADD/FMUL/FFMA per lane per clock",
+                     "flop": {"achieved": achieved_flop, "peak": flop_peak, "unit": "TFLOP/s",
+                              "frac": (achieved_flop / flop_peak) if achieved_flop else None,
+                              "per_cell_update": f"{FLOP_PER_CELL_UPDATE} + {FLOP_PER_WINDOW_UPDATE}"
+                                                 " in the window"}},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,

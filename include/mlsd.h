@@ -314,9 +314,13 @@ int mlsd_coarse_grain_noalloc(int nf, const float *u_dev, int n_macro, float *U_
 /* Work done by the last solve of a level (mlsd_solve_level or the level's part
  * of mlsd_effective_diffusivity): cell_updates = sum over patches and the two
  * fields of n^2 (n_burn + n_avg) (one cell of one field advanced one full RK2
- * step), and the largest per-patch step count.  Synchronises the stream.     */
+ * step), the part of it inside the averaging window (sum of n^2 n_avg over
+ * patches and fields: the updates that also add to the flux sums), and the
+ * largest per-patch step count.  Any out pointer may be NULL.  Synchronises
+ * the stream.                                                               */
 int mlsd_level_work(mlsd_levels *h, int level, int64_t *cell_updates_out,
-                    int64_t *max_steps_out, void *cuda_stream);
+                    int64_t *window_updates_out, int64_t *max_steps_out,
+                    void *cuda_stream);
 
 /* Kernel timing of the patch solves: when enabled, every patch-solve launch of
  * the handle is bracketed by CUDA events recorded on the launching stream.

@@ -80,7 +80,7 @@ _lib.mlsd_macro_dt.argtypes = [_I, _P, _D, ctypes.POINTER(_D), _P]
 _lib.mlsd_grid_psi.argtypes = [_I, _P, _P, _P, _P, _I, _P, _P]
 _lib.mlsd_dns_run.argtypes = [_I, _P, _P, _P, _D, _D, _I, _P]
 _lib.mlsd_coarse_grain.argtypes = [_I, _P, _I, _P, _P, _P]
-_lib.mlsd_level_work.argtypes = [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_L), _P]
+_lib.mlsd_level_work.argtypes = [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_L), ctypes.POINTER(_L), _P]
 _lib.mlsd_profile.argtypes = [_P, _I]
 _lib.mlsd_profile_collect.argtypes = [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_L)]
 _lib.mlsd_launch_count.argtypes = []
@@ -214,11 +214,12 @@ class Levels:
         return _lib.mlsd_status(self.h, _stream(stream))
 
     def level_work(self, level, stream=None):
-        """(cell-updates, max steps per patch) of the level's last solve."""
-        cu, ms = _L(), _L()
-        _check(_lib.mlsd_level_work(self.h, int(level), ctypes.byref(cu), ctypes.byref(ms),
-                                    _stream(stream)), "mlsd_level_work")
-        return cu.value, ms.value
+        """(cell-updates, max steps per patch, cell-updates inside the averaging
+        window) of the level's last solve."""
+        cu, wu, ms = _L(), _L(), _L()
+        _check(_lib.mlsd_level_work(self.h, int(level), ctypes.byref(cu), ctypes.byref(wu),
+                                    ctypes.byref(ms), _stream(stream)), "mlsd_level_work")
+        return cu.value, ms.value, wu.value
 
 
     def profile(self, enable=True):

@@ -27,7 +27,7 @@ struct PatchParams {
     long long nb_fixed, na_fixed;
     long long P;             // patches
     long long item0, items;  // work items [item0, item0 + items), item = 2p + (j - 1)
-    long long *steps;        // [P] n_burn + n_avg per patch (written by the j = 1 CTA) or nullptr
+    long long *steps;        // [2P]: n_burn + n_avg, then n_avg, per patch (written by the j = 1 CTA) or nullptr
     const int *pidx;         // patch index of work-item pair (item >> 1), or nullptr: identity
 };
 

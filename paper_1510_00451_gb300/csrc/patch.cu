@@ -151,6 +151,14 @@ __device__ __forceinline__ T *rank_ptr(T *p, int r)
     else return cg::this_cluster().map_shared_rank(p, r);
 }
 
+// Uniform coefficients of one stage, from dt, h and the base tensor B:
+// b_ii = dt B_ii / h^2, bx = dt B12 / (2 h^2), bc = 1 - 2 (b11 + b22), and the
+// constant part K = -2h b_JJ of the source term of field J.
+template <typename real>
+struct Coef {
+    real b11x2, b22x2, bx, bc, twoh, K, halfK;
+};
+
 template <int N, int C, int BX, int BY, typename real>
 struct Tile {
     using S = Smem<N, C, BX, BY, real>;
@@ -224,15 +232,19 @@ struct Tile {
         }
     }
 
-    // Exchange the edges of x through buffer `buf`, then form
-    //   g = bc x + b11 (xE + xW) + b22 (xN + xS) + A1 (xE - xW [+2h]) + A2 (xN - xS [+2h])
-    //       + bx (dEW(b+1) - dEW(b-1)),
-    // i.e. x + dt f(x); SECOND: out = (w + g) / 2, else out = g.
+    // Exchange the edges of x through buffer `buf`, then form x + dt f(x),
+    //   bc x + b11 (xE + xW) + b22 (xN + xS) + A1 (xE - xW) + A2 (xN - xS)
+    //      + 2h A_J + bx (dEW(b+1) - dEW(b-1)),
+    // with the per-cell coefficients aE = A1 + b11, aN = A2 + b22 (Coef):
+    //   aE (xE - xW) + 2 b11 xW = A1 (xE - xW) + b11 (xE + xW), likewise in x2, and
+    //   the source 2h A_J = 2h a_J - 2h b_JJ, whose constant part is Coef::K.
+    // Ten FP32 instructions per cell.  SECOND: out = (w + g) / 2, with w (held in
+    // out) seeding the FMA chain and K / 2 added by the final FMA.
     template <int J, bool SECOND>
     __device__ __forceinline__ static void stage(real *sm, int buf, int rank, int tx, int ty,
                                                  const real (&x)[BY][BX], real (&out)[BY][BX],
-                                                 const real (&A1)[BY][BX], const real (&A2)[BY][BX],
-                                                 real b11, real b22, real bx, real bc, real twoh)
+                                                 const real (&aE)[BY][BX], const real (&aN)[BY][BX],
+                                                 const Coef<real> &k)
     {
         publish_edges(sm, buf, rank, tx, ty, x);
         tile_sync<C>();
@@ -271,23 +283,32 @@ struct Tile {
                 const real xW = (c > 0) ? x[r][c - 1] : hW[r + 1];
                 const real xN = (r + 1 < BY) ? x[r + 1][c] : hN[c];
                 const real xS = (r > 0) ? x[r - 1][c] : hS[c];
-                real d1 = d0[c];
-                real d2 = xN - xS;
-                if constexpr (J == 1) d1 = d1 + twoh; else d2 = d2 + twoh;
-                const real s1 = xE + xW, s2 = xN + xS;
-                const real cr = dp[c] - dm[c];
-                real g = A1[r][c] * d1;
-                g = fma(A2[r][c], d2, g);
-                g = fma(b11, s1, g);
-                g = fma(b22, s2, g);
-                g = fma(bx, cr, g);
-                g = fma(bc, xc, g);
-                if constexpr (SECOND) out[r][c] = (real)0.5 * (out[r][c] + g);
-                else out[r][c] = g;
+                (void)xE;
+                cell<J, SECOND>(out[r][c], xc, xW, xN, xS, d0[c], dm[c], dp[c], aE[r][c],
+                                aN[r][c], k);
             }
 #pragma unroll
             for (int c = 0; c < BX; ++c) { dm[c] = d0[c]; d0[c] = dp[c]; }
         }
+    }
+
+    // One cell of a stage (see stage()): dEW = xE - xW of this row, dm / dp those
+    // of the rows below / above; o holds w on entry when SECOND.
+    template <int J, bool SECOND>
+    __device__ __forceinline__ static void cell(real &o, real xc, real xW, real xN, real xS,
+                                                real dEW, real dm, real dp, real aE, real aN,
+                                                const Coef<real> &k)
+    {
+        real d1 = dEW, d2 = xN - xS;
+        if constexpr (J == 1) d1 = d1 + k.twoh; else d2 = d2 + k.twoh;
+        const real cr = dp - dm;
+        real g = fma(aE, d1, SECOND ? o : k.K);
+        g = fma(k.b11x2, xW, g);
+        g = fma(aN, d2, g);
+        g = fma(k.b22x2, xS, g);
+        g = fma(k.bx, cr, g);
+        g = fma(k.bc, xc, g);
+        o = SECOND ? fma(g, (real)0.5, k.halfK) : g;
     }
 
     // Split-phase stage.  On entry x's edges are in buffer `buf` and this thread
@@ -295,30 +316,13 @@ struct Tile {
     // computed while the barrier completes; then the halos are read and the
     // boundary ring is computed; finally out's edges go to buffer buf ^ 1 and
     // the thread arrives for the next stage.
-    __device__ __forceinline__ static void cell(real &o, real w_old, real xc, real xE, real xW,
-                                                real xN, real xS, real dEW, real dm, real dp,
-                                                real a1, real a2, real b11, real b22, real bx,
-                                                real bc, real twoh, int J, bool second)
-    {
-        real d1 = dEW, d2 = xN - xS;
-        if (J == 1) d1 = d1 + twoh; else d2 = d2 + twoh;
-        const real s1 = xE + xW, s2 = xN + xS, cr = dp - dm;
-        real g = a1 * d1;
-        g = fma(a2, d2, g);
-        g = fma(b11, s1, g);
-        g = fma(b22, s2, g);
-        g = fma(bx, cr, g);
-        g = fma(bc, xc, g);
-        o = second ? (real)0.5 * (w_old + g) : g;
-    }
 
     template <int J, bool SECOND>
     __device__ __forceinline__ static void stage_split(real *sm, int buf, int rank, int tx, int ty,
                                                        const real (&x)[BY][BX], real (&out)[BY][BX],
-                                                       const real (&A1)[BY][BX], const real (&A2)[BY][BX],
-                                                       real b11, real b22, real bx, real bc, real twoh)
+                                                       const real (&aE)[BY][BX], const real (&aN)[BY][BX],
+                                                       const Coef<real> &k)
     {
-        const int a0 = tx * BX, b0 = ty * BY;
         // ---- interior: rows 1..BY-2, columns 1..BX-2 (rolling E-W differences) ----
         {
             real dm[BX], d0[BX], dp[BX];
@@ -330,9 +334,8 @@ struct Tile {
                 for (int c = 1; c < BX - 1; ++c) dp[c] = x[r + 1][c + 1] - x[r + 1][c - 1];
 #pragma unroll
                 for (int c = 1; c < BX - 1; ++c)
-                    cell(out[r][c], out[r][c], x[r][c], x[r][c + 1], x[r][c - 1], x[r + 1][c],
-                         x[r - 1][c], d0[c], dm[c], dp[c], A1[r][c], A2[r][c], b11, b22, bx, bc,
-                         twoh, J, SECOND);
+                    cell<J, SECOND>(out[r][c], x[r][c], x[r][c - 1], x[r + 1][c], x[r - 1][c],
+                                    d0[c], dm[c], dp[c], aE[r][c], aN[r][c], k);
 #pragma unroll
                 for (int c = 1; c < BX - 1; ++c) { dm[c] = d0[c]; d0[c] = dp[c]; }
             }
@@ -353,18 +356,16 @@ struct Tile {
             const int r = e == 0 ? 0 : BY - 1;
 #pragma unroll
             for (int c = 0; c < BX; ++c)
-                cell(out[r][c], out[r][c], x[r][c], X(r, c + 1), X(r, c - 1), X(r + 1, c), X(r - 1, c),
-                     D(r, c), D(r - 1, c), D(r + 1, c), A1[r][c], A2[r][c], b11, b22, bx, bc, twoh,
-                     J, SECOND);
+                cell<J, SECOND>(out[r][c], x[r][c], X(r, c - 1), X(r + 1, c), X(r - 1, c), D(r, c),
+                                D(r - 1, c), D(r + 1, c), aE[r][c], aN[r][c], k);
         }
 #pragma unroll
         for (int r = 1; r < BY - 1; ++r)
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int c = e == 0 ? 0 : BX - 1;
-                cell(out[r][c], out[r][c], x[r][c], X(r, c + 1), X(r, c - 1), X(r + 1, c), X(r - 1, c),
-                     D(r, c), D(r - 1, c), D(r + 1, c), A1[r][c], A2[r][c], b11, b22, bx, bc, twoh,
-                     J, SECOND);
+                cell<J, SECOND>(out[r][c], x[r][c], X(r, c - 1), X(r + 1, c), X(r - 1, c), D(r, c),
+                                D(r - 1, c), D(r + 1, c), aE[r][c], aN[r][c], k);
             }
         publish_edges(sm, buf ^ 1, rank, tx, ty, out);
         asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
@@ -438,17 +439,26 @@ struct Tile {
             if constexpr (C > 1) tile_sync<C>();   // no rank leaves while others read its slot
             return;
         }
-        if (J == 1 && tid == 0 && rank == 0 && prm.steps) prm.steps[p] = nb + na;
+        if (J == 1 && tid == 0 && rank == 0 && prm.steps) { prm.steps[p] = nb + na; prm.steps[prm.P + p] = na; }
         const double hh = prm.h * prm.h;
         const real cA = (real)(dt / (2.0 * prm.h));
         const real b11 = (real)(dt * B11 / hh), b22 = (real)(dt * B22 / hh);
-        const real bx = (real)(dt * B12 / (2.0 * hh));
-        const real bc = (real)(1.0 - 2.0 * (dt * B11 / hh + dt * B22 / hh));
-        const real twoh = (real)(2.0 * prm.h);
+        Coef<real> k;
+        k.b11x2 = (real)2 * b11;
+        k.b22x2 = (real)2 * b22;
+        k.bx = (real)(dt * B12 / (2.0 * hh));
+        k.bc = (real)(1.0 - 2.0 * (dt * B11 / hh + dt * B22 / hh));
+        k.twoh = (real)(2.0 * prm.h);
+        k.K = -k.twoh * (J == 1 ? b11 : b22);
+        k.halfK = (real)0.5 * k.K;
+        // A1, A2 become aE = A1 + b11, aN = A2 + b22 (A_i = dt v_i / 2h)
 #pragma unroll
         for (int r = 0; r < BY; ++r)
 #pragma unroll
-            for (int c = 0; c < BX; ++c) { A1[r][c] *= cA; A2[r][c] *= cA; }
+            for (int c = 0; c < BX; ++c) {
+                A1[r][c] = fma(A1[r][c], cA, b11);
+                A2[r][c] = fma(A2[r][c], cA, b22);
+            }
         tile_sync<C>();   // psi tile (and the vmax slots) are dead; the space becomes the exchange buffers
 
         // ---- time stepping ------------------------------------------------
@@ -457,7 +467,8 @@ struct Tile {
         for (int r = 0; r < BY; ++r)
 #pragma unroll
             for (int c = 0; c < BX; ++c) w[r][c] = 0;
-        real p1 = 0, p2 = 0;
+        // flux sums: sum (A_i + b_ii) w = sum A_i w + b_ii sum w, so sum w is kept too
+        real p1 = 0, p2 = 0, pw = 0;
         double f1 = 0.0, f2 = 0.0;
         int win = 0;
         const long long ntot = nb + na;
@@ -467,28 +478,34 @@ struct Tile {
         }
         for (long long step = 0; step < ntot; ++step) {
             if constexpr (SPLIT) {
-                stage_split<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, b11, b22, bx, bc, twoh);
-                stage_split<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, b11, b22, bx, bc, twoh);
+                stage_split<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, k);
+                stage_split<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, k);
             } else {
-                stage<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, b11, b22, bx, bc, twoh);
-                stage<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, b11, b22, bx, bc, twoh);
+                stage<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, k);
+                stage<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, k);
             }
             if (step >= nb) {
-                real q1 = 0, q2 = 0;
+                real q1 = 0, q2 = 0, qw = 0;
 #pragma unroll
                 for (int r = 0; r < BY; ++r)
 #pragma unroll
                     for (int c = 0; c < BX; ++c) {
                         q1 = fma(A1[r][c], w[r][c], q1);
                         q2 = fma(A2[r][c], w[r][c], q2);
+                        qw += w[r][c];
                     }
                 p1 += q1;
                 p2 += q2;
-                if (++win == kFlush) { f1 += (double)p1; f2 += (double)p2; p1 = 0; p2 = 0; win = 0; }
+                pw += qw;
+                if (++win == kFlush) {
+                    f1 += (double)p1 - (double)b11 * (double)pw;
+                    f2 += (double)p2 - (double)b22 * (double)pw;
+                    p1 = 0; p2 = 0; pw = 0; win = 0;
+                }
             }
         }
-        f1 += (double)p1;
-        f2 += (double)p2;
+        f1 += (double)p1 - (double)b11 * (double)pw;
+        f2 += (double)p2 - (double)b22 * (double)pw;
         if constexpr (SPLIT) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 
         // ---- outputs ------------------------------------------------------
@@ -617,9 +634,9 @@ struct Tile2 {
     template <bool SECOND>
     __device__ __forceinline__ static void stage(float2 *sm, int buf, int tx, int ty,
                                                  const float2 (&x)[BY][BX], float2 (&out)[BY][BX],
-                                                 const float2 (&A1)[BY][BX], const float2 (&A2)[BY][BX],
-                                                 float2 b11, float2 b22, float2 bx, float2 bc,
-                                                 float2 T1, float2 T2)
+                                                 const float2 (&aE)[BY][BX], const float2 (&aN)[BY][BX],
+                                                 float2 b11x2, float2 b22x2, float2 bx, float2 bc,
+                                                 float2 T1, float2 T2, float2 K, float2 halfK)
     {
         const int a0 = tx * BX, b0 = ty * BY;
         float2 *rowT = sm + buf * S::STAGE;
@@ -687,18 +704,20 @@ struct Tile2 {
                 const float2 xW = (c > 0) ? x[r][c - 1] : hW[r + 1];
                 const float2 xN = (r + 1 < BY) ? x[r + 1][c] : hN[c];
                 const float2 xS = (r > 0) ? x[r - 1][c] : hS[c];
+                (void)xE;
+                // the scalar kernel's cell (Tile::cell) on both fields at once; the
+                // sources differ per lane: T1 = (2h, 0), T2 = (0, 2h), K = -2h (b11, b22)
                 const float2 d1 = __fadd2_rn(d0[c], T1);
                 const float2 d2 = __fadd2_rn(sub2(xN, xS), T2);
-                const float2 s1 = __fadd2_rn(xE, xW), s2 = __fadd2_rn(xN, xS);
                 const float2 cr = sub2(dp[c], dm[c]);
-                float2 g = __fmul2_rn(A1[r][c], d1);
-                g = __ffma2_rn(A2[r][c], d2, g);
-                g = __ffma2_rn(b11, s1, g);
-                g = __ffma2_rn(b22, s2, g);
+                float2 g = __ffma2_rn(aE[r][c], d1, SECOND ? out[r][c] : K);
+                g = __ffma2_rn(b11x2, xW, g);
+                g = __ffma2_rn(aN[r][c], d2, g);
+                g = __ffma2_rn(b22x2, xS, g);
                 g = __ffma2_rn(bx, cr, g);
                 g = __ffma2_rn(bc, xc, g);
                 if constexpr (SECOND)
-                    out[r][c] = __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(out[r][c], g));
+                    out[r][c] = __ffma2_rn(g, make_float2(0.5f, 0.5f), halfK);
                 else
                     out[r][c] = g;
             }
@@ -758,22 +777,25 @@ struct Tile2 {
             }
             return;
         }
-        if (tid == 0 && prm.steps) prm.steps[p] = nb + na;
+        if (tid == 0 && prm.steps) { prm.steps[p] = nb + na; prm.steps[prm.P + p] = na; }
         const double hh = prm.h * prm.h;
         const float cA = (float)(dt / (2.0 * prm.h));
         const float fb11 = (float)(dt * B11 / hh), fb22 = (float)(dt * B22 / hh);
         const float fbx = (float)(dt * B12 / (2.0 * hh));
         const float fbc = (float)(1.0 - 2.0 * (dt * B11 / hh + dt * B22 / hh));
         const float twoh = (float)(2.0 * prm.h);
-        const float2 b11 = make_float2(fb11, fb11), b22 = make_float2(fb22, fb22);
+        const float2 b11x2 = make_float2(2.f * fb11, 2.f * fb11), b22x2 = make_float2(2.f * fb22, 2.f * fb22);
         const float2 bx = make_float2(fbx, fbx), bc = make_float2(fbc, fbc);
         const float2 T1 = make_float2(twoh, 0.f), T2 = make_float2(0.f, twoh);
+        const float2 K = make_float2(-twoh * fb11, -twoh * fb22);
+        const float2 halfK = make_float2(0.5f * K.x, 0.5f * K.y);
+        // aE = A1 + b11, aN = A2 + b22 with A_i = dt v_i / 2h
         float2 A1[BY][BX], A2[BY][BX];
 #pragma unroll
         for (int r = 0; r < BY; ++r)
 #pragma unroll
             for (int c = 0; c < BX; ++c) {
-                const float a1 = v1r[r][c] * cA, a2 = v2r[r][c] * cA;
+                const float a1 = fmaf(v1r[r][c], cA, fb11), a2 = fmaf(v2r[r][c], cA, fb22);
                 A1[r][c] = make_float2(a1, a1);
                 A2[r][c] = make_float2(a2, a2);
             }
@@ -784,31 +806,38 @@ struct Tile2 {
         for (int r = 0; r < BY; ++r)
 #pragma unroll
             for (int c = 0; c < BX; ++c) w[r][c] = make_float2(0.f, 0.f);
-        float2 p1 = make_float2(0.f, 0.f), p2 = make_float2(0.f, 0.f);
-        double f11 = 0.0, f12 = 0.0, f21 = 0.0, f22 = 0.0;   // f_ij ~ sum A_i w_j
+        // f_ij ~ sum A_i w_j = sum (A_i + b_ii) w_j - b_ii sum w_j
+        float2 p1 = make_float2(0.f, 0.f), p2 = make_float2(0.f, 0.f), pw = make_float2(0.f, 0.f);
+        double f11 = 0.0, f12 = 0.0, f21 = 0.0, f22 = 0.0;
+        const double db11 = (double)fb11, db22 = (double)fb22;
         int win = 0;
         const long long ntot = nb + na;
         for (long long step = 0; step < ntot; ++step) {
-            stage<false>(sm, 0, tx, ty, w, st, A1, A2, b11, b22, bx, bc, T1, T2);
-            stage<true>(sm, 1, tx, ty, st, w, A1, A2, b11, b22, bx, bc, T1, T2);
+            stage<false>(sm, 0, tx, ty, w, st, A1, A2, b11x2, b22x2, bx, bc, T1, T2, K, halfK);
+            stage<true>(sm, 1, tx, ty, st, w, A1, A2, b11x2, b22x2, bx, bc, T1, T2, K, halfK);
             if (step >= nb) {
-                float2 q1 = make_float2(0.f, 0.f), q2 = make_float2(0.f, 0.f);
+                float2 q1 = make_float2(0.f, 0.f), q2 = make_float2(0.f, 0.f), qw = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int r = 0; r < BY; ++r)
 #pragma unroll
                     for (int c = 0; c < BX; ++c) {
                         q1 = __ffma2_rn(A1[r][c], w[r][c], q1);
                         q2 = __ffma2_rn(A2[r][c], w[r][c], q2);
+                        qw = __fadd2_rn(qw, w[r][c]);
                     }
                 p1 = __fadd2_rn(p1, q1);
                 p2 = __fadd2_rn(p2, q2);
+                pw = __fadd2_rn(pw, qw);
                 if (++win == kFlush) {
-                    f11 += (double)p1.x; f12 += (double)p1.y; f21 += (double)p2.x; f22 += (double)p2.y;
-                    p1 = make_float2(0.f, 0.f); p2 = make_float2(0.f, 0.f); win = 0;
+                    f11 += (double)p1.x - db11 * pw.x; f12 += (double)p1.y - db11 * pw.y;
+                    f21 += (double)p2.x - db22 * pw.x; f22 += (double)p2.y - db22 * pw.y;
+                    p1 = make_float2(0.f, 0.f); p2 = make_float2(0.f, 0.f); pw = make_float2(0.f, 0.f);
+                    win = 0;
                 }
             }
         }
-        f11 += (double)p1.x; f12 += (double)p1.y; f21 += (double)p2.x; f22 += (double)p2.y;
+        f11 += (double)p1.x - db11 * pw.x; f12 += (double)p1.y - db11 * pw.y;
+        f21 += (double)p2.x - db22 * pw.x; f22 += (double)p2.y - db22 * pw.y;
 
         if (prm.wdump) {
             float *wd = static_cast<float *>(prm.wdump) + 2 * p * (long long)N * N;

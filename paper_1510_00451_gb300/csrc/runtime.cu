@@ -58,7 +58,7 @@ struct DevLevel {
     int *np_dev = nullptr;      // [P] on the device when sizes are mixed, else nullptr
     double *q12 = nullptr, *q21 = nullptr;   // [P][nq] or null
     double *B = nullptr, *Koff = nullptr, *base = nullptr, *S = nullptr, *Kstar = nullptr;
-    long long *steps = nullptr; // [P] n_burn + n_avg of the last solve
+    long long *steps = nullptr; // [2P] n_burn + n_avg, then n_avg, of the last solve
     std::vector<SizeClass> cls; // largest total work first
     cudaEvent_t fork = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;   // profiling: one pair per launch
@@ -387,8 +387,8 @@ int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
         if ((rc = dev_alloc(h, (void **)&d.base, (size_t)h->P * 3 * 8))) return rc;
         if ((rc = dev_alloc(h, (void **)&d.Kstar, (size_t)h->P * 3 * 8))) return rc;
         if ((rc = dev_alloc(h, (void **)&d.S, (size_t)h->P * 4 * 8))) return rc;
-        if ((rc = dev_alloc(h, (void **)&d.steps, (size_t)h->P * 8))) return rc;
-        CK(cudaMemsetAsync(d.steps, 0, (size_t)h->P * 8, s));
+        if ((rc = dev_alloc(h, (void **)&d.steps, (size_t)h->P * 16))) return rc;
+        CK(cudaMemsetAsync(d.steps, 0, (size_t)h->P * 16, s));
         for (auto &c : d.cls)
             if ((rc = tune_class(h, d, c, s))) return rc;
     }
@@ -750,19 +750,22 @@ int mlsd_status(mlsd_levels *h, void *cuda_stream)
 }
 
 int mlsd_level_work(mlsd_levels *h, int level, int64_t *cell_updates_out,
-                    int64_t *max_steps_out, void *cuda_stream)
+                    int64_t *window_updates_out, int64_t *max_steps_out, void *cuda_stream)
 {
     if (!h || level < 1 || level > h->L) return MLSD_EINVAL;
     const DevLevel &d = h->lev[level - 1];
-    std::vector<long long> st((size_t)h->P);
+    std::vector<long long> st((size_t)h->P * 2);
     CK(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
-    CK(cudaMemcpy(st.data(), d.steps, (size_t)h->P * 8, cudaMemcpyDeviceToHost));
-    long long tot = 0, mx = 0;
+    CK(cudaMemcpy(st.data(), d.steps, (size_t)h->P * 16, cudaMemcpyDeviceToHost));
+    long long tot = 0, win = 0, mx = 0;
     for (long long q = 0; q < h->P; ++q) {
-        tot += st[q] * 2 * (long long)d.np[q] * d.np[q];
+        const long long cells = 2 * (long long)d.np[q] * d.np[q];
+        tot += st[q] * cells;
+        win += st[h->P + q] * cells;
         mx = std::max(mx, st[q]);
     }
     if (cell_updates_out) *cell_updates_out = tot;
+    if (window_updates_out) *window_updates_out = win;
     if (max_steps_out) *max_steps_out = mx;
     return MLSD_OK;
 }

@@ -79,5 +79,7 @@ def test_explicit_size_map_parity():
     for p in range(P):
         assert rel_l2(K[p], want[p]) < 1e-4
     # the work count follows the per-patch sizes
-    cu, ms = lv.level_work(1)
+    cu, ms, wu = lv.level_work(1)
     assert cu == sum(2 * int(n) ** 2 * 140 for n in nmap[0])
+    assert wu == sum(2 * int(n) ** 2 * 60 for n in nmap[0])
+    assert ms == 140
