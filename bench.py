@@ -371,10 +371,18 @@ def profile_case():
                      cfl=cfg["cfl"], n_burn_fixed=100, n_avg_fixed=100, precision=cfg["precision"])
     K = torch.zeros(N * N, 3, dtype=torch.float64, device="cuda:0")
     lv.effective_diffusivity(K)
-    rc = lv.status()
     torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream); lv.effective_diffusivity(K); e1.record(stream)
+    torch.cuda.synchronize()
+    rc = lv.status()
     work = sum(lv.level_work(l + 1)[0] for l in range(len(cfg["patch_n"])))
+    i = lv.info(1)
     print(json.dumps({"case": "profile", "status": rc, "cell_updates": work,
+                      "cell_updates_per_s": work / (e0.elapsed_time(e1) * 1e-3),
+                      "tiling": f"{i['tile_bx']}x{i['tile_by']} m{i['min_ctas']}"
+                                f"{' packed' if i['packed'] else ''}{' split' if i['split'] else ''}",
                       "K0": K[0].tolist()}), flush=True)
     return 0 if rc == 0 else 1
 

@@ -103,8 +103,11 @@ typedef struct {
     int packed;                /* 1: one CTA per patch, both fields in f32x2 pairs; 0: one per field */
     int cluster;               /* CTAs (a thread-block cluster) sharing one patch field, in row slabs */
     int min_ctas;              /* register cap of the kernel: at least this many CTAs per SM */
-    int split;                 /* 1: split-phase stage barriers (interior cells computed while the
-                                  barrier completes) */
+    int split;                 /* stage synchronisation: 0 one barrier per stage (cluster-wide
+                                  when cluster > 1); 1 split-phase barriers (interior cells
+                                  computed while the barrier completes); 2 neighbour signalling
+                                  (cluster > 1: a CTA barrier, and mbarrier arrivals from the two
+                                  neighbouring slabs for the halo rows they push) */
     int n_classes;             /* patch sizes in the level; n, Nl, h and the tile fields describe
                                   the class with the most work; all classes run concurrently */
 } mlsd_level_desc;
@@ -117,10 +120,11 @@ typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and 
  * Set-up also picks the thread-block tiling of the patch kernel per patch
  * size: every compiled candidate is timed on a sample of the level's patches
  * (a short fixed window) and the fastest is kept for the process; the
- * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][c<cluster>][p][s]
+ * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][c<cluster>][p][s|n]
  * forces one where it exists for the level's patch size (p: the packed kernel
  * that advances both fields of a patch in f32x2 pairs; c: CTAs per patch field;
- * s: split-phase stage barriers).
+ * s: split-phase stage barriers; n: neighbour signalling between the slabs of
+ * a cluster instead of a cluster-wide barrier).
  * Patch sizes 32 and 64 run one CTA per field (or per patch, packed); 128 and
  * 256 split each field over a thread-block cluster of 2-16 CTAs that exchange
  * their slab edges through distributed shared memory.

@@ -159,6 +159,38 @@ struct Coef {
     real b11x2, b22x2, bx, bc, twoh, K, halfK;
 };
 
+// Neighbour signalling for cluster-split fields (SYNC = 2).  A thread that
+// pushed a slab edge row into a neighbour's halo slot arrives on that
+// neighbour's mbarrier for the stage buffer (release at cluster scope); the
+// threads that read the halo slots wait on their own CTA's mbarrier (acquire).
+__device__ __forceinline__ void nbr_arrive(uint32_t mbar_local, int rank)
+{
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(mbar_local), "r"(rank));
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" :: "r"(remote)
+                 : "memory");
+}
+
+// Bounded wait for the phase of the given parity: false after about a second
+// (2^31 SM clocks), or at once when another wait of the launch has already
+// timed out (status holds MLSD_ETIMEOUT), so that a failed exchange ends the
+// launch quickly instead of costing every remaining CTA a full second.
+__device__ __forceinline__ bool nbr_wait(uint32_t mbar_local, uint32_t parity, const int *status)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok) : "r"(mbar_local), "r"(parity) : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > (1ll << 31)) return false;
+        if (*(volatile const int *)status == MLSD_ETIMEOUT) return false;
+    }
+}
+
 template <int N, int C, int BX, int BY, typename real>
 struct Tile {
     using S = Smem<N, C, BX, BY, real>;
@@ -240,14 +272,29 @@ struct Tile {
     //   the source 2h A_J = 2h a_J - 2h b_JJ, whose constant part is Coef::K.
     // Ten FP32 instructions per cell.  SECOND: out = (w + g) / 2, with w (held in
     // out) seeding the FMA chain and K / 2 added by the final FMA.
-    template <int J, bool SECOND>
+    //
+    // SYNC = 0: one cluster-wide (C = 1: CTA) barrier after the edges are out.
+    // SYNC = 2: a CTA barrier for the in-slab halos, and neighbour signalling
+    // (mbarrier `mbar` of this buffer, phase `parity`) for the two halo rows
+    // that come from the neighbouring slabs; only the threads on the slab's
+    // first and last block rows wait for those.
+    template <int J, bool SECOND, int SYNC = 0>
     __device__ __forceinline__ static void stage(real *sm, int buf, int rank, int tx, int ty,
                                                  const real (&x)[BY][BX], real (&out)[BY][BX],
                                                  const real (&aE)[BY][BX], const real (&aN)[BY][BX],
-                                                 const Coef<real> &k)
+                                                 const Coef<real> &k, uint32_t mbar = 0,
+                                                 uint32_t parity = 0, int *status = nullptr)
     {
         publish_edges(sm, buf, rank, tx, ty, x);
-        tile_sync<C>();
+        if constexpr (SYNC == 2 && C > 1) {
+            if (ty == NBY - 1) nbr_arrive(mbar, (rank + 1) % C);       // its HS slot
+            if (ty == 0) nbr_arrive(mbar, (rank + C - 1) % C);         // its HN slot
+            __syncthreads();
+            if (ty == 0 || ty == NBY - 1)
+                if (!nbr_wait(mbar, parity, status)) atomicCAS(status, 0, MLSD_ETIMEOUT);
+        } else {
+            tile_sync<C>();
+        }
         // halos: south row b0-1, north row b0+BY, west column a0-1, east column a0+BX
         real hS[BX], hN[BX], hW[BY + 2], hE[BY + 2];
         load_halos(sm, buf, tx, ty, hS, hN, hW, hE);
@@ -371,13 +418,25 @@ struct Tile {
         asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
     }
 
-    template <int J, bool SPLIT>
+    template <int J, int SYNC>
     __device__ static void run(const PatchParams &prm, real *sm, long long p, int rank)
     {
+        constexpr bool SPLIT = SYNC == 1;
         const int tid = threadIdx.x, tx = tid % NBX, ty = tid / NBX;
         const int a0 = tx * BX, b0 = ty * BY;          // slab-local
         const int g0 = rank * NS;                       // first patch row of the slab
         double *red = reinterpret_cast<double *>(sm + S::WORDS);
+        // SYNC = 2: one mbarrier per stage buffer (slots 48, 49 of the reduction
+        // area), 2 NBX arrivals per phase (NBX pushing threads in each neighbour);
+        // the cluster barrier of the set-up orders the init before any arrival
+        const uint32_t mbar0 = (uint32_t)__cvta_generic_to_shared(red + 48);
+        if constexpr (SYNC == 2) {
+            if (tid == 0) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar0), "r"(2 * NBX) : "memory");
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar0 + 8), "r"(2 * NBX) : "memory");
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            }
+        }
         const long long Nl = prm.Nl;
         const long long pi = p % prm.n_macro, pj = p / prm.n_macro;
         const long long ox = patch_origin(pi, prm.n_macro, Nl, N);
@@ -480,6 +539,10 @@ struct Tile {
             if constexpr (SPLIT) {
                 stage_split<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, k);
                 stage_split<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, k);
+            } else if constexpr (SYNC == 2) {
+                const uint32_t par = (uint32_t)(step & 1);
+                stage<J, false, 2>(sm, 0, rank, tx, ty, w, s, A1, A2, k, mbar0, par, prm.status);
+                stage<J, true, 2>(sm, 1, rank, tx, ty, s, w, A1, A2, k, mbar0 + 8, par, prm.status);
             } else {
                 stage<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, k);
                 stage<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, k);
@@ -546,7 +609,7 @@ struct Tile {
     }
 };
 
-template <int N, int BX, int BY, typename real, int MINB, int C, bool SPLIT>
+template <int N, int BX, int BY, typename real, int MINB, int C, int SYNC>
 __global__ void __launch_bounds__((N / BX) * (N / C / BY), MINB)
 k_patch_solve(PatchParams prm)
 {
@@ -556,13 +619,16 @@ k_patch_solve(PatchParams prm)
     const int rank = (int)(blockIdx.x % C);
     if (item >= prm.item0 + prm.items) return;      // whole clusters only: C divides the grid
     const long long p = prm.pidx ? (long long)prm.pidx[item >> 1] : (item >> 1);
-    if (item & 1) Tile<N, C, BX, BY, real>::template run<2, SPLIT>(prm, sm, p, rank);
-    else Tile<N, C, BX, BY, real>::template run<1, SPLIT>(prm, sm, p, rank);
+    if (item & 1) Tile<N, C, BX, BY, real>::template run<2, SYNC>(prm, sm, p, rank);
+    else Tile<N, C, BX, BY, real>::template run<1, SYNC>(prm, sm, p, rank);
 }
 
-template <int N, int BX, int BY, typename real, int MINB = 1, int C = 1, bool SPLIT = false>
+// SYNC: 0 = barrier per stage, 1 = split-phase cluster barrier, 2 = neighbour
+// signalling (clusters only)
+template <int N, int BX, int BY, typename real, int MINB = 1, int C = 1, int SYNC = 0>
 void add_variant(std::vector<PatchVariant> &out)
 {
+    static_assert(SYNC != 2 || C > 1, "neighbour signalling needs a cluster");
     static_assert(((N / BX) * (N / C / BY)) % 32 == 0, "whole warps only");
     static_assert((N / BX) * (N / C / BY) <= 512, "reduction slots 0..31 (warp pairs), 32, 40, 41");
     static_assert(N % C == 0 && (N / C) % BY == 0 && N % BX == 0, "tiling");
@@ -574,10 +640,10 @@ void add_variant(std::vector<PatchVariant> &out)
     v.minb = MINB;
     v.packed = 0;
     v.cluster = C;
-    v.split = SPLIT ? 1 : 0;
+    v.split = SYNC;
     v.threads = (N / BX) * (N / C / BY);
     v.smem = Smem<N, C, BX, BY, real>::BYTES;
-    v.fn = reinterpret_cast<const void *>(&k_patch_solve<N, BX, BY, real, MINB, C, SPLIT>);
+    v.fn = reinterpret_cast<const void *>(&k_patch_solve<N, BX, BY, real, MINB, C, SYNC>);
     out.push_back(v);
 }
 
@@ -928,7 +994,7 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
         switch (n) {
         case 32:
             add_variant<32, 4, 8, float>(out);
-            add_variant<32, 4, 8, float, 1, 1, true>(out);
+            add_variant<32, 4, 8, float, 1, 1, 1>(out);
             add_variant<32, 4, 4, float>(out);
             add_variant<32, 2, 8, float>(out);
             add_variant<32, 2, 4, float>(out);
@@ -939,8 +1005,8 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
         case 64:
             add_variant<64, 4, 8, float>(out);
             add_variant<64, 4, 8, float, 3>(out);
-            add_variant<64, 4, 8, float, 3, 1, true>(out);
-            add_variant<64, 4, 4, float, 2, 1, true>(out);
+            add_variant<64, 4, 8, float, 3, 1, 1>(out);
+            add_variant<64, 4, 4, float, 2, 1, 1>(out);
             add_variant<64, 4, 4, float>(out);
             add_variant<64, 2, 8, float>(out);
             add_variant<64, 8, 4, float>(out);
@@ -951,14 +1017,18 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
             break;
         case 128:   // split over a cluster of CTAs (rows in slabs)
             add_variant<128, 4, 8, float, 3, 4>(out);
-            add_variant<128, 4, 8, float, 3, 4, true>(out);
+            add_variant<128, 4, 8, float, 3, 4, 1>(out);
+            add_variant<128, 4, 8, float, 3, 4, 2>(out);
             add_variant<128, 4, 8, float, 1, 2>(out);
             add_variant<128, 4, 4, float, 1, 4>(out);
             break;
         case 256:
             add_variant<256, 4, 8, float, 1, 8>(out);
-            add_variant<256, 4, 8, float, 1, 8, true>(out);
-            add_variant<256, 4, 8, float, 2, 8, true>(out);
+            add_variant<256, 4, 8, float, 1, 8, 1>(out);
+            add_variant<256, 4, 8, float, 2, 8, 1>(out);
+            add_variant<256, 4, 8, float, 1, 8, 2>(out);
+            add_variant<256, 4, 8, float, 2, 8, 2>(out);
+            add_variant<256, 4, 8, float, 3, 16, 2>(out);
             add_variant<256, 4, 4, float, 1, 8>(out);
             add_variant<256, 4, 8, float, 3, 16>(out);
             break;

@@ -415,8 +415,8 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
     if (vs.empty()) return MLSD_EUNSUPPORTED;
     c.variant = vs[0];
     if (const char *env = std::getenv("MLSD_TILE")) {
-        // <bx>x<by>[m<minb>][c<cluster>][p][s]: p selects the packed two-field kernel,
-        // s the split-phase stage barriers
+        // <bx>x<by>[m<minb>][c<cluster>][p][s|n]: p selects the packed two-field kernel,
+        // s the split-phase stage barriers, n neighbour signalling between slabs
         int bx = 0, by = 0, mb = 1, pk = 0, cl = 1, sp = 0;
         char rest[16] = "";
         if (std::sscanf(env, "%dx%d%15s", &bx, &by, rest) >= 2) {
@@ -425,6 +425,7 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
                 if (*c == 'c') cl = std::atoi(c + 1);
                 if (*c == 'p') pk = 1;
                 if (*c == 's') sp = 1;
+                if (*c == 'n') sp = 2;
             }
             for (auto &v : vs)
                 if (v.bx == bx && v.by == by && v.minb == mb && v.packed == pk && v.cluster == cl &&
