@@ -107,7 +107,9 @@ typedef struct {
                                   when cluster > 1); 1 split-phase barriers (interior cells
                                   computed while the barrier completes); 2 neighbour signalling
                                   (cluster > 1: a CTA barrier, and mbarrier arrivals from the two
-                                  neighbouring slabs for the halo rows they push) */
+                                  neighbouring slabs for the halo rows they push); 3 bulk row
+                                  copies (cluster > 1: a CTA barrier, and the two halo rows moved
+                                  by cp.async.bulk completing on the receiver's mbarrier) */
     int n_classes;             /* patch sizes in the level; n, Nl, h and the tile fields describe
                                   the class with the most work; all classes run concurrently */
 } mlsd_level_desc;
@@ -120,11 +122,12 @@ typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and 
  * Set-up also picks the thread-block tiling of the patch kernel per patch
  * size: every compiled candidate is timed on a sample of the level's patches
  * (a short fixed window) and the fastest is kept for the process; the
- * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][c<cluster>][p][s|n]
+ * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][c<cluster>][p][s|n|b]
  * forces one where it exists for the level's patch size (p: the packed kernel
  * that advances both fields of a patch in f32x2 pairs; c: CTAs per patch field;
  * s: split-phase stage barriers; n: neighbour signalling between the slabs of
- * a cluster instead of a cluster-wide barrier).
+ * a cluster instead of a cluster-wide barrier; b: the slab edge rows moved by
+ * bulk copies that complete on the receiver's mbarrier).
  * Patch sizes 32 and 64 run one CTA per field (or per patch, packed); 128 and
  * 256 split each field over a thread-block cluster of 2-16 CTAs that exchange
  * their slab edges through distributed shared memory.
@@ -189,20 +192,34 @@ int mlsd_effective_diffusivity(mlsd_levels *h, int mode, double *K_macro_dev,
 
 /* ------------------------------------------------------------------------
  * Learned surrogate of the patch solve (not in the paper).  A small ensemble
- * of MLPs maps a patch's features to (K - B) / tr(B); where the members
- * disagree, the plain patch solve above is run instead.
+ * of MLPs maps a patch's features to the part of K that the second-order
+ * (small-Peclet) estimate Q below misses; where the members disagree, the
+ * plain patch solve above is run instead.
  *
- * Features of a patch (MLSD_SUR_FEATURES = 582 values, stored as one bfloat16
- * row of MLSD_SUR_IN = 640, zero padded): Re and Im of the patch DFT
- *   psihat(k) = n^-2 sum_ab (psi[b][a] - mean psi) exp(-2 pi i (k1 a + k2 b)/n)
- * of the level's band at the patch nodes, k2 = -8..8 (slow), k1 = -8..8, each
- * divided by tr(B)/2; then B11/kappa, B12/kappa, B22/kappa, log kappa.
+ * Features of a patch (MLSD_SUR_FEATURES = 585 values, stored as one bfloat16
+ * row of MLSD_SUR_IN = 640, zero padded):
+ *   [0, 578)  Re and Im of the patch DFT
+ *               psihat(k) = n^-2 sum_ab (psi[b][a] - mean psi) exp(-2 pi i (k1 a + k2 b)/n)
+ *             of the level's band at the patch nodes, k2 = -8..8 (slow),
+ *             k1 = -8..8, each times MLSD_SUR_PSI_SCALE / (tr(B)/2);
+ *   578..580  B11/kappa, B12/kappa, B22/kappa;   581  log kappa;
+ *   582..584  MLSD_SUR_Q_SCALE Q / tr(B) for (Q11, Q12, Q22), where
+ *               Q = sum_{k != 0} |psihat(k)|^2 [[s2^2, -s1 s2], [-s1 s2, s1^2]] / D(k),
+ *               D = B11 (2 - 2 cos t1) + B22 (2 - 2 cos t2) + 2 B12 s1 s2,
+ *               t_i = 2 pi k_i / n, s_i = sin t_i,
+ *             over the same modes: the flux of the corrector equation solved
+ *             to first order in v (B:DD w_j = -v_j in Fourier space).  For a
+ *             shear flow inside the window it is K - B exactly.
+ * Network output (the training target): (K - B - Q) MLSD_SUR_Y_SCALE / tr(B).
  * Member network: 640 -> h -> h -> h -> 3, exact-erf GELU after the first three
  * layers, bfloat16 weights and activations, FP32 accumulation.  Parameters of
  * a member in one FP32 array, row-major (out x in):
  *   W1[h][640] b1[h] W2[h][h] b2[h] W3[h][h] b3[h] W4[3][h] b4[3].         */
 #define MLSD_SUR_IN 640
-#define MLSD_SUR_FEATURES 582
+#define MLSD_SUR_FEATURES 585
+#define MLSD_SUR_PSI_SCALE 32.0
+#define MLSD_SUR_Q_SCALE 10.0
+#define MLSD_SUR_Y_SCALE 30.0
 typedef struct mlsd_surrogate mlsd_surrogate;
 
 int64_t mlsd_surrogate_param_count(int hidden);          /* per member */
@@ -214,7 +231,7 @@ void mlsd_surrogate_free(mlsd_surrogate *s);
 int mlsd_surrogate_set_params(mlsd_surrogate *s, int member, const float *params_host);
 int mlsd_surrogate_get_params(mlsd_surrogate *s, int member, float *params_host);
 /* Features of every patch of a level (one patch size <= 64 per level) with
- * base B_dev [P][3]: X_dev bfloat16 [P][640]; F32_dev [P][582] or NULL.     */
+ * base B_dev [P][3]: X_dev bfloat16 [P][640]; F32_dev [P][585] or NULL.     */
 int mlsd_surrogate_features(mlsd_levels *h, int level, const double *B_dev, void *X_dev,
                             float *F32_dev, void *cuda_stream);
 /* Mean-squared-error loss of one member on M <= max_batch rows (X bfloat16
@@ -240,7 +257,8 @@ int mlsd_surrogate_status(mlsd_surrogate *s, void *cuda_stream);
 /* Every member on M rows: out_dev FP32 [members][M][3].                     */
 int mlsd_surrogate_predict(mlsd_surrogate *s, const void *X_dev, int64_t M, float *out_dev,
                            void *cuda_stream);
-/* One level with the surrogate: features, ensemble, K_m = B + tr(B) out_m;
+/* One level with the surrogate: features (with Q), ensemble,
+ *     K_m = B + Q + tr(B) out_m / MLSD_SUR_Y_SCALE;
  * a patch whose members disagree,
  *     max_{m,c} |K_m,c - mean_m K_m,c| > threshold * ||mean K||_F,
  * is solved by the plain patch solve (mlsd_solve_level's kernel) instead; the

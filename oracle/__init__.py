@@ -275,15 +275,27 @@ def coarse_grain(u, N):
     return U, m.value
 
 
-N_FEATURES = 582
+N_FEATURES = 585
+PSI_SCALE, Q_SCALE, Y_SCALE = 32.0, 10.0, 30.0
 
 
 def features(psi, B, kappa):
-    """582 surrogate inputs of one patch (psi with its patch mean removed)."""
+    """585 surrogate inputs of one patch (psi with its patch mean removed)."""
     psi = _f64(psi); B = _f64(B)
     f = np.zeros(N_FEATURES)
     lib().orc_features(psi.shape[0], _ptr(psi), _ptr(B), float(kappa), _ptr(f))
     return f
+
+
+def second_order_K(f, B):
+    """Q (the second-order estimate of K - B that features 582..584 carry) in the
+    units of K, from a feature row and the base tensor."""
+    return np.asarray(f[582:585]) * (B[0] + B[2]) / Q_SCALE
+
+
+def surrogate_K(out, f, B):
+    """K of one patch from a network output (the target (K - B - Q) 30 / tr B)."""
+    return np.asarray(B) + second_order_K(f, B) + (B[0] + B[2]) * np.asarray(out) / Y_SCALE
 
 
 def mlp_param_count(d0, h):

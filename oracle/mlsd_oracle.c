@@ -665,18 +665,32 @@ int orc_num_threads(void)
 /* Learned surrogate of the patch solve (not in the paper; the library's     */
 /* estimator it is checked against is orc_patch_k).                          */
 /*                                                                           */
-/* Features of a patch (582 values):                                         */
+/* Features of a patch (585 values):                                         */
 /*   [0, 578): Re and Im of psihat(k) = n^-2 sum_ab psi[b][a]               */
 /*             exp(-2 pi i (k1 a + k2 b) / n) for k2 = -8..8 (slow),         */
-/*             k1 = -8..8 (fast), each divided by tr(B)/2 (a Peclet scale);  */
-/*             psi is the patch's band with the patch mean removed           */
+/*             k1 = -8..8 (fast), each times 32 / (tr(B)/2) (a Peclet        */
+/*             scale, brought to order one); psi is the patch's band with    */
+/*             the patch mean removed                                        */
 /*   578..580: B11/kappa, B12/kappa, B22/kappa;  581: log(kappa)             */
-/* Target: (K - B) / tr(B) for the three components (K11, K12, K22).         */
+/*   582..584: 10 Q / tr(B) for (Q11, Q12, Q22), the second-order (small     */
+/*             Peclet) solution of the discrete corrector equation on the    */
+/*             same 17 x 17 window of modes:                                 */
+/*               Q = sum_{k != 0} |psihat(k)|^2 M(k) / D(k),                 */
+/*               M = [[s2^2, -s1 s2], [-s1 s2, s1^2]],                       */
+/*               D = B11 (2 - 2 cos t1) + B22 (2 - 2 cos t2) + 2 B12 s1 s2,  */
+/*             t_i = 2 pi k_i / n, s_i = sin t_i.  (To first order in v the  */
+/*             corrector solves B:D D w_j = -v_j; with v1 = -D0y psi,        */
+/*             v2 = D0x psi the Fourier symbols are -D/h^2 for B:D D and     */
+/*             i s_i / h for D0, and sum_k Re(vhat_i conj(what_j)) is Q.)    */
+/* Target: (K - B - Q) 30 / tr(B) for the three components (K11, K12, K22).  */
 /* ------------------------------------------------------------------------ */
-#define ORC_NF 582
+#define ORC_NF 585
+#define ORC_PSI_SCALE 32.0
+#define ORC_Q_SCALE 10.0
 void orc_features(int n, const double *psi, const double *B, double kappa, double *f)
 {
-    double scale = 0.5 * (B[0] + B[2]);
+    const double trh = 0.5 * (B[0] + B[2]);
+    double Q11 = 0.0, Q12 = 0.0, Q22 = 0.0;
     int t = 0;
     for (int k2 = -8; k2 <= 8; ++k2)
         for (int k1 = -8; k1 <= 8; ++k1) {
@@ -688,13 +702,28 @@ void orc_features(int n, const double *psi, const double *B, double kappa, doubl
                     sr += psi[(long)b * n + a] * cos(th);
                     si += psi[(long)b * n + a] * sin(th);
                 }
-            f[t++] = sr / ((double)n * n) / scale;
-            f[t++] = si / ((double)n * n) / scale;
+            sr /= (double)n * n;
+            si /= (double)n * n;
+            f[t++] = sr * ORC_PSI_SCALE / trh;
+            f[t++] = si * ORC_PSI_SCALE / trh;
+            if (k1 != 0 || k2 != 0) {
+                const double t1 = 2.0 * ORC_PI * k1 / n, t2 = 2.0 * ORC_PI * k2 / n;
+                const double s1 = sin(t1), s2 = sin(t2);
+                const double D = B[0] * (2.0 - 2.0 * cos(t1)) + B[2] * (2.0 - 2.0 * cos(t2))
+                                 + 2.0 * B[1] * s1 * s2;
+                const double pw = sr * sr + si * si;
+                Q11 += pw * s2 * s2 / D;
+                Q12 -= pw * s1 * s2 / D;
+                Q22 += pw * s1 * s1 / D;
+            }
         }
     f[t++] = B[0] / kappa;
     f[t++] = B[1] / kappa;
     f[t++] = B[2] / kappa;
     f[t++] = log(kappa);
+    f[t++] = ORC_Q_SCALE * Q11 / (2.0 * trh);
+    f[t++] = ORC_Q_SCALE * Q12 / (2.0 * trh);
+    f[t++] = ORC_Q_SCALE * Q22 / (2.0 * trh);
 }
 
 /* round to bfloat16 (via float, round to nearest even); NaN-free inputs */

@@ -33,7 +33,8 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_solve_level_surrogate", "mlsd_surrogate_set_engine", "mlsd_surrogate_status",
             "mlsd_strerror"]
 SUR_CUDA, SUR_TENSOR = 0, 1
-SUR_IN, SUR_FEATURES = 640, 582
+SUR_IN, SUR_FEATURES = 640, 585
+SUR_PSI_SCALE, SUR_Q_SCALE, SUR_Y_SCALE = 32.0, 10.0, 30.0
 NOALLOC_MAX_MACRO = 256
 
 
@@ -185,7 +186,7 @@ class Levels:
         return out
 
     def features(self, level, B, X, F32=None, stream=None):
-        """Surrogate inputs of every patch: X bfloat16 [P][640], F32 [P][582] or None."""
+        """Surrogate inputs of every patch: X bfloat16 [P][640], F32 [P][585] or None."""
         _check(_lib.mlsd_surrogate_features(self.h, int(level), _dptr(B), _dptr(X), _dptr(F32),
                                             _stream(stream)), "mlsd_surrogate_features")
 

@@ -121,7 +121,7 @@ long long launch_count();
 long long sur_param_count(int h);
 cudaError_t launch_features(const float *band, long long Nl, int n, int n_macro, const int *pidx,
                             long long count, const double *B, double kappa, void *X, float *F32,
-                            cudaStream_t s);
+                            double *Q, cudaStream_t s);
 cudaError_t sur_forward(int h, int M, const void *X, const float *wf, const void *wb,
                         float *Z[4], void *Aact[3], cudaStream_t s);
 cudaError_t sur_grad(int h, int M, const void *X, const float *Y, const float *wf, const void *wb,
@@ -130,8 +130,9 @@ cudaError_t sur_grad(int h, int M, const void *X, const float *Y, const float *w
 cudaError_t sur_adam(long long n, float *w, const float *g, float *m, float *v, float lr, int t,
                      void *wb, cudaStream_t s);
 cudaError_t sur_to_bf16(long long n, const float *w, void *wb, cudaStream_t s);
-cudaError_t sur_disagree(long long P, int members, const float *out, const double *B, double thr,
-                         double *K, int *flag, int *idx, int *count, cudaStream_t s);
+cudaError_t sur_disagree(long long P, int members, const float *out, const double *B,
+                         const double *Q, double thr, double *K, int *flag, int *idx, int *count,
+                         cudaStream_t s);
 cudaError_t sur_merge(int n, const int *idx, const double *B, const double *S, double *K,
                       cudaStream_t s);
 

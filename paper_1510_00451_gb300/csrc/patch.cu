@@ -191,6 +191,26 @@ __device__ __forceinline__ bool nbr_wait(uint32_t mbar_local, uint32_t parity, c
     }
 }
 
+// Bulk copy (async proxy) of `bytes` from this CTA's shared memory to the
+// shared memory of cluster rank `rank`, completing on that rank's mbarrier at
+// the same offset as `mbar_local` (SYNC = 3).
+__device__ __forceinline__ void bulk_to_rank(uint32_t dst_local, uint32_t src_local, uint32_t bytes,
+                                             uint32_t mbar_local, int rank)
+{
+    uint32_t dst, mbar;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(dst) : "r"(dst_local), "r"(rank));
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(mbar) : "r"(mbar_local), "r"(rank));
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "r"(src_local), "r"(bytes), "r"(mbar) : "memory");
+}
+
+// arm the next phase of a local mbarrier: one arrival plus `bytes` expected
+__device__ __forceinline__ void arm_tx(uint32_t mbar_local, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar_local), "r"(bytes)
+                 : "memory");
+}
+
 template <int N, int C, int BX, int BY, typename real>
 struct Tile {
     using S = Smem<N, C, BX, BY, real>;
@@ -199,6 +219,9 @@ struct Tile {
     // Publish the edges of x into buffer `buf`; with a cluster, also push the
     // slab's first row into the HN slot of the rank below (its row above) and the
     // slab's last row into the HS slot of the rank above (its row below).
+    // PUSH = false: local buffers only (the slab's first and last rows are then
+    // moved by bulk copies, see stage()).
+    template <bool PUSH = true>
     __device__ __forceinline__ static void publish_edges(real *sm, int buf, int rank, int tx, int ty,
                                                          const real (&x)[BY][BX])
     {
@@ -217,7 +240,7 @@ struct Tile {
         for (int k = 0; k < BY; ++k) { l[k] = x[k][0]; r[k] = x[k][BX - 1]; }
         st_vec<real, BY>(colL + tx * S::CS + b0, l);
         st_vec<real, BY>(colR + tx * S::CS + b0, r);
-        if constexpr (C > 1) {
+        if constexpr (C > 1 && PUSH) {
             real *HS = colR + S::COL, *HN = HS + N;
             if (ty == NBY - 1) st_vec<real, BX>(rank_ptr<C>(HS + a0, (rank + 1) % C), bt);
             if (ty == 0) st_vec<real, BX>(rank_ptr<C>(HN + a0, (rank + C - 1) % C), t);
@@ -285,8 +308,32 @@ struct Tile {
                                                  const Coef<real> &k, uint32_t mbar = 0,
                                                  uint32_t parity = 0, int *status = nullptr)
     {
-        publish_edges(sm, buf, rank, tx, ty, x);
-        if constexpr (SYNC == 2 && C > 1) {
+        publish_edges<SYNC != 3>(sm, buf, rank, tx, ty, x);
+        if constexpr (SYNC == 3 && C > 1) {
+            // the slab's last row goes to rank + 1's HS slot and its first row to
+            // rank - 1's HN slot by two bulk copies issued by thread 0, each
+            // completing on the receiver's mbarrier of this buffer; the rows
+            // written by the threads must reach the async proxy first.  The
+            // source rows are not rewritten before both copies have landed: the
+            // receivers wait for them before they send the next stage's rows.
+            if (ty == 0 || ty == NBY - 1) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tx == 0 && ty == 0) {
+                real *rowT = sm + buf * S::STAGE, *rowB = rowT + S::ROW;
+                real *HS = rowB + S::ROW + 2 * S::COL, *HN = HS + N;
+                const uint32_t bytes = (uint32_t)(N * sizeof(real));
+                bulk_to_rank((uint32_t)__cvta_generic_to_shared(HS),
+                             (uint32_t)__cvta_generic_to_shared(rowB + (NBY - 1) * N), bytes, mbar,
+                             (rank + 1) % C);
+                bulk_to_rank((uint32_t)__cvta_generic_to_shared(HN),
+                             (uint32_t)__cvta_generic_to_shared(rowT), bytes, mbar, (rank + C - 1) % C);
+            }
+            if (ty == 0 || ty == NBY - 1) {
+                if (!nbr_wait(mbar, parity, status)) atomicCAS(status, 0, MLSD_ETIMEOUT);
+                // thread 0 re-arms this buffer's barrier for its next phase
+                if (tx == 0 && ty == 0) arm_tx(mbar, (uint32_t)(2 * N * sizeof(real)));
+            }
+        } else if constexpr (SYNC == 2 && C > 1) {
             if (ty == NBY - 1) nbr_arrive(mbar, (rank + 1) % C);       // its HS slot
             if (ty == 0) nbr_arrive(mbar, (rank + C - 1) % C);         // its HN slot
             __syncthreads();
@@ -437,6 +484,17 @@ struct Tile {
                 asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
             }
         }
+        // SYNC = 3: one arrival (thread 0's arm) and two incoming rows per phase;
+        // the first phase of both barriers is armed here
+        if constexpr (SYNC == 3) {
+            if (tid == 0) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar0) : "memory");
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar0 + 8) : "memory");
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+                arm_tx(mbar0, (uint32_t)(2 * N * sizeof(real)));
+                arm_tx(mbar0 + 8, (uint32_t)(2 * N * sizeof(real)));
+            }
+        }
         const long long Nl = prm.Nl;
         const long long pi = p % prm.n_macro, pj = p / prm.n_macro;
         const long long ox = patch_origin(pi, prm.n_macro, Nl, N);
@@ -539,10 +597,10 @@ struct Tile {
             if constexpr (SPLIT) {
                 stage_split<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, k);
                 stage_split<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, k);
-            } else if constexpr (SYNC == 2) {
+            } else if constexpr (SYNC >= 2) {
                 const uint32_t par = (uint32_t)(step & 1);
-                stage<J, false, 2>(sm, 0, rank, tx, ty, w, s, A1, A2, k, mbar0, par, prm.status);
-                stage<J, true, 2>(sm, 1, rank, tx, ty, s, w, A1, A2, k, mbar0 + 8, par, prm.status);
+                stage<J, false, SYNC>(sm, 0, rank, tx, ty, w, s, A1, A2, k, mbar0, par, prm.status);
+                stage<J, true, SYNC>(sm, 1, rank, tx, ty, s, w, A1, A2, k, mbar0 + 8, par, prm.status);
             } else {
                 stage<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, k);
                 stage<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, k);
@@ -624,11 +682,11 @@ k_patch_solve(PatchParams prm)
 }
 
 // SYNC: 0 = barrier per stage, 1 = split-phase cluster barrier, 2 = neighbour
-// signalling (clusters only)
+// signalling, 3 = bulk copies of the slab edge rows (2 and 3: clusters only)
 template <int N, int BX, int BY, typename real, int MINB = 1, int C = 1, int SYNC = 0>
 void add_variant(std::vector<PatchVariant> &out)
 {
-    static_assert(SYNC != 2 || C > 1, "neighbour signalling needs a cluster");
+    static_assert(SYNC < 2 || C > 1, "neighbour signalling / bulk row copies need a cluster");
     static_assert(((N / BX) * (N / C / BY)) % 32 == 0, "whole warps only");
     static_assert((N / BX) * (N / C / BY) <= 512, "reduction slots 0..31 (warp pairs), 32, 40, 41");
     static_assert(N % C == 0 && (N / C) % BY == 0 && N % BX == 0, "tiling");
@@ -1019,6 +1077,7 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
             add_variant<128, 4, 8, float, 3, 4>(out);
             add_variant<128, 4, 8, float, 3, 4, 1>(out);
             add_variant<128, 4, 8, float, 3, 4, 2>(out);
+            add_variant<128, 4, 8, float, 3, 4, 3>(out);
             add_variant<128, 4, 8, float, 1, 2>(out);
             add_variant<128, 4, 4, float, 1, 4>(out);
             break;
@@ -1029,6 +1088,8 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
             add_variant<256, 4, 8, float, 1, 8, 2>(out);
             add_variant<256, 4, 8, float, 2, 8, 2>(out);
             add_variant<256, 4, 8, float, 3, 16, 2>(out);
+            add_variant<256, 4, 8, float, 1, 8, 3>(out);
+            add_variant<256, 4, 8, float, 3, 16, 3>(out);
             add_variant<256, 4, 4, float, 1, 8>(out);
             add_variant<256, 4, 8, float, 3, 16>(out);
             break;

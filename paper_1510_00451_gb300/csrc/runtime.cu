@@ -415,8 +415,9 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
     if (vs.empty()) return MLSD_EUNSUPPORTED;
     c.variant = vs[0];
     if (const char *env = std::getenv("MLSD_TILE")) {
-        // <bx>x<by>[m<minb>][c<cluster>][p][s|n]: p selects the packed two-field kernel,
-        // s the split-phase stage barriers, n neighbour signalling between slabs
+        // <bx>x<by>[m<minb>][c<cluster>][p][s|n|b]: p selects the packed two-field kernel,
+        // s the split-phase stage barriers, n neighbour signalling between slabs, b bulk
+        // copies of the slab edge rows
         int bx = 0, by = 0, mb = 1, pk = 0, cl = 1, sp = 0;
         char rest[16] = "";
         if (std::sscanf(env, "%dx%d%15s", &bx, &by, rest) >= 2) {
@@ -426,6 +427,7 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
                 if (*c == 'p') pk = 1;
                 if (*c == 's') sp = 1;
                 if (*c == 'n') sp = 2;
+                if (*c == 'b') sp = 3;
             }
             for (auto &v : vs)
                 if (v.bx == bx && v.by == by && v.minb == mb && v.packed == pk && v.cluster == cl &&
@@ -1036,7 +1038,7 @@ int mlsd_surrogate_features(mlsd_levels *h, int level, const double *B_dev, void
     if (d.cls.size() != 1 || d.cls[0].n > 64 || h->precision != MLSD_FP32) return MLSD_EUNSUPPORTED;
     const SizeClass &c = d.cls[0];
     CK(launch_features(static_cast<const float *>(c.band), c.Nl, c.n, h->N, nullptr, h->P, B_dev,
-                       h->kappa, X_dev, F32_dev, static_cast<cudaStream_t>(cuda_stream)));
+                       h->kappa, X_dev, F32_dev, nullptr, static_cast<cudaStream_t>(cuda_stream)));
     return MLSD_OK;
 }
 
@@ -1129,18 +1131,22 @@ int mlsd_solve_level_surrogate(mlsd_levels *h, mlsd_surrogate *s, int level,
     const long long P = h->P;
     char *ws = nullptr;
     const size_t xb = (size_t)P * MLSD_SUR_IN * 2, ob = (size_t)s->members * P * 3 * 4;
-    const size_t fb = (size_t)P * 4, ib = (size_t)P * 4;
-    CK(cudaMallocAsync((void **)&ws, xb + ob + fb + ib + 256, st));
-    void *X = ws;
-    float *out = reinterpret_cast<float *>(ws + xb);
-    int *flag = reinterpret_cast<int *>(ws + xb + ob);
-    int *idx = reinterpret_cast<int *>(ws + xb + ob + fb);
-    int *cnt = reinterpret_cast<int *>(ws + xb + ob + fb + ib);
+    const size_t fb = (size_t)P * 4, ib = (size_t)P * 4, qb = (size_t)P * 3 * 8;
+    CK(cudaMallocAsync((void **)&ws, qb + xb + ob + fb + ib + 256, st));
+    double *Q = reinterpret_cast<double *>(ws);
+    void *X = ws + qb;
+    float *out = reinterpret_cast<float *>(ws + qb + xb);
+    int *flag = reinterpret_cast<int *>(ws + qb + xb + ob);
+    int *idx = reinterpret_cast<int *>(ws + qb + xb + ob + fb);
+    int *cnt = reinterpret_cast<int *>(ws + qb + xb + ob + fb + ib);
     int count = 0;
-    int rc = mlsd_surrogate_features(h, level, K_base_dev, X, nullptr, cuda_stream);
+    const SizeClass &c0 = d.cls[0];
+    int rc = MLSD_OK;
+    cudaError_t e = launch_features(static_cast<const float *>(c0.band), c0.Nl, c0.n, h->N, nullptr,
+                                    P, K_base_dev, h->kappa, X, nullptr, Q, st);
+    if (e != cudaSuccess) rc = MLSD_ECUDA;
     if (!rc) rc = mlsd_surrogate_predict(s, X, P, out, cuda_stream);
-    cudaError_t e = cudaSuccess;
-    if (!rc) e = sur_disagree(P, s->members, out, K_base_dev, threshold, K_out_dev, flag, idx, cnt, st);
+    if (!rc) e = sur_disagree(P, s->members, out, K_base_dev, Q, threshold, K_out_dev, flag, idx, cnt, st);
     if (!rc && e == cudaSuccess) e = cudaMemcpyAsync(&count, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (!rc && e == cudaSuccess && count > 0) {

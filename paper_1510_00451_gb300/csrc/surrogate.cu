@@ -2,11 +2,13 @@
 // plain patch solve stays its fallback and the judge of its error).
 //
 // Features (K8): per patch, the 17 x 17 low-mode DFT of the patch's band psi
-// (patch mean removed), divided by tr(B)/2, then B/kappa and log kappa:
-// 582 values stored as one bfloat16 row of MLSD_SUR_IN (640, zero padded).
+// (patch mean removed) times MLSD_SUR_PSI_SCALE / (tr(B)/2), then B/kappa,
+// log kappa, and the second-order (small-Peclet) estimate Q of K - B on the
+// same modes, as MLSD_SUR_Q_SCALE Q / tr(B): 585 values stored as one bfloat16
+// row of MLSD_SUR_IN (640, zero padded).
 // Network: an ensemble of members, each 640 -> h -> h -> h -> 3 with the exact
 // erf GELU, bfloat16 weights and activations, FP32 accumulation; output
-// (K - B) / tr(B).  Training kernels here run on the CUDA cores (FP32 FMA on
+// (K - B - Q) MLSD_SUR_Y_SCALE / tr(B).  Training kernels here run on the CUDA cores (FP32 FMA on
 // bfloat16 operands); the inference forward has a tensor-core (tcgen05) kernel
 // in mlp_tc.cu.
 #include <cuda_bf16.h>
@@ -28,7 +30,7 @@ constexpr int NMODE = 2 * KMODE + 1;       // 17
 // K8 features: one CTA per patch (n <= 64: the patch is staged in shared memory)
 __global__ void k_features(const float *band, long long Nl, int n, int n_macro, const int *pidx,
                            long long count, const double *B, double kappa, __nv_bfloat16 *X,
-                           float *F32)
+                           float *F32, double *Qout)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *psi = reinterpret_cast<float *>(smem_raw);              // [n][n]
@@ -67,10 +69,18 @@ __global__ void k_features(const float *band, long long Nl, int n, int n_macro, 
         Fr[t] = make_float2(sr, si);
     }
     __syncthreads();
-    const double trh = 0.5 * (B[3 * p] + B[3 * p + 2]);
-    const float scale = (float)(1.0 / ((double)n * n * trh));
+    const double B11 = B[3 * p], B12 = B[3 * p + 1], B22 = B[3 * p + 2];
+    const double trh = 0.5 * (B11 + B22);
+    const float scale = (float)(MLSD_SUR_PSI_SCALE / ((double)n * n * trh));
+    const double inv_nn = 1.0 / ((double)n * n);
     __nv_bfloat16 *xr = X + item * (long long)MLSD_SUR_IN;
     float *fr = F32 ? F32 + item * (long long)MLSD_SUR_FEATURES : nullptr;
+    // second-order estimate of K - B over the window:
+    //   Q = sum_{k != 0} |psihat(k)|^2 [[s2^2, -s1 s2], [-s1 s2, s1^2]] / D(k),
+    //   D = B11 (2 - 2 cos t1) + B22 (2 - 2 cos t2) + 2 B12 s1 s2, t_i = 2 pi k_i / n:
+    // to first order in v the corrector solves B:DD w_j = -v_j, whose Fourier
+    // symbol is -D / h^2, and v1 = -D0y psi, v2 = D0x psi have symbols i s / h
+    double q11 = 0.0, q12 = 0.0, q22 = 0.0;
     for (int t = threadIdx.x; t < NMODE * NMODE; t += blockDim.x) {
         const int k2 = t / NMODE - KMODE, k1i = t % NMODE;
         float sr = 0.f, si = 0.f;
@@ -87,14 +97,45 @@ __global__ void k_features(const float *band, long long Nl, int n, int n_macro, 
         xr[2 * t] = __float2bfloat16_rn(re);
         xr[2 * t + 1] = __float2bfloat16_rn(im);
         if (fr) { fr[2 * t] = re; fr[2 * t + 1] = im; }
+        const int k1 = k1i - KMODE;
+        if (k1 != 0 || k2 != 0) {
+            double s1, c1, s2, c2;
+            sincospi(2.0 * k1 / n, &s1, &c1);
+            sincospi(2.0 * k2 / n, &s2, &c2);
+            const double D = B11 * (2.0 - 2.0 * c1) + B22 * (2.0 - 2.0 * c2) + 2.0 * B12 * s1 * s2;
+            const double pr = (double)sr * inv_nn, pi = (double)si * inv_nn;
+            const double g = (pr * pr + pi * pi) / D;
+            q11 += g * s2 * s2;
+            q12 -= g * s1 * s2;
+            q22 += g * s1 * s1;
+        }
     }
+    __shared__ double qred[3][32];
+    __shared__ double qsum[3];
+    for (int o = 16; o > 0; o >>= 1) {
+        q11 += __shfl_xor_sync(0xffffffffu, q11, o);
+        q12 += __shfl_xor_sync(0xffffffffu, q12, o);
+        q22 += __shfl_xor_sync(0xffffffffu, q22, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        qred[0][threadIdx.x >> 5] = q11; qred[1][threadIdx.x >> 5] = q12; qred[2][threadIdx.x >> 5] = q22;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += qred[threadIdx.x][w];
+        qsum[threadIdx.x] = t;
+        if (Qout) Qout[item * 3 + threadIdx.x] = t;
+    }
+    __syncthreads();
     if (threadIdx.x < MLSD_SUR_IN - 2 * NMODE * NMODE) {
         const int t = 2 * NMODE * NMODE + threadIdx.x;
         float v = 0.f;
-        if (t == 578) v = (float)(B[3 * p] / kappa);
-        else if (t == 579) v = (float)(B[3 * p + 1] / kappa);
-        else if (t == 580) v = (float)(B[3 * p + 2] / kappa);
+        if (t == 578) v = (float)(B11 / kappa);
+        else if (t == 579) v = (float)(B12 / kappa);
+        else if (t == 580) v = (float)(B22 / kappa);
         else if (t == 581) v = (float)log(kappa);
+        else if (t < 585) v = (float)(MLSD_SUR_Q_SCALE * qsum[t - 582] / (2.0 * trh));
         xr[t] = __float2bfloat16_rn(v);
         if (fr && t < MLSD_SUR_FEATURES) fr[t] = v;
     }
@@ -247,25 +288,26 @@ __global__ void k_to_bf16(long long n, const float *w, __nv_bfloat16 *wb)
     if (i < n) wb[i] = __float2bfloat16_rn(w[i]);
 }
 
-// Ensemble disagreement on K: for every patch, K_m = B + tr(B) out_m; flag when
+// Ensemble disagreement on K: for every patch, K_m = B + Q + tr(B) out_m / YS
+// (Q the second-order estimate from the features); flag when
 //   max_{m,c} |K_m,c - mean_m K_m,c| > thr * ||mean K||_F.
-// Surrogate estimate where not flagged: K = B + tr(B) mean_m out_m.
+// Surrogate estimate where not flagged: K = B + Q + tr(B) mean_m out_m / YS.
 __global__ void k_disagree(long long P, int members, const float *out, const double *B,
-                           double thr, double *K, int *flag)
+                           const double *Q, double thr, double *K, int *flag)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P) return;
-    const double tr = B[3 * p] + B[3 * p + 2];
+    const double tr = (B[3 * p] + B[3 * p + 2]) / MLSD_SUR_Y_SCALE;
     double mean[3] = {0, 0, 0};
     for (int m = 0; m < members; ++m)
         for (int c = 0; c < 3; ++c) mean[c] += (double)out[((long long)m * P + p) * 3 + c];
     double Km[3];
-    for (int c = 0; c < 3; ++c) Km[c] = B[3 * p + c] + tr * mean[c] / members;
+    for (int c = 0; c < 3; ++c) Km[c] = B[3 * p + c] + Q[3 * p + c] + tr * mean[c] / members;
     const double fro = sqrt(Km[0] * Km[0] + 2.0 * Km[1] * Km[1] + Km[2] * Km[2]);
     double dev = 0.0;
     for (int m = 0; m < members; ++m)
         for (int c = 0; c < 3; ++c) {
-            const double km = B[3 * p + c] + tr * (double)out[((long long)m * P + p) * 3 + c];
+            const double km = B[3 * p + c] + Q[3 * p + c] + tr * (double)out[((long long)m * P + p) * 3 + c];
             dev = fmax(dev, fabs(km - Km[c]));
         }
     const int f = !(dev <= thr * fro);           // NaN -> flagged
@@ -321,7 +363,7 @@ long long sur_param_count(int h)
 
 cudaError_t launch_features(const float *band, long long Nl, int n, int n_macro, const int *pidx,
                             long long count, const double *B, double kappa, void *X, float *F32,
-                            cudaStream_t s)
+                            double *Q, cudaStream_t s)
 {
     if (count == 0) return cudaSuccess;
     const size_t smem = (size_t)n * n * 4 + (size_t)n * NMODE * 8;
@@ -330,7 +372,7 @@ cudaError_t launch_features(const float *band, long long Nl, int n, int n_macro,
     if (e != cudaSuccess) return e;
     count_launches(1);
     k_features<<<(unsigned)count, 320, smem, s>>>(band, Nl, n, n_macro, pidx, count, B, kappa,
-                                                  static_cast<__nv_bfloat16 *>(X), F32);
+                                                  static_cast<__nv_bfloat16 *>(X), F32, Q);
     return cudaGetLastError();
 }
 
@@ -427,11 +469,12 @@ cudaError_t sur_to_bf16(long long n, const float *w, void *wb, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t sur_disagree(long long P, int members, const float *out, const double *B, double thr,
-                         double *K, int *flag, int *idx, int *count, cudaStream_t s)
+cudaError_t sur_disagree(long long P, int members, const float *out, const double *B,
+                         const double *Q, double thr, double *K, int *flag, int *idx, int *count,
+                         cudaStream_t s)
 {
     count_launches(2);
-    k_disagree<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(P, members, out, B, thr, K, flag);
+    k_disagree<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(P, members, out, B, Q, thr, K, flag);
     k_compact<<<1, 1024, 0, s>>>(P, flag, idx, count);
     return cudaGetLastError();
 }

@@ -8,24 +8,27 @@ import time
 
 import numpy as np
 
-from . import SUR_IN, Levels, Surrogate
+from . import SUR_FEATURES, SUR_IN, SUR_Q_SCALE, SUR_Y_SCALE, Levels, Surrogate
 
 
 def make_dataset(lv, level, bases):
     """Plain patch solves of one level for each base set: features X (bfloat16
-    [n P][640]) and targets Y = (K - B) / tr(B) (FP32 [n P][3]) on the device."""
+    [n P][640]) and targets Y = (K - B - Q) SUR_Y_SCALE / tr(B) (FP32 [n P][3])
+    on the device, Q the second-order estimate the features carry (mlsd.h)."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     P = lv.P
     X = torch.empty(len(bases) * P, SUR_IN, dtype=torch.bfloat16, device=dev)
     Y = torch.empty(len(bases) * P, 3, dtype=torch.float32, device=dev)
     K = torch.empty(P, 3, dtype=torch.float64, device=dev)
+    F = torch.empty(P, SUR_FEATURES, dtype=torch.float32, device=dev)
     for i, B in enumerate(bases):
         Bd = torch.as_tensor(np.ascontiguousarray(B), dtype=torch.float64, device=dev)
         lv.solve_level(level, Bd, K)
-        lv.features(level, Bd, X[i * P:(i + 1) * P])
+        lv.features(level, Bd, X[i * P:(i + 1) * P], F)
         tr = (Bd[:, 0] + Bd[:, 2]).unsqueeze(1)
-        Y[i * P:(i + 1) * P] = ((K - Bd) / tr).float()
+        q = F[:, 582:585].double() / SUR_Q_SCALE            # Q / tr(B)
+        Y[i * P:(i + 1) * P] = (((K - Bd) / tr - q) * SUR_Y_SCALE).float()
     if lv.status() != 0:
         raise RuntimeError("patch solves reported an error")
     return X, Y

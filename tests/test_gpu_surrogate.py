@@ -49,11 +49,15 @@ def test_features_match_oracle(mlsd, torch_mod, n):
             f = oracle.features(psi, B[p], kappa)
             scale = np.abs(f[:578]).max()
             assert np.abs(Fg[p, :578] - f[:578]).max() < 1e-5 * scale, (level, p)
-            np.testing.assert_allclose(Fg[p, 578:], f[578:], rtol=1e-6)
+            np.testing.assert_allclose(Fg[p, 578:582], f[578:582], rtol=1e-6)
+            # the second-order estimate: sums of squares of FP32 coefficients
+            qs = np.abs(f[582:585]).max()
+            assert np.abs(Fg[p, 582:585] - f[582:585]).max() < 1e-5 * qs, (level, p)
         # the bfloat16 row is the rounded FP32 row, zero padded
         Xg = X.float().cpu().numpy()
-        np.testing.assert_array_equal(Xg[:, :582], F.to(torch_mod.bfloat16).float().cpu().numpy())
-        assert not np.any(Xg[:, 582:])
+        nf = mlsd.SUR_FEATURES
+        np.testing.assert_array_equal(Xg[:, :nf], F.to(torch_mod.bfloat16).float().cpu().numpy())
+        assert not np.any(Xg[:, nf:])
 
 
 def test_gradient_matches_bf16_oracle(mlsd, torch_mod):
@@ -66,7 +70,7 @@ def test_gradient_matches_bf16_oracle(mlsd, torch_mod):
         params[::7] += 0.05                       # nonzero biases too
         sur.set_params(member, params)
         Xf = np.zeros((M, mlsd.SUR_IN), np.float32)
-        Xf[:, :582] = rng.standard_normal((M, 582)).astype(np.float32)
+        Xf[:, :585] = rng.standard_normal((M, 585)).astype(np.float32)
         X = torch_mod.tensor(Xf, device=dev).to(torch_mod.bfloat16)
         Y = torch_mod.tensor(rng.standard_normal((M, 3)) * 0.3, dtype=torch_mod.float32, device=dev)
         g = torch_mod.zeros(sur.n_params, dtype=torch_mod.float32, device=dev)
@@ -129,16 +133,19 @@ def test_surrogate_level_fallback_paths(mlsd, torch_mod):
     K0 = torch_mod.zeros_like(B)
     assert lv.solve_level_surrogate(sur, 2, B, K0, 0.0) == N * N
     assert rel_l2(K0.cpu().numpy(), K_plain.cpu().numpy()) < 1e-6
-    # huge threshold: no fallback, K = B + tr(B) * ensemble mean
+    # huge threshold: no fallback, K = B + Q + tr(B) * ensemble mean / Y_SCALE
     K1 = torch_mod.zeros_like(B)
     assert lv.solve_level_surrogate(sur, 2, B, K1, 1e30) == 0
     X = torch_mod.zeros(N * N, mlsd.SUR_IN, dtype=torch_mod.bfloat16, device=dev)
-    lv.features(2, B, X)
+    F = torch_mod.zeros(N * N, mlsd.SUR_FEATURES, dtype=torch_mod.float32, device=dev)
+    lv.features(2, B, X, F)
     out = torch_mod.zeros(4, N * N, 3, device=dev)
     sur.predict(X, out)
     tr = (B[:, 0] + B[:, 2]).unsqueeze(1)
-    want = B + tr * out.double().mean(0)
-    assert torch_mod.allclose(K1, want, rtol=1e-12, atol=0)
+    Q = F[:, 582:585].double() * tr / mlsd.SUR_Q_SCALE      # FP32-rounded copy of Q
+    want = B + Q + tr * out.double().mean(0) / mlsd.SUR_Y_SCALE
+    assert rel_l2(K1.cpu().numpy(), want.cpu().numpy()) < 1e-6
+    assert torch_mod.allclose(K1, want, rtol=1e-6, atol=0)
     assert lv.status() == 0
 
 
@@ -161,7 +168,7 @@ def test_tensor_core_inference_matches_oracle(mlsd, torch_mod, M, h, tma, monkey
         sur.set_params(m, p)
     dev = torch_mod.device("cuda:0")
     Xf = np.zeros((M, mlsd.SUR_IN), np.float32)
-    Xf[:, :582] = rng.standard_normal((M, 582))
+    Xf[:, :585] = rng.standard_normal((M, 585))
     X = torch_mod.tensor(Xf, device=dev).to(torch_mod.bfloat16)
     out_tc = torch_mod.full((members, M, 3), float("nan"), device=dev)
     sur.set_engine(mlsd.SUR_TENSOR)

@@ -1,6 +1,8 @@
 """Pins of the oracle's surrogate pieces: the patch features are a plain DFT
-(checked against numpy's FFT), and the MLP gradient against central finite
-differences in FP64."""
+(checked against numpy's FFT); the second-order estimate Q they carry equals
+the discrete shear closed form and the patch solve's K - B for shear flows,
+and the patch solve's K - B to O(Pe^4) for a general flow; the MLP gradient
+against central finite differences in FP64."""
 import math
 
 import numpy as np
@@ -17,14 +19,15 @@ def test_features_are_the_normalised_dft():
     psi -= psi.mean()
     B = np.array([0.3, 0.05, 0.5])
     f = oracle.features(psi, B, 0.01)
+    assert f.shape == (585,)
     F = np.fft.fft2(psi) / n ** 2            # F[k2][k1] = n^-2 sum psi[b][a] e^{-2pi i(k1 a + k2 b)/n}
     want = []
     for k2 in range(-8, 9):
         for k1 in range(-8, 9):
-            c = F[k2 % n, k1 % n] / (0.5 * (B[0] + B[2]))
+            c = F[k2 % n, k1 % n] * 32.0 / (0.5 * (B[0] + B[2]))
             want += [c.real, c.imag]
-    np.testing.assert_allclose(f[:578], want, atol=1e-13)
-    np.testing.assert_allclose(f[578:], [30.0, 5.0, 50.0, math.log(0.01)], rtol=1e-14)
+    np.testing.assert_allclose(f[:578], want, atol=1e-11)
+    np.testing.assert_allclose(f[578:582], [30.0, 5.0, 50.0, math.log(0.01)], rtol=1e-14)
 
 
 def test_features_of_a_single_mode():
@@ -33,11 +36,67 @@ def test_features_of_a_single_mode():
     a = np.arange(n)
     psi = np.cos(2 * math.pi * (2 * a[None, :] + 3 * a[:, None]) / n)
     f = oracle.features(psi, np.array([1.0, 0.0, 1.0]), 1.0)
-    c = f[:578].reshape(17, 17, 2)
+    c = f[:578].reshape(17, 17, 2) / 32.0
     assert c[3 + 8, 2 + 8, 0] == pytest.approx(0.5, abs=1e-14)
     assert c[-3 + 8, -2 + 8, 0] == pytest.approx(0.5, abs=1e-14)
     c[3 + 8, 2 + 8, 0] = c[-3 + 8, -2 + 8, 0] = 0
     assert np.abs(c).max() < 1e-14
+
+
+def _steady_K(psi, h, B):
+    # the time-stepped patch estimator run long past its relaxation time
+    v1, v2 = oracle.velocity(psi, h)
+    vmax = float(np.max(np.abs(v1) + np.abs(v2)))
+    dt = oracle.micro_dt(h, vmax, B, 0.2)
+    nb, na = oracle.micro_steps(2 * math.pi, B, dt, 40.0, 4.0)
+    return oracle.patch_k(psi, h, B, dt, nb, na)
+
+
+@pytest.mark.parametrize("k,axis", [(3, 1), (5, 2), (1, 1)])
+def test_second_order_estimate_is_exact_for_shears(k, axis):
+    # psi = a cos(2 pi k x_axis / n): the corrector of a shear solves a linear
+    # equation with no advection of w, so the first-order solution is exact;
+    # K_jj - B_jj = (a^2 / 2) cos^2(t/2) / B_ii (t = 2 pi k / n, i the shear
+    # direction, j the other), and the patch solve gives the same.
+    n, a = 24, 0.07
+    idx = np.arange(n)
+    line = a * np.cos(2 * math.pi * k * idx / n)
+    psi = line[None, :].repeat(n, 0) if axis == 1 else line[:, None].repeat(n, 1)
+    B = np.array([0.031, 0.009, 0.022])
+    f = oracle.features(psi, B, 0.01)
+    Q = oracle.second_order_K(f, B)
+    t = 2 * math.pi * k / n
+    if axis == 1:
+        want = np.array([0.0, 0.0, 0.5 * a * a * math.cos(t / 2) ** 2 / B[0]])
+    else:
+        want = np.array([0.5 * a * a * math.cos(t / 2) ** 2 / B[2], 0.0, 0.0])
+    np.testing.assert_allclose(Q, want, rtol=1e-12, atol=1e-15)
+    h = 2 * math.pi / n
+    K = _steady_K(psi, h, B)
+    np.testing.assert_allclose(K - B, want, rtol=1e-8, atol=1e-13)
+
+
+def test_second_order_estimate_is_the_small_peclet_limit():
+    # a non-shear flow inside the 17 x 17 window with a full-tensor base: the
+    # patch solve's K - B equals Q up to O(Pe^4), so halving the amplitude
+    # shrinks the relative gap about fourfold (a wrong sign on the cross terms
+    # of M or D would leave an O(1) gap)
+    n = 20
+    idx = np.arange(n)
+    A, Bi = np.meshgrid(idx, idx)             # A: a (fast, x1), Bi: b (slow, x2)
+    shape = (np.cos(2 * math.pi * (2 * A + 3 * Bi) / n) + 0.5 * np.sin(2 * math.pi * (A - 2 * Bi) / n)
+             + 0.3 * np.cos(2 * math.pi * 4 * A / n))
+    B = np.array([0.05, 0.012, 0.035])
+    h = 2 * math.pi / n
+    gaps = []
+    for eps in (4e-3, 2e-3):
+        psi = eps * shape
+        Q = oracle.second_order_K(oracle.features(psi, B, 0.01), B)
+        K = _steady_K(psi, h, B)
+        gaps.append(np.linalg.norm(K - B - Q) / np.linalg.norm(Q))
+        assert abs(Q[1]) > 0.05 * abs(Q[0])       # the cross term is exercised
+    assert gaps[0] < 2e-2
+    assert 3.0 < gaps[0] / gaps[1] < 5.0, gaps
 
 
 def _params(d0, h, rng):
