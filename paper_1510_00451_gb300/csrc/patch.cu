@@ -1078,6 +1078,7 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
             add_variant<128, 4, 8, float, 3, 4, 1>(out);
             add_variant<128, 4, 8, float, 3, 4, 2>(out);
             add_variant<128, 4, 8, float, 3, 4, 3>(out);
+            add_variant<128, 4, 4, float, 1, 4, 3>(out);
             add_variant<128, 4, 8, float, 1, 2>(out);
             add_variant<128, 4, 4, float, 1, 4>(out);
             break;
@@ -1090,6 +1091,7 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
             add_variant<256, 4, 8, float, 3, 16, 2>(out);
             add_variant<256, 4, 8, float, 1, 8, 3>(out);
             add_variant<256, 4, 8, float, 3, 16, 3>(out);
+            add_variant<256, 4, 4, float, 1, 8, 3>(out);
             add_variant<256, 4, 4, float, 1, 8>(out);
             add_variant<256, 4, 8, float, 3, 16>(out);
             break;

@@ -462,8 +462,12 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
     PatchParams pp;
     pp.band = c.band; pp.Nl = c.Nl; pp.n_macro = h->N; pp.h = c.h; pp.L = d.L;
     pp.Kb = d.B; pp.S = d.S; pp.wdump = nullptr; pp.status = h->status;
+    // trial window: the problem's own fixed window when it has one (its per-patch
+    // set-up share then counts as it will in the solve), else 64 steps, where the
+    // stepping rate of a long relaxation window dominates
     pp.cfl = h->cfl; pp.t_burn = 8; pp.t_avg = 4; pp.nb_fixed = 0;
-    pp.na_fixed = c.n <= 32 ? 64 : (c.n <= 64 ? 32 : 8);
+    pp.na_fixed = h->na_fixed > 0 ? std::min<long long>(std::max<long long>(h->nb_fixed + h->na_fixed, 8), 64)
+                                  : 64;
     pp.P = h->P; pp.item0 = 0; pp.steps = nullptr; pp.pidx = c.idx;
     pp.items = std::min<long long>(2 * c.count, (long long)sms * (c.n <= 64 ? 48 : 8));
     cudaEvent_t e0, e1;

@@ -186,3 +186,35 @@ def test_tensor_core_inference_matches_oracle(mlsd, torch_mod, M, h, tma, monkey
         ref = oracle.mlp(Xo, params[m].astype(np.float64), h, bf16=True)
         assert rel_l2(out_tc[m].cpu().numpy(), ref) < 1e-3, m
         assert rel_l2(out_cc[m].cpu().numpy(), ref) < 1e-3, m
+
+
+def test_trained_surrogate_replaces_most_patch_solves(mlsd, torch_mod):
+    # What the learned part gains over the method without it: trained on the
+    # library's own plain solves of a level (3 base sets), the ensemble answers
+    # most patches of a fresh base set, and only the patches where its members
+    # disagree are solved again; the answers stay close to the plain solve.
+    from paper_1510_00451_gb300 import surrogate as S
+    full = flows.continuous_spectrum(256)
+    a, b = np.abs(full.k1), np.abs(full.k2)
+    keep = (a >= 32) & (a < 64) & (b >= 32) & (b < 64)
+    band = flows.Spectrum(full.k1[keep], full.k2[keep], full.re[keep], full.im[keep])
+    N, kappa = 64, 1e-3
+    lv = mlsd.Levels(band, kappa, N, [32.0, 64.0], [32], patch_div=[32], cfl=0.2)
+    P = N * N
+    X, Y = S.make_dataset(lv, 1, [inputs.random_bases(P, kappa, 70 + i) for i in range(3)])
+    sur = mlsd.Surrogate(members=4, hidden=128, max_batch=512)
+    for m in range(4):
+        sur.set_params(m, inputs.mlp_init(mlsd.SUR_IN, 128, 90 + m))
+    losses = S.train(sur, X, Y, epochs=60, batch=512, lr=3e-3, seed=1, lr_final=1e-5)
+    assert max(losses) < 0.05                 # targets are O(1): the fit is far below that
+    dev = torch_mod.device("cuda:0")
+    Bt = torch_mod.tensor(inputs.random_bases(P, kappa, 99), dtype=torch_mod.float64, device=dev)
+    K_plain = torch_mod.zeros_like(Bt)
+    lv.solve_level(1, Bt, K_plain)
+    K_sur = torch_mod.zeros_like(Bt)
+    n_fb = lv.solve_level_surrogate(sur, 1, Bt, K_sur, 3e-3)
+    assert lv.status() == 0 and sur.status() == 0
+    err = S.k_error(K_sur.cpu().numpy(), K_plain.cpu().numpy())
+    assert n_fb < P // 2, n_fb                  # most patch solves are replaced
+    assert np.median(err) < 2e-3, np.median(err)
+    assert err.max() < 0.05
