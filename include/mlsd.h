@@ -165,6 +165,26 @@ int mlsd_patch_sizes(const mlsd_levels *h, int level, int32_t *n_out_host);
 int mlsd_solve_level(mlsd_levels *h, int level, const double *K_base_dev, double *K_out_dev,
                      void *w_dump_dev, void *cuda_stream);
 
+/* Energy diagnostic of a level's correctors (HMM step 3, the energy form of
+ * the estimator): from the w_dump of an mlsd_solve_level call with the same
+ * base, per patch
+ *   E_jk = < B11 D+x w_j D+x w_k + B12 (D0x w_j D0y w_k + D0y w_j D0x w_k)
+ *            + B22 D+y w_j D+y w_k >,
+ * with D+ forward and D0 central differences (periodic on the patch), and the
+ * means <w_j>.  Multiplying the steady corrector equation by w_k and summing by
+ * parts gives E = K - B at steady state up to the O(h^2) part of the central
+ * advection term, which is not skew-adjoint on the grid (exactly for shear
+ * flows, whose correctors are not advected): E against the flux estimate is a
+ * resolution and relaxation check.  Evaluated on the final corrector, not
+ * summed over the window.
+ *   K_base_dev device [P][3]; w_dump_dev device [P][2][n][n] (float for MLSD_FP32,
+ *   double for MLSD_FP64); E_out_dev device [P][3] (E11, E12, E22);
+ *   mass_out_dev device [P][2] or NULL.  One patch size per level (else
+ *   MLSD_EINVAL).                                                           */
+int mlsd_corrector_energy(mlsd_levels *h, int level, const double *K_base_dev,
+                          const void *w_dump_dev, double *E_out_dev, double *mass_out_dev,
+                          void *cuda_stream);
+
 /* Algorithms 1-2 of level l for every patch: each off-diagonal part is treated
  * as a shear on every patch line (Eq. shearhomoX/Y with base B), the line
  * values are combined by the layered-medium harmonic mean, and

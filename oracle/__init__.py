@@ -49,6 +49,7 @@ def _declare(L):
     L.orc_micro_steps.argtypes = [_d, _p, _d, _d, _d, _p, _p]
     L.orc_corrector_rhs.argtypes = [_i, _d, _p, _p, _i, _p, _p]
     L.orc_patch_k.argtypes = [_i, _d, _p, _p, _d, _l, _l, _p, _p, _p]
+    L.orc_corrector_energy.argtypes = [_i, _d, _p, _p, _p, _p]
     L.orc_offdiag_q.argtypes = [_i, _p, _p, _p, _p, _p, _p, _l, _l, _l, _i, _d, _p, _p]
     L.orc_offdiag_apply.argtypes = [_i, _p, _p, _p, _p]
     L.orc_chain.argtypes = [_i, _p, _p, _p, _p, _i, _p, _p, _p, _i, _d, _d, _d, _d, _l, _l,
@@ -158,6 +159,14 @@ def patch_k(psi, h, B, dt, n_burn, n_avg, want_w=False, want_S=False):
     if want_S:
         out.append(S)
     return out[0] if len(out) == 1 else tuple(out)
+
+
+def corrector_energy(w, h, B):
+    """Energy form E (E11, E12, E22) and the means of the corrector pair w[2][n][n]."""
+    w = _f64(w); B = _f64(B)
+    E = np.zeros(3); m = np.zeros(2)
+    lib().orc_corrector_energy(w.shape[1], float(h), _ptr(w), _ptr(B), _ptr(E), _ptr(m))
+    return E, m
 
 
 def offdiag_q(spec, use12, use21, Nl, ox, oy, n, L):

@@ -209,6 +209,44 @@ void orc_corrector_rhs(int n, double h, const double *psi, const double *B, int 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Energy form of the corrector pair (the other side of HMM step 3's flux    */
+/* average): for the periodic fields w[2][n][n] and the base B,              */
+/*   E_jk = mean over nodes of  B11 (D+x w_j)(D+x w_k)                       */
+/*          + B12 ((D0x w_j)(D0y w_k) + (D0y w_j)(D0x w_k))                  */
+/*          + B22 (D+y w_j)(D+y w_k),                                        */
+/* D+ forward, D0 central differences; and mass[j] = mean of w_j.  These are */
+/* the forms that summation by parts gives for the stencil of orc_corrector_ */
+/* rhs: at the steady state E = K - B up to the O(h^2) remainder of the      */
+/* central advection term (exactly for shear flows).                         */
+/* ------------------------------------------------------------------------ */
+void orc_corrector_energy(int n, double h, const double *w, const double *B, double *E,
+                          double *mass)
+{
+    const double *w1 = w, *w2 = w + (long)n * n;
+    double e11 = 0.0, e12 = 0.0, e22 = 0.0, m1 = 0.0, m2 = 0.0;
+    for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+            const int ap = (a + 1) % n, am = (a + n - 1) % n, bp = (b + 1) % n, bm = (b + n - 1) % n;
+#define W(f, x, y) f[(long)(y) * n + (x)]
+            const double fx1 = (W(w1, ap, b) - W(w1, a, b)) / h, fy1 = (W(w1, a, bp) - W(w1, a, b)) / h;
+            const double fx2 = (W(w2, ap, b) - W(w2, a, b)) / h, fy2 = (W(w2, a, bp) - W(w2, a, b)) / h;
+            const double cx1 = (W(w1, ap, b) - W(w1, am, b)) / (2.0 * h);
+            const double cy1 = (W(w1, a, bp) - W(w1, a, bm)) / (2.0 * h);
+            const double cx2 = (W(w2, ap, b) - W(w2, am, b)) / (2.0 * h);
+            const double cy2 = (W(w2, a, bp) - W(w2, a, bm)) / (2.0 * h);
+            m1 += W(w1, a, b);
+            m2 += W(w2, a, b);
+#undef W
+            e11 += B[0] * fx1 * fx1 + 2.0 * B[1] * cx1 * cy1 + B[2] * fy1 * fy1;
+            e12 += B[0] * fx1 * fx2 + B[1] * (cx1 * cy2 + cy1 * cx2) + B[2] * fy1 * fy2;
+            e22 += B[0] * fx2 * fx2 + 2.0 * B[1] * cx2 * cy2 + B[2] * fy2 * fy2;
+        }
+    const double nn = (double)n * n;
+    E[0] = e11 / nn; E[1] = e12 / nn; E[2] = e22 / nn;
+    if (mass) { mass[0] = m1 / nn; mass[1] = m2 / nn; }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 2.2 (HMM steps 1-3) and the K[psi, B; D] notation of Sec. 2.2:       */
 /* for each gradient G = e_j the reconstruction is u = G.x + w with w        */
 /* periodic on the patch, w(0) = 0; w is advanced with Heun's RK2 for        */

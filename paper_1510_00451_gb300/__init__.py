@@ -25,7 +25,7 @@ ERRORS = {0: "MLSD_OK", -1: "MLSD_EINVAL", -2: "MLSD_ENOMEM", -3: "MLSD_ECUDA",
 EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_solve_level",
             "mlsd_offdiag", "mlsd_effective_diffusivity", "mlsd_status", "mlsd_macro_step",
             "mlsd_macro_dt", "mlsd_grid_psi", "mlsd_dns_run", "mlsd_coarse_grain",
-            "mlsd_level_work", "mlsd_launch_count", "mlsd_profile", "mlsd_profile_collect",
+            "mlsd_level_work", "mlsd_corrector_energy", "mlsd_launch_count", "mlsd_profile", "mlsd_profile_collect",
             "mlsd_coarse_grain_noalloc", "mlsd_dns_dt", "mlsd_patch_sizes",
             "mlsd_surrogate_param_count", "mlsd_surrogate_create", "mlsd_surrogate_free",
             "mlsd_surrogate_set_params", "mlsd_surrogate_get_params", "mlsd_surrogate_features",
@@ -82,6 +82,7 @@ _lib.mlsd_grid_psi.argtypes = [_I, _P, _P, _P, _P, _I, _P, _P]
 _lib.mlsd_dns_run.argtypes = [_I, _P, _P, _P, _D, _D, _I, _P]
 _lib.mlsd_coarse_grain.argtypes = [_I, _P, _I, _P, _P, _P]
 _lib.mlsd_level_work.argtypes = [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_L), ctypes.POINTER(_L), _P]
+_lib.mlsd_corrector_energy.argtypes = [_P, _I, _P, _P, _P, _P, _P]
 _lib.mlsd_profile.argtypes = [_P, _I]
 _lib.mlsd_profile_collect.argtypes = [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_L)]
 _lib.mlsd_launch_count.argtypes = []
@@ -213,6 +214,12 @@ class Levels:
 
     def status(self, stream=None):
         return _lib.mlsd_status(self.h, _stream(stream))
+
+    def corrector_energy(self, level, K_base, w_dump, E_out, mass_out=None, stream=None):
+        """Energy form E (and the means of w) of the correctors in w_dump."""
+        _check(_lib.mlsd_corrector_energy(self.h, int(level), _dptr(K_base), _dptr(w_dump),
+                                          _dptr(E_out), _dptr(mass_out), _stream(stream)),
+               "mlsd_corrector_energy")
 
     def level_work(self, level, stream=None):
         """(cell-updates, max steps per patch, cell-updates inside the averaging

@@ -204,6 +204,53 @@ __global__ void k_level_base(long long P, int finest, const double *base_next, c
     base_out[3 * p] = K[0]; base_out[3 * p + 1] = K[1]; base_out[3 * p + 2] = K[2];
 }
 
+// Energy form of the corrector pair of one patch (one CTA per patch, FP64 sums):
+//   E_jk = < B11 D+x w_j D+x w_k + B12 (D0x w_j D0y w_k + D0y w_j D0x w_k) + B22 D+y w_j D+y w_k >
+// and the means <w_j>.  Multiplying the steady corrector equation by w_k and
+// summing by parts (D+D- against D+, D0 skew-adjoint) gives E = sym<v w> = K - B
+// up to the O(h^2) remainder of the central advection term, which the grid does
+// not make skew-adjoint (exact for shear flows).
+template <typename real>
+__global__ void __launch_bounds__(256) k_corrector_energy(int n, double h, const real *w, const double *B,
+                                                          double *E, double *M)
+{
+    const long long p = blockIdx.x;
+    const long long nn = (long long)n * n;
+    const real *w1 = w + 2 * p * nn, *w2 = w1 + nn;
+    const double B11 = B[3 * p], B12 = B[3 * p + 1], B22 = B[3 * p + 2];
+    double acc[5] = {0, 0, 0, 0, 0};               // e11, e12, e22, m1, m2
+    for (long long c = threadIdx.x; c < nn; c += blockDim.x) {
+        const int a = (int)(c % n), b = (int)(c / n);
+        const int ap = (a + 1) % n, am = (a + n - 1) % n, bp = (b + 1) % n, bm = (b + n - 1) % n;
+        const double u1 = w1[c], u2 = w2[c];
+        const double fx1 = (double)w1[(long long)b * n + ap] - u1, fy1 = (double)w1[(long long)bp * n + a] - u1;
+        const double fx2 = (double)w2[(long long)b * n + ap] - u2, fy2 = (double)w2[(long long)bp * n + a] - u2;
+        const double cx1 = 0.5 * ((double)w1[(long long)b * n + ap] - (double)w1[(long long)b * n + am]);
+        const double cy1 = 0.5 * ((double)w1[(long long)bp * n + a] - (double)w1[(long long)bm * n + a]);
+        const double cx2 = 0.5 * ((double)w2[(long long)b * n + ap] - (double)w2[(long long)b * n + am]);
+        const double cy2 = 0.5 * ((double)w2[(long long)bp * n + a] - (double)w2[(long long)bm * n + a]);
+        acc[0] += B11 * fx1 * fx1 + 2.0 * B12 * cx1 * cy1 + B22 * fy1 * fy1;
+        acc[1] += B11 * fx1 * fx2 + B12 * (cx1 * cy2 + cy1 * cx2) + B22 * fy1 * fy2;
+        acc[2] += B11 * fx2 * fx2 + 2.0 * B12 * cx2 * cy2 + B22 * fy2 * fy2;
+        acc[3] += u1;
+        acc[4] += u2;
+    }
+    __shared__ double red[5][8];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
+        if (threadIdx.x < 3) E[3 * p + threadIdx.x] = t / ((double)nn * h * h);
+        else if (M) M[2 * p + threadIdx.x - 3] = t / (double)nn;
+    }
+}
+
 __global__ void k_offdiag_apply(long long P, OffdiagLevel off, const double *B, double *Koff)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -272,6 +319,18 @@ cudaError_t launch_level_base(long long P, int finest, const double *base_next,
     k_level_base<<<(unsigned)((P + th - 1) / th), th, 0, s>>>(P, finest, base_next, S_next,
                                                                Kstar_next, Koff_l, B_l, off,
                                                                base_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_corrector_energy(int n, double h, long long P, int precision, const void *w,
+                                   const double *B, double *E, double *M, cudaStream_t s)
+{
+    if (P == 0) return cudaSuccess;
+    count_launches(1);
+    if (precision == MLSD_FP64)
+        k_corrector_energy<double><<<(unsigned)P, 256, 0, s>>>(n, h, static_cast<const double *>(w), B, E, M);
+    else
+        k_corrector_energy<float><<<(unsigned)P, 256, 0, s>>>(n, h, static_cast<const float *>(w), B, E, M);
     return cudaGetLastError();
 }
 

@@ -756,6 +756,18 @@ int mlsd_status(mlsd_levels *h, void *cuda_stream)
     return v;
 }
 
+int mlsd_corrector_energy(mlsd_levels *h, int level, const double *K_base_dev, const void *w_dump_dev,
+                          double *E_out_dev, double *mass_out_dev, void *cuda_stream)
+{
+    if (!h || level < 1 || level > h->L || !K_base_dev || !w_dump_dev || !E_out_dev) return MLSD_EINVAL;
+    const DevLevel &d = h->lev[level - 1];
+    if (d.cls.size() != 1) return MLSD_EINVAL;                  // the dump layout needs one size
+    const SizeClass &c = d.cls[0];
+    CK(launch_corrector_energy(c.n, c.h, h->P, h->precision, w_dump_dev, K_base_dev, E_out_dev,
+                               mass_out_dev, static_cast<cudaStream_t>(cuda_stream)));
+    return MLSD_OK;
+}
+
 int mlsd_level_work(mlsd_levels *h, int level, int64_t *cell_updates_out,
                     int64_t *window_updates_out, int64_t *max_steps_out, void *cuda_stream)
 {

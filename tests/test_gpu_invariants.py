@@ -1,6 +1,7 @@
 """The oracle's pins applied to the GPU's own output: discrete shear closed
 forms with a full-tensor base, the symmetry of the cellular flow, positive
-semidefinite enhancement K - B, and conservation of the corrector's mean."""
+semidefinite enhancement K - B, conservation of the corrector's mean, and the
+energy form of the correctors (equal to K - B for a shear)."""
 import math
 
 import numpy as np
@@ -104,3 +105,49 @@ def test_corrector_mean_is_conserved_on_gpu(mlsd, torch_mod):
         for j in range(2):
             assert abs(w[p, j].sum(dtype=np.float64)) < 1e-5 * np.abs(w[p, j]).sum(dtype=np.float64)
         assert np.abs(w[p]).max() > 1e-3
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("fp64", 1e-10)])
+def test_energy_form_on_gpu(mlsd, torch_mod, prec, tol):
+    # the energy form of the GPU's own correctors: for a diagonal shear with a
+    # full-tensor base it equals K - B (the correctors are not advected), and
+    # for a general flow it matches the oracle's energy form of the oracle's
+    # correctors on the same patches
+    dev = torch_mod.device("cuda:0")
+    dtype = torch_mod.float64 if prec == "fp64" else torch_mod.float32
+    N, n = 2, 32
+    lv = mlsd.Levels(flows.shear_diag(0.6, 2), 0.1, N, [1, 8], [n], n_burn_fixed=3000,
+                     n_avg_fixed=500, precision=prec)
+    B = np.tile([0.3, 0.08, 0.2], (N * N, 1))
+    Bd = torch_mod.tensor(B, dtype=torch_mod.float64, device=dev)
+    K = torch_mod.zeros_like(Bd)
+    w = torch_mod.zeros(N * N, 2, n, n, dtype=dtype, device=dev)
+    lv.solve_level(1, Bd, K, w)
+    E = torch_mod.zeros_like(Bd)
+    M = torch_mod.zeros(N * N, 2, dtype=torch_mod.float64, device=dev)
+    lv.corrector_energy(1, Bd, w, E, M)
+    assert lv.status() == 0
+    Kc, Ec = K.cpu().numpy(), E.cpu().numpy()
+    for p in range(N * N):
+        np.testing.assert_allclose(Ec[p], Kc[p] - B[p], rtol=tol, atol=tol * np.abs(Kc[p] - B[p]).max())
+    mtol = 2e-5 if prec == "fp32" else 1e-12
+    assert np.abs(M.cpu().numpy()).max() < mtol * float(w.abs().max())
+
+    spec = flows.cellular_two_scale(0.8, 0.5, 4)
+    edges, pn, N = [1, 4, 8], [n, n], 3
+    lv = mlsd.Levels(spec, 0.03, N, edges, pn, n_burn_fixed=200, n_avg_fixed=100, precision=prec)
+    B = random_spd(N * N, np.random.default_rng(4), 0.03, 0.1)
+    Bd = torch_mod.tensor(B, dtype=torch_mod.float64, device=dev)
+    K = torch_mod.zeros_like(Bd)
+    w = torch_mod.zeros(N * N, 2, n, n, dtype=dtype, device=dev)
+    lv.solve_level(2, Bd, K, w)
+    E = torch_mod.zeros_like(Bd)
+    lv.corrector_energy(2, Bd, w, E)
+    Ec = E.cpu().numpy()
+    from tests._parity import oracle_level, level_geometry, rel_l2
+    ref = oracle_level(spec, edges, pn, 2, N, B, list(range(N * N)), n_burn_fixed=200,
+                       n_avg_fixed=100, want_w=True)
+    h = level_geometry(edges, pn, 2)[2]
+    for p, (_, w_or) in enumerate(ref):
+        E_or, _ = oracle.corrector_energy(w_or, h, B[p])
+        assert rel_l2(Ec[p], E_or) < (1e-4 if prec == "fp32" else 1e-10), (p, Ec[p], E_or)

@@ -175,3 +175,46 @@ def test_micro_dt_and_window_rules():
     assert nb == math.ceil(8 * tau / dt) and na == math.ceil(4 * tau / dt)
     # pure diffusion: only the diffusive bound
     assert oracle.micro_dt(h, 0.0, B, 0.2) == pytest.approx(0.2 * h * h / 0.06)
+
+
+def _steady(psi, h, B, want_w=False):
+    v1, v2 = oracle.velocity(psi, h)
+    vmax = float(np.max(np.abs(v1) + np.abs(v2)))
+    dt = oracle.micro_dt(h, vmax, B, 0.2)
+    nb, na = oracle.micro_steps(2 * math.pi, B, dt, 40.0, 4.0)
+    return oracle.patch_k(psi, h, B, dt, nb, na, want_w=want_w)
+
+
+@pytest.mark.parametrize("flow", ["x1", "x2", "diag"])
+def test_energy_form_is_exact_for_shears(flow):
+    # for a shear the advection of w vanishes (w depends on the shear coordinate
+    # only, and for the diagonal shear D0x w = D0y w against v1 = -v2), so summing
+    # the steady corrector equation against w_k by parts gives E = K - B exactly;
+    # the diagonal shear with B12 != 0 pins the mixed-derivative term's form
+    n = 16
+    spec = {"x1": inputs.flows.shear_x1(0.7, 3, 0.2), "x2": inputs.flows.shear_x2(0.5, 2),
+            "diag": inputs.flows.shear_diag(0.6, 2)}[flow]
+    psi, h = _patch(spec, n)
+    B = np.array([0.4, 0.09, 0.25])
+    K, w = _steady(psi, h, B, want_w=True)
+    E, mass = oracle.corrector_energy(w, h, B)
+    np.testing.assert_allclose(E, K - B, rtol=1e-9, atol=1e-13)
+    assert np.abs(K - B).max() > 1e-2
+    assert np.abs(mass).max() < 1e-13 * np.abs(w).max()
+
+
+def test_energy_form_converges_to_flux_form():
+    # for a general flow the central advection term is not skew-adjoint on the
+    # grid, so E and K - B differ by the O(h^2) truncation: doubling n cuts the
+    # gap about fourfold (a plain sum by parts would have made it vanish)
+    spec = inputs.flows.combine(inputs.flows.cellular_two_scale(0.6, 0.25, 2),
+                                inputs.flows.shear_x2(0.3, 3, 0.5))
+    B = np.array([0.45, 0.08, 0.3])
+    gaps = []
+    for n in (16, 32):
+        psi, h = _patch(spec, n)
+        K, w = _steady(psi, h, B, want_w=True)
+        E, _ = oracle.corrector_energy(w, h, B)
+        gaps.append(np.linalg.norm(E - (K - B)) / np.linalg.norm(K - B))
+    assert gaps[0] > 1e-4
+    assert 3.0 < gaps[0] / gaps[1] < 5.0, gaps
