@@ -127,7 +127,8 @@ typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and 
  * that advances both fields of a patch in f32x2 pairs; c: CTAs per patch field;
  * s: split-phase stage barriers; n: neighbour signalling between the slabs of
  * a cluster instead of a cluster-wide barrier; b: the slab edge rows moved by
- * bulk copies that complete on the receiver's mbarrier).
+ * bulk copies that complete on the receiver's mbarrier).  MLSD_TUNE_LOG set to
+ * anything prints every candidate's trial time to stderr.
  * Patch sizes 32 and 64 run one CTA per field (or per patch, packed); 128 and
  * 256 split each field over a thread-block cluster of 2-16 CTAs that exchange
  * their slab edges through distributed shared memory.

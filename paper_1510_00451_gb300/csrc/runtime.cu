@@ -486,6 +486,10 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
             if (ok && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t = std::min(t, ms);
         }
         if (!ok) { cudaGetLastError(); continue; }   // a tiling this device cannot launch
+        if (std::getenv("MLSD_TUNE_LOG"))
+            std::fprintf(stderr, "mlsd tune n=%d items=%lld steps=%lld %dx%d m%d c%d sync%d%s: %.4f ms\n",
+                         c.n, pp.items, pp.na_fixed, v.bx, v.by, v.minb, v.cluster, v.split,
+                         v.packed ? " packed" : "", t);
         if (t < best) { best = t; c.variant = v; }
     }
     cudaEventDestroy(e0);
