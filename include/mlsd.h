@@ -265,6 +265,29 @@ int mlsd_surrogate_grad(mlsd_surrogate *s, int member, const void *X_dev, const 
 int mlsd_surrogate_train_step(mlsd_surrogate *s, int member, const void *X_dev,
                               const float *Y_dev, int M, float lr, double *loss_host,
                               void *cuda_stream);
+/* Training data of one level, all on the device: the plain patch solve of
+ * every patch with base B_dev [P][3], its features X_dev (bfloat16 [P][640])
+ * and targets Y_dev (FP32 [P][3]) = (K - B - Q) MLSD_SUR_Y_SCALE / tr(B), Q
+ * the features' second-order estimate in FP64.  Same level limits as
+ * mlsd_surrogate_features.                                                  */
+int mlsd_surrogate_dataset(mlsd_levels *h, int level, const double *B_dev, void *X_dev,
+                           float *Y_dev, void *cuda_stream);
+/* Train every member with Adam on the n_rows rows of (X_dev, Y_dev) for
+ * `epochs` passes in batches of `batch` (<= max_batch) rows; n_rows / batch
+ * steps per epoch.  Each member draws its own row order per epoch (Fisher-Yates
+ * on a SplitMix64 stream seeded from `seed` and the member index; the rows are
+ * gathered on the device); the learning rate decays geometrically from lr to
+ * lr_final over the run.  losses_host (or NULL) receives each member's mean
+ * batch loss over the last epoch.  Blocks at the end of each member.        */
+int mlsd_surrogate_train(mlsd_surrogate *s, const void *X_dev, const float *Y_dev, int64_t n_rows,
+                         int epochs, int batch, float lr, float lr_final, uint64_t seed,
+                         double *losses_host, void *cuda_stream);
+/* Checkpoint: every member's FP32 parameters in one file (magic "MLSDSUR1",
+ * int64 members, hidden, parameter count, then the arrays).  load requires
+ * the same members and width and resets the Adam state; MLSD_EINVAL on any
+ * file or shape mismatch.  Both synchronise the device.                     */
+int mlsd_surrogate_save(mlsd_surrogate *s, const char *path);
+int mlsd_surrogate_load(mlsd_surrogate *s, const char *path);
 /* Inference engine: MLSD_SUR_TENSOR (default where the width allows: one
  * tcgen05 kernel running all layers of a member on 128-row tiles, bfloat16
  * operands in shared memory, FP32 accumulators in tensor memory) or

@@ -31,7 +31,8 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_surrogate_set_params", "mlsd_surrogate_get_params", "mlsd_surrogate_features",
             "mlsd_surrogate_grad", "mlsd_surrogate_train_step", "mlsd_surrogate_predict",
             "mlsd_solve_level_surrogate", "mlsd_surrogate_set_engine", "mlsd_surrogate_status",
-            "mlsd_strerror"]
+            "mlsd_surrogate_dataset", "mlsd_surrogate_train", "mlsd_surrogate_save",
+            "mlsd_surrogate_load", "mlsd_strerror"]
 SUR_CUDA, SUR_TENSOR = 0, 1
 SUR_IN, SUR_FEATURES = 640, 585
 SUR_PSI_SCALE, SUR_Q_SCALE, SUR_Y_SCALE = 32.0, 10.0, 30.0
@@ -103,6 +104,11 @@ _lib.mlsd_surrogate_train_step.argtypes = [_P, _I, _P, _P, _I, ctypes.c_float, c
 _lib.mlsd_surrogate_predict.argtypes = [_P, _P, _L, _P, _P]
 _lib.mlsd_solve_level_surrogate.argtypes = [_P, _P, _I, _P, _P, _D, ctypes.POINTER(_L), _P]
 _lib.mlsd_surrogate_set_engine.argtypes = [_P, _I]
+_lib.mlsd_surrogate_dataset.argtypes = [_P, _I, _P, _P, _P, _P]
+_lib.mlsd_surrogate_train.argtypes = [_P, _P, _P, _L, _I, _I, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_uint64, _P, _P]
+_lib.mlsd_surrogate_save.argtypes = [_P, ctypes.c_char_p]
+_lib.mlsd_surrogate_load.argtypes = [_P, ctypes.c_char_p]
 _lib.mlsd_surrogate_status.argtypes = [_P, _P]
 _lib.mlsd_strerror.argtypes = [_I]
 _lib.mlsd_strerror.restype = ctypes.c_char_p
@@ -190,6 +196,11 @@ class Levels:
         """Surrogate inputs of every patch: X bfloat16 [P][640], F32 [P][585] or None."""
         _check(_lib.mlsd_surrogate_features(self.h, int(level), _dptr(B), _dptr(X), _dptr(F32),
                                             _stream(stream)), "mlsd_surrogate_features")
+
+    def surrogate_dataset(self, level, B, X, Y, stream=None):
+        """Plain solves, features X and targets Y of every patch (mlsd_surrogate_dataset)."""
+        _check(_lib.mlsd_surrogate_dataset(self.h, int(level), _dptr(B), _dptr(X), _dptr(Y),
+                                           _stream(stream)), "mlsd_surrogate_dataset")
 
     def solve_level_surrogate(self, sur, level, K_base, K_out, threshold, stream=None):
         """Surrogate level solve; returns the number of plain fallback solves."""
@@ -346,6 +357,22 @@ class Surrogate:
                                               float(lr), ctypes.byref(loss) if want_loss else None,
                                               _stream(stream)), "mlsd_surrogate_train_step")
         return loss.value if want_loss else None
+
+    def train(self, X, Y, epochs, batch, lr, lr_final=None, seed=0, stream=None):
+        """Adam on every member over the rows of (X, Y) (mlsd_surrogate_train);
+        returns each member's mean loss over the last epoch."""
+        losses = np.zeros(self.members)
+        lr_final = lr if lr_final is None else lr_final
+        _check(_lib.mlsd_surrogate_train(self.s, _dptr(X), _dptr(Y), X.shape[0], int(epochs),
+                                         int(batch), float(lr), float(lr_final), int(seed),
+                                         losses.ctypes.data, _stream(stream)), "mlsd_surrogate_train")
+        return losses.tolist()
+
+    def save(self, path):
+        _check(_lib.mlsd_surrogate_save(self.s, str(path).encode()), "mlsd_surrogate_save")
+
+    def load(self, path):
+        _check(_lib.mlsd_surrogate_load(self.s, str(path).encode()), "mlsd_surrogate_load")
 
     def set_engine(self, engine):
         _check(_lib.mlsd_surrogate_set_engine(self.s, int(engine)), "mlsd_surrogate_set_engine")

@@ -248,9 +248,6 @@ struct Tile {
     }
 
     // halos of block (tx, ty) from buffer `buf`, all local after the barrier
-    // PART: 1 the column halos, 2 the south row and its corners, 4 the north row
-    // and its corners
-    template <int PART = 7>
     __device__ __forceinline__ static void load_halos(real *sm, int buf, int tx, int ty,
                                                       real (&hS)[BX], real (&hN)[BX],
                                                       real (&hW)[BY + 2], real (&hE)[BY + 2])
@@ -264,16 +261,13 @@ struct Tile {
         const int txW = (tx + NBX - 1) % NBX, txE = (tx + 1) % NBX;
         const real *cw = colR + txW * S::CS;
         const real *ce = colL + txE * S::CS;
-        if constexpr ((PART & 1) != 0) {
-            real tmpw[BY], tmpe[BY];
-            ld_vec<real, BY>(tmpw, cw + b0);
-            ld_vec<real, BY>(tmpe, ce + b0);
+        real tmpw[BY], tmpe[BY];
+        ld_vec<real, BY>(tmpw, cw + b0);
+        ld_vec<real, BY>(tmpe, ce + b0);
 #pragma unroll
-            for (int k = 0; k < BY; ++k) { hW[k + 1] = tmpw[k]; hE[k + 1] = tmpe[k]; }
-        }
+        for (int k = 0; k < BY; ++k) { hW[k + 1] = tmpw[k]; hE[k + 1] = tmpe[k]; }
         const int aw = (a0 + N - 1) % N, ae = (a0 + BX) % N;
-        if constexpr ((PART & 2) == 0) {
-        } else if (C > 1 && ty == 0) {
+        if (C > 1 && ty == 0) {
             const real *HS = colR + S::COL;
             ld_vec<real, BX>(hS, HS + a0);
             hW[0] = HS[aw]; hE[0] = HS[ae];
@@ -282,8 +276,7 @@ struct Tile {
             const int bs = (b0 + NS - 1) % NS;
             hW[0] = cw[bs]; hE[0] = ce[bs];
         }
-        if constexpr ((PART & 4) == 0) {
-        } else if (C > 1 && ty == NBY - 1) {
+        if (C > 1 && ty == NBY - 1) {
             const real *HN = colR + S::COL + N;
             ld_vec<real, BX>(hN, HN + a0);
             hW[BY + 1] = HN[aw]; hE[BY + 1] = HN[ae];
@@ -335,7 +328,11 @@ struct Tile {
                 bulk_to_rank((uint32_t)__cvta_generic_to_shared(HN),
                              (uint32_t)__cvta_generic_to_shared(rowT), bytes, mbar, (rank + C - 1) % C);
             }
-            if constexpr (NBY == 1) wait_rows(mbar, parity, status, tx);
+            if (ty == 0 || ty == NBY - 1) {
+                if (!nbr_wait(mbar, parity, status)) atomicCAS(status, 0, MLSD_ETIMEOUT);
+                // thread 0 re-arms this buffer's barrier for its next phase
+                if (tx == 0 && ty == 0) arm_tx(mbar, (uint32_t)(2 * N * sizeof(real)));
+            }
         } else if constexpr (SYNC == 2 && C > 1) {
             if (ty == NBY - 1) nbr_arrive(mbar, (rank + 1) % C);       // its HS slot
             if (ty == 0) nbr_arrive(mbar, (rank + C - 1) % C);         // its HN slot
@@ -347,79 +344,20 @@ struct Tile {
         }
         // halos: south row b0-1, north row b0+BY, west column a0-1, east column a0+BX
         real hS[BX], hN[BX], hW[BY + 2], hE[BY + 2];
-        real dm[BX], d0[BX];
-        if constexpr (SYNC == 3 && C > 1 && NBY > 1) {
-            // rows that need no halo row from a neighbouring slab are computed
-            // while that row is in flight; the edge row follows the wait
-            if (ty == 0) {
-                load_halos<5>(sm, buf, tx, ty, hS, hN, hW, hE);
-                dline<0>(x, hS, hN, hW, hE, dm);
-                dline<1>(x, hS, hN, hW, hE, d0);
-                rows<J, SECOND, 1, BY>(x, out, aE, aN, k, hS, hN, hW, hE, dm, d0);
-                wait_rows(mbar, parity, status, tx);
-                load_halos<2>(sm, buf, tx, ty, hS, hN, hW, hE);
-                dline<-1>(x, hS, hN, hW, hE, dm);
-                dline<0>(x, hS, hN, hW, hE, d0);
-                rows<J, SECOND, 0, 1>(x, out, aE, aN, k, hS, hN, hW, hE, dm, d0);
-            } else if (ty == NBY - 1) {
-                load_halos<3>(sm, buf, tx, ty, hS, hN, hW, hE);
-                dline<-1>(x, hS, hN, hW, hE, dm);
-                dline<0>(x, hS, hN, hW, hE, d0);
-                rows<J, SECOND, 0, BY - 1>(x, out, aE, aN, k, hS, hN, hW, hE, dm, d0);
-                wait_rows(mbar, parity, status, tx);
-                load_halos<4>(sm, buf, tx, ty, hS, hN, hW, hE);
-                rows<J, SECOND, BY - 1, BY>(x, out, aE, aN, k, hS, hN, hW, hE, dm, d0);
-            } else {
-                load_halos(sm, buf, tx, ty, hS, hN, hW, hE);
-                dline<-1>(x, hS, hN, hW, hE, dm);
-                dline<0>(x, hS, hN, hW, hE, d0);
-                rows<J, SECOND, 0, BY>(x, out, aE, aN, k, hS, hN, hW, hE, dm, d0);
-            }
-            return;
-        }
         load_halos(sm, buf, tx, ty, hS, hN, hW, hE);
         // rolling E-W differences of rows r-1, r, r+1
-        dline<-1>(x, hS, hN, hW, hE, dm);
-        dline<0>(x, hS, hN, hW, hE, d0);
-        rows<J, SECOND, 0, BY>(x, out, aE, aN, k, hS, hN, hW, hE, dm, d0);
-    }
-
-    // E-W difference of block row r (-1: the south halo row, BY: the north one)
-    template <int R>
-    __device__ __forceinline__ static void dline(const real (&x)[BY][BX], const real (&hS)[BX],
-                                                 const real (&hN)[BX], const real (&hW)[BY + 2],
-                                                 const real (&hE)[BY + 2], real (&d)[BX])
-    {
+        real dm[BX], d0[BX], dp[BX];
 #pragma unroll
         for (int c = 0; c < BX; ++c) {
-            real e, w;
-            if constexpr (R < 0) {
-                e = (c + 1 < BX) ? hS[c + 1] : hE[0];
-                w = (c > 0) ? hS[c - 1] : hW[0];
-            } else if constexpr (R >= BY) {
-                e = (c + 1 < BX) ? hN[c + 1] : hE[BY + 1];
-                w = (c > 0) ? hN[c - 1] : hW[BY + 1];
-            } else {
-                e = (c + 1 < BX) ? x[R][c + 1] : hE[R + 1];
-                w = (c > 0) ? x[R][c - 1] : hW[R + 1];
-            }
-            d[c] = e - w;
+            real e = (c + 1 < BX) ? hS[c + 1] : hE[0];
+            real w = (c > 0) ? hS[c - 1] : hW[0];
+            dm[c] = e - w;
+            real e0 = (c + 1 < BX) ? x[0][c + 1] : hE[1];
+            real w0 = (c > 0) ? x[0][c - 1] : hW[1];
+            d0[c] = e0 - w0;
         }
-    }
-
-    // Block rows R0 .. R1-1 of a stage; on entry dm, d0 hold the E-W differences
-    // of rows R0-1 and R0, on exit those of rows R1-1 and R1.
-    template <int J, bool SECOND, int R0, int R1>
-    __device__ __forceinline__ static void rows(const real (&x)[BY][BX], real (&out)[BY][BX],
-                                                const real (&aE)[BY][BX], const real (&aN)[BY][BX],
-                                                const Coef<real> &k, const real (&hS)[BX],
-                                                const real (&hN)[BX], const real (&hW)[BY + 2],
-                                                const real (&hE)[BY + 2], real (&dm)[BX],
-                                                real (&d0)[BX])
-    {
 #pragma unroll
-        for (int r = R0; r < R1; ++r) {
-            real dp[BX];
+        for (int r = 0; r < BY; ++r) {
 #pragma unroll
             for (int c = 0; c < BX; ++c) {
                 real e, w;
@@ -435,23 +373,17 @@ struct Tile {
 #pragma unroll
             for (int c = 0; c < BX; ++c) {
                 const real xc = x[r][c];
+                const real xE = (c + 1 < BX) ? x[r][c + 1] : hE[r + 1];
                 const real xW = (c > 0) ? x[r][c - 1] : hW[r + 1];
                 const real xN = (r + 1 < BY) ? x[r + 1][c] : hN[c];
                 const real xS = (r > 0) ? x[r - 1][c] : hS[c];
+                (void)xE;
                 cell<J, SECOND>(out[r][c], xc, xW, xN, xS, d0[c], dm[c], dp[c], aE[r][c],
                                 aN[r][c], k);
             }
 #pragma unroll
             for (int c = 0; c < BX; ++c) { dm[c] = d0[c]; d0[c] = dp[c]; }
         }
-    }
-
-    // the two incoming halo rows of this stage buffer; thread 0 then re-arms
-    // the barrier for the buffer's next phase
-    __device__ __forceinline__ static void wait_rows(uint32_t mbar, uint32_t parity, int *status, int tx)
-    {
-        if (!nbr_wait(mbar, parity, status)) atomicCAS(status, 0, MLSD_ETIMEOUT);
-        if (tx == 0 && threadIdx.x == 0) arm_tx(mbar, (uint32_t)(2 * N * sizeof(real)));
     }
 
     // One cell of a stage (see stage()): dEW = xE - xW of this row, dm / dp those

@@ -1099,6 +1099,129 @@ int mlsd_surrogate_train_step(mlsd_surrogate *s, int member, const void *X_dev,
     return MLSD_OK;
 }
 
+int mlsd_surrogate_dataset(mlsd_levels *h, int level, const double *B_dev, void *X_dev, float *Y_dev,
+                           void *cuda_stream)
+{
+    if (!h || level < 1 || level > h->L || !B_dev || !X_dev || !Y_dev) return MLSD_EINVAL;
+    DevLevel &d = h->lev[level - 1];
+    if (d.cls.size() != 1 || d.cls[0].n > 64 || h->precision != MLSD_FP32) return MLSD_EUNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const long long P = h->P;
+    double *ws = nullptr;
+    CK(cudaMallocAsync((void **)&ws, (size_t)P * 6 * 8, st));
+    double *K = ws, *Q = ws + 3 * P;
+    int rc = mlsd_solve_level(h, level, B_dev, K, nullptr, cuda_stream);
+    cudaError_t e = cudaSuccess;
+    const SizeClass &c = d.cls[0];
+    if (!rc) e = launch_features(static_cast<const float *>(c.band), c.Nl, c.n, h->N, nullptr, P, B_dev,
+                                 h->kappa, X_dev, nullptr, Q, st);
+    if (!rc && e == cudaSuccess) e = sur_targets(P, B_dev, K, Q, Y_dev, st);
+    cudaFreeAsync(ws, st);
+    if (rc) return rc;
+    CK(e);
+    return MLSD_OK;
+}
+
+namespace {
+uint64_t splitmix64(uint64_t &x)
+{
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+}  // namespace
+
+int mlsd_surrogate_train(mlsd_surrogate *s, const void *X_dev, const float *Y_dev, int64_t n_rows,
+                         int epochs, int batch, float lr, float lr_final, uint64_t seed,
+                         double *losses_host, void *cuda_stream)
+{
+    if (!s || !X_dev || !Y_dev || epochs < 1 || batch < 1 || batch > s->max_batch ||
+        n_rows < batch || n_rows > (int64_t)0x7fffffff || !(lr > 0) || !(lr_final > 0))
+        return MLSD_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const long long steps = n_rows / batch, total = steps * epochs;
+    char *ws = nullptr;
+    const size_t xb = (size_t)batch * MLSD_SUR_IN * 2, yb = (size_t)batch * 3 * 4, ib = (size_t)n_rows * 4;
+    CK(cudaMallocAsync((void **)&ws, xb + yb + ib + 16, st));
+    void *Xb = ws;
+    float *Yb = reinterpret_cast<float *>(ws + xb);
+    int *idx = reinterpret_cast<int *>(ws + xb + yb);
+    double *acc = reinterpret_cast<double *>(ws + xb + yb + ((ib + 7) / 8) * 8);
+    std::vector<int> perm((size_t)n_rows);
+    cudaError_t e = cudaSuccess;
+    for (int m = 0; m < s->members && e == cudaSuccess; ++m) {
+        // each member its own shuffles: Fisher-Yates on a SplitMix64 stream
+        uint64_t rs = seed * 0x9E3779B97F4A7C15ull + (uint64_t)m;
+        long long t = 0;
+        e = cudaMemsetAsync(acc, 0, 8, st);
+        for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+            for (int64_t i = 0; i < n_rows; ++i) perm[(size_t)i] = (int)i;
+            for (int64_t i = n_rows - 1; i > 0; --i) {
+                const int64_t j = (int64_t)(splitmix64(rs) % (uint64_t)(i + 1));
+                std::swap(perm[(size_t)i], perm[(size_t)j]);
+            }
+            e = cudaMemcpyAsync(idx, perm.data(), ib, cudaMemcpyHostToDevice, st);
+            for (long long q = 0; q < steps && e == cudaSuccess; ++q, ++t) {
+                const float r = lr * (float)std::pow((double)lr_final / lr, (double)t / (double)std::max(1LL, total - 1));
+                e = sur_gather(batch, idx + q * batch, X_dev, Y_dev, Xb, Yb, st);
+                if (e == cudaSuccess)
+                    e = sur_grad(s->h, batch, Xb, Yb, s->w[m], s->wb[m], s->Z, s->A, s->dA, s->dB,
+                                 s->g[m], s->part, s->loss, st);
+                s->t[m] += 1;
+                if (e == cudaSuccess)
+                    e = sur_adam(s->np, s->w[m], s->g[m], s->m[m], s->v[m], r, s->t[m], s->wb[m], st);
+                if (e == cudaSuccess && ep == epochs - 1) e = sur_add_loss(s->loss, acc, st);
+            }
+            // the host permutation buffer is refilled next epoch: the copy above must have
+            // read it (pageable copies are staged before the call returns)
+        }
+        if (e == cudaSuccess && losses_host) {
+            double a = 0.0;
+            e = cudaMemcpyAsync(&a, acc, 8, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            losses_host[m] = a / (double)steps;
+        }
+    }
+    cudaFreeAsync(ws, st);
+    CK(e);
+    return MLSD_OK;
+}
+
+int mlsd_surrogate_save(mlsd_surrogate *s, const char *path)
+{
+    if (!s || !path) return MLSD_EINVAL;
+    std::vector<float> buf((size_t)s->np);
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return MLSD_EINVAL;
+    const char magic[8] = {'M', 'L', 'S', 'D', 'S', 'U', 'R', '1'};
+    const int64_t hdr[3] = {s->members, s->h, s->np};
+    bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, 8, 3, f) == 3;
+    for (int m = 0; m < s->members && ok; ++m) {
+        ok = mlsd_surrogate_get_params(s, m, buf.data()) == MLSD_OK &&
+             std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? MLSD_OK : MLSD_EINVAL;
+}
+
+int mlsd_surrogate_load(mlsd_surrogate *s, const char *path)
+{
+    if (!s || !path) return MLSD_EINVAL;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return MLSD_EINVAL;
+    char magic[8];
+    int64_t hdr[3];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "MLSDSUR1", 8) == 0 &&
+              std::fread(hdr, 8, 3, f) == 3 && hdr[0] == s->members && hdr[1] == s->h && hdr[2] == s->np;
+    std::vector<float> buf((size_t)s->np);
+    for (int m = 0; m < s->members && ok; ++m)
+        ok = std::fread(buf.data(), 4, buf.size(), f) == buf.size() &&
+             mlsd_surrogate_set_params(s, m, buf.data()) == MLSD_OK;
+    std::fclose(f);
+    return ok ? MLSD_OK : MLSD_EINVAL;
+}
+
 int mlsd_surrogate_set_engine(mlsd_surrogate *s, int engine)
 {
     if (!s || (engine != MLSD_SUR_CUDA && engine != MLSD_SUR_TENSOR)) return MLSD_EINVAL;

@@ -340,6 +340,33 @@ __global__ void __launch_bounds__(1024) k_compact(long long P, const int *flag, 
     if (threadIdx.x == 0) *count = base;
 }
 
+// rows idx[0..M) of (X, Y) into the batch buffers (Xb, Yb)
+__global__ void k_gather_rows(int M, const int *idx, const __nv_bfloat16 *X, const float *Y,
+                              __nv_bfloat16 *Xb, float *Yb)
+{
+    const int r = blockIdx.x;
+    if (r >= M) return;
+    const long long src = idx[r];
+    const uint4 *xs = reinterpret_cast<const uint4 *>(X + src * MLSD_SUR_IN);
+    uint4 *xd = reinterpret_cast<uint4 *>(Xb + (long long)r * MLSD_SUR_IN);
+    for (int c = threadIdx.x; c < MLSD_SUR_IN / 8; c += blockDim.x) xd[c] = xs[c];
+    if (threadIdx.x < 3) Yb[3 * r + threadIdx.x] = Y[3 * src + threadIdx.x];
+}
+
+__global__ void k_add_loss(const double *loss, double *acc)
+{
+    if (threadIdx.x == 0) *acc += *loss;
+}
+
+// training targets (K - B - Q) YS / tr(B) of one plain-solved level
+__global__ void k_targets(long long P, const double *B, const double *K, const double *Q, float *Y)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const double f = MLSD_SUR_Y_SCALE / (B[3 * p] + B[3 * p + 2]);
+    for (int c = 0; c < 3; ++c) Y[3 * p + c] = (float)((K[3 * p + c] - B[3 * p + c] - Q[3 * p + c]) * f);
+}
+
 // flagged patches take the plain solve: K = sym(B e_j + S_.j)
 __global__ void k_merge_fallback(int n, const int *idx, const double *B, const double *S, double *K)
 {
@@ -466,6 +493,30 @@ cudaError_t sur_to_bf16(long long n, const float *w, void *wb, cudaStream_t s)
 {
     count_launches(1);
     k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, w, static_cast<__nv_bfloat16 *>(wb));
+    return cudaGetLastError();
+}
+
+cudaError_t sur_gather(int M, const int *idx, const void *X, const float *Y, void *Xb, float *Yb,
+                       cudaStream_t s)
+{
+    count_launches(1);
+    k_gather_rows<<<(unsigned)M, 128, 0, s>>>(M, idx, static_cast<const __nv_bfloat16 *>(X), Y,
+                                              static_cast<__nv_bfloat16 *>(Xb), Yb);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_add_loss(const double *loss, double *acc, cudaStream_t s)
+{
+    count_launches(1);
+    k_add_loss<<<1, 32, 0, s>>>(loss, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_targets(long long P, const double *B, const double *K, const double *Q, float *Y,
+                        cudaStream_t s)
+{
+    count_launches(1);
+    k_targets<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(P, B, K, Q, Y);
     return cudaGetLastError();
 }
 

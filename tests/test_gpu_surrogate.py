@@ -117,6 +117,39 @@ def test_training_lowers_the_loss(mlsd, torch_mod):
     assert torch_mod.equal(o1, o2)
 
 
+def test_library_training_loop_and_checkpoint(mlsd, torch_mod, tmp_path):
+    # mlsd_surrogate_train (device gather of shuffled rows, Adam, geometric lr
+    # decay) fits a smooth synthetic regression; the checkpoint file restores
+    # the members bit for bit into a new handle
+    h, n = 64, 1024
+    sur = mlsd.Surrogate(members=2, hidden=h, max_batch=256)
+    for m in range(2):
+        sur.set_params(m, inputs.mlp_init(mlsd.SUR_IN, h, 17 + m))
+    rng = np.random.default_rng(21)
+    Xf = np.zeros((n, mlsd.SUR_IN), np.float32)
+    Xf[:, :8] = rng.uniform(-1, 1, (n, 8))
+    Yf = np.stack([np.sin(Xf[:, 0]), Xf[:, 1] * Xf[:, 2], 0.5 * Xf[:, 3] ** 2], 1).astype(np.float32)
+    dev = torch_mod.device("cuda:0")
+    X = torch_mod.tensor(Xf, device=dev).to(torch_mod.bfloat16)
+    Y = torch_mod.tensor(Yf, device=dev)
+    first = sur.train(X, Y, epochs=1, batch=128, lr=2e-3, seed=3)
+    last = sur.train(X, Y, epochs=60, batch=128, lr=2e-3, lr_final=2e-4, seed=4)
+    for m in range(2):
+        assert last[m] < 0.1 * first[m], (first, last)
+    path = tmp_path / "ensemble.bin"
+    sur.save(path)
+    sur2 = mlsd.Surrogate(members=2, hidden=h, max_batch=256)
+    sur2.load(path)
+    for m in range(2):
+        assert np.array_equal(sur.get_params(m), sur2.get_params(m))
+    o1 = torch_mod.zeros(2, n, 3, device=dev); o2 = torch_mod.zeros(2, n, 3, device=dev)
+    sur.predict(X, o1); sur2.predict(X, o2)
+    assert torch_mod.equal(o1, o2)
+    # a file of another shape is refused
+    with pytest.raises(mlsd.MlsdError):
+        mlsd.Surrogate(members=3, hidden=h, max_batch=256).load(path)
+
+
 def test_surrogate_level_fallback_paths(mlsd, torch_mod):
     spec = flows.continuous_spectrum(40, seed=9)
     edges, N, kappa = [1, 4, 16, 41], 4, 2e-3
