@@ -122,6 +122,17 @@ def _oracle_sample(cores):
     return cu / dt, dt, sample, nodes, K
 
 
+def _config(world):
+    """The workload's config object, shared by both arms' JSON lines."""
+    cfg = _workload()
+    N = cfg["n_macro"]
+    return {"workload": WORKLOAD, "n_macro": N, "patch_n": cfg["patch_n"][0],
+            "levels": len(cfg["patch_n"]), "patches_per_level": N * N, "kappa": cfg["kappa"],
+            "window": "8 tau burn-in + 4 tau average", "macro_T": cfg["T"],
+            "l2": "flushed between steps (512 MiB write)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -140,7 +151,7 @@ def reference_arm(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_macro": 128, "patch_n": 64, "levels": 3},
+        "config": _config(args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -578,11 +589,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_macro": N, "patch_n": cfg["patch_n"][0],
-                   "levels": L, "patches_per_level": N * N, "kappa": cfg["kappa"],
-                   "window": "8 tau burn-in + 4 tau average", "macro_T": cfg["T"],
-                   "l2": "flushed between steps (512 MiB write)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": _config(world),
         "k_eff_tensors_per_s": tensors,
         "cell_updates_per_step": cell_updates * world,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,

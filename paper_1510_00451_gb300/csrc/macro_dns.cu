@@ -228,6 +228,9 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
 
     const int g = threadIdx.x % DG, seg = threadIdx.x / DG;
     const int c0 = 4 + 4 * g;                 // staged column of the group's first column
+    // x + dt f(x) = cC x + cA [(psiS - psiN)(xE - xW) + (psiE - psiW)(xN - xS)]
+    //               + cD (xE + xW + xN + xS),   cA = dt / (4 h^2), cD = dt kappa / h^2
+    const float cA = dt * ax * ax, cD = dt * kd, cC = 1.0f - 4.0f * cD;
     const int rbase = 2 + DRS * seg;          // staged row of the segment's first output row
     // ---- stage 1 on rows rbase-1 .. rbase+DRS (registers s[0..DRS+1]) ----
     float s1[DRS + 2][4];
@@ -251,10 +254,10 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
             for (int c = 0; c < 4; ++c) {
                 const float uE = c < 3 ? uc[c + 1] : ue, uW = c > 0 ? uc[c - 1] : uw;
                 const float pE = c < 3 ? pc[c + 1] : pe, pW = c > 0 ? pc[c - 1] : pw;
-                const float v1 = (pm[c] - pp[c]) * ax, v2 = (pE - pW) * ax;
-                const float f = v1 * (uE - uW) * ax + v2 * (up[c] - um[c]) * ax +
-                                kd * (uE + uW + up[c] + um[c] - 4.0f * uc[c]);
-                s1[k][c] = uc[c] + dt * f;
+                float t = (pm[c] - pp[c]) * (uE - uW);
+                t = fmaf(pE - pW, up[c] - um[c], t);
+                const float sg = (uE + uW) + (up[c] + um[c]);
+                s1[k][c] = fmaf(cA, t, fmaf(cD, sg, cC * uc[c]));
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) { um[c] = uc[c]; uc[c] = up[c]; pm[c] = pc[c]; pc[c] = pp[c]; }
@@ -287,15 +290,16 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
             const float4 u4 = *reinterpret_cast<const float4 *>(su + r * DLX + c0);
             const float uo[4] = {u4.x, u4.y, u4.z, u4.w};
             float o[4];
+            // (u + s + dt f(s)) / 2 with the halved coefficients
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float sC = s1[k + 1][c], sN = s1[k + 2][c], sS = s1[k][c];
                 const float sE = c < 3 ? s1[k + 1][c + 1] : se, sW = c > 0 ? s1[k + 1][c - 1] : sw;
                 const float pE = c < 3 ? pc[c + 1] : pe, pW = c > 0 ? pc[c - 1] : pw;
-                const float v1 = (pm[c] - pp[c]) * ax, v2 = (pE - pW) * ax;
-                const float f = v1 * (sE - sW) * ax + v2 * (sN - sS) * ax +
-                                kd * (sE + sW + sN + sS - 4.0f * sC);
-                o[c] = 0.5f * (uo[c] + sC + dt * f);
+                float t = (pm[c] - pp[c]) * (sE - sW);
+                t = fmaf(pE - pW, sN - sS, t);
+                const float sg = (sE + sW) + (sN + sS);
+                o[c] = fmaf(0.5f * cA, t, fmaf(0.5f * cD, sg, fmaf(0.5f * cC, sC, 0.5f * uo[c])));
             }
             *reinterpret_cast<float4 *>(un + (long long)(y0 + DRS * seg + k) * nf + gx) =
                 make_float4(o[0], o[1], o[2], o[3]);
