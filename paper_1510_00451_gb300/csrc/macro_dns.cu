@@ -228,9 +228,11 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
 
     const int g = threadIdx.x % DG, seg = threadIdx.x / DG;
     const int c0 = 4 + 4 * g;                 // staged column of the group's first column
-    // x + dt f(x) = cC x + cA [(psiS - psiN)(xE - xW) + (psiE - psiW)(xN - xS)]
-    //               + cD (xE + xW + xN + xS),   cA = dt / (4 h^2), cD = dt kappa / h^2
-    const float cA = dt * ax * ax, cD = dt * kd, cC = 1.0f - 4.0f * cD;
+    // x + dt f(x) = x + cD (xE + xW + xN + xS - 4 x)
+    //                 + cA [(psiS - psiN)(xE - xW) + (psiE - psiW)(xN - xS)],
+    // cA = dt / (4 h^2), cD = dt kappa / h^2; the Laplacian stays a difference so
+    // that rounding does not bias the sum of u
+    const float cA = dt * ax * ax, cD = dt * kd;
     const int rbase = 2 + DRS * seg;          // staged row of the segment's first output row
     // ---- stage 1 on rows rbase-1 .. rbase+DRS (registers s[0..DRS+1]) ----
     float s1[DRS + 2][4];
@@ -256,8 +258,8 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
                 const float pE = c < 3 ? pc[c + 1] : pe, pW = c > 0 ? pc[c - 1] : pw;
                 float t = (pm[c] - pp[c]) * (uE - uW);
                 t = fmaf(pE - pW, up[c] - um[c], t);
-                const float sg = (uE + uW) + (up[c] + um[c]);
-                s1[k][c] = fmaf(cA, t, fmaf(cD, sg, cC * uc[c]));
+                const float lap = fmaf(-4.0f, uc[c], (uE + uW) + (up[c] + um[c]));
+                s1[k][c] = fmaf(cA, t, fmaf(cD, lap, uc[c]));
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) { um[c] = uc[c]; uc[c] = up[c]; pm[c] = pc[c]; pc[c] = pp[c]; }
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
             const float4 u4 = *reinterpret_cast<const float4 *>(su + r * DLX + c0);
             const float uo[4] = {u4.x, u4.y, u4.z, u4.w};
             float o[4];
-            // (u + s + dt f(s)) / 2 with the halved coefficients
+            // (u + s + dt f(s)) / 2
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float sC = s1[k + 1][c], sN = s1[k + 2][c], sS = s1[k][c];
@@ -298,8 +300,8 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
                 const float pE = c < 3 ? pc[c + 1] : pe, pW = c > 0 ? pc[c - 1] : pw;
                 float t = (pm[c] - pp[c]) * (sE - sW);
                 t = fmaf(pE - pW, sN - sS, t);
-                const float sg = (sE + sW) + (sN + sS);
-                o[c] = fmaf(0.5f * cA, t, fmaf(0.5f * cD, sg, fmaf(0.5f * cC, sC, 0.5f * uo[c])));
+                const float lap = fmaf(-4.0f, sC, (sE + sW) + (sN + sS));
+                o[c] = 0.5f * (uo[c] + fmaf(cA, t, fmaf(cD, lap, sC)));
             }
             *reinterpret_cast<float4 *>(un + (long long)(y0 + DRS * seg + k) * nf + gx) =
                 make_float4(o[0], o[1], o[2], o[3]);
