@@ -43,6 +43,11 @@ OPS_PER_CELL_UPDATE = 21       # FP32-pipe instructions
 OPS_PER_WINDOW_UPDATE = 3
 FLOP_PER_CELL_UPDATE = 34
 FLOP_PER_WINDOW_UPDATE = 5
+# DRAM bytes (read + write) per patch-solve launch of this workload, measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the three level launches of
+# `--case profile`: the same grids, bands and tiling as the timed step (the window
+# length does not change it); 5.15 MB, 1.46 MB and 0.73 MB read, nothing written.
+PATCH_DRAM_BYTES_PER_LAUNCH = (5153792 + 1461504 + 733696) / 3
 WORKLOAD = "three_level_cellular"
 
 
@@ -594,7 +599,9 @@ def main():
         "cell_updates_per_step": cell_updates * world,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
                      "unit": "T FP32-pipe instructions/s",
-                     "frac": (achieved / issue_peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / issue_peak) if achieved else None,
+                     "traffic": PATCH_DRAM_BYTES_PER_LAUNCH,
+                     "traffic_unit": "DRAM bytes per launch (ncu), against 0 algorithmic",
                      "kernel": "k_patch_solve", "launches": kern_n,
                      "kernel_ms_per_step": kern_ms / args.steps,
                      "algorithmic": f"{OPS_PER_CELL_UPDATE} FP32 FADD/FMUL/FFMA per cell-update "
