@@ -48,6 +48,9 @@ FLOP_PER_WINDOW_UPDATE = 5
 # `--case profile`: the same grids, bands and tiling as the timed step (the window
 # length does not change it); 5.15 MB, 1.46 MB and 0.73 MB read, nothing written.
 PATCH_DRAM_BYTES_PER_LAUNCH = (5153792 + 1461504 + 733696) / 3
+# DRAM bytes per k_dns_step launch on the 8192^2 grid, ncu on `--case dns-full`
+# (32-row tiles): 537.2 MB read + 235.7 MB written (algorithmic: 805.3 MB)
+DNS_DRAM_BYTES_PER_LAUNCH = (537197056 + 237457408 + 537173248 + 234027520) / 2
 WORKLOAD = "three_level_cellular"
 
 
@@ -415,8 +418,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--case", default="full",
-                    choices=["full", "profile", "dns-profile", "surrogate", "uneven", "mlp-profile",
-                             "cluster-profile"],
+                    choices=["full", "profile", "dns-profile", "dns-full", "surrogate", "uneven",
+                             "mlp-profile", "cluster-profile"],
                     help="profile: one pass of the same workload with a fixed 200-step window "
                          "per patch (a small case for ncu captures); prints no bench line")
     args = ap.parse_args()
@@ -426,6 +429,8 @@ def main():
         return profile_case()
     if args.case == "dns-profile":
         return dns_case(4096, 20, warmup=2, report=True)
+    if args.case == "dns-full":
+        return dns_case(8192, 10, warmup=2, report=True)
     if args.case == "surrogate":
         print(json.dumps({"case": "surrogate", **surrogate_case()}), flush=True)
         return 0
@@ -555,7 +560,9 @@ def main():
         dns = {"workload": "continuous_spectrum_dns (8192^2 FP32, |k|<=256, kappa=1e-3, 1000 steps)",
                "value": d["cell_steps_per_s"] * world, "unit": "cell-steps/s", "ms": d["ms"],
                "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                            "frac": gbs / hbm, "traffic": None, "kernel": "k_dns_step",
+                            "frac": gbs / hbm, "traffic": DNS_DRAM_BYTES_PER_LAUNCH,
+                            "traffic_unit": "DRAM bytes per launch (ncu, 8192^2)",
+                            "kernel": "k_dns_step",
                             "algorithmic_bytes_per_cell_step": DNS_BYTES_PER_CELL_STEP},
                "mass_rel_drift": d["mass_rel_drift"], "finite": d["finite"]}
 

@@ -200,7 +200,12 @@ int mlsd_offdiag(mlsd_levels *h, int level, const double *B_dev, double *Koff_de
  *   K*_L = K[psi_L; K_off,L(B_L)];
  *   K*_l = K[psi_l; K_off,l(K*_{l+1} - Koff_l + B_l)] for l = L-1 .. 1;
  *   K_macro = K*_1.
- *   mode            MLSD_PLAIN (MLSD_SURROGATE needs a loaded surrogate)
+ *   mode            MLSD_PLAIN, or MLSD_SURROGATE: the levels with an attached
+ *                   surrogate (mlsd_attach_surrogate) take mlsd_solve_level_surrogate's
+ *                   K* (ensemble, plain solves where the members disagree), the
+ *                   others the plain solve; MLSD_EINVAL if no level has one.
+ *                   This mode blocks once per surrogate level and is not captured
+ *                   in a graph.
  *   K_macro_dev     device [P][3]
  *   K_levels_dev    device [L][P][3] receiving K*_l, or NULL
  * The first call (and any call with other output pointers) captures the
@@ -311,6 +316,16 @@ int mlsd_surrogate_predict(mlsd_surrogate *s, const void *X_dev, int64_t M, floa
 int mlsd_solve_level_surrogate(mlsd_levels *h, mlsd_surrogate *s, int level,
                                const double *K_base_dev, double *K_out_dev, double threshold,
                                int64_t *n_fallback_out, void *cuda_stream);
+
+/* Attach a trained surrogate to a level for MLSD_SURROGATE chains, with its
+ * disagreement threshold (as in mlsd_solve_level_surrogate); s = NULL detaches.
+ * The handle keeps the pointer, not the surrogate: the caller keeps it alive
+ * while attached.  Same level limits as mlsd_surrogate_features
+ * (MLSD_EUNSUPPORTED otherwise).                                            */
+int mlsd_attach_surrogate(mlsd_levels *h, int level, mlsd_surrogate *s, double threshold);
+/* Plain fallback solves of a level in the last MLSD_SURROGATE chain (-1 if
+ * none ran since the surrogate was attached).                               */
+int mlsd_surrogate_fallbacks(mlsd_levels *h, int level, int64_t *n_out);
 
 /* Synchronise the handle's stream and return the first error latched on the
  * device since the last call (MLSD_ENONFINITE ...), then clear it.          */

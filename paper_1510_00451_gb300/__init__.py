@@ -32,7 +32,8 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_surrogate_grad", "mlsd_surrogate_train_step", "mlsd_surrogate_predict",
             "mlsd_solve_level_surrogate", "mlsd_surrogate_set_engine", "mlsd_surrogate_status",
             "mlsd_surrogate_dataset", "mlsd_surrogate_train", "mlsd_surrogate_save",
-            "mlsd_surrogate_load", "mlsd_strerror"]
+            "mlsd_surrogate_load", "mlsd_attach_surrogate", "mlsd_surrogate_fallbacks",
+            "mlsd_strerror"]
 SUR_CUDA, SUR_TENSOR = 0, 1
 SUR_IN, SUR_FEATURES = 640, 585
 SUR_PSI_SCALE, SUR_Q_SCALE, SUR_Y_SCALE = 32.0, 10.0, 30.0
@@ -108,6 +109,8 @@ _lib.mlsd_surrogate_dataset.argtypes = [_P, _I, _P, _P, _P, _P]
 _lib.mlsd_surrogate_train.argtypes = [_P, _P, _P, _L, _I, _I, ctypes.c_float, ctypes.c_float,
                                       ctypes.c_uint64, _P, _P]
 _lib.mlsd_surrogate_save.argtypes = [_P, ctypes.c_char_p]
+_lib.mlsd_attach_surrogate.argtypes = [_P, _I, _P, _D]
+_lib.mlsd_surrogate_fallbacks.argtypes = [_P, _I, ctypes.POINTER(_L)]
 _lib.mlsd_surrogate_load.argtypes = [_P, ctypes.c_char_p]
 _lib.mlsd_surrogate_status.argtypes = [_P, _P]
 _lib.mlsd_strerror.argtypes = [_I]
@@ -196,6 +199,19 @@ class Levels:
         """Surrogate inputs of every patch: X bfloat16 [P][640], F32 [P][585] or None."""
         _check(_lib.mlsd_surrogate_features(self.h, int(level), _dptr(B), _dptr(X), _dptr(F32),
                                             _stream(stream)), "mlsd_surrogate_features")
+
+    def attach_surrogate(self, level, sur, threshold):
+        """Use `sur` at `level` in MLSD_SURROGATE chains (None detaches)."""
+        self._sur = getattr(self, "_sur", {})
+        self._sur[int(level)] = sur                 # keep the handle alive while attached
+        _check(_lib.mlsd_attach_surrogate(self.h, int(level), sur.s if sur is not None else None,
+                                          float(threshold)), "mlsd_attach_surrogate")
+
+    def surrogate_fallbacks(self, level):
+        n = _L()
+        _check(_lib.mlsd_surrogate_fallbacks(self.h, int(level), ctypes.byref(n)),
+               "mlsd_surrogate_fallbacks")
+        return n.value
 
     def surrogate_dataset(self, level, B, X, Y, stream=None):
         """Plain solves, features X and targets Y of every patch (mlsd_surrogate_dataset)."""

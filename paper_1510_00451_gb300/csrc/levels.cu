@@ -251,6 +251,17 @@ __global__ void __launch_bounds__(256) k_corrector_energy(int n, double h, const
     }
 }
 
+// flux averages that reproduce a given K* on the base: S = K* - B (both off-diagonal
+// entries carry K*12 - B12), as the chain reads a surrogate level
+__global__ void k_S_from_K(long long P, const double *base, const double *K, double *S)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    S[4 * p] = K[3 * p] - base[3 * p];
+    S[4 * p + 1] = S[4 * p + 2] = K[3 * p + 1] - base[3 * p + 1];
+    S[4 * p + 3] = K[3 * p + 2] - base[3 * p + 2];
+}
+
 __global__ void k_offdiag_apply(long long P, OffdiagLevel off, const double *B, double *Koff)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -319,6 +330,13 @@ cudaError_t launch_level_base(long long P, int finest, const double *base_next,
     k_level_base<<<(unsigned)((P + th - 1) / th), th, 0, s>>>(P, finest, base_next, S_next,
                                                                Kstar_next, Koff_l, B_l, off,
                                                                base_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_S_from_K(long long P, const double *base, const double *K, double *S, cudaStream_t s)
+{
+    count_launches(1);
+    k_S_from_K<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(P, base, K, S);
     return cudaGetLastError();
 }
 

@@ -97,6 +97,7 @@ cudaError_t launch_line_var(const ModeGroups &grp, long long Nl, int n, int r, i
                             double2 *Gscratch, cudaStream_t s);
 // max |v| of a band over every patch's nref x nref reference nodes (v1, v2 on an
 // Nr = nref * m lattice)
+cudaError_t launch_S_from_K(long long P, const double *base, const double *K, double *S, cudaStream_t s);
 cudaError_t launch_corrector_energy(int n, double h, long long P, int precision, const void *w,
                                    const double *B, double *E, double *M, cudaStream_t s);
 cudaError_t launch_patch_vmax(const double *v1, const double *v2, long long Nr, int nref,

@@ -62,6 +62,9 @@ struct DevLevel {
     std::vector<SizeClass> cls; // largest total work first
     cudaEvent_t fork = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;   // profiling: one pair per launch
+    mlsd_surrogate *sur = nullptr;   // attached surrogate (MLSD_SURROGATE chains) or null
+    double sur_thr = 0;
+    long long sur_fallbacks = -1;    // plain solves of the last surrogate-mode chain
 };
 
 }  // namespace
@@ -682,7 +685,8 @@ int mlsd_offdiag(mlsd_levels *h, int level, const double *B_dev, double *Koff_de
 
 namespace {
 // Algorithm 3 over all levels, enqueued on stream s
-int enqueue_chain(mlsd_levels *h, double *K_macro_dev, double *K_levels_dev, cudaStream_t s)
+int enqueue_chain(mlsd_levels *h, double *K_macro_dev, double *K_levels_dev, cudaStream_t s,
+                  bool surrogate = false)
 {
     const int L = h->L;
     ChainTables t;
@@ -701,7 +705,21 @@ int enqueue_chain(mlsd_levels *h, double *K_macro_dev, double *K_levels_dev, cud
         const DevLevel *nx = finest ? nullptr : &h->lev[l + 1];
         CK(launch_level_base(h->P, finest ? 1 : 0, nx ? nx->base : nullptr, nx ? nx->S : nullptr,
                              nx ? nx->Kstar : nullptr, d.Koff, d.B, off_of(d), d.base, s));
-        int rc = run_patches(h, d, d.base, d.S, nullptr, s);
+        int rc;
+        if (surrogate && d.sur) {
+            // the level's K* from the ensemble (plain solves where it disagrees), then
+            // S = K* - base so that the rest of the chain reads it like a plain solve;
+            // the step counts then cover the fallback solves only
+            int64_t nfb = 0;
+            CK(cudaMemsetAsync(d.steps, 0, (size_t)h->P * 16, s));
+            rc = mlsd_solve_level_surrogate(h, d.sur, l + 1, d.base, d.Kstar, d.sur_thr, &nfb, s);
+            if (!rc) {
+                d.sur_fallbacks = nfb;
+                CK(launch_S_from_K(h->P, d.base, d.Kstar, d.S, s));
+            }
+        } else {
+            rc = run_patches(h, d, d.base, d.S, nullptr, s);
+        }
         if (rc) return rc;
     }
     DevLevel &c = h->lev[0];
@@ -721,9 +739,15 @@ extern "C" {
 int mlsd_effective_diffusivity(mlsd_levels *h, int mode, double *K_macro_dev,
                                double *K_levels_dev, void *cuda_stream)
 {
-    if (!h || !K_macro_dev) return MLSD_EINVAL;
-    if (mode != MLSD_PLAIN) return MLSD_EUNSUPPORTED;
+    if (!h || !K_macro_dev || (mode != MLSD_PLAIN && mode != MLSD_SURROGATE)) return MLSD_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (mode == MLSD_SURROGATE) {
+        bool any = false;
+        for (const DevLevel &d : h->lev) any = any || d.sur;
+        if (!any) return MLSD_EINVAL;
+        // the surrogate levels size their fallback launches on the host: no graph
+        return enqueue_chain(h, K_macro_dev, K_levels_dev, s, true);
+    }
     // profiling records events per launch: run the sequence directly then
     if (h->profile || std::getenv("MLSD_NO_GRAPH")) return enqueue_chain(h, K_macro_dev, K_levels_dev, s);
     if (!h->graph || h->graph_out != K_macro_dev || h->graph_levels != K_levels_dev) {
@@ -746,6 +770,25 @@ int mlsd_effective_diffusivity(mlsd_levels *h, int mode, double *K_macro_dev,
     }
     CK(cudaGraphLaunch(h->graph, s));
     count_launches(h->graph_launches);
+    return MLSD_OK;
+}
+
+int mlsd_attach_surrogate(mlsd_levels *h, int level, mlsd_surrogate *s, double threshold)
+{
+    if (!h || level < 1 || level > h->L || !(threshold >= 0)) return MLSD_EINVAL;
+    DevLevel &d = h->lev[level - 1];
+    if (s && (d.cls.size() != 1 || d.cls[0].n > 64 || h->precision != MLSD_FP32))
+        return MLSD_EUNSUPPORTED;
+    d.sur = s;
+    d.sur_thr = threshold;
+    d.sur_fallbacks = -1;
+    return MLSD_OK;
+}
+
+int mlsd_surrogate_fallbacks(mlsd_levels *h, int level, int64_t *n_out)
+{
+    if (!h || level < 1 || level > h->L || !n_out) return MLSD_EINVAL;
+    *n_out = h->lev[level - 1].sur_fallbacks;
     return MLSD_OK;
 }
 

@@ -251,3 +251,47 @@ def test_trained_surrogate_replaces_most_patch_solves(mlsd, torch_mod):
     assert n_fb < P // 2, n_fb                  # most patch solves are replaced
     assert np.median(err) < 2e-3, np.median(err)
     assert err.max() < 0.05
+
+
+def test_chain_in_surrogate_mode(mlsd, torch_mod):
+    # Algorithm 3 with a surrogate attached to the finest level: at threshold 0
+    # every patch falls back and the chain equals the plain chain; at a huge
+    # threshold the finest K* is the ensemble's and the coarser level is solved
+    # on it as on any base
+    spec = flows.cellular_two_scale(1.0, 0.4, 8)
+    N, kappa = 4, 0.05
+    lv = mlsd.Levels(spec, kappa, N, [1, 8, 16], [32, 32], n_burn_fixed=120, n_avg_fixed=80)
+    dev = torch_mod.device("cuda:0")
+    P = N * N
+    K_plain = torch_mod.zeros(P, 3, dtype=torch_mod.float64, device=dev)
+    KL_plain = torch_mod.zeros(2, P, 3, dtype=torch_mod.float64, device=dev)
+    lv.effective_diffusivity(K_plain, KL_plain)
+    sur = mlsd.Surrogate(members=2, hidden=64, max_batch=64)
+    for m in range(2):
+        sur.set_params(m, inputs.mlp_init(mlsd.SUR_IN, 64, 5 + m))
+    with pytest.raises(mlsd.MlsdError):                 # no surrogate attached yet
+        lv.effective_diffusivity(K_plain.clone(), mode=mlsd.MLSD_SURROGATE)
+    lv.attach_surrogate(2, sur, 0.0)
+    K0 = torch_mod.zeros_like(K_plain)
+    lv.effective_diffusivity(K0, mode=mlsd.MLSD_SURROGATE)
+    assert lv.status() == 0 and lv.surrogate_fallbacks(2) == P
+    assert rel_l2(K0.cpu().numpy(), K_plain.cpu().numpy()) < 1e-6
+    lv.attach_surrogate(2, sur, 1e30)
+    K1 = torch_mod.zeros_like(K_plain)
+    KL1 = torch_mod.zeros_like(KL_plain)
+    lv.effective_diffusivity(K1, KL1, mode=mlsd.MLSD_SURROGATE)
+    assert lv.status() == 0 and lv.surrogate_fallbacks(2) == 0
+    # finest level: no off-diagonal parts, so its base is kappa I
+    Bf = torch_mod.tensor(np.tile([kappa, 0.0, kappa], (P, 1)), dtype=torch_mod.float64, device=dev)
+    Ks = torch_mod.zeros_like(Bf)
+    lv.solve_level_surrogate(sur, 2, Bf, Ks, 1e30)
+    assert torch_mod.allclose(KL1[1], Ks, rtol=1e-12, atol=0)
+    # coarse level on that base, solved plainly (the chain's base is K* - B + B,
+    # equal to K* up to FP64 rounding, which can move the FP32 coefficients)
+    Kc = torch_mod.zeros_like(Bf)
+    lv.solve_level(1, Ks, Kc)
+    assert rel_l2(K1.cpu().numpy(), Kc.cpu().numpy()) < 1e-6
+    lv.attach_surrogate(2, None, 0.0)
+    K2 = torch_mod.zeros_like(K_plain)
+    lv.effective_diffusivity(K2)                        # plain chain again (graph replay)
+    assert torch_mod.equal(K2, K_plain)
