@@ -137,3 +137,27 @@ def test_two_scale_cellular_fp64_end_to_end(mlsd, torch_mod):
     mg = mlsd.macro_step(Ug, K, cfg["T"] / ns, ns)
     assert rel_l2(Ug.cpu().numpy(), Ur) < 1e-9
     assert np.max(np.abs(mg - mg[0])) < 1e-13 * mg[0]
+
+
+@pytest.mark.slow
+def test_dns_full_grid_conserves_mass(mlsd, torch_mod):
+    # the 8192^2 grid of the DNS workload (the oracle cannot follow it step by step
+    # at this size): 50 fused steps keep sum(u) to FP32 rounding and stay finite,
+    # and the coarse-grained field stays close to the one of the first step's start
+    cfg = inputs.config_problem("continuous_spectrum")
+    nf, kappa = 8192, cfg["kappa"]
+    dev = torch_mod.device("cuda:0")
+    psi = torch_mod.empty(nf, nf, dtype=torch_mod.float32, device=dev)
+    mlsd.grid_psi(cfg["spectrum"], nf, psi)
+    dt = mlsd.dns_dt(psi, kappa, cfg["cfl"])
+    u = torch_mod.tensor(flows.gaussian_u0(nf, cfg["sigma"]), dtype=torch_mod.float32, device=dev)
+    ut = torch_mod.empty_like(u)
+    N = cfg["n_macro"]
+    U0 = torch_mod.zeros(N, N, dtype=torch_mod.float32, device=dev)
+    m0 = mlsd.coarse_grain(u, N, U0)
+    mlsd.dns_run(u, ut, psi, kappa, dt, 50)
+    U = torch_mod.zeros_like(U0)
+    m = mlsd.coarse_grain(u, N, U)
+    assert bool(torch_mod.isfinite(u).all())
+    assert m == pytest.approx(m0, rel=1e-6)
+    assert rel_l2(U.cpu().numpy(), U0.cpu().numpy()) < 1e-2      # 50 steps of dt ~ 3e-5
