@@ -130,6 +130,23 @@ def _oracle_sample(cores):
     return cu / dt, dt, sample, nodes, K
 
 
+def ranks_max(x, world, device):
+    """Max of a per-rank float over the job (all_reduce MAX; the value itself at
+    world 1).  Replicas share no data: this timing reduction is the only exchange."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ms_max, world):
+    """Whole-job throughput of `world` replicas: all units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def _config(world):
     """The workload's config object, shared by both arms' JSON lines."""
     cfg = _workload()
@@ -517,12 +534,9 @@ def main():
     kern_flop = args.steps * (cell_updates * FLOP_PER_CELL_UPDATE
                               + window_updates * FLOP_PER_WINDOW_UPDATE)
     assert lv.status() == 0
-    t_max = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_step = float(t_max.item())
-    value = world * cell_updates / (ms_step * 1e-3)
-    tensors = world * N * N / (ms_step * 1e-3)
+    ms_step = ranks_max(ms_step, world, dev)
+    value = job_rate(cell_updates, ms_step, world)
+    tensors = job_rate(N * N, ms_step, world)
 
     # ---- end to end through the C ABI with host buffers (pinned)
     e2e = None
@@ -544,11 +558,8 @@ def main():
             U_h.copy_(Ud, non_blocking=True)
         e1.record(stream)
         barrier()
-        ms_e2e = e0.elapsed_time(e1) / args.steps
-        te = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * cell_updates / (float(te.item()) * 1e-3), "unit": UNIT,
+        ms_e2e = ranks_max(e0.elapsed_time(e1) / args.steps, world, dev)
+        e2e = {"value": job_rate(cell_updates, ms_e2e, world), "unit": UNIT,
                "h2d_bytes_per_step": U0_h.numel() * 4,
                "d2h_bytes_per_step": K_h.numel() * 8 + U_h.numel() * 4}
 
