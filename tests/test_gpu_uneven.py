@@ -83,3 +83,40 @@ def test_explicit_size_map_parity():
     assert cu == sum(2 * int(n) ** 2 * 140 for n in nmap[0])
     assert wu == sum(2 * int(n) ** 2 * 60 for n in nmap[0])
     assert ms == 140
+
+
+@pytest.mark.slow
+def test_full_size_continuous_spectrum_sampled_patches():
+    # the continuous-spectrum hierarchy at full size (8 octave levels, 256 x 256 macro
+    # nodes, 32^2 .. 256^2 patches from the size rule), every level solved on seeded
+    # full-tensor bases with the bench's 32-step window; sampled patches of every
+    # level and size class against the oracle's patch solve (w and K)
+    import torch
+    import inputs
+    import paper_1510_00451_gb300 as mlsd
+    from tests._parity import oracle_level
+    cfg = inputs.config_problem("continuous_spectrum")
+    N, L, kappa = cfg["n_macro"], len(cfg["edges"]) - 1, cfg["kappa"]
+    P = N * N
+    lv = mlsd.Levels(cfg["spectrum"], kappa, N, cfg["edges"], [0] * L, cfl=cfg["cfl"],
+                     n_burn_fixed=0, n_avg_fixed=32)
+    rng = np.random.default_rng(1510)
+    dev = torch.device("cuda:0")
+    for level in range(1, L + 1):
+        sizes = lv.patch_sizes(level)
+        B = inputs.random_bases(P, kappa, 2000 + level)
+        Bd = torch.tensor(B, dtype=torch.float64, device=dev)
+        K = torch.zeros_like(Bd)
+        lv.solve_level(level, Bd, K)
+        assert lv.status() == 0
+        K = K.cpu().numpy()
+        assert np.isfinite(K).all()
+        for n in sorted(set(int(v) for v in sizes)):
+            cand = np.flatnonzero(sizes == n)
+            picks = rng.choice(cand, size=min(3, len(cand)), replace=False)
+            pn = [32] * L
+            pn[level - 1] = n
+            ref = oracle_level(cfg["spectrum"], cfg["edges"], pn, level, N, B, list(picks),
+                               cfl=cfg["cfl"], n_burn_fixed=0, n_avg_fixed=32)
+            for p, Kr in zip(picks, ref):
+                assert rel_l2(K[p], Kr) < 1e-4, (level, n, p, K[p], Kr)
