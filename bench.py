@@ -354,8 +354,18 @@ def mlp_case(M=65536, members=4, hidden=256):
     out = torch.empty(members, M, 3, device=dev)
     sur.predict(X, out)
     sur.predict(X, out)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        sur.predict(X, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    flop = 2.0 * M * members * (mlsd.SUR_IN * hidden + 2 * hidden * hidden + hidden * 16)
     ok = sur.status() == 0 and bool(torch.isfinite(out).all().item())
-    print(json.dumps({"case": "mlp-profile", "ok": ok, "rows": M}), flush=True)
+    print(json.dumps({"case": "mlp-profile", "ok": ok, "rows": M, "ms": ms,
+                      "tflops": flop / (ms * 1e-3) / 1e12}), flush=True)
     return 0 if ok else 1
 
 

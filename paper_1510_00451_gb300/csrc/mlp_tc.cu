@@ -85,6 +85,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
     return false;
 }
 
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes, one wait for all
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
     uint32_t r[16];
@@ -257,6 +275,10 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(TcArgs a)
 // layers while one thread issues the MMAs; the epilogue writes activations in the
 // same layout (conflict-free 16-byte stores) for the next layer's A operand.
 constexpr int RING = 3;
+// 8 warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (the lane quarter a warp may
+// access) and columns of half w / 4 of the layer's outputs, so the bias + GELU
+// epilogue between layers runs on twice the warps of the 128 rows
+constexpr int TMA_THREADS = 256;
 constexpr int A_BYTES = TM * KC * 2;           // 16 KB
 constexpr int B_BYTES = HMAX * KC * 2;         // 32 KB
 constexpr int SLOT = A_BYTES + B_BYTES;
@@ -287,7 +309,7 @@ __device__ __forceinline__ void expect_tx(uint32_t mbar, uint32_t bytes)
                  : "memory");
 }
 
-__global__ void __launch_bounds__(128, 1) k_mlp_tma(const __grid_constant__ TmaArgs a)
+__global__ void __launch_bounds__(TMA_THREADS, 1) k_mlp_tma(const __grid_constant__ TmaArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *ring = smem;                          // RING x (A 16 KB | B 32 KB)
@@ -295,6 +317,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tma(const __grid_constant__ TmaA
     __shared__ __align__(8) uint64_t full[RING], empty[RING], accb;
     __shared__ uint32_t tmem_slot;
     __shared__ int failed;
+    __shared__ float sbias[3][HMAX];                    // the hidden layers' biases
 
     const int member = blockIdx.y;
     const long long row0 = (long long)blockIdx.x * TM;
@@ -312,6 +335,10 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tma(const __grid_constant__ TmaA
     auto kc_of = [&](int q) { return q < nk1 ? q : (q - nk1) % nkh; };
     auto nrows = [&](int l) { return l < 3 ? h : 16; };
 
+    for (int i = threadIdx.x; i < 3 * h; i += blockDim.x) {
+        const int l = i / h, c = i % h;
+        sbias[l][c] = wf[(l == 0 ? ob1 : (l == 1 ? ob2 : ob3)) + c];
+    }
     if (threadIdx.x == 0) {
         failed = 0;
         for (int i = 0; i < RING; ++i) {
@@ -331,7 +358,8 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tma(const __grid_constant__ TmaA
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const uint32_t taddr_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const int lq = warp & 3, cgrp = warp >> 2;           // lane quarter, column half
+    const uint32_t taddr_row = tmem + ((uint32_t)(lq * 32) << 16);
 
     auto issue_load = [&](int q) {
         const int l = layer_of(q), kc = kc_of(q), slot = q % RING;
@@ -389,22 +417,25 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tma(const __grid_constant__ TmaA
         if (!got) failed = 1;
         __syncthreads();
         if (failed) { ok = false; break; }
-        const int r = warp * 32 + lane;
+        const int r = lq * 32 + lane;
         if (l < 3) {
-            const float *bias = wf + (l == 0 ? ob1 : (l == 1 ? ob2 : ob3));
-            for (int c0 = 0; c0 < h; c0 += 16) {
-                float v[16];
-                tmem_ld16(taddr_row + (uint32_t)c0, v);
-                __align__(16) __nv_bfloat16 o[16];
+            const float *bias = sbias[l];                // staged at entry: broadcast reads
+            const int cw = h / (TMA_THREADS / 128);          // columns per half (a multiple of 32)
+            for (int c0 = cgrp * cw; c0 < (cgrp + 1) * cw; c0 += 32) {
+                float v[32];
+                tmem_ld32(taddr_row + (uint32_t)c0, v);
+                __align__(16) __nv_bfloat16 o[32];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(gelu_tc(v[i] + bias[c0 + i]));
-                *reinterpret_cast<uint4 *>(Hs + (c0 >> 3) * (TM * 16) + r * 16) = *reinterpret_cast<const uint4 *>(o);
-                *reinterpret_cast<uint4 *>(Hs + ((c0 >> 3) + 1) * (TM * 16) + r * 16) = *reinterpret_cast<const uint4 *>(o + 8);
+                for (int i = 0; i < 32; ++i) o[i] = __float2bfloat16_rn(gelu_tc(v[i] + bias[c0 + i]));
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+                    *reinterpret_cast<uint4 *>(Hs + ((c0 >> 3) + g) * (TM * 16) + r * 16) =
+                        *reinterpret_cast<const uint4 *>(o + 8 * g);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
-        } else {
+        } else if (cgrp == 0) {
             float v[16];
             tmem_ld16(taddr_row, v);
             if (r < rows_valid) {
@@ -503,7 +534,7 @@ cudaError_t launch_mlp_tma(const void *X, long long M, int h, int members, const
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)members);
     count_launches(1);
-    k_mlp_tma<<<grid, 128, smem, s>>>(a);
+    k_mlp_tma<<<grid, TMA_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
