@@ -267,7 +267,8 @@ def surrogate_case(N=256, epochs=200, members=4, hidden=256, batch=2048, lr=3e-3
             "mlp_tensor_core": {"ms": t_mlp * 1e3, "achieved_tflops": mlp_flop / t_mlp / 1e12,
                                 "peak_bf16_tflops": peaks.get("bf16_tflops", 1939.8),
                                 "frac": mlp_flop / t_mlp / 1e12 / peaks.get("bf16_tflops", 1939.8),
-                                "kernel": "k_mlp_tc"},
+                                "bound": "tensor", "unit": "TFLOP/s",
+                                "kernel": "k_mlp_tma (k_mlp_tc where tensor maps are unavailable)"},
             "seconds": {"dataset": t_data, "train": t_train, "plain": t_plain}}
 
 
