@@ -109,7 +109,9 @@ typedef struct {
                                   (cluster > 1: a CTA barrier, and mbarrier arrivals from the two
                                   neighbouring slabs for the halo rows they push); 3 bulk row
                                   copies (cluster > 1: a CTA barrier, and the two halo rows moved
-                                  by cp.async.bulk completing on the receiver's mbarrier) */
+                                  by cp.async.bulk completing on the receiver's mbarrier); 4 the
+                                  row-paired f32x2 kernel (not a synchronisation mode: one
+                                  barrier per stage, two cells per FFMA2) */
     int n_classes;             /* patch sizes in the level; n, Nl, h and the tile fields describe
                                   the class with the most work; all classes run concurrently */
 } mlsd_level_desc;
@@ -127,7 +129,8 @@ typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and 
  * that advances both fields of a patch in f32x2 pairs; c: CTAs per patch field;
  * s: split-phase stage barriers; n: neighbour signalling between the slabs of
  * a cluster instead of a cluster-wide barrier; b: the slab edge rows moved by
- * bulk copies that complete on the receiver's mbarrier).  MLSD_TUNE_LOG set to
+ * bulk copies that complete on the receiver's mbarrier; r: rows r and r + by/2
+ * of a thread's block in f32x2 pairs, one FFMA2/FADD2 per two cells).  MLSD_TUNE_LOG set to
  * anything prints every candidate's trial time to stderr.
  * Patch sizes 32 and 64 run one CTA per field (or per patch, packed); 128 and
  * 256 split each field over a thread-block cluster of 2-16 CTAs that exchange

@@ -211,6 +211,11 @@ __device__ __forceinline__ void arm_tx(uint32_t mbar_local, uint32_t bytes)
                  : "memory");
 }
 
+// Coef as f32x2 pairs (both lanes equal) for the row-paired kernel (SYNC = 4)
+struct CoefP {
+    float2 b11x2, b22x2, bx, bc, T, K, halfK;
+};
+
 template <int N, int C, int BX, int BY, typename real>
 struct Tile {
     using S = Smem<N, C, BX, BY, real>;
@@ -465,6 +470,166 @@ struct Tile {
         asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
     }
 
+    // ---- row-paired kernel (SYNC = 4; one CTA per field, FP32) -------------
+    // Rows r and r + BY/2 of a thread's block share one f32x2 register, so every
+    // stencil operation is one FFMA2 / FADD2 for two cells: the same arithmetic
+    // as stage() (a - b as fma(b, -1, a), which rounds like the subtraction) in
+    // half the FP32 issue slots.  Pair row k holds rows (k, k + HB).
+    static constexpr int HB = BY / 2;
+    __device__ __forceinline__ static float2 psub(float2 a, float2 b)
+    {
+        return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+    }
+
+    template <int J, bool SECOND>
+    __device__ __forceinline__ static void stage_pair(real *sm, int buf, int tx, int ty,
+                                                      const float2 (&x)[HB][BX], float2 (&out)[HB][BX],
+                                                      const float2 (&aE)[HB][BX], const float2 (&aN)[HB][BX],
+                                                      const CoefP &kp)
+    {
+        const int a0 = tx * BX, b0 = ty * BY;
+        real *rowT = sm + buf * S::STAGE;
+        real *rowB = rowT + S::ROW;
+        real *colL = rowB + S::ROW;
+        real *colR = colL + S::COL;
+        {
+            real t[BX], bt[BX];
+#pragma unroll
+            for (int c = 0; c < BX; ++c) { t[c] = x[0][c].x; bt[c] = x[HB - 1][c].y; }
+            st_vec<real, BX>(rowT + ty * N + a0, t);
+            st_vec<real, BX>(rowB + ty * N + a0, bt);
+            real l[BY], r[BY];
+#pragma unroll
+            for (int q = 0; q < HB; ++q) {
+                l[q] = x[q][0].x; l[q + HB] = x[q][0].y;
+                r[q] = x[q][BX - 1].x; r[q + HB] = x[q][BX - 1].y;
+            }
+            st_vec<real, BY>(colL + tx * S::CS + b0, l);
+            st_vec<real, BY>(colR + tx * S::CS + b0, r);
+        }
+        __syncthreads();
+        real hS[BX], hN[BX], hW[BY + 2], hE[BY + 2];
+        load_halos(sm, buf, tx, ty, hS, hN, hW, hE);
+        // E-W differences: dm of pair row -1 = (south halo row, row HB-1), d0 of pair row 0
+        float2 dm[BX], d0[BX], dp[BX];
+#pragma unroll
+        for (int c = 0; c < BX; ++c) {
+            const float2 e = make_float2((c + 1 < BX) ? hS[c + 1] : hE[0],
+                                         (c + 1 < BX) ? x[HB - 1][c + 1].x : hE[HB]);
+            const float2 w = make_float2((c > 0) ? hS[c - 1] : hW[0],
+                                         (c > 0) ? x[HB - 1][c - 1].x : hW[HB]);
+            dm[c] = psub(e, w);
+            const float2 e0 = (c + 1 < BX) ? x[0][c + 1] : make_float2(hE[1], hE[1 + HB]);
+            const float2 w0 = (c > 0) ? x[0][c - 1] : make_float2(hW[1], hW[1 + HB]);
+            d0[c] = psub(e0, w0);
+        }
+#pragma unroll
+        for (int kr = 0; kr < HB; ++kr) {
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                float2 e, w;
+                if (kr + 1 < HB) {
+                    e = (c + 1 < BX) ? x[kr + 1][c + 1] : make_float2(hE[kr + 2], hE[kr + 2 + HB]);
+                    w = (c > 0) ? x[kr + 1][c - 1] : make_float2(hW[kr + 2], hW[kr + 2 + HB]);
+                } else {                                // pair row HB = (row HB, north halo row)
+                    e = make_float2((c + 1 < BX) ? x[0][c + 1].y : hE[HB + 1],
+                                    (c + 1 < BX) ? hN[c + 1] : hE[BY + 1]);
+                    w = make_float2((c > 0) ? x[0][c - 1].y : hW[HB + 1],
+                                    (c > 0) ? hN[c - 1] : hW[BY + 1]);
+                }
+                dp[c] = psub(e, w);
+            }
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                const float2 xc = x[kr][c];
+                const float2 xW = (c > 0) ? x[kr][c - 1] : make_float2(hW[kr + 1], hW[kr + 1 + HB]);
+                const float2 xN = (kr + 1 < HB) ? x[kr + 1][c] : make_float2(x[0][c].y, hN[c]);
+                const float2 xS = (kr > 0) ? x[kr - 1][c] : make_float2(hS[c], x[HB - 1][c].x);
+                float2 d1 = d0[c], d2 = psub(xN, xS);
+                if constexpr (J == 1) d1 = __fadd2_rn(d1, kp.T); else d2 = __fadd2_rn(d2, kp.T);
+                const float2 cr = psub(dp[c], dm[c]);
+                float2 g = __ffma2_rn(aE[kr][c], d1, SECOND ? out[kr][c] : kp.K);
+                g = __ffma2_rn(kp.b11x2, xW, g);
+                g = __ffma2_rn(aN[kr][c], d2, g);
+                g = __ffma2_rn(kp.b22x2, xS, g);
+                g = __ffma2_rn(kp.bx, cr, g);
+                g = __ffma2_rn(kp.bc, xc, g);
+                out[kr][c] = SECOND ? __ffma2_rn(g, make_float2(0.5f, 0.5f), kp.halfK) : g;
+            }
+#pragma unroll
+            for (int c = 0; c < BX; ++c) { dm[c] = d0[c]; d0[c] = dp[c]; }
+        }
+    }
+
+    // the time loop, flux sums and dump of the row-paired kernel
+    template <int J>
+    __device__ __forceinline__ static void pairs(const PatchParams &prm, real *sm, long long p, int tx,
+                                                 int ty, const real (&A1)[BY][BX], const real (&A2)[BY][BX],
+                                                 const Coef<real> &k, real b11, real b22, long long nb,
+                                                 long long na, double &f1, double &f2)
+    {
+        static_assert(C == 1 && sizeof(real) == 4 && BY % 2 == 0, "row pairs: FP32, one CTA per field");
+        float2 aE[HB][BX], aN[HB][BX], w[HB][BX], s[HB][BX];
+#pragma unroll
+        for (int q = 0; q < HB; ++q)
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                aE[q][c] = make_float2(A1[q][c], A1[q + HB][c]);
+                aN[q][c] = make_float2(A2[q][c], A2[q + HB][c]);
+                w[q][c] = make_float2(0.f, 0.f);
+            }
+        CoefP kp;
+        kp.b11x2 = make_float2(k.b11x2, k.b11x2);
+        kp.b22x2 = make_float2(k.b22x2, k.b22x2);
+        kp.bx = make_float2(k.bx, k.bx);
+        kp.bc = make_float2(k.bc, k.bc);
+        kp.T = make_float2(k.twoh, k.twoh);
+        kp.K = make_float2(k.K, k.K);
+        kp.halfK = make_float2(k.halfK, k.halfK);
+        float2 p1 = make_float2(0.f, 0.f), p2 = p1, pw = p1;
+        const double db11 = (double)b11, db22 = (double)b22;
+        int win = 0;
+        const long long ntot = nb + na;
+        for (long long step = 0; step < ntot; ++step) {
+            stage_pair<J, false>(sm, 0, tx, ty, w, s, aE, aN, kp);
+            stage_pair<J, true>(sm, 1, tx, ty, s, w, aE, aN, kp);
+            if (step >= nb) {
+                float2 q1 = make_float2(0.f, 0.f), q2 = q1, qw = q1;
+#pragma unroll
+                for (int q = 0; q < HB; ++q)
+#pragma unroll
+                    for (int c = 0; c < BX; ++c) {
+                        q1 = __ffma2_rn(aE[q][c], w[q][c], q1);
+                        q2 = __ffma2_rn(aN[q][c], w[q][c], q2);
+                        qw = __fadd2_rn(qw, w[q][c]);
+                    }
+                p1 = __fadd2_rn(p1, q1);
+                p2 = __fadd2_rn(p2, q2);
+                pw = __fadd2_rn(pw, qw);
+                if (++win == kFlush) {
+                    const double sw = (double)pw.x + (double)pw.y;
+                    f1 += (double)p1.x + (double)p1.y - db11 * sw;
+                    f2 += (double)p2.x + (double)p2.y - db22 * sw;
+                    p1 = make_float2(0.f, 0.f); p2 = p1; pw = p1; win = 0;
+                }
+            }
+        }
+        const double sw = (double)pw.x + (double)pw.y;
+        f1 += (double)p1.x + (double)p1.y - db11 * sw;
+        f2 += (double)p2.x + (double)p2.y - db22 * sw;
+        if (prm.wdump) {
+            const int a0 = tx * BX, b0 = ty * BY;
+            real *wd = static_cast<real *>(prm.wdump) + (2 * p + (J - 1)) * (long long)N * N;
+#pragma unroll
+            for (int q = 0; q < HB; ++q)
+#pragma unroll
+                for (int c = 0; c < BX; ++c) {
+                    wd[(b0 + q) * N + a0 + c] = w[q][c].x;
+                    wd[(b0 + q + HB) * N + a0 + c] = w[q][c].y;
+                }
+        }
+    }
+
     template <int J, int SYNC>
     __device__ static void run(const PatchParams &prm, real *sm, long long p, int rank)
     {
@@ -578,6 +743,10 @@ struct Tile {
             }
         tile_sync<C>();   // psi tile (and the vmax slots) are dead; the space becomes the exchange buffers
 
+        double f1 = 0.0, f2 = 0.0;
+        if constexpr (SYNC == 4) {
+            pairs<J>(prm, sm, p, tx, ty, A1, A2, k, b11, b22, nb, na, f1, f2);
+        } else {
         // ---- time stepping ------------------------------------------------
         real w[BY][BX], s[BY][BX];
 #pragma unroll
@@ -586,7 +755,6 @@ struct Tile {
             for (int c = 0; c < BX; ++c) w[r][c] = 0;
         // flux sums: sum (A_i + b_ii) w = sum A_i w + b_ii sum w, so sum w is kept too
         real p1 = 0, p2 = 0, pw = 0;
-        double f1 = 0.0, f2 = 0.0;
         int win = 0;
         const long long ntot = nb + na;
         if constexpr (SPLIT) {
@@ -637,6 +805,7 @@ struct Tile {
 #pragma unroll
                 for (int c = 0; c < BX; ++c) wd[(g0 + b0 + r) * N + a0 + c] = w[r][c];
         }
+        }   // SYNC != 4
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             f1 += __shfl_xor_sync(0xffffffffu, f1, o);
@@ -682,11 +851,13 @@ k_patch_solve(PatchParams prm)
 }
 
 // SYNC: 0 = barrier per stage, 1 = split-phase cluster barrier, 2 = neighbour
-// signalling, 3 = bulk copies of the slab edge rows (2 and 3: clusters only)
+// signalling, 3 = bulk copies of the slab edge rows (2 and 3: clusters only),
+// 4 = row-paired f32x2 arithmetic (one CTA per field, FP32)
 template <int N, int BX, int BY, typename real, int MINB = 1, int C = 1, int SYNC = 0>
 void add_variant(std::vector<PatchVariant> &out)
 {
-    static_assert(SYNC < 2 || C > 1, "neighbour signalling / bulk row copies need a cluster");
+    static_assert(SYNC < 2 || SYNC == 4 || C > 1, "neighbour signalling / bulk row copies need a cluster");
+    static_assert(SYNC != 4 || (C == 1 && sizeof(real) == 4), "row pairs: FP32, one CTA per field");
     static_assert(((N / BX) * (N / C / BY)) % 32 == 0, "whole warps only");
     static_assert((N / BX) * (N / C / BY) <= 512, "reduction slots 0..31 (warp pairs), 32, 40, 41");
     static_assert(N % C == 0 && (N / C) % BY == 0 && N % BX == 0, "tiling");
@@ -1053,6 +1224,7 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
         case 32:
             add_variant<32, 4, 8, float>(out);
             add_variant<32, 4, 8, float, 1, 1, 1>(out);
+            add_variant<32, 4, 8, float, 1, 1, 4>(out);
             add_variant<32, 4, 4, float>(out);
             add_variant<32, 2, 8, float>(out);
             add_variant<32, 2, 4, float>(out);
@@ -1064,6 +1236,10 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
             add_variant<64, 4, 8, float>(out);
             add_variant<64, 4, 8, float, 3>(out);
             add_variant<64, 4, 8, float, 3, 1, 1>(out);
+            add_variant<64, 4, 8, float, 3, 1, 4>(out);
+            add_variant<64, 4, 8, float, 2, 1, 4>(out);
+            add_variant<64, 4, 4, float, 1, 1, 4>(out);
+            add_variant<64, 4, 4, float, 2, 1, 4>(out);
             add_variant<64, 4, 4, float, 2, 1, 1>(out);
             add_variant<64, 4, 4, float>(out);
             add_variant<64, 2, 8, float>(out);
@@ -1121,7 +1297,7 @@ cudaError_t launch_patch(const PatchVariant &v, const PatchParams &p, long long 
     if (e != cudaSuccess) return e;
     void *args[] = {const_cast<PatchParams *>(&p)};
     count_launches(1);
-    if (v.cluster > 1 || v.split) {
+    if (v.cluster > 1 || v.split == 1) {        // barrier.cluster needs a cluster launch
         if (v.cluster > 8) {
             e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return e;
