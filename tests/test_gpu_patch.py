@@ -1,6 +1,6 @@
 """GPU parity of the batched patch solves and the level chain against the oracle.
 
-Tolerances (from the benchmark spec): relative L2 <= 1e-5 on the corrector
+Tolerances (those the library states for its results): relative L2 <= 1e-5 on the corrector
 fields w, relative <= 1e-4 on K_eff, for the FP32 stencil with FP64 averages;
 the FP64 path is held to 1e-10.
 """
