@@ -39,7 +39,7 @@ extern "C" {
 #define MLSD_ECUDA        -3   /* a CUDA runtime call failed */
 #define MLSD_ETIMEOUT     -4   /* a bounded device wait ran out */
 #define MLSD_ENONFINITE   -5   /* a NaN or Inf appeared in a result */
-#define MLSD_EUNSUPPORTED -6   /* configuration not supported by this build */
+#define MLSD_EUNSUPPORTED -6   /* configuration without a compiled kernel */
 
 #define MLSD_FP32 0            /* stencil arithmetic and storage in FP32, averages in FP64 */
 #define MLSD_FP64 1            /* everything in FP64 */

@@ -1,5 +1,5 @@
 // Learned surrogate of the patch solve (not part of the paper's method; the
-// plain patch solve stays its fallback and the judge of its error).
+// plain patch solve stays its fallback and the reference for its error).
 //
 // Features (K8): per patch, the 17 x 17 low-mode DFT of the patch's band psi
 // (patch mean removed) times MLSD_SUR_PSI_SCALE / (tr(B)/2), then B/kappa,
