@@ -537,9 +537,15 @@ def main():
     clocks = _clock_summary(clk_path)
     ms_step = sum(a.elapsed_time(b) for a, b in evs) / args.steps
     kern_ms, kern_n = 0.0, 0
+    per_level = []
     for l in range(L):
         ms, n = lv.profile_collect(l + 1)
         kern_ms += ms; kern_n += n
+        cu_l = work[l][0]
+        per_level.append({"level": l + 1, "kernel_ms_per_step": ms / args.steps,
+                          "cell_updates": cu_l, "max_steps_per_patch": work[l][1],
+                          "cell_updates_per_s": cu_l / (ms / args.steps * 1e-3) if ms > 0 else None,
+                          "k_eff_tensors_per_s": N * N / (ms / args.steps * 1e-3) if ms > 0 else None})
     kern_ops = args.steps * (cell_updates * OPS_PER_CELL_UPDATE
                              + window_updates * OPS_PER_WINDOW_UPDATE)
     kern_flop = args.steps * (cell_updates * FLOP_PER_CELL_UPDATE
@@ -626,6 +632,7 @@ def main():
         "config": _config(world),
         "k_eff_tensors_per_s": tensors,
         "cell_updates_per_step": cell_updates * world,
+        "per_level": per_level,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
                      "unit": "T FP32-pipe instructions/s",
                      "frac": (achieved / issue_peak) if achieved else None,

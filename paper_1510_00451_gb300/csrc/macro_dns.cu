@@ -228,6 +228,11 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
 
     const int g = threadIdx.x % DG, seg = threadIdx.x / DG;
     const int c0 = 4 + 4 * g;                 // staged column of the group's first column
+    // the last warp is partial (DTH = 34 DTY/8 threads): shuffles name its lanes only;
+    // its last thread is a g = DG - 1 thread, so no lane reads past it
+    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+    const unsigned wmask = DTH - wbase >= 32 ? 0xffffffffu : ((1u << (DTH - wbase)) - 1u);
+    const bool edgeW = g == 0 || lane == 0, edgeE = g == DG - 1 || lane == 31;
     // x + dt f(x) = x + cD (xE + xW + xN + xS - 4 x)
     //                 + cA [(psiS - psiN)(xE - xW) + (psiE - psiW)(xN - xS)],
     // cA = dt / (4 h^2), cD = dt kappa / h^2; the Laplacian stays a difference so
@@ -250,8 +255,13 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
             const float4 pn4 = *reinterpret_cast<const float4 *>(sp + (r + 1) * DLX + c0);
             up[0] = un4.x; up[1] = un4.y; up[2] = un4.z; up[3] = un4.w;
             pp[0] = pn4.x; pp[1] = pn4.y; pp[2] = pn4.z; pp[3] = pn4.w;
-            const float uw = su[r * DLX + c0 - 1], ue = su[r * DLX + c0 + 4];
-            const float pw = sp[r * DLX + c0 - 1], pe = sp[r * DLX + c0 + 4];
+            // the neighbouring columns come from the neighbouring lanes (the groups of a
+            // segment are consecutive threads); lanes at a warp or segment edge read
+            // shared memory (a scalar column read is a 4-way bank conflict)
+            float uw = __shfl_up_sync(wmask, uc[3], 1), ue = __shfl_down_sync(wmask, uc[0], 1);
+            float pw = __shfl_up_sync(wmask, pc[3], 1), pe = __shfl_down_sync(wmask, pc[0], 1);
+            if (edgeW) { uw = su[r * DLX + c0 - 1]; pw = sp[r * DLX + c0 - 1]; }
+            if (edgeE) { ue = su[r * DLX + c0 + 4]; pe = sp[r * DLX + c0 + 4]; }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float uE = c < 3 ? uc[c + 1] : ue, uW = c > 0 ? uc[c - 1] : uw;
