@@ -295,3 +295,32 @@ def test_chain_in_surrogate_mode(mlsd, torch_mod):
     K2 = torch_mod.zeros_like(K_plain)
     lv.effective_diffusivity(K2)                        # plain chain again (graph replay)
     assert torch_mod.equal(K2, K_plain)
+
+
+def test_dataset_targets_match_oracle(mlsd, torch_mod):
+    # mlsd_surrogate_dataset: Y = (K - B - Q) 30 / tr(B) from the library's own
+    # plain solves and features, against the oracle's patch solves and features
+    from tests._parity import oracle_level
+    spec = flows.continuous_spectrum(40, seed=9)
+    edges, N, kappa, n = [1, 4, 16, 41], 3, 2e-3, 32
+    lv = mlsd.Levels(spec, kappa, N, edges, [n, n, n], n_burn_fixed=60, n_avg_fixed=40)
+    P = N * N
+    B = inputs.random_bases(P, kappa, 12)
+    dev = torch_mod.device("cuda:0")
+    Bd = torch_mod.tensor(B, dtype=torch_mod.float64, device=dev)
+    X = torch_mod.zeros(P, mlsd.SUR_IN, dtype=torch_mod.bfloat16, device=dev)
+    Y = torch_mod.zeros(P, 3, dtype=torch_mod.float32, device=dev)
+    lv.surrogate_dataset(3, Bd, X, Y)
+    assert lv.status() == 0
+    Yg = Y.cpu().numpy()
+    Kr = oracle_level(spec, edges, [n] * 3, 3, N, B, list(range(P)), n_burn_fixed=60, n_avg_fixed=40)
+    lev, kind = oracle.band_of(spec, edges)
+    Nl = oracle.level_lattice(edges, [n] * 3)[2]
+    for p in range(P):
+        ox = oracle.patch_origin(p % N, N, Nl, n); oy = oracle.patch_origin(p // N, N, Nl, n)
+        psi = oracle.patch_psi(spec, Nl, ox, oy, n, use=(lev == 3) & (kind == 0))
+        f = oracle.features(psi, B[p], kappa)
+        tr = B[p, 0] + B[p, 2]
+        want = (Kr[p] - B[p] - oracle.second_order_K(f, B[p])) * 30.0 / tr
+        scale = 30.0 * np.abs(Kr[p]).max() / tr
+        assert np.abs(Yg[p] - want).max() < 1e-4 * scale, (p, Yg[p], want)
