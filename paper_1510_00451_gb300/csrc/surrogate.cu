@@ -158,46 +158,49 @@ __device__ __forceinline__ float gelu_d(float z)
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
-constexpr int GT = 64, GK = 16;
+constexpr int GK = 16;
 
-template <typename TA, typename TB>
+// T x T output tile per CTA of 256 threads, (T/16) x (T/16) outputs per thread at
+// rows ty + 16 q and columns tx + 16 r (conflict-free shared-memory reads)
+template <typename TA, typename TB, int T>
 __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const TA *A, long long sam,
                                               long long sak, const TB *Bm, long long sbk,
                                               long long sbn, float *C, long long scm,
                                               const float *bias, int accumulate,
                                               __nv_bfloat16 *act, long long sactm)
 {
-    __shared__ float As[GK][GT + 4], Bs[GK][GT + 4];
+    constexpr int R = T / 16;
+    __shared__ float As[GK][T + 4], Bs[GK][T + 4];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
-    float acc[4][4] = {};
+    const int i0 = blockIdx.y * T, j0 = blockIdx.x * T;
+    float acc[R][R] = {};
     for (int k0 = 0; k0 < K; k0 += GK) {
-        for (int t = threadIdx.x; t < GT * GK; t += 256) {
+        for (int t = threadIdx.x; t < T * GK; t += 256) {
             const int r = t / GK, k = t % GK;              // A tile: row r, col k
             const int gi = i0 + r, gk = k0 + k;
             As[k][r] = (gi < M && gk < K) ? to_f(A[gi * sam + gk * sak]) : 0.f;
-            const int c = t % GT, kb = t / GT;             // B tile: k row kb, col c
+            const int c = t % T, kb = t / T;               // B tile: k row kb, col c
             const int gj = j0 + c, gkb = k0 + kb;
             Bs[kb][c] = (gj < N && gkb < K) ? to_f(Bm[gkb * sbk + gj * sbn]) : 0.f;
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < GK; ++k) {
-            float a[4], b[4];
+            float a[R], b[R];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { a[q] = As[k][ty * 4 + q]; b[q] = Bs[k][tx * 4 + q]; }
+            for (int q = 0; q < R; ++q) { a[q] = As[k][ty + 16 * q]; b[q] = Bs[k][tx + 16 * q]; }
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < R; ++q)
 #pragma unroll
-                for (int r = 0; r < 4; ++r) acc[q][r] = fmaf(a[q], b[r], acc[q][r]);
+                for (int r = 0; r < R; ++r) acc[q][r] = fmaf(a[q], b[r], acc[q][r]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < R; ++q)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int gi = i0 + ty * 4 + q, gj = j0 + tx * 4 + r;
+        for (int r = 0; r < R; ++r) {
+            const int gi = i0 + ty + 16 * q, gj = j0 + tx + 16 * r;
             if (gi >= M || gj >= N) continue;
             float v = acc[q][r];
             if (bias) v += bias[gj];
@@ -212,10 +215,20 @@ cudaError_t gemm(cudaStream_t s, int M, int N, int K, const TA *A, long long sam
                  const TB *B, long long sbk, long long sbn, float *C, long long scm,
                  const float *bias, int accumulate, __nv_bfloat16 *act, long long sactm)
 {
-    dim3 g((N + GT - 1) / GT, (M + GT - 1) / GT);
     count_launches(1);
-    k_gemm<TA, TB><<<g, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, scm, bias, accumulate,
-                                     act, sactm);
+    // 128-wide tiles only where they still give every SM two CTAs: the training
+    // shapes (2048 x 256 outputs) are too small for that, and fewer, larger tiles
+    // leave SMs idle (measured slower there)
+    const long long big = (long long)((M + 127) / 128) * ((N + 127) / 128);
+    if (big >= 304) {                    // 8 x 8 outputs per thread
+        dim3 g((N + 127) / 128, (M + 127) / 128);
+        k_gemm<TA, TB, 128><<<g, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, scm, bias,
+                                              accumulate, act, sactm);
+    } else {
+        dim3 g((N + 63) / 64, (M + 63) / 64);
+        k_gemm<TA, TB, 64><<<g, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, scm, bias,
+                                             accumulate, act, sactm);
+    }
     return cudaGetLastError();
 }
 
