@@ -183,7 +183,7 @@ def test_surrogate_level_fallback_paths(mlsd, torch_mod):
 
 
 @pytest.mark.parametrize("tma", [True, False])
-@pytest.mark.parametrize("M,h", [(300, 256), (128, 64), (1000, 128), (4099, 256)])
+@pytest.mark.parametrize("M,h", [(300, 256), (128, 64), (1000, 128), (4099, 256), (20000, 256)])
 def test_tensor_core_inference_matches_oracle(mlsd, torch_mod, M, h, tma, monkeypatch):
     # tcgen05 engine (TMA-fed ring, or the thread-staged fallback) against the
     # bfloat16-emulating oracle and the CUDA-core engine
