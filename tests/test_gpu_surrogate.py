@@ -190,7 +190,9 @@ def test_tensor_core_inference_matches_oracle(mlsd, torch_mod, M, h, tma, monkey
     if not tma:
         monkeypatch.setenv("MLSD_NO_TMA", "1")
     members = 2
-    sur = mlsd.Surrogate(members=members, hidden=h, max_batch=512)
+    # the CUDA-core engine runs in chunks of max_batch rows; the largest case is one
+    # chunk big enough for its GEMMs to take the 128-wide tiles
+    sur = mlsd.Surrogate(members=members, hidden=h, max_batch=M if M >= 20000 else 512)
     rng = np.random.default_rng(M + h)
     params = []
     for m in range(members):
