@@ -125,11 +125,14 @@ long long sur_param_count(int h);
 cudaError_t launch_features(const float *band, long long Nl, int n, int n_macro, const int *pidx,
                             long long count, const double *B, double kappa, void *X, float *F32,
                             double *Q, cudaStream_t s);
+// ws: split-k partials of the CUDA-core GEMMs, ws_n floats (sur_split_workspace(h) lets
+// every training shape split fully; nullptr disables splitting)
+long long sur_split_workspace(int h);
 cudaError_t sur_forward(int h, int M, const void *X, const float *wf, const void *wb,
-                        float *Z[4], void *Aact[3], cudaStream_t s);
+                        float *Z[4], void *Aact[3], float *ws, long long ws_n, cudaStream_t s);
 cudaError_t sur_grad(int h, int M, const void *X, const float *Y, const float *wf, const void *wb,
                      float *Z[4], void *Aact[3], float *dA, float *dB, float *g, double *part,
-                     double *loss_dev, cudaStream_t s);
+                     double *loss_dev, float *ws, long long ws_n, cudaStream_t s);
 cudaError_t sur_adam(long long n, float *w, const float *g, float *m, float *v, float lr, int t,
                      void *wb, cudaStream_t s);
 cudaError_t sur_to_bf16(long long n, const float *w, void *wb, cudaStream_t s);

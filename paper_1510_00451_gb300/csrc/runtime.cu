@@ -991,6 +991,8 @@ struct mlsd_surrogate {
     float *Z[4] = {};
     void *A[3] = {};
     float *dA = nullptr, *dB = nullptr;
+    float *ws = nullptr;                  // split-k partials of the training GEMMs
+    long long ws_n = 0;
     double *part = nullptr, *loss = nullptr;
     void **wb_ptrs = nullptr;             // device arrays of the members' parameter pointers
     float **wf_ptrs = nullptr;
@@ -1052,6 +1054,8 @@ int mlsd_surrogate_create(int members, int hidden, int max_batch, mlsd_surrogate
     for (int l = 0; l < 3 && !rc; ++l) rc = sur_alloc(s, &s->A[l], M * H * 2);
     if (!rc) rc = sur_alloc(s, (void **)&s->dA, M * H * 4);
     if (!rc) rc = sur_alloc(s, (void **)&s->dB, M * H * 4);
+    s->ws_n = sur_split_workspace(hidden);
+    if (!rc) rc = sur_alloc(s, (void **)&s->ws, (size_t)s->ws_n * 4);
     if (!rc) rc = sur_alloc(s, (void **)&s->part, ((3 * M + 255) / 256 + 1) * 8);
     if (!rc) rc = sur_alloc(s, (void **)&s->loss, 8);
     if (!rc) rc = sur_alloc(s, (void **)&s->wb_ptrs, members * sizeof(void *));
@@ -1113,7 +1117,7 @@ int mlsd_surrogate_grad(mlsd_surrogate *s, int member, const void *X_dev, const 
         return MLSD_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     CK(sur_grad(s->h, M, X_dev, Y_dev, s->w[member], s->wb[member], s->Z, s->A, s->dA, s->dB,
-                s->g[member], s->part, s->loss, st));
+                s->g[member], s->part, s->loss, s->ws, s->ws_n, st));
     if (grad_dev)
         CK(cudaMemcpyAsync(grad_dev, s->g[member], (size_t)s->np * 4, cudaMemcpyDeviceToDevice, st));
     if (loss_host) {
@@ -1132,7 +1136,7 @@ int mlsd_surrogate_train_step(mlsd_surrogate *s, int member, const void *X_dev,
         return MLSD_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     CK(sur_grad(s->h, M, X_dev, Y_dev, s->w[member], s->wb[member], s->Z, s->A, s->dA, s->dB,
-                s->g[member], s->part, s->loss, st));
+                s->g[member], s->part, s->loss, s->ws, s->ws_n, st));
     s->t[member] += 1;
     CK(sur_adam(s->np, s->w[member], s->g[member], s->m[member], s->v[member], lr, s->t[member],
                 s->wb[member], st));
@@ -1211,7 +1215,7 @@ int mlsd_surrogate_train(mlsd_surrogate *s, const void *X_dev, const float *Y_de
                 e = sur_gather(batch, idx + q * batch, X_dev, Y_dev, Xb, Yb, st);
                 if (e == cudaSuccess)
                     e = sur_grad(s->h, batch, Xb, Yb, s->w[m], s->wb[m], s->Z, s->A, s->dA, s->dB,
-                                 s->g[m], s->part, s->loss, st);
+                                 s->g[m], s->part, s->loss, s->ws, s->ws_n, st);
                 s->t[m] += 1;
                 if (e == cudaSuccess)
                     e = sur_adam(s->np, s->w[m], s->g[m], s->m[m], s->v[m], r, s->t[m], s->wb[m], st);
@@ -1301,7 +1305,8 @@ int mlsd_surrogate_predict(mlsd_surrogate *s, const void *X_dev, int64_t M, floa
         for (int64_t r0 = 0; r0 < M; r0 += s->max_batch) {
             const int mb = (int)std::min<int64_t>(s->max_batch, M - r0);
             float *Z[4] = {s->Z[0], s->Z[1], s->Z[2], out_dev + ((size_t)k * M + r0) * 3};
-            CK(sur_forward(s->h, mb, X + (size_t)r0 * MLSD_SUR_IN * 2, s->w[k], s->wb[k], Z, s->A, st));
+            CK(sur_forward(s->h, mb, X + (size_t)r0 * MLSD_SUR_IN * 2, s->w[k], s->wb[k], Z, s->A,
+                           s->ws, s->ws_n, st));
         }
     return MLSD_OK;
 }

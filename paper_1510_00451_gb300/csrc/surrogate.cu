@@ -158,37 +158,85 @@ __device__ __forceinline__ float gelu_d(float z)
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
-constexpr int GK = 16;
+constexpr int GK = 16;          // k depth of one shared-memory stage
+constexpr int SPLIT_MAX = 16;   // most k splits of one GEMM
 
-// T x T output tile per CTA of 256 threads, (T/16) x (T/16) outputs per thread at
-// rows ty + 16 q and columns tx + 16 r (conflict-free shared-memory reads)
-template <typename TA, typename TB, int T>
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const TA *A, long long sam,
-                                              long long sak, const TB *Bm, long long sbk,
-                                              long long sbn, float *C, long long scm,
-                                              const float *bias, int accumulate,
-                                              __nv_bfloat16 *act, long long sactm)
+// Epilogue of the GEMM and of its split-k reduction, applied to output (i, j) in order:
+// + bias[j]; + the old C(i, j) (accumulate); times gelu'(dgelu(i, j)) (the backward GELU,
+// dgelu shares C's row stride); store C; act(i, j) = gelu(C(i, j)) in bfloat16.
+struct Epi {
+    const float *bias = nullptr;
+    int accumulate = 0;
+    const float *dgelu = nullptr;
+    __nv_bfloat16 *act = nullptr;
+    long long sactm = 0;
+};
+
+__device__ __forceinline__ void epilogue(const Epi &e, float v, int gi, int gj, float *C,
+                                         long long scm)
 {
-    constexpr int R = T / 16;
-    __shared__ float As[GK][T + 4], Bs[GK][T + 4];
+    if (e.bias) v += e.bias[gj];
+    if (e.accumulate) v += C[gi * scm + gj];
+    if (e.dgelu) v *= gelu_d(e.dgelu[gi * scm + gj]);
+    C[gi * scm + gj] = v;
+    if (e.act) e.act[gi * e.sactm + gj] = __float2bfloat16_rn(gelu_f(v));
+}
+
+// C[M x N] = A[M x K] B[K x N] on the CUDA cores with FP32 accumulation, where
+// A(i, k) = A[i sam + k sak] and B(k, j) = B[k sbk + j sbn]. Either operand may have either
+// index contiguous; the tile loads run along the contiguous one, so every warp's global
+// reads are coalesced. One T x T output tile per CTA of 256 threads: thread (tx, ty) owns
+// rows 4 ty + 64 a + (0..3) and columns 4 tx + 64 b + (0..3), read from shared memory as
+// float4. The next k stage is loaded into registers while the current one is multiplied.
+// With gridDim.z > 1 the CTA sums only k in [z kc, (z + 1) kc) and stores its raw partial
+// at C + z scz (row stride scm); k_split_reduce adds the partials and applies the epilogue.
+template <typename TA, typename TB, int T>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kc, const TA *A,
+                                              long long sam, long long sak, const TB *Bm,
+                                              long long sbk, long long sbn, float *C,
+                                              long long scm, long long scz, Epi ep)
+{
+    constexpr int R = T / 16, E = T * GK / 256;
+    __shared__ __align__(16) float As[GK][T + 4];
+    __shared__ __align__(16) float Bs[GK][T + 4];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int i0 = blockIdx.y * T, j0 = blockIdx.x * T;
-    float acc[R][R] = {};
-    for (int k0 = 0; k0 < K; k0 += GK) {
-        for (int t = threadIdx.x; t < T * GK; t += 256) {
-            const int r = t / GK, k = t % GK;              // A tile: row r, col k
+    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
+    const bool a_rows = sam == 1, b_cols = sbn == 1;
+    float ra[E], rb[E];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int t = threadIdx.x + 256 * e;
+            const int r = a_rows ? t % T : t / GK, k = a_rows ? t / T : t % GK;
             const int gi = i0 + r, gk = k0 + k;
-            As[k][r] = (gi < M && gk < K) ? to_f(A[gi * sam + gk * sak]) : 0.f;
-            const int c = t % T, kb = t / T;               // B tile: k row kb, col c
-            const int gj = j0 + c, gkb = k0 + kb;
-            Bs[kb][c] = (gj < N && gkb < K) ? to_f(Bm[gkb * sbk + gj * sbn]) : 0.f;
+            ra[e] = (gi < M && gk < ke) ? to_f(A[gi * sam + gk * sak]) : 0.f;
+            const int c = b_cols ? t % T : t / GK, q = b_cols ? t / T : t % GK;
+            const int gj = j0 + c, gq = k0 + q;
+            rb[e] = (gj < N && gq < ke) ? to_f(Bm[gq * sbk + gj * sbn]) : 0.f;
+        }
+    };
+    float acc[R][R] = {};
+    if (kb < ke) load(kb);
+    for (int k0 = kb; k0 < ke; k0 += GK) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int t = threadIdx.x + 256 * e;
+            As[a_rows ? t / T : t % GK][a_rows ? t % T : t / GK] = ra[e];
+            Bs[b_cols ? t / T : t % GK][b_cols ? t % T : t / GK] = rb[e];
         }
         __syncthreads();
+        if (k0 + GK < ke) load(k0 + GK);
 #pragma unroll
         for (int k = 0; k < GK; ++k) {
             float a[R], b[R];
 #pragma unroll
-            for (int q = 0; q < R; ++q) { a[q] = As[k][ty + 16 * q]; b[q] = Bs[k][tx + 16 * q]; }
+            for (int q = 0; q < R / 4; ++q) {
+                const float4 va = *reinterpret_cast<const float4 *>(&As[k][64 * q + 4 * ty]);
+                const float4 vb = *reinterpret_cast<const float4 *>(&Bs[k][64 * q + 4 * tx]);
+                a[4 * q] = va.x; a[4 * q + 1] = va.y; a[4 * q + 2] = va.z; a[4 * q + 3] = va.w;
+                b[4 * q] = vb.x; b[4 * q + 1] = vb.y; b[4 * q + 2] = vb.z; b[4 * q + 3] = vb.w;
+            }
 #pragma unroll
             for (int q = 0; q < R; ++q)
 #pragma unroll
@@ -196,57 +244,110 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const TA *A, 
         }
         __syncthreads();
     }
+    const bool split = gridDim.z > 1;
+    float *Cz = C + blockIdx.z * scz;
 #pragma unroll
     for (int q = 0; q < R; ++q)
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int gi = i0 + ty + 16 * q, gj = j0 + tx + 16 * r;
+            const int gi = i0 + 64 * (q / 4) + 4 * ty + q % 4;
+            const int gj = j0 + 64 * (r / 4) + 4 * tx + r % 4;
             if (gi >= M || gj >= N) continue;
-            float v = acc[q][r];
-            if (bias) v += bias[gj];
-            if (accumulate) v += C[gi * scm + gj];
-            C[gi * scm + gj] = v;
-            if (act) act[gi * sactm + gj] = __float2bfloat16_rn(gelu_f(v));
+            if (split) Cz[gi * scm + gj] = acc[q][r];
+            else epilogue(ep, acc[q][r], gi, gj, C, scm);
         }
 }
 
+// C = sum over z = 0 .. S-1 of the partials ws[z M N + i N + j], in that order, then the
+// epilogue
+__global__ void k_split_reduce(int M, int N, int S, const float *ws, float *C, long long scm,
+                               Epi ep)
+{
+    const long long n = (long long)M * N;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n;
+         x += (long long)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int z = 0; z < S; ++z) v += ws[z * n + x];
+        epilogue(ep, v, (int)(x / N), (int)(x % N), C, scm);
+    }
+}
+
+int device_sms()
+{
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            return 152;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
+// One GEMM with its tiling: 128-wide tiles where they still give every SM two CTAs, else
+// 64-wide tiles, and where even those leave SMs idle, k split over up to SPLIT_MAX CTAs
+// (each at least 64 deep) whose partials go to ws (ws_n floats; no split without it)
 template <typename TA, typename TB>
 cudaError_t gemm(cudaStream_t s, int M, int N, int K, const TA *A, long long sam, long long sak,
-                 const TB *B, long long sbk, long long sbn, float *C, long long scm,
-                 const float *bias, int accumulate, __nv_bfloat16 *act, long long sactm)
+                 const TB *B, long long sbk, long long sbn, float *C, long long scm, Epi ep,
+                 float *ws, long long ws_n)
 {
-    count_launches(1);
-    // 128-wide tiles only where they still give every SM two CTAs: the training
-    // shapes (2048 x 256 outputs) are too small for that, and fewer, larger tiles
-    // leave SMs idle (measured slower there)
+    const long long target = 2LL * device_sms();
     const long long big = (long long)((M + 127) / 128) * ((N + 127) / 128);
-    if (big >= 304) {                    // 8 x 8 outputs per thread
+    if (big >= target) {
+        count_launches(1);
         dim3 g((N + 127) / 128, (M + 127) / 128);
-        k_gemm<TA, TB, 128><<<g, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, scm, bias,
-                                              accumulate, act, sactm);
-    } else {
-        dim3 g((N + 63) / 64, (M + 63) / 64);
-        k_gemm<TA, TB, 64><<<g, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, scm, bias,
-                                             accumulate, act, sactm);
+        k_gemm<TA, TB, 128><<<g, 256, 0, s>>>(M, N, K, K, A, sam, sak, B, sbk, sbn, C, scm, 0, ep);
+        return cudaGetLastError();
     }
+    const long long tiles = (long long)((M + 63) / 64) * ((N + 63) / 64);
+    long long S = 1;
+    if (ws && tiles < target) {
+        S = std::min<long long>({(long long)SPLIT_MAX, (target + tiles - 1) / tiles, K / 64});
+        while (S > 1 && S * M * N > ws_n) --S;
+        S = std::max(S, 1LL);
+    }
+    const int kc = (int)((((K + S - 1) / S) + GK - 1) / GK * GK);
+    S = std::max(1, (K + kc - 1) / kc);
+    dim3 g((N + 63) / 64, (M + 63) / 64, (unsigned)S);
+    count_launches(S > 1 ? 2 : 1);
+    if (S == 1) {
+        k_gemm<TA, TB, 64><<<g, 256, 0, s>>>(M, N, K, K, A, sam, sak, B, sbk, sbn, C, scm, 0, ep);
+        return cudaGetLastError();
+    }
+    const long long n = (long long)M * N;
+    k_gemm<TA, TB, 64><<<g, 256, 0, s>>>(M, N, K, kc, A, sam, sak, B, sbk, sbn, ws, N, n, Epi{});
+    const long long nb = std::min<long long>((n + 255) / 256, 8LL * device_sms());
+    k_split_reduce<<<(unsigned)nb, 256, 0, s>>>(M, N, (int)S, ws, C, scm, ep);
     return cudaGetLastError();
 }
 
-// dZ = dA * gelu'(Z)   (in place on dA)
-__global__ void k_gelu_bwd(long long n, const float *Z, float *dA)
+// db[j] = sum_i dZ[i][j]: a CTA takes 32 columns; its 32 warps sum interleaved rows with
+// four accumulators each, and the warps' sums are added in warp order
+__global__ void __launch_bounds__(1024) k_colsum(int M, int N, const float *dZ, float *db)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) dA[i] *= gelu_d(Z[i]);
-}
-
-// db[j] = sum_i dZ[i][j]
-__global__ void k_colsum(int M, int N, const float *dZ, float *db)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
-    float s = 0.f;
-    for (int i = 0; i < M; ++i) s += dZ[(long long)i * N + j];
-    db[j] = s;
+    __shared__ float part[32][33];
+    const int c = threadIdx.x % 32, w = threadIdx.x / 32, j = blockIdx.x * 32 + c;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    if (j < N) {
+        int i = w;
+        for (; i + 96 < M; i += 128) {
+            s0 += dZ[(long long)i * N + j];
+            s1 += dZ[(long long)(i + 32) * N + j];
+            s2 += dZ[(long long)(i + 64) * N + j];
+            s3 += dZ[(long long)(i + 96) * N + j];
+        }
+        for (; i < M; i += 32) s0 += dZ[(long long)i * N + j];
+    }
+    part[w][c] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    if (w == 0 && j < N) {
+        float t = 0.f;
+        for (int q = 0; q < 32; ++q) t += part[q][c];
+        db[j] = t;
+    }
 }
 
 // dZ4 = 2 (Z4 - Y) / (3 M), loss partial sums per block
@@ -438,31 +539,34 @@ static Layers layers(int h)
 // Forward of one member on M rows: Z_l (FP32) and bf16 activations A_l.
 // ws: Z1..Z3 [M][h], Z4 [M][3] FP32; A1..A3 [M][h] bf16.
 cudaError_t sur_forward(int h, int M, const void *X, const float *wf, const void *wb_,
-                        float *Z[4], void *Aact[3], cudaStream_t s)
+                        float *Z[4], void *Aact[3], float *ws, long long ws_n, cudaStream_t s)
 {
     const Layers L = layers(h);
     const __nv_bfloat16 *wb = static_cast<const __nv_bfloat16 *>(wb_);
     const __nv_bfloat16 *in = static_cast<const __nv_bfloat16 *>(X);
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
-        __nv_bfloat16 *act = l < 3 ? static_cast<__nv_bfloat16 *>(Aact[l]) : nullptr;
+        Epi ep;
+        ep.bias = wf + L.b[l];
+        ep.act = l < 3 ? static_cast<__nv_bfloat16 *>(Aact[l]) : nullptr;
+        ep.sactm = L.dout[l];
         e = gemm<__nv_bfloat16, __nv_bfloat16>(s, M, L.dout[l], L.din[l], in, L.din[l], 1,
-                                               wb + L.w[l], 1, L.din[l], Z[l], L.dout[l],
-                                               wf + L.b[l], 0, act, L.dout[l]);
-        in = act;
+                                               wb + L.w[l], 1, L.din[l], Z[l], L.dout[l], ep, ws,
+                                               ws_n);
+        in = ep.act;
     }
     return e;
 }
 
-// Loss and gradient of one member (forward included).  ws holds Z[4], A[3] and
-// two [M][h] FP32 gradient buffers; part: >= (3M + 255)/256 doubles; loss_dev: 1 double.
+long long sur_split_workspace(int h) { return (long long)SPLIT_MAX * h * MLSD_SUR_IN; }
+
 cudaError_t sur_grad(int h, int M, const void *X, const float *Y, const float *wf, const void *wb_,
                      float *Z[4], void *Aact[3], float *dA, float *dB_, float *g, double *part,
-                     double *loss_dev, cudaStream_t s)
+                     double *loss_dev, float *ws, long long ws_n, cudaStream_t s)
 {
     const Layers L = layers(h);
     const __nv_bfloat16 *wb = static_cast<const __nv_bfloat16 *>(wb_);
-    cudaError_t e = sur_forward(h, M, X, wf, wb_, Z, Aact, s);
+    cudaError_t e = sur_forward(h, M, X, wf, wb_, Z, Aact, ws, ws_n, s);
     if (e != cudaSuccess) return e;
     const int nb = (3 * M + 255) / 256;
     count_launches(2);
@@ -474,18 +578,17 @@ cudaError_t sur_grad(int h, int M, const void *X, const float *Y, const float *w
                                          : static_cast<const __nv_bfloat16 *>(X);
         // dW_l[j][k] = sum_m dZ[m][j] Ain[m][k]
         e = gemm<float, __nv_bfloat16>(s, L.dout[l], L.din[l], M, dZ, 1, L.dout[l], Ain, L.din[l],
-                                       1, g + L.w[l], L.din[l], nullptr, 0, nullptr, 0);
+                                       1, g + L.w[l], L.din[l], Epi{}, ws, ws_n);
         if (e != cudaSuccess) return e;
         count_launches(1);
-        k_colsum<<<(L.dout[l] + 127) / 128, 128, 0, s>>>(M, L.dout[l], dZ, g + L.b[l]);
+        k_colsum<<<(L.dout[l] + 31) / 32, 1024, 0, s>>>(M, L.dout[l], dZ, g + L.b[l]);
         if (l == 0) break;
-        // dA_{l-1}[m][k] = sum_j dZ[m][j] W_l[j][k];  dZ_{l-1} = dA * gelu'(Z_{l-1})
+        // dZ_{l-1}[m][k] = (sum_j dZ[m][j] W_l[j][k]) gelu'(Z_{l-1}[m][k])
+        Epi ep;
+        ep.dgelu = Z[l - 1];
         e = gemm<float, __nv_bfloat16>(s, M, L.din[l], L.dout[l], dZ, L.dout[l], 1, wb + L.w[l],
-                                       L.din[l], 1, dN, L.din[l], nullptr, 0, nullptr, 0);
+                                       L.din[l], 1, dN, L.din[l], ep, ws, ws_n);
         if (e != cudaSuccess) return e;
-        const long long n = (long long)M * L.din[l];
-        count_launches(1);
-        k_gelu_bwd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, Z[l - 1], dN);
         float *t = dZ; dZ = dN; dN = t;
     }
     return cudaGetLastError();

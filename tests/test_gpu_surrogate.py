@@ -60,10 +60,12 @@ def test_features_match_oracle(mlsd, torch_mod, n):
         assert not np.any(Xg[:, nf:])
 
 
-def test_gradient_matches_bf16_oracle(mlsd, torch_mod):
-    h, M = 64, 96
-    sur = mlsd.Surrogate(members=2, hidden=h, max_batch=128)
-    rng = np.random.default_rng(5)
+@pytest.mark.parametrize("h,M", [(64, 96), (128, 777), (256, 2048)])
+def test_gradient_matches_bf16_oracle(mlsd, torch_mod, h, M):
+    # 96 rows: the short-k GEMMs run unsplit; 777 and 2048 rows (the training batch):
+    # the weight-gradient GEMMs split k over CTAs, 777 with a ragged last split
+    sur = mlsd.Surrogate(members=2, hidden=h, max_batch=M)
+    rng = np.random.default_rng(5 + M)
     dev = torch_mod.device("cuda:0")
     for member in range(2):
         params = inputs.mlp_init(mlsd.SUR_IN, h, 100 + member) * 3.0
