@@ -188,7 +188,7 @@ def reference_arm(args):
 DNS_BYTES_PER_CELL_STEP = 12     # read u, read psi, write u (both RK stages fused)
 
 
-def surrogate_case(N=256, epochs=200, members=4, hidden=256, batch=2048, lr=3e-3,
+def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3,
                    thresholds=(5e-4, 1e-3, 2e-3, 3e-3, 1e-2), seed=1510):
     """Surrogate vs plain on the diagonal band of the continuous-spectrum flow's
     6th octave (32 <= |k1|, |k2| < 64, patch side 2 pi / 32, 32^2 patches,

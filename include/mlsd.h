@@ -280,16 +280,36 @@ int mlsd_surrogate_train_step(mlsd_surrogate *s, int member, const void *X_dev,
  * mlsd_surrogate_features.                                                  */
 int mlsd_surrogate_dataset(mlsd_levels *h, int level, const double *B_dev, void *X_dev,
                            float *Y_dev, void *cuda_stream);
+/* The symmetry group of the square acting on training rows: element g (0..7)
+ * reflects x1 (bit 0: grid index a -> -a mod n), then x2 (bit 1), then swaps
+ * x1 and x2 (bit 2).  The patch problem is equivariant under it: psi maps to
+ * -psi on the mapped grid for a reflection or a swap (a stream function is a
+ * pseudo-scalar), v = (-psi_x2, psi_x1) maps as a vector, the central
+ * differences, the periodic wrap, dt and the windows are unchanged, and every
+ * symmetric tensor (B, Q, K, the target) maps as R T R^T.  So the image of a
+ * plain-solved row is the exact row of the mapped patch.  On a row: DFT entry
+ * (k1, k2) takes sign * entry (k1s, k2s), (q1, q2) = bit 2 ? (k2, k1) : (k1, k2),
+ * k1s = bit 0 ? -q1 : q1, k2s = bit 1 ? -q2 : q2, sign = (-1)^(bits set);
+ * tensors (T11, T12, T22) -> (T11, s T12, T22), s = (-1)^(bit 0 + bit 1), then
+ * T11 <-> T22 if bit 2; log kappa and the padding are unchanged.
+ * mlsd_surrogate_symmetry writes the images under g of n_rows rows (X_out
+ * bfloat16 [n][640], Y_out FP32 [n][3]; either output may be NULL with its
+ * input); the outputs must not overlap the inputs.                         */
+int mlsd_surrogate_symmetry(const void *X_dev, const float *Y_dev, int64_t n_rows, int g,
+                            void *X_out, float *Y_out, void *cuda_stream);
 /* Train every member with Adam on the n_rows rows of (X_dev, Y_dev) for
- * `epochs` passes in batches of `batch` (<= max_batch) rows; n_rows / batch
- * steps per epoch.  Each member draws its own row order per epoch (Fisher-Yates
- * on a SplitMix64 stream seeded from `seed` and the member index; the rows are
- * gathered on the device); the learning rate decays geometrically from lr to
- * lr_final over the run.  losses_host (or NULL) receives each member's mean
- * batch loss over the last epoch.  Blocks at the end of each member.        */
+ * `epochs` passes in batches of `batch` (<= max_batch) rows.  With augment != 0
+ * every row also enters through its 7 other images under the symmetry group
+ * above (8 n_rows rows per epoch, mapped as they are gathered; n_rows <=
+ * 2^28 - 1), else n_rows rows per epoch; rows / batch steps per epoch.  Each
+ * member draws its own row order per epoch (Fisher-Yates on a SplitMix64
+ * stream seeded from `seed` and the member index; the rows are gathered on
+ * the device); the learning rate decays geometrically from lr to lr_final over
+ * the run.  losses_host (or NULL) receives each member's mean batch loss over
+ * the last epoch.  Blocks at the end of each member.                        */
 int mlsd_surrogate_train(mlsd_surrogate *s, const void *X_dev, const float *Y_dev, int64_t n_rows,
                          int epochs, int batch, float lr, float lr_final, uint64_t seed,
-                         double *losses_host, void *cuda_stream);
+                         int augment, double *losses_host, void *cuda_stream);
 /* Checkpoint: every member's FP32 parameters in one file (magic "MLSDSUR1",
  * int64 members, hidden, parameter count, then the arrays).  load requires
  * the same members and width and resets the Adam state; MLSD_EINVAL on any

@@ -33,7 +33,7 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_solve_level_surrogate", "mlsd_surrogate_set_engine", "mlsd_surrogate_status",
             "mlsd_surrogate_dataset", "mlsd_surrogate_train", "mlsd_surrogate_save",
             "mlsd_surrogate_load", "mlsd_attach_surrogate", "mlsd_surrogate_fallbacks",
-            "mlsd_strerror"]
+            "mlsd_surrogate_symmetry", "mlsd_strerror"]
 SUR_CUDA, SUR_TENSOR = 0, 1
 SUR_IN, SUR_FEATURES = 640, 585
 SUR_PSI_SCALE, SUR_Q_SCALE, SUR_Y_SCALE = 32.0, 10.0, 30.0
@@ -107,7 +107,8 @@ _lib.mlsd_solve_level_surrogate.argtypes = [_P, _P, _I, _P, _P, _D, ctypes.POINT
 _lib.mlsd_surrogate_set_engine.argtypes = [_P, _I]
 _lib.mlsd_surrogate_dataset.argtypes = [_P, _I, _P, _P, _P, _P]
 _lib.mlsd_surrogate_train.argtypes = [_P, _P, _P, _L, _I, _I, ctypes.c_float, ctypes.c_float,
-                                      ctypes.c_uint64, _P, _P]
+                                      ctypes.c_uint64, _I, _P, _P]
+_lib.mlsd_surrogate_symmetry.argtypes = [_P, _P, _L, _I, _P, _P, _P]
 _lib.mlsd_surrogate_save.argtypes = [_P, ctypes.c_char_p]
 _lib.mlsd_attach_surrogate.argtypes = [_P, _I, _P, _D]
 _lib.mlsd_surrogate_fallbacks.argtypes = [_P, _I, ctypes.POINTER(_L)]
@@ -326,6 +327,15 @@ def coarse_grain_noalloc(u, n_macro, U_out, want_mass=True, stream=None):
     return m.value if want_mass else None
 
 
+def surrogate_symmetry(X, Y, g, X_out, Y_out, stream=None):
+    """Images under symmetry g (0..7) of the square of feature rows X (bfloat16
+    [n][640]) and targets Y (FP32 [n][3]) into X_out / Y_out (either pair may be
+    None) (mlsd_surrogate_symmetry)."""
+    n = X.shape[0] if X is not None else Y.shape[0]
+    _check(_lib.mlsd_surrogate_symmetry(_dptr(X), _dptr(Y), n, int(g), _dptr(X_out),
+                                        _dptr(Y_out), _stream(stream)), "mlsd_surrogate_symmetry")
+
+
 class Surrogate:
     """Ensemble MLP surrogate handle (mlsd_surrogate_*)."""
 
@@ -374,14 +384,16 @@ class Surrogate:
                                               _stream(stream)), "mlsd_surrogate_train_step")
         return loss.value if want_loss else None
 
-    def train(self, X, Y, epochs, batch, lr, lr_final=None, seed=0, stream=None):
-        """Adam on every member over the rows of (X, Y) (mlsd_surrogate_train);
+    def train(self, X, Y, epochs, batch, lr, lr_final=None, seed=0, augment=False, stream=None):
+        """Adam on every member over the rows of (X, Y) (mlsd_surrogate_train),
+        with augment over each row's 8 images under the square's symmetries;
         returns each member's mean loss over the last epoch."""
         losses = np.zeros(self.members)
         lr_final = lr if lr_final is None else lr_final
         _check(_lib.mlsd_surrogate_train(self.s, _dptr(X), _dptr(Y), X.shape[0], int(epochs),
                                          int(batch), float(lr), float(lr_final), int(seed),
-                                         losses.ctypes.data, _stream(stream)), "mlsd_surrogate_train")
+                                         1 if augment else 0, losses.ctypes.data,
+                                         _stream(stream)), "mlsd_surrogate_train")
         return losses.tolist()
 
     def save(self, path):

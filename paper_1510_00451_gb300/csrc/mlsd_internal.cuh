@@ -136,8 +136,12 @@ cudaError_t sur_grad(int h, int M, const void *X, const float *Y, const float *w
 cudaError_t sur_adam(long long n, float *w, const float *g, float *m, float *v, float lr, int t,
                      void *wb, cudaStream_t s);
 cudaError_t sur_to_bf16(long long n, const float *w, void *wb, cudaStream_t s);
+// rows idx[r] of (X, Y); with aug, idx[r] = 8 row + g takes the row's image under
+// symmetry g of the square (mlsd_surrogate_symmetry)
 cudaError_t sur_gather(int M, const int *idx, const void *X, const float *Y, void *Xb, float *Yb,
-                       cudaStream_t s);
+                       int aug, cudaStream_t s);
+cudaError_t sur_symmetry(long long n, int g, const void *X, const float *Y, void *Xo, float *Yo,
+                         cudaStream_t s);
 cudaError_t sur_add_loss(const double *loss, double *acc, cudaStream_t s);
 cudaError_t sur_targets(long long P, const double *B, const double *K, const double *Q, float *Y,
                         cudaStream_t s);

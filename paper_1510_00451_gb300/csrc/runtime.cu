@@ -1180,23 +1180,36 @@ uint64_t splitmix64(uint64_t &x)
 }
 }  // namespace
 
+int mlsd_surrogate_symmetry(const void *X_dev, const float *Y_dev, int64_t n_rows, int g,
+                            void *X_out, float *Y_out, void *cuda_stream)
+{
+    if (n_rows < 0 || g < 0 || g > 7 || (!X_out && !Y_out) || (X_out && !X_dev) ||
+        (Y_out && !Y_dev))
+        return MLSD_EINVAL;
+    CK(sur_symmetry(n_rows, g, X_dev, Y_dev, X_out, Y_out, static_cast<cudaStream_t>(cuda_stream)));
+    return MLSD_OK;
+}
+
 int mlsd_surrogate_train(mlsd_surrogate *s, const void *X_dev, const float *Y_dev, int64_t n_rows,
                          int epochs, int batch, float lr, float lr_final, uint64_t seed,
-                         double *losses_host, void *cuda_stream)
+                         int augment, double *losses_host, void *cuda_stream)
 {
+    const int64_t mult = augment ? 8 : 1;
     if (!s || !X_dev || !Y_dev || epochs < 1 || batch < 1 || batch > s->max_batch ||
-        n_rows < batch || n_rows > (int64_t)0x7fffffff || !(lr > 0) || !(lr_final > 0))
+        n_rows < 1 || n_rows * mult < batch || n_rows > (int64_t)0x7fffffff / mult ||
+        !(lr > 0) || !(lr_final > 0))
         return MLSD_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    const long long steps = n_rows / batch, total = steps * epochs;
+    const int64_t rows = n_rows * mult;           // rows per epoch, images included
+    const long long steps = rows / batch, total = steps * epochs;
     char *ws = nullptr;
-    const size_t xb = (size_t)batch * MLSD_SUR_IN * 2, yb = (size_t)batch * 3 * 4, ib = (size_t)n_rows * 4;
+    const size_t xb = (size_t)batch * MLSD_SUR_IN * 2, yb = (size_t)batch * 3 * 4, ib = (size_t)rows * 4;
     CK(cudaMallocAsync((void **)&ws, xb + yb + ib + 16, st));
     void *Xb = ws;
     float *Yb = reinterpret_cast<float *>(ws + xb);
     int *idx = reinterpret_cast<int *>(ws + xb + yb);
     double *acc = reinterpret_cast<double *>(ws + xb + yb + ((ib + 7) / 8) * 8);
-    std::vector<int> perm((size_t)n_rows);
+    std::vector<int> perm((size_t)rows);
     cudaError_t e = cudaSuccess;
     for (int m = 0; m < s->members && e == cudaSuccess; ++m) {
         // each member its own shuffles: Fisher-Yates on a SplitMix64 stream
@@ -1204,15 +1217,15 @@ int mlsd_surrogate_train(mlsd_surrogate *s, const void *X_dev, const float *Y_de
         long long t = 0;
         e = cudaMemsetAsync(acc, 0, 8, st);
         for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
-            for (int64_t i = 0; i < n_rows; ++i) perm[(size_t)i] = (int)i;
-            for (int64_t i = n_rows - 1; i > 0; --i) {
+            for (int64_t i = 0; i < rows; ++i) perm[(size_t)i] = (int)i;
+            for (int64_t i = rows - 1; i > 0; --i) {
                 const int64_t j = (int64_t)(splitmix64(rs) % (uint64_t)(i + 1));
                 std::swap(perm[(size_t)i], perm[(size_t)j]);
             }
             e = cudaMemcpyAsync(idx, perm.data(), ib, cudaMemcpyHostToDevice, st);
             for (long long q = 0; q < steps && e == cudaSuccess; ++q, ++t) {
                 const float r = lr * (float)std::pow((double)lr_final / lr, (double)t / (double)std::max(1LL, total - 1));
-                e = sur_gather(batch, idx + q * batch, X_dev, Y_dev, Xb, Yb, st);
+                e = sur_gather(batch, idx + q * batch, X_dev, Y_dev, Xb, Yb, augment ? 1 : 0, st);
                 if (e == cudaSuccess)
                     e = sur_grad(s->h, batch, Xb, Yb, s->w[m], s->wb[m], s->Z, s->A, s->dA, s->dB,
                                  s->g[m], s->part, s->loss, s->ws, s->ws_n, st);

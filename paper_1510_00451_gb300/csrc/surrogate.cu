@@ -455,16 +455,80 @@ __global__ void __launch_bounds__(1024) k_compact(long long P, const int *flag, 
 }
 
 // rows idx[0..M) of (X, Y) into the batch buffers (Xb, Yb)
+// Source column and sign of column c of a feature row's image under symmetry g
+// of the square (bit 0: reflect x1, bit 1: reflect x2, bit 2: then swap x1 and
+// x2).  A reflection or a swap negates psi, so DFT entry (k1, k2) of the image
+// is -1 per set bit times entry (k1s, k2s) of the source; symmetric tensors
+// map as R T R^T.
+__device__ __forceinline__ int sym_source(int c, int g, bool &neg)
+{
+    const bool rx = g & 1, ry = g & 2, sw = g & 4;
+    neg = false;
+    if (c < 2 * NMODE * NMODE) {
+        const int m = c >> 1, k1 = m % NMODE - KMODE, k2 = m / NMODE - KMODE;
+        const int q1 = sw ? k2 : k1, q2 = sw ? k1 : k2;
+        const int k1s = rx ? -q1 : q1, k2s = ry ? -q2 : q2;
+        neg = (rx != ry) != sw;
+        return 2 * ((k2s + KMODE) * NMODE + (k1s + KMODE)) + (c & 1);
+    }
+    // B / kappa at 578..580, log kappa at 581, Q at 582..584, padding after
+    const int base = c >= 582 && c < 585 ? 582 : (c >= 578 && c < 581 ? 578 : -1);
+    if (base < 0) return c;
+    const int i = c - base;
+    if (i == 1) { neg = rx != ry; return c; }
+    return sw ? base + 2 - i : c;
+}
+
+__device__ __forceinline__ float sym_target(const float *y, int i, int g)
+{
+    const bool rx = g & 1, ry = g & 2, sw = g & 4;
+    if (i == 1) return rx != ry ? -y[1] : y[1];
+    return sw ? y[2 - i] : y[i];
+}
+
+// Batch rows r < M: row idx[r] of (X, Y), or with aug its image under symmetry
+// idx[r] & 7 of row idx[r] >> 3.  One CTA per row.
 __global__ void k_gather_rows(int M, const int *idx, const __nv_bfloat16 *X, const float *Y,
-                              __nv_bfloat16 *Xb, float *Yb)
+                              __nv_bfloat16 *Xb, float *Yb, int aug)
 {
     const int r = blockIdx.x;
     if (r >= M) return;
-    const long long src = idx[r];
-    const uint4 *xs = reinterpret_cast<const uint4 *>(X + src * MLSD_SUR_IN);
-    uint4 *xd = reinterpret_cast<uint4 *>(Xb + (long long)r * MLSD_SUR_IN);
-    for (int c = threadIdx.x; c < MLSD_SUR_IN / 8; c += blockDim.x) xd[c] = xs[c];
-    if (threadIdx.x < 3) Yb[3 * r + threadIdx.x] = Y[3 * src + threadIdx.x];
+    const int v = idx[r];
+    const long long src = aug ? v >> 3 : v;
+    const int g = aug ? v & 7 : 0;
+    if (g == 0) {
+        const uint4 *xs = reinterpret_cast<const uint4 *>(X + src * MLSD_SUR_IN);
+        uint4 *xd = reinterpret_cast<uint4 *>(Xb + (long long)r * MLSD_SUR_IN);
+        for (int c = threadIdx.x; c < MLSD_SUR_IN / 8; c += blockDim.x) xd[c] = xs[c];
+        if (threadIdx.x < 3) Yb[3 * r + threadIdx.x] = Y[3 * src + threadIdx.x];
+        return;
+    }
+    const unsigned short *xs = reinterpret_cast<const unsigned short *>(X) + src * MLSD_SUR_IN;
+    unsigned short *xd = reinterpret_cast<unsigned short *>(Xb) + (long long)r * MLSD_SUR_IN;
+    for (int c = threadIdx.x; c < MLSD_SUR_IN; c += blockDim.x) {
+        bool neg;
+        const int sc = sym_source(c, g, neg);
+        xd[c] = xs[sc] ^ (neg ? 0x8000u : 0u);          // bfloat16 negation: the sign bit
+    }
+    if (threadIdx.x < 3) Yb[3 * r + threadIdx.x] = sym_target(Y + 3 * src, threadIdx.x, g);
+}
+
+// image under symmetry g of rows r < n (either part skipped when its output is null)
+__global__ void k_symmetry(long long n, int g, const __nv_bfloat16 *X, const float *Y,
+                           __nv_bfloat16 *Xo, float *Yo)
+{
+    for (long long r = blockIdx.x; r < n; r += gridDim.x) {
+        if (Xo) {
+            const unsigned short *xs = reinterpret_cast<const unsigned short *>(X) + r * MLSD_SUR_IN;
+            unsigned short *xd = reinterpret_cast<unsigned short *>(Xo) + r * MLSD_SUR_IN;
+            for (int c = threadIdx.x; c < MLSD_SUR_IN; c += blockDim.x) {
+                bool neg;
+                const int sc = sym_source(c, g, neg);
+                xd[c] = xs[sc] ^ (neg ? 0x8000u : 0u);
+            }
+        }
+        if (Yo && threadIdx.x < 3) Yo[3 * r + threadIdx.x] = sym_target(Y + 3 * r, threadIdx.x, g);
+    }
 }
 
 __global__ void k_add_loss(const double *loss, double *acc)
@@ -613,11 +677,22 @@ cudaError_t sur_to_bf16(long long n, const float *w, void *wb, cudaStream_t s)
 }
 
 cudaError_t sur_gather(int M, const int *idx, const void *X, const float *Y, void *Xb, float *Yb,
-                       cudaStream_t s)
+                       int aug, cudaStream_t s)
 {
     count_launches(1);
     k_gather_rows<<<(unsigned)M, 128, 0, s>>>(M, idx, static_cast<const __nv_bfloat16 *>(X), Y,
-                                              static_cast<__nv_bfloat16 *>(Xb), Yb);
+                                              static_cast<__nv_bfloat16 *>(Xb), Yb, aug);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_symmetry(long long n, int g, const void *X, const float *Y, void *Xo, float *Yo,
+                         cudaStream_t s)
+{
+    if (n < 1) return cudaSuccess;
+    count_launches(1);
+    const unsigned nb = (unsigned)std::min<long long>(n, 65535LL * 16);
+    k_symmetry<<<nb, 128, 0, s>>>(n, g, static_cast<const __nv_bfloat16 *>(X), Y,
+                                  static_cast<__nv_bfloat16 *>(Xo), Yo);
     return cudaGetLastError();
 }
 

@@ -29,11 +29,12 @@ def make_dataset(lv, level, bases):
     return X, Y
 
 
-def train(sur, X, Y, epochs, batch, lr, seed=0, lr_final=None):
-    """Adam on mean-squared error, each member on its own shuffles of the data;
-    the learning rate decays geometrically to lr_final over the run.  Returns
-    the last epoch's mean loss per member (mlsd_surrogate_train)."""
-    return sur.train(X, Y, epochs, batch, lr, lr_final=lr_final, seed=seed)
+def train(sur, X, Y, epochs, batch, lr, seed=0, lr_final=None, augment=False):
+    """Adam on mean-squared error, each member on its own shuffles of the data
+    (with augment, of every row's 8 images under the square's symmetries); the
+    learning rate decays geometrically to lr_final over the run.  Returns the
+    last epoch's mean loss per member (mlsd_surrogate_train)."""
+    return sur.train(X, Y, epochs, batch, lr, lr_final=lr_final, seed=seed, augment=augment)
 
 
 def k_error(K, Kref):

@@ -53,3 +53,32 @@ def random_spd(P, rng, lo=0.02, hi=0.08):
     a = rng.uniform(lo, hi, (P, 2))
     c = rng.uniform(-0.4, 0.4, P) * np.sqrt(a[:, 0] * a[:, 1])
     return np.stack([a[:, 0], c, a[:, 1]], 1)
+
+
+def square_symmetry_psi(psi, g):
+    """Patch samples psi[b][a] (b along x2, a along x1) under element g of the
+    square's symmetry group: bit 0 reflects x1 (a -> -a mod n), bit 1 reflects
+    x2, bit 2 then swaps x1 and x2.  Each reflection or swap negates psi, as a
+    stream function is a pseudo-scalar, so that v maps as a vector."""
+    out = np.asarray(psi, dtype=np.float64)
+    if g & 1:
+        out = -np.roll(out[:, ::-1], 1, axis=1)
+    if g & 2:
+        out = -np.roll(out[::-1, :], 1, axis=0)
+    if g & 4:
+        out = -out.T
+    return np.ascontiguousarray(out)
+
+
+def square_symmetry_tensor(T, g):
+    """Symmetric tensor (T11, T12, T22) under the same element: R T R^T with R
+    the product of the element's reflections and swap."""
+    R = np.eye(2)
+    if g & 1:
+        R = np.diag([-1.0, 1.0]) @ R
+    if g & 2:
+        R = np.diag([1.0, -1.0]) @ R
+    if g & 4:
+        R = np.array([[0.0, 1.0], [1.0, 0.0]]) @ R
+    M = R @ np.array([[T[0], T[1]], [T[1], T[2]]], dtype=np.float64) @ R.T
+    return np.array([M[0, 0], M[0, 1], M[1, 1]])

@@ -328,3 +328,72 @@ def test_dataset_targets_match_oracle(mlsd, torch_mod):
         want = (Kr[p] - B[p] - oracle.second_order_K(f, B[p])) * 30.0 / tr
         scale = 30.0 * np.abs(Kr[p]).max() / tr
         assert np.abs(Yg[p] - want).max() < 1e-4 * scale, (p, Yg[p], want)
+
+
+@pytest.mark.parametrize("g", range(8))
+def test_symmetry_images_match_the_oracle(mlsd, torch_mod, g):
+    # mlsd_surrogate_symmetry on the library's own dataset rows: the image under
+    # element g of the square's group against the oracle's features and target
+    # of the mapped patch (psi mapped on the grid, base R B R^T, its own solve)
+    from tests._parity import level_geometry, square_symmetry_psi, square_symmetry_tensor
+    spec = flows.continuous_spectrum(40, seed=9)
+    edges, N, kappa, n, nb, na = [1, 4, 16, 41], 3, 2e-3, 32, 60, 40
+    lv = mlsd.Levels(spec, kappa, N, edges, [n, n, n], n_burn_fixed=nb, n_avg_fixed=na)
+    P = N * N
+    B = inputs.random_bases(P, kappa, 12)
+    dev = torch_mod.device("cuda:0")
+    Bd = torch_mod.tensor(B, dtype=torch_mod.float64, device=dev)
+    X = torch_mod.zeros(P, mlsd.SUR_IN, dtype=torch_mod.bfloat16, device=dev)
+    Y = torch_mod.zeros(P, 3, dtype=torch_mod.float32, device=dev)
+    lv.surrogate_dataset(3, Bd, X, Y)
+    Xg = torch_mod.full_like(X, float("nan"))
+    Yg = torch_mod.full_like(Y, float("nan"))
+    mlsd.surrogate_symmetry(X, Y, g, Xg, Yg)
+    torch_mod.cuda.synchronize()
+    assert lv.status() == 0
+    Xn = Xg.float().cpu().numpy()
+    Yn = Yg.cpu().numpy()
+    lev, kind = oracle.band_of(spec, edges)
+    _, Nl, h, _ = level_geometry(edges, [n] * 3, 3)
+    for p in range(P):
+        ox = oracle.patch_origin(p % N, N, Nl, n); oy = oracle.patch_origin(p // N, N, Nl, n)
+        psi = square_symmetry_psi(oracle.patch_psi(spec, Nl, ox, oy, n, use=(lev == 3) & (kind == 0)), g)
+        Bg = square_symmetry_tensor(B[p], g)
+        f = oracle.features(psi, Bg, kappa)
+        # bfloat16 rows: the FP32 features (1e-5 of each group's scale) rounded to 8 bits
+        for lo, hi, tol in ((0, 578, 2e-5), (578, 582, 1e-6), (582, 585, 2e-5)):
+            d = np.abs(Xn[p, lo:hi] - f[lo:hi])
+            assert np.all(d <= 2.0 ** -8 * np.abs(f[lo:hi]) + tol * np.abs(f[lo:hi]).max()), (g, p, lo)
+        assert not np.any(Xn[p, 585:])
+        v1, v2 = oracle.velocity(psi, h)
+        dt = oracle.micro_dt(h, float(np.max(np.abs(v1) + np.abs(v2))), Bg, 0.2)
+        Kg = oracle.patch_k(psi, h, Bg, dt, nb, na)
+        tr = Bg[0] + Bg[2]
+        want = (Kg - Bg - oracle.second_order_K(f, Bg)) * 30.0 / tr
+        assert np.abs(Yn[p] - want).max() < 1e-4 * 30.0 * np.abs(Kg).max() / tr, (g, p, Yn[p], want)
+
+
+def test_augmented_training_is_deterministic_and_learns(mlsd, torch_mod):
+    # mlsd_surrogate_train with augment: every row enters with its 8 images; on
+    # an equivariant regression (the matrix square of B / kappa, a tensor) the
+    # loss drops, and one seed gives the same parameters twice
+    h, n = 64, 512
+    rng = np.random.default_rng(8)
+    Xf = np.zeros((n, mlsd.SUR_IN), np.float32)
+    a = rng.uniform(0.5, 2.0, (n, 2))
+    c = rng.uniform(-0.5, 0.5, n) * np.sqrt(a[:, 0] * a[:, 1])
+    Xf[:, 578], Xf[:, 579], Xf[:, 580] = a[:, 0], c, a[:, 1]
+    Xf[:, 581] = math.log(1e-3)
+    Yf = 0.2 * np.stack([a[:, 0] ** 2 + c ** 2, c * (a[:, 0] + a[:, 1]), a[:, 1] ** 2 + c ** 2], 1)
+    dev = torch_mod.device("cuda:0")
+    X = torch_mod.tensor(Xf, device=dev).to(torch_mod.bfloat16)
+    Y = torch_mod.tensor(Yf.astype(np.float32), device=dev)
+    runs = []
+    for _ in range(2):
+        sur = mlsd.Surrogate(members=1, hidden=h, max_batch=256)
+        sur.set_params(0, inputs.mlp_init(mlsd.SUR_IN, h, 5))
+        first = sur.train(X, Y, epochs=1, batch=256, lr=2e-3, seed=7, augment=True)
+        last = sur.train(X, Y, epochs=40, batch=256, lr=2e-3, lr_final=2e-4, seed=8, augment=True)
+        assert last[0] < 0.3 * first[0], (first, last)
+        runs.append(sur.get_params(0))
+    assert np.array_equal(runs[0], runs[1])

@@ -162,3 +162,71 @@ def test_bf16_emulation_rounds_like_bfloat16():
     bf = lambda v: float(torch.tensor(v, dtype=torch.float32).to(torch.bfloat16).double())
     want = [bf(gl(bf(gl(bf(gl(xr[m, 0])))))) for m in range(2)]
     np.testing.assert_allclose(oracle.mlp(X, p1, h, bf16=True)[:, 0], want, rtol=1e-15)
+
+
+def _smooth_psi(n, rng, modes=6):
+    a, b = np.meshgrid(np.arange(n), np.arange(n))
+    psi = np.zeros((n, n))
+    for _ in range(modes):
+        k1, k2 = rng.integers(-3, 4, 2)
+        ph = rng.uniform(0, 2 * math.pi)
+        psi += rng.normal() * np.cos(2 * math.pi * (k1 * a + k2 * b) / n + ph)
+    return psi - psi.mean()
+
+
+@pytest.mark.parametrize("g", range(1, 8))
+def test_patch_problem_is_equivariant_under_the_square_group(g):
+    # the discrete corrector problem (central differences, periodic wrap, Heun,
+    # window average) maps onto itself: the patch psi' = -psi o R^-1 (det R = -1)
+    # or psi o R^-1 with base R B R^T has K' = R K R^T, to rounding
+    from tests._parity import square_symmetry_psi, square_symmetry_tensor
+    rng = np.random.default_rng(g)
+    n = 16
+    h = 2 * math.pi / n
+    psi = 0.3 * _smooth_psi(n, rng)
+    B = np.array([0.05, 0.012, 0.03])
+    v1, v2 = oracle.velocity(psi, h)
+    dt = oracle.micro_dt(h, float(np.max(np.abs(v1) + np.abs(v2))), B, 0.2)
+    K = oracle.patch_k(psi, h, B, dt, 150, 100)
+    psi_g = square_symmetry_psi(psi, g)
+    B_g = square_symmetry_tensor(B, g)
+    w1, w2 = oracle.velocity(psi_g, h)
+    assert np.max(np.abs(w1) + np.abs(w2)) == pytest.approx(np.max(np.abs(v1) + np.abs(v2)), rel=1e-14)
+    K_g = oracle.patch_k(psi_g, h, B_g, dt, 150, 100)
+    want = square_symmetry_tensor(K, g)
+    np.testing.assert_allclose(K_g, want, rtol=0, atol=1e-12 * np.abs(K).max())
+    assert np.abs(psi_g - psi).max() > 0.1 * np.abs(psi).max()   # a different patch
+
+
+def _feature_rule(f, g):
+    # the signed permutation of a feature row that mlsd.h states for element g
+    from tests._parity import square_symmetry_tensor
+    out = np.array(f, dtype=np.float64)
+    sign = -1.0 if bin(g).count("1") % 2 else 1.0
+    for k2 in range(-8, 9):
+        for k1 in range(-8, 9):
+            q1, q2 = (k2, k1) if g & 4 else (k1, k2)
+            s1 = -q1 if g & 1 else q1
+            s2 = -q2 if g & 2 else q2
+            d = 2 * ((k2 + 8) * 17 + k1 + 8)
+            s = 2 * ((s2 + 8) * 17 + s1 + 8)
+            out[d:d + 2] = sign * np.asarray(f)[s:s + 2]
+    out[578:581] = square_symmetry_tensor(f[578:581], g)
+    out[582:585] = square_symmetry_tensor(f[582:585], g)
+    return out
+
+
+@pytest.mark.parametrize("g", range(1, 8))
+def test_features_of_the_mapped_patch_follow_the_stated_rule(g):
+    # features of the mapped patch (DFT, base, second-order estimate) are the
+    # signed permutation of the patch's own features
+    from tests._parity import square_symmetry_psi, square_symmetry_tensor
+    n, kappa = 32, 2e-3
+    spec = flows.continuous_spectrum(40, seed=9)
+    psi = oracle.patch_psi(spec, 96, 5, 17, n)
+    B = np.array([3.0, 0.7, 2.0]) * kappa
+    f = oracle.features(psi, B, kappa)
+    f_g = oracle.features(square_symmetry_psi(psi, g), square_symmetry_tensor(B, g), kappa)
+    scale = np.abs(f[:578]).max()
+    np.testing.assert_allclose(f_g[:578], _feature_rule(f, g)[:578], rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(f_g[578:], _feature_rule(f, g)[578:], rtol=1e-12, atol=1e-15)
