@@ -370,6 +370,39 @@ def mlp_case(M=65536, members=4, hidden=256):
     return 0 if ok else 1
 
 
+def train_case(rows=16384, epochs=2, members=4, hidden=256, batch=2048):
+    """Surrogate training steps on random rows of the training shape (ncu case):
+    `epochs` passes of rows / batch Adam steps per member, timed with CUDA events
+    after one untimed epoch."""
+    import torch
+    import inputs
+    import paper_1510_00451_gb300 as mlsd
+    dev = torch.device("cuda", _local_rank())
+    sur = mlsd.Surrogate(members=members, hidden=hidden, max_batch=batch)
+    for m in range(members):
+        sur.set_params(m, inputs.mlp_init(mlsd.SUR_IN, hidden, m))
+    g = torch.Generator(device=dev); g.manual_seed(0)
+    X = (0.5 * torch.randn(rows, mlsd.SUR_IN, device=dev, generator=g)).to(torch.bfloat16)
+    Y = 0.1 * torch.randn(rows, 3, device=dev, generator=g)
+    sur.train(X, Y, 1, batch, 3e-3)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    losses = sur.train(X, Y, epochs, batch, 3e-3, lr_final=1e-3, seed=1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    steps = members * epochs * (rows // batch)
+    ms = e0.elapsed_time(e1) / steps
+    # forward and weight gradients of the 4 layers, data gradients of layers 2..4
+    per_row = 2 * (mlsd.SUR_IN * hidden + 2 * hidden * hidden + hidden * 3)
+    flop = batch * (2 * per_row + 2 * (2 * hidden * hidden + hidden * 3))
+    ok = sur.status() == 0 and all(math.isfinite(x) for x in losses)
+    print(json.dumps({"case": "train-profile", "ok": ok, "steps": steps, "ms_per_step": ms,
+                      "gflop_per_step": flop / 1e9, "tflops": flop / (ms * 1e-3) / 1e12}),
+          flush=True)
+    return 0 if ok else 1
+
+
 def dns_case(nf, steps, warmup=20, report=False):
     """Direct simulation of the continuous-spectrum flow (|k| <= 256, kappa = 1e-3)
     on an nf x nf FP32 grid: `steps` fused RK2 steps timed with CUDA events."""
@@ -447,7 +480,7 @@ def main():
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--case", default="full",
                     choices=["full", "profile", "dns-profile", "dns-full", "surrogate", "uneven",
-                             "mlp-profile", "cluster-profile"],
+                             "mlp-profile", "cluster-profile", "train-profile"],
                     help="profile: one pass of the same workload with a fixed 200-step window "
                          "per patch (a small case for ncu captures); prints no bench line")
     args = ap.parse_args()
@@ -466,6 +499,8 @@ def main():
         return mlp_case()
     if args.case == "cluster-profile":
         return cluster_case()
+    if args.case == "train-profile":
+        return train_case()
     if args.case == "uneven":
         print(json.dumps({"case": "uneven", **uneven_case()}), flush=True)
         return 0
