@@ -190,11 +190,13 @@ __device__ __forceinline__ void epilogue(const Epi &e, float v, int gi, int gj, 
 // float4. The next k stage is loaded into registers while the current one is multiplied.
 // With gridDim.z > 1 the CTA sums only k in [z kc, (z + 1) kc) and stores its raw partial
 // at C + z scz (row stride scm); k_split_reduce adds the partials and applies the epilogue.
-template <typename TA, typename TB, int T>
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kc, const TA *A,
+// With rs, the CTAs of the first column tile also sum A's rows over their k range into
+// rs[z M + i] (the bias gradient, when A is the transposed output gradient).
+template <typename TA, typename TB, int T, bool RS = false>
+__global__ void __launch_bounds__(256, RS ? 3 : 0) k_gemm(int M, int N, int K, int kc, const TA *A,
                                               long long sam, long long sak, const TB *Bm,
                                               long long sbk, long long sbn, float *C,
-                                              long long scm, long long scz, Epi ep)
+                                              long long scm, long long scz, Epi ep, float *rs)
 {
     constexpr int R = T / 16, E = T * GK / 256;
     __shared__ __align__(16) float As[GK][T + 4];
@@ -217,6 +219,9 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kc, const
         }
     };
     float acc[R][R] = {};
+    __shared__ float rsum[T];
+    const bool rows_sum = RS && blockIdx.x == 0;
+    if (rows_sum && threadIdx.x < T) rsum[threadIdx.x] = 0.f;
     if (kb < ke) load(kb);
     for (int k0 = kb; k0 < ke; k0 += GK) {
 #pragma unroll
@@ -226,6 +231,12 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kc, const
             Bs[b_cols ? t / T : t % GK][b_cols ? t % T : t / GK] = rb[e];
         }
         __syncthreads();
+        if (rows_sum && threadIdx.x < T) {
+            float t = 0.f;
+#pragma unroll
+            for (int k = 0; k < GK; ++k) t += As[k][threadIdx.x];
+            rsum[threadIdx.x] += t;
+        }
         if (k0 + GK < ke) load(k0 + GK);
 #pragma unroll
         for (int k = 0; k < GK; ++k) {
@@ -245,6 +256,8 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kc, const
         __syncthreads();
     }
     const bool split = gridDim.z > 1;
+    if (rows_sum && threadIdx.x < T && i0 + (int)threadIdx.x < M)
+        rs[blockIdx.z * M + i0 + threadIdx.x] = rsum[threadIdx.x];
     float *Cz = C + blockIdx.z * scz;
 #pragma unroll
     for (int q = 0; q < R; ++q)
@@ -259,16 +272,21 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kc, const
 }
 
 // C = sum over z = 0 .. S-1 of the partials ws[z M N + i N + j], in that order, then the
-// epilogue
+// epilogue; with rs, also rs[i] = sum over z of the row-sum partials rs_part[z M + i]
 __global__ void k_split_reduce(int M, int N, int S, const float *ws, float *C, long long scm,
-                               Epi ep)
+                               Epi ep, const float *rs_part, float *rs)
 {
-    const long long n = (long long)M * N;
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n;
+    const long long n = (long long)M * N, total = n + (rs ? M : 0);
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
          x += (long long)gridDim.x * blockDim.x) {
         float v = 0.f;
-        for (int z = 0; z < S; ++z) v += ws[z * n + x];
-        epilogue(ep, v, (int)(x / N), (int)(x % N), C, scm);
+        if (x < n) {
+            for (int z = 0; z < S; ++z) v += ws[z * n + x];
+            epilogue(ep, v, (int)(x / N), (int)(x % N), C, scm);
+        } else {
+            for (int z = 0; z < S; ++z) v += rs_part[z * M + (x - n)];
+            rs[x - n] = v;
+        }
     }
 }
 
@@ -286,69 +304,71 @@ int device_sms()
     return cache[dev];
 }
 
-// One GEMM with its tiling: 128-wide tiles where they still give every SM two CTAs, else
-// 64-wide tiles, and where even those leave SMs idle, k split over up to SPLIT_MAX CTAs
-// (each at least 64 deep) whose partials go to ws (ws_n floats; no split without it)
+// CTAs of the 64-wide kernel resident on one SM (its registers decide)
+template <typename TA, typename TB, bool RS>
+int gemm_residency()
+{
+    static int n = 0;
+    if (!n) {
+        int r = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_gemm<TA, TB, 64, RS>, 256, 0) !=
+                cudaSuccess || r < 1)
+            r = 1;
+        n = r;
+    }
+    return n;
+}
+
+// One GEMM with its tiling: 128-wide tiles where they alone give every SM two CTAs, else
+// 64-wide tiles, and where even those fill less than one wave of resident CTAs, k split over
+// up to SPLIT_MAX CTAs (each at least 64 deep) whose partials go to ws (ws_n floats; no split
+// without it).  With rs (length M), also rs[i] = sum over k of A(i, k).
 template <typename TA, typename TB>
 cudaError_t gemm(cudaStream_t s, int M, int N, int K, const TA *A, long long sam, long long sak,
                  const TB *B, long long sbk, long long sbn, float *C, long long scm, Epi ep,
-                 float *ws, long long ws_n)
+                 float *ws, long long ws_n, float *rs = nullptr)
 {
-    const long long target = 2LL * device_sms();
     const long long big = (long long)((M + 127) / 128) * ((N + 127) / 128);
-    if (big >= target) {
+    if (big >= 2LL * device_sms() && !rs) {
         count_launches(1);
         dim3 g((N + 127) / 128, (M + 127) / 128);
-        k_gemm<TA, TB, 128><<<g, 256, 0, s>>>(M, N, K, K, A, sam, sak, B, sbk, sbn, C, scm, 0, ep);
+        k_gemm<TA, TB, 128><<<g, 256, 0, s>>>(M, N, K, K, A, sam, sak, B, sbk, sbn, C, scm, 0, ep,
+                                              nullptr);
         return cudaGetLastError();
     }
+    const long long slots = (long long)(rs ? gemm_residency<TA, TB, true>()
+                                          : gemm_residency<TA, TB, false>()) * device_sms();
     const long long tiles = (long long)((M + 63) / 64) * ((N + 63) / 64);
     long long S = 1;
-    if (ws && tiles < target) {
-        S = std::min<long long>({(long long)SPLIT_MAX, (target + tiles - 1) / tiles, K / 64});
-        while (S > 1 && S * M * N > ws_n) --S;
+    if (ws && tiles < slots) {
+        S = std::min<long long>({(long long)SPLIT_MAX, slots / tiles, K / 64});
+        while (S > 1 && S * M * N + (rs ? S * M : 0) > ws_n) --S;
         S = std::max(S, 1LL);
     }
     const int kc = (int)((((K + S - 1) / S) + GK - 1) / GK * GK);
     S = std::max(1, (K + kc - 1) / kc);
     dim3 g((N + 63) / 64, (M + 63) / 64, (unsigned)S);
     count_launches(S > 1 ? 2 : 1);
+    auto run64 = [&](int kc_, float *Cp, long long ldc, long long scz, Epi e, float *r) {
+        if (r)
+            k_gemm<TA, TB, 64, true><<<g, 256, 0, s>>>(M, N, K, kc_, A, sam, sak, B, sbk, sbn, Cp,
+                                                       ldc, scz, e, r);
+        else
+            k_gemm<TA, TB, 64, false><<<g, 256, 0, s>>>(M, N, K, kc_, A, sam, sak, B, sbk, sbn, Cp,
+                                                        ldc, scz, e, nullptr);
+    };
     if (S == 1) {
-        k_gemm<TA, TB, 64><<<g, 256, 0, s>>>(M, N, K, K, A, sam, sak, B, sbk, sbn, C, scm, 0, ep);
+        run64(K, C, scm, 0, ep, rs);
         return cudaGetLastError();
     }
     const long long n = (long long)M * N;
-    k_gemm<TA, TB, 64><<<g, 256, 0, s>>>(M, N, K, kc, A, sam, sak, B, sbk, sbn, ws, N, n, Epi{});
-    const long long nb = std::min<long long>((n + 255) / 256, 8LL * device_sms());
-    k_split_reduce<<<(unsigned)nb, 256, 0, s>>>(M, N, (int)S, ws, C, scm, ep);
+    float *rs_part = rs ? ws + S * n : nullptr;
+    run64(kc, ws, N, n, Epi{}, rs_part);
+    const long long nb = std::min<long long>((n + (rs ? M : 0) + 255) / 256, 8LL * device_sms());
+    k_split_reduce<<<(unsigned)nb, 256, 0, s>>>(M, N, (int)S, ws, C, scm, ep, rs_part, rs);
     return cudaGetLastError();
 }
 
-// db[j] = sum_i dZ[i][j]: a CTA takes 32 columns; its 32 warps sum interleaved rows with
-// four accumulators each, and the warps' sums are added in warp order
-__global__ void __launch_bounds__(1024) k_colsum(int M, int N, const float *dZ, float *db)
-{
-    __shared__ float part[32][33];
-    const int c = threadIdx.x % 32, w = threadIdx.x / 32, j = blockIdx.x * 32 + c;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    if (j < N) {
-        int i = w;
-        for (; i + 96 < M; i += 128) {
-            s0 += dZ[(long long)i * N + j];
-            s1 += dZ[(long long)(i + 32) * N + j];
-            s2 += dZ[(long long)(i + 64) * N + j];
-            s3 += dZ[(long long)(i + 96) * N + j];
-        }
-        for (; i < M; i += 32) s0 += dZ[(long long)i * N + j];
-    }
-    part[w][c] = (s0 + s1) + (s2 + s3);
-    __syncthreads();
-    if (w == 0 && j < N) {
-        float t = 0.f;
-        for (int q = 0; q < 32; ++q) t += part[q][c];
-        db[j] = t;
-    }
-}
 
 // dZ4 = 2 (Z4 - Y) / (3 M), loss partial sums per block
 __global__ void k_mse(int M, const float *Z4, const float *Y, float *dZ4, double *part)
@@ -622,7 +642,7 @@ cudaError_t sur_forward(int h, int M, const void *X, const float *wf, const void
     return e;
 }
 
-long long sur_split_workspace(int h) { return (long long)SPLIT_MAX * h * MLSD_SUR_IN; }
+long long sur_split_workspace(int h) { return (long long)SPLIT_MAX * h * (MLSD_SUR_IN + 1); }
 
 cudaError_t sur_grad(int h, int M, const void *X, const float *Y, const float *wf, const void *wb_,
                      float *Z[4], void *Aact[3], float *dA, float *dB_, float *g, double *part,
@@ -640,12 +660,11 @@ cudaError_t sur_grad(int h, int M, const void *X, const float *Y, const float *w
     for (int l = 3; l >= 0; --l) {
         const __nv_bfloat16 *Ain = l > 0 ? static_cast<const __nv_bfloat16 *>(Aact[l - 1])
                                          : static_cast<const __nv_bfloat16 *>(X);
-        // dW_l[j][k] = sum_m dZ[m][j] Ain[m][k]
+        // dW_l[j][k] = sum_m dZ[m][j] Ain[m][k], and the bias gradient db_l[j] = sum_m dZ[m][j]
+        // as the row sums of the same GEMM's A operand
         e = gemm<float, __nv_bfloat16>(s, L.dout[l], L.din[l], M, dZ, 1, L.dout[l], Ain, L.din[l],
-                                       1, g + L.w[l], L.din[l], Epi{}, ws, ws_n);
+                                       1, g + L.w[l], L.din[l], Epi{}, ws, ws_n, g + L.b[l]);
         if (e != cudaSuccess) return e;
-        count_launches(1);
-        k_colsum<<<(L.dout[l] + 31) / 32, 1024, 0, s>>>(M, L.dout[l], dZ, g + L.b[l]);
         if (l == 0) break;
         // dZ_{l-1}[m][k] = (sum_j dZ[m][j] W_l[j][k]) gelu'(Z_{l-1}[m][k])
         Epi ep;
