@@ -48,3 +48,17 @@ def test_invalid_problem_rejected_on_host():
                        re=re_.ctypes.data, im=im.ctypes.data, n_levels=1, band_edges=e.ctypes.data,
                        patch_n=pn.ctypes.data, cfl=0.2, t_burn_tau=8.0, t_avg_tau=4.0)
     assert m.lib().mlsd_build_levels(ctypes.byref(p), None, ctypes.byref(h)) == -1
+
+
+def test_surrogate_calls_reject_bad_arguments_on_host():
+    # the symmetry map and the training loop validate before any device work
+    import paper_1510_00451_gb300 as m
+    L = m.lib()
+    fake = ctypes.c_void_p(16)                       # never dereferenced: rejected first
+    assert L.mlsd_surrogate_symmetry(fake, fake, 4, 8, fake, fake, None) == -1      # g > 7
+    assert L.mlsd_surrogate_symmetry(fake, fake, -1, 0, fake, fake, None) == -1     # n < 0
+    assert L.mlsd_surrogate_symmetry(fake, fake, 4, 0, None, None, None) == -1      # no output
+    assert L.mlsd_surrogate_symmetry(None, fake, 4, 0, fake, None, None) == -1      # X_out, no X
+    # training without a handle
+    assert L.mlsd_surrogate_train(None, fake, fake, 1024, 1, 128, ctypes.c_float(1e-3),
+                                  ctypes.c_float(1e-3), 0, 1, None, None) == -1
