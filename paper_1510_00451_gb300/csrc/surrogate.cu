@@ -190,13 +190,13 @@ __device__ __forceinline__ void epilogue(const Epi &e, float v, int gi, int gj, 
 // float4. The next k stage is loaded into registers while the current one is multiplied.
 // With gridDim.z > 1 the CTA sums only k in [z kc, (z + 1) kc) and stores its raw partial
 // at C + z scz (row stride scm); k_split_reduce adds the partials and applies the epilogue.
-// With rs, the CTAs of the first column tile also sum A's rows over their k range into
-// rs[z M + i] (the bias gradient, when A is the transposed output gradient).
+// With RS, the CTAs of the first column tile also sum A's rows over their k range into
+// rs[z M + i] (the bias gradient, when A is the transposed output gradient). That variant
+// is capped to keep 3 CTAs per SM; the plain one reaches it uncapped.
 template <typename TA, typename TB, int T, bool RS = false>
-__global__ void __launch_bounds__(256, RS ? 3 : 0) k_gemm(int M, int N, int K, int kc, const TA *A,
-                                              long long sam, long long sak, const TB *Bm,
-                                              long long sbk, long long sbn, float *C,
-                                              long long scm, long long scz, Epi ep, float *rs)
+__global__ void __launch_bounds__(256, RS ? 3 : 0)
+    k_gemm(int M, int N, int K, int kc, const TA *A, long long sam, long long sak, const TB *Bm,
+           long long sbk, long long sbn, float *C, long long scm, long long scz, Epi ep, float *rs)
 {
     constexpr int R = T / 16, E = T * GK / 256;
     __shared__ __align__(16) float As[GK][T + 4];
