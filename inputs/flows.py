@@ -167,6 +167,15 @@ def gaussian_u0(n, sigma=0.5, center=(math.pi, math.pi), dtype=np.float64):
     return np.exp(-(dx ** 2 + dy ** 2) / (2.0 * sigma ** 2)).astype(dtype)
 
 
+def step_u0(n, u_left=1.0, u_right=0.0, dtype=np.float64):
+    """The step initial condition of the Sec. 4 set-up on [0, 2 pi] x [0, 2 pi):
+    u0 = u_left for x1 <= pi, u_right for x1 > pi, on the n x n node grid
+    x1 = 2 pi i / n (column 0 is the boundary x1 = 0); layout [j][i]."""
+    x = 2.0 * math.pi * np.arange(n) / n
+    row = np.where(x <= math.pi, u_left, u_right)
+    return np.tile(row, (n, 1)).astype(dtype)
+
+
 def config_problem(name):
     """Problem parameters of the named workload (inputs only; no method logic).
 

@@ -60,6 +60,8 @@ def _declare(L):
     L.orc_macro_dt.restype = _d
     L.orc_macro_run.argtypes = [_i, _p, _p, _d, _l, _p]
     L.orc_dns_run.argtypes = [_i, _p, _d, _d, _l, _p]
+    L.orc_macro_run_dirichlet.argtypes = [_i, _p, _p, _d, _l, _d, _d]
+    L.orc_dns_run_dirichlet.argtypes = [_i, _p, _d, _d, _l, _d, _d, _p]
     L.orc_grid_psi.argtypes = [_i, _p, _p, _p, _p, _i, _p]
     L.orc_coarse_grain.argtypes = [_i, _p, _i, _p, _p]
     L.orc_num_threads.restype = _i
@@ -274,6 +276,24 @@ def grid_psi(spec, Nf):
 def dns_run(psi, kappa, dt, nsteps, u0):
     psi = _f64(psi); u = _f64(u0).copy()
     lib().orc_dns_run(psi.shape[0], _ptr(psi), float(kappa), float(dt), int(nsteps), _ptr(u))
+    return u
+
+
+def macro_run_dirichlet(U, K, dt, nsteps, u_left=1.0, u_right=0.0):
+    """Macro steps with the Sec. 4 boundaries: Dirichlet in x1 (column 0 held at
+    u_left, the virtual column N at u_right), periodic in x2.  Returns U."""
+    U = _f64(U).copy(); K = _f64(K)
+    N = U.shape[0]
+    lib().orc_macro_run_dirichlet(N, _ptr(U), _ptr(K), float(dt), int(nsteps), float(u_left),
+                                  float(u_right))
+    return U
+
+
+def dns_run_dirichlet(psi, kappa, dt, nsteps, u0, u_left=1.0, u_right=0.0):
+    """Direct simulation with the Sec. 4 boundaries (as macro_run_dirichlet)."""
+    psi = _f64(psi); u = _f64(u0).copy()
+    lib().orc_dns_run_dirichlet(psi.shape[0], _ptr(psi), float(kappa), float(dt), int(nsteps),
+                                float(u_left), float(u_right), _ptr(u))
     return u
 
 

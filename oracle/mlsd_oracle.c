@@ -28,6 +28,9 @@
  *   orc_chain           -- Algorithm 3 applied level by level, finest first
  *   orc_macro_run       -- macro solver for U_t = div(K grad U), Eq. (homo)
  *   orc_dns_run         -- direct simulation of Eq. (model) on the full grid
+ *   orc_macro_run_dirichlet / orc_dns_run_dirichlet
+ *                       -- the same two solvers with the Sec. 4 boundary
+ *                          conditions (Dirichlet in x1, periodic in x2)
  */
 #include <math.h>
 #include <stdint.h>
@@ -652,6 +655,122 @@ void orc_dns_run(int Nf, const double *psi, double kappa, double dt, long nsteps
         dns_rhs(Nf, h, v1, v2, kappa, u, f);
         for (long c = 0; c < nn; ++c) us[c] = u[c] + dt * f[c];
         dns_rhs(Nf, h, v1, v2, kappa, us, f);
+        for (long c = 0; c < nn; ++c) u[c] = 0.5 * (u[c] + us[c] + dt * f[c]);
+    }
+    free(v1); free(v2); free(f); free(us);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4 set-up: Dirichlet conditions in x1, periodic in x2.  The paper     */
+/* solves on [0,1]^2 with u = 1 at x1 = 0, u = 0 at x1 = 1 and the step      */
+/* u0 = 1 for x1 <= 1/2, else 0.  Here the same problem is posed on          */
+/* [0, 2 pi] x [0, 2 pi): nodes x1 = i H (H = 2 pi / N), column i = 0 is the  */
+/* boundary x1 = 0 (held at u_left) and a virtual column i = N is the        */
+/* boundary x1 = 2 pi (value u_right); columns 1..N-1 are the unknowns.  The */
+/* K field (or the velocity) is periodic, so its column N is its column 0.   */
+/* The interior scheme is the periodic one unchanged.                        */
+/* ------------------------------------------------------------------------ */
+static double u_dir(const double *U, int N, int i, int j, double u_right)
+{
+    return i == N ? u_right : U[(long)j * N + i];
+}
+
+static void macro_rhs_dir(int N, double H, const double *K, const double *U, double ur, double *R)
+{
+#pragma omp parallel for
+    for (int j = 0; j < N; ++j) {
+        int jp = (j + 1) % N, jm = (j + N - 1) % N;
+        R[(long)j * N] = 0.0;
+        for (int i = 1; i < N; ++i) {
+            int ip = i + 1, im_ = i - 1, ipk = ip % N;
+            double fe, fw, fn, fs;
+            {
+                const double *a = K + 3L * (j * N + i), *b = K + 3L * (j * N + ipk);
+                double k11 = 0.5 * (a[0] + b[0]), k12 = 0.5 * (a[1] + b[1]);
+                fe = k11 * (u_dir(U, N, ip, j, ur) - u_dir(U, N, i, j, ur)) / H
+                   + k12 * (u_dir(U, N, i, jp, ur) + u_dir(U, N, ip, jp, ur)
+                            - u_dir(U, N, i, jm, ur) - u_dir(U, N, ip, jm, ur)) / (4.0 * H);
+            }
+            {
+                const double *a = K + 3L * (j * N + im_), *b = K + 3L * (j * N + i);
+                double k11 = 0.5 * (a[0] + b[0]), k12 = 0.5 * (a[1] + b[1]);
+                fw = k11 * (u_dir(U, N, i, j, ur) - u_dir(U, N, im_, j, ur)) / H
+                   + k12 * (u_dir(U, N, im_, jp, ur) + u_dir(U, N, i, jp, ur)
+                            - u_dir(U, N, im_, jm, ur) - u_dir(U, N, i, jm, ur)) / (4.0 * H);
+            }
+            {
+                const double *a = K + 3L * (j * N + i), *b = K + 3L * (jp * N + i);
+                double k22 = 0.5 * (a[2] + b[2]), k12 = 0.5 * (a[1] + b[1]);
+                fn = k22 * (u_dir(U, N, i, jp, ur) - u_dir(U, N, i, j, ur)) / H
+                   + k12 * (u_dir(U, N, ip, j, ur) + u_dir(U, N, ip, jp, ur)
+                            - u_dir(U, N, im_, j, ur) - u_dir(U, N, im_, jp, ur)) / (4.0 * H);
+            }
+            {
+                const double *a = K + 3L * (jm * N + i), *b = K + 3L * (j * N + i);
+                double k22 = 0.5 * (a[2] + b[2]), k12 = 0.5 * (a[1] + b[1]);
+                fs = k22 * (u_dir(U, N, i, j, ur) - u_dir(U, N, i, jm, ur)) / H
+                   + k12 * (u_dir(U, N, ip, jm, ur) + u_dir(U, N, ip, j, ur)
+                            - u_dir(U, N, im_, jm, ur) - u_dir(U, N, im_, j, ur)) / (4.0 * H);
+            }
+            R[(long)j * N + i] = (fe - fw + fn - fs) / H;
+        }
+    }
+}
+
+/* Heun steps of the macro problem with the Dirichlet x1 boundaries; column 0 */
+/* of U is set to u_left first and stays there.                              */
+void orc_macro_run_dirichlet(int N, double *U, const double *K, double dt, long nsteps,
+                             double u_left, double u_right)
+{
+    double H = 2.0 * ORC_PI / N;
+    long nn = (long)N * N;
+    double *R = malloc(sizeof(double) * nn), *Us = malloc(sizeof(double) * nn);
+    for (int j = 0; j < N; ++j) U[(long)j * N] = u_left;
+    for (long s = 1; s <= nsteps; ++s) {
+        macro_rhs_dir(N, H, K, U, u_right, R);
+        for (long c = 0; c < nn; ++c) Us[c] = U[c] + dt * R[c];
+        macro_rhs_dir(N, H, K, Us, u_right, R);
+        for (long c = 0; c < nn; ++c) U[c] = 0.5 * (U[c] + Us[c] + dt * R[c]);
+    }
+    free(R); free(Us);
+}
+
+/* The direct simulation of the Sec. 4 set-up: the DNS scheme of             */
+/* orc_dns_run on the interior columns 1..Nf-1, column 0 held at u_left and  */
+/* the virtual column Nf at u_right.                                         */
+static void dns_rhs_dir(int Nf, double h, const double *v1, const double *v2, double kappa,
+                        const double *u, double ur, double *f)
+{
+#pragma omp parallel for
+    for (int b = 0; b < Nf; ++b) {
+        int bp = (b + 1) % Nf, bm = (b + Nf - 1) % Nf;
+        f[(long)b * Nf] = 0.0;
+        for (int a = 1; a < Nf; ++a) {
+            long c = (long)b * Nf + a;
+            double uc = u[c];
+            double ue = u_dir(u, Nf, a + 1, b, ur), uw = u[c - 1];
+            double un = u[(long)bp * Nf + a], us = u[(long)bm * Nf + a];
+            double d0x = (ue - uw) / (2.0 * h);
+            double d0y = (un - us) / (2.0 * h);
+            double lap = (ue + uw + un + us - 4.0 * uc) / (h * h);
+            f[c] = v1[c] * d0x + v2[c] * d0y + kappa * lap;
+        }
+    }
+}
+
+void orc_dns_run_dirichlet(int Nf, const double *psi, double kappa, double dt, long nsteps,
+                           double u_left, double u_right, double *u)
+{
+    long nn = (long)Nf * Nf;
+    double h = 2.0 * ORC_PI / Nf;
+    double *v1 = malloc(sizeof(double) * nn), *v2 = malloc(sizeof(double) * nn);
+    double *f = malloc(sizeof(double) * nn), *us = malloc(sizeof(double) * nn);
+    orc_velocity(Nf, h, psi, v1, v2);
+    for (int b = 0; b < Nf; ++b) u[(long)b * Nf] = u_left;
+    for (long s = 0; s < nsteps; ++s) {
+        dns_rhs_dir(Nf, h, v1, v2, kappa, u, u_right, f);
+        for (long c = 0; c < nn; ++c) us[c] = u[c] + dt * f[c];
+        dns_rhs_dir(Nf, h, v1, v2, kappa, us, u_right, f);
         for (long c = 0; c < nn; ++c) u[c] = 0.5 * (u[c] + us[c] + dt * f[c]);
     }
     free(v1); free(v2); free(f); free(us);
