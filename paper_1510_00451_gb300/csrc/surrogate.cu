@@ -304,19 +304,21 @@ int device_sms()
     return cache[dev];
 }
 
-// CTAs of the 64-wide kernel resident on one SM (its registers decide)
+// CTAs of the 64-wide kernel resident on one SM (its registers decide), per device
 template <typename TA, typename TB, bool RS>
 int gemm_residency()
 {
-    static int n = 0;
-    if (!n) {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!cache[dev]) {
         int r = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_gemm<TA, TB, 64, RS>, 256, 0) !=
                 cudaSuccess || r < 1)
             r = 1;
-        n = r;
+        cache[dev] = r;
     }
-    return n;
+    return cache[dev];
 }
 
 // One GEMM with its tiling: 128-wide tiles where they alone give every SM two CTAs, else
