@@ -272,6 +272,93 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
             "seconds": {"dataset": t_data, "train": t_train, "plain": t_plain}}
 
 
+def _profile_gap(a, b):
+    """max |a - b| and relative L2 of two x1-profiles."""
+    a = np.asarray(a, dtype=np.float64); b = np.asarray(b, dtype=np.float64)
+    return {"max_abs": float(np.abs(a - b).max()),
+            "rel_l2": float(np.linalg.norm(a - b) / np.linalg.norm(b))}
+
+
+def sec4_case(amps=(1.0 / 3.0, 2.5), N=64, nf=512, t_end=0.4 * math.pi ** 2):
+    """The paper's Sec. 4 set-up with two separated cellular modes (the structure
+    of its Sec. 4.2 example): psi = a (sin 5x sin 5y + sin 25x sin 25y), kappa = 1,
+    u = 1 at x1 = 0 and 0 at x1 = 2 pi, periodic in x2, step initial condition,
+    t_end = 0.4 pi^2 (the paper's t = 0.1 on [0,1]^2; x -> 2 pi x, t -> 4 pi^2 t).
+    a = 1/3 is the printed amplitude; a = 2.5 gives K near the printed K values.
+    SHMM: two levels (edges 1, 6, 26; patch sides 2 pi and 2 pi / 5; 64^2
+    patches; full relaxation window), then the macro solve on N x N.  Reference:
+    the direct simulation on nf x nf.  Baseline: pure diffusion.  Compared: the
+    x2-averaged profiles U(x1) at the macro nodes, and K11 fitted to the DNS
+    profile by the macro solver with a constant K."""
+    import torch
+    import inputs
+    from inputs import flows
+    import paper_1510_00451_gb300 as mlsd
+    dev = torch.device("cuda", _local_rank())
+    kappa, r = 1.0, nf // N
+    out = []
+    for amp in amps:
+        spec = flows.cellular([(amp, 5, 5), (amp, 25, 25)])
+        t0 = time.perf_counter()
+        lv = mlsd.Levels(spec, kappa, N, [1.0, 6.0, 26.0], [64, 64], patch_div=[1, 5], cfl=0.2)
+        K = torch.zeros(N * N, 3, dtype=torch.float64, device=dev)
+        lv.effective_diffusivity(K)
+        torch.cuda.synchronize()
+        t_chain = time.perf_counter() - t0
+        assert lv.status() == 0
+        lv.close()
+
+        def macro(Kf):
+            dt = mlsd.macro_dt(Kf, N, 0.2)
+            ns = max(1, math.ceil(t_end / dt))
+            U = torch.tensor(inputs.step_u0(N), dtype=torch.float64, device=dev)
+            mlsd.macro_step_dirichlet(U, Kf, t_end / ns, ns, 1.0, 0.0)
+            return U.cpu().numpy()
+
+        Ushmm = macro(K)
+        Knone = torch.tensor(np.tile([kappa, 0.0, kappa], (N * N, 1)), dtype=torch.float64,
+                             device=dev)
+        Unone = macro(Knone)
+        psi = torch.empty(nf, nf, dtype=torch.float32, device=dev)
+        mlsd.grid_psi(spec, nf, psi)
+        dt = mlsd.dns_dt(psi, kappa, 0.2)
+        ns = math.ceil(t_end / dt)
+        u = torch.tensor(inputs.step_u0(nf), dtype=torch.float32, device=dev)
+        ut = torch.empty_like(u)
+        t0 = time.perf_counter()
+        mlsd.dns_run_dirichlet(u, ut, psi, kappa, t_end / ns, ns, 1.0, 0.0)
+        torch.cuda.synchronize()
+        t_dns = time.perf_counter() - t0
+        un = u.cpu().numpy().astype(np.float64)
+        prof_dns = un[:, ::r].mean(0)                   # x2-average at the macro nodes x1 = i H
+        prof_shmm, prof_none = Ushmm.mean(0), Unone.mean(0)
+        # K11 of the DNS: the constant K11 whose macro profile fits the DNS profile best
+        lo, hi = kappa, 10.0 * float(K[:, 0].max().item()) + kappa
+
+        def gap(k11):
+            Kc = torch.tensor(np.tile([k11, 0.0, kappa], (N * N, 1)), dtype=torch.float64,
+                              device=dev)
+            return float(np.linalg.norm(macro(Kc).mean(0) - prof_dns))
+        for _ in range(40):                              # golden-section search on K11
+            a1 = hi - 0.618 * (hi - lo); a2 = lo + 0.618 * (hi - lo)
+            if gap(a1) < gap(a2):
+                hi = a2
+            else:
+                lo = a1
+        Kn = K.cpu().numpy()
+        out.append({"amplitude": amp, "K_shmm_mean": Kn.mean(0).tolist(),
+                    "K_shmm_node_spread": float(np.abs(Kn - Kn.mean(0)).max()),
+                    "K11_fitted_to_dns": 0.5 * (lo + hi),
+                    "shmm_vs_dns": _profile_gap(prof_shmm, prof_dns),
+                    "no_advection_vs_dns": _profile_gap(prof_none, prof_dns),
+                    "dns": {"grid": nf, "steps": ns, "dt": t_end / ns, "seconds": t_dns},
+                    "chain_seconds": t_chain})
+    return {"workload": f"Sec. 4 set-up, psi = a(sin5x sin5y + sin25x sin25y), kappa=1, "
+                        f"Dirichlet x1 / periodic x2, step IC, t={t_end:.4f}; SHMM 2 levels, "
+                        f"{N}^2 macro, 64^2 patches; DNS {nf}^2",
+            "cases": out}
+
+
 def uneven_case(n_avg=32):
     """The continuous-spectrum workload at full size: |k| <= 256, 8 octave levels,
     256 x 256 macro nodes (65536 patches per level), patch sizes 32^2 .. 256^2
@@ -480,7 +567,7 @@ def main():
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--case", default="full",
                     choices=["full", "profile", "dns-profile", "dns-full", "surrogate", "uneven",
-                             "mlp-profile", "cluster-profile", "train-profile"],
+                             "mlp-profile", "cluster-profile", "train-profile", "sec4"],
                     help="profile: one pass of the same workload with a fixed 200-step window "
                          "per patch (a small case for ncu captures); prints no bench line")
     args = ap.parse_args()
@@ -503,6 +590,9 @@ def main():
         return train_case()
     if args.case == "uneven":
         print(json.dumps({"case": "uneven", **uneven_case()}), flush=True)
+        return 0
+    if args.case == "sec4":
+        print(json.dumps({"case": "sec4", **sec4_case()}), flush=True)
         return 0
 
     import torch

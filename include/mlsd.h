@@ -366,6 +366,21 @@ int mlsd_status(mlsd_levels *h, void *cuda_stream);
 int mlsd_macro_step(int n_macro, void *U_dev, int precision, const double *K_dev, double dt,
                     int nsteps, double *mass_out_host, void *cuda_stream);
 
+/* The macro step with the boundary conditions of the paper's numerical
+ * examples (Sec. 4): Dirichlet in x1, periodic in x2.  The paper's [0,1]^2 is
+ * posed here as [0, 2 pi] x [0, 2 pi) (x -> 2 pi x, t -> 4 pi^2 t, psi
+ * unchanged, kappa unchanged).  Nodes x1 = i H, H = 2 pi / N:
+ *   column i = 0 of U is the boundary x1 = 0: set to u_left on entry and held;
+ *   the boundary x1 = 2 pi is a virtual column N with the value u_right;
+ *   columns 1..N-1 follow the interior scheme of mlsd_macro_step unchanged.
+ * K_dev is a periodic field (the level chain's output), so the face tensor
+ * between column N-1 and the boundary is (K(N-1) + K(0)) / 2.  Other
+ * arguments, the mass list (H^2 sum(U), not conserved here) and the errors
+ * are those of mlsd_macro_step.                                             */
+int mlsd_macro_step_dirichlet(int n_macro, void *U_dev, int precision, const double *K_dev,
+                              double dt, int nsteps, double u_left, double u_right,
+                              double *mass_out_host, void *cuda_stream);
+
 /* Stable macro time step dt = cfl H^2 / max_nodes(K11 + K22 + |K12|).
  * Blocks until it is known.                                                 */
 int mlsd_macro_dt(int n_macro, const double *K_dev, double cfl, double *dt_out_host,
@@ -383,6 +398,16 @@ int mlsd_grid_psi(int n_modes, const int32_t *k1, const int32_t *k2, const doubl
  * caller-provided work field of the same size.  nf a multiple of 128.        */
 int mlsd_dns_run(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev, double kappa,
                  double dt, int nsteps, void *cuda_stream);
+
+/* The direct simulation with the Sec. 4 boundary conditions (Dirichlet in x1,
+ * periodic in x2), posed on [0, 2 pi] x [0, 2 pi) as mlsd_macro_step_dirichlet:
+ * column 0 of u_dev is set to u_left and held, the virtual column nf has the
+ * value u_right; psi (and so v) stays periodic.  One launch per RK stage (the
+ * paper's 512 x 512 reference, L2-resident); any nf >= 4.  u_tmp_dev is a
+ * caller-provided work field of the same size.  Asynchronous on the stream. */
+int mlsd_dns_run_dirichlet(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev,
+                           double kappa, double dt, int nsteps, double u_left, double u_right,
+                           void *cuda_stream);
 
 /* Stable DNS time step: dt = cfl * min(h / max(|v1| + |v2|), h^2 / (4 kappa)),
  * v from psi by central differences, h = 2*pi/nf.  Blocks until known.    */

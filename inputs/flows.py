@@ -67,6 +67,15 @@ def cellular_two_scale(a0=1.0, a1=1.0, m=8):
     return _from_dict(d, {"kind": "cellular_two_scale", "m": m})
 
 
+def cellular(terms):
+    """psi = sum over (a, m1, m2) of a sin(m1 x1) sin(m2 x2) (the paper's phi_c
+    cellular modes, Sec. 4.2 / 4.3, on [0, 2 pi)^2)."""
+    d = {}
+    for a, m1, m2 in terms:
+        _add_sinsin(d, a, m1, m2)
+    return _from_dict(d, {"kind": "cellular", "terms": list(terms)})
+
+
 def cellular_hierarchy(levels=3, alpha=4):
     """psi = sum_j alpha^-j sin(alpha^j x) sin(alpha^j y), j = 0..levels-1."""
     d = {}

@@ -27,6 +27,7 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_macro_dt", "mlsd_grid_psi", "mlsd_dns_run", "mlsd_coarse_grain",
             "mlsd_level_work", "mlsd_corrector_energy", "mlsd_launch_count", "mlsd_profile", "mlsd_profile_collect",
             "mlsd_coarse_grain_noalloc", "mlsd_dns_dt", "mlsd_patch_sizes",
+            "mlsd_macro_step_dirichlet", "mlsd_dns_run_dirichlet",
             "mlsd_surrogate_param_count", "mlsd_surrogate_create", "mlsd_surrogate_free",
             "mlsd_surrogate_set_params", "mlsd_surrogate_get_params", "mlsd_surrogate_features",
             "mlsd_surrogate_grad", "mlsd_surrogate_train_step", "mlsd_surrogate_predict",
@@ -91,6 +92,8 @@ _lib.mlsd_launch_count.argtypes = []
 _lib.mlsd_launch_count.restype = _L
 _lib.mlsd_patch_sizes.argtypes = [_P, _I, _P]
 _lib.mlsd_dns_dt.argtypes = [_I, _P, _D, _D, ctypes.POINTER(_D), _P]
+_lib.mlsd_macro_step_dirichlet.argtypes = [_I, _P, _I, _P, _D, _I, _D, _D, _P, _P]
+_lib.mlsd_dns_run_dirichlet.argtypes = [_I, _P, _P, _P, _D, _D, _I, _D, _D, _P]
 _lib.mlsd_coarse_grain_noalloc.argtypes = [_I, _P, _I, _P, _P, _P]
 _lib.mlsd_surrogate_param_count.argtypes = [_I]
 _lib.mlsd_surrogate_param_count.restype = _L
@@ -284,6 +287,20 @@ def macro_step(U, K, dt, nsteps, want_mass=True, stream=None):
     return mass
 
 
+def macro_step_dirichlet(U, K, dt, nsteps, u_left=1.0, u_right=0.0, want_mass=False,
+                         stream=None):
+    """In-place Heun steps with the Sec. 4 boundaries (Dirichlet in x1, periodic
+    in x2; column 0 is the boundary x1 = 0); returns the mass list or None."""
+    import torch
+    prec = MLSD_FP64 if U.dtype == torch.float64 else MLSD_FP32
+    mass = np.zeros(nsteps + 1) if want_mass else None
+    _check(_lib.mlsd_macro_step_dirichlet(U.shape[0], _dptr(U), prec, _dptr(K), float(dt),
+                                          int(nsteps), float(u_left), float(u_right),
+                                          None if mass is None else mass.ctypes.data,
+                                          _stream(stream)), "mlsd_macro_step_dirichlet")
+    return mass
+
+
 def macro_dt(K, n_macro, cfl, stream=None):
     out = ctypes.c_double()
     _check(_lib.mlsd_macro_dt(int(n_macro), _dptr(K), float(cfl), ctypes.byref(out),
@@ -301,6 +318,12 @@ def grid_psi(spectrum, nf, psi_out, stream=None):
 def dns_run(u, u_tmp, psi, kappa, dt, nsteps, stream=None):
     _check(_lib.mlsd_dns_run(u.shape[0], _dptr(u), _dptr(u_tmp), _dptr(psi), float(kappa),
                              float(dt), int(nsteps), _stream(stream)), "mlsd_dns_run")
+
+
+def dns_run_dirichlet(u, u_tmp, psi, kappa, dt, nsteps, u_left=1.0, u_right=0.0, stream=None):
+    _check(_lib.mlsd_dns_run_dirichlet(u.shape[0], _dptr(u), _dptr(u_tmp), _dptr(psi),
+                                       float(kappa), float(dt), int(nsteps), float(u_left),
+                                       float(u_right), _stream(stream)), "mlsd_dns_run_dirichlet")
 
 
 def dns_dt(psi, kappa, cfl, stream=None):

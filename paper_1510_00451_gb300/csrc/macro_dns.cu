@@ -21,19 +21,27 @@
 namespace mlsd {
 namespace {
 
-template <typename real>
+// DIR = false: periodic in both directions.  DIR = true: the Sec. 4 set-up,
+// Dirichlet in x1 -- column 0 is the boundary x1 = 0 (held by the caller) and
+// the virtual column N the boundary x1 = 2 pi with value ur; the K field stays
+// periodic (its column N is column 0).  Column 0 itself has no update (0).
+template <typename real, bool DIR = false>
 __device__ __forceinline__ real macro_rhs(int N, real invH, real inv4H, const real *U,
                                           const real *K11, const real *K12, const real *K22,
-                                          int i, int j)
+                                          int i, int j, real ur = (real)0)
 {
-    const int ip = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
+    if (DIR && i == 0) return (real)0;
+    const int ipk = (i + 1 == N) ? 0 : i + 1, im = (i == 0) ? N - 1 : i - 1;
     const int jp = (j + 1 == N) ? 0 : j + 1, jm = (j == 0) ? N - 1 : j - 1;
     const int c = j * N + i;
+    const bool edge = DIR && i + 1 == N;        // east neighbours are the boundary value
+    const real uE = edge ? ur : U[j * N + ipk], uEn = edge ? ur : U[jp * N + ipk];
+    const real uEs = edge ? ur : U[jm * N + ipk];
     const real h = (real)0.5;
     // east face (i+1/2, j)
-    real k11 = h * (K11[c] + K11[j * N + ip]), k12 = h * (K12[c] + K12[j * N + ip]);
-    const real fe = k11 * (U[j * N + ip] - U[c]) * invH
-                  + k12 * (U[jp * N + i] + U[jp * N + ip] - U[jm * N + i] - U[jm * N + ip]) * inv4H;
+    real k11 = h * (K11[c] + K11[j * N + ipk]), k12 = h * (K12[c] + K12[j * N + ipk]);
+    const real fe = k11 * (uE - U[c]) * invH
+                  + k12 * (U[jp * N + i] + uEn - U[jm * N + i] - uEs) * inv4H;
     // west face (i-1/2, j)
     k11 = h * (K11[j * N + im] + K11[c]); k12 = h * (K12[j * N + im] + K12[c]);
     const real fw = k11 * (U[c] - U[j * N + im]) * invH
@@ -41,11 +49,11 @@ __device__ __forceinline__ real macro_rhs(int N, real invH, real inv4H, const re
     // north face (i, j+1/2)
     real k22 = h * (K22[c] + K22[jp * N + i]); k12 = h * (K12[c] + K12[jp * N + i]);
     const real fn = k22 * (U[jp * N + i] - U[c]) * invH
-                  + k12 * (U[j * N + ip] + U[jp * N + ip] - U[j * N + im] - U[jp * N + im]) * inv4H;
+                  + k12 * (uE + uEn - U[j * N + im] - U[jp * N + im]) * inv4H;
     // south face (i, j-1/2)
     k22 = h * (K22[jm * N + i] + K22[c]); k12 = h * (K12[jm * N + i] + K12[c]);
     const real fs = k22 * (U[c] - U[jm * N + i]) * invH
-                  + k12 * (U[jm * N + ip] + U[c + (ip - i)] - U[jm * N + im] - U[c + (im - i)]) * inv4H;
+                  + k12 * (uEs + uE - U[jm * N + im] - U[j * N + im]) * inv4H;
     return (fe - fw + fn - fs) * invH;
 }
 
@@ -61,10 +69,11 @@ __device__ double block_sum(double v, double *red)
     return t;
 }
 
-// one CTA, everything in shared memory
-template <typename real>
+// one CTA, everything in shared memory (DIR: column 0 set to ul, east boundary ur)
+template <typename real, bool DIR = false>
 __global__ void __launch_bounds__(1024) k_macro_resident(int N, real *Ug, const double *Kg,
-                                                         real dt, int nsteps, double *mass)
+                                                         real dt, int nsteps, double *mass,
+                                                         real ul = (real)0, real ur = (real)0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *U = reinterpret_cast<real *>(smem_raw);
@@ -76,7 +85,7 @@ __global__ void __launch_bounds__(1024) k_macro_resident(int N, real *Ug, const 
     const double H2 = H * H;
     double m = 0.0;
     for (int c = threadIdx.x; c < NN; c += blockDim.x) {
-        U[c] = Ug[c];
+        U[c] = (DIR && c % N == 0) ? ul : Ug[c];
         K11[c] = (real)Kg[3 * c]; K12[c] = (real)Kg[3 * c + 1]; K22[c] = (real)Kg[3 * c + 2];
         m += (double)U[c];
     }
@@ -84,12 +93,12 @@ __global__ void __launch_bounds__(1024) k_macro_resident(int N, real *Ug, const 
     if (threadIdx.x == 0 && mass) mass[0] = m * H2;
     for (int s = 1; s <= nsteps; ++s) {
         for (int c = threadIdx.x; c < NN; c += blockDim.x)
-            Us[c] = U[c] + dt * macro_rhs<real>(N, invH, inv4H, U, K11, K12, K22, c % N, c / N);
+            Us[c] = U[c] + dt * macro_rhs<real, DIR>(N, invH, inv4H, U, K11, K12, K22, c % N, c / N, ur);
         __syncthreads();
         real nu[4];
         int k = 0;
         for (int c = threadIdx.x; c < NN; c += blockDim.x, ++k)
-            nu[k] = (real)0.5 * (U[c] + Us[c] + dt * macro_rhs<real>(N, invH, inv4H, Us, K11, K12, K22, c % N, c / N));
+            nu[k] = (real)0.5 * (U[c] + Us[c] + dt * macro_rhs<real, DIR>(N, invH, inv4H, Us, K11, K12, K22, c % N, c / N, ur));
         __syncthreads();
         k = 0;
         m = 0.0;
@@ -114,9 +123,9 @@ __global__ void k_split_K(int NN, const double *Kg, real *K11, real *K12, real *
 
 // stage 1: Us = U + dt R(U); stage 2: U = (U + Us + dt R(Us)) / 2, with the block's
 // share of sum(U) written to part[block]
-template <typename real, bool SECOND>
+template <typename real, bool SECOND, bool DIR = false>
 __global__ void k_macro_stage(int N, real *U, real *Us, const real *K11, const real *K12,
-                              const real *K22, real dt, double *part)
+                              const real *K22, real dt, double *part, real ur = (real)0)
 {
     __shared__ double red[32];
     const int NN = N * N;
@@ -126,9 +135,9 @@ __global__ void k_macro_stage(int N, real *U, real *Us, const real *K11, const r
     double m = 0.0;
     if (c < NN) {
         if (!SECOND) {
-            Us[c] = U[c] + dt * macro_rhs<real>(N, invH, inv4H, U, K11, K12, K22, c % N, c / N);
+            Us[c] = U[c] + dt * macro_rhs<real, DIR>(N, invH, inv4H, U, K11, K12, K22, c % N, c / N, ur);
         } else {
-            const real v = (real)0.5 * (U[c] + Us[c] + dt * macro_rhs<real>(N, invH, inv4H, Us, K11, K12, K22, c % N, c / N));
+            const real v = (real)0.5 * (U[c] + Us[c] + dt * macro_rhs<real, DIR>(N, invH, inv4H, Us, K11, K12, K22, c % N, c / N, ur));
             m = (double)v;
             // U is read by neighbours only in stage 1, so the in-place write is safe here
             U[c] = v;
@@ -138,6 +147,14 @@ __global__ void k_macro_stage(int N, real *U, real *Us, const real *K11, const r
         m = block_sum(m, red);
         if (threadIdx.x == 0) part[blockIdx.x] = m;
     }
+}
+
+// Dirichlet set-up: column 0 (the boundary x1 = 0) takes the boundary value
+template <typename real>
+__global__ void k_set_col0(int N, real *U, real ul)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < N) U[(long long)j * N] = ul;
 }
 
 template <typename real>
@@ -321,6 +338,39 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
     }
 }
 
+// DNS with the Sec. 4 boundaries (Dirichlet in x1, periodic in x2): one launch
+// per Heun stage, one thread per node.  Column 0 is the boundary x1 = 0 (held
+// at ul), the virtual column nf the boundary x1 = 2 pi (value ur); psi and the
+// velocity stay periodic.  Stage 1: s = u + dt f(u) into `out`; stage 2:
+// out = (u + s + dt f(s)) / 2 with `s` the stage-1 field.  The same folded
+// constants as k_dns_step: cA = dt / (4 h^2) on psi differences times u
+// differences, cD = dt kappa / h^2 on the Laplacian (kept as a difference).
+template <bool SECOND>
+__global__ void k_dns_dir_stage(int nf, const float *__restrict__ u, const float *__restrict__ sfield,
+                                const float *__restrict__ psi, float *__restrict__ out, float cA,
+                                float cD, float ul, float ur)
+{
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= (long long)nf * nf) return;
+    const int a = (int)(c % nf), b = (int)(c / nf);
+    if (a == 0) { out[c] = ul; return; }
+    const float *x = SECOND ? sfield : u;
+    const int bp = b + 1 == nf ? 0 : b + 1, bm = b == 0 ? nf - 1 : b - 1;
+    const int ap = a + 1 == nf ? 0 : a + 1;
+    const long long row = (long long)b * nf;
+    const float xc = x[c];
+    const float xE = a + 1 == nf ? ur : x[row + ap], xW = x[c - 1];
+    const float xN = x[(long long)bp * nf + a], xS = x[(long long)bm * nf + a];
+    // dt (v1 D0x + v2 D0y) x = cA [(psiS - psiN)(xE - xW) + (psiE - psiW)(xN - xS)]
+    const float pN = psi[(long long)bp * nf + a], pS = psi[(long long)bm * nf + a];
+    const float pE = psi[row + ap], pW = psi[row + a - 1];
+    float t = (pS - pN) * (xE - xW);
+    t = fmaf(pE - pW, xN - xS, t);
+    const float lap = fmaf(-4.0f, xc, (xE + xW) + (xN + xS));
+    const float g = fmaf(cA, t, fmaf(cD, lap, xc));
+    out[c] = SECOND ? 0.5f * (u[c] + g) : g;
+}
+
 // max over the grid of |v1| + |v2| (non-negative floats order like their bit patterns)
 __global__ void k_dns_vmax(int nf, const float *psi, float ax, unsigned *out)
 {
@@ -378,20 +428,21 @@ size_t macro_scratch_bytes(int N, int precision, int nsteps)
     return 4 * NN * rs + 256 + (size_t)(nsteps + 1) * nblocks * sizeof(double);
 }
 
-template <typename real>
+template <typename real, bool DIR>
 static cudaError_t macro_run_t(int N, real *U, const double *K, double dt, int nsteps,
-                               double *mass, void *scratch, cudaStream_t s)
+                               double *mass, void *scratch, cudaStream_t s, double ul, double ur)
 {
     const int NN = N * N;
     const double H = 2.0 * kPi / N;
     if (N <= 64) {
         const size_t smem = 5 * (size_t)NN * sizeof(real);
-        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_macro_resident<real>),
+        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_macro_resident<real, DIR>),
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int threads = NN >= 1024 ? 1024 : ((NN + 31) / 32) * 32;
         count_launches(1);
-        k_macro_resident<real><<<1, threads, smem, s>>>(N, U, K, (real)dt, nsteps, mass);
+        k_macro_resident<real, DIR><<<1, threads, smem, s>>>(N, U, K, (real)dt, nsteps, mass,
+                                                             (real)ul, (real)ur);
         return cudaGetLastError();
     }
     real *Us = static_cast<real *>(scratch);
@@ -399,13 +450,16 @@ static cudaError_t macro_run_t(int N, real *U, const double *K, double dt, int n
     const int th = 256, nb = (NN + th - 1) / th;
     double *part = reinterpret_cast<double *>(
         (reinterpret_cast<uintptr_t>(K22 + NN) + 255) & ~(uintptr_t)255);
-    count_launches(1 + 2 * (long long)nsteps + (mass ? 2 : 0));
+    count_launches(1 + 2 * (long long)nsteps + (mass ? 2 : 0) + (DIR ? 1 : 0));
     k_split_K<real><<<nb, th, 0, s>>>(NN, K, K11, K12, K22);
+    if (DIR) k_set_col0<real><<<(N + 255) / 256, 256, 0, s>>>(N, U, (real)ul);
     if (mass) k_mass_part<real><<<nb, th, 0, s>>>(NN, U, part);
     for (int st = 1; st <= nsteps; ++st) {
-        k_macro_stage<real, false><<<nb, th, 0, s>>>(N, U, Us, K11, K12, K22, (real)dt, nullptr);
-        k_macro_stage<real, true><<<nb, th, 0, s>>>(N, U, Us, K11, K12, K22, (real)dt,
-                                                    mass ? part + (size_t)st * nb : nullptr);
+        k_macro_stage<real, false, DIR><<<nb, th, 0, s>>>(N, U, Us, K11, K12, K22, (real)dt, nullptr,
+                                                          (real)ur);
+        k_macro_stage<real, true, DIR><<<nb, th, 0, s>>>(N, U, Us, K11, K12, K22, (real)dt,
+                                                         mass ? part + (size_t)st * nb : nullptr,
+                                                         (real)ur);
     }
     if (mass) k_mass_final<<<(nsteps + 1 + 127) / 128, 128, 0, s>>>(nsteps + 1, nb, part, H * H, mass);
     return cudaGetLastError();
@@ -415,8 +469,21 @@ cudaError_t macro_run(int N, void *U, int precision, const double *K, double dt,
                       double *mass_dev, void *scratch, cudaStream_t s)
 {
     if (precision == MLSD_FP64)
-        return macro_run_t<double>(N, static_cast<double *>(U), K, dt, nsteps, mass_dev, scratch, s);
-    return macro_run_t<float>(N, static_cast<float *>(U), K, dt, nsteps, mass_dev, scratch, s);
+        return macro_run_t<double, false>(N, static_cast<double *>(U), K, dt, nsteps, mass_dev,
+                                          scratch, s, 0.0, 0.0);
+    return macro_run_t<float, false>(N, static_cast<float *>(U), K, dt, nsteps, mass_dev, scratch,
+                                     s, 0.0, 0.0);
+}
+
+cudaError_t macro_run_dirichlet(int N, void *U, int precision, const double *K, double dt,
+                                int nsteps, double ul, double ur, double *mass_dev, void *scratch,
+                                cudaStream_t s)
+{
+    if (precision == MLSD_FP64)
+        return macro_run_t<double, true>(N, static_cast<double *>(U), K, dt, nsteps, mass_dev,
+                                         scratch, s, ul, ur);
+    return macro_run_t<float, true>(N, static_cast<float *>(U), K, dt, nsteps, mass_dev, scratch,
+                                    s, ul, ur);
 }
 
 cudaError_t macro_dt_max(int N, const double *K, double *max_dev, cudaStream_t s)
@@ -488,6 +555,25 @@ cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kap
     }
     if (a != u)
         return cudaMemcpyAsync(u, a, (size_t)nf * nf * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError();
+}
+
+cudaError_t dns_run_dirichlet(int nf, float *u, float *u_tmp, const float *psi, double kappa,
+                              double dt, int nsteps, double ul, double ur, cudaStream_t s)
+{
+    const double h = 2.0 * kPi / nf;
+    const float cA = (float)(dt / (4.0 * h * h));
+    const float cD = (float)(dt * kappa / (h * h));
+    const long long n2 = (long long)nf * nf;
+    const unsigned nb = (unsigned)((n2 + 255) / 256);
+    count_launches(1 + 2 * (long long)nsteps);
+    k_set_col0<float><<<(nf + 255) / 256, 256, 0, s>>>(nf, u, (float)ul);
+    for (int st = 0; st < nsteps; ++st) {
+        k_dns_dir_stage<false><<<nb, 256, 0, s>>>(nf, u, nullptr, psi, u_tmp, cA, cD, (float)ul,
+                                                  (float)ur);
+        // stage 2 writes u in place: each node reads only its own u
+        k_dns_dir_stage<true><<<nb, 256, 0, s>>>(nf, u, u_tmp, psi, u, cA, cD, (float)ul, (float)ur);
+    }
     return cudaGetLastError();
 }
 

@@ -107,6 +107,11 @@ cudaError_t launch_patch_vmax(const double *v1, const double *v2, long long Nr, 
 // Macro solver and direct simulation.
 cudaError_t macro_run(int N, void *U, int precision, const double *K, double dt, int nsteps,
                       double *mass_dev, void *scratch, cudaStream_t s);
+cudaError_t macro_run_dirichlet(int N, void *U, int precision, const double *K, double dt,
+                                int nsteps, double ul, double ur, double *mass_dev, void *scratch,
+                                cudaStream_t s);
+cudaError_t dns_run_dirichlet(int nf, float *u, float *u_tmp, const float *psi, double kappa,
+                              double dt, int nsteps, double ul, double ur, cudaStream_t s);
 size_t macro_scratch_bytes(int N, int precision, int nsteps);
 cudaError_t macro_dt_max(int N, const double *K, double *max_dev, cudaStream_t s);
 

@@ -885,6 +885,31 @@ int mlsd_macro_step(int n_macro, void *U_dev, int precision, const double *K_dev
     return MLSD_OK;
 }
 
+int mlsd_macro_step_dirichlet(int n_macro, void *U_dev, int precision, const double *K_dev,
+                              double dt, int nsteps, double u_left, double u_right,
+                              double *mass_out_host, void *cuda_stream)
+{
+    if (n_macro < 2 || !U_dev || !K_dev || !(dt > 0) || nsteps < 0) return MLSD_EINVAL;
+    if (precision != MLSD_FP32 && precision != MLSD_FP64) return MLSD_EINVAL;
+    if (!std::isfinite(u_left) || !std::isfinite(u_right)) return MLSD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t sb = macro_scratch_bytes(n_macro, precision, nsteps);
+    const size_t mb = mass_out_host ? (size_t)(nsteps + 1) * sizeof(double) : 0;
+    void *scratch = nullptr;
+    if (sb + mb) CK(cudaMallocAsync(&scratch, sb + mb + 256, s));
+    double *mass = mass_out_host
+        ? reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(scratch) + sb + 255) & ~(uintptr_t)255)
+        : nullptr;
+    cudaError_t e = macro_run_dirichlet(n_macro, U_dev, precision, K_dev, dt, nsteps, u_left,
+                                        u_right, mass, scratch, s);
+    if (e == cudaSuccess && mass_out_host)
+        e = cudaMemcpyAsync(mass_out_host, mass, mb, cudaMemcpyDeviceToHost, s);
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess && mass_out_host) e = cudaStreamSynchronize(s);
+    CK(e);
+    return MLSD_OK;
+}
+
 int mlsd_macro_dt(int n_macro, const double *K_dev, double cfl, double *dt_out_host,
                   void *cuda_stream)
 {
@@ -935,6 +960,18 @@ int mlsd_dns_run(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev, d
         return MLSD_EINVAL;
     CK(dns_run(nf, u_dev, u_tmp_dev, psi_dev, kappa, dt, nsteps,
                static_cast<cudaStream_t>(cuda_stream)));
+    return MLSD_OK;
+}
+
+int mlsd_dns_run_dirichlet(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev,
+                           double kappa, double dt, int nsteps, double u_left, double u_right,
+                           void *cuda_stream)
+{
+    if (nf < 4 || !u_dev || !u_tmp_dev || !psi_dev || u_dev == u_tmp_dev || !(kappa >= 0) ||
+        !(dt > 0) || nsteps < 0 || !std::isfinite(u_left) || !std::isfinite(u_right))
+        return MLSD_EINVAL;
+    CK(dns_run_dirichlet(nf, u_dev, u_tmp_dev, psi_dev, kappa, dt, nsteps, u_left, u_right,
+                         static_cast<cudaStream_t>(cuda_stream)));
     return MLSD_OK;
 }
 
