@@ -354,6 +354,18 @@ int mlsd_surrogate_fallbacks(mlsd_levels *h, int level, int64_t *n_out);
  * device since the last call (MLSD_ENONFINITE ...), then clear it.          */
 int mlsd_status(mlsd_levels *h, void *cuda_stream);
 
+/* Failure-path check of the library's bounded device waits (failure
+ * detection; the paper has no counterpart).  Launches one CTA on the stream
+ * that waits on an mbarrier which never receives an arrival, with nothing
+ * else in flight:
+ *   which = 0: the wait of the cluster-split patch kernels' slab exchanges;
+ *   which = 1: the wait of the tensor-core inference kernels.
+ * Each wait gives up after about a second of SM clocks and latches
+ * MLSD_ETIMEOUT in the handle's status word, exactly as on a real failure;
+ * mlsd_status then reports it (and clears it), and the context stays usable.
+ * Returns MLSD_OK once launched; MLSD_EINVAL for another `which`.           */
+int mlsd_check_wait_timeout(mlsd_levels *h, int which, void *cuda_stream);
+
 /* Macro solver for Eq. (homo), U_t = div(K grad U), HMM step 4: conservative
  * flux form on the periodic N x N grid with face tensors
  * K_f = (K_node + K_neighbour)/2 (full tensor, 9-point), Heun's RK2.

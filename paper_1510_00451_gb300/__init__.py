@@ -27,7 +27,7 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_macro_dt", "mlsd_grid_psi", "mlsd_dns_run", "mlsd_coarse_grain",
             "mlsd_level_work", "mlsd_corrector_energy", "mlsd_launch_count", "mlsd_profile", "mlsd_profile_collect",
             "mlsd_coarse_grain_noalloc", "mlsd_dns_dt", "mlsd_patch_sizes",
-            "mlsd_macro_step_dirichlet", "mlsd_dns_run_dirichlet",
+            "mlsd_macro_step_dirichlet", "mlsd_dns_run_dirichlet", "mlsd_check_wait_timeout",
             "mlsd_surrogate_param_count", "mlsd_surrogate_create", "mlsd_surrogate_free",
             "mlsd_surrogate_set_params", "mlsd_surrogate_get_params", "mlsd_surrogate_features",
             "mlsd_surrogate_grad", "mlsd_surrogate_train_step", "mlsd_surrogate_predict",
@@ -94,6 +94,7 @@ _lib.mlsd_patch_sizes.argtypes = [_P, _I, _P]
 _lib.mlsd_dns_dt.argtypes = [_I, _P, _D, _D, ctypes.POINTER(_D), _P]
 _lib.mlsd_macro_step_dirichlet.argtypes = [_I, _P, _I, _P, _D, _I, _D, _D, _P, _P]
 _lib.mlsd_dns_run_dirichlet.argtypes = [_I, _P, _P, _P, _D, _D, _I, _D, _D, _P]
+_lib.mlsd_check_wait_timeout.argtypes = [_P, _I, _P]
 _lib.mlsd_coarse_grain_noalloc.argtypes = [_I, _P, _I, _P, _P, _P]
 _lib.mlsd_surrogate_param_count.argtypes = [_I]
 _lib.mlsd_surrogate_param_count.restype = _L

@@ -29,7 +29,7 @@ constexpr int TM = 128;                // rows per tile (MMA M)
 constexpr int KC = 64;                 // K chunk staged per round
 constexpr int HMAX = 256;              // hidden width supported by this kernel
 constexpr unsigned TMEM_COLS = 256;
-constexpr long long kWaitLimit = 1ll << 24;
+constexpr long long kWaitClocks = 1ll << 31;   // about a second of SM clocks
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -70,10 +70,12 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
                  :: "r"(mbar) : "memory");
 }
 
-// bounded wait for the mbarrier phase with the given parity; false on timeout
+// bounded wait for the mbarrier phase with the given parity; false once about
+// a second of SM clocks has passed without the phase completing
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
 {
-    for (long long it = 0; it < kWaitLimit; ++it) {
+    const long long t0 = clock64();
+    for (;;) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -81,8 +83,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
             "selp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
         if (ok) return true;
+        if (clock64() - t0 > kWaitClocks) return false;
     }
-    return false;
 }
 
 // 32 consecutive FP32 columns of this warp's 32 TMEM lanes, one wait for all
@@ -493,6 +495,23 @@ bool encode_view(CUtensorMap *m, const void *base, long long rows, int K, int bo
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Failure-path check of mbar_wait: one thread waits on a fresh mbarrier that
+// receives no arrival (no copy or MMA is in flight), so the wait expires and
+// the kernel latches MLSD_ETIMEOUT the way the inference kernels do.
+__global__ void k_wait_check_mbar(int *status)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t mb = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(mb, 0)) atomicCAS(status, 0, MLSD_ETIMEOUT);
+    __syncthreads();
+    if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(mb) : "memory");
+}
+
 }  // namespace
 
 // Host: tensor maps of every member's weights; false when TMA views are unavailable.
@@ -514,6 +533,13 @@ bool mlp_tma_prepare(int h, int members, void *const *wb_host, void *maps_out)
 }
 
 size_t mlp_tma_maps_bytes() { return sizeof(CUtensorMap) * 16; }
+
+cudaError_t launch_wait_check_mbar(int *status, cudaStream_t s)
+{
+    count_launches(1);
+    k_wait_check_mbar<<<1, 32, 0, s>>>(status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mlp_tma(const void *X, long long M, int h, int members, const void *maps,
                            const float *const *wf_dev, float *out, int *status, cudaStream_t s)

@@ -104,6 +104,11 @@ cudaError_t launch_patch_vmax(const double *v1, const double *v2, long long Nr, 
                               int n_macro, long long P, double *vmax, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// Failure-path checks of the two bounded device waits (nothing in flight).
+cudaError_t launch_wait_check_nbr(int *status, cudaStream_t s);
+cudaError_t launch_wait_check_mbar(int *status, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // Macro solver and direct simulation.
 cudaError_t macro_run(int N, void *U, int precision, const double *K, double dt, int nsteps,
                       double *mass_dev, void *scratch, cudaStream_t s);

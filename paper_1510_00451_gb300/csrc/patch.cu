@@ -306,12 +306,20 @@ struct Tile {
     // (mbarrier `mbar` of this buffer, phase `parity`) for the two halo rows
     // that come from the neighbouring slabs; only the threads on the slab's
     // first and last block rows wait for those.
+    //
+    // SYNC = 2, 3 after a timeout: `live` (per thread) turns false when this
+    // thread's wait runs out; the thread then waits no more, and thread 0 stops
+    // re-arming the barriers and issuing bulk copies.  The neighbours' waits run
+    // out in turn (at once, once the status word holds MLSD_ETIMEOUT), so every
+    // rank finishes its remaining steps without waiting and the ranks meet at the
+    // cluster barriers after the loop.
     template <int J, bool SECOND, int SYNC = 0>
     __device__ __forceinline__ static void stage(real *sm, int buf, int rank, int tx, int ty,
                                                  const real (&x)[BY][BX], real (&out)[BY][BX],
                                                  const real (&aE)[BY][BX], const real (&aN)[BY][BX],
                                                  const Coef<real> &k, uint32_t mbar = 0,
-                                                 uint32_t parity = 0, int *status = nullptr)
+                                                 uint32_t parity = 0, int *status = nullptr,
+                                                 bool *live = nullptr)
     {
         publish_edges<SYNC != 3>(sm, buf, rank, tx, ty, x);
         if constexpr (SYNC == 3 && C > 1) {
@@ -323,7 +331,7 @@ struct Tile {
             // receivers wait for them before they send the next stage's rows.
             if (ty == 0 || ty == NBY - 1) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
-            if (tx == 0 && ty == 0) {
+            if (tx == 0 && ty == 0 && *live) {
                 real *rowT = sm + buf * S::STAGE, *rowB = rowT + S::ROW;
                 real *HS = rowB + S::ROW + 2 * S::COL, *HN = HS + N;
                 const uint32_t bytes = (uint32_t)(N * sizeof(real));
@@ -333,17 +341,24 @@ struct Tile {
                 bulk_to_rank((uint32_t)__cvta_generic_to_shared(HN),
                              (uint32_t)__cvta_generic_to_shared(rowT), bytes, mbar, (rank + C - 1) % C);
             }
-            if (ty == 0 || ty == NBY - 1) {
-                if (!nbr_wait(mbar, parity, status)) atomicCAS(status, 0, MLSD_ETIMEOUT);
-                // thread 0 re-arms this buffer's barrier for its next phase
-                if (tx == 0 && ty == 0) arm_tx(mbar, (uint32_t)(2 * N * sizeof(real)));
+            if ((ty == 0 || ty == NBY - 1) && *live) {
+                if (!nbr_wait(mbar, parity, status)) {
+                    *live = false;
+                    atomicCAS(status, 0, MLSD_ETIMEOUT);
+                } else if (tx == 0 && ty == 0) {
+                    // the phase completed: thread 0 re-arms this buffer's barrier
+                    arm_tx(mbar, (uint32_t)(2 * N * sizeof(real)));
+                }
             }
         } else if constexpr (SYNC == 2 && C > 1) {
             if (ty == NBY - 1) nbr_arrive(mbar, (rank + 1) % C);       // its HS slot
             if (ty == 0) nbr_arrive(mbar, (rank + C - 1) % C);         // its HN slot
             __syncthreads();
-            if (ty == 0 || ty == NBY - 1)
-                if (!nbr_wait(mbar, parity, status)) atomicCAS(status, 0, MLSD_ETIMEOUT);
+            if ((ty == 0 || ty == NBY - 1) && *live)
+                if (!nbr_wait(mbar, parity, status)) {
+                    *live = false;
+                    atomicCAS(status, 0, MLSD_ETIMEOUT);
+                }
         } else {
             tile_sync<C>();
         }
@@ -756,6 +771,7 @@ struct Tile {
         // flux sums: sum (A_i + b_ii) w = sum A_i w + b_ii sum w, so sum w is kept too
         real p1 = 0, p2 = 0, pw = 0;
         int win = 0;
+        bool live = true;                               // SYNC = 2, 3: no wait has run out
         const long long ntot = nb + na;
         if constexpr (SPLIT) {
             publish_edges(sm, 0, rank, tx, ty, w);
@@ -767,8 +783,10 @@ struct Tile {
                 stage_split<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, k);
             } else if constexpr (SYNC >= 2) {
                 const uint32_t par = (uint32_t)(step & 1);
-                stage<J, false, SYNC>(sm, 0, rank, tx, ty, w, s, A1, A2, k, mbar0, par, prm.status);
-                stage<J, true, SYNC>(sm, 1, rank, tx, ty, s, w, A1, A2, k, mbar0 + 8, par, prm.status);
+                stage<J, false, SYNC>(sm, 0, rank, tx, ty, w, s, A1, A2, k, mbar0, par, prm.status,
+                                      &live);
+                stage<J, true, SYNC>(sm, 1, rank, tx, ty, s, w, A1, A2, k, mbar0 + 8, par,
+                                     prm.status, &live);
             } else {
                 stage<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, k);
                 stage<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, k);
@@ -1199,6 +1217,24 @@ void add_variant2(std::vector<PatchVariant> &out)
     out.push_back(v);
 }
 
+// Failure-path check of nbr_wait (the cluster exchanges' bounded wait): one
+// thread waits on a fresh mbarrier that receives no arrival and nothing else
+// is in flight, so the wait expires and MLSD_ETIMEOUT is latched as in the
+// patch kernels.
+__global__ void k_wait_check_nbr(int *status)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !nbr_wait(mb, 0, status)) atomicCAS(status, 0, MLSD_ETIMEOUT);
+    __syncthreads();
+    if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(mb) : "memory");
+}
+
 __global__ void k_compose(long long P, const double *B, const double *S, double *K, int *status)
 {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1214,6 +1250,13 @@ __global__ void k_compose(long long P, const double *B, const double *S, double 
 }
 
 }  // namespace
+
+cudaError_t launch_wait_check_nbr(int *status, cudaStream_t s)
+{
+    count_launches(1);
+    k_wait_check_nbr<<<1, 32, 0, s>>>(status);
+    return cudaGetLastError();
+}
 
 int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
 {

@@ -804,6 +804,14 @@ int mlsd_status(mlsd_levels *h, void *cuda_stream)
     return v;
 }
 
+int mlsd_check_wait_timeout(mlsd_levels *h, int which, void *cuda_stream)
+{
+    if (!h || (which != 0 && which != 1)) return MLSD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    CK(which == 0 ? launch_wait_check_nbr(h->status, s) : launch_wait_check_mbar(h->status, s));
+    return MLSD_OK;
+}
+
 int mlsd_corrector_energy(mlsd_levels *h, int level, const double *K_base_dev, const void *w_dump_dev,
                           double *E_out_dev, double *mass_out_dev, void *cuda_stream)
 {
