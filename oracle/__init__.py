@@ -66,6 +66,8 @@ def _declare(L):
     L.orc_coarse_grain.argtypes = [_i, _p, _i, _p, _p]
     L.orc_num_threads.restype = _i
     L.orc_features.argtypes = [_i, _p, _p, _d, _p]
+    L.orc_series.argtypes = [_i, _d, _p, _p, _i, _p]
+    L.orc_series_estimate.argtypes = [_p, _p, _p]
     L.orc_mlp.argtypes = [_i, _i, _i, _p, _p, _i, _p, _p, _p]
     L.orc_mlp.restype = _d
 
@@ -304,27 +306,46 @@ def coarse_grain(u, N):
     return U, m.value
 
 
-N_FEATURES = 585
-PSI_SCALE, Q_SCALE, Y_SCALE = 32.0, 10.0, 30.0
+N_FEATURES = 603
+PSI_SCALE, T_SCALE, Y_SCALE, Y_CLAMP = 32.0, 10.0, 300.0, 3.0
 
 
 def features(psi, B, kappa):
-    """585 surrogate inputs of one patch (psi with its patch mean removed)."""
+    """603 surrogate inputs of one patch (psi with its patch mean removed)."""
     psi = _f64(psi); B = _f64(B)
     f = np.zeros(N_FEATURES)
     lib().orc_features(psi.shape[0], _ptr(psi), _ptr(B), float(kappa), _ptr(f))
     return f
 
 
-def second_order_K(f, B):
-    """Q (the second-order estimate of K - B that features 582..584 carry) in the
-    units of K, from a feature row and the base tensor."""
-    return np.asarray(f[582:585]) * (B[0] + B[2]) / Q_SCALE
+def series(psi, B, M=6, h=None):
+    """Perturbation moments T_2..T_M of the steady corrector equation: [M-1][3]
+    (components 11, 12, 22); sum_m T_m = K - B where the series converges."""
+    psi = _f64(psi); B = _f64(B)
+    n = psi.shape[0]
+    T = np.zeros((M - 1, 3))
+    lib().orc_series(n, float(2 * np.pi / n if h is None else h), _ptr(psi), _ptr(B), int(M),
+                     _ptr(T))
+    return T
 
 
-def surrogate_K(out, f, B):
-    """K of one patch from a network output (the target (K - B - Q) 30 / tr B)."""
-    return np.asarray(B) + second_order_K(f, B) + (B[0] + B[2]) * np.asarray(out) / Y_SCALE
+def series_estimate(T):
+    """(E, S6): the resummed estimate of K - B and the partial sum, from T_2..T_6."""
+    T = _f64(T)
+    E = np.zeros(3); S6 = np.zeros(3)
+    lib().orc_series_estimate(_ptr(T), _ptr(E), _ptr(S6))
+    return E, S6
+
+
+def surrogate_target(K, B, E):
+    """Training target of one patch: clamp((K - B - E) Y_SCALE / tr B, -Y_CLAMP, Y_CLAMP)."""
+    y = (np.asarray(K) - np.asarray(B) - np.asarray(E)) * Y_SCALE / (B[0] + B[2])
+    return np.clip(y, -Y_CLAMP, Y_CLAMP)
+
+
+def surrogate_K(out, E, B):
+    """K of one patch from a network output and the resummed series estimate E."""
+    return np.asarray(B) + np.asarray(E) + (B[0] + B[2]) * np.asarray(out) / Y_SCALE
 
 
 def mlp_param_count(d0, h):

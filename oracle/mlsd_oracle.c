@@ -819,35 +819,148 @@ int orc_num_threads(void)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Perturbation moments of the steady corrector equation (used by the        */
+/* learned surrogate; not in the paper).                                     */
+/*                                                                           */
+/* At steady state the corrector of field j solves (L0 + A) w_j = -v_j with   */
+/* L0 = B11 D+D-x + 2 B12 D0x D0y + B22 D+D-y (Fourier symbol -D(k)/h^2,      */
+/* D = B11 (2 - 2 cos t1) + B22 (2 - 2 cos t2) + 2 B12 sin t1 sin t2,        */
+/* t_i = 2 pi k_i / n) and A w = v1 D0x w + v2 D0y w.  Expanding in v:         */
+/*   c_j^0 = -L0^{-1} v_j,  c_j^m = -L0^{-1} A c_j^{m-1},  w_j = sum_m c_j^m,  */
+/* so K - B = sum_{m>=2} T_m with T_m = sym <v_i c_j^{m-2}> (mean over the    */
+/* cells): T_2 is the small-Peclet limit, T_m is of order v^m.  L0^{-1} is a */
+/* division of the DFT by -D/h^2 (the zero mode, where the source has no      */
+/* component, set to zero).  The DFT is written out below (separable, plain  */
+/* sums); the operators are the patch problem's own (orc_velocity and the    */
+/* central differences of Sec. 2.1).                                          */
+/* ------------------------------------------------------------------------ */
+static void dft2(int n, const double *fr, const double *fi, double *gr, double *gi, int sgn)
+{
+    double *tr = malloc(sizeof(double) * n * n), *ti = malloc(sizeof(double) * n * n);
+    for (int b = 0; b < n; ++b)
+        for (int k = 0; k < n; ++k) {
+            double sr = 0.0, si = 0.0;
+            for (int a = 0; a < n; ++a) {
+                double th = sgn * 2.0 * ORC_PI * (double)(((long)k * a) % n) / n;
+                double c = cos(th), s = sin(th);
+                sr += fr[b * n + a] * c - fi[b * n + a] * s;
+                si += fr[b * n + a] * s + fi[b * n + a] * c;
+            }
+            tr[b * n + k] = sr; ti[b * n + k] = si;
+        }
+    for (int k2 = 0; k2 < n; ++k2)
+        for (int k1 = 0; k1 < n; ++k1) {
+            double sr = 0.0, si = 0.0;
+            for (int b = 0; b < n; ++b) {
+                double th = sgn * 2.0 * ORC_PI * (double)(((long)k2 * b) % n) / n;
+                double c = cos(th), s = sin(th);
+                sr += tr[b * n + k1] * c - ti[b * n + k1] * s;
+                si += tr[b * n + k1] * s + ti[b * n + k1] * c;
+            }
+            gr[k2 * n + k1] = sr; gi[k2 * n + k1] = si;
+        }
+    free(tr); free(ti);
+}
+
+/* out = -L0^{-1} f for a real field f (mean of f ignored) */
+static void neg_l0_inverse(int n, double h, const double *B, const double *f, double *out)
+{
+    long nn = (long)n * n;
+    double *zr = calloc(nn, sizeof(double)), *Fr = malloc(sizeof(double) * nn),
+           *Fi = malloc(sizeof(double) * nn), *gi = malloc(sizeof(double) * nn);
+    dft2(n, f, zr, Fr, Fi, -1);
+    for (int k2 = 0; k2 < n; ++k2)
+        for (int k1 = 0; k1 < n; ++k1) {
+            long c = (long)k2 * n + k1;
+            if (k1 == 0 && k2 == 0) { Fr[c] = Fi[c] = 0.0; continue; }
+            double t1 = 2.0 * ORC_PI * k1 / n, t2 = 2.0 * ORC_PI * k2 / n;
+            double D = B[0] * (2.0 - 2.0 * cos(t1)) + B[2] * (2.0 - 2.0 * cos(t2))
+                     + 2.0 * B[1] * sin(t1) * sin(t2);
+            Fr[c] *= h * h / D; Fi[c] *= h * h / D;
+        }
+    dft2(n, Fr, Fi, out, gi, +1);
+    for (long c = 0; c < nn; ++c) out[c] /= (double)nn;
+    free(zr); free(Fr); free(Fi); free(gi);
+}
+
+/* T[(m-2)*3 + (0,1,2)] = (T_m11, T_m12, T_m22) for m = 2..M */
+void orc_series(int n, double h, const double *psi, const double *B, int M, double *T)
+{
+    long nn = (long)n * n;
+    double *v1 = malloc(sizeof(double) * nn), *v2 = malloc(sizeof(double) * nn);
+    double *c1 = malloc(sizeof(double) * nn), *c2 = malloc(sizeof(double) * nn);
+    double *Ac = malloc(sizeof(double) * nn);
+    orc_velocity(n, h, psi, v1, v2);
+    neg_l0_inverse(n, h, B, v1, c1);
+    neg_l0_inverse(n, h, B, v2, c2);
+    for (int m = 2; m <= M; ++m) {
+        double s11 = 0.0, s12 = 0.0, s21 = 0.0, s22 = 0.0;
+        for (long c = 0; c < nn; ++c) {
+            s11 += v1[c] * c1[c]; s12 += v1[c] * c2[c];
+            s21 += v2[c] * c1[c]; s22 += v2[c] * c2[c];
+        }
+        T[(m - 2) * 3 + 0] = s11 / nn;
+        T[(m - 2) * 3 + 1] = 0.5 * (s12 + s21) / nn;
+        T[(m - 2) * 3 + 2] = s22 / nn;
+        if (m == M) break;
+        for (int j = 0; j < 2; ++j) {
+            double *cj = j == 0 ? c1 : c2;
+            for (int b = 0; b < n; ++b)
+                for (int a = 0; a < n; ++a) {
+                    int ap = (a + 1) % n, am = (a + n - 1) % n, bp = (b + 1) % n, bm = (b + n - 1) % n;
+                    double dx = (cj[b * n + ap] - cj[b * n + am]) / (2.0 * h);
+                    double dy = (cj[bp * n + a] - cj[bm * n + a]) / (2.0 * h);
+                    Ac[b * n + a] = v1[b * n + a] * dx + v2[b * n + a] * dy;
+                }
+            neg_l0_inverse(n, h, B, Ac, cj);
+        }
+    }
+    free(v1); free(v2); free(c1); free(c2); free(Ac);
+}
+
+/* Resummation of the series per component from T_2..T_6 (odd terms added     */
+/* as they are): the partial sum S6 = T_2 + ... + T_6, and the estimate        */
+/*   E = T_2 + T_3 + T_5 + T_4 / (1 - rho),  rho = clamp(T_6 / T_4, -1/2, 4/5) */
+/* (rho = 0 where T_4 = 0).  In the even terms the series is close to         */
+/* geometric, T_6 ~ rho T_4, and T_4 / (1 - rho) sums that tail (the Shanks   */
+/* transform of the partial sums S_2, S_4, S_6); the clamp keeps E finite and */
+/* continuous where the series does not converge.                             */
+void orc_series_estimate(const double *T, double *E, double *S6)
+{
+    for (int c = 0; c < 3; ++c) {
+        double t2 = T[c], t3 = T[3 + c], t4 = T[6 + c], t5 = T[9 + c], t6 = T[12 + c];
+        double rho = fabs(t4) > 1e-300 ? t6 / t4 : 0.0;
+        if (rho < -0.5) rho = -0.5;
+        if (rho > 0.8) rho = 0.8;
+        E[c] = t2 + t3 + t5 + t4 / (1.0 - rho);
+        S6[c] = t2 + t3 + t4 + t5 + t6;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Learned surrogate of the patch solve (not in the paper; the library's     */
 /* estimator it is checked against is orc_patch_k).                          */
 /*                                                                           */
-/* Features of a patch (585 values):                                         */
+/* Features of a patch (603 values):                                         */
 /*   [0, 578): Re and Im of psihat(k) = n^-2 sum_ab psi[b][a]               */
 /*             exp(-2 pi i (k1 a + k2 b) / n) for k2 = -8..8 (slow),         */
 /*             k1 = -8..8 (fast), each times 32 / (tr(B)/2) (a Peclet        */
 /*             scale, brought to order one); psi is the patch's band with    */
 /*             the patch mean removed                                        */
 /*   578..580: B11/kappa, B12/kappa, B22/kappa;  581: log(kappa)             */
-/*   582..584: 10 Q / tr(B) for (Q11, Q12, Q22), the second-order (small     */
-/*             Peclet) solution of the discrete corrector equation on the    */
-/*             same 17 x 17 window of modes:                                 */
-/*               Q = sum_{k != 0} |psihat(k)|^2 M(k) / D(k),                 */
-/*               M = [[s2^2, -s1 s2], [-s1 s2, s1^2]],                       */
-/*               D = B11 (2 - 2 cos t1) + B22 (2 - 2 cos t2) + 2 B12 s1 s2,  */
-/*             t_i = 2 pi k_i / n, s_i = sin t_i.  (To first order in v the  */
-/*             corrector solves B:D D w_j = -v_j; with v1 = -D0y psi,        */
-/*             v2 = D0x psi the Fourier symbols are -D/h^2 for B:D D and     */
-/*             i s_i / h for D0, and sum_k Re(vhat_i conj(what_j)) is Q.)    */
-/* Target: (K - B - Q) 30 / tr(B) for the three components (K11, K12, K22).  */
+/*   582..596: asinh(10 T_m / tr B) for m = 2..6 (components 11, 12, 22)     */
+/*   597..599: asinh(10 S6 / tr B);  600..602: asinh(10 E / tr B)            */
+/*   (the perturbation moments, the partial sum and the resummed estimate    */
+/*   of orc_series / orc_series_estimate; asinh keeps the diverging series   */
+/*   of high-Peclet patches at a usable scale).                              */
+/* Target: clamp((K - B - E) 300 / tr(B), -3, 3) per component; the         */
+/* surrogate's K is B + E + tr(B) out / 300.                                  */
 /* ------------------------------------------------------------------------ */
-#define ORC_NF 585
 #define ORC_PSI_SCALE 32.0
-#define ORC_Q_SCALE 10.0
+#define ORC_T_SCALE 10.0
 void orc_features(int n, const double *psi, const double *B, double kappa, double *f)
 {
     const double trh = 0.5 * (B[0] + B[2]);
-    double Q11 = 0.0, Q12 = 0.0, Q22 = 0.0;
     int t = 0;
     for (int k2 = -8; k2 <= 8; ++k2)
         for (int k1 = -8; k1 <= 8; ++k1) {
@@ -863,24 +976,18 @@ void orc_features(int n, const double *psi, const double *B, double kappa, doubl
             si /= (double)n * n;
             f[t++] = sr * ORC_PSI_SCALE / trh;
             f[t++] = si * ORC_PSI_SCALE / trh;
-            if (k1 != 0 || k2 != 0) {
-                const double t1 = 2.0 * ORC_PI * k1 / n, t2 = 2.0 * ORC_PI * k2 / n;
-                const double s1 = sin(t1), s2 = sin(t2);
-                const double D = B[0] * (2.0 - 2.0 * cos(t1)) + B[2] * (2.0 - 2.0 * cos(t2))
-                                 + 2.0 * B[1] * s1 * s2;
-                const double pw = sr * sr + si * si;
-                Q11 += pw * s2 * s2 / D;
-                Q12 -= pw * s1 * s2 / D;
-                Q22 += pw * s1 * s1 / D;
-            }
         }
     f[t++] = B[0] / kappa;
     f[t++] = B[1] / kappa;
     f[t++] = B[2] / kappa;
     f[t++] = log(kappa);
-    f[t++] = ORC_Q_SCALE * Q11 / (2.0 * trh);
-    f[t++] = ORC_Q_SCALE * Q12 / (2.0 * trh);
-    f[t++] = ORC_Q_SCALE * Q22 / (2.0 * trh);
+    double T[15], E[3], S6[3];
+    orc_series(n, 2.0 * ORC_PI / n, psi, B, 6, T);   /* h cancels in T: any patch side */
+    orc_series_estimate(T, E, S6);
+    const double sc = ORC_T_SCALE / (2.0 * trh);
+    for (int q = 0; q < 15; ++q) f[t++] = asinh(sc * T[q]);
+    for (int c = 0; c < 3; ++c) f[t++] = asinh(sc * S6[c]);
+    for (int c = 0; c < 3; ++c) f[t++] = asinh(sc * E[c]);
 }
 
 /* round to bfloat16 (via float, round to nearest even); NaN-free inputs */

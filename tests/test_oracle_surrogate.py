@@ -1,8 +1,10 @@
 """Pins of the oracle's surrogate pieces: the patch features are a plain DFT
-(checked against numpy's FFT); the second-order estimate Q they carry equals
-the discrete shear closed form and the patch solve's K - B for shear flows,
-and the patch solve's K - B to O(Pe^4) for a general flow; the MLP gradient
-against central finite differences in FP64."""
+(checked against numpy's FFT); the perturbation moments T_m of the steady
+corrector equation they carry give the discrete shear closed form (T_2, with
+every higher moment zero) and, summed, the dense direct solve of the steady
+corrector for a general flow with a full-tensor base; the resummed estimate
+is the Shanks transform of the partial sums; the MLP gradient against central
+finite differences in FP64."""
 import math
 
 import numpy as np
@@ -19,7 +21,7 @@ def test_features_are_the_normalised_dft():
     psi -= psi.mean()
     B = np.array([0.3, 0.05, 0.5])
     f = oracle.features(psi, B, 0.01)
-    assert f.shape == (585,)
+    assert f.shape == (603,)
     F = np.fft.fft2(psi) / n ** 2            # F[k2][k1] = n^-2 sum psi[b][a] e^{-2pi i(k1 a + k2 b)/n}
     want = []
     for k2 in range(-8, 9):
@@ -52,51 +54,127 @@ def _steady_K(psi, h, B):
     return oracle.patch_k(psi, h, B, dt, nb, na)
 
 
+def _direct_steady_K(psi, h, B):
+    """K from a dense direct solve of the steady corrector f_j(w) = 0 with sum(w) = 0."""
+    n = psi.shape[0]
+    N = n * n
+    v1, v2 = oracle.velocity(psi, h)
+    W = []
+    for j in (1, 2):
+        src = oracle.corrector_rhs(psi, h, B, j, np.zeros((n, n))).ravel()
+        M = np.zeros((N, N))
+        for c in range(N):
+            e = np.zeros(N); e[c] = 1.0
+            M[:, c] = oracle.corrector_rhs(psi, h, B, j, e.reshape(n, n)).ravel() - src
+        A = np.vstack([M, np.ones((1, N))])
+        w = np.linalg.lstsq(A, np.concatenate([-src, [0.0]]), rcond=None)[0]
+        W.append(w.reshape(n, n))
+    S = np.array([[np.mean(v * w) for w in W] for v in (v1, v2)])
+    return np.array([B[0] + S[0, 0], B[1] + 0.5 * (S[0, 1] + S[1, 0]), B[2] + S[1, 1]])
+
+
 @pytest.mark.parametrize("k,axis", [(3, 1), (5, 2), (1, 1)])
-def test_second_order_estimate_is_exact_for_shears(k, axis):
-    # psi = a cos(2 pi k x_axis / n): the corrector of a shear solves a linear
-    # equation with no advection of w, so the first-order solution is exact;
+def test_series_of_a_shear_is_its_closed_form(k, axis):
+    # psi = a cos(2 pi k x_axis / n): the corrector of a shear is not advected
+    # (A c = 0), so T_2 is exact and every higher moment vanishes;
     # K_jj - B_jj = (a^2 / 2) cos^2(t/2) / B_ii (t = 2 pi k / n, i the shear
-    # direction, j the other), and the patch solve gives the same.
+    # direction, j the other), which the patch solve also gives
     n, a = 24, 0.07
     idx = np.arange(n)
     line = a * np.cos(2 * math.pi * k * idx / n)
     psi = line[None, :].repeat(n, 0) if axis == 1 else line[:, None].repeat(n, 1)
     B = np.array([0.031, 0.009, 0.022])
-    f = oracle.features(psi, B, 0.01)
-    Q = oracle.second_order_K(f, B)
+    T = oracle.series(psi, B)
     t = 2 * math.pi * k / n
     if axis == 1:
         want = np.array([0.0, 0.0, 0.5 * a * a * math.cos(t / 2) ** 2 / B[0]])
     else:
         want = np.array([0.5 * a * a * math.cos(t / 2) ** 2 / B[2], 0.0, 0.0])
-    np.testing.assert_allclose(Q, want, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(T[0], want, rtol=1e-12, atol=1e-15)
+    assert np.abs(T[1:]).max() < 1e-13 * np.abs(want).max()
+    E, S6 = oracle.series_estimate(T)
+    np.testing.assert_allclose(E, want, rtol=1e-12, atol=1e-15)
     h = 2 * math.pi / n
-    K = _steady_K(psi, h, B)
-    np.testing.assert_allclose(K - B, want, rtol=1e-8, atol=1e-13)
+    np.testing.assert_allclose(_steady_K(psi, h, B) - B, want, rtol=1e-8, atol=1e-13)
 
 
-def test_second_order_estimate_is_the_small_peclet_limit():
-    # a non-shear flow inside the 17 x 17 window with a full-tensor base: the
-    # patch solve's K - B equals Q up to O(Pe^4), so halving the amplitude
-    # shrinks the relative gap about fourfold (a wrong sign on the cross terms
-    # of M or D would leave an O(1) gap)
-    n = 20
+def _general_flow(n, eps):
     idx = np.arange(n)
     A, Bi = np.meshgrid(idx, idx)             # A: a (fast, x1), Bi: b (slow, x2)
     shape = (np.cos(2 * math.pi * (2 * A + 3 * Bi) / n) + 0.5 * np.sin(2 * math.pi * (A - 2 * Bi) / n)
              + 0.3 * np.cos(2 * math.pi * 4 * A / n))
+    return eps * shape
+
+
+def test_series_sums_to_the_direct_steady_solve():
+    # the moments are the terms of the Neumann series of (L0 + A) w = -v_j: for
+    # a small Peclet number, T_2 + ... + T_20 is the dense direct solve's K - B
+    n = 12
+    psi = _general_flow(n, 0.02)
+    B = np.array([0.05, 0.012, 0.035])
+    h = 2 * math.pi / n
+    Kd = _direct_steady_K(psi, h, B)
+    T = oracle.series(psi, B, M=20)
+    assert abs(T[0, 1]) > 0.05 * abs(T[0, 0])          # the cross term is exercised
+    assert np.abs(T[2]).max() > 1e-3 * np.abs(T[0]).max()  # so are the higher orders
+    np.testing.assert_allclose(B + T.sum(0), Kd, rtol=0, atol=1e-12 * np.abs(Kd - B).max())
+
+
+def test_series_truncation_error_has_the_right_order():
+    # S6 = T_2 + ... + T_6 misses the O(v^7) tail: halving the amplitude shrinks
+    # the gap to the direct solve ~2^7-fold (a wrong T_4 would leave O(v^4))
+    n = 12
     B = np.array([0.05, 0.012, 0.035])
     h = 2 * math.pi / n
     gaps = []
-    for eps in (4e-3, 2e-3):
-        psi = eps * shape
-        Q = oracle.second_order_K(oracle.features(psi, B, 0.01), B)
-        K = _steady_K(psi, h, B)
-        gaps.append(np.linalg.norm(K - B - Q) / np.linalg.norm(Q))
-        assert abs(Q[1]) > 0.05 * abs(Q[0])       # the cross term is exercised
-    assert gaps[0] < 2e-2
-    assert 3.0 < gaps[0] / gaps[1] < 5.0, gaps
+    for eps in (0.08, 0.04):
+        psi = _general_flow(n, eps)
+        Kd = _direct_steady_K(psi, h, B)
+        E, S6 = oracle.series_estimate(oracle.series(psi, B))
+        gaps.append(np.abs(B + S6 - Kd).max())
+    assert 60 < gaps[0] / gaps[1] < 300, gaps
+
+
+def test_estimate_is_the_shanks_transform_of_the_partial_sums():
+    # where the clamp is inactive, E = (S_c S_a - S_b^2) / (S_c + S_a - 2 S_b) over
+    # the even partial sums S_a = T2, S_b = T2 + T4, S_c = T2 + T4 + T6 (plus T3 + T5)
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        t = rng.standard_normal((5, 3))
+        t[2] = np.sign(t[0]) * np.abs(t[2]) * 0.3
+        t[4] = t[2] * rng.uniform(-0.45, 0.75, 3)
+        E, S6 = oracle.series_estimate(t)
+        Sa, Sb, Sc = t[0], t[0] + t[2], t[0] + t[2] + t[4]
+        shanks = (Sc * Sa - Sb * Sb) / (Sc + Sa - 2 * Sb)
+        np.testing.assert_allclose(E, shanks + t[1] + t[3], rtol=1e-12)
+        np.testing.assert_allclose(S6, t.sum(0), rtol=1e-14)
+    # and for a geometric even tail T6 = r T4, T8 = r^2 T4, ... it is the sum
+    t = np.array([[1.0, 0.1, 2.0], [0.0] * 3, [0.5, -0.02, 0.4], [0.0] * 3, [0.2, -0.008, 0.16]])
+    E, _ = oracle.series_estimate(t)
+    np.testing.assert_allclose(E, t[0] + t[2] / (1 - 0.4), rtol=1e-14)
+
+
+def test_estimate_beats_the_partial_sum_at_moderate_peclet():
+    n = 12
+    B = np.array([0.05, 0.012, 0.035])
+    h = 2 * math.pi / n
+    psi = _general_flow(n, 0.12)
+    Kd = _direct_steady_K(psi, h, B)
+    E, S6 = oracle.series_estimate(oracle.series(psi, B))
+    assert np.abs(B + E - Kd).max() < 0.5 * np.abs(B + S6 - Kd).max()
+
+
+def test_features_carry_the_series():
+    n = 16
+    psi = _general_flow(n, 0.05)
+    B = np.array([0.05, 0.012, 0.035])
+    f = oracle.features(psi, B, 0.01)
+    T = oracle.series(psi, B)
+    E, S6 = oracle.series_estimate(T)
+    sc = 10.0 / (B[0] + B[2])
+    np.testing.assert_allclose(np.sinh(f[582:597]), sc * T.ravel(), rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(np.sinh(f[597:600]), sc * S6, rtol=1e-12)
+    np.testing.assert_allclose(np.sinh(f[600:603]), sc * E, rtol=1e-12)
 
 
 def _params(d0, h, rng):
@@ -212,13 +290,14 @@ def _feature_rule(f, g):
             s = 2 * ((s2 + 8) * 17 + s1 + 8)
             out[d:d + 2] = sign * np.asarray(f)[s:s + 2]
     out[578:581] = square_symmetry_tensor(f[578:581], g)
-    out[582:585] = square_symmetry_tensor(f[582:585], g)
+    for q in range(582, 603, 3):              # T_2..T_6, S6, E: tensors under R . R^T
+        out[q:q + 3] = np.arcsinh(square_symmetry_tensor(np.sinh(np.asarray(f[q:q + 3])), g))
     return out
 
 
 @pytest.mark.parametrize("g", range(1, 8))
 def test_features_of_the_mapped_patch_follow_the_stated_rule(g):
-    # features of the mapped patch (DFT, base, second-order estimate) are the
+    # features of the mapped patch (DFT, base, series moments) are the
     # signed permutation of the patch's own features
     from tests._parity import square_symmetry_psi, square_symmetry_tensor
     n, kappa = 32, 2e-3
