@@ -53,7 +53,7 @@ def _declare(L):
     L.orc_offdiag_q.argtypes = [_i, _p, _p, _p, _p, _p, _p, _l, _l, _l, _i, _d, _p, _p]
     L.orc_offdiag_apply.argtypes = [_i, _p, _p, _p, _p]
     L.orc_chain.argtypes = [_i, _p, _p, _p, _p, _i, _p, _p, _p, _i, _d, _d, _d, _d, _l, _l,
-                            _i, _p, _p, _p, _p, _p]
+                            _i, _p, _p, _p, _p, _p, _i]
     L.orc_patch_n_rule.argtypes = [_i, _p, _p, _p, _p, _p, _l, _i, _i, _i, _d, _i, _i, _i, _p]
     L.orc_patch_n_rule.restype = _i
     L.orc_macro_dt.argtypes = [_i, _p, _d]
@@ -68,6 +68,7 @@ def _declare(L):
     L.orc_features.argtypes = [_i, _p, _p, _d, _p]
     L.orc_series.argtypes = [_i, _d, _p, _p, _i, _p]
     L.orc_series_estimate.argtypes = [_p, _p, _p]
+    L.orc_periodic_smooth.argtypes = [_i, _p, _p]
     L.orc_mlp.argtypes = [_i, _i, _i, _p, _p, _i, _p, _p, _p]
     L.orc_mlp.restype = _d
 
@@ -225,7 +226,7 @@ def patch_n_rule(spec, edges, level, node, n_macro, kappa, n_min=32, n_max=256, 
 
 def chain(spec, edges, patch_n, n_macro, kappa, nodes, cfl=0.2, t_burn=8.0, t_avg=4.0,
           n_burn_fixed=-1, n_avg_fixed=0, patch_div=None, want_levels=False, want_steps=False,
-          node_n=None):
+          node_n=None, periodize=False):
     """Algorithm 3 down the whole level hierarchy for the macro nodes (i, j) given.
 
     patch_n gives n per level; node_n (optional, [nodes][L]) overrides it per node.
@@ -246,7 +247,7 @@ def chain(spec, edges, patch_n, n_macro, kappa, nodes, cfl=0.2, t_burn=8.0, t_av
     lib().orc_chain(len(k1), _ptr(k1), _ptr(k2), _ptr(re), _ptr(im), Lc, _ptr(e), _ptr(nn),
                     _ptr(md), int(n_macro), float(kappa), float(cfl), float(t_burn), float(t_avg),
                     int(n_burn_fixed), int(n_avg_fixed), len(ni), _ptr(ni), _ptr(nj),
-                    _ptr(K), _ptr(Kl), _ptr(st))
+                    _ptr(K), _ptr(Kl), _ptr(st), 1 if periodize else 0)
     out = [K]
     if want_levels:
         out.append(Kl)
@@ -316,6 +317,14 @@ def features(psi, B, kappa):
     f = np.zeros(N_FEATURES)
     lib().orc_features(psi.shape[0], _ptr(psi), _ptr(B), float(kappa), _ptr(f))
     return f
+
+
+def periodic_smooth(u):
+    """Periodic component p of an n x n patch field (u = p + s, Moisan 2011)."""
+    u = _f64(u)
+    p = np.zeros_like(u)
+    lib().orc_periodic_smooth(u.shape[0], _ptr(u), _ptr(p))
+    return p
 
 
 def series(psi, B, M=6, h=None):

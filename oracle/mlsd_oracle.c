@@ -43,6 +43,8 @@
 
 #define ORC_PI 3.14159265358979323846
 
+void orc_periodic_smooth(int n, const double *u, double *p);
+
 /* ------------------------------------------------------------------------ */
 /* Sec. 3.1: Fourier decomposition.                                          */
 /*                                                                           */
@@ -459,7 +461,7 @@ void orc_chain(int n_modes, const int *k1, const int *k2, const double *re, cons
                int n_macro, double kappa, double cfl, double t_burn, double t_avg,
                long n_burn_fixed, long n_avg_fixed,
                int n_nodes, const int *node_i, const int *node_j,
-               double *K_out, double *Kstar_levels_out, long *steps_out)
+               double *K_out, double *Kstar_levels_out, long *steps_out, int periodize)
 {
     int *lev = malloc(sizeof(int) * n_modes), *kind = malloc(sizeof(int) * n_modes);
     orc_band_of(n_modes, k1, k2, n_levels, edges, lev, kind);
@@ -517,6 +519,12 @@ void orc_chain(int n_modes, const int *k1, const int *k2, const double *re, cons
             }
             for (int t = 0; t < n_modes; ++t) ud[t] = (lev[t] == l && kind[t] == 0);
             orc_patch_psi(n_modes, k1, k2, re, im, ud, Nl, ox, oy, n, psi);
+            if (periodize) {              /* the band's periodic component on the patch */
+                double *pp = malloc(sizeof(double) * n * n);
+                orc_periodic_smooth(n, psi, pp);
+                memcpy(psi, pp, sizeof(double) * n * n);
+                free(pp);
+            }
             double *v1 = malloc(sizeof(double) * n * n), *v2 = malloc(sizeof(double) * n * n);
             orc_velocity(n, h, psi, v1, v2);
             double vmax = 0.0;
@@ -881,6 +889,46 @@ static void neg_l0_inverse(int n, double h, const double *B, const double *f, do
     dft2(n, Fr, Fi, out, gi, +1);
     for (long c = 0; c < nn; ++c) out[c] /= (double)nn;
     free(zr); free(Fr); free(Fi); free(gi);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Periodic-plus-smooth decomposition of a patch field (the periodisation of */
+/* a band that is not periodic on the patch; Moisan, "Periodic plus smooth   */
+/* image decomposition", 2011).  u = p + s on the n x n samples, where the   */
+/* periodic 5-point Laplacian of p equals the Laplacian of u taken over the  */
+/* patch's own neighbours only (no neighbour across the seam), and s is the */
+/* rest:  Lap_per s = v,  v = Lap_per u - Lap_int u,  which is nonzero on    */
+/* the border samples only (v(x) = sum over the seam neighbours y of         */
+/* u(y) - u(x)).  s is solved in Fourier space (symbol                       */
+/* 2 cos t1 + 2 cos t2 - 4), with mean(s) = 0, so mean(p) = mean(u).         */
+/* ------------------------------------------------------------------------ */
+void orc_periodic_smooth(int n, const double *u, double *p)
+{
+    long nn = (long)n * n;
+    double *v = calloc(nn, sizeof(double)), *zi = calloc(nn, sizeof(double));
+    double *Vr = malloc(sizeof(double) * nn), *Vi = malloc(sizeof(double) * nn);
+    double *sr = malloc(sizeof(double) * nn), *si = malloc(sizeof(double) * nn);
+    for (int a = 0; a < n; ++a) {          /* rows b = 0 and b = n-1 see each other */
+        double j = u[(long)(n - 1) * n + a] - u[a];
+        v[a] += j;
+        v[(long)(n - 1) * n + a] -= j;
+    }
+    for (int b = 0; b < n; ++b) {          /* columns a = 0 and a = n-1 */
+        double j = u[(long)b * n + n - 1] - u[(long)b * n];
+        v[(long)b * n] += j;
+        v[(long)b * n + n - 1] -= j;
+    }
+    dft2(n, v, zi, Vr, Vi, -1);
+    for (int k2 = 0; k2 < n; ++k2)
+        for (int k1 = 0; k1 < n; ++k1) {
+            long c = (long)k2 * n + k1;
+            if (k1 == 0 && k2 == 0) { Vr[c] = Vi[c] = 0.0; continue; }
+            double d = 2.0 * cos(2.0 * ORC_PI * k1 / n) + 2.0 * cos(2.0 * ORC_PI * k2 / n) - 4.0;
+            Vr[c] /= d; Vi[c] /= d;
+        }
+    dft2(n, Vr, Vi, sr, si, +1);
+    for (long c = 0; c < nn; ++c) p[c] = u[c] - sr[c] / (double)nn;
+    free(v); free(zi); free(Vr); free(Vi); free(sr); free(si);
 }
 
 /* T[(m-2)*3 + (0,1,2)] = (T_m11, T_m12, T_m22) for m = 2..M */
