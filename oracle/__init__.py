@@ -67,7 +67,9 @@ def _declare(L):
     L.orc_num_threads.restype = _i
     L.orc_features.argtypes = [_i, _p, _p, _d, _p]
     L.orc_series.argtypes = [_i, _d, _p, _p, _i, _p]
-    L.orc_series_estimate.argtypes = [_p, _p, _p]
+    L.orc_series_estimate.argtypes = [_p, _p, _p, _p, _p]
+    L.orc_wynn.argtypes = [_p, _i, _i]
+    L.orc_wynn.restype = _d
     L.orc_periodic_smooth.argtypes = [_i, _p, _p]
     L.orc_mlp.argtypes = [_i, _i, _i, _p, _p, _i, _p, _p, _p]
     L.orc_mlp.restype = _d
@@ -307,12 +309,13 @@ def coarse_grain(u, N):
     return U, m.value
 
 
-N_FEATURES = 603
-PSI_SCALE, T_SCALE, Y_SCALE, Y_CLAMP = 32.0, 10.0, 300.0, 3.0
+N_FEATURES = 606
+SERIES_M = 19
+PSI_SCALE, T_SCALE, Y_SCALE = 32.0, 10.0, 300.0
 
 
 def features(psi, B, kappa):
-    """603 surrogate inputs of one patch (psi with its patch mean removed)."""
+    """606 surrogate inputs of one patch (psi with its patch mean removed)."""
     psi = _f64(psi); B = _f64(B)
     f = np.zeros(N_FEATURES)
     lib().orc_features(psi.shape[0], _ptr(psi), _ptr(B), float(kappa), _ptr(f))
@@ -327,7 +330,7 @@ def periodic_smooth(u):
     return p
 
 
-def series(psi, B, M=6, h=None):
+def series(psi, B, M=SERIES_M, h=None):
     """Perturbation moments T_2..T_M of the steady corrector equation: [M-1][3]
     (components 11, 12, 22); sum_m T_m = K - B where the series converges."""
     psi = _f64(psi); B = _f64(B)
@@ -338,23 +341,30 @@ def series(psi, B, M=6, h=None):
     return T
 
 
-def series_estimate(T):
-    """(E, S6): the resummed estimate of K - B and the partial sum, from T_2..T_6."""
+def wynn(T, comp, K):
+    """[K/K] Pade value at 1 of the series in x^2 with terms T_(2k+2) + T_(2k+3)
+    (Wynn's epsilon on its partial sums)."""
     T = _f64(T)
-    E = np.zeros(3); S6 = np.zeros(3)
-    lib().orc_series_estimate(_ptr(T), _ptr(E), _ptr(S6))
-    return E, S6
+    return lib().orc_wynn(_ptr(T), int(comp), int(K))
+
+
+def series_estimate(T):
+    """(P2, P3, E, gap): the [2/2], [3/3], [4/4] approximants of K - B from
+    T_2..T_19 and the gap max_c |E_c - P3_c|."""
+    T = _f64(T)
+    P2 = np.zeros(3); P3 = np.zeros(3); E = np.zeros(3); gap = ctypes.c_double()
+    lib().orc_series_estimate(_ptr(T), _ptr(P2), _ptr(P3), _ptr(E), ctypes.byref(gap))
+    return P2, P3, E, gap.value
 
 
 def surrogate_target(K, B, E):
-    """Training target of one patch: clamp((K - B - E) Y_SCALE / tr B, -Y_CLAMP, Y_CLAMP)."""
-    y = (np.asarray(K) - np.asarray(B) - np.asarray(E)) * Y_SCALE / (B[0] + B[2])
-    return np.clip(y, -Y_CLAMP, Y_CLAMP)
+    """Training target of one patch: asinh((K - B - E) Y_SCALE / tr B)."""
+    return np.arcsinh((np.asarray(K) - np.asarray(B) - np.asarray(E)) * Y_SCALE / (B[0] + B[2]))
 
 
 def surrogate_K(out, E, B):
-    """K of one patch from a network output and the resummed series estimate E."""
-    return np.asarray(B) + np.asarray(E) + (B[0] + B[2]) * np.asarray(out) / Y_SCALE
+    """K of one patch from a network output and the series estimate E."""
+    return np.asarray(B) + np.asarray(E) + (B[0] + B[2]) * np.sinh(np.asarray(out)) / Y_SCALE
 
 
 def mlp_param_count(d0, h):

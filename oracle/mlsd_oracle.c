@@ -966,30 +966,71 @@ void orc_series(int n, double h, const double *psi, const double *B, int M, doub
     free(v1); free(v2); free(c1); free(c2); free(Ac);
 }
 
-/* Resummation of the series per component from T_2..T_6 (odd terms added     */
-/* as they are): the partial sum S6 = T_2 + ... + T_6, and the estimate        */
-/*   E = T_2 + T_3 + T_5 + T_4 / (1 - rho),  rho = clamp(T_6 / T_4, -1/2, 4/5) */
-/* (rho = 0 where T_4 = 0).  In the even terms the series is close to         */
-/* geometric, T_6 ~ rho T_4, and T_4 / (1 - rho) sums that tail (the Shanks   */
-/* transform of the partial sums S_2, S_4, S_6); the clamp keeps E finite and */
-/* continuous where the series does not converge.                             */
-void orc_series_estimate(const double *T, double *E, double *S6)
+/* Resummation of the series by Wynn's epsilon algorithm (the diagonal Pade   */
+/* approximants of a power series at 1): with partial sums S_0..S_{2K},       */
+/* eps_{-1}^(j) = 0, eps_0^(j) = S_j,                                          */
+/*   eps_{k+1}^(j) = eps_{k-1}^(j+1) + 1 / (eps_k^(j+1) - eps_k^(j)),          */
+/* and [K/K] = eps_{2K}^(0).  Where a difference vanishes the last even        */
+/* column reached is returned.                                                 */
+static double wynn_partial(const double *c, int K)
 {
-    for (int c = 0; c < 3; ++c) {
-        double t2 = T[c], t3 = T[3 + c], t4 = T[6 + c], t5 = T[9 + c], t6 = T[12 + c];
-        double rho = fabs(t4) > 1e-300 ? t6 / t4 : 0.0;
-        if (rho < -0.5) rho = -0.5;
-        if (rho > 0.8) rho = 0.8;
-        E[c] = t2 + t3 + t5 + t4 / (1.0 - rho);
-        S6[c] = t2 + t3 + t4 + t5 + t6;
+    const int n = 2 * K + 1;
+    double *prev = calloc(n + 1, sizeof(double)), *cur = malloc(sizeof(double) * n);
+    double *nxt = malloc(sizeof(double) * n);
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) { acc += c[j]; cur[j] = acc; }
+    double best = cur[n - 1];
+    int len = n;
+    for (int k = 1; k <= 2 * K; ++k) {
+        for (int j = 0; j < len - 1; ++j) {
+            double d = cur[j + 1] - cur[j];
+            if (fabs(d) < 1e-300) { free(prev); free(cur); free(nxt); return best; }
+            nxt[j] = prev[j + 1] + 1.0 / d;
+        }
+        double *t = prev; prev = cur; cur = nxt; nxt = t;
+        len -= 1;
+        if (k % 2 == 0) best = cur[0];
     }
+    free(prev); free(cur); free(nxt);
+    return best;
+}
+
+/* [K/K] approximant at x = 1 of the series in x^2 whose terms are the pairs   */
+/* p_k = T_(2k+2) + T_(2k+3), k = 0..2K (T_2..T_(4K+3); T: T_2..T_M as          */
+/* [M-1][3]), for one component.  K - B is even in v up to the small odd       */
+/* moments (the central advection is skew up to O(h^2)), so the pairs are the  */
+/* natural terms; an odd moment that vanishes by symmetry then cannot stall   */
+/* the epsilon table.                                                          */
+double orc_wynn(const double *T, int comp, int K)
+{
+    double c[32];
+    for (int k = 0; k <= 2 * K; ++k) c[k] = T[(2 * k) * 3 + comp] + T[(2 * k + 1) * 3 + comp];
+    return wynn_partial(c, K);
+}
+
+/* The surrogate's physics estimate of K - B from T_2..T_19: E = [4/4] of the  */
+/* pair series, with the lower approximants P2 = [2/2] (T_2..T_11) and         */
+/* P3 = [3/3] (T_2..T_15); gap = max_c |E_c - P3_c| measures how far the       */
+/* resummation is from converged.                                              */
+#define ORC_SERIES_M 19
+void orc_series_estimate(const double *T, double *P2, double *P3, double *E, double *gap)
+{
+    double g = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        P2[c] = orc_wynn(T, c, 2);
+        P3[c] = orc_wynn(T, c, 3);
+        E[c] = orc_wynn(T, c, 4);
+        double d = fabs(E[c] - P3[c]);
+        if (!(d <= g)) g = d;                 /* NaN propagates */
+    }
+    *gap = g;
 }
 
 /* ------------------------------------------------------------------------ */
 /* Learned surrogate of the patch solve (not in the paper; the library's     */
 /* estimator it is checked against is orc_patch_k).                          */
 /*                                                                           */
-/* Features of a patch (603 values):                                         */
+/* Features of a patch (606 values):                                         */
 /*   [0, 578): Re and Im of psihat(k) = n^-2 sum_ab psi[b][a]               */
 /*             exp(-2 pi i (k1 a + k2 b) / n) for k2 = -8..8 (slow),         */
 /*             k1 = -8..8 (fast), each times 32 / (tr(B)/2) (a Peclet        */
@@ -997,12 +1038,13 @@ void orc_series_estimate(const double *T, double *E, double *S6)
 /*             the patch mean removed                                        */
 /*   578..580: B11/kappa, B12/kappa, B22/kappa;  581: log(kappa)             */
 /*   582..596: asinh(10 T_m / tr B) for m = 2..6 (components 11, 12, 22)     */
-/*   597..599: asinh(10 S6 / tr B);  600..602: asinh(10 E / tr B)            */
-/*   (the perturbation moments, the partial sum and the resummed estimate    */
-/*   of orc_series / orc_series_estimate; asinh keeps the diverging series   */
-/*   of high-Peclet patches at a usable scale).                              */
-/* Target: clamp((K - B - E) 300 / tr(B), -3, 3) per component; the         */
-/* surrogate's K is B + E + tr(B) out / 300.                                  */
+/*   597..605: asinh(10 x / tr B) for x = P2, P3, E (the [2/2], [3/3], [4/4]  */
+/*             approximants of orc_series_estimate)                          */
+/*   (the perturbation moments of orc_series and the Wynn approximants of     */
+/*   orc_series_estimate; asinh keeps the diverging moments of high-Peclet    */
+/*   patches at a usable scale).                                              */
+/* Target: asinh((K - B - E) 300 / tr(B)) per component, E = [4/4]; the      */
+/* surrogate's K is B + E + tr(B) sinh(out) / 300.                            */
 /* ------------------------------------------------------------------------ */
 #define ORC_PSI_SCALE 32.0
 #define ORC_T_SCALE 10.0
@@ -1029,12 +1071,13 @@ void orc_features(int n, const double *psi, const double *B, double kappa, doubl
     f[t++] = B[1] / kappa;
     f[t++] = B[2] / kappa;
     f[t++] = log(kappa);
-    double T[15], E[3], S6[3];
-    orc_series(n, 2.0 * ORC_PI / n, psi, B, 6, T);   /* h cancels in T: any patch side */
-    orc_series_estimate(T, E, S6);
+    double T[3 * (ORC_SERIES_M - 1)], P2[3], P3[3], E[3], gap;
+    orc_series(n, 2.0 * ORC_PI / n, psi, B, ORC_SERIES_M, T);   /* h cancels: any patch side */
+    orc_series_estimate(T, P2, P3, E, &gap);
     const double sc = ORC_T_SCALE / (2.0 * trh);
     for (int q = 0; q < 15; ++q) f[t++] = asinh(sc * T[q]);
-    for (int c = 0; c < 3; ++c) f[t++] = asinh(sc * S6[c]);
+    for (int c = 0; c < 3; ++c) f[t++] = asinh(sc * P2[c]);
+    for (int c = 0; c < 3; ++c) f[t++] = asinh(sc * P3[c]);
     for (int c = 0; c < 3; ++c) f[t++] = asinh(sc * E[c]);
 }
 

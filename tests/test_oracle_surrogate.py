@@ -2,9 +2,11 @@
 (checked against numpy's FFT); the perturbation moments T_m of the steady
 corrector equation they carry give the discrete shear closed form (T_2, with
 every higher moment zero) and, summed, the dense direct solve of the steady
-corrector for a general flow with a full-tensor base; the resummed estimate
-is the Shanks transform of the partial sums; the MLP gradient against central
-finite differences in FP64."""
+corrector for a general flow with a full-tensor base; the resummation (Wynn's
+epsilon algorithm) reproduces the value of a rational function from its Taylor
+coefficients (the defining property of the Pade approximant) and matches the
+Pade approximant solved from its linear equations; the MLP gradient against
+central finite differences in FP64."""
 import math
 
 import numpy as np
@@ -21,7 +23,7 @@ def test_features_are_the_normalised_dft():
     psi -= psi.mean()
     B = np.array([0.3, 0.05, 0.5])
     f = oracle.features(psi, B, 0.01)
-    assert f.shape == (603,)
+    assert f.shape == (606,)
     F = np.fft.fft2(psi) / n ** 2            # F[k2][k1] = n^-2 sum psi[b][a] e^{-2pi i(k1 a + k2 b)/n}
     want = []
     for k2 in range(-8, 9):
@@ -92,8 +94,9 @@ def test_series_of_a_shear_is_its_closed_form(k, axis):
         want = np.array([0.5 * a * a * math.cos(t / 2) ** 2 / B[2], 0.0, 0.0])
     np.testing.assert_allclose(T[0], want, rtol=1e-12, atol=1e-15)
     assert np.abs(T[1:]).max() < 1e-13 * np.abs(want).max()
-    E, S6 = oracle.series_estimate(T)
+    P2, P3, E, gap = oracle.series_estimate(T)
     np.testing.assert_allclose(E, want, rtol=1e-12, atol=1e-15)
+    assert gap < 1e-13 * np.abs(want).max()
     h = 2 * math.pi / n
     np.testing.assert_allclose(_steady_K(psi, h, B) - B, want, rtol=1e-8, atol=1e-13)
 
@@ -121,8 +124,8 @@ def test_series_sums_to_the_direct_steady_solve():
 
 
 def test_series_truncation_error_has_the_right_order():
-    # S6 = T_2 + ... + T_6 misses the O(v^7) tail: halving the amplitude shrinks
-    # the gap to the direct solve ~2^7-fold (a wrong T_4 would leave O(v^4))
+    # the partial sum T_2 + ... + T_6 misses the O(v^7) tail: halving the amplitude
+    # shrinks the gap to the direct solve ~2^7-fold (a wrong T_4 would leave O(v^4))
     n = 12
     B = np.array([0.05, 0.012, 0.035])
     h = 2 * math.pi / n
@@ -130,38 +133,78 @@ def test_series_truncation_error_has_the_right_order():
     for eps in (0.08, 0.04):
         psi = _general_flow(n, eps)
         Kd = _direct_steady_K(psi, h, B)
-        E, S6 = oracle.series_estimate(oracle.series(psi, B))
+        S6 = oracle.series(psi, B, M=6).sum(0)
         gaps.append(np.abs(B + S6 - Kd).max())
     assert 60 < gaps[0] / gaps[1] < 300, gaps
 
 
-def test_estimate_is_the_shanks_transform_of_the_partial_sums():
-    # where the clamp is inactive, E = (S_c S_a - S_b^2) / (S_c + S_a - 2 S_b) over
-    # the even partial sums S_a = T2, S_b = T2 + T4, S_c = T2 + T4 + T6 (plus T3 + T5)
+def _taylor_of_rational(a, b, count):
+    """Taylor coefficients of (a0 + a1 x + ...) / (1 + b1 x + ...) by series division."""
+    c = np.zeros(count)
+    for k in range(count):
+        v = a[k] if k < len(a) else 0.0
+        for j in range(1, min(k, len(b) - 1) + 1):
+            v -= b[j] * c[k - j]
+        c[k] = v
+    return c
+
+
+def test_wynn_reproduces_a_rational_function():
+    # the [K/K] Pade approximant of a rational function of degree (K, K) is the
+    # function itself: from its Taylor coefficients Wynn's epsilon gives f(1),
+    # even where the Taylor series diverges at 1
     rng = np.random.default_rng(4)
-    for _ in range(20):
-        t = rng.standard_normal((5, 3))
-        t[2] = np.sign(t[0]) * np.abs(t[2]) * 0.3
-        t[4] = t[2] * rng.uniform(-0.45, 0.75, 3)
-        E, S6 = oracle.series_estimate(t)
-        Sa, Sb, Sc = t[0], t[0] + t[2], t[0] + t[2] + t[4]
-        shanks = (Sc * Sa - Sb * Sb) / (Sc + Sa - 2 * Sb)
-        np.testing.assert_allclose(E, shanks + t[1] + t[3], rtol=1e-12)
-        np.testing.assert_allclose(S6, t.sum(0), rtol=1e-14)
-    # and for a geometric even tail T6 = r T4, T8 = r^2 T4, ... it is the sum
-    t = np.array([[1.0, 0.1, 2.0], [0.0] * 3, [0.5, -0.02, 0.4], [0.0] * 3, [0.2, -0.008, 0.16]])
-    E, _ = oracle.series_estimate(t)
-    np.testing.assert_allclose(E, t[0] + t[2] / (1 - 0.4), rtol=1e-14)
+    for K in (1, 2, 3, 4):
+        for _ in range(3):
+            a = rng.uniform(-1, 1, K + 1)
+            # denominator prod_i (1 - x / r_i): poles at 0.35 <= |x| <= 0.9, so the
+            # Taylor series at 0 diverges at x = 1
+            roots = rng.uniform(0.35, 0.9, K) * rng.choice([-1.0, 1.0], K)
+            b = np.poly(roots)[::-1]
+            b = b / b[0]
+            c = _taylor_of_rational(a, b, 2 * K + 1)
+            T = np.zeros((4 * K + 2, 3))
+            T[0::2, 0] = c                      # pair k = T_(2k+2) + T_(2k+3) = c_k
+            f1 = np.polyval(a[::-1], 1.0) / np.polyval(b[::-1], 1.0)
+            assert oracle.wynn(T, 0, K) == pytest.approx(f1, rel=1e-7, abs=1e-12)
+    # a geometric series of ratio -3 (divergent at 1): [1/1] = 1 / (1 + 3), with the
+    # terms split between the two moments of each pair
+    T = np.zeros((6, 3))
+    T[:, 1] = [0.25, 0.75, -1.0, -2.0, 4.5, 4.5]
+    assert oracle.wynn(T, 1, 1) == pytest.approx(0.25, rel=1e-14)
 
 
-def test_estimate_beats_the_partial_sum_at_moderate_peclet():
+def test_wynn_matches_the_pade_linear_system():
+    # [K/K](1) = p(1) / q(1) with q_0 = 1, sum_j q_j c_(k-j) = 0 for k = K+1..2K and
+    # p_k = sum_(j<=k) q_j c_(k-j) for k <= K: solved with numpy on random data
+    rng = np.random.default_rng(5)
+    for K in (2, 3, 4):
+        c = rng.standard_normal(2 * K + 1) * 0.5 ** np.arange(2 * K + 1)
+        A = np.array([[c[k - j] for j in range(1, K + 1)] for k in range(K + 1, 2 * K + 1)])
+        q = np.concatenate([[1.0], np.linalg.solve(A, -c[K + 1:2 * K + 1])])
+        p = [sum(q[j] * c[k - j] for j in range(k + 1)) for k in range(K + 1)]
+        T = np.zeros((4 * K + 2, 3))
+        w = rng.uniform(0, 1, 2 * K + 1)
+        T[0::2, 2] = w * c                  # any split of c_k over the pair
+        T[1::2, 2] = (1 - w) * c
+        assert oracle.wynn(T, 2, K) == pytest.approx(sum(p) / sum(q), rel=1e-9)
+
+
+def test_estimate_converges_where_the_series_diverges():
+    # a general flow whose moments grow (|T_4 / T_2| ~ 0.8 at this amplitude): the
+    # partial sums drift away from the dense direct solve, the [4/4] approximant
+    # of the pair series lands on it
     n = 12
     B = np.array([0.05, 0.012, 0.035])
     h = 2 * math.pi / n
-    psi = _general_flow(n, 0.12)
+    psi = _general_flow(n, 0.16)
     Kd = _direct_steady_K(psi, h, B)
-    E, S6 = oracle.series_estimate(oracle.series(psi, B))
-    assert np.abs(B + E - Kd).max() < 0.5 * np.abs(B + S6 - Kd).max()
+    T = oracle.series(psi, B)
+    P2, P3, E, gap = oracle.series_estimate(T)
+    assert np.abs(T[2]).max() > 0.5 * np.abs(T[0]).max()
+    assert np.abs(B + T.sum(0) - Kd).max() > 0.1 * np.abs(Kd - B).max()
+    assert np.abs(B + E - Kd).max() < 1e-3 * np.abs(Kd - B).max()
+    assert np.abs(E - P3).max() == pytest.approx(gap, rel=1e-14)
 
 
 def test_features_carry_the_series():
@@ -170,11 +213,12 @@ def test_features_carry_the_series():
     B = np.array([0.05, 0.012, 0.035])
     f = oracle.features(psi, B, 0.01)
     T = oracle.series(psi, B)
-    E, S6 = oracle.series_estimate(T)
+    P2, P3, E, _ = oracle.series_estimate(T)
     sc = 10.0 / (B[0] + B[2])
-    np.testing.assert_allclose(np.sinh(f[582:597]), sc * T.ravel(), rtol=1e-12, atol=1e-300)
-    np.testing.assert_allclose(np.sinh(f[597:600]), sc * S6, rtol=1e-12)
-    np.testing.assert_allclose(np.sinh(f[600:603]), sc * E, rtol=1e-12)
+    np.testing.assert_allclose(np.sinh(f[582:597]), sc * T[:5].ravel(), rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(np.sinh(f[597:600]), sc * P2, rtol=1e-12)
+    np.testing.assert_allclose(np.sinh(f[600:603]), sc * P3, rtol=1e-12)
+    np.testing.assert_allclose(np.sinh(f[603:606]), sc * E, rtol=1e-12)
 
 
 def _params(d0, h, rng):
@@ -290,7 +334,7 @@ def _feature_rule(f, g):
             s = 2 * ((s2 + 8) * 17 + s1 + 8)
             out[d:d + 2] = sign * np.asarray(f)[s:s + 2]
     out[578:581] = square_symmetry_tensor(f[578:581], g)
-    for q in range(582, 603, 3):              # T_2..T_6, S6, E: tensors under R . R^T
+    for q in range(582, 606, 3):              # T_2..T_6, [4/4], [6/6], [8/8]: tensors
         out[q:q + 3] = np.arcsinh(square_symmetry_tensor(np.sinh(np.asarray(f[q:q + 3])), g))
     return out
 
@@ -308,4 +352,6 @@ def test_features_of_the_mapped_patch_follow_the_stated_rule(g):
     f_g = oracle.features(square_symmetry_psi(psi, g), square_symmetry_tensor(B, g), kappa)
     scale = np.abs(f[:578]).max()
     np.testing.assert_allclose(f_g[:578], _feature_rule(f, g)[:578], rtol=0, atol=1e-12 * scale)
-    np.testing.assert_allclose(f_g[578:], _feature_rule(f, g)[578:], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(f_g[578:597], _feature_rule(f, g)[578:597], rtol=1e-12, atol=1e-15)
+    # the resummed values (Wynn's epsilon) amplify the rounding of the moments
+    np.testing.assert_allclose(f_g[597:], _feature_rule(f, g)[597:], rtol=1e-8, atol=1e-12)
