@@ -62,6 +62,19 @@ def _peaks():
         return {}
 
 
+# the profiling recipe's stand-ins, used (and named as such) only when the measured
+# peaks file is absent
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def _peak(key):
+    """(value, source) of a roofline denominator: the measured figure, else the fallback."""
+    v = _peaks().get(key)
+    if v:
+        return float(v), "measured (MEASURED_PEAKS.json)"
+    return FALLBACK_PEAKS[key], "fallback (no measured peaks file)"
+
+
 def _clock_sampler(path):
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -188,29 +201,48 @@ def reference_arm(args):
 DNS_BYTES_PER_CELL_STEP = 12     # read u, read psi, write u (both RK stages fused)
 
 
+SUR_OCTAVES = ((16, 32, 64), (32, 64, 32), (64, 128, 32))   # (lo, hi, patch n) of each level
+SUR_TRAIN_FLOW, SUR_TEST_FLOW = 1510004510, 20261204           # continuous-spectrum seeds
+
+
+def _octave_level(seed, lo, hi, n, N, kappa):
+    """One octave band (lo <= |k1|, |k2| < hi) of a continuous-spectrum realization as
+    a one-level problem: patch side 2 pi / lo, n x n patches on an N x N macro grid."""
+    from inputs import flows
+    import paper_1510_00451_gb300 as mlsd
+    full = flows.continuous_spectrum(256, seed=seed)
+    a, b = np.abs(full.k1), np.abs(full.k2)
+    keep = (a >= lo) & (a < hi) & (b >= lo) & (b < hi)
+    band = flows.Spectrum(full.k1[keep], full.k2[keep], full.re[keep], full.im[keep])
+    return mlsd.Levels(band, kappa, N, [float(lo), float(hi)], [n], patch_div=[lo], cfl=0.2)
+
+
 def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3,
-                   thresholds=(5e-4, 1e-3, 2e-3, 3e-3, 1e-2), seed=1510):
-    """Surrogate vs plain on the diagonal band of the continuous-spectrum flow's
-    6th octave (32 <= |k1|, |k2| < 64, patch side 2 pi / 32, 32^2 patches,
-    kappa = 1e-3, N x N patches, full relaxation window).  Training data: 3
-    seeded base sets on every patch (3 N^2 plain solves); test: a 4th base set.
-    Reports, per disagreement threshold, the fallback fraction, the K error
-    against the plain solve and the K-tensor rate of both paths."""
+                   thresholds=(5e-4, 1e-3, 2e-3), seed=1510):
+    """Surrogate vs plain on three octave levels of the continuous-spectrum flow
+    (kappa = 1e-3, N x N patches per level, full relaxation window): the 5th
+    octave (16 <= |k| < 32, 64^2 patches), the 6th and the 7th (32^2).  Training
+    data: one seeded base set on every patch of each level of one flow
+    realization (3 N^2 plain solves); test: the same levels of ANOTHER
+    realization (no patch psi seen in training) with a fresh base set.  Reports,
+    per level and threshold, the fallback fraction, the K error against the plain
+    solve and the K-tensor rate of both paths, and the totals over the levels."""
     import torch
     import inputs
-    from inputs import flows
     import paper_1510_00451_gb300 as mlsd
     from paper_1510_00451_gb300 import surrogate as S
     dev = torch.device("cuda", _local_rank())
-    full = flows.continuous_spectrum(256)
-    a, b = np.abs(full.k1), np.abs(full.k2)
-    keep = (a >= 32) & (a < 64) & (b >= 32) & (b < 64)
-    band = flows.Spectrum(full.k1[keep], full.k2[keep], full.re[keep], full.im[keep])
     kappa = 1e-3
-    lv = mlsd.Levels(band, kappa, N, [32.0, 64.0], [32], patch_div=[32], cfl=0.2)
     P = N * N
     t0 = time.perf_counter()
-    X, Y = S.make_dataset(lv, 1, [inputs.random_bases(P, kappa, seed + i) for i in range(3)])
+    Xs, Ys = [], []
+    for i, (lo, hi, n) in enumerate(SUR_OCTAVES):
+        lv = _octave_level(SUR_TRAIN_FLOW, lo, hi, n, N, kappa)
+        X, Y = S.make_dataset(lv, 1, [inputs.random_bases(P, kappa, seed + 100 + i)])
+        Xs.append(X); Ys.append(Y)
+        lv.close()
+    X, Y = torch.cat(Xs), torch.cat(Ys)
+    del Xs, Ys
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     sur = mlsd.Surrogate(members=members, hidden=hidden, max_batch=batch)
@@ -220,8 +252,7 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
     losses = S.train(sur, X, Y, epochs, batch, lr, seed=seed, lr_final=1e-5)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    Bt = torch.tensor(inputs.random_bases(P, kappa, seed + 99), dtype=torch.float64, device=dev)
-    Kp = torch.empty_like(Bt); Ks = torch.empty_like(Bt)
+    del X, Y
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
 
@@ -230,46 +261,66 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
         torch.cuda.synchronize()
         return r, e0.elapsed_time(e1) * 1e-3
 
-    lv.solve_level(1, Bt, Kp)                       # warm-up
-    _, t_plain = timed(lambda: lv.solve_level(1, Bt, Kp))
-    cu_plain = lv.level_work(1)[0]
-    Kpn = Kp.cpu().numpy()
-    # the tensor-core ensemble kernel alone on every patch of the level
+    levels, tot_plain, tot_sur, errs = [], 0.0, {t: 0.0 for t in thresholds}, {t: [] for t in thresholds}
+    for i, (lo, hi, n) in enumerate(SUR_OCTAVES):
+        lv = _octave_level(SUR_TEST_FLOW, lo, hi, n, N, kappa)
+        Bt = torch.tensor(inputs.random_bases(P, kappa, seed + 99 + i), dtype=torch.float64,
+                          device=dev)
+        Kp = torch.empty_like(Bt); Ks = torch.empty_like(Bt)
+        lv.solve_level(1, Bt, Kp)                       # warm-up
+        _, t_plain = timed(lambda: lv.solve_level(1, Bt, Kp))
+        Kpn = Kp.cpu().numpy()
+        rows = []
+        for thr in thresholds:
+            lv.solve_level_surrogate(sur, 1, Bt, Ks, thr)   # warm-up
+            nfb, t_sur = timed(lambda: lv.solve_level_surrogate(sur, 1, Bt, Ks, thr))
+            err = S.k_error(Ks.cpu().numpy(), Kpn)
+            errs[thr].append(err)
+            tot_sur[thr] += t_sur
+            rows.append({"threshold": thr, "fallback_frac": nfb / P, "seconds": t_sur,
+                         "k_tensors_per_s": P / t_sur, "speedup_vs_plain": t_plain / t_sur,
+                         "k_rel_err": {"max": float(err.max()), "p99": float(np.quantile(err, 0.99)),
+                                       "median": float(np.median(err)),
+                                       "frac_le_1e-3": float(np.mean(err <= 1e-3))}})
+        tot_plain += t_plain
+        levels.append({"octave": f"{lo}<=|k|<{hi}", "patch_n": n, "plain_seconds": t_plain,
+                       "plain_k_tensors_per_s": P / t_plain,
+                       "plain_cell_updates_per_s": lv.level_work(1)[0] / t_plain,
+                       "by_threshold": rows})
+        assert lv.status() == 0
+        lv.close()
+    overall = []
+    for thr in thresholds:
+        err = np.concatenate(errs[thr])
+        overall.append({"threshold": thr, "speedup_vs_plain": tot_plain / tot_sur[thr],
+                        "k_tensors_per_s": len(SUR_OCTAVES) * P / tot_sur[thr],
+                        "k_rel_err": {"max": float(err.max()), "p99": float(np.quantile(err, 0.99)),
+                                      "median": float(np.median(err)),
+                                      "frac_le_1e-3": float(np.mean(err <= 1e-3))}})
+    # the tensor-core ensemble kernel alone on one level's rows
     Xt = torch.empty(P, mlsd.SUR_IN, dtype=torch.bfloat16, device=dev)
-    lv.features(1, Bt, Xt)
+    lv = _octave_level(SUR_TEST_FLOW, 32, 64, 32, N, kappa)
+    lv.features(1, torch.tensor(inputs.random_bases(P, kappa, seed), dtype=torch.float64,
+                                device=dev), Xt)
+    lv.close()
     out = torch.empty(members, P, 3, dtype=torch.float32, device=dev)
     sur.predict(Xt, out)
     _, t_mlp = timed(lambda: sur.predict(Xt, out))
     mlp_flop = 2.0 * P * members * (mlsd.SUR_IN * hidden + 2 * hidden * hidden + hidden * 16)
-    peaks = _peaks()
-    rows = []
-    for thr in thresholds:
-        lv.solve_level_surrogate(sur, 1, Bt, Ks, thr)   # warm-up
-        nfb, t_sur = timed(lambda: lv.solve_level_surrogate(sur, 1, Bt, Ks, thr))
-        err = S.k_error(Ks.cpu().numpy(), Kpn)
-        rows.append({"threshold": thr, "fallback_frac": nfb / P, "seconds": t_sur,
-                     "k_tensors_per_s": P / t_sur, "speedup_vs_plain": t_plain / t_sur,
-                     "k_rel_err": {"max": float(err.max()), "p99": float(np.quantile(err, 0.99)),
-                                   "median": float(np.median(err)),
-                                   "frac_le_1e-3": float(np.mean(err <= 1e-3))}})
-    Kn = torch.empty_like(Bt)
-    lv.solve_level_surrogate(sur, 1, Bt, Kn, 1e30)
-    err_nf = S.k_error(Kn.cpu().numpy(), Kpn)
-    assert sur.status() == 0 and lv.status() == 0
-    return {"workload": f"continuous-spectrum octave 32-64 diagonal band, {P} patches of 32^2, "
-                        f"kappa=1e-3, full window; training on {3 * P} plain solves",
+    assert sur.status() == 0
+    peak, src = _peak("bf16_tflops")
+    return {"workload": f"continuous-spectrum octaves 16-32 (64^2), 32-64, 64-128 (32^2), {P} "
+                        "patches each, kappa=1e-3, full window; trained on one flow "
+                        f"realization ({len(SUR_OCTAVES) * P} plain solves), tested on another",
             "members": members, "hidden": hidden, "epochs": epochs, "batch": batch,
-            "final_loss": losses, "plain_k_tensors_per_s": P / t_plain,
-            "plain_cell_updates_per_s": cu_plain / t_plain,
-            "by_threshold": rows,
-            "ensemble_only_err": {"max": float(err_nf.max()), "median": float(np.median(err_nf)),
-                                  "frac_le_1e-3": float(np.mean(err_nf <= 1e-3))},
+            "final_loss": losses, "levels": levels, "overall": overall,
+            "plain_k_tensors_per_s": len(SUR_OCTAVES) * P / tot_plain,
             "mlp_tensor_core": {"ms": t_mlp * 1e3, "achieved_tflops": mlp_flop / t_mlp / 1e12,
-                                "peak_bf16_tflops": peaks.get("bf16_tflops", 1939.8),
-                                "frac": mlp_flop / t_mlp / 1e12 / peaks.get("bf16_tflops", 1939.8),
+                                "peak_bf16_tflops": peak, "peak_source": src,
+                                "frac": mlp_flop / t_mlp / 1e12 / peak,
                                 "bound": "tensor", "unit": "TFLOP/s",
                                 "kernel": "k_mlp_tma (k_mlp_tc where tensor maps are unavailable)"},
-            "seconds": {"dataset": t_data, "train": t_train, "plain": t_plain}}
+            "seconds": {"dataset": t_data, "train": t_train, "plain": tot_plain}}
 
 
 def _profile_gap(a, b):
@@ -277,6 +328,36 @@ def _profile_gap(a, b):
     a = np.asarray(a, dtype=np.float64); b = np.asarray(b, dtype=np.float64)
     return {"max_abs": float(np.abs(a - b).max()),
             "rel_l2": float(np.linalg.norm(a - b) / np.linalg.norm(b))}
+
+
+def _fit_k11(profile, t_end, u_left=1.0, u_right=0.0):
+    """K11 of the constant-K homogenized problem whose x1-profile at t_end best
+    fits `profile` (values at x1 = 2 pi i / n, i = 0..n-1; Dirichlet at x1 = 0 and
+    2 pi, step start): the semi-discrete solution on the same n columns is
+    l_i + sum_p c_p exp(-K11 lambda_p t) sin(pi p i / n), l the linear profile,
+    lambda_p = 4 sin^2(pi p / 2n) / H^2, c_p the sine coefficients of the step
+    minus l.  Golden-section search on log K11."""
+    import inputs
+    n = len(profile)
+    H = 2 * math.pi / n
+    i = np.arange(n)
+    lin = u_left + (u_right - u_left) * i / n
+    u0 = inputs.step_u0(n, u_left, u_right)[0]
+    p = np.arange(1, n)
+    S = np.sin(np.pi * np.outer(p, i) / n)                     # [p][i]
+    c = (2.0 / n) * S @ (u0 - lin)
+    lam = 4 * np.sin(np.pi * p / (2 * n)) ** 2 / H ** 2
+
+    def gap(lk):
+        return float(np.linalg.norm(lin + (c * np.exp(-math.exp(lk) * lam * t_end)) @ S - profile))
+    lo, hi = math.log(1e-3), math.log(1e3)
+    for _ in range(80):
+        a1 = hi - 0.618 * (hi - lo); a2 = lo + 0.618 * (hi - lo)
+        if gap(a1) < gap(a2):
+            hi = a2
+        else:
+            lo = a1
+    return math.exp(0.5 * (lo + hi))
 
 
 def sec4_case(amps=(1.0 / 3.0, 2.5), N=64, nf=512, t_end=0.4 * math.pi ** 2):
@@ -287,9 +368,10 @@ def sec4_case(amps=(1.0 / 3.0, 2.5), N=64, nf=512, t_end=0.4 * math.pi ** 2):
     a = 1/3 is the printed amplitude; a = 2.5 gives K near the printed K values.
     SHMM: two levels (edges 1, 6, 26; patch sides 2 pi and 2 pi / 5; 64^2
     patches; full relaxation window), then the macro solve on N x N.  Reference:
-    the direct simulation on nf x nf.  Baseline: pure diffusion.  Compared: the
-    x2-averaged profiles U(x1) at the macro nodes, and K11 fitted to the DNS
-    profile by the macro solver with a constant K."""
+    the direct simulation on nf x nf, and the same without the flow.  Compared:
+    the x2-averaged profiles at the macro nodes, and K11 of each DNS, fitted by
+    the homogenized constant-K solution on the DNS grid (the no-flow DNS
+    checks the fit: it should return kappa)."""
     import torch
     import inputs
     from inputs import flows
@@ -297,6 +379,20 @@ def sec4_case(amps=(1.0 / 3.0, 2.5), N=64, nf=512, t_end=0.4 * math.pi ** 2):
     dev = torch.device("cuda", _local_rank())
     kappa, r = 1.0, nf // N
     out = []
+    zero = torch.zeros(nf, nf, dtype=torch.float32, device=dev)
+
+    def dns(psi):
+        dt = mlsd.dns_dt(psi, kappa, 0.2)
+        ns = math.ceil(t_end / dt)
+        u = torch.tensor(inputs.step_u0(nf), dtype=torch.float32, device=dev)
+        ut = torch.empty_like(u)
+        t0 = time.perf_counter()
+        mlsd.dns_run_dirichlet(u, ut, psi, kappa, t_end / ns, ns, 1.0, 0.0)
+        torch.cuda.synchronize()
+        return u.cpu().numpy().astype(np.float64).mean(0), ns, time.perf_counter() - t0
+
+    prof0, _, _ = dns(zero)
+    k11_fit_noflow = _fit_k11(prof0, t_end)
     for amp in amps:
         spec = flows.cellular([(amp, 5, 5), (amp, 25, 25)])
         t0 = time.perf_counter()
@@ -313,58 +409,220 @@ def sec4_case(amps=(1.0 / 3.0, 2.5), N=64, nf=512, t_end=0.4 * math.pi ** 2):
             ns = max(1, math.ceil(t_end / dt))
             U = torch.tensor(inputs.step_u0(N), dtype=torch.float64, device=dev)
             mlsd.macro_step_dirichlet(U, Kf, t_end / ns, ns, 1.0, 0.0)
-            return U.cpu().numpy()
+            return U.cpu().numpy().mean(0)
 
-        Ushmm = macro(K)
-        Knone = torch.tensor(np.tile([kappa, 0.0, kappa], (N * N, 1)), dtype=torch.float64,
-                             device=dev)
-        Unone = macro(Knone)
+        prof_shmm = macro(K)
+        prof_none = macro(torch.tensor(np.tile([kappa, 0.0, kappa], (N * N, 1)),
+                                       dtype=torch.float64, device=dev))
         psi = torch.empty(nf, nf, dtype=torch.float32, device=dev)
         mlsd.grid_psi(spec, nf, psi)
-        dt = mlsd.dns_dt(psi, kappa, 0.2)
-        ns = math.ceil(t_end / dt)
-        u = torch.tensor(inputs.step_u0(nf), dtype=torch.float32, device=dev)
-        ut = torch.empty_like(u)
-        t0 = time.perf_counter()
-        mlsd.dns_run_dirichlet(u, ut, psi, kappa, t_end / ns, ns, 1.0, 0.0)
-        torch.cuda.synchronize()
-        t_dns = time.perf_counter() - t0
-        un = u.cpu().numpy().astype(np.float64)
-        prof_dns = un[:, ::r].mean(0)                   # x2-average at the macro nodes x1 = i H
-        prof_shmm, prof_none = Ushmm.mean(0), Unone.mean(0)
-        # K11 of the DNS: the constant K11 whose macro profile fits the DNS profile best
-        lo, hi = kappa, 10.0 * float(K[:, 0].max().item()) + kappa
-
-        def gap(k11):
-            Kc = torch.tensor(np.tile([k11, 0.0, kappa], (N * N, 1)), dtype=torch.float64,
-                              device=dev)
-            return float(np.linalg.norm(macro(Kc).mean(0) - prof_dns))
-        for _ in range(40):                              # golden-section search on K11
-            a1 = hi - 0.618 * (hi - lo); a2 = lo + 0.618 * (hi - lo)
-            if gap(a1) < gap(a2):
-                hi = a2
-            else:
-                lo = a1
+        prof_dns, ns, t_dns = dns(psi)
         Kn = K.cpu().numpy()
-        out.append({"amplitude": amp, "K_shmm_mean": Kn.mean(0).tolist(),
+        out.append({"amplitude": amp, "K_shmm": Kn.mean(0).tolist(),
                     "K_shmm_node_spread": float(np.abs(Kn - Kn.mean(0)).max()),
-                    "K11_fitted_to_dns": 0.5 * (lo + hi),
-                    "shmm_vs_dns": _profile_gap(prof_shmm, prof_dns),
-                    "no_advection_vs_dns": _profile_gap(prof_none, prof_dns),
+                    "K11_dns_fit": _fit_k11(prof_dns, t_end),
+                    "shmm_vs_dns": _profile_gap(prof_shmm, prof_dns[::r]),
+                    "no_advection_vs_dns": _profile_gap(prof_none, prof_dns[::r]),
                     "dns": {"grid": nf, "steps": ns, "dt": t_end / ns, "seconds": t_dns},
                     "chain_seconds": t_chain})
     return {"workload": f"Sec. 4 set-up, psi = a(sin5x sin5y + sin25x sin25y), kappa=1, "
                         f"Dirichlet x1 / periodic x2, step IC, t={t_end:.4f}; SHMM 2 levels, "
                         f"{N}^2 macro, 64^2 patches; DNS {nf}^2",
-            "cases": out}
+            "K11_fit_of_the_no_flow_dns": k11_fit_noflow, "cases": out}
 
 
-def uneven_case(n_avg=32):
+def _fit_k_periodic(U0, U, t_end):
+    """Constant K (K11, K12, K22) of the periodic homogenized problem whose
+    solution from U0 best fits U at t_end on the N x N macro grid: each Fourier
+    mode decays as exp(-t lambda), lambda = [4 K11 sin^2(t1/2) + 4 K22 sin^2(t2/2)
+    + 2 K12 sin t1 sin t2] / H^2 (the macro scheme's semi-discrete symbol)."""
+    from scipy.optimize import least_squares
+    N = U0.shape[0]
+    H = 2 * math.pi / N
+    th = 2 * math.pi * np.fft.fftfreq(N)
+    t1, t2 = th[None, :], th[:, None]
+    F0, F1 = np.fft.fft2(U0), np.fft.fft2(U)
+
+    def res(q):
+        k11, k22, c = math.exp(q[0]), math.exp(q[1]), math.tanh(q[2])
+        k12 = c * math.sqrt(k11 * k22)
+        lam = (4 * k11 * np.sin(t1 / 2) ** 2 + 4 * k22 * np.sin(t2 / 2) ** 2
+               + 2 * k12 * np.sin(t1) * np.sin(t2)) / H ** 2
+        d = F0 * np.exp(-t_end * lam) - F1
+        return np.concatenate([d.real.ravel(), d.imag.ravel()])
+    q = least_squares(res, [0.0, 0.0, 0.0]).x
+    k11, k22 = math.exp(q[0]), math.exp(q[1])
+    return [k11, math.tanh(q[2]) * math.sqrt(k11 * k22), k22]
+
+
+def spectrum_dns_case(N=16, nf=8192, t_end=1.0):
+    """The full SHMM pipeline on the continuous-spectrum flow (|k| <= 256,
+    kappa = 1e-3, 8 octave levels, sizes by the size rule): the level chain with
+    the full 8 tau + 4 tau relaxation window on the N x N macro grid, then the
+    macro solve of the Gaussian (sigma = 0.5) to t_end, against the direct
+    simulation on nf x nf to the same time coarse-grained onto the macro grid
+    (the structure of the paper's Sec. 4.4 comparison).  Also the pure-diffusion
+    macro solution, and the constant K fitted to each solution."""
+    import torch
+    import inputs
+    import paper_1510_00451_gb300 as mlsd
+    dev = torch.device("cuda", _local_rank())
+    cfg = inputs.config_problem("continuous_spectrum")
+    Lc = len(cfg["edges"]) - 1
+    t0 = time.perf_counter()
+    lv = mlsd.Levels(cfg["spectrum"], cfg["kappa"], N, cfg["edges"], [0] * Lc, cfl=cfg["cfl"])
+    K = torch.zeros(N * N, 3, dtype=torch.float64, device=dev)
+    lv.effective_diffusivity(K)
+    torch.cuda.synchronize()
+    t_chain = time.perf_counter() - t0
+    assert lv.status() == 0
+    work = sum(lv.level_work(l + 1)[0] for l in range(Lc))
+    lv.close()
+    U0 = inputs.gaussian_u0(N, cfg["sigma"])
+
+    def macro(Kf):
+        dt = mlsd.macro_dt(Kf, N, cfg["cfl"])
+        ns = max(1, math.ceil(t_end / dt))
+        U = torch.tensor(U0, dtype=torch.float64, device=dev)
+        mlsd.macro_step(U, Kf, t_end / ns, ns, want_mass=False)
+        return U.cpu().numpy()
+
+    U_shmm = macro(K)
+    U_none = macro(torch.tensor(np.tile([cfg["kappa"], 0.0, cfg["kappa"]], (N * N, 1)),
+                                dtype=torch.float64, device=dev))
+    psi = torch.empty(nf, nf, dtype=torch.float32, device=dev)
+    mlsd.grid_psi(cfg["spectrum"], nf, psi)
+    dt = mlsd.dns_dt(psi, cfg["kappa"], cfg["cfl"])
+    ns = math.ceil(t_end / dt)
+    u = torch.tensor(inputs.gaussian_u0(nf, cfg["sigma"]), dtype=torch.float32, device=dev)
+    ut = torch.empty_like(u)
+    t0 = time.perf_counter()
+    mlsd.dns_run(u, ut, psi, cfg["kappa"], t_end / ns, ns)
+    torch.cuda.synchronize()
+    t_dns = time.perf_counter() - t0
+    Ud = torch.empty(N, N, dtype=torch.float32, device=dev)
+    mlsd.coarse_grain(u, N, Ud)
+    U_dns = Ud.cpu().numpy().astype(np.float64)
+    # coarse-grained initial field: the DNS's own start on the macro grid
+    U0c = torch.empty(N, N, dtype=torch.float32, device=dev)
+    mlsd.coarse_grain(torch.tensor(inputs.gaussian_u0(nf, cfg["sigma"]), dtype=torch.float32,
+                                   device=dev), N, U0c)
+    U0c = U0c.cpu().numpy().astype(np.float64)
+
+    def dev_gap(a, b):
+        a = a - a.mean(); b = b - b.mean()
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    Kn = K.cpu().numpy()
+    return {"workload": f"continuous spectrum |k|<=256, kappa=1e-3, 8 levels, {N}^2 macro "
+                        f"nodes, full window; Gaussian sigma=0.5 to t={t_end}; DNS {nf}^2",
+            "K_shmm_mean": Kn.mean(0).tolist(), "K_shmm_min": Kn.min(0).tolist(),
+            "K_shmm_max": Kn.max(0).tolist(),
+            "K_fit_dns": _fit_k_periodic(U0c, U_dns, t_end),
+            "K_fit_shmm": _fit_k_periodic(U0, U_shmm, t_end),
+            "shmm_vs_dns_rel_l2_of_deviation": dev_gap(U_shmm, U_dns),
+            "no_advection_vs_dns_rel_l2_of_deviation": dev_gap(U_none, U_dns),
+            "chain_seconds": t_chain, "chain_cell_updates": work,
+            "dns": {"grid": nf, "steps": ns, "dt": t_end / ns, "seconds": t_dns}}
+
+
+def offdiag_case(N=4):
+    """The Sec. 4.3 stress test of the off-diagonal closed forms, at half the
+    paper's wavenumbers (alpha = 2 instead of 5, so that the fully resolved
+    reference fits one 256^2 patch): psi = a(phi_c(2,2) + phi_c(2,18) +
+    phi_c(18,2) + phi_c(20,20)), phi_c(a,b) = sin(a x1) sin(b x2), kappa = 1,
+    a = 1/5 (the printed amplitude) and 1.
+    SHMM: two levels (edges 1, 3, 21; patch sides 2 pi and pi; the (2,18),
+    (18,2) pair is level 1's psi_12, psi_21 and enters through Algorithms 1-2),
+    full relaxation window, N x N macro nodes.  Reference: one patch of side
+    2 pi with every mode in its band (256^2: 12.8 points per wavelength of
+    mode 20).  Also both without the off-diagonal pair."""
+    import torch
+    from inputs import flows
+    import paper_1510_00451_gb300 as mlsd
+    dev = torch.device("cuda", _local_rank())
+
+    def shmm(terms):
+        lv = mlsd.Levels(flows.cellular(terms), 1.0, N, [1.0, 3.0, 21.0], [32, 128],
+                         patch_div=[1, 2], cfl=0.2)
+        K = torch.zeros(N * N, 3, dtype=torch.float64, device=dev)
+        lv.effective_diffusivity(K)
+        assert lv.status() == 0
+        lv.close()
+        Kn = K.cpu().numpy()
+        return Kn.mean(0), float(np.abs(Kn - Kn.mean(0)).max())
+
+    def full(terms):
+        lv = mlsd.Levels(flows.cellular(terms), 1.0, 1, [1.0, 21.0], [256], patch_div=[1],
+                         cfl=0.2)
+        K = torch.zeros(1, 3, dtype=torch.float64, device=dev)
+        B = torch.tensor([[1.0, 0.0, 1.0]], dtype=torch.float64, device=dev)
+        lv.solve_level(1, B, K)
+        assert lv.status() == 0
+        lv.close()
+        return K.cpu().numpy()[0]
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.asarray(a) - b) / np.linalg.norm(b))
+    t0 = time.perf_counter()
+    cases = []
+    for a in (0.2, 1.0):            # the printed amplitude 1/5, and a stronger flow
+        diag = [(a, 2, 2), (a, 20, 20)]
+        off = [(a, 2, 18), (a, 18, 2)]
+        K_s, spread = shmm(diag + off)
+        K_f = full(diag + off)
+        K_s0, _ = shmm(diag)
+        K_f0 = full(diag)
+        cases.append({"amplitude": a, "K_shmm": K_s.tolist(), "K_shmm_node_spread": spread,
+                      "K_full_patch": K_f.tolist(), "rel_err_shmm_vs_full": rel(K_s, K_f),
+                      "without_offdiagonal_pair": {"K_shmm": K_s0.tolist(),
+                                                   "K_full_patch": K_f0.tolist(),
+                                                   "rel_err": rel(K_s0, K_f0)}})
+    torch.cuda.synchronize()
+    return {"workload": "Sec. 4.3 structure at alpha = 2: psi = a(phi_c(2,2) + phi_c(2,18) + "
+                        "phi_c(18,2) + phi_c(20,20)), kappa = 1; SHMM 2 levels (32^2, 128^2 "
+                        f"patches, {N}^2 nodes, full window) vs one fully resolved 256^2 patch",
+            "cases": cases, "seconds": time.perf_counter() - t0}
+
+
+def geometry_case(N=32):
+    """Patch geometry and periodisation on the two-scale cellular flow
+    (psi = sin x sin y + sin 8x sin 8y, kappa = 0.05, 2 levels, 32^2 patches,
+    N x N macro nodes, full relaxation window, FP32): patches of one period of
+    each level's band (the default), and the paper's local domains of side 2H
+    (H = 2 pi / N) on which neither band is periodic, with the band wrapped at
+    the seam or replaced by its periodic component (periodic-plus-smooth)."""
+    import torch
+    from inputs import flows
+    import paper_1510_00451_gb300 as mlsd
+    dev = torch.device("cuda", _local_rank())
+    spec = flows.cellular_two_scale(1.0, 1.0, 8)
+    out = []
+    for name, div, per in (("one period of each band", None, False),
+                           ("side 2H, band wrapped at the seam", [N // 2, N // 2], False),
+                           ("side 2H, periodic component of the band", [N // 2, N // 2], True)):
+        lv = mlsd.Levels(spec, 0.05, N, [1.0, 8.0, 9.0], [32, 32], patch_div=div, periodize=per,
+                         cfl=0.2)
+        K = torch.zeros(N * N, 3, dtype=torch.float64, device=dev)
+        lv.effective_diffusivity(K)
+        rc = lv.status()
+        steps = [lv.level_work(l + 1)[1] for l in range(2)]
+        lv.close()
+        Kn = K.cpu().numpy()
+        out.append({"geometry": name, "status": mlsd.ERRORS.get(rc, rc),
+                    "max_steps_per_level": steps, "K_mean": Kn.mean(0).tolist(),
+                    "K_min": Kn.min(0).tolist(), "K_max": Kn.max(0).tolist()})
+    return {"workload": f"two-scale cellular flow, kappa=0.05, {N}^2 macro nodes, 32^2 patches, "
+                        "full window, FP32", "variants": out}
+
+
+def uneven_case(n_avg=256):
     """The continuous-spectrum workload at full size: |k| <= 256, 8 octave levels,
     256 x 256 macro nodes (65536 patches per level), patch sizes 32^2 .. 256^2
     from the size rule, every level's size classes launched concurrently inside
     one captured graph.  Fixed n_avg-step window per patch (the full window of
-    the 256^2 levels needs ~1e6 steps)."""
+    the 256^2 levels needs ~5e5 steps).  Also per level: the patch kernels'
+    device time (CUDA events around each launch, a second pass outside the
+    graph) and its cell-update rate and FP32-issue fraction."""
     import torch
     import inputs
     import paper_1510_00451_gb300 as mlsd
@@ -379,7 +637,8 @@ def uneven_case(n_avg=32):
         sz = lv.patch_sizes(l)
         vals, cnt = np.unique(sz, return_counts=True)
         hist.append({int(v): int(c) for v, c in zip(vals, cnt)})
-    K = torch.zeros(N * N, 3, dtype=torch.float64, device=torch.device("cuda", _local_rank()))
+    dev = torch.device("cuda", _local_rank())
+    K = torch.zeros(N * N, 3, dtype=torch.float64, device=dev)
     lv.effective_diffusivity(K)                   # capture + warm-up
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -388,12 +647,34 @@ def uneven_case(n_avg=32):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) * 1e-3
     assert lv.status() == 0
-    cu = sum(lv.level_work(l + 1)[0] for l in range(L))
+    work = [lv.level_work(l + 1) for l in range(L)]
+    cu = sum(w[0] for w in work)
+    # per level: kernel time of its patch launches (concurrent classes overlap, so
+    # the sum of their events bounds the level's time from above)
+    for l in range(L):
+        lv.profile_collect(l + 1)
+    lv.profile(True)
+    lv.effective_diffusivity(K)
+    torch.cuda.synchronize()
+    lv.profile(False)
+    peaks = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue_peak = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    per_level = []
+    for l in range(L):
+        ms, n = lv.profile_collect(l + 1)
+        cu_l, _, wu_l = work[l]
+        ops = cu_l * OPS_PER_CELL_UPDATE + wu_l * OPS_PER_WINDOW_UPDATE
+        per_level.append({"level": l + 1, "sizes": hist[l], "kernel_ms": ms, "launches": n,
+                          "cell_updates": cu_l,
+                          "cell_updates_per_s": cu_l / (ms * 1e-3) if ms > 0 else None,
+                          "fp32_issue_frac": ops / (ms * 1e-3) / issue_peak if ms > 0 else None})
     tiles = [lv.info(l + 1) for l in range(L)]
     return {"workload": "continuous spectrum |k|<=256, 8 octave levels, 65536 patches/level, "
                         f"sizes 32^2..256^2 by the size rule, {n_avg}-step window",
             "cell_updates_per_s": cu / t, "seconds": t, "cell_updates": cu,
-            "k_eff_tensors_per_s": N * N / t, "setup_s": t_setup, "sizes_per_level": hist,
+            "k_eff_tensors_per_s": N * N / t, "setup_s": t_setup,
+            "per_level": per_level,
             "largest_class_tiling": [f"{i['tile_bx']}x{i['tile_by']} c{i['cluster']} m{i['min_ctas']}"
                                      f"{' packed' if i['packed'] else ''}{' split' if i['split'] else ''}"
                                      f" n={i['n']}" for i in tiles],
@@ -567,7 +848,8 @@ def main():
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--case", default="full",
                     choices=["full", "profile", "dns-profile", "dns-full", "surrogate", "uneven",
-                             "mlp-profile", "cluster-profile", "train-profile", "sec4"],
+                             "mlp-profile", "cluster-profile", "train-profile", "sec4",
+                             "spectrum-dns", "offdiag", "geometry"],
                     help="profile: one pass of the same workload with a fixed 200-step window "
                          "per patch (a small case for ncu captures); prints no bench line")
     args = ap.parse_args()
@@ -593,6 +875,15 @@ def main():
         return 0
     if args.case == "sec4":
         print(json.dumps({"case": "sec4", **sec4_case()}), flush=True)
+        return 0
+    if args.case == "geometry":
+        print(json.dumps({"case": "geometry", **geometry_case()}), flush=True)
+        return 0
+    if args.case == "offdiag":
+        print(json.dumps({"case": "offdiag", **offdiag_case()}), flush=True)
+        return 0
+    if args.case == "spectrum-dns":
+        print(json.dumps({"case": "spectrum-dns", **spectrum_dns_case()}), flush=True)
         return 0
 
     import torch
@@ -709,10 +1000,11 @@ def main():
     if not args.no_dns:
         d = dns_case(8192, 1000)
         gbs = DNS_BYTES_PER_CELL_STEP * d["cell_steps_per_s"] / 1e9
-        hbm = _peaks().get("hbm_gbs", 6789.6)
+        hbm, hbm_src = _peak("hbm_gbs")
         dns = {"workload": "continuous_spectrum_dns (8192^2 FP32, |k|<=256, kappa=1e-3, 1000 steps)",
                "value": d["cell_steps_per_s"] * world, "unit": "cell-steps/s", "ms": d["ms"],
-               "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+               "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "peak_source": hbm_src,
+                            "unit": "GB/s",
                             "frac": gbs / hbm, "traffic": DNS_DRAM_BYTES_PER_LAUNCH,
                             "traffic_unit": "DRAM bytes per launch (ncu, 8192^2)",
                             "kernel": "k_dns_step",

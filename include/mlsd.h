@@ -89,6 +89,15 @@ typedef struct {
      * explicitly ([L][P], overrides patch_n).                                 */
     const int32_t *patch_n_map;
     int n_min, n_max;          /* 0 -> 32, 256 */
+    /* Periodisation of the diagonal band on the patches (for a band that is
+     * not periodic on its patch, e.g. patches of side 2H, Sec. 3): 0 samples
+     * the band and wraps it at the seam; 1 replaces each patch's samples u by
+     * their periodic component p of the periodic-plus-smooth decomposition
+     * u = p + s (Moisan 2011): the periodic 5-point Laplacian of p equals the
+     * Laplacian of u over in-patch neighbours only.  Computed once at set-up
+     * into per-patch tiles ([P][n][n] per size class).  FP32, n = 32 or 64;
+     * other combinations give MLSD_EUNSUPPORTED.                              */
+    int periodize;
 } mlsd_problem;
 
 /* Description of one level, as built. */
@@ -221,34 +230,44 @@ int mlsd_effective_diffusivity(mlsd_levels *h, int mode, double *K_macro_dev,
 
 /* ------------------------------------------------------------------------
  * Learned surrogate of the patch solve (not in the paper).  A small ensemble
- * of MLPs maps a patch's features to the part of K that the second-order
- * (small-Peclet) estimate Q below misses; where the members disagree, the
- * plain patch solve above is run instead.
+ * of MLPs maps a patch's features to the part of K that the resummed
+ * perturbation series E below misses; where the members disagree, or the
+ * series is far from converged, the plain patch solve above is run instead.
  *
- * Features of a patch (MLSD_SUR_FEATURES = 585 values, stored as one bfloat16
+ * Perturbation moments.  At steady state the corrector of field j solves
+ * (L0 + A) w_j = -v_j, L0 = B11 D+D-x + 2 B12 D0x D0y + B22 D+D-y (Fourier
+ * symbol -D(k)/h^2, D = B11 (2 - 2 cos t1) + B22 (2 - 2 cos t2) + 2 B12 s1 s2,
+ * t_i = 2 pi k_i / n, s_i = sin t_i), A w = v1 D0x w + v2 D0y w.  Expanding in
+ * v: c_j^0 = -L0^{-1} v_j, c_j^m = -L0^{-1} A c_j^{m-1}, and K - B = sum of
+ *   T_m = sym <v_i c_j^{m-2}>  (m >= 2; T_2 is the small-Peclet limit).
+ * The library computes T_2..T_19 on the patch grid with FFTs (n = 32 or 64)
+ * and resums the series where it diverges: with the pairs
+ * p_k = T_(2k+2) + T_(2k+3), the [K/K] Pade approximant at 1 of sum_k p_k x^k
+ * (Wynn's epsilon algorithm on the partial sums) for K = 2, 3, 4; the
+ * estimate is E = [4/4], and gap = max_c |[4/4]_c - [3/3]_c| measures how far
+ * it is from converged.
+ *
+ * Features of a patch (MLSD_SUR_FEATURES = 606 values, stored as one bfloat16
  * row of MLSD_SUR_IN = 640, zero padded):
  *   [0, 578)  Re and Im of the patch DFT
  *               psihat(k) = n^-2 sum_ab (psi[b][a] - mean psi) exp(-2 pi i (k1 a + k2 b)/n)
  *             of the level's band at the patch nodes, k2 = -8..8 (slow),
  *             k1 = -8..8, each times MLSD_SUR_PSI_SCALE / (tr(B)/2);
  *   578..580  B11/kappa, B12/kappa, B22/kappa;   581  log kappa;
- *   582..584  MLSD_SUR_Q_SCALE Q / tr(B) for (Q11, Q12, Q22), where
- *               Q = sum_{k != 0} |psihat(k)|^2 [[s2^2, -s1 s2], [-s1 s2, s1^2]] / D(k),
- *               D = B11 (2 - 2 cos t1) + B22 (2 - 2 cos t2) + 2 B12 s1 s2,
- *               t_i = 2 pi k_i / n, s_i = sin t_i,
- *             over the same modes: the flux of the corrector equation solved
- *             to first order in v (B:DD w_j = -v_j in Fourier space).  For a
- *             shear flow inside the window it is K - B exactly.
- * Network output (the training target): (K - B - Q) MLSD_SUR_Y_SCALE / tr(B).
+ *   582..596  asinh(MLSD_SUR_T_SCALE T_m / tr(B)), m = 2..6, components 11, 12, 22;
+ *   597..605  asinh(MLSD_SUR_T_SCALE x / tr(B)) for x = [2/2], [3/3], [4/4].
+ * Network output (the training target):
+ *   asinh((K - B - E) MLSD_SUR_Y_SCALE / tr(B)).
  * Member network: 640 -> h -> h -> h -> 3, exact-erf GELU after the first three
  * layers, bfloat16 weights and activations, FP32 accumulation.  Parameters of
  * a member in one FP32 array, row-major (out x in):
  *   W1[h][640] b1[h] W2[h][h] b2[h] W3[h][h] b3[h] W4[3][h] b4[3].         */
 #define MLSD_SUR_IN 640
-#define MLSD_SUR_FEATURES 585
+#define MLSD_SUR_FEATURES 606
 #define MLSD_SUR_PSI_SCALE 32.0
-#define MLSD_SUR_Q_SCALE 10.0
-#define MLSD_SUR_Y_SCALE 30.0
+#define MLSD_SUR_T_SCALE 10.0
+#define MLSD_SUR_Y_SCALE 300.0
+#define MLSD_SUR_GAP_WEIGHT 0.3
 typedef struct mlsd_surrogate mlsd_surrogate;
 
 int64_t mlsd_surrogate_param_count(int hidden);          /* per member */
@@ -259,8 +278,9 @@ void mlsd_surrogate_free(mlsd_surrogate *s);
 /* host FP32 parameter arrays (layout above); set resets the Adam state      */
 int mlsd_surrogate_set_params(mlsd_surrogate *s, int member, const float *params_host);
 int mlsd_surrogate_get_params(mlsd_surrogate *s, int member, float *params_host);
-/* Features of every patch of a level (one patch size <= 64 per level) with
- * base B_dev [P][3]: X_dev bfloat16 [P][640]; F32_dev [P][585] or NULL.     */
+/* Features of every patch of a level (one patch size per level, n = 32 or 64)
+ * with base B_dev [P][3]: X_dev bfloat16 [P][640]; F32_dev [P][606] or NULL.
+ * Other sizes: MLSD_EUNSUPPORTED.                                           */
 int mlsd_surrogate_features(mlsd_levels *h, int level, const double *B_dev, void *X_dev,
                             float *F32_dev, void *cuda_stream);
 /* Mean-squared-error loss of one member on M <= max_batch rows (X bfloat16
@@ -275,8 +295,8 @@ int mlsd_surrogate_train_step(mlsd_surrogate *s, int member, const void *X_dev,
                               void *cuda_stream);
 /* Training data of one level, all on the device: the plain patch solve of
  * every patch with base B_dev [P][3], its features X_dev (bfloat16 [P][640])
- * and targets Y_dev (FP32 [P][3]) = (K - B - Q) MLSD_SUR_Y_SCALE / tr(B), Q
- * the features' second-order estimate in FP64.  Same level limits as
+ * and targets Y_dev (FP32 [P][3]) = asinh((K - B - E) MLSD_SUR_Y_SCALE / tr(B)),
+ * E the resummed series estimate in FP64.  Same level limits as
  * mlsd_surrogate_features.                                                  */
 int mlsd_surrogate_dataset(mlsd_levels *h, int level, const double *B_dev, void *X_dev,
                            float *Y_dev, void *cuda_stream);
@@ -286,7 +306,8 @@ int mlsd_surrogate_dataset(mlsd_levels *h, int level, const double *B_dev, void 
  * -psi on the mapped grid for a reflection or a swap (a stream function is a
  * pseudo-scalar), v = (-psi_x2, psi_x1) maps as a vector, the central
  * differences, the periodic wrap, dt and the windows are unchanged, and every
- * symmetric tensor (B, Q, K, the target) maps as R T R^T.  So the image of a
+ * symmetric tensor (B, T_m, the approximants, K, the target) maps as R T R^T
+ * (asinh is odd, so the stored features and targets map the same way).  So the image of a
  * plain-solved row is the exact row of the mapped patch.  On a row: DFT entry
  * (k1, k2) takes sign * entry (k1s, k2s), (q1, q2) = bit 2 ? (k2, k1) : (k1, k2),
  * k1s = bit 0 ? -q1 : q1, k2s = bit 1 ? -q2 : q2, sign = (-1)^(bits set);
@@ -329,10 +350,11 @@ int mlsd_surrogate_status(mlsd_surrogate *s, void *cuda_stream);
 /* Every member on M rows: out_dev FP32 [members][M][3].                     */
 int mlsd_surrogate_predict(mlsd_surrogate *s, const void *X_dev, int64_t M, float *out_dev,
                            void *cuda_stream);
-/* One level with the surrogate: features (with Q), ensemble,
- *     K_m = B + Q + tr(B) out_m / MLSD_SUR_Y_SCALE;
- * a patch whose members disagree,
- *     max_{m,c} |K_m,c - mean_m K_m,c| > threshold * ||mean K||_F,
+/* One level with the surrogate: features (with E), ensemble,
+ *     K_m = B + E + tr(B) sinh(out_m) / MLSD_SUR_Y_SCALE;
+ * a patch whose members disagree or whose resummation has not converged,
+ *     max(max_{m,c} |K_m,c - mean_m K_m,c|, MLSD_SUR_GAP_WEIGHT gap)
+ *         > threshold * ||mean K||_F,
  * is solved by the plain patch solve (mlsd_solve_level's kernel) instead; the
  * rest take the ensemble mean.  n_fallback_out receives the number of plain
  * solves.  Blocks once (to size the fallback launch).                       */

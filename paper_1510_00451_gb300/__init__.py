@@ -36,8 +36,8 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_surrogate_load", "mlsd_attach_surrogate", "mlsd_surrogate_fallbacks",
             "mlsd_surrogate_symmetry", "mlsd_strerror"]
 SUR_CUDA, SUR_TENSOR = 0, 1
-SUR_IN, SUR_FEATURES = 640, 585
-SUR_PSI_SCALE, SUR_Q_SCALE, SUR_Y_SCALE = 32.0, 10.0, 30.0
+SUR_IN, SUR_FEATURES = 640, 606
+SUR_PSI_SCALE, SUR_T_SCALE, SUR_Y_SCALE, SUR_GAP_WEIGHT = 32.0, 10.0, 300.0, 0.3
 NOALLOC_MAX_MACRO = 256
 
 
@@ -57,7 +57,7 @@ class mlsd_problem(ctypes.Structure):
                 ("t_burn_tau", ctypes.c_double), ("t_avg_tau", ctypes.c_double),
                 ("n_burn_fixed", ctypes.c_int64), ("n_avg_fixed", ctypes.c_int64),
                 ("precision", ctypes.c_int), ("patch_n_map", ctypes.c_void_p),
-                ("n_min", ctypes.c_int), ("n_max", ctypes.c_int)]
+                ("n_min", ctypes.c_int), ("n_max", ctypes.c_int), ("periodize", ctypes.c_int)]
 
 
 class mlsd_level_desc(ctypes.Structure):
@@ -152,7 +152,8 @@ class Levels:
 
     def __init__(self, spectrum, kappa, n_macro, edges, patch_n, patch_div=None, cfl=0.2,
                  t_burn_tau=8.0, t_avg_tau=4.0, n_burn_fixed=0, n_avg_fixed=0,
-                 precision="fp32", patch_n_map=None, n_min=0, n_max=0, stream=None):
+                 precision="fp32", patch_n_map=None, n_min=0, n_max=0, periodize=False,
+                 stream=None):
         k1, k2, re, im = spectrum.as_arrays()
         self._keep = [k1, k2, re, im,
                       np.ascontiguousarray(edges, dtype=np.float64),
@@ -170,7 +171,7 @@ class Levels:
                          t_avg_tau=float(t_avg_tau), n_burn_fixed=int(n_burn_fixed),
                          n_avg_fixed=int(n_avg_fixed), precision=self.precision,
                          patch_n_map=None if nmap is None else nmap.ctypes.data,
-                         n_min=int(n_min), n_max=int(n_max))
+                         n_min=int(n_min), n_max=int(n_max), periodize=1 if periodize else 0)
         h = _P()
         _check(_lib.mlsd_build_levels(ctypes.byref(p), _stream(stream), ctypes.byref(h)),
                "mlsd_build_levels")
@@ -201,7 +202,7 @@ class Levels:
         return out
 
     def features(self, level, B, X, F32=None, stream=None):
-        """Surrogate inputs of every patch: X bfloat16 [P][640], F32 [P][585] or None."""
+        """Surrogate inputs of every patch: X bfloat16 [P][640], F32 [P][606] or None."""
         _check(_lib.mlsd_surrogate_features(self.h, int(level), _dptr(B), _dptr(X), _dptr(F32),
                                             _stream(stream)), "mlsd_surrogate_features")
 

@@ -29,7 +29,11 @@ struct PatchParams {
     long long item0, items;  // work items [item0, item0 + items), item = 2p + (j - 1)
     long long *steps;        // [2P]: n_burn + n_avg, then n_avg, per patch (written by the j = 1 CTA) or nullptr
     const int *pidx;         // patch index of work-item pair (item >> 1), or nullptr: identity
+    long long tile = 0;      // 0: band is the level grid; else per-patch tiles, patch p at band + p * tile
+    const int *count_dev = nullptr;   // if set: only the first 2 * (*count_dev) items, taken by a
+                                      // grid-stride loop (a launch sized before the count is known)
 };
+
 
 // Variant of the patch kernel: thread block shape per patch size and precision.
 struct PatchVariant {
@@ -104,6 +108,11 @@ cudaError_t launch_patch_vmax(const double *v1, const double *v2, long long Nr, 
                               int n_macro, long long P, double *vmax, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// Periodic component of every patch of a size class (n = 32 or 64, FP32) into
+// tiles [P][n][n], indexed by patch (pidx lists the class's patches, or null).
+cudaError_t launch_periodize(const float *band, long long Nl, int n, int n_macro, const int *pidx,
+                             long long count, float *tiles, cudaStream_t s);
+
 // Failure-path checks of the two bounded device waits (nothing in flight).
 cudaError_t launch_wait_check_nbr(int *status, cudaStream_t s);
 cudaError_t launch_wait_check_mbar(int *status, cudaStream_t s);
@@ -132,9 +141,9 @@ long long launch_count();
 
 // Surrogate (surrogate.cu)
 long long sur_param_count(int h);
-cudaError_t launch_features(const float *band, long long Nl, int n, int n_macro, const int *pidx,
-                            long long count, const double *B, double kappa, void *X, float *F32,
-                            double *Q, cudaStream_t s);
+cudaError_t launch_features(const float *band, long long Nl, long long tile, int n, int n_macro,
+                            const int *pidx, long long count, const double *B, double kappa,
+                            void *X, float *F32, double *Q, cudaStream_t s);
 // ws: split-k partials of the CUDA-core GEMMs, ws_n floats (sur_split_workspace(h) lets
 // every training shape split fully; nullptr disables splitting)
 long long sur_split_workspace(int h);
@@ -160,6 +169,8 @@ cudaError_t sur_disagree(long long P, int members, const float *out, const doubl
                          cudaStream_t s);
 cudaError_t sur_merge(int n, const int *idx, const double *B, const double *S, double *K,
                       cudaStream_t s);
+cudaError_t sur_merge_dev(long long P, const int *n_dev, const int *idx, const double *B,
+                          const double *S, double *K, cudaStream_t s);
 
 // Tensor-core inference (mlp_tc.cu)
 size_t mlp_tc_smem();
@@ -182,6 +193,17 @@ __host__ __device__ inline long long pmod_ll(long long a, long long m)
 __host__ __device__ inline long long patch_origin(long long i, long long N, long long Nl, int n)
 {
     return (2 * i * Nl + N) / (2 * N) - n / 2;
+}
+
+// psi of patch node (a, b): from the level's band grid at the patch origin
+// (periodic wrap), or from the patch's own tile (periodised band, n x n)
+template <typename real>
+__device__ __forceinline__ real patch_band(const real *band, long long Nl, long long tile,
+                                           long long p, long long ox, long long oy, int n, int a,
+                                           int b)
+{
+    return tile ? band[p * tile + (long long)b * n + a]
+                : band[pmod_ll(oy + b, Nl) * Nl + pmod_ll(ox + a, Nl)];
 }
 
 }  // namespace mlsd

@@ -686,7 +686,7 @@ struct Tile {
         for (int c = tid; c < N * (NS + 2); c += NT) {
             const int rr = c / N, a = c % N;
             const int b = (g0 - 1 + rr + N) % N;
-            psi[c] = band[pmod_ll(oy + b, Nl) * Nl + pmod_ll(ox + a, Nl)];
+            psi[c] = patch_band(band, Nl, prm.tile, p, ox, oy, N, a, b);
         }
         __syncthreads();
         const real inv2h = (real)(1.0 / (2.0 * prm.h));
@@ -860,12 +860,17 @@ k_patch_solve(PatchParams prm)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sm = reinterpret_cast<real *>(smem_raw);
-    const long long item = prm.item0 + blockIdx.x / C;
     const int rank = (int)(blockIdx.x % C);
-    if (item >= prm.item0 + prm.items) return;      // whole clusters only: C divides the grid
-    const long long p = prm.pidx ? (long long)prm.pidx[item >> 1] : (item >> 1);
-    if (item & 1) Tile<N, C, BX, BY, real>::template run<2, SYNC>(prm, sm, p, rank);
-    else Tile<N, C, BX, BY, real>::template run<1, SYNC>(prm, sm, p, rank);
+    // work items [item0, end): one per cluster when the grid covers them all, else a
+    // grid-stride loop over a count read on the device (whole clusters: C divides the grid)
+    const long long end = prm.count_dev ? prm.item0 + 2LL * (long long)*prm.count_dev
+                                        : prm.item0 + prm.items;
+    const long long stride = gridDim.x / C;
+    for (long long item = prm.item0 + blockIdx.x / C; item < end; item += stride) {
+        const long long p = prm.pidx ? (long long)prm.pidx[item >> 1] : (item >> 1);
+        if (item & 1) Tile<N, C, BX, BY, real>::template run<2, SYNC>(prm, sm, p, rank);
+        else Tile<N, C, BX, BY, real>::template run<1, SYNC>(prm, sm, p, rank);
+    }
 }
 
 // SYNC: 0 = barrier per stage, 1 = split-phase cluster barrier, 2 = neighbour
@@ -1051,7 +1056,7 @@ struct Tile2 {
         const float *band = static_cast<const float *>(prm.band);
         for (int c = tid; c < N * N; c += NT) {
             const int b = c / N, a = c % N;
-            psi[c] = band[pmod_ll(oy + b, Nl) * Nl + pmod_ll(ox + a, Nl)];
+            psi[c] = patch_band(band, Nl, prm.tile, p, ox, oy, N, a, b);
         }
         __syncthreads();
         const float inv2h = (float)(1.0 / (2.0 * prm.h));
@@ -1192,9 +1197,10 @@ k_patch_solve2(PatchParams prm)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *sm = reinterpret_cast<float2 *>(smem_raw);
-    const long long pair = prm.item0 / 2 + blockIdx.x;
-    if (2 * pair >= prm.item0 + prm.items) return;
-    Tile2<N, BX, BY>::run(prm, sm, prm.pidx ? (long long)prm.pidx[pair] : pair);
+    const long long end = prm.count_dev ? prm.item0 + 2LL * (long long)*prm.count_dev
+                                        : prm.item0 + prm.items;
+    for (long long pair = prm.item0 / 2 + blockIdx.x; 2 * pair < end; pair += gridDim.x)
+        Tile2<N, BX, BY>::run(prm, sm, prm.pidx ? (long long)prm.pidx[pair] : pair);
 }
 
 template <int N, int BX, int BY, int MINB = 1>
@@ -1300,6 +1306,8 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
             add_variant<128, 4, 4, float, 1, 4, 3>(out);
             add_variant<128, 4, 8, float, 1, 2>(out);
             add_variant<128, 4, 4, float, 1, 4>(out);
+            add_variant<128, 2, 8, float, 2, 4, 3>(out);      // 2x8 cells: 16 warps per SM
+            add_variant<128, 2, 8, float, 2, 4>(out);
             break;
         case 256:
             add_variant<256, 4, 8, float, 1, 8>(out);
@@ -1313,6 +1321,8 @@ int patch_variants(int n, int precision, std::vector<PatchVariant> &out)
             add_variant<256, 4, 4, float, 1, 8, 3>(out);
             add_variant<256, 4, 4, float, 1, 8>(out);
             add_variant<256, 4, 8, float, 3, 16>(out);
+            add_variant<256, 2, 8, float, 1, 8, 3>(out);      // 2x8 cells: 16 warps per SM
+            add_variant<256, 2, 8, float, 1, 8>(out);
             break;
         default: break;
         }

@@ -41,7 +41,8 @@ struct SizeClass {
     int n = 0;
     long long Nl = 0;           // n * m
     double h = 0;
-    void *band = nullptr;       // [Nl][Nl] float or double
+    void *band = nullptr;       // [Nl][Nl] float or double; with periodize: per-patch tiles
+    long long tile = 0;         // 0, or n * n: band holds [P][n][n] periodised patch samples
     int *idx = nullptr;         // device patch indices; nullptr when the class holds every patch
     long long count = 0;
     PatchVariant variant{};
@@ -64,7 +65,14 @@ struct DevLevel {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;   // profiling: one pair per launch
     mlsd_surrogate *sur = nullptr;   // attached surrogate (MLSD_SURROGATE chains) or null
     double sur_thr = 0;
-    long long sur_fallbacks = -1;    // plain solves of the last surrogate-mode chain
+    bool sur_ran = false;            // a surrogate-mode chain ran since the attach
+    // workspace of the attached surrogate (sized at attach): series estimates
+    // [P][4] FP64, features [P][640] bf16, ensemble outputs [members][P][3],
+    // flags [P], compacted fallback indices [P] and their count
+    double *sur_E = nullptr;
+    void *sur_X = nullptr;
+    float *sur_out = nullptr;
+    int *sur_flag = nullptr, *sur_idx = nullptr, *sur_cnt = nullptr;
 };
 
 }  // namespace
@@ -86,6 +94,10 @@ struct mlsd_levels {
     cudaGraphExec_t graph = nullptr;
     const void *graph_out = nullptr, *graph_levels = nullptr;
     long long graph_launches = 0;
+    // the same for MLSD_SURROGATE chains (captured again after any attach)
+    cudaGraphExec_t graph_sur = nullptr;
+    const void *graph_sur_out = nullptr, *graph_sur_levels = nullptr;
+    long long graph_sur_launches = 0;
 };
 
 namespace {
@@ -162,6 +174,7 @@ int validate(const mlsd_problem *p)
         return MLSD_EINVAL;
     if (!p->band_edges || !p->patch_n || !(p->cfl > 0)) return MLSD_EINVAL;
     if (p->precision != MLSD_FP32 && p->precision != MLSD_FP64) return MLSD_EINVAL;
+    if (p->periodize != 0 && p->periodize != 1) return MLSD_EINVAL;
     for (int l = 0; l < p->n_levels; ++l)
         if (!(p->band_edges[l + 1] > p->band_edges[l])) return MLSD_EINVAL;
     if (p->n_avg_fixed <= 0 && (!(p->t_burn_tau >= 0) || !(p->t_avg_tau > 0))) return MLSD_EINVAL;
@@ -311,6 +324,8 @@ int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
         for (auto it = by_n.rbegin(); it != by_n.rend(); ++it) {
             std::vector<PatchVariant> vs;
             if (patch_variants(it->first, p->precision, vs) == 0) return MLSD_EUNSUPPORTED;
+            if (p->periodize && (p->precision != MLSD_FP32 || (it->first != 32 && it->first != 64)))
+                return MLSD_EUNSUPPORTED;
             SizeClass c;
             c.n = it->first;
             c.Nl = (long long)c.n * d.m;
@@ -348,6 +363,15 @@ int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (G) cudaFree(G);
             CK(e);
+            if (p->periodize) {
+                // the periodic component of every patch of the class, into its own tile
+                void *tiles = nullptr;
+                if ((rc = dev_alloc(h, &tiles, (size_t)h->P * c.n * c.n * rs))) return rc;
+                CK(launch_periodize(static_cast<const float *>(c.band), c.Nl, c.n, h->N, c.idx,
+                                    c.count, static_cast<float *>(tiles), s));
+                c.band = tiles;
+                c.tile = (long long)c.n * c.n;
+            }
         }
 
         // Algorithm 1 line variances (set-up; independent of the base tensor),
@@ -464,7 +488,7 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
     for (long long p = 0; p < h->P; ++p) { kb[3 * p] = h->kappa; kb[3 * p + 1] = 0; kb[3 * p + 2] = h->kappa; }
     CK(cudaMemcpyAsync(d.B, kb.data(), kb.size() * 8, cudaMemcpyHostToDevice, s));
     PatchParams pp;
-    pp.band = c.band; pp.Nl = c.Nl; pp.n_macro = h->N; pp.h = c.h; pp.L = d.L;
+    pp.band = c.band; pp.Nl = c.Nl; pp.tile = c.tile; pp.n_macro = h->N; pp.h = c.h; pp.L = d.L;
     pp.Kb = d.B; pp.S = d.S; pp.wdump = nullptr; pp.status = h->status;
     // trial window: the problem's own fixed window when it has one (its per-patch
     // set-up share then counts as it will in the solve), else 64 steps, where the
@@ -521,6 +545,7 @@ PatchParams patch_params(const mlsd_levels *h, const DevLevel &d, const SizeClas
     PatchParams pp;
     pp.band = c.band;
     pp.Nl = c.Nl;
+    pp.tile = c.tile;
     pp.n_macro = h->N;
     pp.h = c.h;
     pp.L = d.L;
@@ -622,6 +647,7 @@ void mlsd_free_levels(mlsd_levels *h)
         if (d.fork) cudaEventDestroy(d.fork);
     }
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->graph_sur) cudaGraphExecDestroy(h->graph_sur);
     if (h->cap) cudaStreamDestroy(h->cap);
     for (void *p : h->allocs) cudaFree(p);
     delete h;
@@ -685,6 +711,9 @@ int mlsd_offdiag(mlsd_levels *h, int level, const double *B_dev, double *Koff_de
 }  // extern "C"
 
 namespace {
+int surrogate_level_async(mlsd_levels *h, DevLevel &d, cudaStream_t s);
+int surrogate_workspace(mlsd_levels *h, DevLevel &d, mlsd_surrogate *sur);
+
 // Algorithm 3 over all levels, enqueued on stream s
 int enqueue_chain(mlsd_levels *h, double *K_macro_dev, double *K_levels_dev, cudaStream_t s,
                   bool surrogate = false)
@@ -708,16 +737,13 @@ int enqueue_chain(mlsd_levels *h, double *K_macro_dev, double *K_levels_dev, cud
                              nx ? nx->Kstar : nullptr, d.Koff, d.B, off_of(d), d.base, s));
         int rc;
         if (surrogate && d.sur) {
-            // the level's K* from the ensemble (plain solves where it disagrees), then
+            // the level's K* from the ensemble (plain solves where it is unsure), then
             // S = K* - base so that the rest of the chain reads it like a plain solve;
-            // the step counts then cover the fallback solves only
-            int64_t nfb = 0;
+            // the step counts then cover the fallback solves only.  No host
+            // synchronisation: the fallback launch reads its count on the device.
             CK(cudaMemsetAsync(d.steps, 0, (size_t)h->P * 16, s));
-            rc = mlsd_solve_level_surrogate(h, d.sur, l + 1, d.base, d.Kstar, d.sur_thr, &nfb, s);
-            if (!rc) {
-                d.sur_fallbacks = nfb;
-                CK(launch_S_from_K(h->P, d.base, d.Kstar, d.S, s));
-            }
+            rc = surrogate_level_async(h, d, s);
+            if (!rc) CK(launch_S_from_K(h->P, d.base, d.Kstar, d.S, s));
         } else {
             rc = run_patches(h, d, d.base, d.S, nullptr, s);
         }
@@ -744,10 +770,32 @@ int mlsd_effective_diffusivity(mlsd_levels *h, int mode, double *K_macro_dev,
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     if (mode == MLSD_SURROGATE) {
         bool any = false;
-        for (const DevLevel &d : h->lev) any = any || d.sur;
+        for (DevLevel &d : h->lev) any = any || d.sur;
         if (!any) return MLSD_EINVAL;
-        // the surrogate levels size their fallback launches on the host: no graph
-        return enqueue_chain(h, K_macro_dev, K_levels_dev, s, true);
+        for (DevLevel &d : h->lev) d.sur_ran = d.sur != nullptr;
+        if (h->profile || std::getenv("MLSD_NO_GRAPH"))
+            return enqueue_chain(h, K_macro_dev, K_levels_dev, s, true);
+        if (!h->graph_sur || h->graph_sur_out != K_macro_dev || h->graph_sur_levels != K_levels_dev) {
+            if (h->graph_sur) { cudaGraphExecDestroy(h->graph_sur); h->graph_sur = nullptr; }
+            if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+            const long long n0 = launch_count();
+            CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+            int rc = enqueue_chain(h, K_macro_dev, K_levels_dev, h->cap, true);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            CK(e);
+            e = cudaGraphInstantiate(&h->graph_sur, g, 0);
+            cudaGraphDestroy(g);
+            CK(e);
+            h->graph_sur_out = K_macro_dev;
+            h->graph_sur_levels = K_levels_dev;
+            h->graph_sur_launches = launch_count() - n0;
+            count_launches(-h->graph_sur_launches);
+        }
+        CK(cudaGraphLaunch(h->graph_sur, s));
+        count_launches(h->graph_sur_launches);
+        return MLSD_OK;
     }
     // profiling records events per launch: run the sequence directly then
     if (h->profile || std::getenv("MLSD_NO_GRAPH")) return enqueue_chain(h, K_macro_dev, K_levels_dev, s);
@@ -778,18 +826,30 @@ int mlsd_attach_surrogate(mlsd_levels *h, int level, mlsd_surrogate *s, double t
 {
     if (!h || level < 1 || level > h->L || !(threshold >= 0)) return MLSD_EINVAL;
     DevLevel &d = h->lev[level - 1];
-    if (s && (d.cls.size() != 1 || d.cls[0].n > 64 || h->precision != MLSD_FP32))
+    if (s && (d.cls.size() != 1 || (d.cls[0].n != 32 && d.cls[0].n != 64) ||
+              h->precision != MLSD_FP32))
         return MLSD_EUNSUPPORTED;
+    if (s) {
+        int rc = surrogate_workspace(h, d, s);
+        if (rc) return rc;
+    }
     d.sur = s;
     d.sur_thr = threshold;
-    d.sur_fallbacks = -1;
+    d.sur_ran = false;
+    if (h->graph_sur) { cudaGraphExecDestroy(h->graph_sur); h->graph_sur = nullptr; }
     return MLSD_OK;
 }
 
 int mlsd_surrogate_fallbacks(mlsd_levels *h, int level, int64_t *n_out)
 {
     if (!h || level < 1 || level > h->L || !n_out) return MLSD_EINVAL;
-    *n_out = h->lev[level - 1].sur_fallbacks;
+    const DevLevel &d = h->lev[level - 1];
+    *n_out = -1;
+    if (!d.sur || !d.sur_ran || !d.sur_cnt) return MLSD_OK;
+    int n = 0;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(&n, d.sur_cnt, sizeof(int), cudaMemcpyDeviceToHost));
+    *n_out = n;
     return MLSD_OK;
 }
 
@@ -1148,9 +1208,10 @@ int mlsd_surrogate_features(mlsd_levels *h, int level, const double *B_dev, void
 {
     if (!h || level < 1 || level > h->L || !B_dev || !X_dev) return MLSD_EINVAL;
     DevLevel &d = h->lev[level - 1];
-    if (d.cls.size() != 1 || d.cls[0].n > 64 || h->precision != MLSD_FP32) return MLSD_EUNSUPPORTED;
+    if (d.cls.size() != 1 || (d.cls[0].n != 32 && d.cls[0].n != 64) || h->precision != MLSD_FP32)
+        return MLSD_EUNSUPPORTED;
     const SizeClass &c = d.cls[0];
-    CK(launch_features(static_cast<const float *>(c.band), c.Nl, c.n, h->N, nullptr, h->P, B_dev,
+    CK(launch_features(static_cast<const float *>(c.band), c.Nl, c.tile, c.n, h->N, nullptr, h->P, B_dev,
                        h->kappa, X_dev, F32_dev, nullptr, static_cast<cudaStream_t>(cuda_stream)));
     return MLSD_OK;
 }
@@ -1197,16 +1258,17 @@ int mlsd_surrogate_dataset(mlsd_levels *h, int level, const double *B_dev, void 
 {
     if (!h || level < 1 || level > h->L || !B_dev || !X_dev || !Y_dev) return MLSD_EINVAL;
     DevLevel &d = h->lev[level - 1];
-    if (d.cls.size() != 1 || d.cls[0].n > 64 || h->precision != MLSD_FP32) return MLSD_EUNSUPPORTED;
+    if (d.cls.size() != 1 || (d.cls[0].n != 32 && d.cls[0].n != 64) || h->precision != MLSD_FP32)
+        return MLSD_EUNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const long long P = h->P;
     double *ws = nullptr;
-    CK(cudaMallocAsync((void **)&ws, (size_t)P * 6 * 8, st));
-    double *K = ws, *Q = ws + 3 * P;
+    CK(cudaMallocAsync((void **)&ws, (size_t)P * 7 * 8, st));
+    double *K = ws, *Q = ws + 3 * P;                 // Q: E and the series gap, [P][4]
     int rc = mlsd_solve_level(h, level, B_dev, K, nullptr, cuda_stream);
     cudaError_t e = cudaSuccess;
     const SizeClass &c = d.cls[0];
-    if (!rc) e = launch_features(static_cast<const float *>(c.band), c.Nl, c.n, h->N, nullptr, P, B_dev,
+    if (!rc) e = launch_features(static_cast<const float *>(c.band), c.Nl, c.tile, c.n, h->N, nullptr, P, B_dev,
                                  h->kappa, X_dev, nullptr, Q, st);
     if (!rc && e == cudaSuccess) e = sur_targets(P, B_dev, K, Q, Y_dev, st);
     cudaFreeAsync(ws, st);
@@ -1376,12 +1438,13 @@ int mlsd_solve_level_surrogate(mlsd_levels *h, mlsd_surrogate *s, int level,
     if (!h || !s || level < 1 || level > h->L || !K_base_dev || !K_out_dev || !(threshold >= 0))
         return MLSD_EINVAL;
     DevLevel &d = h->lev[level - 1];
-    if (d.cls.size() != 1 || d.cls[0].n > 64 || h->precision != MLSD_FP32) return MLSD_EUNSUPPORTED;
+    if (d.cls.size() != 1 || (d.cls[0].n != 32 && d.cls[0].n != 64) || h->precision != MLSD_FP32)
+        return MLSD_EUNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const long long P = h->P;
     char *ws = nullptr;
     const size_t xb = (size_t)P * MLSD_SUR_IN * 2, ob = (size_t)s->members * P * 3 * 4;
-    const size_t fb = (size_t)P * 4, ib = (size_t)P * 4, qb = (size_t)P * 3 * 8;
+    const size_t fb = (size_t)P * 4, ib = (size_t)P * 4, qb = (size_t)P * 4 * 8;
     CK(cudaMallocAsync((void **)&ws, qb + xb + ob + fb + ib + 256, st));
     double *Q = reinterpret_cast<double *>(ws);
     void *X = ws + qb;
@@ -1392,7 +1455,7 @@ int mlsd_solve_level_surrogate(mlsd_levels *h, mlsd_surrogate *s, int level,
     int count = 0;
     const SizeClass &c0 = d.cls[0];
     int rc = MLSD_OK;
-    cudaError_t e = launch_features(static_cast<const float *>(c0.band), c0.Nl, c0.n, h->N, nullptr,
+    cudaError_t e = launch_features(static_cast<const float *>(c0.band), c0.Nl, c0.tile, c0.n, h->N, nullptr,
                                     P, K_base_dev, h->kappa, X, nullptr, Q, st);
     if (e != cudaSuccess) rc = MLSD_ECUDA;
     if (!rc) rc = mlsd_surrogate_predict(s, X, P, out, cuda_stream);
@@ -1425,5 +1488,62 @@ int mlsd_solve_level_surrogate(mlsd_levels *h, mlsd_surrogate *s, int level,
     if (n_fallback_out) *n_fallback_out = count;
     return MLSD_OK;
 }
+
+}  // extern "C"
+
+namespace {
+// The surrogate's workspace for MLSD_SURROGATE chains, allocated with the handle
+// (freed with it) when a surrogate is attached; reused on every chain.
+int surrogate_workspace(mlsd_levels *h, DevLevel &d, mlsd_surrogate *sur)
+{
+    const long long P = h->P;
+    int rc;
+    if (!d.sur_E && (rc = dev_alloc(h, (void **)&d.sur_E, (size_t)P * 4 * 8))) return rc;
+    if (!d.sur_X && (rc = dev_alloc(h, &d.sur_X, (size_t)P * MLSD_SUR_IN * 2))) return rc;
+    if (!d.sur_flag && (rc = dev_alloc(h, (void **)&d.sur_flag, (size_t)P * 4))) return rc;
+    if (!d.sur_idx && (rc = dev_alloc(h, (void **)&d.sur_idx, (size_t)P * 4))) return rc;
+    if (!d.sur_cnt && (rc = dev_alloc(h, (void **)&d.sur_cnt, 16))) return rc;
+    // the ensemble output grows with the member count of the attached surrogate
+    static_assert(sizeof(float) == 4, "");
+    const size_t ob = (size_t)sur->members * P * 3 * 4;
+    if ((rc = dev_alloc(h, (void **)&d.sur_out, ob))) return rc;
+    return MLSD_OK;
+}
+
+// One surrogate level on the stream with no host synchronisation: features and
+// series estimates, the ensemble, the fallback rule with the compacted count
+// left on the device, the plain patch solve of the flagged patches by a launch
+// sized for every patch whose CTAs stride over the first 2 * count work items,
+// and the merge of those solves into K*.
+int surrogate_level_async(mlsd_levels *h, DevLevel &d, cudaStream_t st)
+{
+    mlsd_surrogate *sur = d.sur;
+    const long long P = h->P;
+    const SizeClass &c0 = d.cls[0];
+    CK(launch_features(static_cast<const float *>(c0.band), c0.Nl, c0.tile, c0.n, h->N, nullptr, P,
+                       d.base, h->kappa, d.sur_X, nullptr, d.sur_E, st));
+    int rc = mlsd_surrogate_predict(sur, d.sur_X, P, d.sur_out, st);
+    if (rc) return rc;
+    CK(sur_disagree(P, sur->members, d.sur_out, d.base, d.sur_E, d.sur_thr, d.Kstar, d.sur_flag,
+                    d.sur_idx, d.sur_cnt, st));
+    PatchParams pp = patch_params(h, d, c0, d.base, d.S, nullptr);
+    pp.pidx = d.sur_idx;
+    pp.count_dev = d.sur_cnt;
+    pp.item0 = 0;
+    pp.items = 2 * P;
+    int dev = 0, sms = 0, per_sm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c0.variant.fn, c0.variant.threads,
+                                                     c0.variant.smem));
+    // two waves of resident CTAs (in work items: packed kernels take two per CTA)
+    const long long cap = 2LL * sms * std::max(per_sm, 1) * (c0.variant.packed ? 2 : 1);
+    CK(launch_patch(c0.variant, pp, std::min<long long>(2 * P, cap), st));
+    CK(sur_merge_dev(P, d.sur_cnt, d.sur_idx, d.base, d.S, d.Kstar, st));
+    return MLSD_OK;
+}
+}  // namespace
+
+extern "C" {
 
 }  // extern "C"

@@ -1,16 +1,17 @@
 // Learned surrogate of the patch solve (not part of the paper's method; the
 // plain patch solve stays its fallback and the reference for its error).
 //
-// Features (K8): per patch, the 17 x 17 low-mode DFT of the patch's band psi
-// (patch mean removed) times MLSD_SUR_PSI_SCALE / (tr(B)/2), then B/kappa,
-// log kappa, and the second-order (small-Peclet) estimate Q of K - B on the
-// same modes, as MLSD_SUR_Q_SCALE Q / tr(B): 585 values stored as one bfloat16
-// row of MLSD_SUR_IN (640, zero padded).
+// Features: per patch, the 17 x 17 low-mode DFT of the patch's band psi (patch
+// mean removed) times MLSD_SUR_PSI_SCALE / (tr(B)/2), then B/kappa, log kappa
+// (k_features), and the perturbation moments T_2..T_6 of the steady corrector
+// equation with the [2/2], [3/3], [4/4] Pade approximants of its resummed
+// series (from T_2..T_19), each as asinh(MLSD_SUR_T_SCALE x / tr B) (k_series):
+// 606 values stored as one bfloat16 row of MLSD_SUR_IN (640, zero padded).
 // Network: an ensemble of members, each 640 -> h -> h -> h -> 3 with the exact
 // erf GELU, bfloat16 weights and activations, FP32 accumulation; output
-// (K - B - Q) MLSD_SUR_Y_SCALE / tr(B).  Training kernels here run on the CUDA cores (FP32 FMA on
-// bfloat16 operands); the inference forward has a tensor-core (tcgen05) kernel
-// in mlp_tc.cu.
+// asinh((K - B - E) MLSD_SUR_Y_SCALE / tr(B)), E the [4/4] approximant.  Training
+// kernels here run on the CUDA cores (FP32 FMA on bfloat16 operands); the
+// inference forward has a tensor-core (tcgen05) kernel in mlp_tc.cu.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -27,10 +28,11 @@ constexpr int KMODE = 8;                   // local modes -8..8
 constexpr int NMODE = 2 * KMODE + 1;       // 17
 
 // ---------------------------------------------------------------------------
-// K8 features: one CTA per patch (n <= 64: the patch is staged in shared memory)
-__global__ void k_features(const float *band, long long Nl, int n, int n_macro, const int *pidx,
-                           long long count, const double *B, double kappa, __nv_bfloat16 *X,
-                           float *F32, double *Qout)
+// Features 0..581 and the zero padding: one CTA per patch (n <= 64: the patch is
+// staged in shared memory)
+__global__ void k_features(const float *band, long long Nl, long long tile, int n, int n_macro,
+                           const int *pidx, long long count, const double *B, double kappa,
+                           __nv_bfloat16 *X, float *F32)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *psi = reinterpret_cast<float *>(smem_raw);              // [n][n]
@@ -44,7 +46,7 @@ __global__ void k_features(const float *band, long long Nl, int n, int n_macro, 
     double sum = 0.0;
     for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
         const int b = c / n, a = c % n;
-        const float v = band[pmod_ll(oy + b, Nl) * Nl + pmod_ll(ox + a, Nl)];
+        const float v = patch_band(band, Nl, tile, p, ox, oy, n, a, b);
         psi[c] = v;
         sum += v;
     }
@@ -75,12 +77,6 @@ __global__ void k_features(const float *band, long long Nl, int n, int n_macro, 
     const double inv_nn = 1.0 / ((double)n * n);
     __nv_bfloat16 *xr = X + item * (long long)MLSD_SUR_IN;
     float *fr = F32 ? F32 + item * (long long)MLSD_SUR_FEATURES : nullptr;
-    // second-order estimate of K - B over the window:
-    //   Q = sum_{k != 0} |psihat(k)|^2 [[s2^2, -s1 s2], [-s1 s2, s1^2]] / D(k),
-    //   D = B11 (2 - 2 cos t1) + B22 (2 - 2 cos t2) + 2 B12 s1 s2, t_i = 2 pi k_i / n:
-    // to first order in v the corrector solves B:DD w_j = -v_j, whose Fourier
-    // symbol is -D / h^2, and v1 = -D0y psi, v2 = D0x psi have symbols i s / h
-    double q11 = 0.0, q12 = 0.0, q22 = 0.0;
     for (int t = threadIdx.x; t < NMODE * NMODE; t += blockDim.x) {
         const int k2 = t / NMODE - KMODE, k1i = t % NMODE;
         float sr = 0.f, si = 0.f;
@@ -97,48 +93,300 @@ __global__ void k_features(const float *band, long long Nl, int n, int n_macro, 
         xr[2 * t] = __float2bfloat16_rn(re);
         xr[2 * t + 1] = __float2bfloat16_rn(im);
         if (fr) { fr[2 * t] = re; fr[2 * t + 1] = im; }
-        const int k1 = k1i - KMODE;
-        if (k1 != 0 || k2 != 0) {
-            double s1, c1, s2, c2;
-            sincospi(2.0 * k1 / n, &s1, &c1);
-            sincospi(2.0 * k2 / n, &s2, &c2);
-            const double D = B11 * (2.0 - 2.0 * c1) + B22 * (2.0 - 2.0 * c2) + 2.0 * B12 * s1 * s2;
-            const double pr = (double)sr * inv_nn, pi = (double)si * inv_nn;
-            const double g = (pr * pr + pi * pi) / D;
-            q11 += g * s2 * s2;
-            q12 -= g * s1 * s2;
-            q22 += g * s1 * s1;
-        }
     }
-    __shared__ double qred[3][32];
-    __shared__ double qsum[3];
-    for (int o = 16; o > 0; o >>= 1) {
-        q11 += __shfl_xor_sync(0xffffffffu, q11, o);
-        q12 += __shfl_xor_sync(0xffffffffu, q12, o);
-        q22 += __shfl_xor_sync(0xffffffffu, q22, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        qred[0][threadIdx.x >> 5] = q11; qred[1][threadIdx.x >> 5] = q12; qred[2][threadIdx.x >> 5] = q22;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += qred[threadIdx.x][w];
-        qsum[threadIdx.x] = t;
-        if (Qout) Qout[item * 3 + threadIdx.x] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < MLSD_SUR_IN - 2 * NMODE * NMODE) {
-        const int t = 2 * NMODE * NMODE + threadIdx.x;
+    const int t = 2 * NMODE * NMODE + threadIdx.x;
+    if (t < MLSD_SUR_IN && (t < 582 || t >= MLSD_SUR_FEATURES)) {   // 582..605: k_series
         float v = 0.f;
         if (t == 578) v = (float)(B11 / kappa);
         else if (t == 579) v = (float)(B12 / kappa);
         else if (t == 580) v = (float)(B22 / kappa);
         else if (t == 581) v = (float)log(kappa);
-        else if (t < 585) v = (float)(MLSD_SUR_Q_SCALE * qsum[t - 582] / (2.0 * trh));
         xr[t] = __float2bfloat16_rn(v);
         if (fr && t < MLSD_SUR_FEATURES) fr[t] = v;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Perturbation moments of the steady corrector equation (features 582..605 and
+// the baseline E of the network's target).  In index units (h = 1; the moments
+// do not depend on h):
+//   v1 = -(psi[b+1][a] - psi[b-1][a]) / 2,  v2 = (psi[b][a+1] - psi[b][a-1]) / 2,
+//   g(k) = 1 / D(k), D = B11 (2 - 2 cos t1) + B22 (2 - 2 cos t2) + 2 B12 sin t1 sin t2,
+//   g(0) = 0 (-L0^{-1} is multiplication of the DFT by g),
+//   c_j^0 = -L0^{-1} v_j,  c_j^m = -L0^{-1} (v1 D0x + v2 D0y) c_j^{m-1},
+//   T_m = sym <v_i c_j^{m-2}>  (m = 2..19, means over the cells in FP64).
+// Both fields go through one complex FFT as c1 + i c2: g is real and even in
+// k, so multiplying the transform of (f1 + i f2) by g transforms each part.
+// One CTA of 256 threads per patch, everything in shared memory: the complex
+// work field, v1, v2, c1, c2, the symbol g and the twiddles (n = 32: 28 KB,
+// n = 64: 112 KB).  Radix-2 FFT along rows, then columns, in FP32.
+// Resummation (FP64, one thread per component): pairs p_k = T_(2k+2) + T_(2k+3),
+// k = 0..8, and the [K/K] Pade approximants at 1 of sum_k p_k x^k by Wynn's
+// epsilon algorithm on the partial sums (K = 2, 3, 4); E = [4/4] and
+// Eout[item] = (E11, E12, E22, max_c |[4/4]_c - [3/3]_c|).
+template <int N>
+__device__ void fft2_smem(float2 *z, const float2 *tw, bool inverse)
+{
+    constexpr int LOG = N == 32 ? 5 : 6;
+    for (int pass = 0; pass < 2; ++pass) {
+        // rows: consecutive threads take consecutive elements of a row; columns:
+        // consecutive threads take consecutive columns (no shared-memory bank conflicts
+        // on the strided column accesses)
+        const int es = pass == 0 ? 1 : N, ls = pass == 0 ? N : 1;
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+            const int line = pass == 0 ? e / N : e % N, i = pass == 0 ? e % N : e / N;
+            const int r = (int)(__brev((unsigned)i) >> (32 - LOG));
+            if (i < r) {
+                const float2 a = z[line * ls + i * es];
+                z[line * ls + i * es] = z[line * ls + r * es];
+                z[line * ls + r * es] = a;
+            }
+        }
+        __syncthreads();
+        for (int half = 1; half < N; half <<= 1) {
+            const int tws = N / (2 * half);
+            for (int t = threadIdx.x; t < N * N / 2; t += blockDim.x) {
+                const int line = pass == 0 ? t / (N / 2) : t % N;
+                const int j = pass == 0 ? t % (N / 2) : t / N;
+                const int pos = j & (half - 1), grp = j / half;
+                const int i0 = grp * 2 * half + pos, i1 = i0 + half;
+                float2 w = tw[pos * tws];
+                if (inverse) w.y = -w.y;
+                const float2 a = z[line * ls + i0 * es], b = z[line * ls + i1 * es];
+                const float2 bw = make_float2(b.x * w.x - b.y * w.y, b.x * w.y + b.y * w.x);
+                z[line * ls + i0 * es] = make_float2(a.x + bw.x, a.y + bw.y);
+                z[line * ls + i1 * es] = make_float2(a.x - bw.x, a.y - bw.y);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// block sum of 4 doubles (256 threads = 8 warps); every thread gets the totals
+__device__ __forceinline__ void block_sum4(double (&v)[4], double (*red)[8])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 4; ++q) red[q][threadIdx.x >> 5] = v[q];
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[q][w];
+        v[q] = t;
+    }
+    __syncthreads();
+}
+
+// [K/K] at 1 of sum_k c_k x^k by Wynn's epsilon algorithm on the partial sums
+// (c_0..c_2K, K <= 4); where a difference vanishes, the last even column reached
+__device__ double wynn_dev(const double *c, int K)
+{
+    double ea[10], eb[10];
+    double *prev = ea, *cur = eb;
+    const int n = 2 * K + 1;
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) { acc += c[j]; cur[j] = acc; prev[j] = 0.0; }
+    prev[n] = 0.0;
+    double best = cur[n - 1];
+    int len = n;
+    for (int k = 1; k <= 2 * K; ++k) {
+        for (int j = 0; j < len - 1; ++j) {          // in place: prev[j] <- eps_{k}^{(j)}
+            const double d = cur[j + 1] - cur[j];
+            if (fabs(d) < 1e-300) return best;
+            prev[j] = prev[j + 1] + 1.0 / d;
+        }
+        double *t = prev; prev = cur; cur = t;
+        len -= 1;
+        if ((k & 1) == 0) best = cur[0];
+    }
+    return cur[0];
+}
+
+constexpr int SERIES_M = 19;               // moments T_2..T_19
+
+template <int N>
+__global__ void __launch_bounds__(256) k_series(const float *band, long long Nl, long long tile,
+                                                int n_macro, const int *pidx, long long count,
+                                                const double *B, __nv_bfloat16 *X, float *F32,
+                                                double *Eout)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *z = reinterpret_cast<float2 *>(smem_raw);               // [N][N] complex
+    float *v1 = reinterpret_cast<float *>(z + N * N);                // [N][N] each:
+    float *v2 = v1 + N * N, *c1 = v2 + N * N, *c2 = c1 + N * N;      // velocity, iterates,
+    float *g = c2 + N * N;                                           // 1 / D(k)
+    float2 *tw = reinterpret_cast<float2 *>(g + N * N);              // [N/2]
+    float *psi = c1;                                                 // psi until v is formed
+    __shared__ double red[4][8];
+    __shared__ double Tm[SERIES_M - 1][3];
+    const long long item = blockIdx.x;
+    if (item >= count) return;
+    const long long p = pidx ? (long long)pidx[item] : item;
+    const long long ox = patch_origin(p % n_macro, n_macro, Nl, N);
+    const long long oy = patch_origin(p / n_macro, n_macro, Nl, N);
+    const double B11 = B[3 * p], B12 = B[3 * p + 1], B22 = B[3 * p + 2];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int b = e / N, a = e % N;
+        const float v = patch_band(band, Nl, tile, p, ox, oy, N, a, b);
+        psi[e] = v;
+        acc[0] += v;
+        // the symbol of -L0^{-1}, once per patch
+        float s1, co1, s2, co2;
+        sincospif(2.0f * (float)a / (float)N, &s1, &co1);
+        sincospif(2.0f * (float)b / (float)N, &s2, &co2);
+        const float D = (float)B11 * (2.f - 2.f * co1) + (float)B22 * (2.f - 2.f * co2)
+                        + 2.f * (float)B12 * s1 * s2;
+        g[e] = e == 0 ? 0.f : 1.f / D;
+    }
+    for (int k = threadIdx.x; k < N / 2; k += blockDim.x) {
+        float sn, cs;
+        sincospif(-2.0f * (float)k / (float)N, &sn, &cs);
+        tw[k] = make_float2(cs, sn);
+    }
+    block_sum4(acc, red);
+    const float mean = (float)(acc[0] / (double)(N * N));
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int b = e / N, a = e % N;
+        const int ap = (a + 1) & (N - 1), am = (a + N - 1) & (N - 1);
+        const int bp = (b + 1) & (N - 1), bm = (b + N - 1) & (N - 1);
+        v1[e] = 0.5f * (psi[bm * N + a] - psi[bp * N + a]);
+        v2[e] = 0.5f * (psi[b * N + ap] - psi[b * N + am]);
+        z[e] = make_float2(psi[e] - mean, 0.f);
+    }
+    __syncthreads();
+    fft2_smem<N>(z, tw, false);
+    // c^0: transform of c1 + i c2 = g (-s1 - i s2) psihat
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int k1 = e % N, k2 = e / N;
+        const float s1 = sinpif(2.0f * (float)k1 / (float)N), s2 = sinpif(2.0f * (float)k2 / (float)N);
+        const float2 q = z[e];
+        z[e] = make_float2(g[e] * (-q.x * s1 + q.y * s2), g[e] * (-q.x * s2 - q.y * s1));
+    }
+    __syncthreads();
+    fft2_smem<N>(z, tw, true);
+    const float inv = 1.0f / (float)(N * N);
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) { c1[e] = z[e].x * inv; c2[e] = z[e].y * inv; }
+    __syncthreads();
+    for (int m = 2; m <= SERIES_M; ++m) {
+        double sm[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+            const float a1 = v1[e], a2 = v2[e];
+            sm[0] += (double)(a1 * c1[e]); sm[1] += (double)(a1 * c2[e]);
+            sm[2] += (double)(a2 * c1[e]); sm[3] += (double)(a2 * c2[e]);
+            if (m < SERIES_M) {
+                const int b = e / N, a = e % N;
+                const int ap = (a + 1) & (N - 1), am = (a + N - 1) & (N - 1);
+                const int bp = (b + 1) & (N - 1), bm = (b + N - 1) & (N - 1);
+                const float d1x = 0.5f * (c1[b * N + ap] - c1[b * N + am]);
+                const float d1y = 0.5f * (c1[bp * N + a] - c1[bm * N + a]);
+                const float d2x = 0.5f * (c2[b * N + ap] - c2[b * N + am]);
+                const float d2y = 0.5f * (c2[bp * N + a] - c2[bm * N + a]);
+                z[e] = make_float2(fmaf(a1, d1x, a2 * d1y), fmaf(a1, d2x, a2 * d2y));
+            }
+        }
+        block_sum4(sm, red);
+        if (threadIdx.x == 0) {
+            const double nn = (double)(N * N);
+            Tm[m - 2][0] = sm[0] / nn;
+            Tm[m - 2][1] = 0.5 * (sm[1] + sm[2]) / nn;
+            Tm[m - 2][2] = sm[3] / nn;
+        }
+        if (m == SERIES_M) break;
+        fft2_smem<N>(z, tw, false);
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+            const float q = g[e];
+            z[e] = make_float2(z[e].x * q, z[e].y * q);
+        }
+        __syncthreads();
+        fft2_smem<N>(z, tw, true);
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) { c1[e] = z[e].x * inv; c2[e] = z[e].y * inv; }
+        __syncthreads();
+    }
+    __syncthreads();
+    const double sc = MLSD_SUR_T_SCALE / (B11 + B22);
+    __nv_bfloat16 *xr = X + item * (long long)MLSD_SUR_IN;
+    float *fr = F32 ? F32 + item * (long long)MLSD_SUR_FEATURES : nullptr;
+    if (threadIdx.x < 3) {
+        const int c = threadIdx.x;
+        double pk[9];
+        for (int k = 0; k < 9; ++k) pk[k] = Tm[2 * k][c] + Tm[2 * k + 1][c];
+        const double P2 = wynn_dev(pk, 2), P3 = wynn_dev(pk, 3), E = wynn_dev(pk, 4);
+        red[0][c] = fabs(E - P3);
+        if (Eout) Eout[item * 4 + c] = E;
+        const float f2 = (float)asinh(sc * P2), f3 = (float)asinh(sc * P3),
+                    fe = (float)asinh(sc * E);
+        xr[597 + c] = __float2bfloat16_rn(f2);
+        xr[600 + c] = __float2bfloat16_rn(f3);
+        xr[603 + c] = __float2bfloat16_rn(fe);
+        if (fr) { fr[597 + c] = f2; fr[600 + c] = f3; fr[603 + c] = fe; }
+    }
+    if (threadIdx.x < 15) {
+        const float f = (float)asinh(sc * Tm[threadIdx.x / 3][threadIdx.x % 3]);
+        xr[582 + threadIdx.x] = __float2bfloat16_rn(f);
+        if (fr) fr[582 + threadIdx.x] = f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && Eout) {
+        const double g0 = fmax(red[0][0], fmax(red[0][1], red[0][2]));
+        Eout[item * 4 + 3] = (red[0][0] == red[0][0] && red[0][1] == red[0][1] &&
+                              red[0][2] == red[0][2]) ? g0 : red[0][0] + red[0][1] + red[0][2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Periodic component of a patch's band samples u (periodic-plus-smooth
+// decomposition, Moisan 2011): the boundary image v is nonzero on the border
+// samples only, v(x) = sum over the seam neighbours y of u(y) - u(x); s solves
+// the periodic 5-point Poisson problem Lap s = v (symbol 2 cos t1 + 2 cos t2 - 4,
+// zero mean); p = u - s goes to the patch's tile.  One CTA of 256 threads per
+// patch, FFTs in shared memory (FP32).
+template <int N>
+__global__ void __launch_bounds__(256) k_periodize(const float *band, long long Nl, int n_macro,
+                                                   const int *pidx, long long count, float *tiles)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *z = reinterpret_cast<float2 *>(smem_raw);               // [N][N] complex
+    float *u = reinterpret_cast<float *>(z + N * N);                 // [N][N]
+    float2 *tw = reinterpret_cast<float2 *>(u + N * N);              // [N/2]
+    const long long item = blockIdx.x;
+    if (item >= count) return;
+    const long long p = pidx ? (long long)pidx[item] : item;
+    const long long ox = patch_origin(p % n_macro, n_macro, Nl, N);
+    const long long oy = patch_origin(p / n_macro, n_macro, Nl, N);
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x)
+        u[e] = band[pmod_ll(oy + e / N, Nl) * Nl + pmod_ll(ox + e % N, Nl)];
+    for (int k = threadIdx.x; k < N / 2; k += blockDim.x) {
+        float sn, cs;
+        sincospif(-2.0f * (float)k / (float)N, &sn, &cs);
+        tw[k] = make_float2(cs, sn);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int b = e / N, a = e % N;
+        float v = 0.f;
+        if (b == 0) v += u[(N - 1) * N + a] - u[a];
+        if (b == N - 1) v += u[a] - u[(N - 1) * N + a];
+        if (a == 0) v += u[b * N + N - 1] - u[b * N];
+        if (a == N - 1) v += u[b * N] - u[b * N + N - 1];
+        z[e] = make_float2(v, 0.f);
+    }
+    __syncthreads();
+    fft2_smem<N>(z, tw, false);
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        float s1, c1, s2, c2;
+        sincospif(2.0f * (float)(e % N) / (float)N, &s1, &c1);
+        sincospif(2.0f * (float)(e / N) / (float)N, &s2, &c2);
+        const float d = 2.f * c1 + 2.f * c2 - 4.f;
+        z[e] = e == 0 ? make_float2(0.f, 0.f) : make_float2(z[e].x / d, z[e].y / d);
+    }
+    __syncthreads();
+    fft2_smem<N>(z, tw, true);
+    const float inv = 1.0f / (float)(N * N);
+    float *t = tiles + p * (long long)(N * N);
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) t[e] = u[e] - z[e].x * inv;
 }
 
 // ---------------------------------------------------------------------------
@@ -424,26 +672,28 @@ __global__ void k_to_bf16(long long n, const float *w, __nv_bfloat16 *wb)
     if (i < n) wb[i] = __float2bfloat16_rn(w[i]);
 }
 
-// Ensemble disagreement on K: for every patch, K_m = B + Q + tr(B) out_m / YS
-// (Q the second-order estimate from the features); flag when
-//   max_{m,c} |K_m,c - mean_m K_m,c| > thr * ||mean K||_F.
-// Surrogate estimate where not flagged: K = B + Q + tr(B) mean_m out_m / YS.
+// Fallback rule: for every patch, K_m = B + E + tr(B) sinh(out_m) / YS (E the
+// resummed series estimate); flag when
+//   max(max_{m,c} |K_m,c - mean_m K_m,c|, GAP_WEIGHT * gap) > thr * ||mean K||_F,
+// gap = max_c |[4/4]_c - [3/3]_c| (how far the resummation is from converged).
+// Surrogate estimate where not flagged: K = mean_m K_m.
 __global__ void k_disagree(long long P, int members, const float *out, const double *B,
-                           const double *Q, double thr, double *K, int *flag)
+                           const double *E, double thr, double *K, int *flag)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P) return;
     const double tr = (B[3 * p] + B[3 * p + 2]) / MLSD_SUR_Y_SCALE;
     double mean[3] = {0, 0, 0};
     for (int m = 0; m < members; ++m)
-        for (int c = 0; c < 3; ++c) mean[c] += (double)out[((long long)m * P + p) * 3 + c];
+        for (int c = 0; c < 3; ++c) mean[c] += sinh((double)out[((long long)m * P + p) * 3 + c]);
     double Km[3];
-    for (int c = 0; c < 3; ++c) Km[c] = B[3 * p + c] + Q[3 * p + c] + tr * mean[c] / members;
+    for (int c = 0; c < 3; ++c) Km[c] = B[3 * p + c] + E[4 * p + c] + tr * mean[c] / members;
     const double fro = sqrt(Km[0] * Km[0] + 2.0 * Km[1] * Km[1] + Km[2] * Km[2]);
-    double dev = 0.0;
+    double dev = MLSD_SUR_GAP_WEIGHT * E[4 * p + 3];
     for (int m = 0; m < members; ++m)
         for (int c = 0; c < 3; ++c) {
-            const double km = B[3 * p + c] + Q[3 * p + c] + tr * (double)out[((long long)m * P + p) * 3 + c];
+            const double km = B[3 * p + c] + E[4 * p + c]
+                              + tr * sinh((double)out[((long long)m * P + p) * 3 + c]);
             dev = fmax(dev, fabs(km - Km[c]));
         }
     const int f = !(dev <= thr * fro);           // NaN -> flagged
@@ -493,8 +743,10 @@ __device__ __forceinline__ int sym_source(int c, int g, bool &neg)
         neg = (rx != ry) != sw;
         return 2 * ((k2s + KMODE) * NMODE + (k1s + KMODE)) + (c & 1);
     }
-    // B / kappa at 578..580, log kappa at 581, Q at 582..584, padding after
-    const int base = c >= 582 && c < 585 ? 582 : (c >= 578 && c < 581 ? 578 : -1);
+    // B / kappa at 578..580, log kappa at 581, eight tensors at 582..605 (T_2..T_6
+    // and the three approximants, each stored through the odd asinh), padding after
+    const int base = c >= 582 && c < MLSD_SUR_FEATURES ? 582 + 3 * ((c - 582) / 3)
+                                                       : (c >= 578 && c < 581 ? 578 : -1);
     if (base < 0) return c;
     const int i = c - base;
     if (i == 1) { neg = rx != ry; return c; }
@@ -558,20 +810,24 @@ __global__ void k_add_loss(const double *loss, double *acc)
     if (threadIdx.x == 0) *acc += *loss;
 }
 
-// training targets (K - B - Q) YS / tr(B) of one plain-solved level
-__global__ void k_targets(long long P, const double *B, const double *K, const double *Q, float *Y)
+// training targets asinh((K - B - E) YS / tr(B)) of one plain-solved level
+// (E: the resummed series estimate, [P][4] with the series gap in the 4th column)
+__global__ void k_targets(long long P, const double *B, const double *K, const double *E, float *Y)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P) return;
     const double f = MLSD_SUR_Y_SCALE / (B[3 * p] + B[3 * p + 2]);
-    for (int c = 0; c < 3; ++c) Y[3 * p + c] = (float)((K[3 * p + c] - B[3 * p + c] - Q[3 * p + c]) * f);
+    for (int c = 0; c < 3; ++c)
+        Y[3 * p + c] = (float)asinh((K[3 * p + c] - B[3 * p + c] - E[4 * p + c]) * f);
 }
 
-// flagged patches take the plain solve: K = sym(B e_j + S_.j)
-__global__ void k_merge_fallback(int n, const int *idx, const double *B, const double *S, double *K)
+// flagged patches take the plain solve: K = sym(B e_j + S_.j); with n_dev the
+// count is read on the device (a launch sized for every patch)
+__global__ void k_merge_fallback(int n, const int *n_dev, const int *idx, const double *B,
+                                 const double *S, double *K)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
+    if (t >= (n_dev ? *n_dev : n)) return;
     const long long p = idx[t];
     const double *b = B + 3 * p, *s = S + 4 * p;
     K[3 * p] = b[0] + s[0];
@@ -588,19 +844,60 @@ long long sur_param_count(int h)
     return (long long)h * MLSD_SUR_IN + h + 2 * ((long long)h * h + h) + 3LL * h + 3;
 }
 
-cudaError_t launch_features(const float *band, long long Nl, int n, int n_macro, const int *pidx,
-                            long long count, const double *B, double kappa, void *X, float *F32,
-                            double *Q, cudaStream_t s)
+template <int N>
+static cudaError_t launch_series(const float *band, long long Nl, long long tile, int n_macro,
+                                 const int *pidx, long long count, const double *B, void *X,
+                                 float *F32, double *E, cudaStream_t s)
+{
+    const size_t smem = (size_t)N * N * (8 + 5 * 4) + (size_t)N / 2 * 8;
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_series<N>),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    k_series<N><<<(unsigned)count, 256, smem, s>>>(band, Nl, tile, n_macro, pidx, count, B,
+                                                   static_cast<__nv_bfloat16 *>(X), F32, E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features(const float *band, long long Nl, long long tile, int n, int n_macro,
+                            const int *pidx, long long count, const double *B, double kappa,
+                            void *X, float *F32, double *E, cudaStream_t s)
 {
     if (count == 0) return cudaSuccess;
+    if (n != 32 && n != 64) return cudaErrorInvalidValue;
     const size_t smem = (size_t)n * n * 4 + (size_t)n * NMODE * 8;
     cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_features),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    k_features<<<(unsigned)count, 320, smem, s>>>(band, Nl, n, n_macro, pidx, count, B, kappa,
-                                                  static_cast<__nv_bfloat16 *>(X), F32, Q);
+    k_features<<<(unsigned)count, 320, smem, s>>>(band, Nl, tile, n, n_macro, pidx, count, B,
+                                                  kappa, static_cast<__nv_bfloat16 *>(X), F32);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return n == 32 ? launch_series<32>(band, Nl, tile, n_macro, pidx, count, B, X, F32, E, s)
+                   : launch_series<64>(band, Nl, tile, n_macro, pidx, count, B, X, F32, E, s);
+}
+
+template <int N>
+static cudaError_t launch_periodize_n(const float *band, long long Nl, int n_macro, const int *pidx,
+                                      long long count, float *tiles, cudaStream_t s)
+{
+    const size_t smem = (size_t)N * N * 12 + (size_t)N / 2 * 8;
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_periodize<N>),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    k_periodize<N><<<(unsigned)count, 256, smem, s>>>(band, Nl, n_macro, pidx, count, tiles);
     return cudaGetLastError();
+}
+
+cudaError_t launch_periodize(const float *band, long long Nl, int n, int n_macro, const int *pidx,
+                             long long count, float *tiles, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    if (n == 32) return launch_periodize_n<32>(band, Nl, n_macro, pidx, count, tiles, s);
+    if (n == 64) return launch_periodize_n<64>(band, Nl, n_macro, pidx, count, tiles, s);
+    return cudaErrorInvalidValue;
 }
 
 // Layer views of one member's parameters (FP32 master or bfloat16 copy)
@@ -724,20 +1021,20 @@ cudaError_t sur_add_loss(const double *loss, double *acc, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t sur_targets(long long P, const double *B, const double *K, const double *Q, float *Y,
+cudaError_t sur_targets(long long P, const double *B, const double *K, const double *E, float *Y,
                         cudaStream_t s)
 {
     count_launches(1);
-    k_targets<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(P, B, K, Q, Y);
+    k_targets<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(P, B, K, E, Y);
     return cudaGetLastError();
 }
 
 cudaError_t sur_disagree(long long P, int members, const float *out, const double *B,
-                         const double *Q, double thr, double *K, int *flag, int *idx, int *count,
+                         const double *E, double thr, double *K, int *flag, int *idx, int *count,
                          cudaStream_t s)
 {
     count_launches(2);
-    k_disagree<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(P, members, out, B, Q, thr, K, flag);
+    k_disagree<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(P, members, out, B, E, thr, K, flag);
     k_compact<<<1, 1024, 0, s>>>(P, flag, idx, count);
     return cudaGetLastError();
 }
@@ -747,7 +1044,15 @@ cudaError_t sur_merge(int n, const int *idx, const double *B, const double *S, d
 {
     if (n == 0) return cudaSuccess;
     count_launches(1);
-    k_merge_fallback<<<(n + 255) / 256, 256, 0, s>>>(n, idx, B, S, K);
+    k_merge_fallback<<<(n + 255) / 256, 256, 0, s>>>(n, nullptr, idx, B, S, K);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_merge_dev(long long P, const int *n_dev, const int *idx, const double *B,
+                          const double *S, double *K, cudaStream_t s)
+{
+    count_launches(1);
+    k_merge_fallback<<<(unsigned)((P + 255) / 256), 256, 0, s>>>((int)P, n_dev, idx, B, S, K);
     return cudaGetLastError();
 }
 

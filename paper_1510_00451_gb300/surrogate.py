@@ -13,9 +13,9 @@ from . import SUR_IN, Levels, Surrogate
 
 def make_dataset(lv, level, bases):
     """Plain patch solves of one level for each base set: features X (bfloat16
-    [n P][640]) and targets Y = (K - B - Q) SUR_Y_SCALE / tr(B) (FP32 [n P][3])
-    on the device, Q the second-order estimate the features carry (mlsd.h);
-    all of it in mlsd_surrogate_dataset."""
+    [n P][640]) and targets Y = asinh((K - B - E) SUR_Y_SCALE / tr(B)) (FP32 [n P][3])
+    on the device, E the resummed perturbation series the features carry
+    (mlsd.h); all of it in mlsd_surrogate_dataset."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     P = lv.P

@@ -152,6 +152,10 @@ def _chain_check(mlsd, torch, spec, edges, pn, N, kappa, nodes, tol, prec="fp32"
     okw = {}
     if kw.get("n_avg_fixed", 0) > 0:
         okw = dict(n_burn_fixed=kw["n_burn_fixed"], n_avg_fixed=kw["n_avg_fixed"])
+    if kw.get("patch_div") is not None:
+        okw["patch_div"] = kw["patch_div"]
+    if kw.get("periodize"):
+        okw["periodize"] = True
     want = oracle.chain(spec, edges, pn, N, kappa, nodes, **okw)
     for (i, j), wv in zip(nodes, want):
         assert rel_l2(K[j * N + i], wv) < tol, ((i, j), K[j * N + i], wv)
@@ -214,3 +218,34 @@ def test_graph_replay_matches_direct_launches(mlsd, torch_mod, monkeypatch):
     lv.effective_diffusivity(K3)            # direct launches
     assert lv.status() == 0
     assert torch_mod.equal(K1, K2) and torch_mod.equal(K1, K3)
+
+
+def test_chain_of_the_offdiagonal_stress_flow(mlsd, torch_mod):
+    # the Sec. 4.3 structure at half the wavenumbers: two diagonal cellular
+    # modes (2, 2) and (20, 20) and the off-diagonal pair (2, 18), (18, 2) of
+    # level 1 (psi_12, psi_21), with patch sides 2 pi and pi; 64^2 patches on
+    # level 2 (local wavenumber 10), reduced window
+    spec = flows.cellular([(0.2, 2, 2), (0.2, 2, 18), (0.2, 18, 2), (0.2, 20, 20)])
+    _chain_check(mlsd, torch_mod, spec, [1, 3, 21], [32, 64], 2, 1.0,
+                 [(0, 0), (1, 1)], K_TOL, n_burn_fixed=150, n_avg_fixed=100, patch_div=[1, 2])
+
+
+@pytest.mark.parametrize("periodize", [False, True])
+def test_chain_on_side_2H_patches(mlsd, torch_mod, periodize):
+    # the paper's local domains of side 2H (H = 2 pi / N): the bands are not
+    # periodic on these patches; the seam is wrapped as sampled, or the band is
+    # replaced by its periodic component (periodic-plus-smooth decomposition)
+    N = 8
+    spec = flows.cellular_two_scale(1.0, 0.5, 8)
+    for pn in ([32, 32], [64, 32]):
+        _chain_check(mlsd, torch_mod, spec, [1, 8, 9], pn, N, 0.05, [(0, 0), (3, 5), (7, 2)], K_TOL,
+                     n_burn_fixed=200, n_avg_fixed=100, patch_div=[N // 2, 4 * N // 2],
+                     periodize=periodize)
+
+
+def test_periodize_rejects_what_it_does_not_support(mlsd, torch_mod):
+    spec = flows.cellular_two_scale(1.0, 0.5, 8)
+    for kw in (dict(patch_n=[128, 32]), dict(patch_n=[32, 32], precision="fp64")):
+        pn = kw.pop("patch_n")
+        with pytest.raises(mlsd.MlsdError):
+            mlsd.Levels(spec, 0.05, 4, [1, 8, 9], pn, periodize=True, **kw)

@@ -1,6 +1,7 @@
-"""GPU parity of the surrogate kernels against the oracle: patch features (DFT),
-the MLP forward and gradient with bfloat16 rounding at the same points, and
-the fallback path of the surrogate level solve."""
+"""GPU parity of the surrogate kernels against the oracle: patch features (DFT
+and the perturbation moments of the steady corrector equation), the MLP
+forward and gradient with bfloat16 rounding at the same points, and the
+fallback path of the surrogate level solve."""
 import math
 
 import numpy as np
@@ -50,9 +51,26 @@ def test_features_match_oracle(mlsd, torch_mod, n):
             scale = np.abs(f[:578]).max()
             assert np.abs(Fg[p, :578] - f[:578]).max() < 1e-5 * scale, (level, p)
             np.testing.assert_allclose(Fg[p, 578:582], f[578:582], rtol=1e-6)
-            # the second-order estimate: sums of squares of FP32 coefficients
-            qs = np.abs(f[582:585]).max()
-            assert np.abs(Fg[p, 582:585] - f[582:585]).max() < 1e-5 * qs, (level, p)
+            # the moments T_2..T_6 (FP32 FFTs against the FP64 oracle), compared after
+            # undoing the asinh: each to 1e-4 of itself, or 1e-5 of T_2's scale
+            got, want = np.sinh(Fg[p, 582:606].astype(np.float64)), np.sinh(f[582:606])
+            ts = np.abs(want[:3]).max()
+            assert np.all(np.abs(got[:15] - want[:15]) <= 1e-4 * np.abs(want[:15]) + 1e-5 * ts), \
+                (level, p, got, want)
+            # the approximants: where the oracle's resummation has converged ([4/4]
+            # within 1e-2 of [3/3]) they agree; where it has not (a Peclet number far
+            # beyond the series' reach: Wynn's epsilon then amplifies the FP32
+            # rounding of the moments up to T_19), both sides see it unconverged
+            # and the fallback rule takes the patch
+            T = oracle.series(psi, B[p])
+            _, _, E, gap = oracle.series_estimate(T)
+            gp, ap = np.abs(got[21:24] - got[18:21]).max(), np.abs(got[21:24]).max()
+            assert np.all(np.isfinite(got)), (level, p)
+            if gap <= 1e-2 * np.abs(E).max():
+                assert np.all(np.abs(got[15:] - want[15:]) <= 2e-3 * np.abs(want[15:]) + 1e-5 * ts), \
+                    (level, p, got, want)
+            else:
+                assert gp > 1e-3 * ap, (level, p, got, want)
         # the bfloat16 row is the rounded FP32 row, zero padded
         Xg = X.float().cpu().numpy()
         nf = mlsd.SUR_FEATURES
@@ -72,7 +90,8 @@ def test_gradient_matches_bf16_oracle(mlsd, torch_mod, h, M):
         params[::7] += 0.05                       # nonzero biases too
         sur.set_params(member, params)
         Xf = np.zeros((M, mlsd.SUR_IN), np.float32)
-        Xf[:, :585] = rng.standard_normal((M, 585)).astype(np.float32)
+        nf = mlsd.SUR_FEATURES
+        Xf[:, :nf] = rng.standard_normal((M, nf)).astype(np.float32)
         X = torch_mod.tensor(Xf, device=dev).to(torch_mod.bfloat16)
         Y = torch_mod.tensor(rng.standard_normal((M, 3)) * 0.3, dtype=torch_mod.float32, device=dev)
         g = torch_mod.zeros(sur.n_params, dtype=torch_mod.float32, device=dev)
@@ -168,7 +187,7 @@ def test_surrogate_level_fallback_paths(mlsd, torch_mod):
     K0 = torch_mod.zeros_like(B)
     assert lv.solve_level_surrogate(sur, 2, B, K0, 0.0) == N * N
     assert rel_l2(K0.cpu().numpy(), K_plain.cpu().numpy()) < 1e-6
-    # huge threshold: no fallback, K = B + Q + tr(B) * ensemble mean / Y_SCALE
+    # huge threshold: no fallback, K = B + E + tr(B) * ensemble mean / Y_SCALE
     K1 = torch_mod.zeros_like(B)
     assert lv.solve_level_surrogate(sur, 2, B, K1, 1e30) == 0
     X = torch_mod.zeros(N * N, mlsd.SUR_IN, dtype=torch_mod.bfloat16, device=dev)
@@ -177,8 +196,8 @@ def test_surrogate_level_fallback_paths(mlsd, torch_mod):
     out = torch_mod.zeros(4, N * N, 3, device=dev)
     sur.predict(X, out)
     tr = (B[:, 0] + B[:, 2]).unsqueeze(1)
-    Q = F[:, 582:585].double() * tr / mlsd.SUR_Q_SCALE      # FP32-rounded copy of Q
-    want = B + Q + tr * out.double().mean(0) / mlsd.SUR_Y_SCALE
+    E = torch_mod.sinh(F[:, 603:606].double()) * tr / mlsd.SUR_T_SCALE   # FP32-rounded copy of E
+    want = B + E + tr * torch_mod.sinh(out.double()).mean(0) / mlsd.SUR_Y_SCALE
     assert rel_l2(K1.cpu().numpy(), want.cpu().numpy()) < 1e-6
     assert torch_mod.allclose(K1, want, rtol=1e-6, atol=0)
     assert lv.status() == 0
@@ -205,7 +224,7 @@ def test_tensor_core_inference_matches_oracle(mlsd, torch_mod, M, h, tma, monkey
         sur.set_params(m, p)
     dev = torch_mod.device("cuda:0")
     Xf = np.zeros((M, mlsd.SUR_IN), np.float32)
-    Xf[:, :585] = rng.standard_normal((M, 585))
+    Xf[:, :mlsd.SUR_FEATURES] = rng.standard_normal((M, mlsd.SUR_FEATURES))
     X = torch_mod.tensor(Xf, device=dev).to(torch_mod.bfloat16)
     out_tc = torch_mod.full((members, M, 3), float("nan"), device=dev)
     sur.set_engine(mlsd.SUR_TENSOR)
@@ -225,36 +244,56 @@ def test_tensor_core_inference_matches_oracle(mlsd, torch_mod, M, h, tma, monkey
         assert rel_l2(out_cc[m].cpu().numpy(), ref) < 1e-3, m
 
 
+def _octave_band(seed, lo, hi):
+    full = flows.continuous_spectrum(256, seed=seed)
+    a, b = np.abs(full.k1), np.abs(full.k2)
+    keep = (a >= lo) & (a < hi) & (b >= lo) & (b < hi)
+    return flows.Spectrum(full.k1[keep], full.k2[keep], full.re[keep], full.im[keep])
+
+
 def test_trained_surrogate_replaces_most_patch_solves(mlsd, torch_mod):
     # What the learned part gains over the method without it: trained on the
-    # library's own plain solves of a level (3 base sets), the ensemble answers
-    # most patches of a fresh base set, and only the patches where its members
-    # disagree are solved again; the answers stay close to the plain solve.
+    # library's own plain solves of one flow realization's 5th-octave band (64^2
+    # patches, the highest Peclet numbers of the surrogate's levels; 2 base sets),
+    # the ensemble answers the patches of ANOTHER realization (no psi seen in
+    # training) with a fresh base set; only the patches it is unsure of are solved
+    # again, and the answers stay within 1e-3 of the plain solve.  Without the
+    # network (zero weights: K = B + E, the resummed series) fewer patches are
+    # within 1e-3.
     from paper_1510_00451_gb300 import surrogate as S
-    full = flows.continuous_spectrum(256)
-    a, b = np.abs(full.k1), np.abs(full.k2)
-    keep = (a >= 32) & (a < 64) & (b >= 32) & (b < 64)
-    band = flows.Spectrum(full.k1[keep], full.k2[keep], full.re[keep], full.im[keep])
-    N, kappa = 64, 1e-3
-    lv = mlsd.Levels(band, kappa, N, [32.0, 64.0], [32], patch_div=[32], cfl=0.2)
+    N, kappa = 128, 1e-3
     P = N * N
-    X, Y = S.make_dataset(lv, 1, [inputs.random_bases(P, kappa, 70 + i) for i in range(3)])
-    sur = mlsd.Surrogate(members=4, hidden=128, max_batch=512)
+    lv = mlsd.Levels(_octave_band(1510004510, 16, 32), kappa, N, [16.0, 32.0], [64],
+                     patch_div=[16], cfl=0.2)
+    X, Y = S.make_dataset(lv, 1, [inputs.random_bases(P, kappa, 70 + i) for i in range(2)])
+    lv.close()
+    sur = mlsd.Surrogate(members=4, hidden=128, max_batch=1024)
     for m in range(4):
         sur.set_params(m, inputs.mlp_init(mlsd.SUR_IN, 128, 90 + m))
-    losses = S.train(sur, X, Y, epochs=60, batch=512, lr=3e-3, seed=1, lr_final=1e-5)
-    assert max(losses) < 0.05                 # targets are O(1): the fit is far below that
+    losses = S.train(sur, X, Y, epochs=80, batch=1024, lr=3e-3, seed=1, lr_final=1e-5)
+    assert max(losses) < 1e-3
+    lt = mlsd.Levels(_octave_band(77, 16, 32), kappa, N, [16.0, 32.0], [64], patch_div=[16],
+                     cfl=0.2)
     dev = torch_mod.device("cuda:0")
     Bt = torch_mod.tensor(inputs.random_bases(P, kappa, 99), dtype=torch_mod.float64, device=dev)
     K_plain = torch_mod.zeros_like(Bt)
-    lv.solve_level(1, Bt, K_plain)
+    lt.solve_level(1, Bt, K_plain)
     K_sur = torch_mod.zeros_like(Bt)
-    n_fb = lv.solve_level_surrogate(sur, 1, Bt, K_sur, 3e-3)
-    assert lv.status() == 0 and sur.status() == 0
+    n_fb = lt.solve_level_surrogate(sur, 1, Bt, K_sur, 1e-3)
+    assert lt.status() == 0 and sur.status() == 0
     err = S.k_error(K_sur.cpu().numpy(), K_plain.cpu().numpy())
-    assert n_fb < P // 2, n_fb                  # most patch solves are replaced
-    assert np.median(err) < 2e-3, np.median(err)
-    assert err.max() < 0.05
+    assert n_fb < P // 5, n_fb                  # most patch solves are replaced
+    assert np.median(err) < 1e-4, np.median(err)
+    assert np.quantile(err, 0.99) <= 1e-3, np.quantile(err, 0.99)
+    K_net = torch_mod.zeros_like(Bt)
+    lt.solve_level_surrogate(sur, 1, Bt, K_net, 1e30)
+    sur0 = mlsd.Surrogate(members=4, hidden=128, max_batch=1024)    # zero weights: K = B + E
+    K_ser = torch_mod.zeros_like(Bt)
+    lt.solve_level_surrogate(sur0, 1, Bt, K_ser, 1e30)
+    e_net = S.k_error(K_net.cpu().numpy(), K_plain.cpu().numpy())
+    e_ser = S.k_error(K_ser.cpu().numpy(), K_plain.cpu().numpy())
+    assert np.mean(e_net <= 1e-3) > np.mean(e_ser <= 1e-3) + 0.005, \
+        (np.mean(e_net <= 1e-3), np.mean(e_ser <= 1e-3))
 
 
 def test_chain_in_surrogate_mode(mlsd, torch_mod):
@@ -301,9 +340,14 @@ def test_chain_in_surrogate_mode(mlsd, torch_mod):
     assert torch_mod.equal(K2, K_plain)
 
 
+def _oracle_target(K, B, psi):
+    _, _, E, _ = oracle.series_estimate(oracle.series(psi, B))
+    return oracle.surrogate_target(K, B, E)
+
+
 def test_dataset_targets_match_oracle(mlsd, torch_mod):
-    # mlsd_surrogate_dataset: Y = (K - B - Q) 30 / tr(B) from the library's own
-    # plain solves and features, against the oracle's patch solves and features
+    # mlsd_surrogate_dataset: Y = asinh((K - B - E) 300 / tr(B)) from the library's
+    # own plain solves and series, against the oracle's
     from tests._parity import oracle_level
     spec = flows.continuous_spectrum(40, seed=9)
     edges, N, kappa, n = [1, 4, 16, 41], 3, 2e-3, 32
@@ -323,11 +367,12 @@ def test_dataset_targets_match_oracle(mlsd, torch_mod):
     for p in range(P):
         ox = oracle.patch_origin(p % N, N, Nl, n); oy = oracle.patch_origin(p // N, N, Nl, n)
         psi = oracle.patch_psi(spec, Nl, ox, oy, n, use=(lev == 3) & (kind == 0))
-        f = oracle.features(psi, B[p], kappa)
         tr = B[p, 0] + B[p, 2]
-        want = (Kr[p] - B[p] - oracle.second_order_K(f, B[p])) * 30.0 / tr
-        scale = 30.0 * np.abs(Kr[p]).max() / tr
-        assert np.abs(Yg[p] - want).max() < 1e-4 * scale, (p, Yg[p], want)
+        want = _oracle_target(Kr[p], B[p], psi)
+        # in K units: sinh(Y) tr / 300 against the oracle's, to 1e-5 of K
+        dk = np.abs(np.sinh(Yg[p].astype(np.float64)) - np.sinh(want)) * tr / mlsd.SUR_Y_SCALE
+        assert dk.max() < 1e-5 * np.abs(Kr[p]).max(), (p, Yg[p], want)
+    assert np.abs(Yg).max() > 1e-3                      # targets are not all zero
 
 
 @pytest.mark.parametrize("g", range(8))
@@ -361,16 +406,17 @@ def test_symmetry_images_match_the_oracle(mlsd, torch_mod, g):
         Bg = square_symmetry_tensor(B[p], g)
         f = oracle.features(psi, Bg, kappa)
         # bfloat16 rows: the FP32 features (1e-5 of each group's scale) rounded to 8 bits
-        for lo, hi, tol in ((0, 578, 2e-5), (578, 582, 1e-6), (582, 585, 2e-5)):
+        for lo, hi, tol in ((0, 578, 2e-5), (578, 582, 1e-6), (582, 606, 2e-5)):
             d = np.abs(Xn[p, lo:hi] - f[lo:hi])
             assert np.all(d <= 2.0 ** -8 * np.abs(f[lo:hi]) + tol * np.abs(f[lo:hi]).max()), (g, p, lo)
-        assert not np.any(Xn[p, 585:])
+        assert not np.any(Xn[p, mlsd.SUR_FEATURES:])
         v1, v2 = oracle.velocity(psi, h)
         dt = oracle.micro_dt(h, float(np.max(np.abs(v1) + np.abs(v2))), Bg, 0.2)
         Kg = oracle.patch_k(psi, h, Bg, dt, nb, na)
         tr = Bg[0] + Bg[2]
-        want = (Kg - Bg - oracle.second_order_K(f, Bg)) * 30.0 / tr
-        assert np.abs(Yn[p] - want).max() < 1e-4 * 30.0 * np.abs(Kg).max() / tr, (g, p, Yn[p], want)
+        want = _oracle_target(Kg, Bg, psi)
+        dk = np.abs(np.sinh(Yn[p].astype(np.float64)) - np.sinh(want)) * tr / mlsd.SUR_Y_SCALE
+        assert dk.max() < 1e-5 * np.abs(Kg).max(), (g, p, Yn[p], want)
 
 
 def test_augmented_training_is_deterministic_and_learns(mlsd, torch_mod):
@@ -397,3 +443,41 @@ def test_augmented_training_is_deterministic_and_learns(mlsd, torch_mod):
         assert last[0] < 0.3 * first[0], (first, last)
         runs.append(sur.get_params(0))
     assert np.array_equal(runs[0], runs[1])
+
+
+def test_surrogate_chain_replays_as_a_graph(mlsd, torch_mod, monkeypatch):
+    # MLSD_SURROGATE chains run as one captured CUDA graph: the fallback solve is
+    # launched for every patch and reads the fallback count on the device, so no
+    # step needs the host (a host synchronisation inside the capture would fail
+    # it).  The replays equal the chain launched directly, with the same count;
+    # with every patch falling back the chain is the plain one.
+    spec = flows.combine(flows.cellular_two_scale(1.0, 0.4, 8), flows.continuous_spectrum(12, seed=3))
+    N, kappa = 6, 0.05
+    lv = mlsd.Levels(spec, kappa, N, [1, 8, 16], [32, 32], n_burn_fixed=60, n_avg_fixed=40)
+    dev = torch_mod.device("cuda:0")
+    P = N * N
+    K_plain = torch_mod.zeros(P, 3, dtype=torch_mod.float64, device=dev)
+    lv.effective_diffusivity(K_plain)
+    sur = mlsd.Surrogate(members=2, hidden=64, max_batch=64)
+    for m in range(2):
+        sur.set_params(m, inputs.mlp_init(mlsd.SUR_IN, 64, 11 + m) * (0.05 if m == 0 else 2.0))
+    for thr in (0.0, 2e-3, 1e30):
+        monkeypatch.delenv("MLSD_NO_GRAPH", raising=False)
+        lv.attach_surrogate(2, sur, thr)
+        K1 = torch_mod.zeros(P, 3, dtype=torch_mod.float64, device=dev)
+        lv.effective_diffusivity(K1, mode=mlsd.MLSD_SURROGATE)          # capture + replay
+        n1 = lv.surrogate_fallbacks(2)
+        K1b = torch_mod.zeros_like(K1)
+        lv.effective_diffusivity(K1b, mode=mlsd.MLSD_SURROGATE)         # new output: capture again
+        lv.effective_diffusivity(K1b, mode=mlsd.MLSD_SURROGATE)         # replay
+        assert lv.status() == 0 and sur.status() == 0
+        monkeypatch.setenv("MLSD_NO_GRAPH", "1")
+        K2 = torch_mod.zeros_like(K1)
+        lv.effective_diffusivity(K2, mode=mlsd.MLSD_SURROGATE)
+        assert lv.surrogate_fallbacks(2) == n1
+        assert torch_mod.equal(K1, K1b) and torch_mod.equal(K1, K2), thr
+        if thr == 0.0:
+            assert n1 == P
+            assert rel_l2(K1.cpu().numpy(), K_plain.cpu().numpy()) < 1e-6
+        if thr == 1e30:
+            assert n1 == 0

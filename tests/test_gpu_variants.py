@@ -14,9 +14,10 @@ pytestmark = pytest.mark.gpu
 FP32 = {32: ["4x8", "4x8s", "4x8r", "4x4", "2x8", "2x4", "4x4p", "2x4p", "4x2p"],
         64: ["4x8", "4x8m3", "4x8m3s", "4x8m3r", "4x8m2r", "4x4r", "4x4m2r", "4x4m2s", "4x4", "2x8",
              "8x4", "2x4", "4x4p", "2x4p", "4x2p"],
-        128: ["4x8m3c4", "4x8m3c4s", "4x8m3c4n", "4x8m3c4b", "4x4c4b", "4x8c2", "4x4c4"],
+        128: ["4x8m3c4", "4x8m3c4s", "4x8m3c4n", "4x8m3c4b", "4x4c4b", "4x8c2", "4x4c4",
+              "2x8m2c4b", "2x8m2c4"],
         256: ["4x8c8", "4x8c8s", "4x8m2c8s", "4x8c8n", "4x8m2c8n", "4x8m3c16n", "4x8c8b", "4x8m3c16b",
-              "4x4c8b", "4x4c8", "4x8m3c16"]}
+              "4x4c8b", "4x4c8", "4x8m3c16", "2x8c8b", "2x8c8"]}
 FP64 = {32: ["2x4", "4x4"], 64: ["2x4", "4x4"]}
 CASES = ([(n, "fp32", t) for n, ts in FP32.items() for t in ts]
          + [(n, "fp64", t) for n, ts in FP64.items() for t in ts])
