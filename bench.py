@@ -360,75 +360,100 @@ def _fit_k11(profile, t_end, u_left=1.0, u_right=0.0):
     return math.exp(0.5 * (lo + hi))
 
 
-def sec4_case(amps=(1.0 / 3.0, 2.5), N=64, nf=512, t_end=0.4 * math.pi ** 2):
-    """The paper's Sec. 4 set-up with two separated cellular modes (the structure
-    of its Sec. 4.2 example): psi = a (sin 5x sin 5y + sin 25x sin 25y), kappa = 1,
-    u = 1 at x1 = 0 and 0 at x1 = 2 pi, periodic in x2, step initial condition,
-    t_end = 0.4 pi^2 (the paper's t = 0.1 on [0,1]^2; x -> 2 pi x, t -> 4 pi^2 t).
-    a = 1/3 is the printed amplitude; a = 2.5 gives K near the printed K values.
-    SHMM: two levels (edges 1, 6, 26; patch sides 2 pi and 2 pi / 5; 64^2
-    patches; full relaxation window), then the macro solve on N x N.  Reference:
-    the direct simulation on nf x nf, and the same without the flow.  Compared:
-    the x2-averaged profiles at the macro nodes, and K11 of each DNS, fitted by
-    the homogenized constant-K solution on the DNS grid (the no-flow DNS
-    checks the fit: it should return kappa)."""
+def _sec4_compare(spec, edges, patch_n, patch_div, N, nf, t_end, kappa=1.0):
+    """SHMM (level chain with the full relaxation window, macro solve on N x N)
+    against the direct simulation on nf x nf, both with the Sec. 4 boundaries,
+    from the step; x2-averaged profiles and the K11 fitted to the DNS profile."""
+    import torch
+    import inputs
+    import paper_1510_00451_gb300 as mlsd
+    dev = torch.device("cuda", _local_rank())
+    r = nf // N
+    t0 = time.perf_counter()
+    lv = mlsd.Levels(spec, kappa, N, edges, patch_n, patch_div=patch_div, cfl=0.2)
+    K = torch.zeros(N * N, 3, dtype=torch.float64, device=dev)
+    lv.effective_diffusivity(K)
+    torch.cuda.synchronize()
+    t_chain = time.perf_counter() - t0
+    assert lv.status() == 0
+    sizes = [sorted(set(int(x) for x in lv.patch_sizes(l + 1))) for l in range(len(edges) - 1)]
+    lv.close()
+
+    def macro(Kf):
+        dt = mlsd.macro_dt(Kf, N, 0.2)
+        ns = max(1, math.ceil(t_end / dt))
+        U = torch.tensor(inputs.step_u0(N), dtype=torch.float64, device=dev)
+        mlsd.macro_step_dirichlet(U, Kf, t_end / ns, ns, 1.0, 0.0)
+        return U.cpu().numpy().mean(0)
+
+    def dns(psi):
+        # FP64: ~5e5 steps of a relaxing profile stall in FP32 (increments below half an ulp)
+        dt = mlsd.dns_dt(psi, kappa, 0.2)
+        ns = math.ceil(t_end / dt)
+        u = torch.tensor(inputs.step_u0(nf), dtype=torch.float64, device=dev)
+        ut = torch.empty_like(u)
+        mlsd.dns_run_dirichlet(u, ut, psi, kappa, t_end / ns, ns, 1.0, 0.0)
+        torch.cuda.synchronize()
+        return u.cpu().numpy().mean(0), ns
+
+    prof_shmm = macro(K)
+    prof_none = macro(torch.tensor(np.tile([kappa, 0.0, kappa], (N * N, 1)), dtype=torch.float64,
+                                   device=dev))
+    psi = torch.empty(nf, nf, dtype=torch.float32, device=dev)
+    mlsd.grid_psi(spec, nf, psi)
+    t0 = time.perf_counter()
+    prof_dns, ns = dns(psi)
+    t_dns = time.perf_counter() - t0
+    Kn = K.cpu().numpy()
+    return {"K_shmm_mean": Kn.mean(0).tolist(), "K_shmm_min": Kn.min(0).tolist(),
+            "K_shmm_max": Kn.max(0).tolist(), "patch_sizes": sizes,
+            "K11_dns_fit": _fit_k11(prof_dns, t_end),
+            "K11_shmm_profile_fit": _fit_k11(prof_shmm, t_end),
+            "shmm_vs_dns": _profile_gap(prof_shmm, prof_dns[::r]),
+            "no_advection_vs_dns": _profile_gap(prof_none, prof_dns[::r]),
+            "dns": {"grid": nf, "steps": ns, "dt": t_end / ns, "seconds": t_dns},
+            "chain_seconds": t_chain}
+
+
+def sec4_case(N=64, nf=512, t_end=0.4 * math.pi ** 2):
+    """The paper's Sec. 4 set-up (kappa = 1, u = 1 at x1 = 0 and 0 at x1 = 2 pi,
+    periodic in x2, step initial condition, t_end = 0.4 pi^2: the paper's t = 0.1
+    on [0,1]^2 under x -> 2 pi x, t -> 4 pi^2 t) on two of its flows:
+    * two separated cellular modes (Sec. 4.2): psi = a (sin 5x sin 5y + sin 25x
+      sin 25y), a = 1/3 (printed) and 2.5 (K near the printed values); two levels
+      (edges 1, 6, 26; patch sides 2 pi and 2 pi / 5; 64^2 patches);
+    * a continuous spectrum (Sec. 4.4): random phases, 1 <= |k| <= 50, |psi_hat|
+      ~ |k|^-3, rms speed 4; three levels (edges 1, 5, 25, 51; patch sides 2 pi,
+      2 pi / 5, 2 pi / 25; sizes by the size rule).
+    SHMM: the full relaxation window, then the macro solve on N x N.  Reference:
+    the direct simulation on nf x nf (the paper's 512^2), and the same without the
+    flow (its fit checks the K11 fit, which should return kappa).  Compared: the
+    x2-averaged profiles at the macro nodes and K11 fitted to each profile."""
     import torch
     import inputs
     from inputs import flows
     import paper_1510_00451_gb300 as mlsd
     dev = torch.device("cuda", _local_rank())
-    kappa, r = 1.0, nf // N
-    out = []
     zero = torch.zeros(nf, nf, dtype=torch.float32, device=dev)
-
-    def dns(psi):
-        dt = mlsd.dns_dt(psi, kappa, 0.2)
-        ns = math.ceil(t_end / dt)
-        u = torch.tensor(inputs.step_u0(nf), dtype=torch.float32, device=dev)
-        ut = torch.empty_like(u)
-        t0 = time.perf_counter()
-        mlsd.dns_run_dirichlet(u, ut, psi, kappa, t_end / ns, ns, 1.0, 0.0)
-        torch.cuda.synchronize()
-        return u.cpu().numpy().astype(np.float64).mean(0), ns, time.perf_counter() - t0
-
-    prof0, _, _ = dns(zero)
-    k11_fit_noflow = _fit_k11(prof0, t_end)
-    for amp in amps:
+    dt = mlsd.dns_dt(zero, 1.0, 0.2)
+    ns = math.ceil(t_end / dt)
+    u = torch.tensor(inputs.step_u0(nf), dtype=torch.float64, device=dev)
+    mlsd.dns_run_dirichlet(u, torch.empty_like(u), zero, 1.0, t_end / ns, ns, 1.0, 0.0)
+    k11_noflow = _fit_k11(u.cpu().numpy().mean(0), t_end)
+    cases = []
+    for amp in (1.0 / 3.0, 2.5):
         spec = flows.cellular([(amp, 5, 5), (amp, 25, 25)])
-        t0 = time.perf_counter()
-        lv = mlsd.Levels(spec, kappa, N, [1.0, 6.0, 26.0], [64, 64], patch_div=[1, 5], cfl=0.2)
-        K = torch.zeros(N * N, 3, dtype=torch.float64, device=dev)
-        lv.effective_diffusivity(K)
-        torch.cuda.synchronize()
-        t_chain = time.perf_counter() - t0
-        assert lv.status() == 0
-        lv.close()
-
-        def macro(Kf):
-            dt = mlsd.macro_dt(Kf, N, 0.2)
-            ns = max(1, math.ceil(t_end / dt))
-            U = torch.tensor(inputs.step_u0(N), dtype=torch.float64, device=dev)
-            mlsd.macro_step_dirichlet(U, Kf, t_end / ns, ns, 1.0, 0.0)
-            return U.cpu().numpy().mean(0)
-
-        prof_shmm = macro(K)
-        prof_none = macro(torch.tensor(np.tile([kappa, 0.0, kappa], (N * N, 1)),
-                                       dtype=torch.float64, device=dev))
-        psi = torch.empty(nf, nf, dtype=torch.float32, device=dev)
-        mlsd.grid_psi(spec, nf, psi)
-        prof_dns, ns, t_dns = dns(psi)
-        Kn = K.cpu().numpy()
-        out.append({"amplitude": amp, "K_shmm": Kn.mean(0).tolist(),
-                    "K_shmm_node_spread": float(np.abs(Kn - Kn.mean(0)).max()),
-                    "K11_dns_fit": _fit_k11(prof_dns, t_end),
-                    "shmm_vs_dns": _profile_gap(prof_shmm, prof_dns[::r]),
-                    "no_advection_vs_dns": _profile_gap(prof_none, prof_dns[::r]),
-                    "dns": {"grid": nf, "steps": ns, "dt": t_end / ns, "seconds": t_dns},
-                    "chain_seconds": t_chain})
-    return {"workload": f"Sec. 4 set-up, psi = a(sin5x sin5y + sin25x sin25y), kappa=1, "
-                        f"Dirichlet x1 / periodic x2, step IC, t={t_end:.4f}; SHMM 2 levels, "
-                        f"{N}^2 macro, 64^2 patches; DNS {nf}^2",
-            "K11_fit_of_the_no_flow_dns": k11_fit_noflow, "cases": out}
+        r = _sec4_compare(spec, [1.0, 6.0, 26.0], [64, 64], [1, 5], N, nf, t_end)
+        cases.append({"flow": f"two cellular modes (5, 25), a = {amp:.4g}", **r})
+    # the continuous spectrum's K is larger: at t_end its profile is nearly relaxed,
+    # so it is compared at t_end / 4 (the paper's t = 0.025)
+    spec = flows.continuous_spectrum(50, seed=1510004510, slope=-3.0, vrms=4.0)
+    r = _sec4_compare(spec, [1.0, 5.0, 25.0, 51.0], [0, 0, 0], [1, 5, 25], N, nf, t_end / 4)
+    cases.append({"flow": "continuous spectrum 1 <= |k| <= 50, |psi_hat| ~ k^-3, rms speed 4",
+                  "t": t_end / 4, **r})
+    return {"workload": f"Sec. 4 set-up: kappa=1, Dirichlet x1 / periodic x2, step IC, "
+                        f"t={t_end:.4f}; SHMM on {N}^2 macro nodes; DNS {nf}^2",
+            "K11_fit_of_the_no_flow_dns": k11_noflow, "cases": cases}
 
 
 def _fit_k_periodic(U0, U, t_end):
@@ -738,6 +763,32 @@ def mlp_case(M=65536, members=4, hidden=256):
     return 0 if ok else 1
 
 
+def series_case(N=256, reps=3):
+    """Surrogate features of every patch of the 6th-octave level (65536 patches of
+    32^2): k_features (DFT window) and k_series (moments T_2..T_19 by FFTs and
+    their resummation), timed with CUDA events (ncu case)."""
+    import torch
+    import inputs
+    import paper_1510_00451_gb300 as mlsd
+    dev = torch.device("cuda", _local_rank())
+    lv = _octave_level(SUR_TEST_FLOW, 32, 64, 32, N, 1e-3)
+    P = N * N
+    B = torch.tensor(inputs.random_bases(P, 1e-3, 3), dtype=torch.float64, device=dev)
+    X = torch.empty(P, mlsd.SUR_IN, dtype=torch.bfloat16, device=dev)
+    lv.features(1, B, X)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        lv.features(1, B, X)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ok = lv.status() == 0 and bool(torch.isfinite(X.float()).all().item())
+    print(json.dumps({"case": "series-profile", "ok": ok, "patches": P,
+                      "ms_per_call": e0.elapsed_time(e1) / reps}), flush=True)
+    return 0 if ok else 1
+
+
 def train_case(rows=16384, epochs=2, members=4, hidden=256, batch=2048):
     """Surrogate training steps on random rows of the training shape (ncu case):
     `epochs` passes of rows / batch Adam steps per member, timed with CUDA events
@@ -846,10 +897,12 @@ def main():
     ap.add_argument("--no-dns", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--no-experiments", action="store_true",
+                    help="skip the Sec. 4 comparisons (set-up, off-diagonal stress, geometry)")
     ap.add_argument("--case", default="full",
                     choices=["full", "profile", "dns-profile", "dns-full", "surrogate", "uneven",
                              "mlp-profile", "cluster-profile", "train-profile", "sec4",
-                             "spectrum-dns", "offdiag", "geometry"],
+                             "spectrum-dns", "offdiag", "geometry", "series-profile"],
                     help="profile: one pass of the same workload with a fixed 200-step window "
                          "per patch (a small case for ncu captures); prints no bench line")
     args = ap.parse_args()
@@ -876,6 +929,8 @@ def main():
     if args.case == "sec4":
         print(json.dumps({"case": "sec4", **sec4_case()}), flush=True)
         return 0
+    if args.case == "series-profile":
+        return series_case()
     if args.case == "geometry":
         print(json.dumps({"case": "geometry", **geometry_case()}), flush=True)
         return 0
@@ -1017,6 +1072,15 @@ def main():
     unev = None
     if not args.no_uneven:
         unev = uneven_case()
+    experiments = None
+    if not args.no_experiments and rank == 0:
+        experiments = {}
+        for name, fn in (("sec4_setup", sec4_case), ("offdiag_stress", offdiag_case),
+                         ("patch_geometry", geometry_case)):
+            try:
+                experiments[name] = fn()
+            except Exception as exc:           # reported in the line, not fatal to it
+                experiments[name] = {"error": repr(exc)}
 
     if rank != 0:
         if world > 1:
@@ -1074,6 +1138,7 @@ def main():
         "dns": dns,
         "surrogate": sur,
         "uneven_sizes": unev,
+        "experiments": experiments,
     }
     line.update(line_extra)
     print(json.dumps(line), flush=True)

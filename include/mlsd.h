@@ -437,11 +437,16 @@ int mlsd_dns_run(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev, d
  * periodic in x2), posed on [0, 2 pi] x [0, 2 pi) as mlsd_macro_step_dirichlet:
  * column 0 of u_dev is set to u_left and held, the virtual column nf has the
  * value u_right; psi (and so v) stays periodic.  One launch per RK stage (the
- * paper's 512 x 512 reference, L2-resident); any nf >= 4.  u_tmp_dev is a
- * caller-provided work field of the same size.  Asynchronous on the stream. */
-int mlsd_dns_run_dirichlet(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev,
-                           double kappa, double dt, int nsteps, double u_left, double u_right,
-                           void *cuda_stream);
+ * paper's 512 x 512 reference, L2-resident); any nf >= 4.
+ *   u_dev, u_tmp_dev  device [nf][nf], float (MLSD_FP32) or double (MLSD_FP64);
+ *                     u_tmp_dev is a caller-provided work field
+ *   psi_dev           device [nf][nf] float (mlsd_grid_psi)
+ * FP64 exists for the paper's long runs (~5e5 steps at its time step): there
+ * the FP32 increments of a nearly relaxed profile fall below half an ulp and
+ * the field stops diffusing.  Asynchronous on the stream.                   */
+int mlsd_dns_run_dirichlet(int nf, void *u_dev, void *u_tmp_dev, const float *psi_dev,
+                           int precision, double kappa, double dt, int nsteps, double u_left,
+                           double u_right, void *cuda_stream);
 
 /* Stable DNS time step: dt = cfl * min(h / max(|v1| + |v2|), h^2 / (4 kappa)),
  * v from psi by central differences, h = 2*pi/nf.  Blocks until known.    */

@@ -114,20 +114,44 @@ static double psi_at(int n_modes, const int *k1, const int *k2, const double *re
     return s;
 }
 
+/* The selected modes (use[t] != 0, or all with use == NULL) copied in their  */
+/* order to a list of their own, so that a synthesis visits only those; the   */
+/* sums psi_at forms over the list are the same sums in the same order.       */
+typedef struct { int n; int *k1, *k2; double *re, *im; } mode_list;
+
+static mode_list select_modes(int n_modes, const int *k1, const int *k2, const double *re,
+                              const double *im, const unsigned char *use)
+{
+    mode_list m;
+    m.n = 0;
+    m.k1 = malloc(sizeof(int) * (n_modes + 1)); m.k2 = malloc(sizeof(int) * (n_modes + 1));
+    m.re = malloc(sizeof(double) * (n_modes + 1)); m.im = malloc(sizeof(double) * (n_modes + 1));
+    for (int t = 0; t < n_modes; ++t) {
+        if (use && !use[t]) continue;
+        m.k1[m.n] = k1[t]; m.k2[m.n] = k2[t]; m.re[m.n] = re[t]; m.im[m.n] = im[t];
+        ++m.n;
+    }
+    return m;
+}
+
+static void free_modes(mode_list *m) { free(m->k1); free(m->k2); free(m->re); free(m->im); }
+
 /* psi of the selected modes on the patch nodes, patch mean removed. */
 void orc_patch_psi(int n_modes, const int *k1, const int *k2, const double *re,
                    const double *im, const unsigned char *use, long Nl, long ox, long oy,
                    int n, double *psi)
 {
+    mode_list md = select_modes(n_modes, k1, k2, re, im, use);
     double mean = 0.0;
     for (int b = 0; b < n; ++b)
         for (int a = 0; a < n; ++a) {
-            double p = psi_at(n_modes, k1, k2, re, im, use, Nl, ox + a, oy + b);
+            double p = psi_at(md.n, md.k1, md.k2, md.re, md.im, NULL, Nl, ox + a, oy + b);
             psi[(long)b * n + a] = p;
             mean += p;
         }
     mean /= (double)n * (double)n;
     for (long c = 0; c < (long)n * n; ++c) psi[c] -= mean;
+    free_modes(&md);
 }
 
 /* Sec. 2.1: v = (-d psi/dx2, d psi/dx1) with central differences; indices  */
@@ -328,6 +352,11 @@ void orc_offdiag_q(int n_modes, const int *k1, const int *k2, const double *re,
     int r21 = line_refine(n_modes, k1, use21, L, n);
     int any12 = 0, any21 = 0;
     for (int t = 0; t < n_modes; ++t) { any12 |= use12[t]; any21 |= use21[t]; }
+    mode_list m12 = select_modes(n_modes, k1, k2, re, im, use12);
+    mode_list m21 = select_modes(n_modes, k1, k2, re, im, use21);
+    /* columns and rows are independent; the threads split them (a team only  */
+    /* where no enclosing parallel region is active, e.g. a one-node chain)    */
+#pragma omp parallel for schedule(dynamic, 1)
     for (int a = 0; a < n; ++a) {
         q12[a] = 0.0;
         if (!any12) continue;
@@ -338,7 +367,8 @@ void orc_offdiag_q(int n_modes, const int *k1, const int *k2, const double *re,
         double mean = 0.0, sq = 0.0;
         double *g = malloc(sizeof(double) * m);
         for (long s = 0; s < m; ++s) {
-            g[s] = psi_at(n_modes, k1, k2, re, im, use12, Nr, (ox + a) * (long)r12, oy * r12 + s);
+            g[s] = psi_at(m12.n, m12.k1, m12.k2, m12.re, m12.im, NULL, Nr, (ox + a) * (long)r12,
+                          oy * r12 + s);
             mean += g[s];
         }
         mean /= (double)m;
@@ -346,6 +376,7 @@ void orc_offdiag_q(int n_modes, const int *k1, const int *k2, const double *re,
         q12[a] = sq / (double)m;
         free(g);
     }
+#pragma omp parallel for schedule(dynamic, 1)
     for (int b = 0; b < n; ++b) {
         q21[b] = 0.0;
         if (!any21) continue;
@@ -353,7 +384,8 @@ void orc_offdiag_q(int n_modes, const int *k1, const int *k2, const double *re,
         double mean = 0.0, sq = 0.0;
         double *g = malloc(sizeof(double) * m);
         for (long s = 0; s < m; ++s) {
-            g[s] = psi_at(n_modes, k1, k2, re, im, use21, Nr, ox * r21 + s, (oy + b) * (long)r21);
+            g[s] = psi_at(m21.n, m21.k1, m21.k2, m21.re, m21.im, NULL, Nr, ox * r21 + s,
+                          (oy + b) * (long)r21);
             mean += g[s];
         }
         mean /= (double)m;
@@ -361,6 +393,8 @@ void orc_offdiag_q(int n_modes, const int *k1, const int *k2, const double *re,
         q21[b] = sq / (double)m;
         free(g);
     }
+    free_modes(&m12);
+    free_modes(&m21);
 }
 
 /* Algorithms 1 and 2 given the line variances:                             */
@@ -466,7 +500,7 @@ void orc_chain(int n_modes, const int *k1, const int *k2, const double *re, cons
     int *lev = malloc(sizeof(int) * n_modes), *kind = malloc(sizeof(int) * n_modes);
     orc_band_of(n_modes, k1, k2, n_levels, edges, lev, kind);
 
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) if (n_nodes > 1)
     for (int p = 0; p < n_nodes; ++p) {
         unsigned char *ud = malloc(n_modes), *u12 = malloc(n_modes), *u21 = malloc(n_modes);
         double (*Bl)[3] = malloc(sizeof(double) * 3 * (n_levels + 2));

@@ -93,7 +93,7 @@ _lib.mlsd_launch_count.restype = _L
 _lib.mlsd_patch_sizes.argtypes = [_P, _I, _P]
 _lib.mlsd_dns_dt.argtypes = [_I, _P, _D, _D, ctypes.POINTER(_D), _P]
 _lib.mlsd_macro_step_dirichlet.argtypes = [_I, _P, _I, _P, _D, _I, _D, _D, _P, _P]
-_lib.mlsd_dns_run_dirichlet.argtypes = [_I, _P, _P, _P, _D, _D, _I, _D, _D, _P]
+_lib.mlsd_dns_run_dirichlet.argtypes = [_I, _P, _P, _P, _I, _D, _D, _I, _D, _D, _P]
 _lib.mlsd_check_wait_timeout.argtypes = [_P, _I, _P]
 _lib.mlsd_coarse_grain_noalloc.argtypes = [_I, _P, _I, _P, _P, _P]
 _lib.mlsd_surrogate_param_count.argtypes = [_I]
@@ -323,7 +323,10 @@ def dns_run(u, u_tmp, psi, kappa, dt, nsteps, stream=None):
 
 
 def dns_run_dirichlet(u, u_tmp, psi, kappa, dt, nsteps, u_left=1.0, u_right=0.0, stream=None):
-    _check(_lib.mlsd_dns_run_dirichlet(u.shape[0], _dptr(u), _dptr(u_tmp), _dptr(psi),
+    """Direct simulation with the Sec. 4 boundaries; u, u_tmp float32 or float64, psi float32."""
+    import torch
+    prec = MLSD_FP64 if u.dtype == torch.float64 else MLSD_FP32
+    _check(_lib.mlsd_dns_run_dirichlet(u.shape[0], _dptr(u), _dptr(u_tmp), _dptr(psi), prec,
                                        float(kappa), float(dt), int(nsteps), float(u_left),
                                        float(u_right), _stream(stream)), "mlsd_dns_run_dirichlet")
 

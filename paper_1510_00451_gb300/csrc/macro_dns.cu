@@ -345,30 +345,30 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
 // out = (u + s + dt f(s)) / 2 with `s` the stage-1 field.  The same folded
 // constants as k_dns_step: cA = dt / (4 h^2) on psi differences times u
 // differences, cD = dt kappa / h^2 on the Laplacian (kept as a difference).
-template <bool SECOND>
-__global__ void k_dns_dir_stage(int nf, const float *__restrict__ u, const float *__restrict__ sfield,
-                                const float *__restrict__ psi, float *__restrict__ out, float cA,
-                                float cD, float ul, float ur)
+template <bool SECOND, typename real>
+__global__ void k_dns_dir_stage(int nf, const real *__restrict__ u, const real *__restrict__ sfield,
+                                const float *__restrict__ psi, real *__restrict__ out, real cA,
+                                real cD, real ul, real ur)
 {
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= (long long)nf * nf) return;
     const int a = (int)(c % nf), b = (int)(c / nf);
     if (a == 0) { out[c] = ul; return; }
-    const float *x = SECOND ? sfield : u;
+    const real *x = SECOND ? sfield : u;
     const int bp = b + 1 == nf ? 0 : b + 1, bm = b == 0 ? nf - 1 : b - 1;
     const int ap = a + 1 == nf ? 0 : a + 1;
     const long long row = (long long)b * nf;
-    const float xc = x[c];
-    const float xE = a + 1 == nf ? ur : x[row + ap], xW = x[c - 1];
-    const float xN = x[(long long)bp * nf + a], xS = x[(long long)bm * nf + a];
+    const real xc = x[c];
+    const real xE = a + 1 == nf ? ur : x[row + ap], xW = x[c - 1];
+    const real xN = x[(long long)bp * nf + a], xS = x[(long long)bm * nf + a];
     // dt (v1 D0x + v2 D0y) x = cA [(psiS - psiN)(xE - xW) + (psiE - psiW)(xN - xS)]
-    const float pN = psi[(long long)bp * nf + a], pS = psi[(long long)bm * nf + a];
-    const float pE = psi[row + ap], pW = psi[row + a - 1];
-    float t = (pS - pN) * (xE - xW);
-    t = fmaf(pE - pW, xN - xS, t);
-    const float lap = fmaf(-4.0f, xc, (xE + xW) + (xN + xS));
-    const float g = fmaf(cA, t, fmaf(cD, lap, xc));
-    out[c] = SECOND ? 0.5f * (u[c] + g) : g;
+    const real pN = psi[(long long)bp * nf + a], pS = psi[(long long)bm * nf + a];
+    const real pE = psi[row + ap], pW = psi[row + a - 1];
+    real t = (pS - pN) * (xE - xW);
+    t = fma(pE - pW, xN - xS, t);
+    const real lap = fma((real)-4, xc, (xE + xW) + (xN + xS));
+    const real g = fma(cA, t, fma(cD, lap, xc));
+    out[c] = SECOND ? (real)0.5 * (u[c] + g) : g;
 }
 
 // max over the grid of |v1| + |v2| (non-negative floats order like their bit patterns)
@@ -558,23 +558,37 @@ cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kap
     return cudaGetLastError();
 }
 
-cudaError_t dns_run_dirichlet(int nf, float *u, float *u_tmp, const float *psi, double kappa,
-                              double dt, int nsteps, double ul, double ur, cudaStream_t s)
+template <typename real>
+static cudaError_t dns_run_dirichlet_t(int nf, real *u, real *u_tmp, const float *psi,
+                                       double kappa, double dt, int nsteps, double ul, double ur,
+                                       cudaStream_t s)
 {
     const double h = 2.0 * kPi / nf;
-    const float cA = (float)(dt / (4.0 * h * h));
-    const float cD = (float)(dt * kappa / (h * h));
+    const real cA = (real)(dt / (4.0 * h * h));
+    const real cD = (real)(dt * kappa / (h * h));
     const long long n2 = (long long)nf * nf;
     const unsigned nb = (unsigned)((n2 + 255) / 256);
     count_launches(1 + 2 * (long long)nsteps);
-    k_set_col0<float><<<(nf + 255) / 256, 256, 0, s>>>(nf, u, (float)ul);
+    k_set_col0<real><<<(nf + 255) / 256, 256, 0, s>>>(nf, u, (real)ul);
     for (int st = 0; st < nsteps; ++st) {
-        k_dns_dir_stage<false><<<nb, 256, 0, s>>>(nf, u, nullptr, psi, u_tmp, cA, cD, (float)ul,
-                                                  (float)ur);
+        k_dns_dir_stage<false, real><<<nb, 256, 0, s>>>(nf, u, nullptr, psi, u_tmp, cA, cD,
+                                                        (real)ul, (real)ur);
         // stage 2 writes u in place: each node reads only its own u
-        k_dns_dir_stage<true><<<nb, 256, 0, s>>>(nf, u, u_tmp, psi, u, cA, cD, (float)ul, (float)ur);
+        k_dns_dir_stage<true, real><<<nb, 256, 0, s>>>(nf, u, u_tmp, psi, u, cA, cD, (real)ul,
+                                                       (real)ur);
     }
     return cudaGetLastError();
+}
+
+cudaError_t dns_run_dirichlet(int nf, void *u, void *u_tmp, const float *psi, int precision,
+                              double kappa, double dt, int nsteps, double ul, double ur,
+                              cudaStream_t s)
+{
+    if (precision == MLSD_FP64)
+        return dns_run_dirichlet_t<double>(nf, static_cast<double *>(u), static_cast<double *>(u_tmp),
+                                           psi, kappa, dt, nsteps, ul, ur, s);
+    return dns_run_dirichlet_t<float>(nf, static_cast<float *>(u), static_cast<float *>(u_tmp), psi,
+                                      kappa, dt, nsteps, ul, ur, s);
 }
 
 cudaError_t dns_vmax(int nf, const float *psi, unsigned *vmax_bits, cudaStream_t s)

@@ -45,6 +45,10 @@ struct PatchVariant {
 };
 
 int patch_variants(int n, int precision, std::vector<PatchVariant> &out);
+// the tilings of each patch size, compiled in their own translation units
+int patch_variants_n32(int precision, std::vector<PatchVariant> &out);
+int patch_variants_n64(int precision, std::vector<PatchVariant> &out);
+int patch_variants_cluster(int n, std::vector<PatchVariant> &out);
 cudaError_t launch_patch(const PatchVariant &v, const PatchParams &p, long long grid,
                          cudaStream_t s);
 
@@ -124,8 +128,9 @@ cudaError_t macro_run(int N, void *U, int precision, const double *K, double dt,
 cudaError_t macro_run_dirichlet(int N, void *U, int precision, const double *K, double dt,
                                 int nsteps, double ul, double ur, double *mass_dev, void *scratch,
                                 cudaStream_t s);
-cudaError_t dns_run_dirichlet(int nf, float *u, float *u_tmp, const float *psi, double kappa,
-                              double dt, int nsteps, double ul, double ur, cudaStream_t s);
+cudaError_t dns_run_dirichlet(int nf, void *u, void *u_tmp, const float *psi, int precision,
+                              double kappa, double dt, int nsteps, double ul, double ur,
+                              cudaStream_t s);
 size_t macro_scratch_bytes(int N, int precision, int nsteps);
 cudaError_t macro_dt_max(int N, const double *K, double *max_dev, cudaStream_t s);
 

@@ -1,0 +1,38 @@
+// Patch-kernel tilings of 128^2 and 256^2 patches: each field split over a
+// thread-block cluster (FP32).  A translation unit of its own, so that the
+// instantiations compile in parallel with the others.
+#include "patch_kernels.cuh"
+
+namespace mlsd {
+
+int patch_variants_cluster(int n, std::vector<PatchVariant> &out)
+{
+    if (n == 128) {
+        add_variant<128, 4, 8, float, 3, 4>(out);
+        add_variant<128, 4, 8, float, 3, 4, 1>(out);
+        add_variant<128, 4, 8, float, 3, 4, 2>(out);
+        add_variant<128, 4, 8, float, 3, 4, 3>(out);
+        add_variant<128, 4, 4, float, 1, 4, 3>(out);
+        add_variant<128, 4, 8, float, 1, 2>(out);
+        add_variant<128, 4, 4, float, 1, 4>(out);
+        add_variant<128, 2, 8, float, 2, 4, 3>(out);      // 2x8 cells: 16 warps per SM
+        add_variant<128, 2, 8, float, 2, 4>(out);
+    } else if (n == 256) {
+        add_variant<256, 4, 8, float, 1, 8>(out);
+        add_variant<256, 4, 8, float, 1, 8, 1>(out);
+        add_variant<256, 4, 8, float, 2, 8, 1>(out);
+        add_variant<256, 4, 8, float, 1, 8, 2>(out);
+        add_variant<256, 4, 8, float, 2, 8, 2>(out);
+        add_variant<256, 4, 8, float, 3, 16, 2>(out);
+        add_variant<256, 4, 8, float, 1, 8, 3>(out);
+        add_variant<256, 4, 8, float, 3, 16, 3>(out);
+        add_variant<256, 4, 4, float, 1, 8, 3>(out);
+        add_variant<256, 4, 4, float, 1, 8>(out);
+        add_variant<256, 4, 8, float, 3, 16>(out);
+        add_variant<256, 2, 8, float, 1, 8, 3>(out);      // 2x8 cells: 16 warps per SM
+        add_variant<256, 2, 8, float, 1, 8>(out);
+    }
+    return (int)out.size();
+}
+
+}  // namespace mlsd

@@ -1031,15 +1031,16 @@ int mlsd_dns_run(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev, d
     return MLSD_OK;
 }
 
-int mlsd_dns_run_dirichlet(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev,
-                           double kappa, double dt, int nsteps, double u_left, double u_right,
-                           void *cuda_stream)
+int mlsd_dns_run_dirichlet(int nf, void *u_dev, void *u_tmp_dev, const float *psi_dev,
+                           int precision, double kappa, double dt, int nsteps, double u_left,
+                           double u_right, void *cuda_stream)
 {
     if (nf < 4 || !u_dev || !u_tmp_dev || !psi_dev || u_dev == u_tmp_dev || !(kappa >= 0) ||
         !(dt > 0) || nsteps < 0 || !std::isfinite(u_left) || !std::isfinite(u_right))
         return MLSD_EINVAL;
-    CK(dns_run_dirichlet(nf, u_dev, u_tmp_dev, psi_dev, kappa, dt, nsteps, u_left, u_right,
-                         static_cast<cudaStream_t>(cuda_stream)));
+    if (precision != MLSD_FP32 && precision != MLSD_FP64) return MLSD_EINVAL;
+    CK(dns_run_dirichlet(nf, u_dev, u_tmp_dev, psi_dev, precision, kappa, dt, nsteps, u_left,
+                         u_right, static_cast<cudaStream_t>(cuda_stream)));
     return MLSD_OK;
 }
 

@@ -38,6 +38,7 @@ __global__ void k_features(const float *band, long long Nl, long long tile, int 
     float *psi = reinterpret_cast<float *>(smem_raw);              // [n][n]
     float2 *Fr = reinterpret_cast<float2 *>(psi + n * n);          // [n][17] row transforms
     __shared__ double red[32];
+    __shared__ float2 tw[64];                                      // e^{-2 pi i r / n}
     const long long item = blockIdx.x;
     if (item >= count) return;
     const long long p = pidx ? (long long)pidx[item] : item;
@@ -50,6 +51,11 @@ __global__ void k_features(const float *band, long long Nl, long long tile, int 
         psi[c] = v;
         sum += v;
     }
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        float s, c;
+        sincospif(-2.0f * (float)r / (float)n, &s, &c);
+        tw[r] = make_float2(c, s);
+    }
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
     __syncthreads();
@@ -60,13 +66,15 @@ __global__ void k_features(const float *band, long long Nl, long long tile, int 
     for (int t = threadIdx.x; t < n * NMODE; t += blockDim.x) {
         const int b = t / NMODE, k1 = t % NMODE - KMODE;
         float sr = 0.f, si = 0.f;
+        const int step = (int)pmod_ll((long long)k1, n);
+        int r = 0;
         for (int a = 0; a < n; ++a) {
-            const int r = (int)pmod_ll((long long)k1 * a, n);
-            float s, c;
-            sincospif(-2.0f * (float)r / (float)n, &s, &c);
+            const float2 w = tw[r];
             const float v = psi[b * n + a] - mean;
-            sr = fmaf(v, c, sr);
-            si = fmaf(v, s, si);
+            sr = fmaf(v, w.x, sr);
+            si = fmaf(v, w.y, si);
+            r += step;
+            if (r >= n) r -= n;
         }
         Fr[t] = make_float2(sr, si);
     }
@@ -80,10 +88,12 @@ __global__ void k_features(const float *band, long long Nl, long long tile, int 
     for (int t = threadIdx.x; t < NMODE * NMODE; t += blockDim.x) {
         const int k2 = t / NMODE - KMODE, k1i = t % NMODE;
         float sr = 0.f, si = 0.f;
+        const int step = (int)pmod_ll((long long)k2, n);
+        int r = 0;
         for (int b = 0; b < n; ++b) {
-            const int r = (int)pmod_ll((long long)k2 * b, n);
-            float s, c;
-            sincospif(-2.0f * (float)r / (float)n, &s, &c);
+            const float c = tw[r].x, s = tw[r].y;
+            r += step;
+            if (r >= n) r -= n;
             const float2 f = Fr[b * NMODE + k1i];
             // (f.x + i f.y)(c + i s)
             sr += f.x * c - f.y * s;
@@ -114,7 +124,8 @@ __global__ void k_features(const float *band, long long Nl, long long tile, int 
 //   g(k) = 1 / D(k), D = B11 (2 - 2 cos t1) + B22 (2 - 2 cos t2) + 2 B12 sin t1 sin t2,
 //   g(0) = 0 (-L0^{-1} is multiplication of the DFT by g),
 //   c_j^0 = -L0^{-1} v_j,  c_j^m = -L0^{-1} (v1 D0x + v2 D0y) c_j^{m-1},
-//   T_m = sym <v_i c_j^{m-2}>  (m = 2..19, means over the cells in FP64).
+//   T_m = sym <v_i c_j^{m-2}>  (m = 2..19; means over the cells summed in FP32
+//   per thread and per warp, in FP64 across the warps).
 // Both fields go through one complex FFT as c1 + i c2: g is real and even in
 // k, so multiplying the transform of (f1 + i f2) by g transforms each part.
 // One CTA of 256 threads per patch, everything in shared memory: the complex
@@ -177,6 +188,25 @@ __device__ __forceinline__ void block_sum4(double (&v)[4], double (*red)[8])
         v[q] = t;
     }
     __syncthreads();
+}
+
+// block sum of 4 floats into 4 doubles held by thread 0 only: FP32 within a
+// thread and across the warp, FP64 for the 8 warp partials (the FP64 pipe of
+// this part is narrow, so the per-thread and per-warp sums stay in FP32)
+__device__ __forceinline__ void block_sum4_root(float (&v)[4], double (*red)[8], double (&out)[4])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 4; ++q) red[q][threadIdx.x >> 5] = (double)v[q];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 4; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += red[q][w];
+            out[q] = t;
+        }
 }
 
 // [K/K] at 1 of sum_k c_k x^k by Wynn's epsilon algorithm on the partial sums
@@ -271,11 +301,11 @@ __global__ void __launch_bounds__(256) k_series(const float *band, long long Nl,
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) { c1[e] = z[e].x * inv; c2[e] = z[e].y * inv; }
     __syncthreads();
     for (int m = 2; m <= SERIES_M; ++m) {
-        double sm[4] = {0.0, 0.0, 0.0, 0.0};
+        float sm[4] = {0.f, 0.f, 0.f, 0.f};
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
             const float a1 = v1[e], a2 = v2[e];
-            sm[0] += (double)(a1 * c1[e]); sm[1] += (double)(a1 * c2[e]);
-            sm[2] += (double)(a2 * c1[e]); sm[3] += (double)(a2 * c2[e]);
+            sm[0] = fmaf(a1, c1[e], sm[0]); sm[1] = fmaf(a1, c2[e], sm[1]);
+            sm[2] = fmaf(a2, c1[e], sm[2]); sm[3] = fmaf(a2, c2[e], sm[3]);
             if (m < SERIES_M) {
                 const int b = e / N, a = e % N;
                 const int ap = (a + 1) & (N - 1), am = (a + N - 1) & (N - 1);
@@ -287,12 +317,13 @@ __global__ void __launch_bounds__(256) k_series(const float *band, long long Nl,
                 z[e] = make_float2(fmaf(a1, d1x, a2 * d1y), fmaf(a1, d2x, a2 * d2y));
             }
         }
-        block_sum4(sm, red);
+        double tot[4];
+        block_sum4_root(sm, red, tot);
         if (threadIdx.x == 0) {
             const double nn = (double)(N * N);
-            Tm[m - 2][0] = sm[0] / nn;
-            Tm[m - 2][1] = 0.5 * (sm[1] + sm[2]) / nn;
-            Tm[m - 2][2] = sm[3] / nn;
+            Tm[m - 2][0] = tot[0] / nn;
+            Tm[m - 2][1] = 0.5 * (tot[1] + tot[2]) / nn;
+            Tm[m - 2][2] = tot[3] / nn;
         }
         if (m == SERIES_M) break;
         fft2_smem<N>(z, tw, false);

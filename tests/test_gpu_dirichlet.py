@@ -54,8 +54,9 @@ def test_macro_dirichlet_linear_profile_steady(mlsd, torch_mod):
     assert np.abs(Ug.cpu().numpy() - U0).max() < 1e-13
 
 
-@pytest.mark.parametrize("nf,steps", [(128, 200), (200, 60)])
-def test_dns_dirichlet_parity(mlsd, torch_mod, nf, steps):
+@pytest.mark.parametrize("nf,steps,prec,tol", [(128, 200, "fp32", 1e-5), (200, 60, "fp32", 1e-5),
+                                               (128, 300, "fp64", 1e-12)])
+def test_dns_dirichlet_parity(mlsd, torch_mod, nf, steps, prec, tol):
     dev = torch_mod.device("cuda:0")
     spec = flows.cellular_two_scale(1.0 / 3, 1.0 / 3, 5)
     kappa = 1.0
@@ -63,15 +64,18 @@ def test_dns_dirichlet_parity(mlsd, torch_mod, nf, steps):
     h = 2 * np.pi / nf
     dt = 0.2 * min(h * h / (4 * kappa), h / 2.0)
     U0 = flows.step_u0(nf)
-    u = torch_mod.tensor(U0, dtype=torch_mod.float32, device=dev)
+    dtype = torch_mod.float64 if prec == "fp64" else torch_mod.float32
+    u = torch_mod.tensor(U0, dtype=dtype, device=dev)
     ut = torch_mod.empty_like(u)
     pg = torch_mod.tensor(psi, dtype=torch_mod.float32, device=dev)
     mlsd.dns_run_dirichlet(u, ut, pg, kappa, dt, steps, 1.0, 0.0)
     torch_mod.cuda.synchronize()
-    ref = oracle.dns_run_dirichlet(psi, kappa, dt, steps, U0, 1.0, 0.0)
+    # the oracle on the FP32-rounded stream function the kernel reads
+    psi32 = pg.double().cpu().numpy()
+    ref = oracle.dns_run_dirichlet(psi32 if prec == "fp64" else psi, kappa, dt, steps, U0, 1.0, 0.0)
     got = u.cpu().numpy()
     assert np.all(got[:, 0] == 1.0)
-    assert rel_l2(got, ref) < 1e-5
+    assert rel_l2(got, ref) < tol
     assert np.abs(ref - U0).max() > 0.1
 
 
@@ -84,5 +88,10 @@ def test_dirichlet_argument_checks(mlsd, torch_mod):
                                          None, s) == -1
     assert lib.mlsd_macro_step_dirichlet(8, u.data_ptr(), 0, K.data_ptr(), 0.1, 1,
                                          float("nan"), 0.0, None, s) == -1
-    assert lib.mlsd_dns_run_dirichlet(8, u.data_ptr(), u.data_ptr(), u.data_ptr(), 1.0, 0.1, 1,
-                                      1.0, 0.0, s) == -1
+    # u and its scratch buffer alias
+    assert lib.mlsd_dns_run_dirichlet(8, u.data_ptr(), u.data_ptr(), u.data_ptr(), 0, 1.0, 0.1,
+                                      1, 1.0, 0.0, s) == -1
+    # a precision other than FP32 / FP64
+    t = torch_mod.zeros_like(u)
+    assert lib.mlsd_dns_run_dirichlet(8, u.data_ptr(), t.data_ptr(), u.data_ptr(), 2, 1.0, 1e-4,
+                                      1, 1.0, 0.0, s) == -1

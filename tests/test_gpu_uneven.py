@@ -120,3 +120,33 @@ def test_full_size_continuous_spectrum_sampled_patches():
                                cfl=cfg["cfl"], n_burn_fixed=0, n_avg_fixed=32)
             for p, Kr in zip(picks, ref):
                 assert rel_l2(K[p], Kr) < 1e-4, (level, n, p, K[p], Kr)
+
+
+@pytest.mark.slow
+def test_full_size_continuous_spectrum_chain_at_sampled_nodes():
+    # Algorithm 3 down all 8 octave levels of the full continuous spectrum
+    # (|k| <= 256, ~1e5 modes, 256 x 256 macro nodes, 32^2 .. 256^2 patches from
+    # the size rule, off-diagonal closed forms included), every node solved on
+    # the GPU with a fixed 32-step window; the composed K at sampled nodes
+    # against the oracle's chain at those nodes with the same per-level sizes
+    import torch
+    import paper_1510_00451_gb300 as mlsd
+    from inputs import flows as fl
+    cfg = fl.config_problem("continuous_spectrum")
+    N, L, kappa = cfg["n_macro"], len(cfg["edges"]) - 1, cfg["kappa"]
+    lv = mlsd.Levels(cfg["spectrum"], kappa, N, cfg["edges"], [0] * L, cfl=cfg["cfl"],
+                     n_burn_fixed=0, n_avg_fixed=32)
+    sizes = np.stack([lv.patch_sizes(l + 1) for l in range(L)], 1)      # [P][L]
+    K = torch.zeros(N * N, 3, dtype=torch.float64, device="cuda:0")
+    lv.effective_diffusivity(K)
+    assert lv.status() == 0
+    K = K.cpu().numpy()
+    assert np.isfinite(K).all()
+    rng = np.random.default_rng(20261204)
+    picks = rng.choice(N * N, size=2, replace=False)
+    for p in picks:
+        # one node per call: the oracle's threads then split that node's line variances
+        Kr = oracle.chain(cfg["spectrum"], cfg["edges"], [32] * L, N, kappa,
+                          [(int(p) % N, int(p) // N)], cfl=cfg["cfl"], n_burn_fixed=0,
+                          n_avg_fixed=32, node_n=sizes[[p]])[0]
+        assert rel_l2(K[p], Kr) < 1e-4, (int(p), sizes[p], K[p], Kr)
