@@ -120,7 +120,9 @@ typedef struct {
                                   copies (cluster > 1: a CTA barrier, and the two halo rows moved
                                   by cp.async.bulk completing on the receiver's mbarrier); 4 the
                                   row-paired f32x2 kernel (not a synchronisation mode: one
-                                  barrier per stage, two cells per FFMA2) */
+                                  barrier per stage, two cells per FFMA2); 5 bulk row copies
+                                  with the rows that need a neighbour's row computed last, so
+                                  that the copies land while the others are computed */
     int n_classes;             /* patch sizes in the level; n, Nl, h and the tile fields describe
                                   the class with the most work; all classes run concurrently */
 } mlsd_level_desc;
@@ -133,12 +135,13 @@ typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and 
  * Set-up also picks the thread-block tiling of the patch kernel per patch
  * size: every compiled candidate is timed on a sample of the level's patches
  * (a short fixed window) and the fastest is kept for the process; the
- * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][c<cluster>][p][s|n|b]
+ * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][c<cluster>][p][s|n|b|d|r]
  * forces one where it exists for the level's patch size (p: the packed kernel
  * that advances both fields of a patch in f32x2 pairs; c: CTAs per patch field;
  * s: split-phase stage barriers; n: neighbour signalling between the slabs of
  * a cluster instead of a cluster-wide barrier; b: the slab edge rows moved by
- * bulk copies that complete on the receiver's mbarrier; r: rows r and r + by/2
+ * bulk copies that complete on the receiver's mbarrier; d: as b, with the rows
+ * that need a neighbouring slab's row computed after the others; r: rows r and r + by/2
  * of a thread's block in f32x2 pairs, one FFMA2/FADD2 per two cells).  MLSD_TUNE_LOG set to
  * anything prints every candidate's trial time to stderr.
  * Patch sizes 32 and 64 run one CTA per field (or per patch, packed); 128 and

@@ -17,6 +17,8 @@ int patch_variants_cluster(int n, std::vector<PatchVariant> &out)
         add_variant<128, 4, 4, float, 1, 4>(out);
         add_variant<128, 2, 8, float, 2, 4, 3>(out);      // 2x8 cells: 16 warps per SM
         add_variant<128, 2, 8, float, 2, 4>(out);
+        add_variant<128, 4, 8, float, 3, 4, 5>(out);      // bulk copies, cross-slab rows last
+        add_variant<128, 4, 8, float, 2, 4, 5>(out);
     } else if (n == 256) {
         add_variant<256, 4, 8, float, 1, 8>(out);
         add_variant<256, 4, 8, float, 1, 8, 1>(out);
@@ -31,6 +33,10 @@ int patch_variants_cluster(int n, std::vector<PatchVariant> &out)
         add_variant<256, 4, 8, float, 3, 16>(out);
         add_variant<256, 2, 8, float, 1, 8, 3>(out);      // 2x8 cells: 16 warps per SM
         add_variant<256, 2, 8, float, 1, 8>(out);
+        add_variant<256, 4, 8, float, 1, 8, 5>(out);      // bulk copies, cross-slab rows last
+        add_variant<256, 4, 8, float, 3, 16, 5>(out);
+        add_variant<256, 4, 8, float, 2, 16, 5>(out);
+        add_variant<256, 2, 8, float, 1, 8, 5>(out);
     }
     return (int)out.size();
 }

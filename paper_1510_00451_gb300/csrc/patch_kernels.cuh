@@ -326,6 +326,11 @@ struct Tile {
                                                  uint32_t parity = 0, int *status = nullptr,
                                                  bool *live = nullptr)
     {
+        if constexpr (SYNC == 5 && C > 1) {
+            stage_defer<J, SECOND>(sm, buf, rank, tx, ty, x, out, aE, aN, k, mbar, parity, status,
+                                   live);
+            return;
+        }
         publish_edges<SYNC != 3>(sm, buf, rank, tx, ty, x);
         if constexpr (SYNC == 3 && C > 1) {
             // the slab's last row goes to rank + 1's HS slot and its first row to
@@ -408,6 +413,138 @@ struct Tile {
             }
 #pragma unroll
             for (int c = 0; c < BX; ++c) { dm[c] = d0[c]; d0[c] = dp[c]; }
+        }
+    }
+
+    // E-W difference of row r of x (r = 0 .. BY-1) with the block's column halos
+    __device__ __forceinline__ static void row_diff(real (&d)[BX], const real (&x)[BY][BX], int r,
+                                                    const real (&hW)[BY + 2], const real (&hE)[BY + 2])
+    {
+#pragma unroll
+        for (int c = 0; c < BX; ++c) {
+            const real e = (c + 1 < BX) ? x[r][c + 1] : hE[r + 1];
+            const real w = (c > 0) ? x[r][c - 1] : hW[r + 1];
+            d[c] = e - w;
+        }
+    }
+
+    // E-W difference of a halo row h (the row below, corner = 0, or above, corner = BY + 1)
+    __device__ __forceinline__ static void halo_diff(real (&d)[BX], const real (&h)[BX], int corner,
+                                                     const real (&hW)[BY + 2], const real (&hE)[BY + 2])
+    {
+#pragma unroll
+        for (int c = 0; c < BX; ++c) {
+            const real e = (c + 1 < BX) ? h[c + 1] : hE[corner];
+            const real w = (c > 0) ? h[c - 1] : hW[corner];
+            d[c] = e - w;
+        }
+    }
+
+    // Stage with bulk row copies and the cross-slab rows deferred (SYNC = 5).  As
+    // SYNC = 3, thread 0 sends the slab's first and last rows to the neighbouring
+    // ranks by bulk copies right after the CTA barrier; but every thread first
+    // computes the rows of its block that need no row halo (rows 1 .. BY-2: the
+    // column halos come from this CTA), and only then do the slab-edge threads
+    // wait for the incoming rows.  The copies' latency is spent on (BY-2)/BY of
+    // the stage's arithmetic.  Rows BY-1 and 0 follow, the latter with its E-W
+    // differences of rows 0 and 1 formed again (BX subtractions each).  The
+    // arithmetic per cell is that of stage().
+    template <int J, bool SECOND>
+    __device__ __forceinline__ static void stage_defer(real *sm, int buf, int rank, int tx, int ty,
+                                                       const real (&x)[BY][BX], real (&out)[BY][BX],
+                                                       const real (&aE)[BY][BX], const real (&aN)[BY][BX],
+                                                       const Coef<real> &k, uint32_t mbar, uint32_t parity,
+                                                       int *status, bool *live)
+    {
+        static_assert(BY >= 2, "deferred rows need two rows per block");
+        publish_edges<false>(sm, buf, rank, tx, ty, x);
+        const bool edge = ty == 0 || ty == NBY - 1;
+        if (edge) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        real *rowT = sm + buf * S::STAGE, *rowB = rowT + S::ROW;
+        real *colL = rowB + S::ROW, *colR = colL + S::COL;
+        real *HS = colR + S::COL, *HN = HS + N;
+        if (tx == 0 && ty == 0 && *live) {
+            const uint32_t bytes = (uint32_t)(N * sizeof(real));
+            bulk_to_rank((uint32_t)__cvta_generic_to_shared(HS),
+                         (uint32_t)__cvta_generic_to_shared(rowB + (NBY - 1) * N), bytes, mbar,
+                         (rank + 1) % C);
+            bulk_to_rank((uint32_t)__cvta_generic_to_shared(HN),
+                         (uint32_t)__cvta_generic_to_shared(rowT), bytes, mbar, (rank + C - 1) % C);
+        }
+        const int a0 = tx * BX, b0 = ty * BY;
+        const int txW = (tx + NBX - 1) % NBX, txE = (tx + 1) % NBX;
+        const real *cw = colR + txW * S::CS, *ce = colL + txE * S::CS;
+        // column halos of rows 0 .. BY-1 (this CTA's buffers)
+        real hW[BY + 2], hE[BY + 2];
+        {
+            real tmpw[BY], tmpe[BY];
+            ld_vec<real, BY>(tmpw, cw + b0);
+            ld_vec<real, BY>(tmpe, ce + b0);
+#pragma unroll
+            for (int r = 0; r < BY; ++r) { hW[r + 1] = tmpw[r]; hE[r + 1] = tmpe[r]; }
+        }
+        // rows 1 .. BY-2
+        real dm[BX], d0[BX], dp[BX];
+        row_diff(dm, x, 0, hW, hE);
+        row_diff(d0, x, 1, hW, hE);
+#pragma unroll
+        for (int r = 1; r < BY - 1; ++r) {
+            row_diff(dp, x, r + 1, hW, hE);
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                const real xW = (c > 0) ? x[r][c - 1] : hW[r + 1];
+                cell<J, SECOND>(out[r][c], x[r][c], xW, x[r + 1][c], x[r - 1][c], d0[c], dm[c], dp[c],
+                                aE[r][c], aN[r][c], k);
+            }
+#pragma unroll
+            for (int c = 0; c < BX; ++c) { dm[c] = d0[c]; d0[c] = dp[c]; }
+        }
+        // now dm, d0 hold the differences of rows BY-2, BY-1; the row halos
+        if (edge && *live) {
+            if (!nbr_wait(mbar, parity, status)) {
+                *live = false;
+                atomicCAS(status, 0, MLSD_ETIMEOUT);
+            } else if (tx == 0 && ty == 0) {
+                arm_tx(mbar, (uint32_t)(2 * N * sizeof(real)));
+            }
+        }
+        const int aw = (a0 + N - 1) % N, ae = (a0 + BX) % N;
+        real hN[BX];
+        if (ty == NBY - 1) {
+            ld_vec<real, BX>(hN, HN + a0);
+            hW[BY + 1] = HN[aw]; hE[BY + 1] = HN[ae];
+        } else {
+            ld_vec<real, BX>(hN, rowT + (ty + 1) * N + a0);
+            const int bn = b0 + BY;
+            hW[BY + 1] = cw[bn]; hE[BY + 1] = ce[bn];
+        }
+        // row BY-1
+        halo_diff(dp, hN, BY + 1, hW, hE);
+#pragma unroll
+        for (int c = 0; c < BX; ++c) {
+            const real xW = (c > 0) ? x[BY - 1][c - 1] : hW[BY];
+            cell<J, SECOND>(out[BY - 1][c], x[BY - 1][c], xW, hN[c], x[BY - 2][c], d0[c], dm[c],
+                            dp[c], aE[BY - 1][c], aN[BY - 1][c], k);
+        }
+        real hS[BX];
+        if (ty == 0) {
+            ld_vec<real, BX>(hS, HS + a0);
+            hW[0] = HS[aw]; hE[0] = HS[ae];
+        } else {
+            ld_vec<real, BX>(hS, rowB + (ty - 1) * N + a0);
+            const int bs = b0 - 1;
+            hW[0] = cw[bs]; hE[0] = ce[bs];
+        }
+        // row 0
+        halo_diff(dm, hS, 0, hW, hE);
+        row_diff(d0, x, 0, hW, hE);
+        row_diff(dp, x, 1, hW, hE);
+#pragma unroll
+        for (int c = 0; c < BX; ++c) {
+            const real xW = (c > 0) ? x[0][c - 1] : hW[1];
+            cell<J, SECOND>(out[0][c], x[0][c], xW, x[1][c], hS[c], d0[c], dm[c], dp[c], aE[0][c],
+                            aN[0][c], k);
         }
     }
 
@@ -669,9 +806,9 @@ struct Tile {
                 asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
             }
         }
-        // SYNC = 3: one arrival (thread 0's arm) and two incoming rows per phase;
+        // SYNC = 3, 5: one arrival (thread 0's arm) and two incoming rows per phase;
         // the first phase of both barriers is armed here
-        if constexpr (SYNC == 3) {
+        if constexpr (SYNC == 3 || SYNC == 5) {
             if (tid == 0) {
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar0) : "memory");
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar0 + 8) : "memory");
@@ -887,12 +1024,14 @@ k_patch_solve(PatchParams prm)
 }
 
 // SYNC: 0 = barrier per stage, 1 = split-phase cluster barrier, 2 = neighbour
-// signalling, 3 = bulk copies of the slab edge rows (2 and 3: clusters only),
-// 4 = row-paired f32x2 arithmetic (one CTA per field, FP32)
+// signalling, 3 = bulk copies of the slab edge rows, 5 = bulk copies with the
+// cross-slab rows computed last (2, 3, 5: clusters only), 4 = row-paired
+// f32x2 arithmetic (one CTA per field, FP32)
 template <int N, int BX, int BY, typename real, int MINB = 1, int C = 1, int SYNC = 0>
 void add_variant(std::vector<PatchVariant> &out)
 {
     static_assert(SYNC < 2 || SYNC == 4 || C > 1, "neighbour signalling / bulk row copies need a cluster");
+    static_assert(SYNC != 5 || BY >= 2, "deferred rows: two rows per block");
     static_assert(SYNC != 4 || (C == 1 && sizeof(real) == 4), "row pairs: FP32, one CTA per field");
     static_assert(((N / BX) * (N / C / BY)) % 32 == 0, "whole warps only");
     static_assert((N / BX) * (N / C / BY) <= 512, "reduction slots 0..31 (warp pairs), 32, 40, 41");

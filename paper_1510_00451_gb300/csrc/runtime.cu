@@ -442,9 +442,10 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
     if (vs.empty()) return MLSD_EUNSUPPORTED;
     c.variant = vs[0];
     if (const char *env = std::getenv("MLSD_TILE")) {
-        // <bx>x<by>[m<minb>][c<cluster>][p][s|n|b|r]: p selects the packed two-field kernel,
+        // <bx>x<by>[m<minb>][c<cluster>][p][s|n|b|d|r]: p selects the packed two-field kernel,
         // s the split-phase stage barriers, n neighbour signalling between slabs, b bulk
-        // copies of the slab edge rows, r the row-paired f32x2 kernel
+        // copies of the slab edge rows, d bulk copies with the cross-slab rows computed
+        // last, r the row-paired f32x2 kernel
         int bx = 0, by = 0, mb = 1, pk = 0, cl = 1, sp = 0;
         char rest[16] = "";
         if (std::sscanf(env, "%dx%d%15s", &bx, &by, rest) >= 2) {
@@ -456,6 +457,7 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
                 if (*c == 'n') sp = 2;
                 if (*c == 'b') sp = 3;
                 if (*c == 'r') sp = 4;
+                if (*c == 'd') sp = 5;
             }
             for (auto &v : vs)
                 if (v.bx == bx && v.by == by && v.minb == mb && v.packed == pk && v.cluster == cl &&
