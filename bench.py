@@ -48,9 +48,12 @@ FLOP_PER_WINDOW_UPDATE = 5
 # `--case profile`: the same grids, bands and tiling as the timed step (the window
 # length does not change it); 5.15 MB, 1.46 MB and 0.73 MB read, nothing written.
 PATCH_DRAM_BYTES_PER_LAUNCH = (5153792 + 1461504 + 733696) / 3
-# DRAM bytes per k_dns_step launch on the 8192^2 grid, ncu on `--case dns-full`
-# (32-row tiles, two launches): 537.2 MB read + 236.1 MB written (algorithmic: 805.3 MB)
-DNS_DRAM_BYTES_PER_LAUNCH = (537227776 + 237750016 + 537195776 + 234513664) / 2
+# DRAM bytes per DNS launch on the 8192^2 grid, ncu on `--case dns-full` (two launches),
+# by kernel; a kernel without a capture reports no traffic
+DNS_DRAM_BYTES_PER_LAUNCH = {
+    # 32-row tiles: 537.2 MB read + 236.1 MB written (algorithmic: 805.3 MB)
+    "k_dns_step<32>": (537227776 + 237750016 + 537195776 + 234513664) / 2,
+}
 WORKLOAD = "three_level_cellular"
 
 
@@ -850,7 +853,7 @@ def dns_case(nf, steps, warmup=20, report=False):
     U = torch.empty(N, N, dtype=torch.float32, device=dev)
     mass = mlsd.coarse_grain(u, N, U)
     m0 = mlsd.coarse_grain(u0, N, U.clone())
-    out = {"grid": nf, "steps": steps, "dt": dt, "ms": ms,
+    out = {"grid": nf, "steps": steps, "dt": dt, "ms": ms, "kernel": mlsd.dns_kernel(),
            "cell_steps_per_s": nf * nf * steps / (ms * 1e-3),
            "mass_rel_drift": abs(mass - m0) / m0,
            "finite": bool(torch.isfinite(u).all().item())}
@@ -1060,9 +1063,9 @@ def main():
                "value": d["cell_steps_per_s"] * world, "unit": "cell-steps/s", "ms": d["ms"],
                "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "peak_source": hbm_src,
                             "unit": "GB/s",
-                            "frac": gbs / hbm, "traffic": DNS_DRAM_BYTES_PER_LAUNCH,
+                            "frac": gbs / hbm, "traffic": DNS_DRAM_BYTES_PER_LAUNCH.get(d["kernel"]),
                             "traffic_unit": "DRAM bytes per launch (ncu, 8192^2)",
-                            "kernel": "k_dns_step",
+                            "kernel": d["kernel"],
                             "algorithmic_bytes_per_cell_step": DNS_BYTES_PER_CELL_STEP},
                "mass_rel_drift": d["mass_rel_drift"], "finite": d["finite"]}
 

@@ -384,7 +384,8 @@ int mlsd_status(mlsd_levels *h, void *cuda_stream);
  * that waits on an mbarrier which never receives an arrival, with nothing
  * else in flight:
  *   which = 0: the wait of the cluster-split patch kernels' slab exchanges;
- *   which = 1: the wait of the tensor-core inference kernels.
+ *   which = 1: the wait of the tensor-core inference kernels;
+ *   which = 2: the tile wait of the persistent DNS kernels.
  * Each wait gives up after about a second of SM clocks and latches
  * MLSD_ETIMEOUT in the handle's status word, exactly as on a real failure;
  * mlsd_status then reports it (and clears it), and the context stays usable.
@@ -432,9 +433,24 @@ int mlsd_grid_psi(int n_modes, const int32_t *k1, const int32_t *k2, const doubl
  * reference: second-order central differences, second-order Runge-Kutta):
  * u_t = v.grad_h u + kappa Lap_h u with v from psi by central differences,
  * Heun's RK2, nsteps steps.  u_dev [nf][nf] float in place; u_tmp_dev is a
- * caller-provided work field of the same size.  nf a multiple of 128.        */
+ * caller-provided work field of the same size.  nf a multiple of 128.
+ * One fused launch per step; the kernel (per-tile CTAs staged by cp.async, or
+ * persistent CTAs fed by tensor copies) is picked once per process by timing
+ * each on the caller's grid (MLSD_DNS_TY = 64 | 32 | t32 | t32x2 | t64 pins
+ * one).  The persistent kernels take tiles from a per-device queue: one DNS
+ * run at a time per device.  Asynchronous: a tile copy that never lands (a
+ * wait of about a second runs out) is reported by mlsd_dns_status.           */
 int mlsd_dns_run(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev, double kappa,
                  double dt, int nsteps, void *cuda_stream);
+
+/* Synchronise the stream and return MLSD_ETIMEOUT if a tile wait of a DNS
+ * kernel ran out since the last call (u is then undefined), else MLSD_OK;
+ * clears the flag.  MLSD_ECUDA if the stream reports an error.               */
+int mlsd_dns_status(void *cuda_stream);
+
+/* Name of the DNS kernel this process picked for mlsd_dns_run ("" before the
+ * first run), e.g. "k_dns_tma<32,1>": static storage, not to be freed.      */
+const char *mlsd_dns_kernel(void);
 
 /* The direct simulation with the Sec. 4 boundary conditions (Dirichlet in x1,
  * periodic in x2), posed on [0, 2 pi] x [0, 2 pi) as mlsd_macro_step_dirichlet:

@@ -28,6 +28,7 @@ EXPORTED = ["mlsd_build_levels", "mlsd_free_levels", "mlsd_level_info", "mlsd_so
             "mlsd_level_work", "mlsd_corrector_energy", "mlsd_launch_count", "mlsd_profile", "mlsd_profile_collect",
             "mlsd_coarse_grain_noalloc", "mlsd_dns_dt", "mlsd_patch_sizes",
             "mlsd_macro_step_dirichlet", "mlsd_dns_run_dirichlet", "mlsd_check_wait_timeout",
+            "mlsd_dns_status", "mlsd_dns_kernel",
             "mlsd_surrogate_param_count", "mlsd_surrogate_create", "mlsd_surrogate_free",
             "mlsd_surrogate_set_params", "mlsd_surrogate_get_params", "mlsd_surrogate_features",
             "mlsd_surrogate_grad", "mlsd_surrogate_train_step", "mlsd_surrogate_predict",
@@ -95,6 +96,9 @@ _lib.mlsd_dns_dt.argtypes = [_I, _P, _D, _D, ctypes.POINTER(_D), _P]
 _lib.mlsd_macro_step_dirichlet.argtypes = [_I, _P, _I, _P, _D, _I, _D, _D, _P, _P]
 _lib.mlsd_dns_run_dirichlet.argtypes = [_I, _P, _P, _P, _I, _D, _D, _I, _D, _D, _P]
 _lib.mlsd_check_wait_timeout.argtypes = [_P, _I, _P]
+_lib.mlsd_dns_status.argtypes = [_P]
+_lib.mlsd_dns_kernel.argtypes = []
+_lib.mlsd_dns_kernel.restype = ctypes.c_char_p
 _lib.mlsd_coarse_grain_noalloc.argtypes = [_I, _P, _I, _P, _P, _P]
 _lib.mlsd_surrogate_param_count.argtypes = [_I]
 _lib.mlsd_surrogate_param_count.restype = _L
@@ -320,6 +324,16 @@ def grid_psi(spectrum, nf, psi_out, stream=None):
 def dns_run(u, u_tmp, psi, kappa, dt, nsteps, stream=None):
     _check(_lib.mlsd_dns_run(u.shape[0], _dptr(u), _dptr(u_tmp), _dptr(psi), float(kappa),
                              float(dt), int(nsteps), _stream(stream)), "mlsd_dns_run")
+
+
+def dns_status(stream=None):
+    """MLSD_OK, or MLSD_ETIMEOUT if a DNS tile wait ran out since the last call (clears it)."""
+    return _lib.mlsd_dns_status(_stream(stream))
+
+
+def dns_kernel():
+    """Name of the DNS kernel this process picked ("" before the first run)."""
+    return _lib.mlsd_dns_kernel().decode()
 
 
 def dns_run_dirichlet(u, u_tmp, psi, kappa, dt, nsteps, u_left=1.0, u_right=0.0, stream=None):

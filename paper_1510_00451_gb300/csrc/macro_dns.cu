@@ -15,7 +15,12 @@
 #include <algorithm>
 #include <cstdlib>
 #include <mutex>
+#include <string>
+#include <vector>
 
+#include <cuda.h>
+
+#include "async_copy.cuh"
 #include "mlsd_internal.cuh"
 
 namespace mlsd {
@@ -219,30 +224,15 @@ __device__ __forceinline__ void cp16(void *dst, const void *src)
                  "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
 }
 
+// Both Heun stages of one tile from its staged u and psi (rows y0-2 .. y0+DTY+1,
+// columns x0-8 .. x0+DTX+7 in su, sp): stage 1 in registers, the edge columns
+// of the stage-1 field through eL / eR and one CTA barrier, stage 2 stored to un.
 template <int DTY>
-__global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const float *__restrict__ u,
-                                                               const float *__restrict__ psi,
-                                                               float *__restrict__ un, float ax,
-                                                               float kd, float dt)
+__device__ __forceinline__ void dns_tile(const float *su, const float *sp, float *eL, float *eR,
+                                         int nf, int x0, int y0, float *__restrict__ un, float ax,
+                                         float kd, float dt)
 {
-    constexpr int DLY = DnsTile<DTY>::DLY, DTH = DnsTile<DTY>::DTH;
-    extern __shared__ __align__(16) float dsm[];
-    float *su = dsm;                          // [DLY][DLX]
-    float *sp = su + DLY * DLX;               // [DLY][DLX]
-    float *eL = sp + DLY * DLX;               // [DTY][DG]  stage-1 value of a group's column 0
-    float *eR = eL + DTY * DG;                // [DTY][DG]  ... of its column 3
-    const int x0 = blockIdx.x * DTX, y0 = blockIdx.y * DTY;
-    for (int k = threadIdx.x; k < DLY * (DLX / 4); k += DTH) {
-        const int r = k / (DLX / 4), q = k % (DLX / 4);
-        int gy = y0 - 2 + r; gy = gy < 0 ? gy + nf : (gy >= nf ? gy - nf : gy);
-        int gx = x0 - 8 + 4 * q; gx = gx < 0 ? gx + nf : (gx >= nf ? gx - nf : gx);
-        const long long off = (long long)gy * nf + gx;
-        cp16(su + r * DLX + 4 * q, u + off);
-        cp16(sp + r * DLX + 4 * q, psi + off);
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
-
+    constexpr int DTH = DnsTile<DTY>::DTH;
     const int g = threadIdx.x % DG, seg = threadIdx.x / DG;
     const int c0 = 4 + 4 * g;                 // staged column of the group's first column
     // the last warp is partial (DTH = 34 DTY/8 threads): shuffles name its lanes only;
@@ -299,9 +289,8 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
         eR[(DRS * seg + k) * DG + g] = s1[k + 1][3];
     }
     __syncthreads();
-    if (g == 0 || g == DG - 1) return;        // halo groups: stage-1 values only
-    // ---- stage 2 on the output rows ----
-    {
+    // ---- stage 2 on the output rows (the halo groups hold stage-1 values only) ----
+    if (g != 0 && g != DG - 1) {
         float pm[4], pc[4], pp[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -335,6 +324,145 @@ __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const fl
 #pragma unroll
             for (int c = 0; c < 4; ++c) { pm[c] = pc[c]; pc[c] = pp[c]; }
         }
+    }
+}
+
+template <int DTY>
+__global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const float *__restrict__ u,
+                                                               const float *__restrict__ psi,
+                                                               float *__restrict__ un, float ax,
+                                                               float kd, float dt)
+{
+    constexpr int DLY = DnsTile<DTY>::DLY, DTH = DnsTile<DTY>::DTH;
+    extern __shared__ __align__(16) float dsm[];
+    float *su = dsm;                          // [DLY][DLX]
+    float *sp = su + DLY * DLX;               // [DLY][DLX]
+    float *eL = sp + DLY * DLX;               // [DTY][DG]  stage-1 value of a group's column 0
+    float *eR = eL + DTY * DG;                // [DTY][DG]  ... of its column 3
+    const int x0 = blockIdx.x * DTX, y0 = blockIdx.y * DTY;
+    for (int k = threadIdx.x; k < DLY * (DLX / 4); k += DTH) {
+        const int r = k / (DLX / 4), q = k % (DLX / 4);
+        int gy = y0 - 2 + r; gy = gy < 0 ? gy + nf : (gy >= nf ? gy - nf : gy);
+        int gx = x0 - 8 + 4 * q; gx = gx < 0 ? gx + nf : (gx >= nf ? gx - nf : gx);
+        const long long off = (long long)gy * nf + gx;
+        cp16(su + r * DLX + 4 * q, u + off);
+        cp16(sp + r * DLX + 4 * q, psi + off);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    dns_tile<DTY>(su, sp, eL, eR, nf, x0, y0, un, ax, kd, dt);
+}
+
+// Persistent variant: each CTA takes tiles from a queue (an atomic counter per
+// launch; two counters alternate, and each launch zeroes the next one's) into
+// NBUF staging buffers.  Thread 0 loads a tile's u and psi boxes by two 2-D
+// tensor copies (one box of DLX x DLY each, starting at (x0 - 8, y0 - 2)) that
+// complete on the buffer's mbarrier; the buffer's next tile is claimed and its
+// copy issued as soon as the buffer is free, so with NBUF = 2 it lands while
+// this CTA computes the other buffer's tile.
+// Boxes reaching past the grid's edge are zero-filled by the copy; the threads
+// then put in the periodic images from global memory.  A wait that runs out
+// (about a second) latches MLSD_ETIMEOUT into g_dns_status and ends the CTA's
+// walk after a second bounded wait for each copy it has issued.
+__device__ int g_dns_status;
+
+template <int DTY, int NBUF>
+struct DnsTma {
+    static constexpr int DLY = DnsTile<DTY>::DLY;
+    static constexpr int FIELD = DLY * DLX;                        // floats per staged field
+    static constexpr int BUF = (2 * FIELD * 4 + 1023) / 1024 * 256; // floats per buffer (1 KB steps)
+    static constexpr size_t SMEM = 1024 + (size_t)NBUF * BUF * 4 + (size_t)2 * DTY * DG * 4;
+    static constexpr uint32_t BYTES = 2u * FIELD * 4u;              // one tile's copies
+};
+
+template <int DTY, int NBUF>
+__global__ void __launch_bounds__(DnsTile<DTY>::DTH)
+k_dns_tma(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mp, int nf,
+          const float *__restrict__ u, const float *__restrict__ psi, float *__restrict__ un,
+          float ax, float kd, float dt, int *queue, int which)
+{
+    using T = DnsTma<DTY, NBUF>;
+    constexpr int DLY = T::DLY, DTH = DnsTile<DTY>::DTH;
+    extern __shared__ __align__(16) unsigned char dsm_raw[];
+    __shared__ __align__(8) uint64_t full[NBUF];
+    __shared__ int tile_of[NBUF];
+    // the copies land at 1 KB-aligned buffers
+    float *base = reinterpret_cast<float *>(dsm_raw + ((1024 - (smem_addr(dsm_raw) & 1023)) & 1023));
+    float *eL = base + NBUF * T::BUF, *eR = eL + DTY * DG;
+    const int tiles_x = nf / DTX, ntiles = tiles_x * (nf / DTY);
+    const CUtensorMap *pmu = &mu, *pmp = &mp;
+    // claim the next tile of the launch for buffer b and start its copies; past the
+    // last tile, a plain arrival completes the phase so that the CTA's wait ends
+    auto claim = [&](int b) {
+        const int t = atomicAdd(&queue[which], 1);
+        tile_of[b] = t;
+        const uint32_t mb = smem_addr(&full[b]);
+        if (t < ntiles) {
+            const int x0 = (t % tiles_x) * DTX, y0 = (t / tiles_x) * DTY;
+            float *su = base + b * T::BUF;
+            mbar_expect(mb, T::BYTES);
+            tma_load_2d(smem_addr(su), pmu, x0 - 8, y0 - 2, mb);
+            tma_load_2d(smem_addr(su + T::FIELD), pmp, x0 - 8, y0 - 2, mb);
+        } else {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mb) : "memory");
+        }
+    };
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NBUF; ++b) mbar_init1(smem_addr(&full[b]));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (blockIdx.x == 0) queue[which ^ 1] = 0;      // the next launch's queue
+        for (int b = 0; b < NBUF; ++b) claim(b);
+    }
+    __syncthreads();                                     // the mbarriers are initialised
+    for (int k = 0;; ++k) {
+        const int b = k % NBUF;
+        const uint32_t mb = smem_addr(&full[b]), par = (uint32_t)((k / NBUF) & 1);
+        const bool ok = mbar_wait_bounded(mb, par);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicCAS(&g_dns_status, 0, MLSD_ETIMEOUT);
+                // the copies of this and the other buffers, if still coming
+                for (int j = 0; j < NBUF; ++j)
+                    if (tile_of[(k + j) % NBUF] < ntiles)
+                        mbar_wait_bounded(smem_addr(&full[(k + j) % NBUF]),
+                                          (uint32_t)(((k + j) / NBUF) & 1));
+            }
+            break;
+        }
+        const int t = tile_of[b];
+        if (t >= ntiles) break;                         // claims only grow: no copy is pending
+        const int x0 = (t % tiles_x) * DTX, y0 = (t / tiles_x) * DTY;
+        float *su = base + b * T::BUF, *sp = su + T::FIELD;
+        if (x0 == 0 || x0 + DTX == nf || y0 == 0 || y0 + DTY == nf) {
+            // periodic images of the staged cells outside the grid
+            for (int e = threadIdx.x; e < DLY * DLX; e += DTH) {
+                const int r = e / DLX, c = e % DLX;
+                int gy = y0 - 2 + r, gx = x0 - 8 + c;
+                if (gy >= 0 && gy < nf && gx >= 0 && gx < nf) continue;
+                gy = gy < 0 ? gy + nf : (gy >= nf ? gy - nf : gy);
+                gx = gx < 0 ? gx + nf : (gx >= nf ? gx - nf : gx);
+                su[e] = u[(long long)gy * nf + gx];
+                sp[e] = psi[(long long)gy * nf + gx];
+            }
+            __syncthreads();
+        }
+        dns_tile<DTY>(su, sp, eL, eR, nf, x0, y0, un, ax, kd, dt);
+        // every thread's reads and writes of this buffer come before the next copy into it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) claim(b);
+    }
+}
+
+// Failure-path check of the tile wait: one thread waits on a fresh mbarrier that
+// receives no arrival and no copy, so the wait runs out and latches MLSD_ETIMEOUT
+__global__ void k_wait_check_tile(int *status)
+{
+    __shared__ __align__(8) uint64_t mb;
+    if (threadIdx.x == 0) {
+        mbar_init1(smem_addr(&mb));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait_bounded(smem_addr(&mb), 0)) atomicCAS(status, 0, MLSD_ETIMEOUT);
     }
 }
 
@@ -509,9 +637,84 @@ static cudaError_t dns_launch(int nf, const float *a, const float *psi, float *b
     return cudaGetLastError();
 }
 
-// tile height: 64 rows (2 CTAs/SM) or 32 rows (4 CTAs/SM, loads of one CTA overlap
-// another's compute); picked once per process by timing both on the caller's grid
-static int g_dns_ty = 0;
+// the two tile counters of the persistent kernels, per device (zeroed once), and
+// which one the next launch takes (every persistent launch, of any tile shape,
+// alternates them: each launch zeroes the other for its successor on the stream)
+static int g_dns_which = 0;
+// the two tile counters of the persistent kernels, per device (zeroed once)
+static cudaError_t dns_queue(int dev, cudaStream_t s, int **out)
+{
+    static std::mutex mu;
+    static std::vector<int *> q;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)q.size() <= dev) q.resize(dev + 1, nullptr);
+    if (!q[dev]) {
+        cudaError_t e = cudaMalloc((void **)&q[dev], 2 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(q[dev], 0, 2 * sizeof(int), s);
+        if (e != cudaSuccess) { q[dev] = nullptr; return e; }
+    }
+    *out = q[dev];
+    return cudaSuccess;
+}
+
+template <int DTY, int NBUF>
+static cudaError_t dns_launch_tma(int nf, const CUtensorMap &ma, const CUtensorMap &mp,
+                                  const float *a, const float *psi, float *b, float ax, float kd,
+                                  float dt, cudaStream_t s)
+{
+    using T = DnsTma<DTY, NBUF>;
+    constexpr int DTH = DnsTile<DTY>::DTH;
+    const void *fn = reinterpret_cast<const void *>(&k_dns_tma<DTY, NBUF>);
+    static std::mutex mu;
+    static std::vector<int> per_sm;                 // resident CTAs per SM, by device
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    int res = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if ((int)per_sm.size() <= dev) per_sm.resize(dev + 1, 0);
+        if (per_sm[dev] == 0) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[dev], fn, DTH, T::SMEM);
+            if (e != cudaSuccess) return e;
+            if (per_sm[dev] < 1) return cudaErrorInvalidConfiguration;
+        }
+        res = per_sm[dev];
+    }
+    const long long ntiles = (long long)(nf / DTX) * (nf / DTY);
+    const int grid = (int)std::min<long long>(ntiles, (long long)res * sms);
+    int *queue = nullptr;
+    e = dns_queue(dev, s, &queue);
+    if (e != cudaSuccess) return e;
+    const int which = g_dns_which;                   // launches alternate the two counters
+    g_dns_which ^= 1;
+    k_dns_tma<DTY, NBUF><<<grid, DTH, T::SMEM, s>>>(ma, mp, nf, a, psi, b, ax, kd, dt, queue, which);
+    return cudaGetLastError();
+}
+
+// DNS kernel variants: per-tile CTAs staged by cp.async (tile height 64 rows, 2 CTAs/SM,
+// or 32 rows, 4 CTAs/SM), or persistent CTAs fed by tensor copies (32 rows with one or
+// two staging buffers, 64 rows with one).  Picked once per process by timing each on
+// the caller's grid; MLSD_DNS_TY = 64 | 32 | t32 | t32x2 | t64 pins one.
+enum DnsKind { kCp64, kCp32, kTma32, kTma32x2, kTma64, kDnsKinds };
+static int g_dns_kind = -1;
+
+static cudaError_t dns_launch_kind(int kind, int nf, const CUtensorMap *maps, int ia,
+                                   const float *a, const float *psi, float *b, float ax, float kd,
+                                   float dt, cudaStream_t s)
+{
+    switch (kind) {
+    case kCp64: return dns_launch<64>(nf, a, psi, b, ax, kd, dt, s);
+    case kCp32: return dns_launch<32>(nf, a, psi, b, ax, kd, dt, s);
+    case kTma32: return dns_launch_tma<32, 1>(nf, maps[ia], maps[2], a, psi, b, ax, kd, dt, s);
+    case kTma32x2: return dns_launch_tma<32, 2>(nf, maps[ia], maps[2], a, psi, b, ax, kd, dt, s);
+    case kTma64: return dns_launch_tma<64, 1>(nf, maps[ia], maps[2], a, psi, b, ax, kd, dt, s);
+    }
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kappa, double dt,
                     int nsteps, cudaStream_t s)
@@ -519,19 +722,33 @@ cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kap
     const double h = 2.0 * kPi / nf;
     const float ax = (float)(1.0 / (2.0 * h));
     const float kd = (float)(kappa / (h * h));
-    if (const char *env = std::getenv("MLSD_DNS_TY")) g_dns_ty = std::atoi(env) == 32 ? 32 : 64;
-    if (g_dns_ty == 0 && nsteps > 0) {
+    // tensor maps of u, u_tmp and psi; boxes of DLX x (DTY + 4), one map set per tile height
+    CUtensorMap m32[3], m64[3];
+    const bool tma = encode_f32_2d(&m32[0], u, nf, nf, DLX, 36) &&
+                     encode_f32_2d(&m32[1], u_tmp, nf, nf, DLX, 36) &&
+                     encode_f32_2d(&m32[2], psi, nf, nf, DLX, 36) &&
+                     encode_f32_2d(&m64[0], u, nf, nf, DLX, 68) &&
+                     encode_f32_2d(&m64[1], u_tmp, nf, nf, DLX, 68) &&
+                     encode_f32_2d(&m64[2], psi, nf, nf, DLX, 68);
+    auto maps_of = [&](int kind) -> const CUtensorMap * { return kind == kTma64 ? m64 : m32; };
+    if (const char *env = std::getenv("MLSD_DNS_TY")) {
+        const std::string v(env);
+        g_dns_kind = v == "32" ? kCp32 : v == "t32" ? kTma32 : v == "t32x2" ? kTma32x2
+                   : v == "t64" ? kTma64 : kCp64;
+    }
+    if (!tma && g_dns_kind >= kTma32) g_dns_kind = kCp32;
+    if (g_dns_kind < 0 && nsteps > 0) {
         // one trial step of each into u_tmp (u is not modified), best of two
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f;
-        for (int ty : {64, 32}) {
+        for (int kind = 0; kind < (tma ? (int)kDnsKinds : (int)kTma32); ++kind) {
             float t = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, s);
-                cudaError_t e = ty == 64 ? dns_launch<64>(nf, u, psi, u_tmp, ax, kd, (float)dt, s)
-                                         : dns_launch<32>(nf, u, psi, u_tmp, ax, kd, (float)dt, s);
+                cudaError_t e = dns_launch_kind(kind, nf, maps_of(kind), 0, u, psi, u_tmp, ax, kd,
+                                                (float)dt, s);
                 cudaEventRecord(e1, s);
                 if (e != cudaSuccess) return e;
                 cudaEventSynchronize(e1);
@@ -540,21 +757,50 @@ cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kap
                 if (rep > 0) t = std::min(t, ms);
             }
             count_launches(3);
-            if (t < best) { best = t; g_dns_ty = ty; }
+            if (t < best) { best = t; g_dns_kind = kind; }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
     float *a = u, *b = u_tmp;
+    int ia = 0;
     count_launches(nsteps);
     for (int st = 0; st < nsteps; ++st) {
-        cudaError_t e = g_dns_ty == 32 ? dns_launch<32>(nf, a, psi, b, ax, kd, (float)dt, s)
-                                       : dns_launch<64>(nf, a, psi, b, ax, kd, (float)dt, s);
+        cudaError_t e = dns_launch_kind(g_dns_kind, nf, maps_of(g_dns_kind), ia, a, psi, b, ax, kd,
+                                        (float)dt, s);
         if (e != cudaSuccess) return e;
         float *t = a; a = b; b = t;
+        ia ^= 1;
     }
     if (a != u)
         return cudaMemcpyAsync(u, a, (size_t)nf * nf * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError();
+}
+
+const char *dns_kernel_name()
+{
+    static const char *names[kDnsKinds] = {"k_dns_step<64>", "k_dns_step<32>", "k_dns_tma<32,1>",
+                                           "k_dns_tma<32,2>", "k_dns_tma<64,1>"};
+    return g_dns_kind < 0 ? "" : names[g_dns_kind];
+}
+
+int dns_status_take(cudaStream_t s)
+{
+    int v = 0;
+    const int zero = 0;
+    if (cudaMemcpyFromSymbolAsync(&v, g_dns_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyToSymbolAsync(g_dns_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return MLSD_ECUDA;
+    return v;
+}
+
+cudaError_t launch_wait_check_tile(int *status, cudaStream_t s)
+{
+    count_launches(1);
+    k_wait_check_tile<<<1, 32, 0, s>>>(status);
     return cudaGetLastError();
 }
 

@@ -495,6 +495,27 @@ bool encode_view(CUtensorMap *m, const void *base, long long rows, int K, int bo
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+}  // namespace
+
+// 2-D view of a row-major [height][width] FP32 array with a box of box_h rows of
+// box_w elements (zero fill outside the array)
+bool encode_f32_2d(void *map, const float *base, long long width, long long height, int box_w,
+                   int box_h)
+{
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)height};
+    cuuint64_t strides[1] = {(cuuint64_t)width * 4};
+    cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    cuuint32_t es[2] = {1, 1};
+    return enc(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+               const_cast<float *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+namespace {
+
 // Failure-path check of mbar_wait: one thread waits on a fresh mbarrier that
 // receives no arrival (no copy or MMA is in flight), so the wait expires and
 // the kernel latches MLSD_ETIMEOUT the way the inference kernels do.

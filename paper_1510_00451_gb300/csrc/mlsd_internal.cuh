@@ -120,6 +120,14 @@ cudaError_t launch_periodize(const float *band, long long Nl, int n, int n_macro
 // Failure-path checks of the two bounded device waits (nothing in flight).
 cudaError_t launch_wait_check_nbr(int *status, cudaStream_t s);
 cudaError_t launch_wait_check_mbar(int *status, cudaStream_t s);
+cudaError_t launch_wait_check_tile(int *status, cudaStream_t s);
+// 2-D FP32 tensor map (CUtensorMap, 128 bytes) of a row-major [height][width] array
+bool encode_f32_2d(void *map, const float *base, long long width, long long height, int box_w,
+                   int box_h);
+// MLSD_OK, or MLSD_ETIMEOUT when a tile wait of the DNS kernel ran out since the last call
+int dns_status_take(cudaStream_t s);
+// the DNS kernel the process picked ("" before the first run)
+const char *dns_kernel_name();
 
 // ---------------------------------------------------------------------------
 // Macro solver and direct simulation.

@@ -868,9 +868,10 @@ int mlsd_status(mlsd_levels *h, void *cuda_stream)
 
 int mlsd_check_wait_timeout(mlsd_levels *h, int which, void *cuda_stream)
 {
-    if (!h || (which != 0 && which != 1)) return MLSD_EINVAL;
+    if (!h || which < 0 || which > 2) return MLSD_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    CK(which == 0 ? launch_wait_check_nbr(h->status, s) : launch_wait_check_mbar(h->status, s));
+    CK(which == 0 ? launch_wait_check_nbr(h->status, s)
+       : which == 1 ? launch_wait_check_mbar(h->status, s) : launch_wait_check_tile(h->status, s));
     return MLSD_OK;
 }
 
@@ -1031,6 +1032,16 @@ int mlsd_dns_run(int nf, float *u_dev, float *u_tmp_dev, const float *psi_dev, d
     CK(dns_run(nf, u_dev, u_tmp_dev, psi_dev, kappa, dt, nsteps,
                static_cast<cudaStream_t>(cuda_stream)));
     return MLSD_OK;
+}
+
+int mlsd_dns_status(void *cuda_stream)
+{
+    return dns_status_take(static_cast<cudaStream_t>(cuda_stream));
+}
+
+const char *mlsd_dns_kernel(void)
+{
+    return dns_kernel_name();
 }
 
 int mlsd_dns_run_dirichlet(int nf, void *u_dev, void *u_tmp_dev, const float *psi_dev,

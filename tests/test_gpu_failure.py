@@ -1,8 +1,8 @@
 """Failure detection without a GPU fault: the bounded device waits.
 
-The cluster-split patch kernels and the tensor-core inference kernels wait on
-mbarriers with a bound of about a second of SM clocks; on expiry they latch
-MLSD_ETIMEOUT in the status word and return.  mlsd_check_wait_timeout runs
+The cluster-split patch kernels, the tensor-core inference kernels and the
+persistent DNS kernels wait on mbarriers with a bound of about a second of SM
+clocks; on expiry they latch MLSD_ETIMEOUT in a status word and return.  mlsd_check_wait_timeout runs
 each wait helper on an mbarrier that never receives an arrival, with nothing
 in flight, so the expiry path runs for real.  The test checks that the status
 reports MLSD_ETIMEOUT once, within a few seconds, and that the next ordinary
@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 MLSD_ETIMEOUT = -4
 
 
-@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("which", [0, 1, 2])
 def test_bounded_wait_expires_and_the_context_survives(which):
     import torch
     import paper_1510_00451_gb300 as mlsd
@@ -50,5 +50,5 @@ def test_wait_check_rejects_unknown_kind():
     import paper_1510_00451_gb300 as mlsd
     lv = mlsd.Levels(inputs.cellular_hierarchy(1, 4), 0.05, 2, [1.0, 4.0], [32],
                      n_burn_fixed=2, n_avg_fixed=2)
-    assert mlsd.lib().mlsd_check_wait_timeout(lv.h, 2, None) == -1
+    assert mlsd.lib().mlsd_check_wait_timeout(lv.h, 3, None) == -1
     assert mlsd.lib().mlsd_check_wait_timeout(None, 0, None) == -1

@@ -95,6 +95,7 @@ def test_dns_parity(mlsd, torch_mod, nf, steps):
     u = torch_mod.tensor(u0, dtype=torch_mod.float32, device=dev)
     ut = torch_mod.empty_like(u)
     mlsd.dns_run(u, ut, psi, kappa, dt, steps)
+    assert mlsd.dns_status() == 0
     assert rel_l2(u.cpu().numpy(), ur) < 1e-5
     # coarse-graining and the FP64 mass
     N = 32
@@ -105,6 +106,37 @@ def test_dns_parity(mlsd, torch_mod, nf, steps):
     assert m == pytest.approx(mr, rel=1e-6)
     m0 = oracle.coarse_grain(u0, N)[1]
     assert m == pytest.approx(m0, rel=1e-5)       # the DNS conserves sum(u)
+
+
+_DNS_REF = {}
+
+
+@pytest.mark.parametrize("kind", ["64", "32", "t32", "t32x2", "t64"])
+@pytest.mark.parametrize("nf,steps", [(256, 40), (2048, 6)])
+def test_dns_kernels_parity(mlsd, torch_mod, monkeypatch, kind, nf, steps):
+    # every DNS kernel, forced one at a time: per-tile CTAs staged by cp.async (64- and
+    # 32-row tiles) and persistent CTAs fed by tensor copies (one or two staging buffers).
+    # At 256^2 every tile touches the grid's edge (periodic images filled in after the
+    # copy); at 2048^2 most tiles are interior and each persistent CTA walks several
+    monkeypatch.setenv("MLSD_DNS_TY", kind)
+    spec = flows.cellular_two_scale(1.0, 0.3, 8)
+    kappa = 0.02
+    h = 2 * math.pi / nf
+    if nf not in _DNS_REF:
+        psi_r = oracle.grid_psi(spec, nf)
+        v1, v2 = oracle.velocity(psi_r, h)
+        dt = 0.2 * min(h / np.max(np.abs(v1) + np.abs(v2)), h * h / (4 * kappa))
+        u0 = flows.gaussian_u0(nf)
+        _DNS_REF[nf] = (dt, u0, oracle.dns_run(psi_r, kappa, dt, steps, u0))
+    dt, u0, ur = _DNS_REF[nf]
+    dev = torch_mod.device("cuda:0")
+    psi = torch_mod.zeros(nf, nf, dtype=torch_mod.float32, device=dev)
+    mlsd.grid_psi(spec, nf, psi)
+    u = torch_mod.tensor(u0, dtype=torch_mod.float32, device=dev)
+    ut = torch_mod.empty_like(u)
+    mlsd.dns_run(u, ut, psi, kappa, dt, steps)
+    assert mlsd.dns_status() == 0
+    assert rel_l2(u.cpu().numpy(), ur) < 1e-5
 
 
 @pytest.mark.slow
