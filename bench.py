@@ -46,13 +46,15 @@ FLOP_PER_WINDOW_UPDATE = 5
 # DRAM bytes (read + write) per patch-solve launch of this workload, measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the three level launches of
 # `--case profile`: the same grids, bands and tiling as the timed step (the window
-# length does not change it); 5.15 MB, 1.46 MB and 0.73 MB read, nothing written.
-PATCH_DRAM_BYTES_PER_LAUNCH = (5153792 + 1461504 + 733696) / 3
+# length does not change it); 5.21 MB, 1.38 MB and 0.86 MB read, nothing written.
+PATCH_DRAM_BYTES_PER_LAUNCH = (5206528 + 1382144 + 861952) / 3
 # DRAM bytes per DNS launch on the 8192^2 grid, ncu on `--case dns-full` (two launches),
 # by kernel; a kernel without a capture reports no traffic
 DNS_DRAM_BYTES_PER_LAUNCH = {
     # 32-row tiles: 537.2 MB read + 236.1 MB written (algorithmic: 805.3 MB)
     "k_dns_step<32>": (537227776 + 237750016 + 537195776 + 234513664) / 2,
+    # persistent, tensor copies, 32-row tiles: 537.3 MB read + 235.2 MB written
+    "k_dns_tma<32,1>": (537318656 + 236889344 + 537293824 + 233592832) / 2,
 }
 WORKLOAD = "three_level_cellular"
 

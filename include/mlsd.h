@@ -243,18 +243,23 @@ int mlsd_effective_diffusivity(mlsd_levels *h, int mode, double *K_macro_dev,
  * t_i = 2 pi k_i / n, s_i = sin t_i), A w = v1 D0x w + v2 D0y w.  Expanding in
  * v: c_j^0 = -L0^{-1} v_j, c_j^m = -L0^{-1} A c_j^{m-1}, and K - B = sum of
  *   T_m = sym <v_i c_j^{m-2}>  (m >= 2; T_2 is the small-Peclet limit).
- * The library computes T_2..T_19 on the patch grid with FFTs (n = 32 or 64)
- * and resums the series where it diverges: with the pairs
+ * The library computes T_2..T_19 on the feature grid with FFTs and resums
+ * the series where it diverges: with the pairs
  * p_k = T_(2k+2) + T_(2k+3), the [K/K] Pade approximant at 1 of sum_k p_k x^k
  * (Wynn's epsilon algorithm on the partial sums) for K = 2, 3, 4; the
  * estimate is E = [4/4], and gap = max_c |[4/4]_c - [3/3]_c| measures how far
  * it is from converged.
  *
+ * Feature grid: the patch nodes for n = 32 and 64; for n = 128 and 256 the
+ * nf = 64 x 64 sub-lattice of every (n/64)-th node (psi and the moments are
+ * taken there; a band resolved on the patch is resolved on the sub-lattice:
+ * its modes up to the window's 8 are exact, and the moments converge like
+ * the grid).
  * Features of a patch (MLSD_SUR_FEATURES = 606 values, stored as one bfloat16
  * row of MLSD_SUR_IN = 640, zero padded):
- *   [0, 578)  Re and Im of the patch DFT
- *               psihat(k) = n^-2 sum_ab (psi[b][a] - mean psi) exp(-2 pi i (k1 a + k2 b)/n)
- *             of the level's band at the patch nodes, k2 = -8..8 (slow),
+ *   [0, 578)  Re and Im of the DFT on the feature grid (nf nodes a side)
+ *               psihat(k) = nf^-2 sum_ab (psi[b][a] - mean psi) exp(-2 pi i (k1 a + k2 b)/nf)
+ *             of the level's band, k2 = -8..8 (slow),
  *             k1 = -8..8, each times MLSD_SUR_PSI_SCALE / (tr(B)/2);
  *   578..580  B11/kappa, B12/kappa, B22/kappa;   581  log kappa;
  *   582..596  asinh(MLSD_SUR_T_SCALE T_m / tr(B)), m = 2..6, components 11, 12, 22;
@@ -281,9 +286,9 @@ void mlsd_surrogate_free(mlsd_surrogate *s);
 /* host FP32 parameter arrays (layout above); set resets the Adam state      */
 int mlsd_surrogate_set_params(mlsd_surrogate *s, int member, const float *params_host);
 int mlsd_surrogate_get_params(mlsd_surrogate *s, int member, float *params_host);
-/* Features of every patch of a level (one patch size per level, n = 32 or 64)
- * with base B_dev [P][3]: X_dev bfloat16 [P][640]; F32_dev [P][606] or NULL.
- * Other sizes: MLSD_EUNSUPPORTED.                                           */
+/* Features of every patch of a level (one patch size per level, n = 32, 64,
+ * 128 or 256; FP32) with base B_dev [P][3]: X_dev bfloat16 [P][640]; F32_dev
+ * [P][606] or NULL.  Levels of several sizes: MLSD_EUNSUPPORTED.            */
 int mlsd_surrogate_features(mlsd_levels *h, int level, const double *B_dev, void *X_dev,
                             float *F32_dev, void *cuda_stream);
 /* Mean-squared-error loss of one member on M <= max_batch rows (X bfloat16

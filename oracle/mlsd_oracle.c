@@ -1064,7 +1064,9 @@ void orc_series_estimate(const double *T, double *P2, double *P3, double *E, dou
 /* Learned surrogate of the patch solve (not in the paper; the library's     */
 /* estimator it is checked against is orc_patch_k).                          */
 /*                                                                           */
-/* Features of a patch (606 values):                                         */
+/* Features of a patch (606 values; a patch above 64 x 64 is described by   */
+/* its samples on the 64 x 64 sub-lattice of every (n/64)-th node, with the  */
+/* sub-lattice mean removed, and n below stands for 64):                     */
 /*   [0, 578): Re and Im of psihat(k) = n^-2 sum_ab psi[b][a]               */
 /*             exp(-2 pi i (k1 a + k2 b) / n) for k2 = -8..8 (slow),         */
 /*             k1 = -8..8 (fast), each times 32 / (tr(B)/2) (a Peclet        */
@@ -1084,6 +1086,22 @@ void orc_series_estimate(const double *T, double *P2, double *P3, double *E, dou
 #define ORC_T_SCALE 10.0
 void orc_features(int n, const double *psi, const double *B, double kappa, double *f)
 {
+    if (n > 64) {
+        /* patches above 64 x 64: the features of the samples on the 64 x 64 */
+        /* sub-lattice of every (n/64)-th node, sub-lattice mean removed       */
+        const int s = n / 64;
+        double *q = malloc(sizeof(double) * 64 * 64), mean = 0.0;
+        for (int b = 0; b < 64; ++b)
+            for (int a = 0; a < 64; ++a) {
+                q[b * 64 + a] = psi[(long)(b * s) * n + a * s];
+                mean += q[b * 64 + a];
+            }
+        mean /= 64.0 * 64.0;
+        for (int c = 0; c < 64 * 64; ++c) q[c] -= mean;
+        orc_features(64, q, B, kappa, f);
+        free(q);
+        return;
+    }
     const double trh = 0.5 * (B[0] + B[2]);
     int t = 0;
     for (int k2 = -8; k2 <= 8; ++k2)

@@ -714,6 +714,8 @@ int mlsd_offdiag(mlsd_levels *h, int level, const double *B_dev, double *Koff_de
 
 namespace {
 int surrogate_level_async(mlsd_levels *h, DevLevel &d, cudaStream_t s);
+// patch sizes the surrogate's features serve (above 64: on the 64 x 64 sub-lattice)
+inline bool sur_size_ok(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
 int surrogate_workspace(mlsd_levels *h, DevLevel &d, mlsd_surrogate *sur);
 
 // Algorithm 3 over all levels, enqueued on stream s
@@ -828,7 +830,7 @@ int mlsd_attach_surrogate(mlsd_levels *h, int level, mlsd_surrogate *s, double t
 {
     if (!h || level < 1 || level > h->L || !(threshold >= 0)) return MLSD_EINVAL;
     DevLevel &d = h->lev[level - 1];
-    if (s && (d.cls.size() != 1 || (d.cls[0].n != 32 && d.cls[0].n != 64) ||
+    if (s && (d.cls.size() != 1 || !sur_size_ok(d.cls[0].n) ||
               h->precision != MLSD_FP32))
         return MLSD_EUNSUPPORTED;
     if (s) {
@@ -1222,7 +1224,7 @@ int mlsd_surrogate_features(mlsd_levels *h, int level, const double *B_dev, void
 {
     if (!h || level < 1 || level > h->L || !B_dev || !X_dev) return MLSD_EINVAL;
     DevLevel &d = h->lev[level - 1];
-    if (d.cls.size() != 1 || (d.cls[0].n != 32 && d.cls[0].n != 64) || h->precision != MLSD_FP32)
+    if (d.cls.size() != 1 || !sur_size_ok(d.cls[0].n) || h->precision != MLSD_FP32)
         return MLSD_EUNSUPPORTED;
     const SizeClass &c = d.cls[0];
     CK(launch_features(static_cast<const float *>(c.band), c.Nl, c.tile, c.n, h->N, nullptr, h->P, B_dev,
@@ -1272,7 +1274,7 @@ int mlsd_surrogate_dataset(mlsd_levels *h, int level, const double *B_dev, void 
 {
     if (!h || level < 1 || level > h->L || !B_dev || !X_dev || !Y_dev) return MLSD_EINVAL;
     DevLevel &d = h->lev[level - 1];
-    if (d.cls.size() != 1 || (d.cls[0].n != 32 && d.cls[0].n != 64) || h->precision != MLSD_FP32)
+    if (d.cls.size() != 1 || !sur_size_ok(d.cls[0].n) || h->precision != MLSD_FP32)
         return MLSD_EUNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const long long P = h->P;
@@ -1452,7 +1454,7 @@ int mlsd_solve_level_surrogate(mlsd_levels *h, mlsd_surrogate *s, int level,
     if (!h || !s || level < 1 || level > h->L || !K_base_dev || !K_out_dev || !(threshold >= 0))
         return MLSD_EINVAL;
     DevLevel &d = h->lev[level - 1];
-    if (d.cls.size() != 1 || (d.cls[0].n != 32 && d.cls[0].n != 64) || h->precision != MLSD_FP32)
+    if (d.cls.size() != 1 || !sur_size_ok(d.cls[0].n) || h->precision != MLSD_FP32)
         return MLSD_EUNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const long long P = h->P;

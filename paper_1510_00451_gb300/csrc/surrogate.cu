@@ -28,32 +28,34 @@ constexpr int KMODE = 8;                   // local modes -8..8
 constexpr int NMODE = 2 * KMODE + 1;       // 17
 
 // ---------------------------------------------------------------------------
-// Features 0..581 and the zero padding: one CTA per patch (n <= 64: the patch is
-// staged in shared memory)
-__global__ void k_features(const float *band, long long Nl, long long tile, int n, int n_macro,
-                           const int *pidx, long long count, const double *B, double kappa,
-                           __nv_bfloat16 *X, float *F32)
+// Features 0..581 and the zero padding: one CTA per patch.  The features of an
+// n x n patch are those of its nf x nf samples every sub-th node (nf = n / sub
+// <= 64: the samples are staged in shared memory)
+__global__ void k_features(const float *band, long long Nl, long long tile, int n, int sub,
+                           int n_macro, const int *pidx, long long count, const double *B,
+                           double kappa, __nv_bfloat16 *X, float *F32)
 {
+    const int nf = n / sub;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *psi = reinterpret_cast<float *>(smem_raw);              // [n][n]
-    float2 *Fr = reinterpret_cast<float2 *>(psi + n * n);          // [n][17] row transforms
+    float *psi = reinterpret_cast<float *>(smem_raw);              // [nf][nf]
+    float2 *Fr = reinterpret_cast<float2 *>(psi + nf * nf);        // [nf][17] row transforms
     __shared__ double red[32];
-    __shared__ float2 tw[64];                                      // e^{-2 pi i r / n}
+    __shared__ float2 tw[64];                                      // e^{-2 pi i r / nf}
     const long long item = blockIdx.x;
     if (item >= count) return;
     const long long p = pidx ? (long long)pidx[item] : item;
     const long long ox = patch_origin(p % n_macro, n_macro, Nl, n);
     const long long oy = patch_origin(p / n_macro, n_macro, Nl, n);
     double sum = 0.0;
-    for (int c = threadIdx.x; c < n * n; c += blockDim.x) {
-        const int b = c / n, a = c % n;
-        const float v = patch_band(band, Nl, tile, p, ox, oy, n, a, b);
+    for (int c = threadIdx.x; c < nf * nf; c += blockDim.x) {
+        const int b = c / nf, a = c % nf;
+        const float v = patch_band(band, Nl, tile, p, ox, oy, n, a * sub, b * sub);
         psi[c] = v;
         sum += v;
     }
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    for (int r = threadIdx.x; r < nf; r += blockDim.x) {
         float s, c;
-        sincospif(-2.0f * (float)r / (float)n, &s, &c);
+        sincospif(-2.0f * (float)r / (float)nf, &s, &c);
         tw[r] = make_float2(c, s);
     }
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -61,39 +63,38 @@ __global__ void k_features(const float *band, long long Nl, long long tile, int 
     __syncthreads();
     double tot = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-    const float mean = (float)(tot / ((double)n * n));
-    // rows: Fr[b][k1] = sum_a (psi - mean) e^{-2 pi i k1 a / n}
-    for (int t = threadIdx.x; t < n * NMODE; t += blockDim.x) {
+    const float mean = (float)(tot / ((double)nf * nf));
+    // rows: Fr[b][k1] = sum_a (psi - mean) e^{-2 pi i k1 a / nf}
+    for (int t = threadIdx.x; t < nf * NMODE; t += blockDim.x) {
         const int b = t / NMODE, k1 = t % NMODE - KMODE;
         float sr = 0.f, si = 0.f;
-        const int step = (int)pmod_ll((long long)k1, n);
+        const int step = (int)pmod_ll((long long)k1, nf);
         int r = 0;
-        for (int a = 0; a < n; ++a) {
+        for (int a = 0; a < nf; ++a) {
             const float2 w = tw[r];
-            const float v = psi[b * n + a] - mean;
+            const float v = psi[b * nf + a] - mean;
             sr = fmaf(v, w.x, sr);
             si = fmaf(v, w.y, si);
             r += step;
-            if (r >= n) r -= n;
+            if (r >= nf) r -= nf;
         }
         Fr[t] = make_float2(sr, si);
     }
     __syncthreads();
     const double B11 = B[3 * p], B12 = B[3 * p + 1], B22 = B[3 * p + 2];
     const double trh = 0.5 * (B11 + B22);
-    const float scale = (float)(MLSD_SUR_PSI_SCALE / ((double)n * n * trh));
-    const double inv_nn = 1.0 / ((double)n * n);
+    const float scale = (float)(MLSD_SUR_PSI_SCALE / ((double)nf * nf * trh));
     __nv_bfloat16 *xr = X + item * (long long)MLSD_SUR_IN;
     float *fr = F32 ? F32 + item * (long long)MLSD_SUR_FEATURES : nullptr;
     for (int t = threadIdx.x; t < NMODE * NMODE; t += blockDim.x) {
         const int k2 = t / NMODE - KMODE, k1i = t % NMODE;
         float sr = 0.f, si = 0.f;
-        const int step = (int)pmod_ll((long long)k2, n);
+        const int step = (int)pmod_ll((long long)k2, nf);
         int r = 0;
-        for (int b = 0; b < n; ++b) {
+        for (int b = 0; b < nf; ++b) {
             const float c = tw[r].x, s = tw[r].y;
             r += step;
-            if (r >= n) r -= n;
+            if (r >= nf) r -= nf;
             const float2 f = Fr[b * NMODE + k1i];
             // (f.x + i f.y)(c + i s)
             sr += f.x * c - f.y * s;
@@ -238,9 +239,9 @@ constexpr int SERIES_M = 19;               // moments T_2..T_19
 
 template <int N>
 __global__ void __launch_bounds__(256) k_series(const float *band, long long Nl, long long tile,
-                                                int n_macro, const int *pidx, long long count,
-                                                const double *B, __nv_bfloat16 *X, float *F32,
-                                                double *Eout)
+                                                int n, int sub, int n_macro, const int *pidx,
+                                                long long count, const double *B,
+                                                __nv_bfloat16 *X, float *F32, double *Eout)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *z = reinterpret_cast<float2 *>(smem_raw);               // [N][N] complex
@@ -254,13 +255,13 @@ __global__ void __launch_bounds__(256) k_series(const float *band, long long Nl,
     const long long item = blockIdx.x;
     if (item >= count) return;
     const long long p = pidx ? (long long)pidx[item] : item;
-    const long long ox = patch_origin(p % n_macro, n_macro, Nl, N);
-    const long long oy = patch_origin(p / n_macro, n_macro, Nl, N);
+    const long long ox = patch_origin(p % n_macro, n_macro, Nl, n);
+    const long long oy = patch_origin(p / n_macro, n_macro, Nl, n);
     const double B11 = B[3 * p], B12 = B[3 * p + 1], B22 = B[3 * p + 2];
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
         const int b = e / N, a = e % N;
-        const float v = patch_band(band, Nl, tile, p, ox, oy, N, a, b);
+        const float v = patch_band(band, Nl, tile, p, ox, oy, n, a * sub, b * sub);
         psi[e] = v;
         acc[0] += v;
         // the symbol of -L0^{-1}, once per patch
@@ -876,37 +877,40 @@ long long sur_param_count(int h)
 }
 
 template <int N>
-static cudaError_t launch_series(const float *band, long long Nl, long long tile, int n_macro,
-                                 const int *pidx, long long count, const double *B, void *X,
-                                 float *F32, double *E, cudaStream_t s)
+static cudaError_t launch_series(const float *band, long long Nl, long long tile, int n, int sub,
+                                 int n_macro, const int *pidx, long long count, const double *B,
+                                 void *X, float *F32, double *E, cudaStream_t s)
 {
     const size_t smem = (size_t)N * N * (8 + 5 * 4) + (size_t)N / 2 * 8;
     cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_series<N>),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    k_series<N><<<(unsigned)count, 256, smem, s>>>(band, Nl, tile, n_macro, pidx, count, B,
-                                                   static_cast<__nv_bfloat16 *>(X), F32, E);
+    k_series<N><<<(unsigned)count, 256, smem, s>>>(band, Nl, tile, n, sub, n_macro, pidx, count,
+                                                   B, static_cast<__nv_bfloat16 *>(X), F32, E);
     return cudaGetLastError();
 }
 
+// Features of n x n patches, n = 32, 64, 128 or 256: patches above 64 x 64 are
+// described by their samples on the 64 x 64 sub-lattice (every n/64-th node)
 cudaError_t launch_features(const float *band, long long Nl, long long tile, int n, int n_macro,
                             const int *pidx, long long count, const double *B, double kappa,
                             void *X, float *F32, double *E, cudaStream_t s)
 {
     if (count == 0) return cudaSuccess;
-    if (n != 32 && n != 64) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)n * n * 4 + (size_t)n * NMODE * 8;
+    if (n != 32 && n != 64 && n != 128 && n != 256) return cudaErrorInvalidValue;
+    const int nf = n < 64 ? n : 64, sub = n / nf;
+    const size_t smem = (size_t)nf * nf * 4 + (size_t)nf * NMODE * 8;
     cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_features),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    k_features<<<(unsigned)count, 320, smem, s>>>(band, Nl, tile, n, n_macro, pidx, count, B,
+    k_features<<<(unsigned)count, 320, smem, s>>>(band, Nl, tile, n, sub, n_macro, pidx, count, B,
                                                   kappa, static_cast<__nv_bfloat16 *>(X), F32);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return n == 32 ? launch_series<32>(band, Nl, tile, n_macro, pidx, count, B, X, F32, E, s)
-                   : launch_series<64>(band, Nl, tile, n_macro, pidx, count, B, X, F32, E, s);
+    return nf == 32 ? launch_series<32>(band, Nl, tile, n, sub, n_macro, pidx, count, B, X, F32, E, s)
+                    : launch_series<64>(band, Nl, tile, n, sub, n_macro, pidx, count, B, X, F32, E, s);
 }
 
 template <int N>

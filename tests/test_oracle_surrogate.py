@@ -355,3 +355,49 @@ def test_features_of_the_mapped_patch_follow_the_stated_rule(g):
     np.testing.assert_allclose(f_g[578:597], _feature_rule(f, g)[578:597], rtol=1e-12, atol=1e-15)
     # the resummed values (Wynn's epsilon) amplify the rounding of the moments
     np.testing.assert_allclose(f_g[597:], _feature_rule(f, g)[597:], rtol=1e-8, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_large_patch_features_are_the_full_resolution_dft_window(n):
+    # a band resolved on the patch (local modes |k| <= 3) has the same DFT window on the
+    # 64 x 64 sub-lattice as on all n x n nodes: the sub-lattice features equal the
+    # window of the full-resolution transform (normalised by n^2)
+    rng = np.random.default_rng(n)
+    psi = _smooth_psi(n, rng)
+    B = np.array([0.3, 0.05, 0.5])
+    f = oracle.features(psi, B, 0.01)
+    F = np.fft.fft2(psi) / n ** 2
+    want = []
+    for k2 in range(-8, 9):
+        for k1 in range(-8, 9):
+            c = F[k2 % n, k1 % n] * 32.0 / (0.5 * (B[0] + B[2]))
+            want += [c.real, c.imag]
+    np.testing.assert_allclose(f[:578], want, atol=1e-11)
+    # and it is the 64 x 64 rule: the features of the samples every n/64-th node
+    s = n // 64
+    q = psi[::s, ::s] - psi[::s, ::s].mean()
+    np.testing.assert_allclose(f, oracle.features(q, B, 0.01), rtol=1e-9, atol=1e-10)
+
+
+def test_large_patch_moments_converge_with_the_grid():
+    # the moments on the sub-lattice are the grid moments of a coarser resolution of the
+    # same band: against the full 128 x 128 grid and 256 x 256 grid, T_2..T_6 differ by
+    # the second-order truncation error, which falls ~4x from 64 to 128 nodes a side
+    rng = np.random.default_rng(5)
+    a, b = np.meshgrid(np.arange(256), np.arange(256))
+    psi256 = np.zeros((256, 256))
+    for _ in range(5):
+        k1, k2 = rng.integers(-2, 3, 2)
+        ph = rng.uniform(0, 2 * math.pi)
+        psi256 += 0.02 * rng.normal() * np.cos(2 * math.pi * (k1 * a + k2 * b) / 256 + ph)
+    psi256 -= psi256.mean()
+    B = np.array([0.01, 0.002, 0.015])
+    T = {m: oracle.series(psi256[::256 // m, ::256 // m], B, M=6) for m in (64, 128, 256)}
+    f = oracle.features(psi256, B, 0.01)
+    got = np.sinh(f[582:597]).reshape(5, 3) * (B[0] + B[2]) / 10.0
+    np.testing.assert_allclose(got, T[64], rtol=1e-9, atol=1e-15)
+    e64 = np.abs(T[64] - T[256]).max()
+    e128 = np.abs(T[128] - T[256]).max()
+    scale = np.abs(T[256]).max()
+    assert e64 < 0.05 * scale
+    assert 3.0 < e64 / e128 < 5.5, (e64, e128)
