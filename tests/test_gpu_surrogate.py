@@ -28,7 +28,7 @@ def mlsd():
     return m
 
 
-@pytest.mark.parametrize("n", [32, 64])
+@pytest.mark.parametrize("n", [32, 64, 128, 256])
 def test_features_match_oracle(mlsd, torch_mod, n):
     spec = flows.continuous_spectrum(40, seed=9)
     edges, N, kappa = [1, 4, 16, 41], 3, 2e-3
@@ -62,7 +62,11 @@ def test_features_match_oracle(mlsd, torch_mod, n):
             # beyond the series' reach: Wynn's epsilon then amplifies the FP32
             # rounding of the moments up to T_19), both sides see it unconverged
             # and the fallback rule takes the patch
-            T = oracle.series(psi, B[p])
+            q = psi
+            if n > 64:                         # the features' 64 x 64 sub-lattice
+                q = psi[::n // 64, ::n // 64]
+                q = q - q.mean()
+            T = oracle.series(q, B[p])
             _, _, E, gap = oracle.series_estimate(T)
             gp, ap = np.abs(got[21:24] - got[18:21]).max(), np.abs(got[21:24]).max()
             assert np.all(np.isfinite(got)), (level, p)
@@ -171,10 +175,12 @@ def test_library_training_loop_and_checkpoint(mlsd, torch_mod, tmp_path):
         mlsd.Surrogate(members=3, hidden=h, max_batch=256).load(path)
 
 
-def test_surrogate_level_fallback_paths(mlsd, torch_mod):
+@pytest.mark.parametrize("n", [32, 128])
+def test_surrogate_level_fallback_paths(mlsd, torch_mod, n):
+    # n = 128: features on the 64 x 64 sub-lattice, fallback solves by the cluster kernel
     spec = flows.continuous_spectrum(40, seed=9)
     edges, N, kappa = [1, 4, 16, 41], 4, 2e-3
-    lv = mlsd.Levels(spec, kappa, N, edges, [32] * 3, n_burn_fixed=50, n_avg_fixed=50)
+    lv = mlsd.Levels(spec, kappa, N, edges, [n] * 3, n_burn_fixed=50, n_avg_fixed=50)
     dev = torch_mod.device("cuda:0")
     B = torch_mod.tensor(inputs.random_bases(N * N, kappa, 1), dtype=torch_mod.float64, device=dev)
     K_plain = torch_mod.zeros_like(B)
@@ -296,14 +302,16 @@ def test_trained_surrogate_replaces_most_patch_solves(mlsd, torch_mod):
         (np.mean(e_net <= 1e-3), np.mean(e_ser <= 1e-3))
 
 
-def test_chain_in_surrogate_mode(mlsd, torch_mod):
+@pytest.mark.parametrize("n", [32, 128])
+def test_chain_in_surrogate_mode(mlsd, torch_mod, n):
     # Algorithm 3 with a surrogate attached to the finest level: at threshold 0
     # every patch falls back and the chain equals the plain chain; at a huge
     # threshold the finest K* is the ensemble's and the coarser level is solved
-    # on it as on any base
+    # on it as on any base (n = 128: the finest level's fallback runs the cluster
+    # kernel, sized on the device inside the captured chain)
     spec = flows.cellular_two_scale(1.0, 0.4, 8)
     N, kappa = 4, 0.05
-    lv = mlsd.Levels(spec, kappa, N, [1, 8, 16], [32, 32], n_burn_fixed=120, n_avg_fixed=80)
+    lv = mlsd.Levels(spec, kappa, N, [1, 8, 16], [32, n], n_burn_fixed=120, n_avg_fixed=80)
     dev = torch_mod.device("cuda:0")
     P = N * N
     K_plain = torch_mod.zeros(P, 3, dtype=torch_mod.float64, device=dev)
