@@ -207,6 +207,9 @@ DNS_BYTES_PER_CELL_STEP = 12     # read u, read psi, write u (both RK stages fus
 
 
 SUR_OCTAVES = ((16, 32, 64), (32, 64, 32), (64, 128, 32))   # (lo, hi, patch n) of each level
+# the 4th octave at 128^2 (features on the 64^2 sub-lattice): its plain solve costs ~10 ms a
+# patch, so it trains on 2 base sets of a 64 x 64 macro grid and tests on a 32 x 32 one
+SUR_OCTAVE_128 = (8, 16, 128, 64, 2, 32)                      # (lo, hi, n, N train, bases, N test)
 SUR_TRAIN_FLOW, SUR_TEST_FLOW = 1510004510, 20261204           # continuous-spectrum seeds
 
 
@@ -223,7 +226,7 @@ def _octave_level(seed, lo, hi, n, N, kappa):
 
 
 def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3,
-                   thresholds=(5e-4, 1e-3, 2e-3), seed=1510):
+                   thresholds=(5e-4, 1e-3, 2e-3), seed=1510, large=False):
     """Surrogate vs plain on three octave levels of the continuous-spectrum flow
     (kappa = 1e-3, N x N patches per level, full relaxation window): the 5th
     octave (16 <= |k| < 32, 64^2 patches), the 6th and the 7th (32^2).  Training
@@ -231,7 +234,9 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
     realization (3 N^2 plain solves); test: the same levels of ANOTHER
     realization (no patch psi seen in training) with a fresh base set.  Reports,
     per level and threshold, the fallback fraction, the K error against the plain
-    solve and the K-tensor rate of both paths, and the totals over the levels."""
+    solve and the K-tensor rate of both paths, and the totals over the levels.
+    With large, the 4th octave at 128^2 patches joins (SUR_OCTAVE_128) and is
+    reported on its own (not in the totals)."""
     import torch
     import inputs
     import paper_1510_00451_gb300 as mlsd
@@ -239,11 +244,15 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
     dev = torch.device("cuda", _local_rank())
     kappa = 1e-3
     P = N * N
+    octs = [(lo, hi, n, N, 1, N) for (lo, hi, n) in SUR_OCTAVES]
+    if large:
+        octs = octs + [SUR_OCTAVE_128]
     t0 = time.perf_counter()
     Xs, Ys = [], []
-    for i, (lo, hi, n) in enumerate(SUR_OCTAVES):
-        lv = _octave_level(SUR_TRAIN_FLOW, lo, hi, n, N, kappa)
-        X, Y = S.make_dataset(lv, 1, [inputs.random_bases(P, kappa, seed + 100 + i)])
+    for i, (lo, hi, n, Ntr, nb, _) in enumerate(octs):
+        lv = _octave_level(SUR_TRAIN_FLOW, lo, hi, n, Ntr, kappa)
+        bases = [inputs.random_bases(Ntr * Ntr, kappa, seed + 100 + i + 10 * j) for j in range(nb)]
+        X, Y = S.make_dataset(lv, 1, bases)
         Xs.append(X); Ys.append(Y)
         lv.close()
     X, Y = torch.cat(Xs), torch.cat(Ys)
@@ -267,34 +276,44 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
         return r, e0.elapsed_time(e1) * 1e-3
 
     levels, tot_plain, tot_sur, errs = [], 0.0, {t: 0.0 for t in thresholds}, {t: [] for t in thresholds}
-    for i, (lo, hi, n) in enumerate(SUR_OCTAVES):
-        lv = _octave_level(SUR_TEST_FLOW, lo, hi, n, N, kappa)
+    for i, (lo, hi, n, _, _, Nte) in enumerate(octs):
+        P = Nte * Nte
+        lv = _octave_level(SUR_TEST_FLOW, lo, hi, n, Nte, kappa)
         Bt = torch.tensor(inputs.random_bases(P, kappa, seed + 99 + i), dtype=torch.float64,
                           device=dev)
         Kp = torch.empty_like(Bt); Ks = torch.empty_like(Bt)
-        lv.solve_level(1, Bt, Kp)                       # warm-up
+        if n <= 64:
+            lv.solve_level(1, Bt, Kp)                   # warm-up
         _, t_plain = timed(lambda: lv.solve_level(1, Bt, Kp))
         Kpn = Kp.cpu().numpy()
         rows = []
+        in_total = n <= 64
+        lv.solve_level_surrogate(sur, 1, Bt, Ks, 1e30)      # warm-up; the ensemble alone
+        err0 = S.k_error(Ks.cpu().numpy(), Kpn)
         for thr in thresholds:
-            lv.solve_level_surrogate(sur, 1, Bt, Ks, thr)   # warm-up
             nfb, t_sur = timed(lambda: lv.solve_level_surrogate(sur, 1, Bt, Ks, thr))
             err = S.k_error(Ks.cpu().numpy(), Kpn)
-            errs[thr].append(err)
-            tot_sur[thr] += t_sur
+            if in_total:
+                errs[thr].append(err)
+                tot_sur[thr] += t_sur
             rows.append({"threshold": thr, "fallback_frac": nfb / P, "seconds": t_sur,
                          "k_tensors_per_s": P / t_sur, "speedup_vs_plain": t_plain / t_sur,
                          "k_rel_err": {"max": float(err.max()), "p99": float(np.quantile(err, 0.99)),
                                        "median": float(np.median(err)),
                                        "frac_le_1e-3": float(np.mean(err <= 1e-3))}})
-        tot_plain += t_plain
-        levels.append({"octave": f"{lo}<=|k|<{hi}", "patch_n": n, "plain_seconds": t_plain,
+        if in_total:
+            tot_plain += t_plain
+        levels.append({"octave": f"{lo}<=|k|<{hi}", "patch_n": n, "patches": P,
+                       "in_totals": in_total, "plain_seconds": t_plain,
                        "plain_k_tensors_per_s": P / t_plain,
                        "plain_cell_updates_per_s": lv.level_work(1)[0] / t_plain,
+                       "ensemble_only": {"median": float(np.median(err0)),
+                                         "frac_le_1e-3": float(np.mean(err0 <= 1e-3))},
                        "by_threshold": rows})
         assert lv.status() == 0
         lv.close()
     overall = []
+    P = N * N
     for thr in thresholds:
         err = np.concatenate(errs[thr])
         overall.append({"threshold": thr, "speedup_vs_plain": tot_plain / tot_sur[thr],
@@ -314,9 +333,13 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
     mlp_flop = 2.0 * P * members * (mlsd.SUR_IN * hidden + 2 * hidden * hidden + hidden * 16)
     assert sur.status() == 0
     peak, src = _peak("bf16_tflops")
+    extra = (f"; plus octave 8-16 at 128^2 ({SUR_OCTAVE_128[3] ** 2 * SUR_OCTAVE_128[4]} "
+             f"training solves, {SUR_OCTAVE_128[5] ** 2} test patches, outside the totals)"
+             if large else "")
     return {"workload": f"continuous-spectrum octaves 16-32 (64^2), 32-64, 64-128 (32^2), {P} "
                         "patches each, kappa=1e-3, full window; trained on one flow "
-                        f"realization ({len(SUR_OCTAVES) * P} plain solves), tested on another",
+                        f"realization ({len(SUR_OCTAVES) * P} plain solves), tested on another"
+                        + extra,
             "members": members, "hidden": hidden, "epochs": epochs, "batch": batch,
             "final_loss": losses, "levels": levels, "overall": overall,
             "plain_k_tensors_per_s": len(SUR_OCTAVES) * P / tot_plain,
@@ -905,7 +928,8 @@ def main():
     ap.add_argument("--no-experiments", action="store_true",
                     help="skip the Sec. 4 comparisons (set-up, off-diagonal stress, geometry)")
     ap.add_argument("--case", default="full",
-                    choices=["full", "profile", "dns-profile", "dns-full", "surrogate", "uneven",
+                    choices=["full", "profile", "dns-profile", "dns-full", "surrogate",
+                             "surrogate-large", "uneven",
                              "mlp-profile", "cluster-profile", "train-profile", "sec4",
                              "spectrum-dns", "offdiag", "geometry", "series-profile"],
                     help="profile: one pass of the same workload with a fixed 200-step window "
@@ -921,6 +945,9 @@ def main():
         return dns_case(8192, 10, warmup=2, report=True)
     if args.case == "surrogate":
         print(json.dumps({"case": "surrogate", **surrogate_case()}), flush=True)
+        return 0
+    if args.case == "surrogate-large":
+        print(json.dumps({"case": "surrogate-large", **surrogate_case(large=True)}), flush=True)
         return 0
     if args.case == "mlp-profile":
         return mlp_case()

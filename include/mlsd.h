@@ -441,7 +441,7 @@ int mlsd_grid_psi(int n_modes, const int32_t *k1, const int32_t *k2, const doubl
  * caller-provided work field of the same size.  nf a multiple of 128.
  * One fused launch per step; the kernel (per-tile CTAs staged by cp.async, or
  * persistent CTAs fed by tensor copies) is picked once per process by timing
- * each on the caller's grid (MLSD_DNS_TY = 64 | 32 | t32 | t32x2 | t64 pins
+ * each on the caller's grid (MLSD_DNS_TY = 64 | 32 | t32 | t32x2 | t64 | t32p pins
  * one).  The persistent kernels take tiles from a per-device queue: one DNS
  * run at a time per device.  Asynchronous: a tile copy that never lands (a
  * wait of about a second runs out) is reported by mlsd_dns_status.           */

@@ -327,6 +327,120 @@ __device__ __forceinline__ void dns_tile(const float *su, const float *sp, float
     }
 }
 
+// f32x2 helpers: a - b as fma(b, -1, a), which rounds like the subtraction
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 bcast2(float v) { return make_float2(v, v); }
+
+// dns_tile with the columns of a thread's group in f32x2 pairs (0, 1) and (2, 3):
+// every stencil operation is one FFMA2 / FADD2 / FMUL2 for two cells, with the
+// same operands and order per cell as dns_tile, so the result is the same bit
+// for bit.  The neighbour pairs that straddle the two halves, (1, 2), (w, 0) and
+// (3, e), are assembled from registers.
+template <int DTY>
+__device__ __forceinline__ void dns_tile2(const float *su, const float *sp, float *eL, float *eR,
+                                          int nf, int x0, int y0, float *__restrict__ un, float ax,
+                                          float kd, float dt)
+{
+    constexpr int DTH = DnsTile<DTY>::DTH;
+    const int g = threadIdx.x % DG, seg = threadIdx.x / DG;
+    const int c0 = 4 + 4 * g;
+    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+    const unsigned wmask = DTH - wbase >= 32 ? 0xffffffffu : ((1u << (DTH - wbase)) - 1u);
+    const bool edgeW = g == 0 || lane == 0, edgeE = g == DG - 1 || lane == 31;
+    const float2 cA = bcast2(dt * ax * ax), cD = bcast2(dt * kd), m4 = bcast2(-4.0f);
+    const int rbase = 2 + DRS * seg;
+    float2 sA[DRS + 2], sB[DRS + 2];             // stage-1 field, columns (0, 1) and (2, 3)
+    {
+        auto ld2 = [&](const float *base, int r, float2 &a, float2 &b) {
+            const float4 v = *reinterpret_cast<const float4 *>(base + r * DLX + c0);
+            a = make_float2(v.x, v.y);
+            b = make_float2(v.z, v.w);
+        };
+        float2 umA, umB, ucA, ucB, pmA, pmB, pcA, pcB;
+        ld2(su, rbase - 2, umA, umB); ld2(su, rbase - 1, ucA, ucB);
+        ld2(sp, rbase - 2, pmA, pmB); ld2(sp, rbase - 1, pcA, pcB);
+#pragma unroll
+        for (int k = 0; k < DRS + 2; ++k) {
+            const int r = rbase - 1 + k;
+            float2 upA, upB, ppA, ppB;
+            ld2(su, r + 1, upA, upB);
+            ld2(sp, r + 1, ppA, ppB);
+            float uw = __shfl_up_sync(wmask, ucB.y, 1), ue = __shfl_down_sync(wmask, ucA.x, 1);
+            float pw = __shfl_up_sync(wmask, pcB.y, 1), pe = __shfl_down_sync(wmask, pcA.x, 1);
+            if (edgeW) { uw = su[r * DLX + c0 - 1]; pw = sp[r * DLX + c0 - 1]; }
+            if (edgeE) { ue = su[r * DLX + c0 + 4]; pe = sp[r * DLX + c0 + 4]; }
+            const float2 uMid = make_float2(ucA.y, ucB.x), pMid = make_float2(pcA.y, pcB.x);
+            const float2 uWA = make_float2(uw, ucA.x), uEB = make_float2(ucB.y, ue);
+            const float2 pWA = make_float2(pw, pcA.x), pEB = make_float2(pcB.y, pe);
+            {   // columns 0, 1: east (1, 2), west (w, 0)
+                float2 t = __fmul2_rn(sub2(pmA, ppA), sub2(uMid, uWA));
+                t = __ffma2_rn(sub2(pMid, pWA), sub2(upA, umA), t);
+                const float2 lap = __ffma2_rn(m4, ucA, __fadd2_rn(__fadd2_rn(uMid, uWA),
+                                                                 __fadd2_rn(upA, umA)));
+                sA[k] = __ffma2_rn(cA, t, __ffma2_rn(cD, lap, ucA));
+            }
+            {   // columns 2, 3: east (3, e), west (1, 2)
+                float2 t = __fmul2_rn(sub2(pmB, ppB), sub2(uEB, uMid));
+                t = __ffma2_rn(sub2(pEB, pMid), sub2(upB, umB), t);
+                const float2 lap = __ffma2_rn(m4, ucB, __fadd2_rn(__fadd2_rn(uEB, uMid),
+                                                                 __fadd2_rn(upB, umB)));
+                sB[k] = __ffma2_rn(cA, t, __ffma2_rn(cD, lap, ucB));
+            }
+            umA = ucA; umB = ucB; ucA = upA; ucB = upB;
+            pmA = pcA; pmB = pcB; pcA = ppA; pcB = ppB;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < DRS; ++k) {
+        eL[(DRS * seg + k) * DG + g] = sA[k + 1].x;
+        eR[(DRS * seg + k) * DG + g] = sB[k + 1].y;
+    }
+    __syncthreads();
+    if (g != 0 && g != DG - 1) {
+        const float4 pm4 = *reinterpret_cast<const float4 *>(sp + (rbase - 1) * DLX + c0);
+        const float4 pc4 = *reinterpret_cast<const float4 *>(sp + rbase * DLX + c0);
+        float2 pmA = make_float2(pm4.x, pm4.y), pmB = make_float2(pm4.z, pm4.w);
+        float2 pcA = make_float2(pc4.x, pc4.y), pcB = make_float2(pc4.z, pc4.w);
+        const int gx = x0 + 4 * (g - 1);
+        const float2 half = bcast2(0.5f);
+#pragma unroll
+        for (int k = 0; k < DRS; ++k) {
+            const int r = rbase + k;
+            const float4 pn4 = *reinterpret_cast<const float4 *>(sp + (r + 1) * DLX + c0);
+            const float2 ppA = make_float2(pn4.x, pn4.y), ppB = make_float2(pn4.z, pn4.w);
+            const float pw = sp[r * DLX + c0 - 1], pe = sp[r * DLX + c0 + 4];
+            const float sw = eR[(DRS * seg + k) * DG + g - 1], se = eL[(DRS * seg + k) * DG + g + 1];
+            const float4 u4 = *reinterpret_cast<const float4 *>(su + r * DLX + c0);
+            const float2 uoA = make_float2(u4.x, u4.y), uoB = make_float2(u4.z, u4.w);
+            const float2 sCA = sA[k + 1], sCB = sB[k + 1];
+            const float2 sMid = make_float2(sCA.y, sCB.x), pMid = make_float2(pcA.y, pcB.x);
+            const float2 sWA = make_float2(sw, sCA.x), sEB = make_float2(sCB.y, se);
+            const float2 pWA = make_float2(pw, pcA.x), pEB = make_float2(pcB.y, pe);
+            float2 oA, oB;
+            {
+                float2 t = __fmul2_rn(sub2(pmA, ppA), sub2(sMid, sWA));
+                t = __ffma2_rn(sub2(pMid, pWA), sub2(sA[k + 2], sA[k]), t);
+                const float2 lap = __ffma2_rn(m4, sCA, __fadd2_rn(__fadd2_rn(sMid, sWA),
+                                                                 __fadd2_rn(sA[k + 2], sA[k])));
+                oA = __fmul2_rn(half, __fadd2_rn(uoA, __ffma2_rn(cA, t, __ffma2_rn(cD, lap, sCA))));
+            }
+            {
+                float2 t = __fmul2_rn(sub2(pmB, ppB), sub2(sEB, sMid));
+                t = __ffma2_rn(sub2(pEB, pMid), sub2(sB[k + 2], sB[k]), t);
+                const float2 lap = __ffma2_rn(m4, sCB, __fadd2_rn(__fadd2_rn(sEB, sMid),
+                                                                 __fadd2_rn(sB[k + 2], sB[k])));
+                oB = __fmul2_rn(half, __fadd2_rn(uoB, __ffma2_rn(cA, t, __ffma2_rn(cD, lap, sCB))));
+            }
+            *reinterpret_cast<float4 *>(un + (long long)(y0 + DRS * seg + k) * nf + gx) =
+                make_float4(oA.x, oA.y, oB.x, oB.y);
+            pmA = pcA; pmB = pcB; pcA = ppA; pcB = ppB;
+        }
+    }
+}
+
 template <int DTY>
 __global__ void __launch_bounds__(DnsTile<DTY>::DTH) k_dns_step(int nf, const float *__restrict__ u,
                                                                const float *__restrict__ psi,
@@ -375,7 +489,7 @@ struct DnsTma {
     static constexpr uint32_t BYTES = 2u * FIELD * 4u;              // one tile's copies
 };
 
-template <int DTY, int NBUF>
+template <int DTY, int NBUF, bool PAIR>
 __global__ void __launch_bounds__(DnsTile<DTY>::DTH)
 k_dns_tma(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtensorMap mp, int nf,
           const float *__restrict__ u, const float *__restrict__ psi, float *__restrict__ un,
@@ -446,7 +560,8 @@ k_dns_tma(const __grid_constant__ CUtensorMap mu, const __grid_constant__ CUtens
             }
             __syncthreads();
         }
-        dns_tile<DTY>(su, sp, eL, eR, nf, x0, y0, un, ax, kd, dt);
+        if constexpr (PAIR) dns_tile2<DTY>(su, sp, eL, eR, nf, x0, y0, un, ax, kd, dt);
+        else dns_tile<DTY>(su, sp, eL, eR, nf, x0, y0, un, ax, kd, dt);
         // every thread's reads and writes of this buffer come before the next copy into it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -657,14 +772,14 @@ static cudaError_t dns_queue(int dev, cudaStream_t s, int **out)
     return cudaSuccess;
 }
 
-template <int DTY, int NBUF>
+template <int DTY, int NBUF, bool PAIR = false>
 static cudaError_t dns_launch_tma(int nf, const CUtensorMap &ma, const CUtensorMap &mp,
                                   const float *a, const float *psi, float *b, float ax, float kd,
                                   float dt, cudaStream_t s)
 {
     using T = DnsTma<DTY, NBUF>;
     constexpr int DTH = DnsTile<DTY>::DTH;
-    const void *fn = reinterpret_cast<const void *>(&k_dns_tma<DTY, NBUF>);
+    const void *fn = reinterpret_cast<const void *>(&k_dns_tma<DTY, NBUF, PAIR>);
     static std::mutex mu;
     static std::vector<int> per_sm;                 // resident CTAs per SM, by device
     int dev = 0, sms = 0;
@@ -691,15 +806,17 @@ static cudaError_t dns_launch_tma(int nf, const CUtensorMap &ma, const CUtensorM
     if (e != cudaSuccess) return e;
     const int which = g_dns_which;                   // launches alternate the two counters
     g_dns_which ^= 1;
-    k_dns_tma<DTY, NBUF><<<grid, DTH, T::SMEM, s>>>(ma, mp, nf, a, psi, b, ax, kd, dt, queue, which);
+    k_dns_tma<DTY, NBUF, PAIR><<<grid, DTH, T::SMEM, s>>>(ma, mp, nf, a, psi, b, ax, kd, dt, queue,
+                                                          which);
     return cudaGetLastError();
 }
 
 // DNS kernel variants: per-tile CTAs staged by cp.async (tile height 64 rows, 2 CTAs/SM,
 // or 32 rows, 4 CTAs/SM), or persistent CTAs fed by tensor copies (32 rows with one or
-// two staging buffers, 64 rows with one).  Picked once per process by timing each on
-// the caller's grid; MLSD_DNS_TY = 64 | 32 | t32 | t32x2 | t64 pins one.
-enum DnsKind { kCp64, kCp32, kTma32, kTma32x2, kTma64, kDnsKinds };
+// two staging buffers, 64 rows with one; 32 rows with the f32x2 pair arithmetic).
+// Picked once per process by timing each on the caller's grid;
+// MLSD_DNS_TY = 64 | 32 | t32 | t32x2 | t64 | t32p pins one.
+enum DnsKind { kCp64, kCp32, kTma32, kTma32x2, kTma64, kTma32p, kDnsKinds };
 static int g_dns_kind = -1;
 
 static cudaError_t dns_launch_kind(int kind, int nf, const CUtensorMap *maps, int ia,
@@ -712,6 +829,8 @@ static cudaError_t dns_launch_kind(int kind, int nf, const CUtensorMap *maps, in
     case kTma32: return dns_launch_tma<32, 1>(nf, maps[ia], maps[2], a, psi, b, ax, kd, dt, s);
     case kTma32x2: return dns_launch_tma<32, 2>(nf, maps[ia], maps[2], a, psi, b, ax, kd, dt, s);
     case kTma64: return dns_launch_tma<64, 1>(nf, maps[ia], maps[2], a, psi, b, ax, kd, dt, s);
+    case kTma32p:
+        return dns_launch_tma<32, 1, true>(nf, maps[ia], maps[2], a, psi, b, ax, kd, dt, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -734,7 +853,7 @@ cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kap
     if (const char *env = std::getenv("MLSD_DNS_TY")) {
         const std::string v(env);
         g_dns_kind = v == "32" ? kCp32 : v == "t32" ? kTma32 : v == "t32x2" ? kTma32x2
-                   : v == "t64" ? kTma64 : kCp64;
+                   : v == "t64" ? kTma64 : v == "t32p" ? kTma32p : kCp64;
     }
     if (!tma && g_dns_kind >= kTma32) g_dns_kind = kCp32;
     if (g_dns_kind < 0 && nsteps > 0) {
@@ -780,7 +899,8 @@ cudaError_t dns_run(int nf, float *u, float *u_tmp, const float *psi, double kap
 const char *dns_kernel_name()
 {
     static const char *names[kDnsKinds] = {"k_dns_step<64>", "k_dns_step<32>", "k_dns_tma<32,1>",
-                                           "k_dns_tma<32,2>", "k_dns_tma<64,1>"};
+                                           "k_dns_tma<32,2>", "k_dns_tma<64,1>",
+                                           "k_dns_tma<32,1,pairs>"};
     return g_dns_kind < 0 ? "" : names[g_dns_kind];
 }
 

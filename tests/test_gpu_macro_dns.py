@@ -111,7 +111,7 @@ def test_dns_parity(mlsd, torch_mod, nf, steps):
 _DNS_REF = {}
 
 
-@pytest.mark.parametrize("kind", ["64", "32", "t32", "t32x2", "t64"])
+@pytest.mark.parametrize("kind", ["64", "32", "t32", "t32x2", "t64", "t32p"])
 @pytest.mark.parametrize("nf,steps", [(256, 40), (2048, 6)])
 def test_dns_kernels_parity(mlsd, torch_mod, monkeypatch, kind, nf, steps):
     # every DNS kernel, forced one at a time: per-tile CTAs staged by cp.async (64- and
