@@ -286,13 +286,14 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
             lv.solve_level(1, Bt, Kp)                   # warm-up
         _, t_plain = timed(lambda: lv.solve_level(1, Bt, Kp))
         Kpn = Kp.cpu().numpy()
+        ok = np.isfinite(Kpn).all(1)                    # a non-finite plain solve has no reference
         rows = []
         in_total = n <= 64
         lv.solve_level_surrogate(sur, 1, Bt, Ks, 1e30)      # warm-up; the ensemble alone
-        err0 = S.k_error(Ks.cpu().numpy(), Kpn)
+        err0 = S.k_error(Ks.cpu().numpy()[ok], Kpn[ok])
         for thr in thresholds:
             nfb, t_sur = timed(lambda: lv.solve_level_surrogate(sur, 1, Bt, Ks, thr))
-            err = S.k_error(Ks.cpu().numpy(), Kpn)
+            err = S.k_error(Ks.cpu().numpy()[ok], Kpn[ok])
             if in_total:
                 errs[thr].append(err)
                 tot_sur[thr] += t_sur
@@ -304,13 +305,14 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
         if in_total:
             tot_plain += t_plain
         levels.append({"octave": f"{lo}<=|k|<{hi}", "patch_n": n, "patches": P,
+                       "plain_nonfinite": int((~ok).sum()),
                        "in_totals": in_total, "plain_seconds": t_plain,
                        "plain_k_tensors_per_s": P / t_plain,
                        "plain_cell_updates_per_s": lv.level_work(1)[0] / t_plain,
                        "ensemble_only": {"median": float(np.median(err0)),
                                          "frac_le_1e-3": float(np.mean(err0 <= 1e-3))},
                        "by_threshold": rows})
-        assert lv.status() == 0
+        assert lv.status() in (0, -5)                   # MLSD_ENONFINITE: counted above
         lv.close()
     overall = []
     P = N * N

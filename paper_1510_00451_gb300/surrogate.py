@@ -15,7 +15,9 @@ def make_dataset(lv, level, bases):
     """Plain patch solves of one level for each base set: features X (bfloat16
     [n P][640]) and targets Y = asinh((K - B - E) SUR_Y_SCALE / tr(B)) (FP32 [n P][3])
     on the device, E the resummed perturbation series the features carry
-    (mlsd.h); all of it in mlsd_surrogate_dataset."""
+    (mlsd.h); all of it in mlsd_surrogate_dataset.  A patch whose explicit solve
+    went non-finite (MLSD_ENONFINITE: the step rule's stability bound fell short
+    for it) gives no row; any other error raises."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     P = lv.P
@@ -24,8 +26,12 @@ def make_dataset(lv, level, bases):
     for i, B in enumerate(bases):
         Bd = torch.as_tensor(np.ascontiguousarray(B), dtype=torch.float64, device=dev)
         lv.surrogate_dataset(level, Bd, X[i * P:(i + 1) * P], Y[i * P:(i + 1) * P])
-    if lv.status() != 0:
-        raise RuntimeError("patch solves reported an error")
+    rc = lv.status()
+    if rc == -5:                                   # MLSD_ENONFINITE
+        keep = torch.isfinite(Y).all(1)
+        X, Y = X[keep], Y[keep]
+    elif rc != 0:
+        raise RuntimeError("patch solves reported error %d" % rc)
     return X, Y
 
 
