@@ -315,7 +315,8 @@ PSI_SCALE, T_SCALE, Y_SCALE = 32.0, 10.0, 300.0
 
 
 def features(psi, B, kappa):
-    """606 surrogate inputs of one patch (psi with its patch mean removed)."""
+    """606 surrogate inputs of one patch (psi with its patch mean removed); a patch
+    above 64 x 64 is described by its samples on the 64 x 64 sub-lattice."""
     psi = _f64(psi); B = _f64(B)
     f = np.zeros(N_FEATURES)
     lib().orc_features(psi.shape[0], _ptr(psi), _ptr(B), float(kappa), _ptr(f))
