@@ -226,7 +226,7 @@ def _octave_level(seed, lo, hi, n, N, kappa):
 
 
 def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3,
-                   thresholds=(5e-4, 1e-3, 2e-3), seed=1510, large=False):
+                   thresholds=(5e-4, 1e-3, 2e-3), seed=1510, large=False, bases=(1, 1, 1)):
     """Surrogate vs plain on three octave levels of the continuous-spectrum flow
     (kappa = 1e-3, N x N patches per level, full relaxation window): the 5th
     octave (16 <= |k| < 32, 64^2 patches), the 6th and the 7th (32^2).  Training
@@ -244,7 +244,7 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
     dev = torch.device("cuda", _local_rank())
     kappa = 1e-3
     P = N * N
-    octs = [(lo, hi, n, N, 1, N) for (lo, hi, n) in SUR_OCTAVES]
+    octs = [(lo, hi, n, N, nb, N) for (lo, hi, n), nb in zip(SUR_OCTAVES, bases)]
     if large:
         octs = octs + [SUR_OCTAVE_128]
     t0 = time.perf_counter()
@@ -340,7 +340,8 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
              if large else "")
     return {"workload": f"continuous-spectrum octaves 16-32 (64^2), 32-64, 64-128 (32^2), {P} "
                         "patches each, kappa=1e-3, full window; trained on one flow "
-                        f"realization ({len(SUR_OCTAVES) * P} plain solves), tested on another"
+                        f"realization ({sum(bases) * P} plain solves, {list(bases)} base sets "
+                        "per level), tested on another"
                         + extra,
             "members": members, "hidden": hidden, "epochs": epochs, "batch": batch,
             "final_loss": losses, "levels": levels, "overall": overall,

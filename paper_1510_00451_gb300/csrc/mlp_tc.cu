@@ -277,10 +277,11 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(TcArgs a)
 // layers while one thread issues the MMAs; the epilogue writes activations in the
 // same layout (conflict-free 16-byte stores) for the next layer's A operand.
 constexpr int RING = 3;
-// 8 warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (the lane quarter a warp may
-// access) and columns of half w / 4 of the layer's outputs, so the bias + GELU
-// epilogue between layers runs on twice the warps of the 128 rows
-constexpr int TMA_THREADS = 256;
+// 16 warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (the lane quarter a warp may
+// access) and the 32-column chunks w / 4, w / 4 + 4, ... of the layer's outputs, so the
+// bias + GELU epilogue between layers runs on four times the warps of the 128 rows
+// and hides more of its latency
+constexpr int TMA_THREADS = 512;
 constexpr int A_BYTES = TM * KC * 2;           // 16 KB
 constexpr int B_BYTES = HMAX * KC * 2;         // 32 KB
 constexpr int SLOT = A_BYTES + B_BYTES;
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_mlp_tma(const __grid_constan
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const int lq = warp & 3, cgrp = warp >> 2;           // lane quarter, column half
+    const int lq = warp & 3, cgrp = warp >> 2;           // lane quarter, column group
     const uint32_t taddr_row = tmem + ((uint32_t)(lq * 32) << 16);
 
     auto issue_load = [&](int q) {
@@ -422,8 +423,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1) k_mlp_tma(const __grid_constan
         const int r = lq * 32 + lane;
         if (l < 3) {
             const float *bias = sbias[l];                // staged at entry: broadcast reads
-            const int cw = h / (TMA_THREADS / 128);          // columns per half (a multiple of 32)
-            for (int c0 = cgrp * cw; c0 < (cgrp + 1) * cw; c0 += 32) {
+            // 32-column chunks dealt round-robin to the column groups
+            for (int c0 = 32 * cgrp; c0 < h; c0 += 32 * (TMA_THREADS / 128)) {
                 float v[32];
                 tmem_ld32(taddr_row + (uint32_t)c0, v);
                 __align__(16) __nv_bfloat16 o[32];
