@@ -753,22 +753,25 @@ static cudaError_t dns_launch(int nf, const float *a, const float *psi, float *b
 }
 
 // the two tile counters of the persistent kernels, per device (zeroed once), and
-// which one the next launch takes (every persistent launch, of any tile shape,
-// alternates them: each launch zeroes the other for its successor on the stream)
-static int g_dns_which = 0;
+// which one the next launch on that device takes (every persistent launch, of any
+// tile shape, alternates them: each launch zeroes the other for its successor)
+static std::vector<int> g_dns_which;
 // the two tile counters of the persistent kernels, per device (zeroed once)
-static cudaError_t dns_queue(int dev, cudaStream_t s, int **out)
+static cudaError_t dns_queue(int dev, cudaStream_t s, int **out, int *which)
 {
     static std::mutex mu;
     static std::vector<int *> q;
     std::lock_guard<std::mutex> lock(mu);
     if ((int)q.size() <= dev) q.resize(dev + 1, nullptr);
+    if ((int)g_dns_which.size() <= dev) g_dns_which.resize(dev + 1, 0);
     if (!q[dev]) {
         cudaError_t e = cudaMalloc((void **)&q[dev], 2 * sizeof(int));
         if (e == cudaSuccess) e = cudaMemsetAsync(q[dev], 0, 2 * sizeof(int), s);
         if (e != cudaSuccess) { q[dev] = nullptr; return e; }
     }
     *out = q[dev];
+    *which = g_dns_which[dev];
+    g_dns_which[dev] ^= 1;
     return cudaSuccess;
 }
 
@@ -801,11 +804,9 @@ static cudaError_t dns_launch_tma(int nf, const CUtensorMap &ma, const CUtensorM
     }
     const long long ntiles = (long long)(nf / DTX) * (nf / DTY);
     const int grid = (int)std::min<long long>(ntiles, (long long)res * sms);
-    int *queue = nullptr;
-    e = dns_queue(dev, s, &queue);
+    int *queue = nullptr, which = 0;                 // launches alternate the two counters
+    e = dns_queue(dev, s, &queue, &which);
     if (e != cudaSuccess) return e;
-    const int which = g_dns_which;                   // launches alternate the two counters
-    g_dns_which ^= 1;
     k_dns_tma<DTY, NBUF, PAIR><<<grid, DTH, T::SMEM, s>>>(ma, mp, nf, a, psi, b, ax, kd, dt, queue,
                                                           which);
     return cudaGetLastError();
