@@ -335,7 +335,13 @@ int mlsd_surrogate_symmetry(const void *X_dev, const float *Y_dev, int64_t n_row
  * stream seeded from `seed` and the member index; the rows are gathered on
  * the device); the learning rate decays geometrically from lr to lr_final over
  * the run.  losses_host (or NULL) receives each member's mean batch loss over
- * the last epoch.  Blocks at the end of each member.                        */
+ * the last epoch.  Blocks at the end of each member.
+ * Arithmetic of a step (and of mlsd_surrogate_grad / _train_step): bfloat16
+ * inputs, weights and hidden activations, FP32 accumulation, the hidden
+ * layers' pre-activation gradients dZ rounded to bfloat16.  The hidden layers'
+ * contractions run on the tensor cores (tcgen05, operands by tensor copies)
+ * where the handle could encode tensor maps at creation; MLSD_TRAIN_CUDA set
+ * at creation keeps every GEMM on the CUDA cores.                           */
 int mlsd_surrogate_train(mlsd_surrogate *s, const void *X_dev, const float *Y_dev, int64_t n_rows,
                          int epochs, int batch, float lr, float lr_final, uint64_t seed,
                          int augment, double *losses_host, void *cuda_stream);

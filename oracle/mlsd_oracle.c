@@ -1155,7 +1155,9 @@ static double gelu_d(double z)
 /* exact-erf GELU after the first three.  Parameters (row-major, out x in):    */
 /*   W1[h][d0] b1[h] W2[h][h] b2[h] W3[h][h] b3[h] W4[3][h] b4[3]              */
 /* in one array.  With bf16 != 0 the inputs, weights and hidden activations    */
-/* are rounded to bfloat16 where the GPU stores them in bfloat16.              */
+/* are rounded to bfloat16 where the GPU stores them in bfloat16, and so are   */
+/* the gradients dZ of the hidden layers' pre-activations (the operands of     */
+/* the backward contractions); the output layer's dZ stays unrounded.         */
 /* Forward: out[M][3].  With Y != NULL also the loss mean((out - Y)^2) over    */
 /* the M x 3 entries and its gradient g (same layout as the parameters).       */
 double orc_mlp(int M, int d0, int h, const double *X, const double *params, int bf16,
@@ -1213,7 +1215,8 @@ double orc_mlp(int M, int d0, int h, const double *X, const double *params, int 
                     for (int k = 0; k < din; ++k) {
                         double s = 0.0;
                         for (int j = 0; j < dout; ++j) s += dZ[(long)m * dout + j] * W[(long)j * din + k];
-                        dZn[(long)m * din + k] = s * gelu_d(Z[l][(long)m * din + k]);
+                        const double dz = s * gelu_d(Z[l][(long)m * din + k]);
+                        dZn[(long)m * din + k] = bf16 ? bf16r(dz) : dz;
                     }
                 double *t = dZ; dZ = dZn; dZn = t;
             }

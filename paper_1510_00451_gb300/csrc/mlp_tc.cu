@@ -498,6 +498,25 @@ bool encode_view(CUtensorMap *m, const void *base, long long rows, int K, int bo
 
 }  // namespace
 
+// 3-D core-matrix view of a bfloat16 matrix of `rows` rows and K columns, rows `ld`
+// elements apart (ld a multiple of 8): (8 elements) x (rows) x (ceil(K / 8) groups),
+// box {8, box_rows, 8}; a box lands as the no-swizzle K-major core-matrix layout.
+// Columns K .. 8 ceil(K / 8) - 1 are read from the row's padding.
+bool encode_rows_bf16(void *map, const void *base, long long rows, long long K, long long ld,
+                      int box_rows)
+{
+    EncodeTiled enc = encoder();
+    if (!enc || ld % 8 || ld < 8 * ((K + 7) / 8)) return false;
+    cuuint64_t dims[3] = {8, (cuuint64_t)rows, (cuuint64_t)((K + 7) / 8)};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, 16};
+    cuuint32_t box[3] = {8, (cuuint32_t)box_rows, 8};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+               const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // 2-D view of a row-major [height][width] FP32 array with a box of box_h rows of
 // box_w elements (zero fill outside the array)
 bool encode_f32_2d(void *map, const float *base, long long width, long long height, int box_w,

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 #include <vector>
 
@@ -121,6 +122,16 @@ cudaError_t launch_periodize(const float *band, long long Nl, int n, int n_macro
 cudaError_t launch_wait_check_nbr(int *status, cudaStream_t s);
 cudaError_t launch_wait_check_mbar(int *status, cudaStream_t s);
 cudaError_t launch_wait_check_tile(int *status, cudaStream_t s);
+// tensor-core GEMM D = A B^T of the training step (gemm_tc.cu): mode 0 forward epilogue,
+// 1 backward epilogue, 2 partial sums over K slices
+cudaError_t gemm_tc(int mode, int M, int N, int K, const void *A, long long lda, const void *B,
+                    long long ldb, const float *bias, float *Z, const float *Zprev, void *out,
+                    void *outT, int ldT, float *part, int splits, int *slices, int *status,
+                    cudaStream_t s);
+int gemm_tc_splits(int M, int N, int K, int sms);
+// 3-D core-matrix tensor map (CUtensorMap) of a bfloat16 matrix [rows][K], rows ld apart
+bool encode_rows_bf16(void *map, const void *base, long long rows, long long K, long long ld,
+                      int box_rows);
 // 2-D FP32 tensor map (CUtensorMap, 128 bytes) of a row-major [height][width] array
 bool encode_f32_2d(void *map, const float *base, long long width, long long height, int box_w,
                    int box_h);
@@ -165,6 +176,19 @@ cudaError_t sur_forward(int h, int M, const void *X, const float *wf, const void
 cudaError_t sur_grad(int h, int M, const void *X, const float *Y, const float *wf, const void *wb,
                      float *Z[4], void *Aact[3], float *dA, float *dB, float *g, double *part,
                      double *loss_dev, float *ws, long long ws_n, cudaStream_t s);
+// buffers of the tensor-core training step (sur_grad_tc); ldT >= max_rows rounded up to 8
+struct SurTc {
+    int max_rows = 0, ldT = 0;
+    __nv_bfloat16 *XT = nullptr;          // [640][ldT]
+    __nv_bfloat16 *AT[3] = {};            // [h][ldT] transposed activations
+    __nv_bfloat16 *WT[2] = {};            // [h][h] transposed W_1, W_2
+    __nv_bfloat16 *dZ[2] = {};            // [max_rows][h] bfloat16 gradients
+    __nv_bfloat16 *dZT[2] = {};           // [h][ldT]
+};
+cudaError_t sur_grad_tc(int h, int M, const void *X, const float *Y, const float *wf,
+                        const void *wb, float *Z[4], void *Aact[3], float *dA, float *dB,
+                        float *g, double *part, double *loss_dev, float *ws, long long ws_n,
+                        const SurTc &tc, int *status, cudaStream_t s);
 cudaError_t sur_adam(long long n, float *w, const float *g, float *m, float *v, float lr, int t,
                      void *wb, cudaStream_t s);
 cudaError_t sur_to_bf16(long long n, const float *w, void *wb, cudaStream_t s);

@@ -1121,6 +1121,8 @@ struct mlsd_surrogate {
     int engine = MLSD_SUR_CUDA;
     bool tma = false;                     // TMA-fed tensor-core kernel available
     std::vector<unsigned char> maps;      // its weight tensor maps
+    bool train_tc = false;                // training contractions on the tensor cores
+    SurTc tc;                             // their buffers
     std::vector<void *> allocs;
 };
 
@@ -1131,6 +1133,18 @@ int sur_alloc(mlsd_surrogate *s, void **p, size_t bytes)
     CK(cudaMalloc(p, bytes));
     s->allocs.push_back(*p);
     return MLSD_OK;
+}
+
+// gradient of one member on M rows: the hidden layers' contractions on the tensor
+// cores when the handle has their buffers, else every GEMM on the CUDA cores
+cudaError_t grad_of(mlsd_surrogate *s, int member, int M, const void *X, const float *Y, float *g,
+                    double *part, double *loss, float *ws, long long ws_n, cudaStream_t st)
+{
+    if (s->train_tc && M <= s->tc.max_rows)
+        return sur_grad_tc(s->h, M, X, Y, s->w[member], s->wb[member], s->Z, s->A, s->dA, s->dB,
+                           g, part, loss, ws, ws_n, s->tc, s->status, st);
+    return sur_grad(s->h, M, X, Y, s->w[member], s->wb[member], s->Z, s->A, s->dA, s->dB, g, part,
+                    loss, ws, ws_n, st);
 }
 }  // namespace
 
@@ -1193,6 +1207,21 @@ int mlsd_surrogate_create(int members, int hidden, int max_batch, mlsd_surrogate
         s->maps.assign(mlp_tma_maps_bytes(), 0);
         s->tma = mlp_tma_prepare(hidden, members, s->wb.data(), s->maps.data());
     }
+    if (!rc && s->tma && !std::getenv("MLSD_TRAIN_CUDA")) {
+        // buffers of the tensor-core training step: transposed inputs, activations,
+        // weights and gradients (rows of the transposes padded to a multiple of 8)
+        SurTc &t = s->tc;
+        t.max_rows = max_batch;
+        t.ldT = (max_batch + 7) / 8 * 8;
+        const size_t T = (size_t)t.ldT;
+        void *p = nullptr;
+        if (!rc) { rc = sur_alloc(s, &p, (size_t)MLSD_SUR_IN * T * 2); t.XT = (__nv_bfloat16 *)p; }
+        for (int l = 0; l < 3 && !rc; ++l) { rc = sur_alloc(s, &p, H * T * 2); t.AT[l] = (__nv_bfloat16 *)p; }
+        for (int l = 0; l < 2 && !rc; ++l) { rc = sur_alloc(s, &p, H * H * 2); t.WT[l] = (__nv_bfloat16 *)p; }
+        for (int l = 0; l < 2 && !rc; ++l) { rc = sur_alloc(s, &p, M * H * 2); t.dZ[l] = (__nv_bfloat16 *)p; }
+        for (int l = 0; l < 2 && !rc; ++l) { rc = sur_alloc(s, &p, H * T * 2); t.dZT[l] = (__nv_bfloat16 *)p; }
+        s->train_tc = !rc;
+    }
     if (rc) { mlsd_surrogate_free(s); return rc; }
     *out = s;
     return MLSD_OK;
@@ -1238,7 +1267,7 @@ int mlsd_surrogate_grad(mlsd_surrogate *s, int member, const void *X_dev, const 
     if (!s || member < 0 || member >= s->members || !X_dev || !Y_dev || M < 1 || M > s->max_batch)
         return MLSD_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    CK(sur_grad(s->h, M, X_dev, Y_dev, s->w[member], s->wb[member], s->Z, s->A, s->dA, s->dB,
+    CK(grad_of(s, member, M, X_dev, Y_dev,
                 s->g[member], s->part, s->loss, s->ws, s->ws_n, st));
     if (grad_dev)
         CK(cudaMemcpyAsync(grad_dev, s->g[member], (size_t)s->np * 4, cudaMemcpyDeviceToDevice, st));
@@ -1257,7 +1286,7 @@ int mlsd_surrogate_train_step(mlsd_surrogate *s, int member, const void *X_dev,
         M > s->max_batch || !(lr > 0))
         return MLSD_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    CK(sur_grad(s->h, M, X_dev, Y_dev, s->w[member], s->wb[member], s->Z, s->A, s->dA, s->dB,
+    CK(grad_of(s, member, M, X_dev, Y_dev,
                 s->g[member], s->part, s->loss, s->ws, s->ws_n, st));
     s->t[member] += 1;
     CK(sur_adam(s->np, s->w[member], s->g[member], s->m[member], s->v[member], lr, s->t[member],
@@ -1350,7 +1379,7 @@ int mlsd_surrogate_train(mlsd_surrogate *s, const void *X_dev, const float *Y_de
                 const float r = lr * (float)std::pow((double)lr_final / lr, (double)t / (double)std::max(1LL, total - 1));
                 e = sur_gather(batch, idx + q * batch, X_dev, Y_dev, Xb, Yb, augment ? 1 : 0, st);
                 if (e == cudaSuccess)
-                    e = sur_grad(s->h, batch, Xb, Yb, s->w[m], s->wb[m], s->Z, s->A, s->dA, s->dB,
+                    e = grad_of(s, m, batch, Xb, Yb,
                                  s->g[m], s->part, s->loss, s->ws, s->ws_n, st);
                 s->t[m] += 1;
                 if (e == cudaSuccess)

@@ -443,7 +443,9 @@ constexpr int SPLIT_MAX = 16;   // most k splits of one GEMM
 
 // Epilogue of the GEMM and of its split-k reduction, applied to output (i, j) in order:
 // + bias[j]; + the old C(i, j) (accumulate); times gelu'(dgelu(i, j)) (the backward GELU,
-// dgelu shares C's row stride); store C; act(i, j) = gelu(C(i, j)) in bfloat16.
+// dgelu shares C's row stride), rounded to a bfloat16 value (the hidden layers' dZ are
+// bfloat16 operands of the backward contractions); store C; act(i, j) = gelu(C(i, j)) in
+// bfloat16.
 struct Epi {
     const float *bias = nullptr;
     int accumulate = 0;
@@ -457,7 +459,7 @@ __device__ __forceinline__ void epilogue(const Epi &e, float v, int gi, int gj, 
 {
     if (e.bias) v += e.bias[gj];
     if (e.accumulate) v += C[gi * scm + gj];
-    if (e.dgelu) v *= gelu_d(e.dgelu[gi * scm + gj]);
+    if (e.dgelu) v = __bfloat162float(__float2bfloat16_rn(v * gelu_d(e.dgelu[gi * scm + gj])));
     C[gi * scm + gj] = v;
     if (e.act) e.act[gi * e.sactm + gj] = __float2bfloat16_rn(gelu_f(v));
 }
@@ -867,6 +869,157 @@ __global__ void k_merge_fallback(int n, const int *n_dev, const int *idx, const 
     K[3 * p + 2] = b[2] + s[3];
 }
 
+// Transpose of a row-major bfloat16 [rows][cols] (row stride cols) into [cols][ldT]:
+// dst[c][r] = src[r][c] for r < rows, zero for rows <= r < ldT.  32 x 32 tiles
+// through shared memory (reads and writes along rows).
+__global__ void k_transpose_bf16(int rows, int cols, const __nv_bfloat16 *src, __nv_bfloat16 *dst,
+                                 int ldT)
+{
+    __shared__ __nv_bfloat16 t[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        t[k][threadIdx.x] = (r < rows && c < cols) ? src[(long long)r * cols + c]
+                                                   : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (c < cols && r < ldT) dst[(long long)c * ldT + r] = t[threadIdx.x][k];
+    }
+}
+
+// Output layer of the tensor-core training step (3 outputs: one warp per row).
+// Z4[m][j] = b4[j] + sum_k A3[m][k] W4[j][k]
+__global__ void k_out_fwd(int M, int h, const __nv_bfloat16 *A3, const __nv_bfloat16 *W4,
+                          const float *b4, float *Z4)
+{
+    const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (m >= M) return;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    for (int k = lane; k < h; k += 32) {
+        const float x = __bfloat162float(A3[(long long)m * h + k]);
+        s0 = fmaf(x, __bfloat162float(W4[k]), s0);
+        s1 = fmaf(x, __bfloat162float(W4[h + k]), s1);
+        s2 = fmaf(x, __bfloat162float(W4[2 * h + k]), s2);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+        Z4[3 * m] = b4[0] + s0;
+        Z4[3 * m + 1] = b4[1] + s1;
+        Z4[3 * m + 2] = b4[2] + s2;
+    }
+}
+
+// Partial sums of dW4[j][k] = sum_m dZ4[m][j] A3[m][k] and db4[j] = sum_m dZ4[m][j] over
+// the row chunk blockIdx.y (rows y*chunk .. +chunk-1): a block of 32 columns x 8 row groups
+// (rows g, g + 8, ...), reduced over the groups in order, into part[y][j][k] and (the
+// blocks of the first column tile) bpart[y][j]; k_split_reduce adds the chunks in order
+__global__ void k_out_bwd_w(int M, int h, int chunk, const float *dZ4, const __nv_bfloat16 *A3,
+                            float *part, float *bpart)
+{
+    __shared__ float red[8][4][33];
+    const int c = threadIdx.x & 31, g = threadIdx.x >> 5, k = blockIdx.x * 32 + c;
+    const int mb = blockIdx.y * chunk, me = min(M, mb + chunk);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, b = 0.f;
+    for (int m = mb + g; m < me; m += 8) {
+        const float x = k < h ? __bfloat162float(A3[(long long)m * h + k]) : 0.f;
+        const float d0 = dZ4[3 * m], d1 = dZ4[3 * m + 1], d2 = dZ4[3 * m + 2];
+        s0 = fmaf(d0, x, s0);
+        s1 = fmaf(d1, x, s1);
+        s2 = fmaf(d2, x, s2);
+        if (c < 3) b += c == 0 ? d0 : (c == 1 ? d1 : d2);
+    }
+    red[g][0][c] = s0; red[g][1][c] = s1; red[g][2][c] = s2; red[g][3][c] = b;
+    __syncthreads();
+    if (g < 3 && k < h) {
+        float t = 0.f;
+        for (int q = 0; q < 8; ++q) t += red[q][g][c];
+        part[((long long)blockIdx.y * 3 + g) * h + k] = t;
+    }
+    if (blockIdx.x == 0 && g == 3 && c < 3) {
+        float t = 0.f;
+        for (int q = 0; q < 8; ++q) t += red[q][3][c];
+        bpart[blockIdx.y * 3 + c] = t;
+    }
+}
+
+// dZ3 = bf16((dZ4 W4) gelu'(Z3)) into bfloat16 [M][h] and its transpose [h][ldT] (zero
+// for M <= m < ldT): 32 x 32 tiles through shared memory
+__global__ void k_out_bwd_x(int M, int h, const float *dZ4, const __nv_bfloat16 *W4, const float *Z3,
+                            __nv_bfloat16 *dZ, __nv_bfloat16 *dZT, int ldT)
+{
+    __shared__ __nv_bfloat16 t[32][33];
+    const int m0 = blockIdx.y * 32, k0 = blockIdx.x * 32, k = k0 + threadIdx.x;
+    float w0 = 0.f, w1 = 0.f, w2 = 0.f;
+    if (k < h) {
+        w0 = __bfloat162float(W4[k]); w1 = __bfloat162float(W4[h + k]); w2 = __bfloat162float(W4[2 * h + k]);
+    }
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        const int m = m0 + q;
+        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+        if (m < M && k < h) {
+            float d = dZ4[3 * m] * w0;
+            d = fmaf(dZ4[3 * m + 1], w1, d);
+            d = fmaf(dZ4[3 * m + 2], w2, d);
+            v = __float2bfloat16_rn(d * gelu_d(Z3[(long long)m * h + k]));
+            dZ[(long long)m * h + k] = v;
+        }
+        t[q][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+        const int kk = k0 + q, m = m0 + threadIdx.x;
+        if (kk < h && m < ldT) dZT[(long long)kk * ldT + m] = t[threadIdx.x][q];
+    }
+}
+
+// FP32 [M][N] (bfloat16-valued) to bfloat16 [M][N] and its transpose [N][ldT] (zero for
+// M <= m < ldT)
+__global__ void k_to_bf16_t(int M, int N, const float *src, __nv_bfloat16 *dst, __nv_bfloat16 *dstT,
+                            int ldT)
+{
+    __shared__ __nv_bfloat16 t[32][33];
+    const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int m = m0 + k, n = n0 + threadIdx.x;
+        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+        if (m < M && n < N) {
+            v = __float2bfloat16_rn(src[(long long)m * N + n]);
+            dst[(long long)m * N + n] = v;
+        }
+        t[k][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int n = n0 + k, m = m0 + threadIdx.x;
+        if (n < N && m < ldT) dstT[(long long)n * ldT + m] = t[threadIdx.x][k];
+    }
+}
+
+// out[r] = sum over k < K of src[r][k] (bfloat16, row stride ld a multiple of 8, zero
+// padding up to ld), one warp per row, FP32 in a fixed order (each lane sums 16-byte
+// vectors 8 k apart, then the warp tree)
+__global__ void k_rowsum_bf16(int rows, int K, const __nv_bfloat16 *src, int ld, float *out)
+{
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    float acc = 0.f;
+    const __nv_bfloat16 *row = src + (long long)r * ld;
+    for (int k = 8 * lane; k < K; k += 256) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(row + k);
+        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&q);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc += __bfloat162float(e[i]);   // zeros past K
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[r] = acc;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1009,6 +1162,88 @@ cudaError_t sur_grad(int h, int M, const void *X, const float *Y, const float *w
         float *t = dZ; dZ = dN; dN = t;
     }
     return cudaGetLastError();
+}
+
+// The gradient of one member with the hidden layers' contractions on the tensor cores
+// (gemm_tc): forward Z_l = A_{l-1} W_l^T + b_l with bfloat16 act_l and its transpose,
+// l = 0..2; the output layer, the loss and the output layer's gradients as in sur_grad
+// (CUDA cores); then for l = 2, 1, 0: dW_l = dZ_l^T A_{l-1} (K = the batch, split over
+// CTAs, partials summed in a fixed order), db_l = the row sums of dZ_l^T, and
+// dZ_{l-1} = bf16((dZ_l W_l) gelu'(Z_{l-1})) and its transpose.  dZ of the hidden
+// layers is a bfloat16 operand throughout (the oracle's emulation rounds it the same).
+cudaError_t sur_grad_tc(int h, int M, const void *X, const float *Y, const float *wf,
+                        const void *wb_, float *Z[4], void *Aact[3], float *dA, float *dB_,
+                        float *g, double *part, double *loss_dev, float *ws, long long ws_n,
+                        const SurTc &tc, int *status, cudaStream_t s)
+{
+    const Layers L = layers(h);
+    const __nv_bfloat16 *wb = static_cast<const __nv_bfloat16 *>(wb_);
+    const int ldT = tc.ldT;
+    if (M > tc.max_rows || ldT < ((M + 7) / 8) * 8) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    const dim3 tb(32, 8);
+    auto tgrid = [](int rows, int cols) { return dim3((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)); };
+    // W_1^T, W_2^T for the data gradients
+    count_launches(2);
+    for (int l = 1; l <= 2; ++l)
+        k_transpose_bf16<<<tgrid(h, h), tb, 0, s>>>(h, h, wb + L.w[l], tc.WT[l - 1], h);
+    e = cudaGetLastError();
+    // forward, hidden layers on the tensor cores
+    const __nv_bfloat16 *in = static_cast<const __nv_bfloat16 *>(X);
+    for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
+        e = gemm_tc(0, M, h, L.din[l], in, L.din[l], wb + L.w[l], L.din[l], wf + L.b[l], Z[l],
+                    nullptr, Aact[l], tc.AT[l], ldT, nullptr, 1, nullptr, status, s);
+        in = static_cast<const __nv_bfloat16 *>(Aact[l]);
+    }
+    if (e != cudaSuccess) return e;
+    // output layer (3 outputs) and its gradients, on the CUDA cores: Z4, the loss and
+    // dZ4, dW4 and db4, and dZ3 = bf16((dZ4 W4) gelu'(Z3)) with its transpose
+    const int nb = (3 * M + 255) / 256;
+    count_launches(6);
+    k_out_fwd<<<(unsigned)((M + 7) / 8), 256, 0, s>>>(M, h, in, wb + L.w[3], wf + L.b[3], Z[3]);
+    k_mse<<<nb, 256, 0, s>>>(M, Z[3], Y, dA, part);
+    k_sum_parts<<<1, 32, 0, s>>>(nb, part, 1.0 / (3.0 * M), loss_dev);
+    {
+        const int S = std::min(16, (M + 127) / 128), chunk = (M + S - 1) / S;
+        float *bpart = ws + (long long)S * 3 * h;
+        k_out_bwd_w<<<dim3((unsigned)((h + 31) / 32), (unsigned)S), 256, 0, s>>>(M, h, chunk, dA, in,
+                                                                              ws, bpart);
+        count_launches(1);
+        k_split_reduce<<<(unsigned)((3 * h + 3 + 255) / 256), 256, 0, s>>>(3, h, S, ws, g + L.w[3], h,
+                                                                          Epi{}, bpart, g + L.b[3]);
+    }
+    k_out_bwd_x<<<tgrid(M, h), tb, 0, s>>>(M, h, dA, wb + L.w[3], Z[2], tc.dZ[0], tc.dZT[0], ldT);
+    k_transpose_bf16<<<tgrid(M, MLSD_SUR_IN), tb, 0, s>>>(M, MLSD_SUR_IN, static_cast<const __nv_bfloat16 *>(X),
+                                                         tc.XT, ldT);
+    e = cudaGetLastError();
+    (void)dB_;
+    int cur = 0;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int l = 2; l >= 0 && e == cudaSuccess; --l) {
+        const int din = L.din[l];
+        const void *Bt = l > 0 ? static_cast<const void *>(tc.AT[l - 1]) : static_cast<const void *>(tc.XT);
+        // dW_l[j][k] = sum_m dZ[m][j] A_{l-1}[m][k]: A = dZ^T [h][M], B = A_{l-1}^T [din][M]
+        int splits = gemm_tc_splits(h, din, M, sms);
+        while (splits > 1 && (long long)splits * h * din > ws_n) --splits;
+        int used = 1;
+        e = gemm_tc(2, h, din, M, tc.dZT[cur], ldT, Bt, ldT, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, ldT, ws, splits, &used, status, s);
+        if (e != cudaSuccess) break;
+        const long long n = (long long)h * din;
+        count_launches(2);
+        k_split_reduce<<<(unsigned)std::min<long long>((n + 255) / 256, 8LL * sms), 256, 0, s>>>(
+            h, din, used, ws, g + L.w[l], din, Epi{}, nullptr, nullptr);
+        k_rowsum_bf16<<<(unsigned)((h + 7) / 8), 256, 0, s>>>(h, M, tc.dZT[cur], ldT, g + L.b[l]);
+        e = cudaGetLastError();
+        if (e != cudaSuccess || l == 0) break;
+        // dZ_{l-1} = bf16((dZ_l W_l) gelu'(Z_{l-1})): A = dZ_l [M][h], B = W_l^T [din][h]
+        e = gemm_tc(1, M, din, h, tc.dZ[cur], h, tc.WT[l - 1], h, nullptr, nullptr, Z[l - 1],
+                    tc.dZ[cur ^ 1], tc.dZT[cur ^ 1], ldT, nullptr, 1, nullptr, status, s);
+        cur ^= 1;
+    }
+    return e;
 }
 
 cudaError_t sur_adam(long long n, float *w, const float *g, float *m, float *v, float lr, int t,
