@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gemm_tc(const __grid_constant
                     for (int i = 0; i < 32; i += 4) {
                         const float4 b = *reinterpret_cast<const float4 *>(a.bias + nb + i);
                         const float4 z = make_float4(v[i] + b.x, v[i + 1] + b.y, v[i + 2] + b.z, v[i + 3] + b.w);
-                        *reinterpret_cast<float4 *>(a.Z + e0 + i) = z;
+                        if (a.Z) *reinterpret_cast<float4 *>(a.Z + e0 + i) = z;
                         o[i] = __float2bfloat16_rn(gt_gelu(z.x));
                         o[i + 1] = __float2bfloat16_rn(gt_gelu(z.y));
                         o[i + 2] = __float2bfloat16_rn(gt_gelu(z.z));
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gemm_tc(const __grid_constant
 #pragma unroll
                 for (int i = 0; i < 32; ++i) o[i] = __float2bfloat16_rn(0.f);
             }
-            if (m < a.ldT) {
+            if (a.outT && m < a.ldT) {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) a.outT[(long long)(nb + i) * a.ldT + m] = o[i];
             }
@@ -314,7 +314,8 @@ cudaError_t launch_gt(const GtArgs &a, int splits, cudaStream_t s)
 // elements, lda apart; B: N rows of K, ldb apart (lda, ldb multiples of 8, both at
 // least K rounded up to 8, their padding zero).  mode 0 forward (bias, Z, act,
 // actT), 1 backward (Zprev, dZ, dZT), 2 partial sums of up to `splits` K slices
-// into part [slices][M][N], the number of slices used returned in *slices.
+// into part [slices][M][N], the number of slices used returned in *slices.  In the
+// forward mode Z and the transpose may be NULL.
 // BN = 128, or 64 where 128-column tiles would fill less than a third of the SMs
 // (256 with MLSD_GEMM_BN=256 where N is a multiple of 256).
 cudaError_t gemm_tc(int mode, int M, int N, int K, const void *A, long long lda, const void *B,
