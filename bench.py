@@ -251,8 +251,9 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
     Xs, Ys = [], []
     for i, (lo, hi, n, Ntr, nb, _) in enumerate(octs):
         lv = _octave_level(SUR_TRAIN_FLOW, lo, hi, n, Ntr, kappa)
-        bases = [inputs.random_bases(Ntr * Ntr, kappa, seed + 100 + i + 10 * j) for j in range(nb)]
-        X, Y = S.make_dataset(lv, 1, bases)
+        base_sets = [inputs.random_bases(Ntr * Ntr, kappa, seed + 100 + i + 10 * j)
+                     for j in range(nb)]
+        X, Y = S.make_dataset(lv, 1, base_sets)
         Xs.append(X); Ys.append(Y)
         lv.close()
     X, Y = torch.cat(Xs), torch.cat(Ys)
