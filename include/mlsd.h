@@ -125,6 +125,9 @@ typedef struct {
                                   that the copies land while the others are computed */
     int n_classes;             /* patch sizes in the level; n, Nl, h and the tile fields describe
                                   the class with the most work; all classes run concurrently */
+    int coef_tmem;             /* 1: the kernel keeps the two per-cell stencil coefficients in
+                                  the SM's tensor memory instead of registers (two registers per
+                                  cell instead of four, so a field needs half the SMs) */
 } mlsd_level_desc;
 
 typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and scratch */
@@ -135,18 +138,21 @@ typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and 
  * Set-up also picks the thread-block tiling of the patch kernel per patch
  * size: every compiled candidate is timed on a sample of the level's patches
  * (a short fixed window) and the fastest is kept for the process; the
- * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][c<cluster>][p][s|n|b|d|r]
+ * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][c<cluster>][p][s|n|b|d|r][t]
  * forces one where it exists for the level's patch size (p: the packed kernel
  * that advances both fields of a patch in f32x2 pairs; c: CTAs per patch field;
  * s: split-phase stage barriers; n: neighbour signalling between the slabs of
  * a cluster instead of a cluster-wide barrier; b: the slab edge rows moved by
  * bulk copies that complete on the receiver's mbarrier; d: as b, with the rows
  * that need a neighbouring slab's row computed after the others; r: rows r and r + by/2
- * of a thread's block in f32x2 pairs, one FFMA2/FADD2 per two cells).  MLSD_TUNE_LOG set to
+ * of a thread's block in f32x2 pairs, one FFMA2/FADD2 per two cells; t: the two per-cell
+ * coefficients of the stencil held in tensor memory, loaded a block row at a
+ * time, instead of registers).  MLSD_TUNE_LOG set to
  * anything prints every candidate's trial time to stderr.
  * Patch sizes 32 and 64 run one CTA per field (or per patch, packed); 128 and
  * 256 split each field over a thread-block cluster of 2-16 CTAs that exchange
- * their slab edges through distributed shared memory.
+ * their slab edges through distributed shared memory, or, with the
+ * coefficients in tensor memory, run a 128 field in one CTA of 512 threads.
  * Returns MLSD_EINVAL for an invalid problem, MLSD_EUNSUPPORTED for a patch
  * size or precision without a kernel, MLSD_ENOMEM / MLSD_ECUDA otherwise.   */
 int mlsd_build_levels(const mlsd_problem *p, void *cuda_stream, mlsd_levels **out);

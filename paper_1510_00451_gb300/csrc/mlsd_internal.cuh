@@ -41,6 +41,7 @@ struct PatchVariant {
     int n, precision, bx, by, minb, packed, threads;   // packed: both fields per CTA (f32x2)
     int cluster;             // CTAs per patch field (slabs of n / cluster rows), 1 = one CTA
     int split;               // split-phase stage barriers (interior cells overlap the barrier)
+    int tmem;                // 1: the per-cell coefficients live in tensor memory
     size_t smem;
     const void *fn;
 };

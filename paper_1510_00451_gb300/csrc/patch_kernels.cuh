@@ -32,6 +32,9 @@ namespace mlsd {
 namespace {
 
 constexpr int kFlush = 32;   // FP32 flux partials are flushed to FP64 this often (steps)
+#ifndef TM_PREFETCH
+#define TM_PREFETCH false    // tensor-memory coefficient rows: load each row just before use
+#endif
 constexpr long long kMaxSteps = 1ll << 30;   // larger step counts are rejected
 
 template <typename T, int CNT>
@@ -221,6 +224,53 @@ struct CoefP {
     float2 b11x2, b22x2, bx, bc, T, K, halfK;
 };
 
+// ---------------------------------------------------------------------------
+// Stencil coefficients in tensor memory (the "t" tilings: FP32, 4 x 8 cells per
+// thread).  The two per-cell coefficients aE, aN of a thread's block (64 words)
+// live in the SM's tensor memory instead of its registers, so that a cell needs
+// only two registers (w and the stage value): a field then takes half the
+// register file it takes otherwise, and a 128^2 field fits one CTA of 512
+// threads, a 256^2 field a cluster of 4.  Warp w may address only the TMEM
+// lanes 32 (w % 4) .. +31; its threads own those lanes (one each) and the
+// columns 64 (w / 4) .. +63, block row r at columns 8 r .. 8 r + 7 as
+// (aE[0..3], aN[0..3]).  A CTA of NT threads allocates NT / 2 columns.  Every
+// such kernel holds at least 64 registers per thread (w and the stage value of
+// 32 cells), so the CTAs that fit an SM's register file (65536 registers) ask
+// for at most 65536 / 128 = 512 columns, the SM's whole tensor memory: an
+// allocation never waits on another CTA of these kernels.
+__device__ __forceinline__ void tm_st8(uint32_t taddr, const float (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :: "r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+                    "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+                    "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                    "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tm_wait_st()
+{
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// start loading 8 columns of this thread's lane; the values are valid after tm_wait_ld
+__device__ __forceinline__ void tm_ld8(uint32_t taddr, uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+}
+
+// wait for this thread's outstanding tensor-memory loads; the registers of the
+// last load pass through the statement, so no use of them is placed before it
+__device__ __forceinline__ void tm_wait_ld(uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                   "+r"(v[6]), "+r"(v[7]));
+}
+
 template <int N, int C, int BX, int BY, typename real>
 struct Tile {
     using S = Smem<N, C, BX, BY, real>;
@@ -297,6 +347,41 @@ struct Tile {
         }
     }
 
+    // SYNC = 3 (clusters): after the block edges of buffer `buf` are in shared
+    // memory, the slab's last row goes to rank + 1's HS slot and its first row to
+    // rank - 1's HN slot by two bulk copies issued by thread 0, each completing on
+    // the receiver's mbarrier of this buffer; the rows written by the threads must
+    // reach the async proxy first.  The source rows are not rewritten before both
+    // copies have landed: the receivers wait for them before they send the next
+    // stage's rows.  Only the threads on the slab's first and last block rows wait
+    // for the incoming rows.
+    __device__ __forceinline__ static void bulk_rows(real *sm, int buf, int rank, int tx, int ty,
+                                                     uint32_t mbar, uint32_t parity, int *status,
+                                                     bool *live)
+    {
+        if (ty == 0 || ty == NBY - 1) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tx == 0 && ty == 0 && *live) {
+            real *rowT = sm + buf * S::STAGE, *rowB = rowT + S::ROW;
+            real *HS = rowB + S::ROW + 2 * S::COL, *HN = HS + N;
+            const uint32_t bytes = (uint32_t)(N * sizeof(real));
+            bulk_to_rank((uint32_t)__cvta_generic_to_shared(HS),
+                         (uint32_t)__cvta_generic_to_shared(rowB + (NBY - 1) * N), bytes, mbar,
+                         (rank + 1) % C);
+            bulk_to_rank((uint32_t)__cvta_generic_to_shared(HN),
+                         (uint32_t)__cvta_generic_to_shared(rowT), bytes, mbar, (rank + C - 1) % C);
+        }
+        if ((ty == 0 || ty == NBY - 1) && *live) {
+            if (!nbr_wait(mbar, parity, status)) {
+                *live = false;
+                atomicCAS(status, 0, MLSD_ETIMEOUT);
+            } else if (tx == 0 && ty == 0) {
+                // the phase completed: thread 0 re-arms this buffer's barrier
+                arm_tx(mbar, (uint32_t)(2 * N * sizeof(real)));
+            }
+        }
+    }
+
     // Exchange the edges of x through buffer `buf`, then form x + dt f(x),
     //   bc x + b11 (xE + xW) + b22 (xN + xS) + A1 (xE - xW) + A2 (xN - xS)
     //      + 2h A_J + bx (dEW(b+1) - dEW(b-1)),
@@ -333,33 +418,7 @@ struct Tile {
         }
         publish_edges<SYNC != 3>(sm, buf, rank, tx, ty, x);
         if constexpr (SYNC == 3 && C > 1) {
-            // the slab's last row goes to rank + 1's HS slot and its first row to
-            // rank - 1's HN slot by two bulk copies issued by thread 0, each
-            // completing on the receiver's mbarrier of this buffer; the rows
-            // written by the threads must reach the async proxy first.  The
-            // source rows are not rewritten before both copies have landed: the
-            // receivers wait for them before they send the next stage's rows.
-            if (ty == 0 || ty == NBY - 1) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tx == 0 && ty == 0 && *live) {
-                real *rowT = sm + buf * S::STAGE, *rowB = rowT + S::ROW;
-                real *HS = rowB + S::ROW + 2 * S::COL, *HN = HS + N;
-                const uint32_t bytes = (uint32_t)(N * sizeof(real));
-                bulk_to_rank((uint32_t)__cvta_generic_to_shared(HS),
-                             (uint32_t)__cvta_generic_to_shared(rowB + (NBY - 1) * N), bytes, mbar,
-                             (rank + 1) % C);
-                bulk_to_rank((uint32_t)__cvta_generic_to_shared(HN),
-                             (uint32_t)__cvta_generic_to_shared(rowT), bytes, mbar, (rank + C - 1) % C);
-            }
-            if ((ty == 0 || ty == NBY - 1) && *live) {
-                if (!nbr_wait(mbar, parity, status)) {
-                    *live = false;
-                    atomicCAS(status, 0, MLSD_ETIMEOUT);
-                } else if (tx == 0 && ty == 0) {
-                    // the phase completed: thread 0 re-arms this buffer's barrier
-                    arm_tx(mbar, (uint32_t)(2 * N * sizeof(real)));
-                }
-            }
+            bulk_rows(sm, buf, rank, tx, ty, mbar, parity, status, live);
         } else if constexpr (SYNC == 2 && C > 1) {
             if (ty == NBY - 1) nbr_arrive(mbar, (rank + 1) % C);       // its HS slot
             if (ty == 0) nbr_arrive(mbar, (rank + C - 1) % C);         // its HN slot
@@ -413,6 +472,89 @@ struct Tile {
             }
 #pragma unroll
             for (int c = 0; c < BX; ++c) { dm[c] = d0[c]; d0[c] = dp[c]; }
+        }
+    }
+
+    // stage() with the per-cell coefficients in tensor memory (the "t" tilings):
+    // `tcol` addresses this thread's first column.  Row r + 1's coefficients are
+    // loaded while row r is computed; the arithmetic and its order are those of
+    // stage(), so both give the same bits.  SYNC = 0 (one barrier per stage) or 3
+    // (bulk row copies between the slabs of a cluster).  FLUX (second stage of a
+    // step inside the averaging window): the flux sums q1 += aE w, q2 += aN w,
+    // qw += w of the new values are formed here, in stage()'s cell order, from
+    // the coefficients already loaded.
+    template <int J, bool SECOND, int SYNC, bool FLUX = false, bool PF = TM_PREFETCH>
+    __device__ __forceinline__ static void stage_tm(real *sm, int buf, int rank, int tx, int ty,
+                                                    const real (&x)[BY][BX], real (&out)[BY][BX],
+                                                    uint32_t tcol, const Coef<real> &k, uint32_t mbar,
+                                                    uint32_t parity, int *status, bool *live,
+                                                    real &q1, real &q2, real &qw)
+    {
+        static_assert(BX == 4 && BY == 8 && sizeof(real) == 4, "coefficient rows of 8 words");
+        static_assert(SYNC == 0 || (SYNC == 3 && C > 1), "barrier per stage or bulk row copies");
+        publish_edges<SYNC != 3>(sm, buf, rank, tx, ty, x);
+        if constexpr (SYNC == 3) bulk_rows(sm, buf, rank, tx, ty, mbar, parity, status, live);
+        else tile_sync<C>();
+        real hS[BX], hN[BX], hW[BY + 2], hE[BY + 2];
+        load_halos(sm, buf, tx, ty, hS, hN, hW, hE);
+        uint32_t cv[2][8];
+        __syncwarp();
+        if constexpr (PF) {
+            tm_ld8(tcol, cv[0]);
+            tm_wait_ld(cv[0]);
+        }
+        real dm[BX], d0[BX], dp[BX];
+#pragma unroll
+        for (int c = 0; c < BX; ++c) {
+            real e = (c + 1 < BX) ? hS[c + 1] : hE[0];
+            real w = (c > 0) ? hS[c - 1] : hW[0];
+            dm[c] = e - w;
+            real e0 = (c + 1 < BX) ? x[0][c + 1] : hE[1];
+            real w0 = (c > 0) ? x[0][c - 1] : hW[1];
+            d0[c] = e0 - w0;
+        }
+#pragma unroll
+        for (int r = 0; r < BY; ++r) {
+            if constexpr (PF) {
+                if (r + 1 < BY) tm_ld8(tcol + 8 * (r + 1), cv[(r + 1) & 1]);
+            } else {
+                tm_ld8(tcol + 8 * r, cv[r & 1]);
+                tm_wait_ld(cv[r & 1]);
+            }
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                real e, w;
+                if (r + 1 < BY) {
+                    e = (c + 1 < BX) ? x[r + 1][c + 1] : hE[r + 2];
+                    w = (c > 0) ? x[r + 1][c - 1] : hW[r + 2];
+                } else {
+                    e = (c + 1 < BX) ? hN[c + 1] : hE[BY + 1];
+                    w = (c > 0) ? hN[c - 1] : hW[BY + 1];
+                }
+                dp[c] = e - w;
+            }
+#pragma unroll
+            for (int c = 0; c < BX; ++c) {
+                const real xc = x[r][c];
+                const real xW = (c > 0) ? x[r][c - 1] : hW[r + 1];
+                const real xN = (r + 1 < BY) ? x[r + 1][c] : hN[c];
+                const real xS = (r > 0) ? x[r - 1][c] : hS[c];
+                const real aE = __uint_as_float(cv[r & 1][c]), aN = __uint_as_float(cv[r & 1][4 + c]);
+                cell<J, SECOND>(out[r][c], xc, xW, xN, xS, d0[c], dm[c], dp[c], aE, aN, k);
+            }
+            if constexpr (FLUX) {
+#pragma unroll
+                for (int c = 0; c < BX; ++c) {
+                    q1 = fma(__uint_as_float(cv[r & 1][c]), out[r][c], q1);
+                    q2 = fma(__uint_as_float(cv[r & 1][4 + c]), out[r][c], q2);
+                    qw += out[r][c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < BX; ++c) { dm[c] = d0[c]; d0[c] = dp[c]; }
+            if constexpr (PF) {
+                if (r + 1 < BY) tm_wait_ld(cv[(r + 1) & 1]);
+            }
         }
     }
 
@@ -787,10 +929,14 @@ struct Tile {
         }
     }
 
-    template <int J, int SYNC>
-    __device__ static void run(const PatchParams &prm, real *sm, long long p, int rank)
+    // TM: the per-cell coefficients live in tensor memory at `tmem` (the CTA's
+    // allocation of NT / 2 columns) instead of registers; see stage_tm().
+    template <int J, int SYNC, bool TM = false>
+    __device__ static void run(const PatchParams &prm, real *sm, long long p, int rank,
+                               uint32_t tmem = 0)
     {
         constexpr bool SPLIT = SYNC == 1;
+        static_assert(!TM || SYNC == 0 || SYNC == 3, "tensor-memory coefficients: SYNC 0 or 3");
         const int tid = threadIdx.x, tx = tid % NBX, ty = tid / NBX;
         const int a0 = tx * BX, b0 = ty * BY;          // slab-local
         const int g0 = rank * NS;                       // first patch row of the slab
@@ -891,13 +1037,36 @@ struct Tile {
         k.K = -k.twoh * (J == 1 ? b11 : b22);
         k.halfK = (real)0.5 * k.K;
         // A1, A2 become aE = A1 + b11, aN = A2 + b22 (A_i = dt v_i / 2h)
+        const int warp = tid >> 5;
+        const uint32_t tcol = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 64u * (uint32_t)(warp >> 2);
+        if constexpr (TM) {
+            // the same values, from v formed again from the psi rows, row by row into
+            // tensor memory: (aE[0..3], aN[0..3]) of block row r at column 8 r
+            __syncwarp();
 #pragma unroll
-        for (int r = 0; r < BY; ++r)
+            for (int r = 0; r < BY; ++r) {
+                const int rr = b0 + r + 1;
+                float cf[8];
 #pragma unroll
-            for (int c = 0; c < BX; ++c) {
-                A1[r][c] = fma(A1[r][c], cA, b11);
-                A2[r][c] = fma(A2[r][c], cA, b22);
+                for (int c = 0; c < BX; ++c) {
+                    const int a = a0 + c, ap = (a + 1) % N, am = (a + N - 1) % N;
+                    const real v1 = (psi[(rr - 1) * N + a] - psi[(rr + 1) * N + a]) * inv2h;
+                    const real v2 = (psi[rr * N + ap] - psi[rr * N + am]) * inv2h;
+                    cf[c] = fma(v1, cA, b11);
+                    cf[BX + c] = fma(v2, cA, b22);
+                }
+                tm_st8(tcol + 8 * r, cf);
             }
+            tm_wait_st();
+        } else {
+#pragma unroll
+            for (int r = 0; r < BY; ++r)
+#pragma unroll
+                for (int c = 0; c < BX; ++c) {
+                    A1[r][c] = fma(A1[r][c], cA, b11);
+                    A2[r][c] = fma(A2[r][c], cA, b22);
+                }
+        }
         tile_sync<C>();   // psi tile (and the vmax slots) are dead; the space becomes the exchange buffers
 
         double f1 = 0.0, f2 = 0.0;
@@ -920,6 +1089,28 @@ struct Tile {
             asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
         }
         for (long long step = 0; step < ntot; ++step) {
+            if constexpr (TM) {
+                const uint32_t par = (uint32_t)(step & 1);
+                real q1 = 0, q2 = 0, qw = 0;
+                stage_tm<J, false, SYNC>(sm, 0, rank, tx, ty, w, s, tcol, k, mbar0, par, prm.status,
+                                         &live, q1, q2, qw);
+                if (step < nb) {
+                    stage_tm<J, true, SYNC>(sm, 1, rank, tx, ty, s, w, tcol, k, mbar0 + 8, par,
+                                            prm.status, &live, q1, q2, qw);
+                    continue;
+                }
+                stage_tm<J, true, SYNC, true>(sm, 1, rank, tx, ty, s, w, tcol, k, mbar0 + 8, par,
+                                              prm.status, &live, q1, q2, qw);
+                p1 += q1;
+                p2 += q2;
+                pw += qw;
+                if (++win == kFlush) {
+                    f1 += (double)p1 - (double)b11 * (double)pw;
+                    f2 += (double)p2 - (double)b22 * (double)pw;
+                    p1 = 0; p2 = 0; pw = 0; win = 0;
+                }
+                continue;
+            }
             if constexpr (SPLIT) {
                 stage_split<J, false>(sm, 0, rank, tx, ty, w, s, A1, A2, k);
                 stage_split<J, true>(sm, 1, rank, tx, ty, s, w, A1, A2, k);
@@ -1023,6 +1214,49 @@ k_patch_solve(PatchParams prm)
     }
 }
 
+// Tilings with the per-cell coefficients in tensor memory (Tile::stage_tm): the
+// CTA allocates NT / 2 TMEM columns once, runs its work items as k_patch_solve
+// does, and frees them before it exits.
+template <int N, int BX, int BY, int MINB, int C, int SYNC>
+__global__ void __launch_bounds__((N / BX) * (N / C / BY), MINB)
+k_patch_solve_tm(PatchParams prm)
+{
+    constexpr uint32_t COLS = (uint32_t)((N / BX) * (N / C / BY) / 2);
+    static_assert(COLS >= 32 && (COLS & (COLS - 1)) == 0 && COLS <= 512, "TMEM allocation");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t tm_slot;
+    float *sm = reinterpret_cast<float *>(smem_raw);
+    const int rank = (int)(blockIdx.x % C);
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"((uint32_t)__cvta_generic_to_shared(&tm_slot)), "r"(COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tm_slot;
+    using T = Tile<N, C, BX, BY, float>;
+    // work items as in k_patch_solve: one per cluster, or a grid-stride walk over
+    // the first 2 * (*count_dev) items when the launch was sized before the count
+    const long long first = prm.item0 + blockIdx.x / C;
+    const long long end = prm.count_dev ? prm.item0 + 2LL * (long long)*prm.count_dev
+                                        : prm.item0 + prm.items;
+    const long long stride = prm.count_dev ? (long long)(gridDim.x / C) : end;
+    for (long long item = first; item < end; item += stride) {
+        const long long p = prm.pidx ? (long long)prm.pidx[item >> 1] : (item >> 1);
+        if (item & 1) T::template run<2, SYNC, true>(prm, sm, p, rank, tmem);
+        else T::template run<1, SYNC, true>(prm, sm, p, rank, tmem);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(COLS)
+                     : "memory");
+    }
+}
+
 // SYNC: 0 = barrier per stage, 1 = split-phase cluster barrier, 2 = neighbour
 // signalling, 3 = bulk copies of the slab edge rows, 5 = bulk copies with the
 // cross-slab rows computed last (2, 3, 5: clusters only), 4 = row-paired
@@ -1045,9 +1279,34 @@ void add_variant(std::vector<PatchVariant> &out)
     v.packed = 0;
     v.cluster = C;
     v.split = SYNC;
+    v.tmem = 0;
     v.threads = (N / BX) * (N / C / BY);
     v.smem = Smem<N, C, BX, BY, real>::BYTES;
     v.fn = reinterpret_cast<const void *>(&k_patch_solve<N, BX, BY, real, MINB, C, SYNC>);
+    out.push_back(v);
+}
+
+// a tiling with the per-cell coefficients in tensor memory (FP32, 4 x 8 cells per thread)
+template <int N, int MINB = 1, int C = 1, int SYNC = 0>
+void add_variant_tm(std::vector<PatchVariant> &out)
+{
+    constexpr int BX = 4, BY = 8;
+    static_assert(((N / BX) * (N / C / BY)) % 128 == 0, "whole lane quarters of warps");
+    static_assert((N / BX) * (N / C / BY) <= 512, "reduction slots 0..31 (warp pairs), 32, 40, 41");
+    static_assert(N % C == 0 && (N / C) % BY == 0, "tiling");
+    PatchVariant v;
+    v.n = N;
+    v.precision = MLSD_FP32;
+    v.bx = BX;
+    v.by = BY;
+    v.minb = MINB;
+    v.packed = 0;
+    v.cluster = C;
+    v.split = SYNC;
+    v.tmem = 1;
+    v.threads = (N / BX) * (N / C / BY);
+    v.smem = Smem<N, C, BX, BY, float>::BYTES;
+    v.fn = reinterpret_cast<const void *>(&k_patch_solve_tm<N, BX, BY, MINB, C, SYNC>);
     out.push_back(v);
 }
 
@@ -1374,6 +1633,7 @@ void add_variant2(std::vector<PatchVariant> &out)
     v.packed = 1;
     v.cluster = 1;
     v.split = 0;
+    v.tmem = 0;
     v.threads = (N / BX) * (N / BY);
     v.smem = Smem2<N, BX, BY>::BYTES;
     v.fn = reinterpret_cast<const void *>(&k_patch_solve2<N, BX, BY, MINB>);

@@ -432,7 +432,8 @@ std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;   // -> (bx, co
 
 int tile_code(const PatchVariant &v)
 {
-    return v.by * 16 + v.minb + 4096 * v.packed + 65536 * v.cluster + (1 << 24) * v.split;
+    return v.by * 16 + v.minb + 4096 * v.packed + 65536 * v.cluster + (1 << 24) * v.split +
+           (1 << 28) * v.tmem;
 }
 
 int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
@@ -442,11 +443,11 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
     if (vs.empty()) return MLSD_EUNSUPPORTED;
     c.variant = vs[0];
     if (const char *env = std::getenv("MLSD_TILE")) {
-        // <bx>x<by>[m<minb>][c<cluster>][p][s|n|b|d|r]: p selects the packed two-field kernel,
-        // s the split-phase stage barriers, n neighbour signalling between slabs, b bulk
-        // copies of the slab edge rows, d bulk copies with the cross-slab rows computed
-        // last, r the row-paired f32x2 kernel
-        int bx = 0, by = 0, mb = 1, pk = 0, cl = 1, sp = 0;
+        // <bx>x<by>[m<minb>][c<cluster>][p][s|n|b|d|r][t]: p selects the packed two-field
+        // kernel, s the split-phase stage barriers, n neighbour signalling between slabs, b
+        // bulk copies of the slab edge rows, d bulk copies with the cross-slab rows computed
+        // last, r the row-paired f32x2 kernel, t the per-cell coefficients in tensor memory
+        int bx = 0, by = 0, mb = 1, pk = 0, cl = 1, sp = 0, tm = 0;
         char rest[16] = "";
         if (std::sscanf(env, "%dx%d%15s", &bx, &by, rest) >= 2) {
             for (const char *c = rest; *c; ++c) {
@@ -458,10 +459,11 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
                 if (*c == 'b') sp = 3;
                 if (*c == 'r') sp = 4;
                 if (*c == 'd') sp = 5;
+                if (*c == 't') tm = 1;
             }
             for (auto &v : vs)
                 if (v.bx == bx && v.by == by && v.minb == mb && v.packed == pk && v.cluster == cl &&
-                    v.split == sp) {
+                    v.split == sp && v.tmem == tm) {
                     c.variant = v;
                     return MLSD_OK;
                 }
@@ -517,9 +519,9 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
         }
         if (!ok) { cudaGetLastError(); continue; }   // a tiling this device cannot launch
         if (std::getenv("MLSD_TUNE_LOG"))
-            std::fprintf(stderr, "mlsd tune n=%d items=%lld steps=%lld %dx%d m%d c%d sync%d%s: %.4f ms\n",
+            std::fprintf(stderr, "mlsd tune n=%d items=%lld steps=%lld %dx%d m%d c%d sync%d%s%s: %.4f ms\n",
                          c.n, pp.items, pp.na_fixed, v.bx, v.by, v.minb, v.cluster, v.split,
-                         v.packed ? " packed" : "", t);
+                         v.packed ? " packed" : "", v.tmem ? " tmem" : "", t);
         if (t < best) { best = t; c.variant = v; }
     }
     cudaEventDestroy(e0);
@@ -676,6 +678,7 @@ int mlsd_level_info(const mlsd_levels *h, int level, mlsd_level_desc *out)
     out->min_ctas = c.variant.minb;
     out->split = c.variant.split;
     out->n_classes = (int)d.cls.size();
+    out->coef_tmem = c.variant.tmem;
     return MLSD_OK;
 }
 
