@@ -127,7 +127,8 @@ typedef struct {
                                   the class with the most work; all classes run concurrently */
     int coef_tmem;             /* 1: the kernel keeps the two per-cell stencil coefficients in
                                   the SM's tensor memory instead of registers (two registers per
-                                  cell instead of four, so a field needs half the SMs) */
+                                  cell instead of four, so a field needs half the SMs); 2: the
+                                  same, with the halo columns read as the rows need them */
 } mlsd_level_desc;
 
 typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and scratch */
@@ -138,7 +139,7 @@ typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and 
  * Set-up also picks the thread-block tiling of the patch kernel per patch
  * size: every compiled candidate is timed on a sample of the level's patches
  * (a short fixed window) and the fastest is kept for the process; the
- * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][c<cluster>][p][s|n|b|d|r][t]
+ * environment variable MLSD_TILE=<bx>x<by>[m<min CTAs/SM>][c<cluster>][p][s|n|b|d|r][t|l]
  * forces one where it exists for the level's patch size (p: the packed kernel
  * that advances both fields of a patch in f32x2 pairs; c: CTAs per patch field;
  * s: split-phase stage barriers; n: neighbour signalling between the slabs of
@@ -147,7 +148,8 @@ typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and 
  * that need a neighbouring slab's row computed after the others; r: rows r and r + by/2
  * of a thread's block in f32x2 pairs, one FFMA2/FADD2 per two cells; t: the two per-cell
  * coefficients of the stencil held in tensor memory, loaded a block row at a
- * time, instead of registers).  MLSD_TUNE_LOG set to
+ * time, instead of registers; l: as t, with the west and east halo columns read
+ * two rows at a time as the row loop reaches them).  MLSD_TUNE_LOG set to
  * anything prints every candidate's trial time to stderr.
  * Patch sizes 32 and 64 run one CTA per field (or per patch, packed); 128 and
  * 256 split each field over a thread-block cluster of 2-16 CTAs that exchange

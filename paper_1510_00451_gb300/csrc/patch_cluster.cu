@@ -24,6 +24,8 @@ int patch_variants_cluster(int n, std::vector<PatchVariant> &out)
         // clusters of 2 at 2 CTAs per SM
         add_variant_tm<128>(out);
         add_variant_tm<128, 2, 2, 3>(out);
+        add_variant_tm<128, 1, 1, 0, true>(out);          // column halos as the rows need them
+        add_variant_tm<128, 2, 2, 3, true>(out);
     } else if (n == 256) {
         add_variant<256, 4, 8, float, 1, 8>(out);
         add_variant<256, 4, 8, float, 1, 8, 1>(out);
@@ -46,6 +48,8 @@ int patch_variants_cluster(int n, std::vector<PatchVariant> &out)
         // 8 CTAs of 256 threads at 2 CTAs per SM
         add_variant_tm<256, 1, 4, 3>(out);
         add_variant_tm<256, 2, 8, 3>(out);
+        add_variant_tm<256, 1, 4, 3, true>(out);          // column halos as the rows need them
+        add_variant_tm<256, 2, 8, 3, true>(out);
     }
     return (int)out.size();
 }

@@ -32,9 +32,6 @@ namespace mlsd {
 namespace {
 
 constexpr int kFlush = 32;   // FP32 flux partials are flushed to FP64 this often (steps)
-#ifndef TM_PREFETCH
-#define TM_PREFETCH false    // tensor-memory coefficient rows: load each row just before use
-#endif
 constexpr long long kMaxSteps = 1ll << 30;   // larger step counts are rejected
 
 template <typename T, int CNT>
@@ -180,9 +177,12 @@ __device__ __forceinline__ void nbr_arrive(uint32_t mbar_local, int rank)
 }
 
 // Bounded wait for the phase of the given parity: false after about a second
-// (2^31 SM clocks), or at once when another wait of the launch has already
-// timed out (status holds MLSD_ETIMEOUT), so that a failed exchange ends the
-// launch quickly instead of costing every remaining CTA a full second.
+// (2^31 SM clocks), or after about half a millisecond (2^20 clocks) when another
+// wait of the launch has already timed out (status holds MLSD_ETIMEOUT), so that
+// a failed exchange ends the launch quickly instead of costing every remaining
+// CTA a full second.  The status word (global memory) is not read in the first
+// 2^20 clocks: an ordinary wait for a neighbour's rows lasts a few microseconds,
+// and a global load per retry would delay the retry that sees the phase complete.
 __device__ __forceinline__ bool nbr_wait(uint32_t mbar_local, uint32_t parity, const int *status)
 {
     const long long t0 = clock64();
@@ -194,8 +194,9 @@ __device__ __forceinline__ bool nbr_wait(uint32_t mbar_local, uint32_t parity, c
             "selp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(ok) : "r"(mbar_local), "r"(parity) : "memory");
         if (ok) return true;
-        if (clock64() - t0 > (1ll << 31)) return false;
-        if (*(volatile const int *)status == MLSD_ETIMEOUT) return false;
+        const long long dt = clock64() - t0;
+        if (dt > (1ll << 31)) return false;
+        if (dt > (1ll << 20) && *(volatile const int *)status == MLSD_ETIMEOUT) return false;
     }
 }
 
@@ -400,9 +401,9 @@ struct Tile {
     // SYNC = 2, 3 after a timeout: `live` (per thread) turns false when this
     // thread's wait runs out; the thread then waits no more, and thread 0 stops
     // re-arming the barriers and issuing bulk copies.  The neighbours' waits run
-    // out in turn (at once, once the status word holds MLSD_ETIMEOUT), so every
-    // rank finishes its remaining steps without waiting and the ranks meet at the
-    // cluster barriers after the loop.
+    // out in turn (within half a millisecond once the status word holds
+    // MLSD_ETIMEOUT), so every rank finishes its remaining steps without waiting
+    // and the ranks meet at the cluster barriers after the loop.
     template <int J, bool SECOND, int SYNC = 0>
     __device__ __forceinline__ static void stage(real *sm, int buf, int rank, int tx, int ty,
                                                  const real (&x)[BY][BX], real (&out)[BY][BX],
@@ -476,14 +477,17 @@ struct Tile {
     }
 
     // stage() with the per-cell coefficients in tensor memory (the "t" tilings):
-    // `tcol` addresses this thread's first column.  Row r + 1's coefficients are
-    // loaded while row r is computed; the arithmetic and its order are those of
+    // `tcol` addresses this thread's first column.  Each row's coefficients are
+    // loaded just before the row (loading them one row ahead measured no faster);
+    // the arithmetic and its order are those of
     // stage(), so both give the same bits.  SYNC = 0 (one barrier per stage) or 3
     // (bulk row copies between the slabs of a cluster).  FLUX (second stage of a
     // step inside the averaging window): the flux sums q1 += aE w, q2 += aN w,
     // qw += w of the new values are formed here, in stage()'s cell order, from
-    // the coefficients already loaded.
-    template <int J, bool SECOND, int SYNC, bool FLUX = false, bool PF = TM_PREFETCH>
+    // the coefficients already loaded.  LZ: the west and east halo columns are
+    // read in pairs of rows as the row loop reaches them instead of all at once,
+    // so that fewer of them are live (the values are load_halos()').
+    template <int J, bool SECOND, int SYNC, bool FLUX = false, bool LZ = false>
     __device__ __forceinline__ static void stage_tm(real *sm, int buf, int rank, int tx, int ty,
                                                     const real (&x)[BY][BX], real (&out)[BY][BX],
                                                     uint32_t tcol, const Coef<real> &k, uint32_t mbar,
@@ -496,13 +500,46 @@ struct Tile {
         if constexpr (SYNC == 3) bulk_rows(sm, buf, rank, tx, ty, mbar, parity, status, live);
         else tile_sync<C>();
         real hS[BX], hN[BX], hW[BY + 2], hE[BY + 2];
-        load_halos(sm, buf, tx, ty, hS, hN, hW, hE);
-        uint32_t cv[2][8];
-        __syncwarp();
-        if constexpr (PF) {
-            tm_ld8(tcol, cv[0]);
-            tm_wait_ld(cv[0]);
+        const real *cw = nullptr, *ce = nullptr;      // LZ: this block's rows of the column halos
+        if constexpr (LZ) {
+            const int a0 = tx * BX, b0 = ty * BY;
+            real *rowT = sm + buf * S::STAGE;
+            real *rowB = rowT + S::ROW;
+            real *colL = rowB + S::ROW;
+            real *colR = colL + S::COL;
+            const int tyS = (ty + NBY - 1) % NBY, tyN = (ty + 1) % NBY;
+            const int txW = (tx + NBX - 1) % NBX, txE = (tx + 1) % NBX;
+            const real *cwc = colR + txW * S::CS, *cec = colL + txE * S::CS;
+            cw = cwc + b0;
+            ce = cec + b0;
+            const int aw = (a0 + N - 1) % N, ae = (a0 + BX) % N;
+            if (C > 1 && ty == 0) {
+                const real *HS = colR + S::COL;
+                ld_vec<real, BX>(hS, HS + a0);
+                hW[0] = HS[aw]; hE[0] = HS[ae];
+            } else {
+                ld_vec<real, BX>(hS, rowB + tyS * N + a0);
+                const int bs = (b0 + NS - 1) % NS;
+                hW[0] = cwc[bs]; hE[0] = cec[bs];
+            }
+            if (C > 1 && ty == NBY - 1) {
+                const real *HN = colR + S::COL + N;
+                ld_vec<real, BX>(hN, HN + a0);
+                hW[BY + 1] = HN[aw]; hE[BY + 1] = HN[ae];
+            } else {
+                ld_vec<real, BX>(hN, rowT + tyN * N + a0);
+                const int bn = (b0 + BY) % NS;
+                hW[BY + 1] = cwc[bn]; hE[BY + 1] = cec[bn];
+            }
+            // rows b0, b0 + 1 (16-byte aligned column buffers: cw + 2i is 8-byte aligned)
+            const float2 w2 = *reinterpret_cast<const float2 *>(cw);
+            const float2 e2 = *reinterpret_cast<const float2 *>(ce);
+            hW[1] = w2.x; hW[2] = w2.y; hE[1] = e2.x; hE[2] = e2.y;
+        } else {
+            load_halos(sm, buf, tx, ty, hS, hN, hW, hE);
         }
+        uint32_t cv[8];
+        __syncwarp();
         real dm[BX], d0[BX], dp[BX];
 #pragma unroll
         for (int c = 0; c < BX; ++c) {
@@ -515,12 +552,15 @@ struct Tile {
         }
 #pragma unroll
         for (int r = 0; r < BY; ++r) {
-            if constexpr (PF) {
-                if (r + 1 < BY) tm_ld8(tcol + 8 * (r + 1), cv[(r + 1) & 1]);
-            } else {
-                tm_ld8(tcol + 8 * r, cv[r & 1]);
-                tm_wait_ld(cv[r & 1]);
+            if constexpr (LZ) {
+                if ((r & 1) && r + 2 <= BY) {               // rows b0 + r + 1, b0 + r + 2
+                    const float2 w2 = *reinterpret_cast<const float2 *>(cw + r + 1);
+                    const float2 e2 = *reinterpret_cast<const float2 *>(ce + r + 1);
+                    hW[r + 2] = w2.x; hW[r + 3] = w2.y; hE[r + 2] = e2.x; hE[r + 3] = e2.y;
+                }
             }
+            tm_ld8(tcol + 8 * r, cv);
+            tm_wait_ld(cv);
 #pragma unroll
             for (int c = 0; c < BX; ++c) {
                 real e, w;
@@ -539,22 +579,19 @@ struct Tile {
                 const real xW = (c > 0) ? x[r][c - 1] : hW[r + 1];
                 const real xN = (r + 1 < BY) ? x[r + 1][c] : hN[c];
                 const real xS = (r > 0) ? x[r - 1][c] : hS[c];
-                const real aE = __uint_as_float(cv[r & 1][c]), aN = __uint_as_float(cv[r & 1][4 + c]);
+                const real aE = __uint_as_float(cv[c]), aN = __uint_as_float(cv[4 + c]);
                 cell<J, SECOND>(out[r][c], xc, xW, xN, xS, d0[c], dm[c], dp[c], aE, aN, k);
             }
             if constexpr (FLUX) {
 #pragma unroll
                 for (int c = 0; c < BX; ++c) {
-                    q1 = fma(__uint_as_float(cv[r & 1][c]), out[r][c], q1);
-                    q2 = fma(__uint_as_float(cv[r & 1][4 + c]), out[r][c], q2);
+                    q1 = fma(__uint_as_float(cv[c]), out[r][c], q1);
+                    q2 = fma(__uint_as_float(cv[4 + c]), out[r][c], q2);
                     qw += out[r][c];
                 }
             }
 #pragma unroll
             for (int c = 0; c < BX; ++c) { dm[c] = d0[c]; d0[c] = dp[c]; }
-            if constexpr (PF) {
-                if (r + 1 < BY) tm_wait_ld(cv[(r + 1) & 1]);
-            }
         }
     }
 
@@ -930,13 +967,15 @@ struct Tile {
     }
 
     // TM: the per-cell coefficients live in tensor memory at `tmem` (the CTA's
-    // allocation of NT / 2 columns) instead of registers; see stage_tm().
-    template <int J, int SYNC, bool TM = false>
+    // allocation of NT / 2 columns) instead of registers, see stage_tm(); TM = 2
+    // reads the column halos as the rows need them.
+    template <int J, int SYNC, int TM = 0>
     __device__ static void run(const PatchParams &prm, real *sm, long long p, int rank,
                                uint32_t tmem = 0)
     {
         constexpr bool SPLIT = SYNC == 1;
-        static_assert(!TM || SYNC == 0 || SYNC == 3, "tensor-memory coefficients: SYNC 0 or 3");
+        static_assert(TM == 0 || SYNC == 0 || SYNC == 3, "tensor-memory coefficients: SYNC 0 or 3");
+        constexpr bool LZ = TM == 2;                    // column halos read as the rows need them
         const int tid = threadIdx.x, tx = tid % NBX, ty = tid / NBX;
         const int a0 = tx * BX, b0 = ty * BY;          // slab-local
         const int g0 = rank * NS;                       // first patch row of the slab
@@ -1092,15 +1131,15 @@ struct Tile {
             if constexpr (TM) {
                 const uint32_t par = (uint32_t)(step & 1);
                 real q1 = 0, q2 = 0, qw = 0;
-                stage_tm<J, false, SYNC>(sm, 0, rank, tx, ty, w, s, tcol, k, mbar0, par, prm.status,
-                                         &live, q1, q2, qw);
+                stage_tm<J, false, SYNC, false, LZ>(sm, 0, rank, tx, ty, w, s, tcol, k, mbar0, par,
+                                                    prm.status, &live, q1, q2, qw);
                 if (step < nb) {
-                    stage_tm<J, true, SYNC>(sm, 1, rank, tx, ty, s, w, tcol, k, mbar0 + 8, par,
-                                            prm.status, &live, q1, q2, qw);
+                    stage_tm<J, true, SYNC, false, LZ>(sm, 1, rank, tx, ty, s, w, tcol, k, mbar0 + 8,
+                                                       par, prm.status, &live, q1, q2, qw);
                     continue;
                 }
-                stage_tm<J, true, SYNC, true>(sm, 1, rank, tx, ty, s, w, tcol, k, mbar0 + 8, par,
-                                              prm.status, &live, q1, q2, qw);
+                stage_tm<J, true, SYNC, true, LZ>(sm, 1, rank, tx, ty, s, w, tcol, k, mbar0 + 8, par,
+                                                  prm.status, &live, q1, q2, qw);
                 p1 += q1;
                 p2 += q2;
                 pw += qw;
@@ -1217,7 +1256,7 @@ k_patch_solve(PatchParams prm)
 // Tilings with the per-cell coefficients in tensor memory (Tile::stage_tm): the
 // CTA allocates NT / 2 TMEM columns once, runs its work items as k_patch_solve
 // does, and frees them before it exits.
-template <int N, int BX, int BY, int MINB, int C, int SYNC>
+template <int N, int BX, int BY, int MINB, int C, int SYNC, int TM>
 __global__ void __launch_bounds__((N / BX) * (N / C / BY), MINB)
 k_patch_solve_tm(PatchParams prm)
 {
@@ -1245,8 +1284,8 @@ k_patch_solve_tm(PatchParams prm)
     const long long stride = prm.count_dev ? (long long)(gridDim.x / C) : end;
     for (long long item = first; item < end; item += stride) {
         const long long p = prm.pidx ? (long long)prm.pidx[item >> 1] : (item >> 1);
-        if (item & 1) T::template run<2, SYNC, true>(prm, sm, p, rank, tmem);
-        else T::template run<1, SYNC, true>(prm, sm, p, rank, tmem);
+        if (item & 1) T::template run<2, SYNC, TM>(prm, sm, p, rank, tmem);
+        else T::template run<1, SYNC, TM>(prm, sm, p, rank, tmem);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -1286,10 +1325,12 @@ void add_variant(std::vector<PatchVariant> &out)
     out.push_back(v);
 }
 
-// a tiling with the per-cell coefficients in tensor memory (FP32, 4 x 8 cells per thread)
-template <int N, int MINB = 1, int C = 1, int SYNC = 0>
+// a tiling with the per-cell coefficients in tensor memory (FP32, 4 x 8 cells per
+// thread); LZ: the column halos read as the rows need them
+template <int N, int MINB = 1, int C = 1, int SYNC = 0, bool LZ = false>
 void add_variant_tm(std::vector<PatchVariant> &out)
 {
+    constexpr int TM = LZ ? 2 : 1;
     constexpr int BX = 4, BY = 8;
     static_assert(((N / BX) * (N / C / BY)) % 128 == 0, "whole lane quarters of warps");
     static_assert((N / BX) * (N / C / BY) <= 512, "reduction slots 0..31 (warp pairs), 32, 40, 41");
@@ -1303,10 +1344,10 @@ void add_variant_tm(std::vector<PatchVariant> &out)
     v.packed = 0;
     v.cluster = C;
     v.split = SYNC;
-    v.tmem = 1;
+    v.tmem = TM;
     v.threads = (N / BX) * (N / C / BY);
     v.smem = Smem<N, C, BX, BY, float>::BYTES;
-    v.fn = reinterpret_cast<const void *>(&k_patch_solve_tm<N, BX, BY, MINB, C, SYNC>);
+    v.fn = reinterpret_cast<const void *>(&k_patch_solve_tm<N, BX, BY, MINB, C, SYNC, TM>);
     out.push_back(v);
 }
 

@@ -23,6 +23,7 @@ int patch_variants_n64(int precision, std::vector<PatchVariant> &out)
         add_variant2<64, 2, 4>(out);
         add_variant2<64, 4, 2>(out);
         add_variant_tm<64, 4>(out);                     // coefficients in tensor memory
+        add_variant_tm<64, 4, 1, 0, true>(out);         // ... column halos as the rows need them
     } else {
         add_variant<64, 2, 4, double>(out);
         add_variant<64, 4, 4, double>(out);

@@ -443,10 +443,11 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
     if (vs.empty()) return MLSD_EUNSUPPORTED;
     c.variant = vs[0];
     if (const char *env = std::getenv("MLSD_TILE")) {
-        // <bx>x<by>[m<minb>][c<cluster>][p][s|n|b|d|r][t]: p selects the packed two-field
+        // <bx>x<by>[m<minb>][c<cluster>][p][s|n|b|d|r][t|l]: p selects the packed two-field
         // kernel, s the split-phase stage barriers, n neighbour signalling between slabs, b
         // bulk copies of the slab edge rows, d bulk copies with the cross-slab rows computed
-        // last, r the row-paired f32x2 kernel, t the per-cell coefficients in tensor memory
+        // last, r the row-paired f32x2 kernel, t the per-cell coefficients in tensor memory,
+        // l the same with the column halos read as the rows need them
         int bx = 0, by = 0, mb = 1, pk = 0, cl = 1, sp = 0, tm = 0;
         char rest[16] = "";
         if (std::sscanf(env, "%dx%d%15s", &bx, &by, rest) >= 2) {
@@ -460,6 +461,7 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
                 if (*c == 'r') sp = 4;
                 if (*c == 'd') sp = 5;
                 if (*c == 't') tm = 1;
+                if (*c == 'l') tm = 2;
             }
             for (auto &v : vs)
                 if (v.bx == bx && v.by == by && v.minb == mb && v.packed == pk && v.cluster == cl &&
@@ -521,7 +523,7 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
         if (std::getenv("MLSD_TUNE_LOG"))
             std::fprintf(stderr, "mlsd tune n=%d items=%lld steps=%lld %dx%d m%d c%d sync%d%s%s: %.4f ms\n",
                          c.n, pp.items, pp.na_fixed, v.bx, v.by, v.minb, v.cluster, v.split,
-                         v.packed ? " packed" : "", v.tmem ? " tmem" : "", t);
+                         v.packed ? " packed" : "", v.tmem == 2 ? " tmem lazy" : v.tmem ? " tmem" : "", t);
         if (t < best) { best = t; c.variant = v; }
     }
     cudaEventDestroy(e0);
