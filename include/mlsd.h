@@ -129,6 +129,11 @@ typedef struct {
                                   the SM's tensor memory instead of registers (two registers per
                                   cell instead of four, so a field needs half the SMs); 2: the
                                   same, with the halo columns read as the rows need them */
+    int level_launch;          /* 0: one launch per patch size; 1, 2: every patch of the level in
+                                  one persistent launch (clusters of 4 CTAs of 512 threads with the
+                                  coefficients in tensor memory take tickets of 65 536 cells: a
+                                  256^2 field, or per CTA one 128^2, four 64^2 or sixteen 32^2
+                                  fields), 256^2 tickets first (1) or spread among the others (2) */
 } mlsd_level_desc;
 
 typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and scratch */
@@ -155,6 +160,11 @@ typedef struct mlsd_levels mlsd_levels;   /* opaque; owns all device tables and 
  * 256 split each field over a thread-block cluster of 2-16 CTAs that exchange
  * their slab edges through distributed shared memory, or, with the
  * coefficients in tensor memory, run a 128 field in one CTA of 512 threads.
+ * An FP32 level with several patch sizes (all among 32, 64, 128, 256) is also
+ * timed as one persistent launch of every patch, with two patch-to-cluster
+ * orders, against the per-size launches, and the fastest is kept
+ * (MLSD_LEVEL = 0 keeps the per-size launches, 1 or 2 forces the one launch
+ * with 256^2 fields first or interleaved; mlsd_level_desc.level_launch).
  * Returns MLSD_EINVAL for an invalid problem, MLSD_EUNSUPPORTED for a patch
  * size or precision without a kernel, MLSD_ENOMEM / MLSD_ECUDA otherwise.   */
 int mlsd_build_levels(const mlsd_problem *p, void *cuda_stream, mlsd_levels **out);

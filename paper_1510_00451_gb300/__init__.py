@@ -68,7 +68,8 @@ class mlsd_level_desc(ctypes.Structure):
                 ("n_off21_modes", ctypes.c_int), ("tile_bx", ctypes.c_int),
                 ("tile_by", ctypes.c_int), ("threads", ctypes.c_int), ("packed", ctypes.c_int),
                 ("cluster", ctypes.c_int), ("min_ctas", ctypes.c_int), ("split", ctypes.c_int),
-                ("n_classes", ctypes.c_int), ("coef_tmem", ctypes.c_int)]
+                ("n_classes", ctypes.c_int), ("coef_tmem", ctypes.c_int),
+                ("level_launch", ctypes.c_int)]
 
 
 _P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64

@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmlsd.so")
 SOURCES = ["runtime.cu", "patch.cu", "patch_n32.cu", "patch_n64.cu", "patch_cluster.cu",
-           "levels.cu", "macro_dns.cu", "surrogate.cu", "mlp_tc.cu", "gemm_tc.cu"]
+           "patch_level.cu", "levels.cu", "macro_dns.cu", "surrogate.cu", "mlp_tc.cu", "gemm_tc.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/mlsd.h"
@@ -53,6 +54,20 @@ int patch_variants_n64(int precision, std::vector<PatchVariant> &out);
 int patch_variants_cluster(int n, std::vector<PatchVariant> &out);
 cudaError_t launch_patch(const PatchVariant &v, const PatchParams &p, long long grid,
                          cudaStream_t s);
+
+// All patches of a level in one persistent launch (patch_level.cu): clusters of
+// 4 CTAs of 512 threads with the stencil coefficients in tensor memory take
+// tickets of the level's work, each a 256^2 field or four CTA tasks (one 128^2,
+// four 64^2 or sixteen 32^2 fields).
+struct LevelParams {
+    static constexpr int CLUSTER = 4;
+    PatchParams cls[4];      // per patch size: 0 = 32, 1 = 64, 2 = 128, 3 = 256 (as present)
+    const long long *task;   // [n_tickets][CLUSTER]: (size << 56) | first work item, or -1: none
+    long long n_tickets;
+};
+size_t level_kernel_smem();
+cudaError_t level_kernel_clusters(int *out);
+cudaError_t launch_level(const LevelParams &lp, int clusters, cudaStream_t s);
 
 // Combine the two fields' flux averages: K = B + sym(S).
 cudaError_t launch_compose(long long P, const double *B, const double *S, double *K,

@@ -277,6 +277,23 @@ struct Tile {
     using S = Smem<N, C, BX, BY, real>;
     static constexpr int NS = S::NS, NBX = S::NBX, NBY = S::NBY, NT = NBX * NBY;
 
+    // Barrier over the threads that share this field.  GR = false: the CTA.
+    // GR = true (one field per group of NT threads of a larger CTA, C = 1): the
+    // group, by a named barrier (ids 1.., one per group of NT >= 64 threads) or,
+    // for one-warp groups, __syncwarp.
+    template <bool GR>
+    __device__ __forceinline__ static void csync()
+    {
+        if constexpr (!GR) {
+            __syncthreads();
+        } else if constexpr (NT == 32) {
+            __syncwarp();
+        } else {
+            static_assert(NT % 32 == 0 && C == 1, "groups of whole warps, one CTA per field");
+            asm volatile("bar.sync %0, %1;" :: "r"(1 + (int)(threadIdx.x / NT)), "r"(NT) : "memory");
+        }
+    }
+
     // Publish the edges of x into buffer `buf`; with a cluster, also push the
     // slab's first row into the HN slot of the rank below (its row above) and the
     // slab's last row into the HS slot of the rank above (its row below).
@@ -487,7 +504,7 @@ struct Tile {
     // the coefficients already loaded.  LZ: the west and east halo columns are
     // read in pairs of rows as the row loop reaches them instead of all at once,
     // so that fewer of them are live (the values are load_halos()').
-    template <int J, bool SECOND, int SYNC, bool FLUX = false, bool LZ = false>
+    template <int J, bool SECOND, int SYNC, bool FLUX = false, bool LZ = false, bool GR = false>
     __device__ __forceinline__ static void stage_tm(real *sm, int buf, int rank, int tx, int ty,
                                                     const real (&x)[BY][BX], real (&out)[BY][BX],
                                                     uint32_t tcol, const Coef<real> &k, uint32_t mbar,
@@ -498,7 +515,8 @@ struct Tile {
         static_assert(SYNC == 0 || (SYNC == 3 && C > 1), "barrier per stage or bulk row copies");
         publish_edges<SYNC != 3>(sm, buf, rank, tx, ty, x);
         if constexpr (SYNC == 3) bulk_rows(sm, buf, rank, tx, ty, mbar, parity, status, live);
-        else tile_sync<C>();
+        else if constexpr (C > 1) tile_sync<C>();
+        else csync<GR>();
         real hS[BX], hN[BX], hW[BY + 2], hE[BY + 2];
         const real *cw = nullptr, *ce = nullptr;      // LZ: this block's rows of the column halos
         if constexpr (LZ) {
@@ -969,14 +987,18 @@ struct Tile {
     // TM: the per-cell coefficients live in tensor memory at `tmem` (the CTA's
     // allocation of NT / 2 columns) instead of registers, see stage_tm(); TM = 2
     // reads the column halos as the rows need them.
-    template <int J, int SYNC, int TM = 0>
+    // GR: this field is one of several that groups of NT threads of the CTA
+    // solve side by side (TM kernels, C = 1): `sm` is the group's own shared
+    // memory, thread indices are group-local, barriers are the group's (csync).
+    template <int J, int SYNC, int TM = 0, bool GR = false>
     __device__ static void run(const PatchParams &prm, real *sm, long long p, int rank,
                                uint32_t tmem = 0)
     {
         constexpr bool SPLIT = SYNC == 1;
         static_assert(TM == 0 || SYNC == 0 || SYNC == 3, "tensor-memory coefficients: SYNC 0 or 3");
+        static_assert(!GR || (TM != 0 && C == 1 && SYNC == 0), "groups: TM kernels, one CTA per field");
         constexpr bool LZ = TM == 2;                    // column halos read as the rows need them
-        const int tid = threadIdx.x, tx = tid % NBX, ty = tid / NBX;
+        const int tid = GR ? (int)(threadIdx.x % NT) : (int)threadIdx.x, tx = tid % NBX, ty = tid / NBX;
         const int a0 = tx * BX, b0 = ty * BY;          // slab-local
         const int g0 = rank * NS;                       // first patch row of the slab
         double *red = reinterpret_cast<double *>(sm + S::WORDS);
@@ -1015,7 +1037,7 @@ struct Tile {
             const int b = (g0 - 1 + rr + N) % N;
             psi[c] = patch_band(band, Nl, prm.tile, p, ox, oy, N, a, b);
         }
-        __syncthreads();
+        csync<GR>();
         const real inv2h = (real)(1.0 / (2.0 * prm.h));
         real A1[BY][BX], A2[BY][BX];
         real vmax = 0;
@@ -1036,7 +1058,7 @@ struct Tile {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
         if ((tid & 31) == 0) red[tid >> 5] = (double)vmax;
-        __syncthreads();
+        csync<GR>();
         double vm = 0.0;
         for (int k = 0; k < NT / 32; ++k) vm = fmax(vm, red[k]);
         if constexpr (C > 1) {
@@ -1076,7 +1098,7 @@ struct Tile {
         k.K = -k.twoh * (J == 1 ? b11 : b22);
         k.halfK = (real)0.5 * k.K;
         // A1, A2 become aE = A1 + b11, aN = A2 + b22 (A_i = dt v_i / 2h)
-        const int warp = tid >> 5;
+        const int warp = (int)(threadIdx.x >> 5);      // lane quarter and columns: CTA-wide warp
         const uint32_t tcol = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 64u * (uint32_t)(warp >> 2);
         if constexpr (TM) {
             // the same values, from v formed again from the psi rows, row by row into
@@ -1106,7 +1128,9 @@ struct Tile {
                     A2[r][c] = fma(A2[r][c], cA, b22);
                 }
         }
-        tile_sync<C>();   // psi tile (and the vmax slots) are dead; the space becomes the exchange buffers
+        // psi tile (and the vmax slots) are dead; the space becomes the exchange buffers
+        if constexpr (C > 1) tile_sync<C>();
+        else csync<GR>();
 
         double f1 = 0.0, f2 = 0.0;
         if constexpr (SYNC == 4) {
@@ -1131,15 +1155,16 @@ struct Tile {
             if constexpr (TM) {
                 const uint32_t par = (uint32_t)(step & 1);
                 real q1 = 0, q2 = 0, qw = 0;
-                stage_tm<J, false, SYNC, false, LZ>(sm, 0, rank, tx, ty, w, s, tcol, k, mbar0, par,
-                                                    prm.status, &live, q1, q2, qw);
+                stage_tm<J, false, SYNC, false, LZ, GR>(sm, 0, rank, tx, ty, w, s, tcol, k, mbar0,
+                                                        par, prm.status, &live, q1, q2, qw);
                 if (step < nb) {
-                    stage_tm<J, true, SYNC, false, LZ>(sm, 1, rank, tx, ty, s, w, tcol, k, mbar0 + 8,
-                                                       par, prm.status, &live, q1, q2, qw);
+                    stage_tm<J, true, SYNC, false, LZ, GR>(sm, 1, rank, tx, ty, s, w, tcol, k,
+                                                           mbar0 + 8, par, prm.status, &live, q1, q2,
+                                                           qw);
                     continue;
                 }
-                stage_tm<J, true, SYNC, true, LZ>(sm, 1, rank, tx, ty, s, w, tcol, k, mbar0 + 8, par,
-                                                  prm.status, &live, q1, q2, qw);
+                stage_tm<J, true, SYNC, true, LZ, GR>(sm, 1, rank, tx, ty, s, w, tcol, k, mbar0 + 8,
+                                                      par, prm.status, &live, q1, q2, qw);
                 p1 += q1;
                 p2 += q2;
                 pw += qw;
@@ -1201,9 +1226,9 @@ struct Tile {
             f1 += __shfl_xor_sync(0xffffffffu, f1, o);
             f2 += __shfl_xor_sync(0xffffffffu, f2, o);
         }
-        __syncthreads();
+        csync<GR>();
         if ((tid & 31) == 0) { red[2 * (tid >> 5)] = f1; red[2 * (tid >> 5) + 1] = f2; }
-        __syncthreads();
+        csync<GR>();
         if (tid == 0) {
             double t1 = 0.0, t2 = 0.0;
             for (int k = 0; k < NT / 32; ++k) { t1 += red[2 * k]; t2 += red[2 * k + 1]; }
@@ -1211,7 +1236,7 @@ struct Tile {
             red[41] = t2;
         }
         if constexpr (C > 1) tile_sync<C>();
-        else __syncthreads();
+        else csync<GR>();
         if (tid == 0 && rank == 0) {
             double t1 = 0.0, t2 = 0.0;
             for (int r = 0; r < C; ++r) { t1 += *rank_ptr<C>(red + 40, r); t2 += *rank_ptr<C>(red + 41, r); }

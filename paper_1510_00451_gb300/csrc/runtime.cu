@@ -61,6 +61,12 @@ struct DevLevel {
     double *B = nullptr, *Koff = nullptr, *base = nullptr, *S = nullptr, *Kstar = nullptr;
     long long *steps = nullptr; // [2P] n_burn + n_avg, then n_avg, of the last solve
     std::vector<SizeClass> cls; // largest total work first
+    // one launch for every class (patch_level.cu): 0 = per-class launches; 1, 2 = the
+    // level kernel with ticket schedule 0 or 1 (largest first, interleaved)
+    int lmode = 0;
+    long long *tickets[2] = {nullptr, nullptr};
+    long long nticket[2] = {0, 0};
+    int lv_clusters = 0;        // resident clusters of the level kernel
     cudaEvent_t fork = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;   // profiling: one pair per launch
     mlsd_surrogate *sur = nullptr;   // attached surrogate (MLSD_SURROGATE chains) or null
@@ -210,6 +216,7 @@ int validate(const mlsd_problem *p)
 }
 
 int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s);
+int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s);
 
 // Patch size rule for levels given without a size: at least 10 points per
 // wavelength of the level's finest diagonal mode and a cell Peclet number of at
@@ -418,6 +425,7 @@ int build(const mlsd_problem *p, cudaStream_t s, mlsd_levels *h)
         CK(cudaMemsetAsync(d.steps, 0, (size_t)h->P * 16, s));
         for (auto &c : d.cls)
             if ((rc = tune_class(h, d, c, s))) return rc;
+        if ((rc = tune_level(h, d, s))) return rc;
     }
     CK(cudaStreamSynchronize(s));
     return MLSD_OK;
@@ -451,17 +459,17 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
         int bx = 0, by = 0, mb = 1, pk = 0, cl = 1, sp = 0, tm = 0;
         char rest[16] = "";
         if (std::sscanf(env, "%dx%d%15s", &bx, &by, rest) >= 2) {
-            for (const char *c = rest; *c; ++c) {
-                if (*c == 'm') mb = std::atoi(c + 1);
-                if (*c == 'c') cl = std::atoi(c + 1);
-                if (*c == 'p') pk = 1;
-                if (*c == 's') sp = 1;
-                if (*c == 'n') sp = 2;
-                if (*c == 'b') sp = 3;
-                if (*c == 'r') sp = 4;
-                if (*c == 'd') sp = 5;
-                if (*c == 't') tm = 1;
-                if (*c == 'l') tm = 2;
+            for (const char *q = rest; *q; ++q) {
+                if (*q == 'm') mb = std::atoi(q + 1);
+                if (*q == 'c') cl = std::atoi(q + 1);
+                if (*q == 'p') pk = 1;
+                if (*q == 's') sp = 1;
+                if (*q == 'n') sp = 2;
+                if (*q == 'b') sp = 3;
+                if (*q == 'r') sp = 4;
+                if (*q == 'd') sp = 5;
+                if (*q == 't') tm = 1;
+                if (*q == 'l') tm = 2;
             }
             for (auto &v : vs)
                 if (v.bx == bx && v.by == by && v.minb == mb && v.packed == pk && v.cluster == cl &&
@@ -535,6 +543,126 @@ int tune_class(mlsd_levels *h, DevLevel &d, SizeClass &c, cudaStream_t s)
     return MLSD_OK;
 }
 
+// Size code of a class in the level kernel (LevelParams::cls), or -1: no task shape.
+int level_code(int n)
+{
+    return n == 32 ? 0 : n == 64 ? 1 : n == 128 ? 2 : n == 256 ? 3 : -1;
+}
+
+// Ticket list of the level kernel: LevelParams::CLUSTER codes per ticket, each
+// (size << 56) | first work item, or -1.  A 256^2 field is one ticket (the
+// same code for every CTA of the cluster); the other classes form CTA tasks of
+// 65 536 cells (one 128^2, four 64^2 or sixteen 32^2 fields), four per ticket,
+// larger patches first.  Schedule 0 puts every 256^2 ticket first; schedule 1
+// spreads them evenly among the others.
+void build_tickets(const DevLevel &d, int sched, std::vector<long long> &out)
+{
+    constexpr int CL = LevelParams::CLUSTER;
+    std::vector<long long> big, cta;
+    for (const auto &c : d.cls) {
+        const int z = level_code(c.n);
+        const long long per = z == 1 ? 4 : z == 0 ? 16 : 1;       // fields per task
+        for (long long it = 0; it < 2 * c.count; it += per)
+            (z == 3 ? big : cta).push_back(((long long)z << 56) | it);
+    }
+    std::stable_sort(cta.begin(), cta.end(), [](long long a, long long b) { return (a >> 56) > (b >> 56); });
+    const long long nb = (long long)big.size(), nq = ((long long)cta.size() + CL - 1) / CL, nt = nb + nq;
+    out.clear();
+    out.reserve((size_t)(CL * nt));
+    long long kb = 0, kq = 0;
+    for (long long i = 0; i < nt; ++i) {
+        const bool take_big = kb < nb && (kq >= nq || sched == 0 || kb * nt < (i + 1) * nb);
+        if (take_big) {
+            for (int r = 0; r < CL; ++r) out.push_back(big[kb]);
+            ++kb;
+        } else {
+            for (int r = 0; r < CL; ++r) {
+                const long long q = CL * kq + r;
+                out.push_back(q < (long long)cta.size() ? cta[q] : -1);
+            }
+            ++kq;
+        }
+    }
+}
+
+int run_patches(mlsd_levels *h, DevLevel &d, const double *Kb, double *S, void *wdump,
+                cudaStream_t s);
+
+// One launch for every class of a mixed-size FP32 level: build both ticket
+// schedules and time the whole level (base kappa I, a fixed 16-step window) as
+// per-class launches and as the level kernel with either schedule; keep the
+// fastest.  MLSD_LEVEL = 0 keeps the per-class launches, 1 or 2 forces the
+// level kernel with schedule 0 or 1.
+int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s)
+{
+    d.lmode = 0;
+    if (h->precision != MLSD_FP32 || d.cls.size() < 2) return MLSD_OK;
+    for (const auto &c : d.cls)
+        if (level_code(c.n) < 0) return MLSD_OK;
+    int force = -1;
+    if (const char *env = std::getenv("MLSD_LEVEL")) force = std::atoi(env);
+    if (force == 0) return MLSD_OK;
+    if (level_kernel_clusters(&d.lv_clusters) != cudaSuccess || d.lv_clusters < 1) {
+        cudaGetLastError();
+        d.lv_clusters = 0;
+        return MLSD_OK;                  // the device cannot hold one cluster of it
+    }
+    int rc;
+    for (int k = 0; k < 2; ++k) {
+        std::vector<long long> t;
+        build_tickets(d, k, t);
+        d.nticket[k] = (long long)t.size() / LevelParams::CLUSTER;
+        if ((rc = dev_alloc(h, (void **)&d.tickets[k], t.size() * sizeof(long long)))) return rc;
+        CK(cudaMemcpy(d.tickets[k], t.data(), t.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    }
+    if (force == 1 || force == 2) {
+        d.lmode = force;
+        return MLSD_OK;
+    }
+    std::vector<double> kb((size_t)h->P * 3);
+    for (long long p = 0; p < h->P; ++p) { kb[3 * p] = h->kappa; kb[3 * p + 1] = 0; kb[3 * p + 2] = h->kappa; }
+    CK(cudaMemcpyAsync(d.B, kb.data(), kb.size() * 8, cudaMemcpyHostToDevice, s));
+    const long long nb0 = h->nb_fixed, na0 = h->na_fixed;
+    const bool prof = h->profile;
+    h->nb_fixed = 0;
+    h->na_fixed = 16;
+    h->profile = false;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int pick = 0;
+    rc = MLSD_OK;
+    for (int mode = 0; mode < 3 && !rc; ++mode) {
+        d.lmode = mode;
+        float t = 1e30f;
+        for (int rep = 0; rep < 3 && !rc; ++rep) {
+            cudaEventRecord(e0, s);
+            rc = run_patches(h, d, d.B, d.S, nullptr, s);
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (!rc && cudaEventSynchronize(e1) == cudaSuccess && rep > 0 &&
+                cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                t = std::min(t, ms);
+        }
+        if (std::getenv("MLSD_TUNE_LOG"))
+            std::fprintf(stderr, "mlsd tune level classes=%d %s: %.4f ms\n", (int)d.cls.size(),
+                         mode == 0 ? "per-class launches" : mode == 1 ? "one launch, 256^2 first"
+                                                                      : "one launch, interleaved", t);
+        if (t < best) { best = t; pick = mode; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->nb_fixed = nb0;
+    h->na_fixed = na0;
+    h->profile = prof;
+    d.lmode = pick;
+    if (rc) return rc;
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    return MLSD_OK;
+}
+
 OffdiagLevel off_of(const DevLevel &d)
 {
     OffdiagLevel o;
@@ -577,6 +705,25 @@ PatchParams patch_params(const mlsd_levels *h, const DevLevel &d, const SizeClas
 int run_patches(mlsd_levels *h, DevLevel &d, const double *Kb, double *S, void *wdump,
                 cudaStream_t s)
 {
+    if (d.lmode > 0) {
+        // every class in one launch of the level kernel
+        LevelParams lp{};
+        for (const auto &c : d.cls) lp.cls[level_code(c.n)] = patch_params(h, d, c, Kb, S, wdump);
+        lp.task = d.tickets[d.lmode - 1];
+        lp.n_tickets = d.nticket[d.lmode - 1];
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (h->profile) {
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            CK(cudaEventRecord(e0, s));
+        }
+        CK(launch_level(lp, d.lv_clusters, s));
+        if (h->profile) {
+            CK(cudaEventRecord(e1, s));
+            d.ev.emplace_back(e0, e1);
+        }
+        return MLSD_OK;
+    }
     const bool fork = d.cls.size() > 1;
     if (fork) CK(cudaEventRecord(d.fork, s));
     for (auto &c : d.cls) {
@@ -681,6 +828,7 @@ int mlsd_level_info(const mlsd_levels *h, int level, mlsd_level_desc *out)
     out->split = c.variant.split;
     out->n_classes = (int)d.cls.size();
     out->coef_tmem = c.variant.tmem;
+    out->level_launch = d.lmode;
     return MLSD_OK;
 }
 

@@ -1,12 +1,13 @@
 """Uneven patch sizes within a level: the patch-size rule and the chain with
-mixed 32^2 ... 256^2 patches (size classes launched concurrently) against the
-oracle with the same per-node sizes."""
+mixed 32^2 ... 256^2 patches (size classes launched concurrently, or every
+patch of a level in one persistent launch) against the oracle with the same
+per-node sizes."""
 import numpy as np
 import pytest
 
 from inputs import flows
 import oracle
-from tests._parity import rel_l2
+from tests._parity import oracle_level, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -150,3 +151,70 @@ def test_full_size_continuous_spectrum_chain_at_sampled_nodes():
                           [(int(p) % N, int(p) // N)], cfl=cfg["cfl"], n_burn_fixed=0,
                           n_avg_fixed=32, node_n=sizes[[p]])[0]
         assert rel_l2(K[p], Kr) < 1e-4, (int(p), sizes[p], K[p], Kr)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_uneven_chain_parity_one_launch(problem, monkeypatch, mode):
+    # every mixed-size level in one persistent launch (forced; schedule 1: 256^2
+    # fields first, 2: interleaved), against the oracle with the same per-node sizes
+    import torch
+    import paper_1510_00451_gb300 as mlsd
+    monkeypatch.setenv("MLSD_LEVEL", str(mode))
+    pr = problem
+    L = len(pr["edges"]) - 1
+    N = pr["N"]
+    lv = mlsd.Levels(pr["spec"], pr["kappa"], N, pr["edges"], [0] * L,
+                     n_burn_fixed=60, n_avg_fixed=40)
+    sizes = np.stack([lv.patch_sizes(l + 1) for l in range(L)], 1)      # [P][L]
+    mixed = [l for l in range(L) if len(set(sizes[:, l])) > 1]
+    assert mixed
+    for l in range(L):
+        assert lv.info(l + 1)["level_launch"] == (mode if l in mixed else 0)
+    K = torch.zeros(N * N, 3, dtype=torch.float64, device="cuda:0")
+    lv.effective_diffusivity(K)
+    assert lv.status() == 0
+    K = K.cpu().numpy()
+    nodes = [(p % N, p // N) for p in range(N * N)]
+    want = oracle.chain(pr["spec"], pr["edges"], [32] * L, N, pr["kappa"], nodes,
+                        n_burn_fixed=60, n_avg_fixed=40, node_n=sizes)
+    for p in range(N * N):
+        assert rel_l2(K[p], want[p]) < 1e-4, (p, K[p], want[p])
+
+
+def _all_sizes_level(monkeypatch, mode):
+    import torch
+    import paper_1510_00451_gb300 as mlsd
+    monkeypatch.setenv("MLSD_LEVEL", str(mode))
+    spec = flows.cellular_two_scale(0.8, 0.5, 4)
+    edges, N, kappa = [1, 4, 8], 5, 0.03
+    P = N * N
+    nmap = np.full((2, P), 32, dtype=np.int32)
+    nmap[1] = np.array([32, 64, 128, 256, 64, 32, 128, 32, 64, 256, 32, 64, 128, 32, 32,
+                        64, 32, 128, 64, 32, 256, 32, 64, 32, 128], dtype=np.int32)
+    lv = mlsd.Levels(spec, kappa, N, edges, [0, 0], patch_n_map=nmap,
+                     n_burn_fixed=40, n_avg_fixed=30)
+    assert lv.info(2)["n_classes"] == 4 and lv.info(2)["level_launch"] == mode
+    B = np.tile([kappa * 1.3, 0.2 * kappa, kappa * 0.9], (P, 1))
+    dev = torch.device("cuda:0")
+    Kb = torch.tensor(B, dtype=torch.float64, device=dev)
+    Ko = torch.zeros_like(Kb)
+    lv.solve_level(2, Kb, Ko)
+    assert lv.status() == 0
+    return nmap, B, Ko.cpu().numpy(), spec, edges, N, kappa
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_one_launch_level_of_all_four_sizes(monkeypatch, mode):
+    # a level mixing 32^2, 64^2, 128^2 and 256^2 patches in one launch: the K of the
+    # per-size launches up to the FP32 grouping of the flux sums (the cells'
+    # arithmetic is the same, but a thread's block of cells, over which it sums
+    # in FP32, may have another shape in the tiling the tuner picked for a size),
+    # and K against the oracle for one patch of each size
+    nmap, B, K1, spec, edges, N, kappa = _all_sizes_level(monkeypatch, mode)
+    _, _, K0, *_ = _all_sizes_level(monkeypatch, 0)
+    for p in range(N * N):
+        assert rel_l2(K1[p], K0[p]) < 1e-6, (p, nmap[1, p], K1[p], K0[p])
+    for p in (0, 1, 2, 3):
+        Kr = oracle_level(spec, edges, [32, int(nmap[1, p])], 2, N, B, [p],
+                          n_burn_fixed=40, n_avg_fixed=30)[0]
+        assert rel_l2(K1[p], Kr) < 1e-4, (p, K1[p], Kr)
