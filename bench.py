@@ -264,7 +264,7 @@ def surrogate_case(N=256, epochs=400, members=4, hidden=256, batch=2048, lr=3e-3
     for m in range(members):
         sur.set_params(m, inputs.mlp_init(mlsd.SUR_IN, hidden, seed * 10 + m))
     t0 = time.perf_counter()
-    losses = S.train(sur, X, Y, epochs, batch, lr, seed=seed, lr_final=1e-5)
+    losses = sur.train(X, Y, epochs, batch, lr, lr_final=1e-5, seed=seed)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del X, Y

@@ -1,14 +1,11 @@
-"""Surrogate workflow over the C ABI: data from the method's own patch solves,
-ensemble training with the library's training kernels, and the surrogate level
-solve with its plain-solve fallback.  Argument marshalling and loop control
-only; every computation runs in libmlsd's kernels.
+"""Surrogate data set from the method's own patch solves (over the C ABI), and
+the relative K error the surrogate is judged by.  Argument marshalling only;
+every computation of the path runs in libmlsd's kernels (training is
+Surrogate.train, mlsd_surrogate_train).
 """
-import math
-import time
-
 import numpy as np
 
-from . import SUR_IN, Levels, Surrogate
+from . import SUR_IN
 
 
 def make_dataset(lv, level, bases):
@@ -33,14 +30,6 @@ def make_dataset(lv, level, bases):
     elif rc != 0:
         raise RuntimeError("patch solves reported error %d" % rc)
     return X, Y
-
-
-def train(sur, X, Y, epochs, batch, lr, seed=0, lr_final=None, augment=False):
-    """Adam on mean-squared error, each member on its own shuffles of the data
-    (with augment, of every row's 8 images under the square's symmetries); the
-    learning rate decays geometrically to lr_final over the run.  Returns the
-    last epoch's mean loss per member (mlsd_surrogate_train)."""
-    return sur.train(X, Y, epochs, batch, lr, lr_final=lr_final, seed=seed, augment=augment)
 
 
 def k_error(K, Kref):

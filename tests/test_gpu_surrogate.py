@@ -276,7 +276,7 @@ def test_trained_surrogate_replaces_most_patch_solves(mlsd, torch_mod):
     sur = mlsd.Surrogate(members=4, hidden=128, max_batch=1024)
     for m in range(4):
         sur.set_params(m, inputs.mlp_init(mlsd.SUR_IN, 128, 90 + m))
-    losses = S.train(sur, X, Y, epochs=80, batch=1024, lr=3e-3, seed=1, lr_final=1e-5)
+    losses = sur.train(X, Y, epochs=80, batch=1024, lr=3e-3, seed=1, lr_final=1e-5)
     assert max(losses) < 0.02                   # asinh targets; the accuracy is checked below
     lt = mlsd.Levels(_octave_band(77, 16, 32), kappa, N, [16.0, 32.0], [64], patch_div=[16],
                      cfl=0.2)
