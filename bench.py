@@ -733,8 +733,14 @@ def uneven_case(n_avg=256):
             "k_eff_tensors_per_s": N * N / t, "setup_s": t_setup,
             "per_level": per_level,
             "largest_class_tiling": [f"{i['tile_bx']}x{i['tile_by']} c{i['cluster']} m{i['min_ctas']}"
-                                     f"{' packed' if i['packed'] else ''}{' split' if i['split'] else ''}"
+                                     f"{' packed' if i['packed'] else ''}"
+                                     f"{' sync%d' % i['split'] if i['split'] else ''}"
+                                     f"{' tmem' if i['coef_tmem'] == 1 else ''}"
+                                     f"{' tmem-lazy' if i['coef_tmem'] == 2 else ''}"
                                      f" n={i['n']}" for i in tiles],
+            "level_launch": ["one launch" if i["level_launch"] else
+                             ("per-size launches" if i["n_classes"] > 1 else "one size")
+                             for i in tiles],
             "finite": bool(torch.isfinite(K).all().item())}
 
 
@@ -761,7 +767,8 @@ def cluster_case(N=32, n_burn=32, n_avg=32):
     i = lv.info(1)
     print(json.dumps({"case": "cluster-profile", "status": rc, "cell_updates_per_s": cu / t,
                       "seconds": t, "tiling": f"{i['tile_bx']}x{i['tile_by']} c{i['cluster']} "
-                      f"m{i['min_ctas']}{' split' if i['split'] else ''}",
+                      f"m{i['min_ctas']}{' sync%d' % i['split'] if i['split'] else ''}"
+                      f"{' tmem' if i['coef_tmem'] == 1 else ''}{' tmem-lazy' if i['coef_tmem'] == 2 else ''}",
                       "finite": bool(torch.isfinite(K).all().item())}), flush=True)
     return 0 if rc == 0 else 1
 
