@@ -727,9 +727,11 @@ def uneven_case(n_avg=256):
                           "cell_updates_per_s": cu_l / (ms * 1e-3) if ms > 0 else None,
                           "fp32_issue_frac": ops / (ms * 1e-3) / issue_peak if ms > 0 else None})
     tiles = [lv.info(l + 1) for l in range(L)]
+    ops = sum(w[0] * OPS_PER_CELL_UPDATE + w[2] * OPS_PER_WINDOW_UPDATE for w in work)
     return {"workload": "continuous spectrum |k|<=256, 8 octave levels, 65536 patches/level, "
                         f"sizes 32^2..256^2 by the size rule, {n_avg}-step window",
             "cell_updates_per_s": cu / t, "seconds": t, "cell_updates": cu,
+            "fp32_issue_frac": ops / t / issue_peak,
             "k_eff_tensors_per_s": N * N / t, "setup_s": t_setup,
             "per_level": per_level,
             "largest_class_tiling": [f"{i['tile_bx']}x{i['tile_by']} c{i['cluster']} m{i['min_ctas']}"
