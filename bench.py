@@ -677,9 +677,10 @@ def uneven_case(n_avg=256):
     256 x 256 macro nodes (65536 patches per level), patch sizes 32^2 .. 256^2
     from the size rule, every level's size classes launched concurrently inside
     one captured graph.  Fixed n_avg-step window per patch (the full window of
-    the 256^2 levels needs ~5e5 steps).  Also per level: the patch kernels'
-    device time (CUDA events around each launch, a second pass outside the
-    graph) and its cell-update rate and FP32-issue fraction."""
+    the 256^2 levels needs ~5e5 steps).  Also per level and per patch size: the
+    patch kernels' device time (CUDA events around each launch, in a second pass
+    outside the graph with the sizes of a level run one after another) and its
+    cell-update rate and FP32-issue fraction."""
     import torch
     import inputs
     import paper_1510_00451_gb300 as mlsd
@@ -706,11 +707,12 @@ def uneven_case(n_avg=256):
     assert lv.status() == 0
     work = [lv.level_work(l + 1) for l in range(L)]
     cu = sum(w[0] for w in work)
-    # per level: kernel time of its patch launches (concurrent classes overlap, so
-    # the sum of their events bounds the level's time from above)
+    # per level and per patch size: a second pass outside the graph with each level's
+    # size classes run one after another (profiling mode 2), so that every class's
+    # events time it alone; the chain above runs them concurrently
     for l in range(L):
         lv.profile_collect(l + 1)
-    lv.profile(True)
+    lv.profile(True, serial_classes=True)
     lv.effective_diffusivity(K)
     torch.cuda.synchronize()
     lv.profile(False)
@@ -719,13 +721,26 @@ def uneven_case(n_avg=256):
     issue_peak = sm_count * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
     per_level = []
     for l in range(L):
-        ms, n = lv.profile_collect(l + 1)
+        cls = lv.profile_collect_classes(l + 1)
+        ms = sum(v[0] for v in cls.values())
+        n = sum(v[1] for v in cls.values())
         cu_l, _, wu_l = work[l]
         ops = cu_l * OPS_PER_CELL_UPDATE + wu_l * OPS_PER_WINDOW_UPDATE
+        classes = []
+        for size, (ms_c, n_c) in sorted(cls.items()):
+            if size == 0 or ms_c <= 0:
+                continue
+            # fixed window without burn-in: every step of every field is inside it
+            cu_c = hist[l][size] * 2 * size * size * n_avg
+            classes.append({"n": size, "patches": hist[l][size], "kernel_ms": ms_c,
+                            "cell_updates_per_s": cu_c / (ms_c * 1e-3),
+                            "fp32_issue_frac": cu_c * (OPS_PER_CELL_UPDATE + OPS_PER_WINDOW_UPDATE)
+                                               / (ms_c * 1e-3) / issue_peak})
         per_level.append({"level": l + 1, "sizes": hist[l], "kernel_ms": ms, "launches": n,
                           "cell_updates": cu_l,
                           "cell_updates_per_s": cu_l / (ms * 1e-3) if ms > 0 else None,
-                          "fp32_issue_frac": ops / (ms * 1e-3) / issue_peak if ms > 0 else None})
+                          "fp32_issue_frac": ops / (ms * 1e-3) / issue_peak if ms > 0 else None,
+                          "classes": classes})
     tiles = [lv.info(l + 1) for l in range(L)]
     ops = sum(w[0] * OPS_PER_CELL_UPDATE + w[2] * OPS_PER_WINDOW_UPDATE for w in work)
     return {"workload": "continuous spectrum |k|<=256, 8 octave levels, 65536 patches/level, "

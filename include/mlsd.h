@@ -540,12 +540,23 @@ int mlsd_level_work(mlsd_levels *h, int level, int64_t *cell_updates_out,
 
 /* Kernel timing of the patch solves: when enabled, every patch-solve launch of
  * the handle is bracketed by CUDA events recorded on the launching stream.
+ * enable = 2 also runs the size classes of a level one after another on the
+ * caller's stream instead of concurrently, so that each class's events time it
+ * alone (per-class rates; the level then takes longer than without profiling).
  * mlsd_profile_collect synchronises, returns the summed device time (ms) and
  * the number of patch-solve launches of the level since the last collect, and
- * clears them.                                                              */
+ * clears them.  mlsd_profile_collect_classes does the same per patch size:
+ * patch_n_out, kernel_ms_out, launches_out [capacity] receive, for each patch
+ * size launched, the size (0 for a launch of every class at once, see
+ * mlsd_level_desc.level_launch), its summed device time and its launches;
+ * *n_written the number of sizes.  MLSD_EINVAL (nothing cleared) when capacity
+ * is too small.  Host arrays, caller-owned.                                 */
 int mlsd_profile(mlsd_levels *h, int enable);
 int mlsd_profile_collect(mlsd_levels *h, int level, double *kernel_ms_out,
                          int64_t *launches_out);
+int mlsd_profile_collect_classes(mlsd_levels *h, int level, int capacity, int32_t *patch_n_out,
+                                 double *kernel_ms_out, int64_t *launches_out,
+                                 int32_t *n_written);
 
 /* Number of CUDA kernels this library has launched since it was loaded
  * (process-wide counter, host side).                                        */

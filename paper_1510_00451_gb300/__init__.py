@@ -90,6 +90,7 @@ _lib.mlsd_level_work.argtypes = [_P, _I, ctypes.POINTER(_L), ctypes.POINTER(_L),
 _lib.mlsd_corrector_energy.argtypes = [_P, _I, _P, _P, _P, _P, _P]
 _lib.mlsd_profile.argtypes = [_P, _I]
 _lib.mlsd_profile_collect.argtypes = [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_L)]
+_lib.mlsd_profile_collect_classes.argtypes = [_P, _I, _I, _P, _P, _P, ctypes.POINTER(ctypes.c_int32)]
 _lib.mlsd_launch_count.argtypes = []
 _lib.mlsd_launch_count.restype = _L
 _lib.mlsd_patch_sizes.argtypes = [_P, _I, _P]
@@ -268,8 +269,21 @@ class Levels:
         return cu.value, ms.value, wu.value
 
 
-    def profile(self, enable=True):
-        _check(_lib.mlsd_profile(self.h, 1 if enable else 0), "mlsd_profile")
+    def profile(self, enable=True, serial_classes=False):
+        _check(_lib.mlsd_profile(self.h, (2 if serial_classes else 1) if enable else 0),
+               "mlsd_profile")
+
+    def profile_collect_classes(self, level, capacity=8):
+        """{patch size: (summed patch-kernel ms, launches)} of the level since the last
+        collect (size 0: a launch of every size at once)."""
+        n = np.zeros(capacity, dtype=np.int32)
+        ms = np.zeros(capacity, dtype=np.float64)
+        cnt = np.zeros(capacity, dtype=np.int64)
+        k = ctypes.c_int32()
+        _check(_lib.mlsd_profile_collect_classes(self.h, int(level), capacity, n.ctypes.data,
+                                                 ms.ctypes.data, cnt.ctypes.data, ctypes.byref(k)),
+               "mlsd_profile_collect_classes")
+        return {int(n[i]): (float(ms[i]), int(cnt[i])) for i in range(k.value)}
 
     def profile_collect(self, level):
         """(summed patch-kernel ms, launches) of the level since the last collect."""

@@ -69,6 +69,7 @@ struct DevLevel {
     int lv_clusters = 0;        // resident clusters of the level kernel
     cudaEvent_t fork = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;   // profiling: one pair per launch
+    std::vector<int> ev_n;      // the launch's patch size (0: every class in one launch)
     mlsd_surrogate *sur = nullptr;   // attached surrogate (MLSD_SURROGATE chains) or null
     double sur_thr = 0;
     bool sur_ran = false;            // a surrogate-mode chain ran since the attach
@@ -94,6 +95,7 @@ struct mlsd_levels {
     int *status = nullptr;
     std::vector<void *> allocs;
     bool profile = false;
+    bool profile_serial = false;     // profiling: a level's size classes one after another
     int n_min = 32, n_max = 256;
     // CUDA graph of the whole Algorithm 3 sequence (captured on first use)
     cudaStream_t cap = nullptr;
@@ -721,10 +723,11 @@ int run_patches(mlsd_levels *h, DevLevel &d, const double *Kb, double *S, void *
         if (h->profile) {
             CK(cudaEventRecord(e1, s));
             d.ev.emplace_back(e0, e1);
+            d.ev_n.push_back(0);
         }
         return MLSD_OK;
     }
-    const bool fork = d.cls.size() > 1;
+    const bool fork = d.cls.size() > 1 && !(h->profile && h->profile_serial);
     if (fork) CK(cudaEventRecord(d.fork, s));
     for (auto &c : d.cls) {
         cudaStream_t cs = fork ? c.stream : s;
@@ -740,6 +743,7 @@ int run_patches(mlsd_levels *h, DevLevel &d, const double *Kb, double *S, void *
         if (h->profile) {
             CK(cudaEventRecord(e1, cs));
             d.ev.emplace_back(e0, e1);
+            d.ev_n.push_back(c.n);
         }
         if (fork) {
             CK(cudaEventRecord(c.join, cs));
@@ -753,6 +757,7 @@ void drop_events(DevLevel &d)
 {
     for (auto &e : d.ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     d.ev.clear();
+    d.ev_n.clear();
 }
 
 }  // namespace
@@ -1067,8 +1072,41 @@ int64_t mlsd_launch_count(void) { return launch_count(); }
 
 int mlsd_profile(mlsd_levels *h, int enable)
 {
-    if (!h) return MLSD_EINVAL;
+    if (!h || enable < 0 || enable > 2) return MLSD_EINVAL;
     h->profile = enable != 0;
+    h->profile_serial = enable == 2;
+    return MLSD_OK;
+}
+
+int mlsd_profile_collect_classes(mlsd_levels *h, int level, int capacity, int32_t *patch_n_out,
+                                 double *kernel_ms_out, int64_t *launches_out, int32_t *n_written)
+{
+    if (!h || level < 1 || level > h->L || capacity < 0 || !n_written ||
+        (capacity > 0 && (!patch_n_out || !kernel_ms_out || !launches_out)))
+        return MLSD_EINVAL;
+    DevLevel &d = h->lev[level - 1];
+    std::vector<int> ns;
+    std::vector<double> ms;
+    std::vector<int64_t> cnt;
+    for (size_t i = 0; i < d.ev.size(); ++i) {
+        CK(cudaEventSynchronize(d.ev[i].second));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, d.ev[i].first, d.ev[i].second));
+        const int n = d.ev_n[i];
+        size_t k = 0;
+        while (k < ns.size() && ns[k] != n) ++k;
+        if (k == ns.size()) { ns.push_back(n); ms.push_back(0.0); cnt.push_back(0); }
+        ms[k] += t;
+        cnt[k] += 1;
+    }
+    if ((int)ns.size() > capacity) return MLSD_EINVAL;   // events kept for a larger call
+    for (size_t k = 0; k < ns.size(); ++k) {
+        patch_n_out[k] = ns[k];
+        kernel_ms_out[k] = ms[k];
+        launches_out[k] = cnt[k];
+    }
+    *n_written = (int32_t)ns.size();
+    drop_events(d);
     return MLSD_OK;
 }
 

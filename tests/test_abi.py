@@ -62,3 +62,13 @@ def test_surrogate_calls_reject_bad_arguments_on_host():
     # training without a handle
     assert L.mlsd_surrogate_train(None, fake, fake, 1024, 1, 128, ctypes.c_float(1e-3),
                                   ctypes.c_float(1e-3), 0, 1, None, None) == -1
+
+
+def test_profiling_calls_reject_bad_arguments_on_host():
+    # no handle, an unknown profiling mode, no output count: rejected before any work
+    import paper_1510_00451_gb300 as m
+    L = m.lib()
+    n = ctypes.c_int32()
+    assert L.mlsd_profile(None, 1) == -1
+    assert L.mlsd_profile_collect_classes(None, 1, 4, None, None, None, ctypes.byref(n)) == -1
+    assert L.mlsd_profile_collect_classes(None, 1, 0, None, None, None, None) == -1

@@ -153,6 +153,36 @@ def test_full_size_continuous_spectrum_chain_at_sampled_nodes():
         assert rel_l2(K[p], Kr) < 1e-4, (int(p), sizes[p], K[p], Kr)
 
 
+def test_profile_by_patch_size(problem):
+    # profiling mode 2 runs a level's sizes one after another: the same K bit for bit
+    # as the concurrent launches, and one timing entry per patch size of each level
+    import torch
+    import paper_1510_00451_gb300 as mlsd
+    pr = problem
+    L = len(pr["edges"]) - 1
+    N = pr["N"]
+    lv = mlsd.Levels(pr["spec"], pr["kappa"], N, pr["edges"], [0] * L,
+                     n_burn_fixed=20, n_avg_fixed=10)
+    K = torch.zeros(N * N, 3, dtype=torch.float64, device="cuda:0")
+    lv.effective_diffusivity(K)
+    K0 = K.clone()
+    for l in range(L):
+        lv.profile_collect_classes(l + 1)
+    lv.profile(True, serial_classes=True)
+    lv.effective_diffusivity(K)
+    torch.cuda.synchronize()
+    lv.profile(False)
+    assert lv.status() == 0
+    assert torch.equal(K, K0)
+    for l in range(L):
+        cls = lv.profile_collect_classes(l + 1)
+        if lv.info(l + 1)["level_launch"]:
+            assert set(cls) == {0}
+        else:
+            assert set(cls) == set(int(n) for n in lv.patch_sizes(l + 1))
+        assert all(ms > 0 and n == 1 for ms, n in cls.values())
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_uneven_chain_parity_one_launch(problem, monkeypatch, mode):
     # every mixed-size level in one persistent launch (forced; schedule 1: 256^2
