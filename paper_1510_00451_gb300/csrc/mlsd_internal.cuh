@@ -42,7 +42,8 @@ struct PatchVariant {
     int n, precision, bx, by, minb, packed, threads;   // packed: both fields per CTA (f32x2)
     int cluster;             // CTAs per patch field (slabs of n / cluster rows), 1 = one CTA
     int split;               // split-phase stage barriers (interior cells overlap the barrier)
-    int tmem;                // 1: the per-cell coefficients live in tensor memory
+    int tmem;                // 1: the per-cell coefficients live in tensor memory; 2: the same,
+                             // with the column halos read as the rows need them
     size_t smem;
     const void *fn;
 };
