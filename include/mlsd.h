@@ -538,6 +538,20 @@ int mlsd_level_work(mlsd_levels *h, int level, int64_t *cell_updates_out,
                     int64_t *window_updates_out, int64_t *max_steps_out,
                     void *cuda_stream);
 
+/* The ticket list of the one-launch level kernel (mlsd_level_desc.level_launch)
+ * for a level with n_classes patch sizes patch_n[i] (32, 64, 128 or 256, each
+ * once) holding patches[i] patches: 4 codes per ticket, one per CTA of a
+ * cluster, each (size << 56) | first work item or -1, size 0..3 for 32 .. 256
+ * and work item 2q + j - 1 for field j of the class's q-th patch.  A 256^2
+ * field is one ticket (the same code 4 times); the other sizes form CTA tasks
+ * of 65 536 cells (one 128^2, four 64^2 or sixteen 32^2 fields from the given
+ * item on), four per ticket, larger sizes first.  schedule 0 puts every 256^2
+ * ticket first, 1 spreads them evenly among the others.  Host only: writes
+ * *n_tickets_out always and codes_out [capacity] (4 per ticket) when it fits;
+ * MLSD_EINVAL for invalid arguments or too small a capacity.                */
+int mlsd_level_schedule(const int32_t *patch_n, const int64_t *patches, int n_classes, int schedule,
+                        int64_t capacity, int64_t *codes_out, int64_t *n_tickets_out);
+
 /* Kernel timing of the patch solves: when enabled, every patch-solve launch of
  * the handle is bracketed by CUDA events recorded on the launching stream.
  * enable = 2 also runs the size classes of a level one after another on the

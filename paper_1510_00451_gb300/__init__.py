@@ -91,6 +91,7 @@ _lib.mlsd_corrector_energy.argtypes = [_P, _I, _P, _P, _P, _P, _P]
 _lib.mlsd_profile.argtypes = [_P, _I]
 _lib.mlsd_profile_collect.argtypes = [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_L)]
 _lib.mlsd_profile_collect_classes.argtypes = [_P, _I, _I, _P, _P, _P, ctypes.POINTER(ctypes.c_int32)]
+_lib.mlsd_level_schedule.argtypes = [_P, _P, _I, _I, _L, _P, ctypes.POINTER(_L)]
 _lib.mlsd_launch_count.argtypes = []
 _lib.mlsd_launch_count.restype = _L
 _lib.mlsd_patch_sizes.argtypes = [_P, _I, _P]
@@ -291,6 +292,23 @@ class Levels:
         _check(_lib.mlsd_profile_collect(self.h, int(level), ctypes.byref(ms), ctypes.byref(n)),
                "mlsd_profile_collect")
         return ms.value, n.value
+
+
+def level_schedule(patch_n, patches, schedule):
+    """Ticket list [tickets][4] (int64 codes) of the one-launch level kernel for a
+    level with the given patch sizes and patch counts (mlsd_level_schedule)."""
+    n = np.ascontiguousarray(patch_n, dtype=np.int32)
+    c = np.ascontiguousarray(patches, dtype=np.int64)
+    nt = _L()
+    _lib.mlsd_level_schedule(n.ctypes.data, c.ctypes.data, len(n), int(schedule), 0, None,
+                             ctypes.byref(nt))
+    if nt.value < 1:
+        raise MlsdError(-1, "mlsd_level_schedule")
+    out = np.zeros((nt.value, 4), dtype=np.int64)
+    _check(_lib.mlsd_level_schedule(n.ctypes.data, c.ctypes.data, len(n), int(schedule),
+                                    out.size, out.ctypes.data, ctypes.byref(nt)),
+           "mlsd_level_schedule")
+    return out
 
 
 def launch_count():

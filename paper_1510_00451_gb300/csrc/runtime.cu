@@ -557,14 +557,15 @@ int level_code(int n)
 // 65 536 cells (one 128^2, four 64^2 or sixteen 32^2 fields), four per ticket,
 // larger patches first.  Schedule 0 puts every 256^2 ticket first; schedule 1
 // spreads them evenly among the others.
-void build_tickets(const DevLevel &d, int sched, std::vector<long long> &out)
+void build_tickets(const std::vector<std::pair<int, long long>> &classes, int sched,
+                   std::vector<long long> &out)
 {
     constexpr int CL = LevelParams::CLUSTER;
     std::vector<long long> big, cta;
-    for (const auto &c : d.cls) {
-        const int z = level_code(c.n);
+    for (const auto &c : classes) {
+        const int z = level_code(c.first);
         const long long per = z == 1 ? 4 : z == 0 ? 16 : 1;       // fields per task
-        for (long long it = 0; it < 2 * c.count; it += per)
+        for (long long it = 0; it < 2 * c.second; it += per)
             (z == 3 ? big : cta).push_back(((long long)z << 56) | it);
     }
     std::stable_sort(cta.begin(), cta.end(), [](long long a, long long b) { return (a >> 56) > (b >> 56); });
@@ -610,9 +611,11 @@ int tune_level(mlsd_levels *h, DevLevel &d, cudaStream_t s)
         return MLSD_OK;                  // the device cannot hold one cluster of it
     }
     int rc;
+    std::vector<std::pair<int, long long>> classes;
+    for (const auto &c : d.cls) classes.emplace_back(c.n, c.count);
     for (int k = 0; k < 2; ++k) {
         std::vector<long long> t;
-        build_tickets(d, k, t);
+        build_tickets(classes, k, t);
         d.nticket[k] = (long long)t.size() / LevelParams::CLUSTER;
         if ((rc = dev_alloc(h, (void **)&d.tickets[k], t.size() * sizeof(long long)))) return rc;
         CK(cudaMemcpy(d.tickets[k], t.data(), t.size() * sizeof(long long), cudaMemcpyHostToDevice));
@@ -1069,6 +1072,27 @@ int mlsd_level_work(mlsd_levels *h, int level, int64_t *cell_updates_out,
 }
 
 int64_t mlsd_launch_count(void) { return launch_count(); }
+
+int mlsd_level_schedule(const int32_t *patch_n, const int64_t *patches, int n_classes, int schedule,
+                        int64_t capacity, int64_t *codes_out, int64_t *n_tickets_out)
+{
+    if (!patch_n || !patches || n_classes < 1 || n_classes > 4 || schedule < 0 || schedule > 1 ||
+        capacity < 0 || !n_tickets_out || (capacity > 0 && !codes_out))
+        return MLSD_EINVAL;
+    std::vector<std::pair<int, long long>> classes;
+    for (int i = 0; i < n_classes; ++i) {
+        if (level_code(patch_n[i]) < 0 || patches[i] < 1) return MLSD_EINVAL;
+        for (const auto &c : classes)
+            if (c.first == patch_n[i]) return MLSD_EINVAL;
+        classes.emplace_back(patch_n[i], (long long)patches[i]);
+    }
+    std::vector<long long> t;
+    build_tickets(classes, schedule, t);
+    *n_tickets_out = (int64_t)t.size() / LevelParams::CLUSTER;
+    if ((int64_t)t.size() > capacity) return MLSD_EINVAL;
+    std::copy(t.begin(), t.end(), codes_out);
+    return MLSD_OK;
+}
 
 int mlsd_profile(mlsd_levels *h, int enable)
 {
