@@ -495,15 +495,16 @@ struct Tile {
 
     // stage() with the per-cell coefficients in tensor memory (the "t" tilings):
     // `tcol` addresses this thread's first column.  Each row's coefficients are
-    // loaded just before the row (loading them one row ahead measured no faster);
-    // the arithmetic and its order are those of
-    // stage(), so both give the same bits.  SYNC = 0 (one barrier per stage) or 3
-    // (bulk row copies between the slabs of a cluster).  FLUX (second stage of a
-    // step inside the averaging window): the flux sums q1 += aE w, q2 += aN w,
-    // qw += w of the new values are formed here, in stage()'s cell order, from
-    // the coefficients already loaded.  LZ: the west and east halo columns are
-    // read in pairs of rows as the row loop reaches them instead of all at once,
-    // so that fewer of them are live (the values are load_halos()').
+    // loaded just before the row (loading them one row ahead measured no
+    // faster); the arithmetic and its order are those of stage(), so both give
+    // the same bits for the same block shape.  SYNC = 0 (one barrier per stage)
+    // or 3 (bulk row copies between the slabs of a cluster).  FLUX (second stage
+    // of a step inside the averaging window): the flux sums q1 += aE w,
+    // q2 += aN w, qw += w of the new values are formed here, in stage()'s cell
+    // order, from the coefficients already loaded.  LZ: the west and east halo
+    // columns are read in pairs of rows as the row loop reaches them instead of
+    // all at once, so that fewer of them are live (the values are
+    // load_halos()').  GR: the field is one of a CTA's groups (see run()).
     template <int J, bool SECOND, int SYNC, bool FLUX = false, bool LZ = false, bool GR = false>
     __device__ __forceinline__ static void stage_tm(real *sm, int buf, int rank, int tx, int ty,
                                                     const real (&x)[BY][BX], real (&out)[BY][BX],
